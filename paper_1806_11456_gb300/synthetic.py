@@ -1,0 +1,415 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/benchmark and the oracle.
+
+This module holds no arithmetic of the discretisation: it builds hexahedral
+mesh topologies (element mapping nodes, face-neighbour tables, boundary tags),
+order maps and flow states sampled from closed-form fields.  Both the CUDA
+library and the oracle receive these arrays as plain data.
+
+Mesh dictionary keys
+--------------------
+dim   : 2 or 3 (2 = one-element-thick extrusion, N3 = 0)
+K     : element count
+M     : mapping order (mapping nodes equispaced on [-1, 1] per direction)
+xmap  : float64 (K, (M+1)**dim, 3) mapping nodes, node (a, b[, c]) at
+        index (c*(M+1) + b)*(M+1) + a
+ftab  : int32 (K, 6, 4) per face (neighbour element or -1, neighbour face,
+        orientation code, boundary tag); faces 4, 5 unused in 2D
+Faces: 0 xi=-1, 1 xi=+1, 2 eta=-1, 3 eta=+1, 4 zeta=-1, 5 zeta=+1.
+Orientation code o maps the first side's face coordinates (s, t) (the two
+tangential reference directions in increasing order) to the second side's:
+bit0 swaps them, bit1 negates the first, bit2 negates the second.
+Boundary tags: 0 interior, 1 freestream, 2 subsonic outflow (far-field
+pressure), 3 free-slip, 4 no-slip adiabatic wall.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+BC_INTERIOR, BC_FREESTREAM, BC_OUTFLOW, BC_SLIP, BC_WALL = 0, 1, 2, 3, 4
+
+
+def flow_params(mach=0.3, re=100.0, pr=0.72, gamma=1.4, ca=0.4, cnu=0.4):
+    """Parameter vector (16 doubles) understood by both implementations.
+
+    0 gamma, 1 Pr, 2 Mach, 3 Re, 4 Sutherland constant (110.4 K / 288.15 K),
+    5 C_a, 6 C_nu, 7..11 freestream conserved state (rho=1, |v|=1 along x,
+    p = 1/(gamma M^2)), 12..15 reserved.
+    """
+    p_inf = 1.0 / (gamma * mach * mach)
+    qinf = [1.0, 1.0, 0.0, 0.0, p_inf / (gamma - 1.0) + 0.5]
+    v = np.zeros(16)
+    v[:12] = [gamma, pr, mach, re, 110.4 / 288.15, ca, cnu] + qinf
+    return v
+
+
+# --------------------------------------------------------------------------
+# meshes
+# --------------------------------------------------------------------------
+def box_mesh(xs, ys, zs=None, periodic=(False, False, False), bc=None):
+    """Structured box of axis-aligned hexahedra on the tensor grid xs x ys x zs.
+
+    zs=None gives a 2D mesh (dim=2).  ``bc`` maps 'xmin','xmax','ymin','ymax',
+    'zmin','zmax' to a boundary tag or to a callable(i_or_j, k) -> tag taking
+    the element's tangential indices, for non-periodic sides.
+    Elements are numbered e = (k*ny + j)*nx + i.
+    """
+    xs, ys = np.asarray(xs, float), np.asarray(ys, float)
+    dim = 2 if zs is None else 3
+    zs = np.asarray([0.0, 1.0] if zs is None else zs, float)
+    nx, ny, nz = len(xs) - 1, len(ys) - 1, len(zs) - 1
+    if dim == 2:
+        nz = 1
+    bc = dict(bc or {})
+    K = nx * ny * nz
+    npe = 8 if dim == 3 else 4
+    xmap = np.zeros((K, npe, 3))
+    ftab = np.full((K, 6, 4), -1, dtype=np.int32)
+    ftab[:, :, 2:] = 0
+
+    def eid(i, j, k):
+        return (k * ny + j) * nx + i
+
+    def tag(side, a, b):
+        t = bc.get(side, BC_FREESTREAM)
+        return int(t(a, b)) if callable(t) else int(t)
+
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                e = eid(i, j, k)
+                if dim == 3:
+                    for c in range(2):
+                        for b in range(2):
+                            for a in range(2):
+                                xmap[e, (c * 2 + b) * 2 + a] = (xs[i + a], ys[j + b], zs[k + c])
+                else:
+                    for b in range(2):
+                        for a in range(2):
+                            xmap[e, b * 2 + a] = (xs[i + a], ys[j + b], 0.0)
+                # neighbours in each direction
+                idx = [i, j, k]
+                ncell = [nx, ny, nz]
+                for d in range(dim):
+                    for side in range(2):
+                        f = 2 * d + side
+                        nb = list(idx)
+                        nb[d] += 1 if side else -1
+                        if 0 <= nb[d] < ncell[d] or periodic[d]:
+                            nb[d] %= ncell[d]
+                            ftab[e, f] = (eid(*nb), 2 * d + (1 - side), 0, BC_INTERIOR)
+                        else:
+                            name = "xyz"[d] + ("max" if side else "min")
+                            tang = [idx[t] for t in range(3) if t != d]
+                            ftab[e, f] = (-1, -1, 0, tag(name, tang[0], tang[1]))
+    return dict(dim=dim, K=K, M=1, xmap=xmap, ftab=ftab)
+
+
+def periodic_box(nx, ny, nz, L=(1.0, 1.0, 1.0), dim=3):
+    """Fully periodic uniform box [0,Lx]x[0,Ly]x[0,Lz] (2D if dim == 2)."""
+    xs = np.linspace(0.0, L[0], nx + 1)
+    ys = np.linspace(0.0, L[1], ny + 1)
+    zs = np.linspace(0.0, L[2], nz + 1) if dim == 3 else None
+    return box_mesh(xs, ys, zs, periodic=(True, True, True))
+
+
+def flat_plate_mesh(nx=60, ny=24, x0=-0.2, x1=1.0, dy0=1e-3, ratio=1.15):
+    """2D flat-plate boundary-layer mesh: uniform in x on [x0, x1] with the
+    leading edge x = 0 at a vertex, geometric growth in y from the wall.
+    Inflow x = x0 and top: freestream; outflow x = x1: far-field pressure;
+    y = 0: free-slip for x < 0, adiabatic no-slip wall for x > 0."""
+    xs = np.linspace(x0, x1, nx + 1)
+    ys = np.concatenate([[0.0], np.cumsum(dy0 * ratio ** np.arange(ny))])
+
+    def wall(i, _k):
+        return BC_WALL if 0.5 * (xs[i] + xs[i + 1]) > 0.0 else BC_SLIP
+
+    return box_mesh(xs, ys, None, bc=dict(xmin=BC_FREESTREAM, xmax=BC_OUTFLOW,
+                                          ymin=wall, ymax=BC_FREESTREAM))
+
+
+_PERMS = [(0, 1, 2), (1, 2, 0), (2, 0, 1), (0, 2, 1), (2, 1, 0), (1, 0, 2)]
+
+
+def rotate_elements(mesh, seed, frac=0.5):
+    """Re-label the local reference axes of a random subset of the elements of
+    a 3D box mesh (axis permutations and reversals), keeping the geometry.
+    Face tables and orientation codes are rebuilt from the vertex positions, so
+    neighbouring elements see each other through non-trivial orientations."""
+    assert mesh["dim"] == 3 and mesh["M"] == 1
+    rng = np.random.default_rng(seed)
+    K = mesh["K"]
+    xmap = mesh["xmap"].copy()
+    for e in range(K):
+        if rng.random() >= frac:
+            continue
+        perm = _PERMS[rng.integers(len(_PERMS))]
+        flips = rng.integers(0, 2, size=3)
+        old = xmap[e].reshape(2, 2, 2, 3)  # [c][b][a]
+        new = np.empty_like(old)
+        for c in range(2):
+            for b in range(2):
+                for a in range(2):
+                    loc = [a, b, c]          # new local index along new axes
+                    src = [0, 0, 0]
+                    for nd in range(3):      # new axis nd is old axis perm[nd]
+                        v = loc[nd]
+                        src[perm[nd]] = 1 - v if flips[nd] else v
+                    new[c, b, a] = old[src[2], src[1], src[0]]
+        # keep a right-handed frame: odd permutations with an even number of
+        # flips (or vice versa) would invert the element, so flip axis 0 once more
+        det = np.linalg.det(np.stack([new[0, 0, 1] - new[0, 0, 0], new[0, 1, 0] - new[0, 0, 0],
+                                      new[1, 0, 0] - new[0, 0, 0]]))
+        if det < 0:
+            new = new[:, :, ::-1].copy()
+        xmap[e] = new.reshape(8, 3)
+    out = dict(mesh)
+    out["xmap"] = xmap
+    out["ftab"] = _faces_from_vertices(xmap, mesh["ftab"])
+    return out
+
+
+def _face_vertices(xm, f):
+    """The 4 corner positions of face f of a trilinear element, in the face's
+    (s, t) corner order (-,-), (+,-), (-,+), (+,+)."""
+    v = xm.reshape(2, 2, 2, 3)  # [c][b][a]
+    d, side = f // 2, f % 2
+    ta, tb = [t for t in range(3) if t != d]
+    out = []
+    for bt in range(2):
+        for at in range(2):
+            idx = [0, 0, 0]
+            idx[d] = side
+            idx[ta] = at
+            idx[tb] = bt
+            out.append(v[idx[2], idx[1], idx[0]])
+    return np.array(out)
+
+
+def _faces_from_vertices(xmap, ftab_old):
+    """Rebuild neighbour faces and orientation codes by matching face corners.
+    Periodic neighbours are matched up to the periodic translation: the old
+    table supplies which element pairs touch."""
+    K = xmap.shape[0]
+    cent = xmap.mean(axis=1)
+    new_tab = np.full_like(ftab_old, -1)
+    new_tab[:, :, 2:] = 0
+
+    # old faces of the axis-aligned box are named by their outward direction;
+    # a re-labelled face is matched to the old one through its centroid
+    def outward_dir(e, f):
+        fv = _face_vertices(xmap[e], f)
+        c = fv.mean(axis=0) - cent[e]
+        d = int(np.argmax(np.abs(c)))
+        return 2 * d + (1 if c[d] > 0 else 0)
+
+    new_of_old = np.zeros((K, 6), dtype=int)
+    for e in range(K):
+        for f in range(6):
+            new_of_old[e, outward_dir(e, f)] = f
+    for e in range(K):
+        for f in range(6):
+            fo = outward_dir(e, f)
+            nb, nbf_old, _, tg = ftab_old[e, fo]
+            if nb < 0:
+                new_tab[e, f] = (-1, -1, 0, tg)
+                continue
+            nbf = new_of_old[nb, nbf_old]
+            A = _face_vertices(xmap[e], f)
+            B = _face_vertices(xmap[nb], nbf)
+            # remove the (periodic) translation between the two faces
+            B = B - B.mean(axis=0) + A.mean(axis=0)
+            code = None
+            for o in range(8):
+                ok = True
+                for bt in range(2):
+                    for at in range(2):
+                        s, t = 2 * at - 1, 2 * bt - 1
+                        s2, t2 = (t, s) if (o & 1) else (s, t)
+                        if o & 2:
+                            s2 = -s2
+                        if o & 4:
+                            t2 = -t2
+                        ia, ib = (s2 + 1) // 2, (t2 + 1) // 2
+                        if np.linalg.norm(A[bt * 2 + at] - B[ib * 2 + ia]) > 1e-9:
+                            ok = False
+                if ok:
+                    code = o
+                    break
+            assert code is not None, "face corners do not match"
+            new_tab[e, f] = (nb, nbf, code, 0)
+    return new_tab
+
+
+# --------------------------------------------------------------------------
+# order maps
+# --------------------------------------------------------------------------
+def uniform_orders(K, dim, N):
+    o = np.full((K, 3), N, dtype=np.int32)
+    if dim == 2:
+        o[:, 2] = 0
+    return o
+
+
+def random_orders(K, dim, lo, hi, seed):
+    rng = np.random.default_rng(seed)
+    o = rng.integers(lo, hi + 1, size=(K, 3)).astype(np.int32)
+    if dim == 2:
+        o[:, 2] = 0
+    return o
+
+
+def layout_offsets(orders, dim):
+    """Node count per element and its prefix sum (element-blocked layout)."""
+    n = orders.astype(np.int64) + 1
+    if dim == 2:
+        n[:, 2] = 1
+    nn = n[:, 0] * n[:, 1] * n[:, 2]
+    off = np.concatenate([[0], np.cumsum(nn)])
+    return nn, off
+
+
+# --------------------------------------------------------------------------
+# states
+# --------------------------------------------------------------------------
+def _gauss(n):
+    return np.polynomial.legendre.leggauss(n)
+
+
+def node_coordinates(mesh, orders):
+    """Physical coordinates of every element's tensor Gauss nodes, node-major
+    (total_nodes, 3): used only to sample closed-form fields."""
+    dim, M = mesh["dim"], mesh["M"]
+    nn, off = layout_offsets(orders, dim)
+    X = np.zeros((off[-1], 3))
+    eq = np.linspace(-1.0, 1.0, M + 1)
+
+    def lag(x):
+        L = np.ones((len(x), M + 1))
+        for a in range(M + 1):
+            for b in range(M + 1):
+                if b != a:
+                    L[:, a] *= (x - eq[b]) / (eq[a] - eq[b])
+        return L
+
+    for e in range(mesh["K"]):
+        n = orders[e] + 1
+        if dim == 2:
+            n = [n[0], n[1], 1]
+        x0, x1 = _gauss(n[0])[0], _gauss(n[1])[0]
+        x2 = _gauss(n[2])[0] if dim == 3 else np.zeros(1)
+        L0, L1 = lag(x0), lag(x1)
+        if dim == 3:
+            L2 = lag(x2)
+            P = mesh["xmap"][e].reshape(M + 1, M + 1, M + 1, 3)
+            pts = np.einsum("ia,jb,kc,cbax->kjix", L0, L1, L2, P)
+        else:
+            P = mesh["xmap"][e].reshape(M + 1, M + 1, 3)
+            pts = np.einsum("ia,jb,bax->jix", L0, L1, P)[None]
+            pts = pts.copy()
+            pts[..., 2] = x2[:, None, None]
+        X[off[e]:off[e + 1]] = pts.reshape(-1, 3)
+    return X
+
+
+def conserved(rho, u, v, w, p, gamma):
+    return np.stack([rho, rho * u, rho * v, rho * w, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w)])
+
+
+def to_blocked(fields, orders, dim):
+    """(nvar, total_nodes) node-major fields -> element-blocked flat vector."""
+    nvar = fields.shape[0]
+    nn, off = layout_offsets(orders, dim)
+    out = np.empty(off[-1] * nvar)
+    for e in range(len(nn)):
+        out[nvar * off[e]: nvar * off[e + 1]] = fields[:, off[e]:off[e + 1]].reshape(-1)
+    return out
+
+
+def from_blocked(vec, orders, dim, nvar=5):
+    nn, off = layout_offsets(orders, dim)
+    out = np.empty((nvar, off[-1]))
+    for e in range(len(nn)):
+        out[:, off[e]:off[e + 1]] = vec[nvar * off[e]: nvar * off[e + 1]].reshape(nvar, nn[e])
+    return out
+
+
+def manufactured_phases(seed):
+    rng = np.random.default_rng(seed)
+    return rng.uniform(0.0, 2.0 * np.pi, size=(4, 2, 2))
+
+
+def manufactured_primitives(X, phases, mach, gamma, amp=0.1):
+    """rho, u, v, w, p of the smooth periodic field
+    g_m(x,y) = sum_{k=1,2} sin(2 pi k x + phi_mk) cos(2 pi k y + psi_mk):
+    rho = 1 + a g_0, u = 1 + a g_1, v = a g_2, w = 0, p = (1 + a g_3)/(gamma M^2)."""
+    x, y = X[:, 0], X[:, 1]
+
+    def g(m):
+        s = 0.0
+        for k in (1, 2):
+            s = s + np.sin(2 * np.pi * k * x + phases[m, k - 1, 0]) * np.cos(2 * np.pi * k * y + phases[m, k - 1, 1])
+        return s
+
+    rho = 1.0 + amp * g(0)
+    u = 1.0 + amp * g(1)
+    v = amp * g(2)
+    w = np.zeros_like(x)
+    p = (1.0 + amp * g(3)) / (gamma * mach * mach)
+    return rho, u, v, w, p
+
+
+def manufactured_state(mesh, orders, seed, mach, gamma, amp=0.1):
+    X = node_coordinates(mesh, orders)
+    rho, u, v, w, p = manufactured_primitives(X, manufactured_phases(seed), mach, gamma, amp)
+    return to_blocked(conserved(rho, u, v, w, p, gamma), orders, mesh["dim"])
+
+
+def freestream_state(mesh, orders, prm):
+    nn, off = layout_offsets(orders, mesh["dim"])
+    q = np.tile(np.asarray(prm[7:12])[:, None], (1, off[-1]))
+    return to_blocked(q, orders, mesh["dim"])
+
+
+def perturbed_state(mesh, orders, prm, seed, amp=0.05):
+    """Freestream plus independent seeded perturbations of rho, u, v, (w), p at
+    every node (not smooth: exercises every term of the operator)."""
+    rng = np.random.default_rng(seed)
+    gamma, mach = prm[0], prm[2]
+    nn, off = layout_offsets(orders, mesh["dim"])
+    Nt = off[-1]
+    rho = 1.0 + amp * rng.uniform(-1, 1, Nt)
+    u = 1.0 + amp * rng.uniform(-1, 1, Nt)
+    v = amp * rng.uniform(-1, 1, Nt)
+    w = amp * rng.uniform(-1, 1, Nt) if mesh["dim"] == 3 else np.zeros(Nt)
+    p = (1.0 + amp * rng.uniform(-1, 1, Nt)) / (gamma * mach * mach)
+    return to_blocked(conserved(rho, u, v, w, p, gamma), orders, mesh["dim"])
+
+
+def random_source(mesh, orders, seed, amp=1e-2):
+    rng = np.random.default_rng(seed + 1000)
+    nn, off = layout_offsets(orders, mesh["dim"])
+    s = amp * rng.uniform(-1, 1, (5, off[-1]))
+    if mesh["dim"] == 2:
+        s[3] = 0.0
+    return to_blocked(s, orders, mesh["dim"])
+
+
+# --------------------------------------------------------------------------
+# named workloads
+# --------------------------------------------------------------------------
+def config_box_c1(seed=0):
+    """4x4x1 periodic unit box, N=3, manufactured state (Mach 0.3, Re 100)."""
+    mesh = periodic_box(4, 4, 1)
+    prm = flow_params(mach=0.3, re=100.0)
+    orders = uniform_orders(mesh["K"], 3, 3)
+    q = manufactured_state(mesh, orders, seed, prm[2], prm[0])
+    return mesh, orders, prm, q
+
+
+def config_flat_plate_c2(N=7):
+    """60x24 stretched 2D flat plate, uniform N, freestream start (Mach 0.2, Re 1e5)."""
+    mesh = flat_plate_mesh()
+    prm = flow_params(mach=0.2, re=1e5)
+    orders = uniform_orders(mesh["K"], 2, N)
+    q = freestream_state(mesh, orders, prm)
+    return mesh, orders, prm, q

@@ -1,0 +1,534 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix
+(no GPU).  Each test names the property it checks; a plausible mistake in the
+oracle (dropped term, wrong sign or index, transposed operand) fails one."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from oracle import manufactured as man
+from oracle import oracle as orc
+from paper_1806_11456_gb300 import synthetic as syn
+
+
+# ---------------------------------------------------------------------------
+# 1-D tables: Gauss rule, Lagrange basis (Sec. 2, Gauss-point DGSEM)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", range(1, 14))
+def test_gauss_matches_numpy_and_is_exact(n):
+    x, w = orc.gauss(n)
+    xr, wr = np.polynomial.legendre.leggauss(n)
+    assert np.allclose(x, xr, atol=2e-15, rtol=0)
+    assert np.allclose(w, wr, atol=2e-15, rtol=0)
+    assert abs(w.sum() - 2.0) < 1e-14
+    for k in range(2 * n):  # exact for degree <= 2n-1
+        exact = 0.0 if k % 2 else 2.0 / (k + 1)
+        assert abs(np.dot(w, x ** k) - exact) < 1e-13
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 8, 11])
+def test_lagrange_derivative_exact_on_polynomials(n):
+    x, _ = orc.gauss(n)
+    rng = np.random.default_rng(n)
+    c = rng.normal(size=n)  # degree n-1 polynomial
+    for xe in (-1.0, -0.3, 0.77, 1.0):
+        l, dl = orc.lagrange_at(n, xe)
+        p = np.polynomial.polynomial.polyval(x, c)
+        assert abs(l @ p - np.polynomial.polynomial.polyval(xe, c)) < 1e-12
+        dp = np.polynomial.polynomial.polyval(xe, np.polynomial.polynomial.polyder(c))
+        assert abs(dl @ p - dp) < 1e-10 * max(1.0, abs(dp))
+
+
+# ---------------------------------------------------------------------------
+# transfers (Sec. 3.1, L2 restriction / interpolation)
+# ---------------------------------------------------------------------------
+def _orders(K, dim, lo, hi, seed):
+    return syn.random_orders(K, dim, lo, hi, seed)
+
+
+def test_restriction_of_prolongation_is_identity():
+    K, dim = 6, 3
+    oc = _orders(K, dim, 1, 4, 1)
+    of = oc + np.random.default_rng(2).integers(0, 3, size=oc.shape).astype(np.int32)
+    v = np.random.default_rng(3).normal(size=orc.nodes_total(oc, dim) * 5)
+    back = orc.transfer(dim, of, oc, orc.transfer(dim, oc, of, v))
+    assert np.max(np.abs(back - v)) < 1e-13
+
+
+def test_restriction_is_l2_projection_and_exact_on_low_degree():
+    # a polynomial of degree <= N in each direction restricted from P keeps its
+    # nodal values (projection of an element of the target space is itself)
+    mesh = syn.periodic_box(2, 1, 1)
+    P = np.array([[6, 5, 4], [5, 6, 6]], dtype=np.int32)
+    N = np.array([[3, 2, 4], [1, 4, 2]], dtype=np.int32)
+    Xf = syn.node_coordinates(mesh, P)
+    Xc = syn.node_coordinates(mesh, N)
+    rng = np.random.default_rng(7)
+
+    def field(X, elem_of_node):
+        out = np.zeros(len(X))
+        for idx in range(len(X)):
+            e = elem_of_node[idx]
+            c0 = 2 * X[idx, 0] - (2 * e + 1)  # local xi of element e (width 0.5)
+            c1 = 2 * X[idx, 1] - 1
+            c2 = 2 * X[idx, 2] - 1
+            out[idx] = sum(coef[e][a, b, c] * c0 ** a * c1 ** b * c2 ** c
+                           for a in range(N[e, 0] + 1) for b in range(N[e, 1] + 1) for c in range(N[e, 2] + 1))
+        return out
+
+    coef = [rng.normal(size=(N[e, 0] + 1, N[e, 1] + 1, N[e, 2] + 1)) for e in range(2)]
+    _, offf = syn.layout_offsets(P, 3)
+    _, offc = syn.layout_offsets(N, 3)
+    ef = np.repeat(np.arange(2), np.diff(offf))
+    ec = np.repeat(np.arange(2), np.diff(offc))
+    ff = field(Xf, ef)
+    fc = field(Xc, ec)
+    vf = syn.to_blocked(np.tile(ff, (5, 1)), P, 3)
+    vc = syn.to_blocked(np.tile(fc, (5, 1)), N, 3)
+    got = orc.transfer(3, P, N, vf)
+    assert np.max(np.abs(got - vc)) < 1e-12
+    # L2 property: the projection error is orthogonal to the coarse space --
+    # restricting the prolongation of the restriction changes nothing
+    v = rng.normal(size=orc.nodes_total(P, 3) * 5)
+    r1 = orc.transfer(3, P, N, v)
+    r2 = orc.transfer(3, P, N, orc.transfer(3, N, P, r1))
+    assert np.max(np.abs(r1 - r2)) < 1e-13
+
+
+def test_chained_restriction_equals_direct():
+    dim = 2
+    P = np.array([[7, 6, 0], [5, 7, 0]], dtype=np.int32)
+    mid = np.array([[5, 4, 0], [4, 6, 0]], dtype=np.int32)
+    low = np.array([[2, 3, 0], [1, 2, 0]], dtype=np.int32)
+    v = np.random.default_rng(11).normal(size=orc.nodes_total(P, dim) * 5)
+    chain = orc.transfer(dim, mid, low, orc.transfer(dim, P, mid, v))
+    direct = orc.transfer(dim, P, low, v)
+    assert np.max(np.abs(chain - direct)) < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# Roe and viscous fluxes (Sec. 2 numerical fluxes, Appendix A)
+# ---------------------------------------------------------------------------
+def _rand_state(rng, prm):
+    g, M = prm[0], prm[2]
+    rho = 1 + 0.3 * rng.uniform(-1, 1)
+    u = rng.uniform(-1, 1, 3)
+    p = (1 + 0.3 * rng.uniform(-1, 1)) / (g * M * M)
+    return np.array([rho, *(rho * u), p / (g - 1) + 0.5 * rho * u @ u])
+
+
+def test_roe_consistency_and_antisymmetry():
+    prm = syn.flow_params(mach=0.3)
+    rng = np.random.default_rng(0)
+    for _ in range(50):
+        qL, qR = _rand_state(rng, prm), _rand_state(rng, prm)
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        assert np.allclose(orc.roe(prm, qL, qL, n), orc.adv_flux(prm, qL, n), rtol=1e-14, atol=1e-12)
+        f1 = orc.roe(prm, qL, qR, n)
+        f2 = orc.roe(prm, qR, qL, -n)
+        assert np.allclose(f1, -f2, rtol=1e-13, atol=1e-12)
+
+
+def test_roe_exact_for_single_shear_and_contact_jump():
+    # a pure contact (density jump, same u_n and p) moving right: upwinding
+    # picks the left state's flux exactly
+    prm = syn.flow_params(mach=0.3)
+    g, M = prm[0], prm[2]
+    p = 1.0 / (g * M * M)
+    u = np.array([0.4, 0.0, 0.0])
+    qL = np.array([1.0, *(1.0 * u), p / (g - 1) + 0.5 * 1.0 * u @ u])
+    qR = np.array([1.3, *(1.3 * u), p / (g - 1) + 0.5 * 1.3 * u @ u])
+    n = np.array([1.0, 0.0, 0.0])
+    assert np.allclose(orc.roe(prm, qL, qR, n), orc.adv_flux(prm, qL, n), rtol=1e-13, atol=1e-12)
+
+
+def test_viscous_flux_closed_form():
+    # uniform shear u = a y: tau_xy = mu a, energy flux u tau + heat flux
+    prm = syn.flow_params(mach=0.3, pr=0.72)
+    g, M, Pr, S = prm[0], prm[2], prm[1], prm[4]
+    rho, uvel, p = 1.1, 0.7, 1.0 / (g * M * M) * 1.2
+    q = np.array([rho, rho * uvel, 0, 0, p / (g - 1) + 0.5 * rho * uvel ** 2])
+    T = g * M * M * p / rho
+    mu = T ** 1.5 * (1 + S) / (T + S)
+    G = np.zeros(12)
+    G[0 * 3 + 1] = 0.5      # du/dy
+    G[3 * 3 + 1] = 0.25     # dT/dy
+    f = orc.visc_flux(prm, q, G, np.array([0.0, 1.0, 0.0]))
+    hc = mu / ((g - 1) * Pr * M * M)
+    assert np.allclose(f, [0, mu * 0.5, 0, 0, uvel * mu * 0.5 + hc * 0.25], rtol=1e-14, atol=1e-14)
+    # normal compression: tau_xx = 2 mu du/dx - 2/3 mu du/dx
+    G = np.zeros(12)
+    G[0] = 0.3
+    f = orc.visc_flux(prm, q, G, np.array([1.0, 0.0, 0.0]))
+    assert abs(f[1] - (4.0 / 3.0) * mu * 0.3) < 1e-14
+
+
+# ---------------------------------------------------------------------------
+# the residual (Sec. 2): free stream, conservation, convergence, isolation
+# ---------------------------------------------------------------------------
+def _scale(mesh, orders, prm, seed=1):
+    qp = syn.perturbed_state(mesh, orders, prm, seed)
+    return np.max(np.abs(orc.operator_A(mesh, orders, prm, qp)))
+
+
+MESHES = {
+    "periodic3d_mixed": lambda: (syn.periodic_box(3, 2, 2), 3, 1, 5),
+    "rotated3d_mixed": lambda: (syn.rotate_elements(syn.periodic_box(2, 2, 2), seed=4, frac=0.75), 3, 1, 4),
+    "plate2d_mixed": lambda: (syn.box_mesh(np.linspace(-0.2, 1, 5), [0, 0.05, 0.12, 0.3],
+                                           bc=dict(xmin=1, xmax=2, ymin=3, ymax=1)), 2, 1, 7),
+}
+
+
+@pytest.mark.parametrize("name", list(MESHES))
+@pytest.mark.parametrize("isolated", [False, True])
+def test_free_stream_preservation(name, isolated):
+    mesh, dim, lo, hi = MESHES[name]()
+    orders = syn.random_orders(mesh["K"], dim, lo, hi, 5)
+    prm = syn.flow_params(mach=0.3, re=100.0)
+    q = syn.freestream_state(mesh, orders, prm)
+    r = orc.residual(mesh, orders, prm, q, None, isolated)
+    assert np.max(np.abs(r)) <= 1e-13 * _scale(mesh, orders, prm)
+
+
+@pytest.mark.parametrize("name", ["periodic3d_mixed", "rotated3d_mixed"])
+def test_discrete_conservation(name):
+    mesh, dim, lo, hi = MESHES[name]()
+    orders = syn.random_orders(mesh["K"], dim, lo, hi, 9)
+    prm = syn.flow_params(mach=0.3, re=100.0)
+    q = syn.perturbed_state(mesh, orders, prm, 3)
+    r = orc.residual(mesh, orders, prm, q)
+    _, J = orc.geometry(mesh, orders)
+    nn, off = syn.layout_offsets(orders, dim)
+    tot, mag = np.zeros(5), np.zeros(5)
+    for e in range(mesh["K"]):
+        n = orders[e] + 1
+        w = [np.polynomial.legendre.leggauss(int(k))[1] for k in n]
+        W = np.einsum("k,j,i->kji", w[2], w[1], w[0]).reshape(-1)
+        blk = r[5 * off[e]:5 * off[e + 1]].reshape(5, -1) * W * J[off[e]:off[e + 1]]
+        tot += blk.sum(1)
+        mag += np.abs(blk).sum(1)
+    assert np.all(np.abs(tot) <= 1e-13 * mag.max())
+    # and a wrong sign on either side of a mortar would not conserve: the
+    # per-element sums themselves are far from zero
+    assert mag.max() > 1e-3
+
+
+def test_spectral_convergence_manufactured():
+    mesh = syn.periodic_box(4, 4, 1)
+    prm = syn.flow_params(mach=0.3, re=100.0)
+    ph = syn.manufactured_phases(0)
+    errs = []
+    Ns = list(range(2, 9))
+    for N in Ns:
+        o = syn.uniform_orders(mesh["K"], 3, N)
+        o[:, 2] = 1
+        X = syn.node_coordinates(mesh, o)
+        q = syn.manufactured_state(mesh, o, 0, prm[2], prm[0])
+        S = syn.to_blocked(man.source_at(X, ph, prm[2], prm[0], prm[3], prm[1], prm[4]), o, 3)
+        errs.append(np.max(np.abs(orc.residual(mesh, o, prm, q, S))))
+    slope = np.polyfit(Ns, np.log10(errs), 1)[0]
+    assert slope < -0.25, (errs, slope)
+    assert errs[-1] < 1e-2 * errs[0]
+
+
+def test_isolated_equals_strong_form():
+    """The isolated weak form (own flux on the boundary) equals the strong-form
+    collocation derivative (1/J) sum_d D_d (Ja^d . F) with gradients
+    (1/J) sum_d D_d (Ja^d U): summation by parts is exact under Gauss quadrature."""
+    mesh = syn.rotate_elements(syn.periodic_box(2, 1, 1), seed=2, frac=1.0)
+    orders = np.array([[3, 4, 2], [2, 3, 5]], dtype=np.int32)
+    prm = syn.flow_params(mach=0.3, re=50.0)
+    q = syn.perturbed_state(mesh, orders, prm, 8)
+    A_or = orc.operator_A(mesh, orders, prm, q, isolated=True)
+    Ja, J = orc.geometry(mesh, orders)
+    nn, off = syn.layout_offsets(orders, 3)
+    g, M = prm[0], prm[2]
+
+    def dmat(n):  # D_ij = l_j'(x_i) via numpy polynomial fits
+        x = np.polynomial.legendre.leggauss(n)[0]
+        D = np.zeros((n, n))
+        for j in range(n):
+            e = np.zeros(n)
+            e[j] = 1
+            c = np.polynomial.polynomial.polyfit(x, e, n - 1)
+            D[:, j] = np.polynomial.polynomial.polyval(x, np.polynomial.polynomial.polyder(c))
+        return D
+
+    for e in range(2):
+        n = orders[e] + 1
+        D = [dmat(int(k)) for k in n]
+        sl = slice(off[e], off[e + 1])
+        qe = q[5 * off[e]:5 * off[e + 1]].reshape(5, n[2], n[1], n[0])
+        Jae = Ja[sl].reshape(n[2], n[1], n[0], 3, 3)
+        Je = J[sl].reshape(n[2], n[1], n[0])
+        rho = qe[0]
+        U = np.stack([qe[1] / rho, qe[2] / rho, qe[3] / rho,
+                      g * M * M * (g - 1) * (qe[4] - 0.5 * (qe[1] ** 2 + qe[2] ** 2 + qe[3] ** 2) / rho) / rho])
+
+        def deriv(f, d):  # f[..., k, j, i]
+            if d == 0:
+                return np.einsum("ia,...kja->...kji", D[0], f)
+            if d == 1:
+                return np.einsum("ja,...kai->...kji", D[1], f)
+            return np.einsum("ka,...aji->...kji", D[2], f)
+
+        G = np.zeros((4, 3) + U.shape[1:])
+        for d in range(3):
+            for c in range(3):
+                G[:, c] += deriv(U * Jae[..., d, c], d)
+        G /= Je
+        A = np.zeros_like(qe)
+        for d in range(3):
+            Fd = np.zeros_like(qe)
+            for kk in range(n[2]):
+                for jj in range(n[1]):
+                    for ii in range(n[0]):
+                        nv = Jae[kk, jj, ii, d]
+                        Gp = G[:, :, kk, jj, ii].reshape(12)
+                        Fd[:, kk, jj, ii] = orc.adv_flux(prm, qe[:, kk, jj, ii], nv) - \
+                            orc.visc_flux(prm, qe[:, kk, jj, ii], Gp, nv) / prm[3]
+            A += deriv(Fd, d)
+        A /= Je
+        got = A_or[5 * off[e]:5 * off[e + 1]].reshape(A.shape)
+        assert np.max(np.abs(got - A)) <= 1e-12 * np.max(np.abs(A))
+
+
+def test_gradient_exact_for_linear_fields_inside():
+    # continuous linear primitive field: BR1 averages equal the trace, the
+    # lifting vanishes and the gradient is exact in elements away from the
+    # boundary (N >= 2: the energy of a linear velocity field is quadratic)
+    mesh = syn.box_mesh([0, 0.3, 0.7, 1.0], [0, 0.4, 0.5, 1.0], [0, 0.5, 0.6, 1.0])
+    orders = syn.random_orders(mesh["K"], 3, 2, 4, 2)
+    prm = syn.flow_params(mach=0.3)
+    g, M = prm[0], prm[2]
+    X = syn.node_coordinates(mesh, orders)
+    rho = np.full(len(X), 1.0)
+    u = 1 + 0.2 * X[:, 0] - 0.1 * X[:, 1] + 0.3 * X[:, 2]
+    v = 0.1 * X[:, 0] + 0.4 * X[:, 2]
+    w = -0.2 * X[:, 1] + 0.05 * X[:, 0]
+    T = 1 + 0.1 * X[:, 0] + 0.2 * X[:, 1] - 0.3 * X[:, 2]
+    p = rho * T / (g * M * M)
+    q = syn.to_blocked(syn.conserved(rho, u, v, w, p, g), orders, 3)
+    G = orc.gradients(mesh, orders, prm, q)
+    exact = np.array([[0.2, -0.1, 0.3], [0.1, 0, 0.4], [0.05, -0.2, 0], [0.1, 0.2, -0.3]]).reshape(12)
+    _, off = syn.layout_offsets(orders, 3)
+    center = (1 * 3 + 1) * 3 + 1
+    assert np.max(np.abs(G[off[center]:off[center + 1]] - exact)) < 1e-12
+
+
+def test_viscous_divergence_zero_for_linear_velocity():
+    # constant rho and p, linear velocity: the stress is constant, so the
+    # viscous contribution to the momentum equations vanishes in the interior;
+    # the difference of the residuals at Re and at 2 Re isolates it.  BR1's
+    # face flux also uses the neighbours' gradients, so the checked element is
+    # two layers away from the boundary.
+    edges = [0, 0.15, 0.3, 0.7, 0.85, 1.0]
+    mesh = syn.box_mesh(edges, edges, edges)
+    orders = syn.random_orders(mesh["K"], 3, 2, 3, 3)
+    X = syn.node_coordinates(mesh, orders)
+    p1 = syn.flow_params(mach=0.3, re=10.0)
+    p2 = syn.flow_params(mach=0.3, re=20.0)
+    g, M = p1[0], p1[2]
+    rho = np.ones(len(X))
+    u = 1 + 0.2 * X[:, 1]
+    v = 0.1 * X[:, 0]
+    w = np.zeros(len(X))
+    p = np.full(len(X), 1 / (g * M * M))
+    q = syn.to_blocked(syn.conserved(rho, u, v, w, p, g), orders, 3)
+    r1 = orc.residual(mesh, orders, p1, q)
+    r2 = orc.residual(mesh, orders, p2, q)
+    _, off = syn.layout_offsets(orders, 3)
+    center = (2 * 5 + 2) * 5 + 2
+    nn = off[center + 1] - off[center]
+    d = (r1 - r2)[5 * off[center]:5 * off[center + 1]].reshape(5, nn)
+    # momentum equations see no viscous force for a constant stress (T is
+    # constant, so mu is constant); the energy equation sees div(u.tau) != 0
+    assert np.max(np.abs(d[1:4])) < 1e-10
+    assert np.max(np.abs(d[4])) > 1e-4
+
+
+# ---------------------------------------------------------------------------
+# RK3 smoother (Sec. 3.1, Williamson)
+# ---------------------------------------------------------------------------
+def test_rk3_stability_polynomial():
+    for z in (-0.3, -1.1, -2.0, 0.4):
+        q = 1.0
+        g = 0.0
+        for k in range(3):
+            g = orc.RK3_A[k] * g + z * q  # dt * lambda * q with dt*lambda = z
+            q = q + orc.RK3_B[k] * g
+        assert abs(q - (1 + z + z * z / 2 + z ** 3 / 6)) < 1e-15
+
+
+# ---------------------------------------------------------------------------
+# FAS V-cycle (Algorithm 1)
+# ---------------------------------------------------------------------------
+def test_fas_two_level_reduces_to_coarse_grid_correction(monkeypatch):
+    """With a linear operator, no smoothing and an exact coarse solve, one
+    two-level FAS cycle is the textbook correction Q + P Ac^{-1} R (S - A Q).
+    Exercises the coarse source (eq FAScoarseSource), eps = Q - Q0 and the
+    correction sign."""
+    rng = np.random.default_rng(0)
+    dim = 2
+    of = np.array([[2, 2, 0], [2, 1, 0]], dtype=np.int32)
+    oc = orc.level_orders(of, 1, dim)
+    nf, nc = orc.nodes_total(of, dim) * 5, orc.nodes_total(oc, dim) * 5
+    Af = rng.normal(size=(nf, nf)) + nf * np.eye(nf)
+    Pm = np.array([orc.transfer(dim, oc, of, np.eye(nc)[i]) for i in range(nc)]).T
+    Rm = np.array([orc.transfer(dim, of, oc, np.eye(nf)[i]) for i in range(nf)]).T
+    Ac = Rm @ Af @ Pm + np.eye(nc)
+    mats = {nf: Af, nc: Ac}
+
+    def fake_res(mesh, o, prm, q, s=None, isolated=False):
+        A = mats[len(q)]
+        return (s if s is not None else 0.0) - A @ q
+
+    def fake_smooth(mesh, o, prm, q, S, sweeps):
+        if sweeps == 0:
+            return q
+        return np.linalg.solve(mats[len(q)], S)  # exact solve
+
+    monkeypatch.setattr(orc, "residual", fake_res)
+    monkeypatch.setattr(orc, "smooth", fake_smooth)
+    q = rng.normal(size=nf)
+    S = rng.normal(size=nf)
+    got = orc.fas_vcycle({"dim": dim}, of, None, q, S, 0, 0, 1)
+    want = q + Pm @ np.linalg.solve(Ac, Rm @ (S - Af @ q))
+    assert np.max(np.abs(got - want)) < 1e-12
+
+
+def test_converged_state_is_a_vcycle_fixed_point():
+    mesh = syn.periodic_box(2, 2, 1, dim=2)
+    orders = syn.uniform_orders(mesh["K"], 2, 3)
+    prm = syn.flow_params(mach=0.3, re=100.0)
+    q = syn.perturbed_state(mesh, orders, prm, 2)
+    S = -orc.residual(mesh, orders, prm, q)  # A(q) = S exactly: q is the solution
+    q1 = orc.fas_vcycle(mesh, orders, prm, q, S, 1, 1, 2)
+    assert np.max(np.abs(q1 - q)) < 1e-11 * np.max(np.abs(q))
+
+
+# ---------------------------------------------------------------------------
+# tau estimation (Sec. 3.2.1, 3.3.1)
+# ---------------------------------------------------------------------------
+def test_tau_vanishes_for_free_stream_and_for_fields_constant_along_direction():
+    mesh = syn.box_mesh(np.linspace(0, 1, 4), np.linspace(0, 1, 3), None, periodic=(True, True, True))
+    orders = syn.random_orders(mesh["K"], 2, 3, 6, 1)
+    prm = syn.flow_params(mach=0.3, re=100.0)
+    qf = syn.freestream_state(mesh, orders, prm)
+    t = orc.tau_estimate(mesh, orders, prm, qf, None)
+    meas = t[t >= 0]
+    assert meas.size > 0 and np.max(meas) < 1e-11
+    # a field that depends on x only: coarsening eta changes nothing
+    X = syn.node_coordinates(mesh, orders)
+    g, M = prm[0], prm[2]
+    rho = 1 + 0.1 * np.sin(2 * np.pi * X[:, 0])
+    u = 1 + 0.1 * np.cos(2 * np.pi * X[:, 0])
+    p = (1 + 0.05 * np.sin(2 * np.pi * X[:, 0] + 1)) / (g * M * M)
+    q = syn.to_blocked(syn.conserved(rho, u, 0 * u, 0 * u, p, g), orders, 2)
+    t = orc.tau_estimate(mesh, orders, prm, q, None, dir_mask=3)
+    assert np.max(t[:, 1][t[:, 1] >= 0]) < 1e-10
+    assert np.max(t[:, 0][t[:, 0] >= 0]) > 1e-4   # the x-direction does see it
+
+
+def test_tau_decays_spectrally_along_direction():
+    mesh = syn.periodic_box(6, 6, 1, dim=2)
+    orders = syn.uniform_orders(mesh["K"], 2, 8)
+    prm = syn.flow_params(mach=0.3, re=100.0)
+    q = syn.manufactured_state(mesh, orders, 0, prm[2], prm[0], amp=0.05)
+    t = orc.tau_estimate(mesh, orders, prm, q, None, dir_mask=3)
+    for i in range(2):
+        series = t[:, i, 1:8].max(axis=0)
+        slope = np.polyfit(np.arange(1, 8), np.log10(series), 1)[0]
+        assert slope < -0.3, series
+
+
+# ---------------------------------------------------------------------------
+# adaptation (Sec. 3.3.2; jump rules Sec. 4.1.2, 4.2.1)
+# ---------------------------------------------------------------------------
+def _brute_select(ttab, P, tau_max, n_min, n_max, dim):
+    """Independent restatement: linear-log fit with numpy.polyfit, enumeration
+    with itertools, ranking by sorting."""
+    fns = []
+    for i in range(dim):
+        pts = [(N, ttab[i][N]) for N in range(1, int(P[i])) if ttab[i][N] > 0]
+        coef = None
+        if len(pts) >= 2:
+            b, a = np.polyfit([p[0] for p in pts], [math.log10(p[1]) for p in pts], 1)
+            if b < 0:
+                coef = (a, b)
+        last = ttab[i][int(P[i]) - 1] if P[i] >= 2 and ttab[i][int(P[i]) - 1] >= 0 else 0.0
+        fns.append((coef, last, int(P[i])))
+
+    def tv(i, N):
+        coef, last, Pi = fns[i]
+        if N < Pi:
+            return max(ttab[i][N], 0.0)
+        return last if coef is None else 10 ** (coef[0] + coef[1] * N)
+
+    def pick(ranges):
+        cands = []
+        for N in itertools.product(*ranges):
+            t = sum(tv(i, N[i]) for i in range(dim))
+            if t < tau_max:
+                cands.append((int(np.prod([n + 1 for n in N])), t, N))
+        return sorted(cands)[0][2] if cands else None
+
+    inner = [range(n_min, min(int(P[i]) - 1, n_max) + 1) for i in range(dim)]
+    N = pick(inner) if all(len(r) for r in inner) else None
+    if N is None:
+        N = pick([range(n_min, n_max + 1)] * dim)
+    if N is None:
+        N = (n_max,) * dim
+    return list(N)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_order_selection_matches_brute_force(dim):
+    rng = np.random.default_rng(dim)
+    mism = 0
+    for trial in range(300):
+        P = rng.integers(2, 7, size=3)
+        ttab = np.full((3, 16), -1.0)
+        for i in range(dim):
+            rate = rng.uniform(0.1, 1.5)
+            base = 10 ** rng.uniform(-4, 0)
+            for N in range(1, P[i]):
+                ttab[i, N] = base * 10 ** (-rate * N) * 10 ** rng.uniform(-0.3, 0.3)
+        tau_max = 10 ** rng.uniform(-6, -1)
+        got = orc.select_orders(ttab, P, tau_max, 1, 9, dim)[:dim]
+        want = _brute_select(ttab, P, tau_max, 1, 9, dim)
+        if got != want:
+            mism += 1
+    # polyfit and the explicit normal equations can differ in the last bits;
+    # a flipped comparison at such a tie is the only allowed disagreement
+    assert mism <= 2
+
+
+def test_jump_rules_fix_point():
+    mesh = syn.box_mesh(np.linspace(0, 1, 7), np.linspace(0, 1, 6), None)
+    rng = np.random.default_rng(1)
+    orders = syn.random_orders(mesh["K"], 2, 1, 9, 4)
+    lim = orc.limit_jumps(mesh, orders, "2d")
+    assert np.all(lim >= orders)
+    assert np.array_equal(orc.limit_jumps(mesh, lim, "2d"), lim)
+    ft = mesh["ftab"]
+    for e in range(mesh["K"]):
+        for f in range(4):
+            nb, fn, o, _ = ft[e, f]
+            if nb >= 0:
+                for i in range(2):
+                    assert abs(int(lim[e, i]) - int(lim[nb, i])) <= 1
+    mesh3 = syn.rotate_elements(syn.box_mesh(np.linspace(0, 1, 4), np.linspace(0, 1, 4), np.linspace(0, 1, 3)), 3)
+    o3 = syn.random_orders(mesh3["K"], 3, 2, 9, 5)
+    lim3 = orc.limit_jumps(mesh3, o3, "3d")
+    assert np.all(lim3 >= o3)
+    for e in range(mesh3["K"]):
+        for f in range(6):
+            nb, fn, o, _ = mesh3["ftab"][e, f]
+            if nb >= 0:
+                m = orc.face_direction_map(f, fn, o)
+                for i in range(3):
+                    assert lim3[e, i] >= (2 * lim3[nb, m[i]]) // 3
+    del rng
