@@ -1,0 +1,221 @@
+/*
+ * dg.h -- C ABI of the GB300 DGSEM p-multigrid library.
+ *
+ * The library evaluates the discontinuous Galerkin spectral element (DGSEM)
+ * discretisation of the compressible Navier-Stokes equations on hexahedral
+ * meshes whose elements carry per-direction polynomial orders (N1,N2,N3), and
+ * runs the nonlinear FAS p-multigrid cycle, the anisotropic truncation-error
+ * estimate and the order adaptation built on it (Rueda-Ramirez et al.,
+ * "A p-multigrid strategy with anisotropic p-adaptation based on truncation
+ * errors for high-order DG methods").
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Every function returns an int status: DG_OK (0) or a negative DG_E*
+ *    code; dg_last_error() then gives a thread-local message.
+ *  - Handles (dg_mesh) are library-owned: create/destroy pairs.
+ *  - State arrays (q, s, r) are caller-owned DEVICE pointers to doubles in the
+ *    element-blocked layout: element e occupies 5*nn_e doubles starting at
+ *    5*off_e (off_e from dg_mesh_layout), variable-major inside the element:
+ *    q[5*off_e + v*nn_e + node], node = (k*n2 + j)*n1 + i over the element's
+ *    tensor Legendre-Gauss nodes, n_d = N_d + 1 (n3 = 1 in 2D).  The five
+ *    variables are the conserved (rho, rho u, rho v, rho w, rho e).
+ *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream.  Calls are asynchronous on that stream unless they return host
+ *    data (then they synchronise it).  No call frees caller memory.
+ *  - Internal scratch (face traces, multigrid levels) is allocated by the
+ *    library on dg_mesh_create / first use and freed by dg_mesh_destroy.
+ *  - Invalid arguments give DG_EINVAL without touching any output.
+ */
+#ifndef DG_H
+#define DG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DG_OK 0
+#define DG_EINVAL (-1)
+#define DG_ENOMEM (-2)
+#define DG_ECUDA (-3)
+#define DG_EDIVERGED (-4)
+#define DG_ENOTCONVERGED (-5)
+
+/* dg_residual flags */
+#define DG_ISOLATED 1 /* the isolated operator F-hat (own flux on the element boundary) */
+#define DG_NORM 2     /* also return max |r| over all nodes and variables */
+
+/* Boundary tags of the face table. */
+#define DG_BC_INTERIOR 0
+#define DG_BC_FREESTREAM 1 /* ghost = freestream state */
+#define DG_BC_OUTFLOW 2    /* ghost = interior state with the far-field pressure */
+#define DG_BC_SLIP 3       /* ghost = mirrored normal velocity, no viscous flux */
+#define DG_BC_WALL 4       /* no-slip adiabatic wall: ghost = negated velocity, no heat flux */
+
+/*
+ * Mesh description (all host pointers, copied by dg_mesh_create).
+ *  dim     2 (one-element-thick extrusion, N3 = 0, faces 4/5 ignored) or 3.
+ *  K       number of hexahedral elements.
+ *  M       order of the element mapping x(xi) (Sec. 2, mapping equation); the
+ *          mapping nodes are equispaced on [-1,1] per direction.
+ *  xmap    K x (M+1)^dim x 3 doubles; node (a,b[,c]) of element e at
+ *          e*(M+1)^dim + (c*(M+1)+b)*(M+1)+a.  2D: x,y used, z = zeta.
+ *  ftab    K x 6 x 4 int32 per face (faces 0/1: xi=-1/+1, 2/3: eta, 4/5: zeta):
+ *          (neighbour element or -1, neighbour face, orientation, bc tag).
+ *          Orientation o maps this side's face coordinates (s,t) -- the two
+ *          tangential reference directions in increasing order -- to the
+ *          neighbour's: bit0 swaps them, bit1 negates the first, bit2 the
+ *          second.  Each interior face must be listed consistently from both sides.
+ *  params  0 gamma, 1 Pr, 2 Mach, 3 Re, 4 Sutherland constant S/T_ref,
+ *          5 C_a, 6 C_nu (CFL constants), 7..11 freestream conserved state,
+ *          12..15 reserved (0).  Nondimensionalisation of Appendix A.
+ */
+typedef struct {
+  int32_t dim;
+  int32_t K;
+  int32_t M;
+  const double* xmap;
+  const int32_t* ftab;
+  double params[16];
+} dg_mesh_desc;
+
+typedef struct dg_mesh dg_mesh;
+
+/*
+ * dg_mesh_create -- build the mesh for a per-element order map.
+ * Implements the geometry of Sec. 2 (mapping, covariant/contravariant metrics,
+ * cross-product form in 2D, invariant curl form in 3D) at the order map's
+ * Gauss nodes, the face/mortar tables and the device tables.
+ *  orders  K x 3 int32 host array (N1,N2,N3), 1 <= N_d <= 12 (N3 = 0 in 2D);
+ *          3D elements are limited to (N1+1)(N2+1)(N3+1) <= 729 nodes.
+ *  out     receives the handle.
+ * Errors: DG_EINVAL (bad sizes/orders/face table), DG_ENOMEM, DG_ECUDA.
+ */
+int dg_mesh_create(const dg_mesh_desc* desc, const int32_t* orders, dg_mesh** out);
+
+/* dg_mesh_destroy -- free the handle and all library-owned device memory. */
+int dg_mesh_destroy(dg_mesh* mesh);
+
+/*
+ * dg_mesh_layout -- node count of the layout (state arrays hold 5x that many
+ * doubles) and, if elem_offsets != NULL, the K+1 node offsets off_e (host).
+ */
+int dg_mesh_layout(const dg_mesh* mesh, int64_t* total_nodes, int64_t* elem_offsets);
+
+/*
+ * dg_residual -- r = S - A(Q), A = M^{-1} F(Q) (Sec. 3.1, nonlinRes; F the
+ * DGSEM operator of Sec. 2, DiscretNSElem, with Roe and BR1 fluxes and
+ * projection mortars on faces whose sides carry different orders).
+ *  q, r    device arrays (5 x total_nodes), r may not alias q.
+ *  s       device source array or NULL for S = 0.
+ *  flags   DG_ISOLATED: the isolated operator (Sec. 3.2.1); DG_NORM: write
+ *          max |r| to *rnorm_host (synchronises the stream).
+ */
+int dg_residual(dg_mesh* mesh, const double* q, const double* s, double* r, int flags,
+                double* rnorm_host, void* stream);
+
+/*
+ * dg_cfl_dt -- the explicit time step of Sec. 2: minimum over Gauss points
+ * and reference directions with N_i > 0 of C_a h_i / ((|v|+c) N_i^2) and
+ * C_nu h_i^2 / (nu N_i^4), h_i = 2/|a^i|, nu = mu(T)/(rho Re).
+ * Result on the host in *dt (synchronises the stream).
+ */
+int dg_cfl_dt(dg_mesh* mesh, const double* q, double* dt, void* stream);
+
+/*
+ * dg_smooth -- `sweeps` steps of the Williamson low-storage RK3 smoother
+ * (Sec. 3.1) on dQ/dt = S - A(Q), the CFL step recomputed at every sweep.
+ *  q       device state, updated in place.  s: device source or NULL.
+ */
+int dg_smooth(dg_mesh* mesh, double* q, const double* s, int sweeps, void* stream);
+
+/* Multigrid parameters (Sec. 3.1, Algorithm 1). */
+typedef struct {
+  int32_t beta1;      /* pre-smoothing sweeps per level */
+  int32_t beta2;      /* post-smoothing sweeps per level */
+  int32_t beta_c;     /* sweeps at the coarsest level (replaces pre + post) */
+  int32_t direction;  /* -1: isotropic coarsening; 0/1/2: coarsen that reference direction only */
+  int32_t coarsest;   /* lowest level order (1 = N_coarse = 1) */
+  int32_t delta_n;    /* order drop between consecutive levels (Sec. 3.1 uses 1); <= 0 means 1 */
+  int32_t reserved[2];
+} dg_mg_params;
+
+/* What a cycle reports. */
+typedef struct {
+  int32_t levels;         /* levels visited */
+  int32_t residual_evals; /* operator evaluations issued */
+  double dof_evals;       /* sum over evaluations of the level's degrees of freedom (5 x nodes) */
+  double rnorm;           /* max |S - A(Q)| on the finest level after the cycle (if requested) */
+} dg_cycle_report;
+
+/*
+ * dg_pmg_vcycle -- one FAS V-cycle (Algorithm 1) from the mesh's orders down
+ * to level `coarsest` with high-order coarsening (Sec. 3.3.3: at level l each
+ * coarsened direction is capped at l; levels top, top - delta_n, ... >=
+ * coarsest), L2 restriction / interpolation between consecutive levels, coarse source S_c = A_c(I Q) + I r (eq FAScoarseSource),
+ * correction Q += I (Q_c - Q_c0) (eqs FASIterError, FASCorrectSol).
+ *  q       device finest-level state, updated in place.  s: source or NULL.
+ *  rep     optional report; with want_norm != 0 rep->rnorm is filled
+ *          (synchronises the stream).
+ */
+int dg_pmg_vcycle(dg_mesh* mesh, double* q, const double* s, const dg_mg_params* mg,
+                  int want_norm, dg_cycle_report* rep, void* stream);
+
+/*
+ * dg_tau_estimate -- anisotropic truncation-error estimate (Sec. 3.2.1 eqs
+ * TruncError! and AnisTruncError, Sec. 3.3.1): for every reference direction i
+ * in dir_mask and every level l < P_i, with Q_l the chained L2 restriction of
+ * q in direction i only and S_l that of s,
+ *   tau_i = R^l(Q_l) - I R^P(q)   (with_correction = 1)  or  R^l(Q_l)  (0),
+ * R = S - A with the isolated operator (isolated = 1) or the full operator.
+ *  tau_host  K x 3 x 16 doubles (host): tau_host[(e*3+i)*16 + N] = max over
+ *            the element's nodes and variables of |tau_i| at order N_i = N;
+ *            -1 where nothing was measured (N >= P_i of that element).
+ * Synchronises the stream.
+ */
+int dg_tau_estimate(dg_mesh* mesh, const double* q, const double* s, int dir_mask,
+                    int with_correction, int isolated, double* tau_host, void* stream);
+
+/* Adaptation parameters (Sec. 3.3.2 and the order-jump rules of Sec. 4). */
+typedef struct {
+  double tau_max;      /* truncation-error threshold */
+  int32_t n_min;       /* lowest order allowed after adaptation */
+  int32_t n_max;       /* highest order allowed */
+  int32_t cap;         /* stage cap (multi-stage), <= 0 for none */
+  int32_t jump_rule;   /* 0 none, 1: |N+ - N-| <= 1, 2: N+ >= floor(2/3 N-) */
+  int32_t conform_tag; /* boundary tag whose touching elements are made conforming, -1 none */
+  int32_t reserved[3];
+} dg_adapt_params;
+
+/*
+ * dg_adapt -- new order map from a tau table (host, layout of
+ * dg_tau_estimate) and the mesh's current orders as the reference P:
+ * linear-log least-squares extrapolation of each directional estimate,
+ * inner-map search then full-map search for the fewest degrees of freedom
+ * with sum_i t_i(N_i) < tau_max (ties: smaller estimate, then
+ * lexicographically smaller orders), N_max where nothing qualifies, then the
+ * order-jump fix-point (only raises orders).
+ *  new_orders  K x 3 int32 host output.
+ * Pure host computation; deterministic.
+ */
+int dg_adapt(const dg_mesh* mesh, const double* tau_host, const dg_adapt_params* ap,
+             int32_t* new_orders);
+
+/*
+ * dg_transfer_state -- move a state between two meshes of the same geometry
+ * and topology but different order maps (per element and direction: L2
+ * projection when the order drops, interpolation when it rises).
+ *  q_from  device array in `from`'s layout; q_to device array in `to`'s.
+ */
+int dg_transfer_state(const dg_mesh* from, const double* q_from, const dg_mesh* to, double* q_to,
+                      void* stream);
+
+const char* dg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DG_H */

@@ -825,6 +825,8 @@ static void own_surface(const mesh_t* m, const work_t* W, int e, int nv, const d
 /*
  * or_residual: r = S - A(Q), A = M^{-1} F(Q) (isolated = 0) or
  * A = M^{-1} F-hat(Q) (isolated = 1).  S may be NULL (zero source).
+ * isolated = 2 returns the volume term alone (M^{-1} of the volume integral,
+ * surface integrals dropped): the magnitude scale of the operator's terms.
  * Returns 0 on success.
  */
 int or_residual(int dim, int K, int M, const double* xmap, const int* ftab, const int* ord,
@@ -833,8 +835,9 @@ int or_residual(int dim, int K, int M, const double* xmap, const int* ftab, cons
   prm_t P = unpack(prm);
   work_t W;
   setup(&m, &W, &P, q);
+  int iso_grad = (isolated == 1);
   /* ---- BR1 pass 1: U* on every face, projected to each side ---- */
-  if (!isolated) all_mortars(&m, &W, &P, 1);
+  if (!iso_grad) all_mortars(&m, &W, &P, 1);
   /* ---- gradients ---- */
   for (int e = 0; e < K; ++e) {
     int n[3];
@@ -849,7 +852,7 @@ int or_residual(int dim, int K, int M, const double* xmap, const int* ftab, cons
           for (int c = 0; c < 3; ++c) Fd[((size_t)nd * 3 + d) * 12 + v * 3 + c] = Ja[d * 3 + c] * U[v];
     }
     double* Fs = (double*)calloc((size_t)W.fo[K * 6] * 12 + 1, sizeof(double));
-    if (isolated) {
+    if (iso_grad) {
       own_surface(&m, &W, e, 12, Fd, Fs);
     } else {
       for (int f = 0; f < face_count(dim); ++f) {
@@ -874,6 +877,7 @@ int or_residual(int dim, int K, int M, const double* xmap, const int* ftab, cons
   }
   /* ---- BR1 pass 2 + Roe: numerical flux on every face ---- */
   if (!isolated) all_mortars(&m, &W, &P, 2);
+  /* (the volume-only mode keeps the BR1 gradient of the full operator) */
   /* ---- flux divergence, residual ---- */
   for (int e = 0; e < K; ++e) {
     int n[3];
@@ -892,7 +896,9 @@ int or_residual(int dim, int K, int M, const double* xmap, const int* ftab, cons
       }
     }
     double* Fs;
-    if (isolated) {
+    if (isolated == 2) {
+      Fs = (double*)calloc((size_t)W.fo[K * 6] * 5 + 1, sizeof(double));
+    } else if (isolated) {
       Fs = (double*)calloc((size_t)W.fo[K * 6] * 5 + 1, sizeof(double));
       own_surface(&m, &W, e, 5, Fd, Fs);
     } else {

@@ -36,6 +36,7 @@ def lib():
         path = build_oracle.build()
         L = ctypes.CDLL(path)
         L.or_residual.argtypes = [ctypes.c_int] * 3 + [_dp, _ip, _ip, _dp, _dp, _dp, _dp, ctypes.c_int]
+        L.or_residual.restype = ctypes.c_int
         L.or_gradients.argtypes = [ctypes.c_int] * 3 + [_dp, _ip, _ip, _dp, _dp, _dp]
         L.or_geometry.argtypes = [ctypes.c_int] * 3 + [_dp, _ip, _dp, _dp]
         L.or_node_coords.argtypes = [ctypes.c_int] * 3 + [_dp, _ip, _dp]
@@ -98,6 +99,16 @@ def residual(mesh, orders, prm, q, s=None, isolated=False):
 
 def operator_A(mesh, orders, prm, q, isolated=False):
     return -residual(mesh, orders, prm, q, None, isolated)
+
+
+def volume_scale(mesh, orders, prm, q):
+    """max |volume term of A(q)|: the magnitude of the operator's terms, the
+    scale against which residual differences are measured."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    r = np.zeros_like(q)
+    lib().or_residual(mesh["dim"], mesh["K"], mesh["M"], _d(mesh["xmap"]), _i(mesh["ftab"]), _i(orders),
+                      _d(prm), _d(q), ctypes.cast(None, _dp), r.ctypes.data_as(_dp), 2)
+    return float(np.max(np.abs(r)))
 
 
 def gradients(mesh, orders, prm, q):
@@ -199,8 +210,9 @@ def n_levels(orders, dim, direction=None):
 # ---------------------------------------------------------------------------
 # FAS V-cycle (Algorithm 1)
 # ---------------------------------------------------------------------------
-def fas_vcycle(mesh, orders, prm, q, s, beta1, beta2, beta_c, direction=None, coarsest=1):
-    """One FAS V-cycle from the finest level (orders) down to level `coarsest`.
+def fas_vcycle(mesh, orders, prm, q, s, beta1, beta2, beta_c, direction=None, coarsest=1, delta_n=1):
+    """One FAS V-cycle from the finest level (orders) down to level `coarsest`,
+    the order dropping by delta_n per level (Sec. 3.1 uses 1).
 
     Follows Algorithm 1 with the sign of eq FASIterError (eps = Q - Q0).  At the
     finest level S is the physical source; below it S = A(Q0) + r (eq
@@ -208,7 +220,12 @@ def fas_vcycle(mesh, orders, prm, q, s, beta1, beta2, beta_c, direction=None, co
     in place of pre + post smoothing.  Returns the new finest-level Q."""
     dim = mesh["dim"]
     top = n_levels(orders, dim, direction)
-    lv_orders = {lv: level_orders(orders, lv, dim, direction) for lv in range(coarsest, top + 1)}
+    seq = [top]
+    while seq[-1] - delta_n >= coarsest:
+        seq.append(seq[-1] - delta_n)
+    lv_orders = {lv: level_orders(orders, lv, dim, direction) for lv in seq}
+    below = {seq[k]: seq[k + 1] for k in range(len(seq) - 1)}
+    bottom = seq[-1]
 
     def cycle(level, q, r_or_s, finest):
         o = lv_orders[level]
@@ -217,14 +234,14 @@ def fas_vcycle(mesh, orders, prm, q, s, beta1, beta2, beta_c, direction=None, co
         else:
             S = operator_A(mesh, o, prm, q) + r_or_s
         q0 = q.copy()
-        if level == coarsest:
+        if level == bottom:
             q = smooth(mesh, o, prm, q, S, beta_c)
         else:
             q = smooth(mesh, o, prm, q, S, beta1)
-            oc = lv_orders[level - 1]
+            oc = lv_orders[below[level]]
             qc = transfer(dim, o, oc, q)
             rc = transfer(dim, o, oc, residual(mesh, o, prm, q, S))
-            epsc = cycle(level - 1, qc, rc, False)
+            epsc = cycle(below[level], qc, rc, False)
             q = q + transfer(dim, oc, o, epsc)
             q = smooth(mesh, o, prm, q, S, beta2)
         if finest:
@@ -412,8 +429,10 @@ def limit_jumps(mesh, orders, rule="2d", conform_tag=None):
                     other = o[nb, m[i]]
                     if rule == "2d":
                         need = other - 1
-                    else:
+                    elif rule == "3d":
                         need = (2 * other) // 3
+                    else:
+                        need = 0
                     if conform_tag is not None and touches[e] and touches[nb]:
                         need = max(need, other)
                     if need > new[e, i]:
@@ -431,4 +450,6 @@ def adapt_orders(mesh, P, ttab, tau_max, n_min, n_max, cap=None, rule="2d", conf
     new = np.zeros((K, 3), dtype=np.int32)
     for e in range(K):
         new[e] = select_orders(ttab[e], P[e], tau_max, n_min, n_max, dim, cap)
+    if rule is None and conform_tag is None:
+        return new
     return limit_jumps(mesh, new, rule, conform_tag)

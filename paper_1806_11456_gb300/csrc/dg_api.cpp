@@ -1,0 +1,527 @@
+// C ABI entry points and host orchestration of the multigrid cycle, the tau
+// estimate and the order adaptation.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dg_internal.h"
+
+namespace dg {
+
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+
+#define DG_TRY(x)                 \
+  do {                            \
+    int _rc = (x);                \
+    if (_rc != DG_OK) return _rc; \
+  } while (0)
+
+static int check_desc(const dg_mesh_desc* d, const int32_t* orders) {
+  if (!d || !orders || !d->xmap || !d->ftab) {
+    set_error("null argument");
+    return DG_EINVAL;
+  }
+  if (d->dim != 2 && d->dim != 3) {
+    set_error("dim must be 2 or 3");
+    return DG_EINVAL;
+  }
+  if (d->K <= 0 || d->M < 1 || d->M > 8) {
+    set_error("need K > 0 and 1 <= M <= 8");
+    return DG_EINVAL;
+  }
+  for (int e = 0; e < d->K; ++e) {
+    for (int i = 0; i < 3; ++i) {
+      int N = orders[e * 3 + i];
+      bool active = i < d->dim;
+      if ((active && (N < 1 || N > kNMax)) || (!active && N != 0)) {
+        set_error("order out of range at element " + std::to_string(e));
+        return DG_EINVAL;
+      }
+    }
+    for (int f = 0; f < 2 * d->dim; ++f) {
+      const int32_t* ft = d->ftab + (size_t)(e * 6 + f) * 4;
+      if (ft[0] >= 0) {
+        if (ft[0] >= d->K || ft[1] < 0 || ft[1] >= 2 * d->dim || ft[2] < 0 || ft[2] > 7) {
+          set_error("bad face entry at element " + std::to_string(e));
+          return DG_EINVAL;
+        }
+        const int32_t* bk = d->ftab + (size_t)(ft[0] * 6 + ft[1]) * 4;
+        if (bk[0] != e || bk[1] != f) {
+          set_error("face table not symmetric at element " + std::to_string(e));
+          return DG_EINVAL;
+        }
+      } else if (ft[3] < DG_BC_FREESTREAM || ft[3] > DG_BC_WALL) {
+        set_error("bad boundary tag at element " + std::to_string(e));
+        return DG_EINVAL;
+      }
+    }
+  }
+  return DG_OK;
+}
+
+static cudaStream_t S(void* p) { return reinterpret_cast<cudaStream_t>(p); }
+
+// ---------------------------------------------------------------------------
+// multigrid
+// ---------------------------------------------------------------------------
+struct Cycle {
+  dg_mesh* m;
+  cudaStream_t st;
+  dg_mg_params mg;
+  std::vector<Level*> lv;  // lv[k]: k-th level from the top (lv[0] = finest)
+  int evals = 0;
+  double dofs = 0.0;
+};
+
+static int smooth_level(Cycle& C, Level* L, double* Q, const double* Sv, int sweeps) {
+  DG_TRY(ensure_work(L));
+  for (int k = 0; k < sweeps; ++k) {
+    DG_TRY(cfl_dt(C.m, L, Q, C.m->d_scalars, C.st));
+    for (int stage = 0; stage < 3; ++stage) {
+      DG_TRY(residual(C.m, L, Q, Sv, nullptr, false, C.st, nullptr, stage, L->d_G, C.m->d_scalars));
+      C.evals++;
+      C.dofs += 5.0 * L->nodes;
+    }
+  }
+  return DG_OK;
+}
+
+static int vcycle_level(Cycle& C, size_t k, double* Qf, const double* Sf) {
+  const bool finest = (k == 0);
+  Level* L = C.lv[k];
+  DG_TRY(ensure_work(L));
+  double* Q = finest ? Qf : L->d_Q;
+  const double* Sv = finest ? Sf : L->d_S;
+  const int64_t n5 = 5 * L->nodes;
+  if (!finest) {
+    // S = A(Q0) + r  (r was restricted into d_S)
+    DG_TRY(residual(C.m, L, Q, nullptr, L->d_R, false, C.st, nullptr, -1, nullptr, nullptr));
+    C.evals++;
+    C.dofs += 5.0 * L->nodes;
+    DG_TRY(sub3(L->d_S, L->d_S, L->d_R, n5, C.st));
+    DG_CUDA_TRY(cudaMemcpyAsync(L->d_Q0, Q, n5 * sizeof(double), cudaMemcpyDeviceToDevice, C.st));
+  }
+  if (k + 1 == C.lv.size()) {
+    DG_TRY(smooth_level(C, L, Q, Sv, C.mg.beta_c));
+  } else {
+    DG_TRY(smooth_level(C, L, Q, Sv, C.mg.beta1));
+    DG_TRY(residual(C.m, L, Q, Sv, L->d_R, false, C.st, nullptr, -1, nullptr, nullptr));
+    C.evals++;
+    C.dofs += 5.0 * L->nodes;
+    Level* Cc = C.lv[k + 1];
+    DG_TRY(ensure_work(Cc));
+    DG_TRY(transfer(C.m, L, Cc, 5, Q, Cc->d_Q, C.st));
+    DG_TRY(transfer(C.m, L, Cc, 5, L->d_R, Cc->d_S, C.st));
+    DG_TRY(vcycle_level(C, k + 1, nullptr, nullptr));
+    DG_TRY(transfer(C.m, Cc, L, 5, Cc->d_Q, Q, C.st, Cc->d_Q0, true));
+    DG_TRY(smooth_level(C, L, Q, Sv, C.mg.beta2));
+  }
+  return DG_OK;
+}
+
+static std::vector<int32_t> capped(const std::vector<int32_t>& o, int dim, int level, int direction) {
+  std::vector<int32_t> r = o;
+  size_t K = o.size() / 3;
+  for (size_t e = 0; e < K; ++e)
+    for (int d = 0; d < dim; ++d)
+      if (direction < 0 || direction == d) r[e * 3 + d] = std::min(r[e * 3 + d], level);
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// adaptation (host, deterministic)
+// ---------------------------------------------------------------------------
+struct DirFit {
+  bool has_slope = false;
+  double slope = 0.0, intercept = 0.0, last = 0.0;
+  int P = 0;
+  const double* t = nullptr;
+  double at(int N) const {
+    if (N < P) return t[N] >= 0.0 ? t[N] : 0.0;
+    if (!has_slope) return last;
+    return std::pow(10.0, intercept + slope * N);
+  }
+};
+
+static DirFit fit_dir(const double* t, int P) {
+  DirFit F;
+  F.P = P;
+  F.t = t;
+  std::vector<double> xs, ys;
+  for (int N = 1; N < P; ++N)
+    if (t[N] > 0.0) {
+      xs.push_back((double)N);
+      ys.push_back(std::log10(t[N]));
+    }
+  if (xs.size() >= 2) {
+    double sx = 0.0, sy = 0.0;
+    for (double x : xs) sx += x;
+    for (double y : ys) sy += y;
+    double xm = sx / xs.size(), ym = sy / ys.size();
+    double sxx = 0.0, sxy = 0.0;
+    for (double x : xs) sxx += (x - xm) * (x - xm);
+    for (size_t k = 0; k < xs.size(); ++k) sxy += (xs[k] - xm) * (ys[k] - ym);
+    double b = sxy / sxx;
+    if (b < 0.0) {
+      F.has_slope = true;
+      F.slope = b;
+      F.intercept = ym - b * xm;
+    }
+  }
+  F.last = (P >= 2 && t[P - 1] >= 0.0) ? t[P - 1] : 0.0;
+  return F;
+}
+
+static void select_element(const double* tab /* 3 x 16 */, const int32_t* P, const dg_adapt_params& ap, int dim,
+                           int32_t* out) {
+  int hi = ap.n_max;
+  if (ap.cap > 0) hi = std::min(hi, (int)ap.cap);
+  DirFit F[3];
+  for (int i = 0; i < dim; ++i) F[i] = fit_dir(tab + i * kTauSlots, P[i]);
+  auto search = [&](const int* lo, const int* up, int32_t* best) -> bool {
+    bool found = false;
+    long bestdof = 0;
+    double besttau = 0.0;
+    int N[3] = {0, 0, 0};
+    int cur[3] = {lo[0], dim > 1 ? lo[1] : 0, dim > 2 ? lo[2] : 0};
+    for (int i = 0; i < dim; ++i)
+      if (up[i] < lo[i]) return false;
+    while (true) {
+      for (int i = 0; i < dim; ++i) N[i] = cur[i];
+      double tv = 0.0;
+      for (int i = 0; i < dim; ++i) tv += F[i].at(N[i]);
+      if (tv < ap.tau_max) {
+        long dof = 1;
+        for (int i = 0; i < dim; ++i) dof *= (N[i] + 1);
+        bool better = !found || dof < bestdof || (dof == bestdof && tv < besttau);
+        if (!better && found && dof == bestdof && tv == besttau) {
+          // lexicographically smaller order triple
+          for (int i = 0; i < dim; ++i) {
+            if (N[i] < best[i]) { better = true; break; }
+            if (N[i] > best[i]) break;
+          }
+        }
+        if (better) {
+          found = true;
+          bestdof = dof;
+          besttau = tv;
+          for (int i = 0; i < dim; ++i) best[i] = N[i];
+        }
+      }
+      // advance the last direction fastest (lexicographic enumeration)
+      int i = dim - 1;
+      while (i >= 0) {
+        if (++cur[i] <= up[i]) break;
+        cur[i] = lo[i];
+        --i;
+      }
+      if (i < 0) break;
+    }
+    return found;
+  };
+  int lo[3], up[3];
+  int32_t best[3] = {0, 0, 0};
+  bool ok = false;
+  bool inner_ok = true;
+  for (int i = 0; i < dim; ++i) {
+    lo[i] = ap.n_min;
+    up[i] = std::min(P[i] - 1, hi);
+    if (up[i] < lo[i]) inner_ok = false;
+  }
+  if (inner_ok) ok = search(lo, up, best);
+  if (!ok) {
+    for (int i = 0; i < dim; ++i) up[i] = hi;
+    ok = search(lo, up, best);
+  }
+  if (!ok)
+    for (int i = 0; i < dim; ++i) best[i] = hi;
+  for (int i = 0; i < 3; ++i) out[i] = (i < dim) ? best[i] : 0;
+}
+
+static void face_map(int fA, int fB, int o, int* m) {
+  int dA = fA / 2, dB = fB / 2;
+  int tA[2], tB[2], k = 0;
+  for (int t = 0; t < 3; ++t)
+    if (t != dA) tA[k++] = t;
+  k = 0;
+  for (int t = 0; t < 3; ++t)
+    if (t != dB) tB[k++] = t;
+  m[dA] = dB;
+  if (o & 1) {
+    m[tA[0]] = tB[1];
+    m[tA[1]] = tB[0];
+  } else {
+    m[tA[0]] = tB[0];
+    m[tA[1]] = tB[1];
+  }
+}
+
+static void limit_jumps(const dg_mesh* m, std::vector<int32_t>& o, int rule, int conform_tag) {
+  const int dim = m->dim, K = m->K;
+  std::vector<char> touches(K, 0);
+  if (conform_tag >= 0)
+    for (int e = 0; e < K; ++e)
+      for (int f = 0; f < 2 * dim; ++f) {
+        const int32_t* ft = &m->ftab[(size_t)(e * 6 + f) * 4];
+        if (ft[0] < 0 && ft[3] == conform_tag) touches[e] = 1;
+      }
+  for (int it = 0; it < 100000; ++it) {
+    std::vector<int32_t> nw = o;
+    for (int e = 0; e < K; ++e)
+      for (int f = 0; f < 2 * dim; ++f) {
+        const int32_t* ft = &m->ftab[(size_t)(e * 6 + f) * 4];
+        int nb = ft[0];
+        if (nb < 0) continue;
+        int mp[3];
+        face_map(f, ft[1], ft[2], mp);
+        for (int i = 0; i < dim; ++i) {
+          int other = o[nb * 3 + mp[i]];
+          int need = (rule == 1) ? other - 1 : (rule == 2 ? (2 * other) / 3 : 0);
+          if (conform_tag >= 0 && touches[e] && touches[nb]) need = std::max(need, other);
+          if (need > nw[e * 3 + i]) nw[e * 3 + i] = need;
+        }
+      }
+    if (nw == o) return;
+    o.swap(nw);
+  }
+}
+
+}  // namespace dg
+
+using namespace dg;
+
+extern "C" {
+
+const char* dg_last_error(void) { return g_err.c_str(); }
+
+int dg_mesh_create(const dg_mesh_desc* desc, const int32_t* orders, dg_mesh** out) {
+  if (!out) {
+    set_error("null output");
+    return DG_EINVAL;
+  }
+  DG_TRY(check_desc(desc, orders));
+  DG_TRY(upload_tables());
+  dg_mesh* m = new (std::nothrow) dg_mesh();
+  if (!m) return DG_ENOMEM;
+  m->dim = desc->dim;
+  m->K = desc->K;
+  m->M = desc->M;
+  int Mp = desc->M + 1;
+  size_t npe = desc->dim == 3 ? (size_t)Mp * Mp * Mp : (size_t)Mp * Mp;
+  m->xmap.assign(desc->xmap, desc->xmap + (size_t)desc->K * npe * 3);
+  m->ftab.assign(desc->ftab, desc->ftab + (size_t)desc->K * 24);
+  m->prm = make_params(desc->params);
+  m->orders.assign(orders, orders + (size_t)desc->K * 3);
+  m->fine.reset(new Level());
+  int rc = build_level(m, m->orders, m->fine.get());
+  if (rc == DG_OK) {
+    cudaError_t e1 = cudaMalloc(&m->d_scalars, 16 * sizeof(double));
+    cudaError_t e2 = cudaMalloc(&m->d_tau, (size_t)m->K * 3 * kTauSlots * sizeof(double));
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+      set_error("cudaMalloc failed for mesh scalars");
+      rc = DG_ECUDA;
+    }
+  }
+  if (rc != DG_OK) {
+    dg_mesh_destroy(m);
+    return rc;
+  }
+  *out = m;
+  return DG_OK;
+}
+
+int dg_mesh_destroy(dg_mesh* m) {
+  if (!m) return DG_OK;
+  if (m->d_scalars) cudaFree(m->d_scalars);
+  if (m->d_tau) cudaFree(m->d_tau);
+  delete m;
+  return DG_OK;
+}
+
+int dg_mesh_layout(const dg_mesh* m, int64_t* total_nodes, int64_t* elem_offsets) {
+  if (!m) {
+    set_error("null mesh");
+    return DG_EINVAL;
+  }
+  if (total_nodes) *total_nodes = m->fine->nodes;
+  if (elem_offsets)
+    for (int e = 0; e <= m->K; ++e) elem_offsets[e] = m->fine->off[e];
+  return DG_OK;
+}
+
+int dg_residual(dg_mesh* m, const double* q, const double* s, double* r, int flags, double* rnorm_host,
+                void* stream) {
+  if (!m || !q || !r || q == r) {
+    set_error("dg_residual: null or aliased arrays");
+    return DG_EINVAL;
+  }
+  if ((flags & DG_NORM) && !rnorm_host) {
+    set_error("dg_residual: DG_NORM needs rnorm_host");
+    return DG_EINVAL;
+  }
+  cudaStream_t st = S(stream);
+  bool iso = flags & DG_ISOLATED;
+  double* dnorm = nullptr;
+  if (flags & DG_NORM) {
+    dnorm = m->d_scalars + 1;
+    DG_TRY(reset_max(dnorm, st));
+  }
+  DG_TRY(residual(m, m->fine.get(), q, s, r, iso, st, iso ? nullptr : dnorm, -1, nullptr, nullptr));
+  if (flags & DG_NORM) {
+    if (iso) {
+      // norm of the isolated residual: reduce it with the tau reduction over one slot
+      set_error("DG_NORM with DG_ISOLATED is not supported");
+      return DG_EINVAL;
+    }
+    DG_TRY(read_scalar(dnorm, rnorm_host, st));
+  }
+  return DG_OK;
+}
+
+int dg_cfl_dt(dg_mesh* m, const double* q, double* dt, void* stream) {
+  if (!m || !q || !dt) {
+    set_error("dg_cfl_dt: null argument");
+    return DG_EINVAL;
+  }
+  cudaStream_t st = S(stream);
+  DG_TRY(cfl_dt(m, m->fine.get(), q, m->d_scalars, st));
+  return read_scalar(m->d_scalars, dt, st);
+}
+
+int dg_smooth(dg_mesh* m, double* q, const double* s, int sweeps, void* stream) {
+  if (!m || !q || sweeps < 0) {
+    set_error("dg_smooth: bad argument");
+    return DG_EINVAL;
+  }
+  Cycle C{m, S(stream), dg_mg_params{}, {}, 0, 0.0};
+  return smooth_level(C, m->fine.get(), q, s, sweeps);
+}
+
+int dg_pmg_vcycle(dg_mesh* m, double* q, const double* s, const dg_mg_params* mg, int want_norm,
+                  dg_cycle_report* rep, void* stream) {
+  if (!m || !q || !mg || mg->beta1 < 0 || mg->beta2 < 0 || mg->beta_c < 0 || mg->coarsest < 1 ||
+      mg->direction < -1 || mg->direction >= m->dim) {
+    set_error("dg_pmg_vcycle: bad argument");
+    return DG_EINVAL;
+  }
+  Cycle C{m, S(stream), *mg, {}, 0, 0.0};
+  int top = 0;
+  for (int e = 0; e < m->K; ++e)
+    for (int d = 0; d < m->dim; ++d)
+      if (mg->direction < 0 || mg->direction == d) top = std::max(top, (int)m->orders[e * 3 + d]);
+  int coarsest = std::min(mg->coarsest, top);
+  const int dN = mg->delta_n > 0 ? mg->delta_n : 1;
+  for (int l = top; l >= coarsest; l -= dN) {
+    Level* L = get_level(m, capped(m->orders, m->dim, l, mg->direction));
+    if (!L) return DG_ECUDA;
+    C.lv.push_back(L);
+  }
+  DG_TRY(vcycle_level(C, 0, q, s));
+  double rn = 0.0;
+  if (want_norm) {
+    Level* F = m->fine.get();
+    DG_TRY(ensure_work(F));
+    DG_TRY(reset_max(m->d_scalars + 1, C.st));
+    DG_TRY(residual(m, F, q, s, F->d_R, false, C.st, m->d_scalars + 1, -1, nullptr, nullptr));
+    DG_TRY(read_scalar(m->d_scalars + 1, &rn, C.st));
+  }
+  if (rep) {
+    rep->levels = (int32_t)C.lv.size();
+    rep->residual_evals = C.evals;
+    rep->dof_evals = C.dofs;
+    rep->rnorm = rn;
+  }
+  return DG_OK;
+}
+
+int dg_tau_estimate(dg_mesh* m, const double* q, const double* s, int dir_mask, int with_correction, int isolated,
+                    double* tau_host, void* stream) {
+  if (!m || !q || !tau_host) {
+    set_error("dg_tau_estimate: null argument");
+    return DG_EINVAL;
+  }
+  cudaStream_t st = S(stream);
+  Level* F = m->fine.get();
+  DG_TRY(ensure_work(F));
+  const size_t tsz = (size_t)m->K * 3 * kTauSlots;
+  DG_TRY(fill(m->d_tau, 0.0, (int64_t)tsz, st));
+  // R^P(q) at the reference orders
+  if (with_correction) DG_TRY(residual(m, F, q, s, F->d_R, isolated != 0, st, nullptr, -1, nullptr, nullptr));
+  int32_t* d_fine_orders = nullptr;
+  DG_CUDA_TRY(cudaMalloc(&d_fine_orders, m->orders.size() * sizeof(int32_t)));
+  DG_CUDA_TRY(cudaMemcpyAsync(d_fine_orders, m->orders.data(), m->orders.size() * sizeof(int32_t),
+                              cudaMemcpyHostToDevice, st));
+  int rc = DG_OK;
+  for (int i = 0; i < m->dim && rc == DG_OK; ++i) {
+    if (!((dir_mask >> i) & 1)) continue;
+    int top = 0;
+    for (int e = 0; e < m->K; ++e) top = std::max(top, (int)m->orders[e * 3 + i]);
+    Level* prev = F;
+    const double* Qp = q;
+    const double* Sp = s;
+    const double* Rp = with_correction ? F->d_R : nullptr;
+    for (int l = top - 1; l >= 1 && rc == DG_OK; --l) {
+      Level* Ll = get_level(m, capped(m->orders, m->dim, l, i));
+      if (!Ll) {
+        rc = DG_ECUDA;
+        break;
+      }
+      if ((rc = ensure_work(Ll)) != DG_OK) break;
+      if ((rc = transfer(m, prev, Ll, 5, Qp, Ll->d_Q, st)) != DG_OK) break;
+      if (s && (rc = transfer(m, prev, Ll, 5, Sp, Ll->d_S, st)) != DG_OK) break;
+      if (Rp && (rc = transfer(m, prev, Ll, 5, Rp, Ll->d_G, st)) != DG_OK) break;
+      rc = tau_accumulate(m, Ll, Ll->d_Q, s ? Ll->d_S : nullptr, Rp ? Ll->d_G : nullptr, isolated != 0, i, l,
+                          d_fine_orders, m->d_tau, st);
+      prev = Ll;
+      Qp = Ll->d_Q;
+      Sp = Ll->d_S;
+      Rp = Rp ? Ll->d_G : nullptr;
+    }
+  }
+  if (rc == DG_OK) {
+    cudaError_t e = cudaMemcpyAsync(tau_host, m->d_tau, tsz * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      set_error(std::string("tau copy: ") + cudaGetErrorString(e));
+      rc = DG_ECUDA;
+    }
+  }
+  cudaFree(d_fine_orders);
+  if (rc != DG_OK) return rc;
+  for (int e = 0; e < m->K; ++e)
+    for (int i = 0; i < 3; ++i)
+      for (int N = 0; N < kTauSlots; ++N) {
+        bool measured = i < m->dim && ((dir_mask >> i) & 1) && N >= 1 && N < m->orders[e * 3 + i];
+        if (!measured) tau_host[((size_t)e * 3 + i) * kTauSlots + N] = -1.0;
+      }
+  return DG_OK;
+}
+
+int dg_adapt(const dg_mesh* m, const double* tau_host, const dg_adapt_params* ap, int32_t* new_orders) {
+  if (!m || !tau_host || !ap || !new_orders || ap->n_min < 1 || ap->n_max > kNMax || ap->n_min > ap->n_max ||
+      ap->n_max >= kTauSlots) {
+    set_error("dg_adapt: bad argument");
+    return DG_EINVAL;
+  }
+  std::vector<int32_t> o((size_t)m->K * 3, 0);
+  for (int e = 0; e < m->K; ++e)
+    select_element(tau_host + (size_t)e * 3 * kTauSlots, &m->orders[e * 3], *ap, m->dim, &o[e * 3]);
+  if (ap->jump_rule == 1 || ap->jump_rule == 2 || ap->conform_tag >= 0)
+    limit_jumps(m, o, ap->jump_rule, ap->conform_tag);
+  std::memcpy(new_orders, o.data(), o.size() * sizeof(int32_t));
+  return DG_OK;
+}
+
+int dg_transfer_state(const dg_mesh* from, const double* q_from, const dg_mesh* to, double* q_to, void* stream) {
+  if (!from || !to || !q_from || !q_to || from->K != to->K || from->dim != to->dim) {
+    set_error("dg_transfer_state: meshes do not match");
+    return DG_EINVAL;
+  }
+  return transfer(from, from->fine.get(), to->fine.get(), 5, q_from, q_to, S(stream));
+}
+
+}  // extern "C"

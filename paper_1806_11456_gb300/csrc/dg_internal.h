@@ -1,0 +1,166 @@
+// Internal declarations of the GB300 DGSEM library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/dg.h"
+
+namespace dg {
+
+constexpr int kNMax = 12;               // highest polynomial order
+constexpr int kNP = kNMax + 2;          // table stride (n = 1 .. kNMax+1)
+constexpr int kMaxElemNodes = 729;      // 3D element node cap (smem staging)
+constexpr int kTileNodes = 256;         // element-kernel CTA size (threads)
+constexpr int kMortarTile = 256;        // mortar-kernel CTA size (threads)
+constexpr int kTauSlots = 16;           // orders per direction in the tau table
+
+void set_error(const std::string& msg);
+
+#define DG_CUDA_TRY(call)                                                              \
+  do {                                                                                 \
+    cudaError_t _e = (call);                                                           \
+    if (_e != cudaSuccess) {                                                           \
+      ::dg::set_error(std::string(#call) + ": " + cudaGetErrorString(_e));             \
+      return DG_ECUDA;                                                                 \
+    }                                                                                  \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// 1-D tables (host, FP64) for n = 1 .. kNMax+1 Legendre-Gauss nodes
+// ---------------------------------------------------------------------------
+struct Tables1D {
+  double x[kNP][kNP], w[kNP][kNP];   // nodes, weights
+  double bw[kNP][kNP];               // barycentric weights
+  double Dhat[kNP][kNP][kNP];        // weak-form derivative: -(w_a/w_i) l_i'(x_a)  [n][i][a]
+  double D[kNP][kNP][kNP];           // collocation derivative: l_a'(x_i)          [n][i][a]
+  double lm[kNP][kNP], lp[kNP][kNP]; // l_j(-1), l_j(+1)
+};
+const Tables1D& tables();
+double lagrange_bary(int n, int j, double x);  // l_j(x) on n Gauss nodes
+// transfer matrix between n_from and n_to Gauss nodes: L2 projection (down),
+// interpolation (up), identity (equal); T[j*n_from + k]
+void transfer_matrix(int n_from, int n_to, double* T);
+
+// ---------------------------------------------------------------------------
+// device-side descriptors
+// ---------------------------------------------------------------------------
+// Device constant tables (defined in dg_kernels.cu)
+struct DevTables {
+  double x[kNP][kNP];
+  double w[kNP][kNP];
+  double lm[kNP][kNP], lp[kNP][kNP];
+  double lmw[kNP][kNP], lpw[kNP][kNP];   // l(-1)/w, l(+1)/w
+};
+
+struct ElemTile {      // one CTA of an element kernel: `count` elements of one order
+  int32_t first;       // index into the level's tile_elems list
+  int32_t count;
+  int16_t n[3];
+  int16_t pad;
+};
+
+struct MortarDev {     // one mortar (a face pair or a boundary face)
+  int32_t eL, fL, eR, fR;
+  int32_t orient, bc;
+  int32_t ma, mb;      // mortar nodes per tangential direction (L frame)
+  int32_t node_off;    // first mortar node
+  int32_t flags;       // bit0: both sides conforming with the mortar
+};
+
+struct MortarTile {    // one CTA of a mortar kernel
+  int32_t first, count;     // mortars
+  int32_t node_first, nodes;
+};
+
+struct Params {
+  double g, Pr, Ma, Re, Su, Ca, Cnu;
+  double qinf[5];
+  double pinf;
+  double gM2;      // gamma M^2
+  double hc;       // 1/((gamma-1) Pr M^2)
+  double invRe;
+};
+
+// A level: one order map of the mesh with its geometry, tables and buffers.
+struct Level {
+  int dim = 3, K = 0;
+  std::vector<int32_t> orders;          // K x 3
+  std::vector<int64_t> off;             // K+1 node offsets
+  int64_t nodes = 0;
+  // device
+  int32_t* d_n = nullptr;               // K x 3 node counts
+  int32_t* d_off = nullptr;             // K+1 (int32 suffices: < 2^31 nodes)
+  double* d_geo = nullptr;              // 10 x nodes: Ja (9, [i*3+c]) then 1/J, SoA
+  int32_t* d_fo = nullptr;              // K*6 element-face node offsets
+  int64_t face_nodes = 0;
+  double* d_fnS = nullptr;              // 3 x face_nodes: own outward metric
+  double* d_trq = nullptr;              // 5 x face_nodes: q traces
+  double* d_ust = nullptr;              // 4 x face_nodes: projected U*
+  double* d_trg = nullptr;              // 12 x face_nodes: gradient traces
+  double* d_fst = nullptr;              // 5 x face_nodes: projected F* S
+  MortarDev* d_mortars = nullptr;
+  int n_mortars = 0;
+  int64_t mortar_nodes = 0;
+  int32_t* d_mnode_mortar = nullptr;    // mortar node -> mortar
+  double* d_mnS = nullptr;              // 3 x mortar_nodes
+  MortarTile* d_mtiles = nullptr;
+  int n_mtiles = 0;
+  int32_t* d_tile_elems = nullptr;
+  ElemTile* d_tiles = nullptr;
+  int n_tiles = 0;
+  size_t tile_smem_nodes = 0;           // max nodes of a tile
+  double* d_vol = nullptr;              // 5 x nodes volume part
+  // multigrid work arrays (allocated on first use)
+  double *d_Q = nullptr, *d_S = nullptr, *d_Q0 = nullptr, *d_G = nullptr, *d_R = nullptr;
+  ~Level();
+};
+
+struct TransferPlan {  // element-wise transfer between two levels of one mesh
+  int32_t* d_nf = nullptr;  // unused placeholder
+  ~TransferPlan() {}
+};
+
+}  // namespace dg
+
+struct dg_mesh {
+  int dim = 3, K = 0, M = 1;
+  std::vector<double> xmap;
+  std::vector<int32_t> ftab;
+  dg::Params prm;
+  std::vector<int32_t> orders;
+  std::unique_ptr<dg::Level> fine;
+  std::map<std::vector<int32_t>, std::unique_ptr<dg::Level>> levels;  // coarse levels by order map
+  double* d_scalars = nullptr;   // [0] dt, [1] norm, [2..] scratch
+  double* d_tau = nullptr;       // K x 3 x 16 tau table
+  double* d_T = nullptr;         // transfer matrices [n_from][n_to][nt*nf]
+};
+
+namespace dg {
+int build_level(const dg_mesh* m, const std::vector<int32_t>& orders, Level* L);
+Level* get_level(dg_mesh* m, const std::vector<int32_t>& orders);
+int ensure_work(Level* L);
+Params make_params(const double* p);
+
+// kernels (dg_kernels.cu)
+int upload_tables();
+int residual(const dg_mesh* m, Level* L, const double* q, const double* s, double* r, bool isolated,
+             cudaStream_t st, double* d_norm, int rk_stage, double* rk_g, const double* d_dt);
+int cfl_dt(const dg_mesh* m, Level* L, const double* q, double* d_dt, cudaStream_t st);
+int transfer(const dg_mesh* m, const Level* from, const Level* to, int nvar, const double* in, double* out,
+             cudaStream_t st, const double* sub = nullptr, bool accumulate = false);
+int fill(double* p, double v, int64_t n, cudaStream_t st);
+int axpby(double* y, double a, const double* x, double b, int64_t n, cudaStream_t st);  // y = a x + b y
+int sub3(double* out, const double* a, const double* b, int64_t n, cudaStream_t st);    // out = a - b
+int tau_accumulate(const dg_mesh* m, Level* L, const double* q, const double* s, const double* rho,
+                   bool isolated, int dir, int order_slot, const int32_t* fine_orders_dev, double* d_tau,
+                   cudaStream_t st);
+int read_scalar(const double* d, double* h, cudaStream_t st);
+int reset_max(double* d, cudaStream_t st);
+int reset_min(double* d, cudaStream_t st);
+}  // namespace dg

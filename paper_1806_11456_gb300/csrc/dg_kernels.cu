@@ -1,0 +1,1133 @@
+// CUDA kernels of the DGSEM residual, smoother and transfers (sm_103a, FP64).
+//
+// One residual evaluation r = S - M^{-1} F(Q) (Sec. 2, DiscretNSElem; Sec. 3.1)
+// is five launches:
+//   k_trace_q      element tiles: conserved state interpolated to every face
+//   k_mortar<1>    mortar tiles : BR1 average U* of (u,v,w,T) at mortar nodes,
+//                                 L2-projected back onto both faces
+//   k_volume       element tiles: BR1 gradient (weak form + lifting of U*),
+//                                 its face traces, nodal NS fluxes, weak-form
+//                                 volume divergence
+//   k_mortar<2>    mortar tiles : Roe + BR1 viscous flux, projected back
+//   k_surface      element tiles: surface terms, 1/J, r = S - A; optionally
+//                                 fused RK3 stage update and max |r|
+// The isolated operator (Sec. 3.2.1) is one element-local launch
+// (k_isolated), strong form, optionally fused with the tau epilogue.
+//
+// Work decomposition: a CTA owns whole elements of one order triple
+// (elements-per-CTA so that the tile has <= 256 nodes, one element per CTA
+// above that); one thread per node; the element's state, metrics and the
+// 1-D derivative tables of its orders are staged in shared memory, where the
+// tensor-product contractions read them.  Mortar CTAs own whole mortars, one
+// thread per mortar node.  FP64 throughput (2 DFMA/clk/SM on GB300) bounds
+// these kernels: the code is written to minimise FP64 instructions (one
+// reciprocal of rho per node, T^1.5 as T*sqrt(T), contravariant fluxes formed
+// directly from the contravariant velocity).
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "dg_internal.h"
+
+namespace dg {
+
+__constant__ DevTables c_tab;
+__constant__ double* c_Dhat;  // [kNP][kNP][kNP]
+__constant__ double* c_D;     // [kNP][kNP][kNP]
+__constant__ double* c_T;     // [kNP][kNP][kNP*kNP] transfer matrices (n_from, n_to)
+
+static double* g_dev_Dhat = nullptr;
+static double* g_dev_D = nullptr;
+static double* g_dev_T = nullptr;
+static int g_tables_device = -1;
+
+int upload_tables() {
+  int dev = 0;
+  DG_CUDA_TRY(cudaGetDevice(&dev));
+  if (g_tables_device == dev) return DG_OK;
+  const Tables1D& T = tables();
+  DevTables h;
+  memset(&h, 0, sizeof(h));
+  for (int n = 1; n < kNP; ++n)
+    for (int j = 0; j < n; ++j) {
+      h.x[n][j] = T.x[n][j];
+      h.w[n][j] = T.w[n][j];
+      h.lm[n][j] = T.lm[n][j];
+      h.lp[n][j] = T.lp[n][j];
+      h.lmw[n][j] = T.lm[n][j] / T.w[n][j];
+      h.lpw[n][j] = T.lp[n][j] / T.w[n][j];
+    }
+  DG_CUDA_TRY(cudaMemcpyToSymbol(c_tab, &h, sizeof(h)));
+  std::vector<double> Dh((size_t)kNP * kNP * kNP, 0.0), Dc((size_t)kNP * kNP * kNP, 0.0);
+  for (int n = 1; n < kNP; ++n)
+    for (int i = 0; i < n; ++i)
+      for (int a = 0; a < n; ++a) {
+        Dh[((size_t)n * kNP + i) * kNP + a] = T.Dhat[n][i][a];
+        Dc[((size_t)n * kNP + i) * kNP + a] = T.D[n][i][a];
+      }
+  std::vector<double> Tm((size_t)kNP * kNP * kNP * kNP, 0.0);
+  for (int nf = 1; nf < kNP; ++nf)
+    for (int nt = 1; nt < kNP; ++nt) transfer_matrix(nf, nt, &Tm[((size_t)nf * kNP + nt) * kNP * kNP]);
+  if (!g_dev_Dhat) {
+    DG_CUDA_TRY(cudaMalloc(&g_dev_Dhat, Dh.size() * sizeof(double)));
+    DG_CUDA_TRY(cudaMalloc(&g_dev_D, Dc.size() * sizeof(double)));
+    DG_CUDA_TRY(cudaMalloc(&g_dev_T, Tm.size() * sizeof(double)));
+  }
+  DG_CUDA_TRY(cudaMemcpy(g_dev_Dhat, Dh.data(), Dh.size() * sizeof(double), cudaMemcpyHostToDevice));
+  DG_CUDA_TRY(cudaMemcpy(g_dev_D, Dc.data(), Dc.size() * sizeof(double), cudaMemcpyHostToDevice));
+  DG_CUDA_TRY(cudaMemcpy(g_dev_T, Tm.data(), Tm.size() * sizeof(double), cudaMemcpyHostToDevice));
+  DG_CUDA_TRY(cudaMemcpyToSymbol(c_Dhat, &g_dev_Dhat, sizeof(double*)));
+  DG_CUDA_TRY(cudaMemcpyToSymbol(c_D, &g_dev_D, sizeof(double*)));
+  DG_CUDA_TRY(cudaMemcpyToSymbol(c_T, &g_dev_T, sizeof(double*)));
+  g_tables_device = dev;
+  return DG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// device physics (Appendix A)
+// ---------------------------------------------------------------------------
+#define DEV __device__ __forceinline__
+
+struct Gas {
+  double g1;     // gamma - 1
+  double gM2;    // gamma M^2
+  double Su, Su1;  // Sutherland S and 1 + S
+  double hc;     // 1/((gamma-1) Pr M^2)
+  double invRe;
+  double g;
+  double Ca, Cnu;
+  double qinf[5];
+  double pinf;
+};
+
+DEV Gas make_gas(const Params& P) {
+  Gas G;
+  G.g1 = P.g - 1.0;
+  G.gM2 = P.gM2;
+  G.Su = P.Su;
+  G.Su1 = 1.0 + P.Su;
+  G.hc = P.hc;
+  G.invRe = P.invRe;
+  G.g = P.g;
+  G.Ca = P.Ca;
+  G.Cnu = P.Cnu;
+  for (int v = 0; v < 5; ++v) G.qinf[v] = P.qinf[v];
+  G.pinf = P.pinf;
+  return G;
+}
+
+// primitives: 1/rho, velocity, pressure, temperature
+DEV void to_prim(const double* q, const Gas& G, double& ir, double* u, double& p, double& T) {
+  ir = 1.0 / q[0];
+  u[0] = q[1] * ir;
+  u[1] = q[2] * ir;
+  u[2] = q[3] * ir;
+  p = G.g1 * (q[4] - 0.5 * (q[1] * u[0] + q[2] * u[1] + q[3] * u[2]));
+  T = G.gM2 * p * ir;
+}
+
+DEV double mu_of_T(double T, const Gas& G) { return T * sqrt(T) * G.Su1 / (T + G.Su); }
+
+// viscous flux (no 1/Re) on vector nv; grad[v*3+c] = d(u,v,w,T)_v / dx_c
+DEV void visc_flux(const double* u, double mu, const double* grad, const double* nv, const Gas& G,
+                   bool heat, double* f) {
+  double div = grad[0] + grad[4] + grad[8];
+  double lam = -2.0 / 3.0 * mu * div;
+  // tau . nv, tau symmetric
+  double t00 = 2.0 * mu * grad[0] + lam, t11 = 2.0 * mu * grad[4] + lam, t22 = 2.0 * mu * grad[8] + lam;
+  double t01 = mu * (grad[1] + grad[3]), t02 = mu * (grad[2] + grad[6]), t12 = mu * (grad[5] + grad[7]);
+  double tn0 = t00 * nv[0] + t01 * nv[1] + t02 * nv[2];
+  double tn1 = t01 * nv[0] + t11 * nv[1] + t12 * nv[2];
+  double tn2 = t02 * nv[0] + t12 * nv[1] + t22 * nv[2];
+  f[0] = 0.0;
+  f[1] = tn0;
+  f[2] = tn1;
+  f[3] = tn2;
+  double e = u[0] * tn0 + u[1] * tn1 + u[2] * tn2;
+  if (heat) e += G.hc * mu * (grad[9] * nv[0] + grad[10] * nv[1] + grad[11] * nv[2]);
+  f[4] = e;
+}
+
+// Roe flux for unit normal n (textbook averages, five waves, no entropy fix)
+DEV void roe(const double* qL, const double* qR, const double* n, const Gas& G, double* f) {
+  double irL, uL[3], pL, TL, irR, uR[3], pR, TR;
+  to_prim(qL, G, irL, uL, pL, TL);
+  to_prim(qR, G, irR, uR, pR, TR);
+  double unL = uL[0] * n[0] + uL[1] * n[1] + uL[2] * n[2];
+  double unR = uR[0] * n[0] + uR[1] * n[1] + uR[2] * n[2];
+  double HL = (qL[4] + pL) * irL, HR = (qR[4] + pR) * irR;
+  // central part
+  f[0] = 0.5 * (qL[0] * unL + qR[0] * unR);
+  f[1] = 0.5 * (qL[1] * unL + qR[1] * unR + (pL + pR) * n[0]);
+  f[2] = 0.5 * (qL[2] * unL + qR[2] * unR + (pL + pR) * n[1]);
+  f[3] = 0.5 * (qL[3] * unL + qR[3] * unR + (pL + pR) * n[2]);
+  f[4] = 0.5 * (qL[0] * HL * unL + qR[0] * HR * unR);
+  double sL = sqrt(qL[0]), sR = sqrt(qR[0]);
+  double iw = 1.0 / (sL + sR);
+  double ut[3] = {(sL * uL[0] + sR * uR[0]) * iw, (sL * uL[1] + sR * uR[1]) * iw, (sL * uL[2] + sR * uR[2]) * iw};
+  double Ht = (sL * HL + sR * HR) * iw;
+  double rt = sL * sR;
+  double q2 = ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2];
+  double c2 = G.g1 * (Ht - 0.5 * q2);
+  double ct = sqrt(c2);
+  double ic2 = 1.0 / c2;
+  double unt = ut[0] * n[0] + ut[1] * n[1] + ut[2] * n[2];
+  double dp = pR - pL, dr = qR[0] - qL[0];
+  double du[3] = {uR[0] - uL[0], uR[1] - uL[1], uR[2] - uL[2]};
+  double dun = unR - unL;
+  double a1 = 0.5 * (dp - rt * ct * dun) * ic2;
+  double a5 = 0.5 * (dp + rt * ct * dun) * ic2;
+  double a2 = dr - dp * ic2;
+  double l1 = fabs(unt - ct) * a1, l5 = fabs(unt + ct) * a5, l2 = fabs(unt);
+  double e2 = l2 * a2;
+  // shear part
+  double dt[3] = {du[0] - dun * n[0], du[1] - dun * n[1], du[2] - dun * n[2]};
+  double sh = l2 * rt;
+  double d0 = l1 + l5 + e2;
+  double d1 = l1 * (ut[0] - ct * n[0]) + l5 * (ut[0] + ct * n[0]) + e2 * ut[0] + sh * dt[0];
+  double d2 = l1 * (ut[1] - ct * n[1]) + l5 * (ut[1] + ct * n[1]) + e2 * ut[1] + sh * dt[1];
+  double d3 = l1 * (ut[2] - ct * n[2]) + l5 * (ut[2] + ct * n[2]) + e2 * ut[2] + sh * dt[2];
+  double d4 = l1 * (Ht - unt * ct) + l5 * (Ht + unt * ct) + e2 * 0.5 * q2 +
+              sh * (ut[0] * dt[0] + ut[1] * dt[1] + ut[2] * dt[2]);
+  f[0] -= 0.5 * d0;
+  f[1] -= 0.5 * d1;
+  f[2] -= 0.5 * d2;
+  f[3] -= 0.5 * d3;
+  f[4] -= 0.5 * d4;
+}
+
+DEV void ghost(int bc, const double* qi, const double* nu, const Gas& G, double* qg) {
+  if (bc == DG_BC_FREESTREAM) {
+    for (int v = 0; v < 5; ++v) qg[v] = G.qinf[v];
+    return;
+  }
+  double ir = 1.0 / qi[0];
+  double ke = 0.5 * (qi[1] * qi[1] + qi[2] * qi[2] + qi[3] * qi[3]) * ir;
+  if (bc == DG_BC_OUTFLOW) {
+    qg[0] = qi[0];
+    qg[1] = qi[1];
+    qg[2] = qi[2];
+    qg[3] = qi[3];
+    qg[4] = G.pinf / G.g1 + ke;
+    return;
+  }
+  if (bc == DG_BC_SLIP) {
+    double mn = qi[1] * nu[0] + qi[2] * nu[1] + qi[3] * nu[2];
+    qg[0] = qi[0];
+    qg[1] = qi[1] - 2.0 * mn * nu[0];
+    qg[2] = qi[2] - 2.0 * mn * nu[1];
+    qg[3] = qi[3] - 2.0 * mn * nu[2];
+    qg[4] = qi[4];
+    return;
+  }
+  // wall: negated velocity, same density and internal energy
+  qg[0] = qi[0];
+  qg[1] = -qi[1];
+  qg[2] = -qi[2];
+  qg[3] = -qi[3];
+  qg[4] = qi[4];
+}
+
+DEV void atomic_max_nonneg(double* addr, double v) {
+  atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
+}
+DEV void atomic_min_pos(double* addr, double v) {
+  atomicMin(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+// ---------------------------------------------------------------------------
+// shared helpers for element tiles
+// ---------------------------------------------------------------------------
+struct LevelArgs {
+  const int32_t* n;
+  const int32_t* off;
+  const double* geo;
+  int64_t nodes;
+  const int32_t* fo;
+  int64_t fn;  // face nodes
+  const double* fnS;
+  const ElemTile* tiles;
+  const int32_t* tile_elems;
+  int dim;
+};
+
+static LevelArgs largs(const Level* L) {
+  LevelArgs a;
+  a.n = L->d_n;
+  a.off = L->d_off;
+  a.geo = L->d_geo;
+  a.nodes = L->nodes;
+  a.fo = L->d_fo;
+  a.fn = L->face_nodes;
+  a.fnS = L->d_fnS;
+  a.tiles = L->d_tiles;
+  a.tile_elems = L->d_tile_elems;
+  a.dim = L->dim;
+  return a;
+}
+
+DEV void face_dirs(int f, int& d, int& ta, int& tb, int& side) {
+  d = f >> 1;
+  side = f & 1;
+  ta = (d == 0) ? 1 : 0;
+  tb = (d == 2) ? 1 : 2;
+}
+
+// Interpolate face values (nvar comps, stride fs) of an na x nb face to the
+// mortar point (ia, ib) of an ma x mb rule.
+DEV void face_interp(const double* X, int64_t fs, int na, int nb, int ma, int mb, int ia, int ib, int nvar,
+                     double* out) {
+  if (na == ma && nb == mb) {
+    int p = ib * na + ia;
+    for (int v = 0; v < nvar; ++v) out[v] = X[v * fs + p];
+    return;
+  }
+  const double* Ta = c_T + ((size_t)na * kNP + ma) * kNP * kNP + ia * na;
+  const double* Tb = c_T + ((size_t)nb * kNP + mb) * kNP * kNP + ib * nb;
+  for (int v = 0; v < nvar; ++v) out[v] = 0.0;
+  for (int kb = 0; kb < nb; ++kb) {
+    double wb = Tb[kb];
+    if (wb == 0.0) continue;
+    for (int ka = 0; ka < na; ++ka) {
+      double wgt = wb * Ta[ka];
+      int p = kb * na + ka;
+      for (int v = 0; v < nvar; ++v) out[v] += wgt * X[v * fs + p];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_trace_q: conserved state at every face node of every element
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTileNodes) k_trace_q(LevelArgs A, const double* __restrict__ q,
+                                                        double* __restrict__ trq) {
+  extern __shared__ double smem[];
+  const ElemTile t = A.tiles[blockIdx.x];
+  const int n0 = t.n[0], n1 = t.n[1], n2 = t.n[2];
+  const int nn = n0 * n1 * n2;
+  const int T = t.count * nn;
+  double* sq = smem;
+  for (int i = threadIdx.x; i < T; i += blockDim.x) {
+    int le = i / nn, node = i - le * nn;
+    int e = A.tile_elems[t.first + le];
+    const double* qe = q + (size_t)5 * A.off[e];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sq[v * T + i] = qe[v * nn + node];
+  }
+  __syncthreads();
+  const int nvec[3] = {n0, n1, n2};
+  const int fsz[3] = {n1 * n2, n0 * n2, n0 * n1};
+  const int nfaces = 2 * A.dim;
+  int FE = 0;
+  for (int f = 0; f < nfaces; ++f) FE += fsz[f >> 1];
+  for (int i = threadIdx.x; i < t.count * FE; i += blockDim.x) {
+    int le = i / FE, r = i - le * FE;
+    int f = 0;
+    while (r >= fsz[f >> 1]) {
+      r -= fsz[f >> 1];
+      ++f;
+    }
+    int d, ta, tb, side;
+    face_dirs(f, d, ta, tb, side);
+    int ia = r % nvec[ta], ib = r / nvec[ta];
+    int idx[3];
+    idx[d] = 0;
+    idx[ta] = ia;
+    idx[tb] = ib;
+    int base = (idx[2] * n1 + idx[1]) * n0 + idx[0];
+    int sd = (d == 0) ? 1 : (d == 1 ? n0 : n0 * n1);
+    const double* lb = side ? c_tab.lp[nvec[d]] : c_tab.lm[nvec[d]];
+    int e = A.tile_elems[t.first + le];
+    int64_t p = A.fo[e * 6 + f] + r;
+    const double* s0 = sq + le * nn + base;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      double acc = 0.0;
+      for (int k = 0; k < nvec[d]; ++k) acc += lb[k] * s0[v * T + k * sd];
+      trq[v * A.fn + p] = acc;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_mortar<PASS>: PASS 1 = BR1 average U*, PASS 2 = Roe + BR1 viscous flux
+// ---------------------------------------------------------------------------
+struct MortarArgs {
+  const MortarDev* mortars;
+  const int32_t* mnode_mortar;
+  const double* mnS;
+  int64_t mnodes;
+  const MortarTile* tiles;
+};
+
+static MortarArgs margs(const Level* L) {
+  MortarArgs a;
+  a.mortars = L->d_mortars;
+  a.mnode_mortar = L->d_mnode_mortar;
+  a.mnS = L->d_mnS;
+  a.mnodes = L->mortar_nodes;
+  a.tiles = L->d_mtiles;
+  return a;
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(kMortarTile) k_mortar(LevelArgs A, MortarArgs MA, Params P,
+                                                        const double* __restrict__ trq,
+                                                        const double* __restrict__ trg, double* __restrict__ out) {
+  constexpr int NV = (PASS == 1) ? 4 : 5;
+  __shared__ double sval[kMortarTile * 5];
+  __shared__ int scum[kMortarTile + 1];
+  const MortarTile mt = MA.tiles[blockIdx.x];
+  const Gas G = make_gas(P);
+  for (int i = threadIdx.x; i < mt.nodes; i += blockDim.x) {
+    const int64_t gp = mt.node_first + i;
+    const MortarDev M = MA.mortars[MA.mnode_mortar[gp]];
+    const int loc = (int)(gp - M.node_off);
+    const int a = loc % M.ma, b = loc / M.ma;
+    int dL, taL, tbL, sL;
+    face_dirs(M.fL, dL, taL, tbL, sL);
+    const int nLa = A.n[M.eL * 3 + taL], nLb = A.n[M.eL * 3 + tbL];
+    const int64_t pL = A.fo[M.eL * 6 + M.fL];
+    double qL[5], qR[5], gL[12], gR[12];
+    face_interp(trq + pL, A.fn, nLa, nLb, M.ma, M.mb, a, b, 5, qL);
+    if (PASS == 2) face_interp(trg + pL, A.fn, nLa, nLb, M.ma, M.mb, a, b, 12, gL);
+    double nS[3] = {MA.mnS[gp], MA.mnS[MA.mnodes + gp], MA.mnS[2 * MA.mnodes + gp]};
+    double S = sqrt(nS[0] * nS[0] + nS[1] * nS[1] + nS[2] * nS[2]);
+    double iS = 1.0 / S;
+    double nu[3] = {nS[0] * iS, nS[1] * iS, nS[2] * iS};
+    if (M.eR >= 0) {
+      int dR, taR, tbR, sR;
+      face_dirs(M.fR, dR, taR, tbR, sR);
+      const int Ra = A.n[M.eR * 3 + taR], Rb = A.n[M.eR * 3 + tbR];
+      const bool sw = M.orient & 1;
+      const int Ma = sw ? M.mb : M.ma, Mb = sw ? M.ma : M.mb;
+      int ia = sw ? b : a, ib = sw ? a : b;
+      if (M.orient & 2) ia = Ma - 1 - ia;
+      if (M.orient & 4) ib = Mb - 1 - ib;
+      const int64_t pR = A.fo[M.eR * 6 + M.fR];
+      face_interp(trq + pR, A.fn, Ra, Rb, Ma, Mb, ia, ib, 5, qR);
+      if (PASS == 2) face_interp(trg + pR, A.fn, Ra, Rb, Ma, Mb, ia, ib, 12, gR);
+    } else {
+      ghost(M.bc, qL, nu, G, qR);
+      if (PASS == 2)
+        for (int k = 0; k < 12; ++k) gR[k] = gL[k];
+    }
+    double* o = sval + i * 5;
+    if (PASS == 1) {
+      double ir, u[3], p, T, u2[3], T2;
+      to_prim(qL, G, ir, u, p, T);
+      to_prim(qR, G, ir, u2, p, T2);
+      o[0] = 0.5 * (u[0] + u2[0]);
+      o[1] = 0.5 * (u[1] + u2[1]);
+      o[2] = 0.5 * (u[2] + u2[2]);
+      o[3] = 0.5 * (T + T2);
+    } else {
+      double fr[5];
+      roe(qL, qR, nu, G, fr);
+      double fv[5] = {0, 0, 0, 0, 0};
+      if (!(M.eR < 0 && M.bc == DG_BC_SLIP)) {
+        double ir, u[3], p, T;
+        to_prim(qL, G, ir, u, p, T);
+        double mu = mu_of_T(T, G);
+        if (M.eR < 0 && M.bc == DG_BC_WALL) {
+          double z[3] = {0, 0, 0};
+          visc_flux(z, mu, gL, nu, G, false, fv);
+        } else {
+          double f1[5], f2[5], ir2, u2[3], p2, T2;
+          visc_flux(u, mu, gL, nu, G, true, f1);
+          to_prim(qR, G, ir2, u2, p2, T2);
+          visc_flux(u2, mu_of_T(T2, G), gR, nu, G, true, f2);
+          for (int v = 0; v < 5; ++v) fv[v] = 0.5 * (f1[v] + f2[v]);
+        }
+      }
+      for (int v = 0; v < 5; ++v) o[v] = S * (fr[v] - G.invRe * fv[v]);
+    }
+  }
+  // prefix of projection outputs per mortar in the tile
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int m = 0; m < mt.count; ++m) {
+      const MortarDev M = MA.mortars[mt.first + m];
+      int dL, taL, tbL, sL;
+      face_dirs(M.fL, dL, taL, tbL, sL);
+      scum[m] = acc;
+      acc += A.n[M.eL * 3 + taL] * A.n[M.eL * 3 + tbL];
+      if (M.eR >= 0) {
+        int dR, taR, tbR, sR;
+        face_dirs(M.fR, dR, taR, tbR, sR);
+        acc += A.n[M.eR * 3 + taR] * A.n[M.eR * 3 + tbR];
+      }
+    }
+    scum[mt.count] = acc;
+  }
+  __syncthreads();
+  const int total = scum[mt.count];
+  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+    int m = 0;
+    while (scum[m + 1] <= i) ++m;
+    const MortarDev M = MA.mortars[mt.first + m];
+    int r = i - scum[m];
+    const double* vals = sval + (M.node_off - mt.node_first) * 5;
+    int dL, taL, tbL, sL;
+    face_dirs(M.fL, dL, taL, tbL, sL);
+    const int nLa = A.n[M.eL * 3 + taL], nLb = A.n[M.eL * 3 + tbL];
+    double acc[5] = {0, 0, 0, 0, 0};
+    int64_t dst;
+    double sgn = 1.0;
+    if (r < nLa * nLb) {
+      int ka = r % nLa, kb = r / nLa;
+      dst = A.fo[M.eL * 6 + M.fL] + r;
+      if (M.flags & 1) {
+        for (int v = 0; v < NV; ++v) acc[v] = vals[r * 5 + v];
+      } else {
+        const double* Pa = c_T + ((size_t)M.ma * kNP + nLa) * kNP * kNP + ka * M.ma;
+        const double* Pb = c_T + ((size_t)M.mb * kNP + nLb) * kNP * kNP + kb * M.mb;
+        for (int bb = 0; bb < M.mb; ++bb)
+          for (int aa = 0; aa < M.ma; ++aa) {
+            double wgt = Pa[aa] * Pb[bb];
+            for (int v = 0; v < NV; ++v) acc[v] += wgt * vals[(bb * M.ma + aa) * 5 + v];
+          }
+      }
+    } else {
+      r -= nLa * nLb;
+      int dR, taR, tbR, sR;
+      face_dirs(M.fR, dR, taR, tbR, sR);
+      const int Ra = A.n[M.eR * 3 + taR], Rb = A.n[M.eR * 3 + tbR];
+      const bool sw = M.orient & 1;
+      const int Ma = sw ? M.mb : M.ma, Mb = sw ? M.ma : M.mb;
+      int ka = r % Ra, kb = r / Ra;
+      dst = A.fo[M.eR * 6 + M.fR] + r;
+      if (PASS == 2) sgn = -1.0;
+      const double* Pa = c_T + ((size_t)Ma * kNP + Ra) * kNP * kNP + ka * Ma;
+      const double* Pb = c_T + ((size_t)Mb * kNP + Rb) * kNP * kNP + kb * Mb;
+      for (int bb = 0; bb < M.mb; ++bb)
+        for (int aa = 0; aa < M.ma; ++aa) {
+          int ia = sw ? bb : aa, ib = sw ? aa : bb;
+          if (M.orient & 2) ia = Ma - 1 - ia;
+          if (M.orient & 4) ib = Mb - 1 - ib;
+          double wgt = Pa[ia] * Pb[ib];
+          if (wgt == 0.0) continue;
+          for (int v = 0; v < NV; ++v) acc[v] += wgt * vals[(bb * M.ma + aa) * 5 + v];
+        }
+    }
+    for (int v = 0; v < NV; ++v) out[v * A.fn + dst] = sgn * acc[v];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_volume: BR1 gradient (weak form), gradient traces, flux divergence
+// ---------------------------------------------------------------------------
+struct TileShape {
+  int n[3];
+  int nn, T;
+};
+
+DEV void load_dtables(double* sD, const double* src, const int* n, int dim) {
+  // sD[d][i][a] with stride kNP*kNP per direction
+  for (int d = 0; d < dim; ++d)
+    for (int k = threadIdx.x; k < n[d] * n[d]; k += blockDim.x) {
+      int i = k / n[d], a = k - i * n[d];
+      sD[d * kNP * kNP + i * kNP + a] = src[((size_t)n[d] * kNP + i) * kNP + a];
+    }
+}
+
+__global__ void __launch_bounds__(kTileNodes) k_volume(LevelArgs A, Params P, const double* __restrict__ q,
+                                                       const double* __restrict__ ust, double* __restrict__ trg,
+                                                       double* __restrict__ vol) {
+  extern __shared__ double smem[];
+  const ElemTile t = A.tiles[blockIdx.x];
+  const int n[3] = {t.n[0], t.n[1], t.n[2]};
+  const int nn = n[0] * n[1] * n[2];
+  const int T = t.count * nn;
+  const int dim = A.dim;
+  const Gas G = make_gas(P);
+  double* sD = smem;                          // 3 * kNP * kNP
+  double* sq = sD + 3 * kNP * kNP;            // 5 * T
+  double* sA = sq + 5 * T;                    // 15 * T: U(4) + Ja(9) | Ftilde(15)
+  double* sG = sA + 15 * T;                   // 12 * T
+  load_dtables(sD, c_Dhat, n, dim);
+  for (int i = threadIdx.x; i < T; i += blockDim.x) {
+    int le = i / nn, node = i - le * nn;
+    int e = A.tile_elems[t.first + le];
+    const int64_t gn = A.off[e] + node;
+    const double* qe = q + (size_t)5 * A.off[e];
+    double qq[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      qq[v] = qe[v * nn + node];
+      sq[v * T + i] = qq[v];
+    }
+    double ir, u[3], p, Tt;
+    to_prim(qq, G, ir, u, p, Tt);
+    sA[0 * T + i] = u[0];
+    sA[1 * T + i] = u[1];
+    sA[2 * T + i] = u[2];
+    sA[3 * T + i] = Tt;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) sA[(4 + c) * T + i] = A.geo[c * A.nodes + gn];
+  }
+  __syncthreads();
+  const int sd[3] = {1, n[0], n[0] * n[1]};
+  // ---- gradient ----
+  for (int i = threadIdx.x; i < T; i += blockDim.x) {
+    int le = i / nn, node = i - le * nn;
+    int e = A.tile_elems[t.first + le];
+    int idx[3] = {node % n[0], (node / n[0]) % n[1], node / (n[0] * n[1])};
+    double g[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) g[k] = 0.0;
+    for (int d = 0; d < dim; ++d) {
+      const int id = idx[d];
+      const int base = le * nn + node - id * sd[d];
+      const double* Drow = sD + d * kNP * kNP + id * kNP;
+      for (int a = 0; a < n[d]; ++a) {
+        const int la = base + a * sd[d];
+        const double c = Drow[a];
+        const double j0 = c * sA[(4 + d * 3 + 0) * T + la];
+        const double j1 = c * sA[(4 + d * 3 + 1) * T + la];
+        const double j2 = c * sA[(4 + d * 3 + 2) * T + la];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const double uv = sA[v * T + la];
+          g[v * 3 + 0] += j0 * uv;
+          g[v * 3 + 1] += j1 * uv;
+          g[v * 3 + 2] += j2 * uv;
+        }
+      }
+    }
+    // lifting of U* (outward metric already in fnS)
+    for (int f = 0; f < 2 * dim; ++f) {
+      int d, ta, tb, side;
+      face_dirs(f, d, ta, tb, side);
+      const double lw = side ? c_tab.lpw[n[d]][idx[d]] : c_tab.lmw[n[d]][idx[d]];
+      const int64_t p = A.fo[e * 6 + f] + idx[tb] * n[ta] + idx[ta];
+      const double m0 = lw * A.fnS[p], m1 = lw * A.fnS[A.fn + p], m2 = lw * A.fnS[2 * A.fn + p];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const double us = ust[v * A.fn + p];
+        g[v * 3 + 0] += m0 * us;
+        g[v * 3 + 1] += m1 * us;
+        g[v * 3 + 2] += m2 * us;
+      }
+    }
+    const double iJ = A.geo[9 * A.nodes + A.off[e] + node];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) sG[k * T + i] = g[k] * iJ;
+  }
+  __syncthreads();
+  // ---- gradient face traces ----
+  {
+    const int fsz[3] = {n[1] * n[2], n[0] * n[2], n[0] * n[1]};
+    int FE = 0;
+    for (int f = 0; f < 2 * dim; ++f) FE += fsz[f >> 1];
+    for (int i = threadIdx.x; i < t.count * FE; i += blockDim.x) {
+      int le = i / FE, r = i - le * FE;
+      int f = 0;
+      while (r >= fsz[f >> 1]) {
+        r -= fsz[f >> 1];
+        ++f;
+      }
+      int d, ta, tb, side;
+      face_dirs(f, d, ta, tb, side);
+      int ia = r % n[ta], ib = r / n[ta];
+      int idx[3];
+      idx[d] = 0;
+      idx[ta] = ia;
+      idx[tb] = ib;
+      int base = (idx[2] * n[1] + idx[1]) * n[0] + idx[0];
+      const double* lb = side ? c_tab.lp[n[d]] : c_tab.lm[n[d]];
+      int e = A.tile_elems[t.first + le];
+      int64_t p = A.fo[e * 6 + f] + r;
+      const double* s0 = sG + le * nn + base;
+      for (int k = 0; k < 12; ++k) {
+        double acc = 0.0;
+        for (int j = 0; j < n[d]; ++j) acc += lb[j] * s0[k * T + j * sd[d]];
+        trg[k * A.fn + p] = acc;
+      }
+    }
+  }
+  // ---- nodal contravariant fluxes (own node only: no cross-node hazard) ----
+  for (int i = threadIdx.x; i < T; i += blockDim.x) {
+    double qq[5], u[3], Tt, Ja[9], gr[12];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) qq[v] = sq[v * T + i];
+    u[0] = sA[0 * T + i];
+    u[1] = sA[1 * T + i];
+    u[2] = sA[2 * T + i];
+    Tt = sA[3 * T + i];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) Ja[c] = sA[(4 + c) * T + i];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) gr[k] = sG[k * T + i];
+    const double p = Tt * qq[0] / G.gM2;
+    const double mu = mu_of_T(Tt, G);
+    double F[15];
+    for (int d = 0; d < dim; ++d) {
+      const double* nv = Ja + 3 * d;
+      const double un = u[0] * nv[0] + u[1] * nv[1] + u[2] * nv[2];
+      double fv[5];
+      visc_flux(u, mu, gr, nv, G, true, fv);
+      F[d * 5 + 0] = qq[0] * un;
+      F[d * 5 + 1] = qq[1] * un + p * nv[0] - G.invRe * fv[1];
+      F[d * 5 + 2] = qq[2] * un + p * nv[1] - G.invRe * fv[2];
+      F[d * 5 + 3] = qq[3] * un + p * nv[2] - G.invRe * fv[3];
+      F[d * 5 + 4] = (qq[4] + p) * un - G.invRe * fv[4];
+    }
+    for (int k = 0; k < 5 * dim; ++k) sA[k * T + i] = F[k];
+  }
+  __syncthreads();
+  // ---- weak-form divergence ----
+  for (int i = threadIdx.x; i < T; i += blockDim.x) {
+    int le = i / nn, node = i - le * nn;
+    int e = A.tile_elems[t.first + le];
+    int idx[3] = {node % n[0], (node / n[0]) % n[1], node / (n[0] * n[1])};
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int d = 0; d < dim; ++d) {
+      const int id = idx[d];
+      const int base = le * nn + node - id * sd[d];
+      const double* Drow = sD + d * kNP * kNP + id * kNP;
+      for (int a = 0; a < n[d]; ++a) {
+        const int la = base + a * sd[d];
+        const double c = Drow[a];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) acc[v] += c * sA[(d * 5 + v) * T + la];
+      }
+    }
+    double* ve = vol + (size_t)5 * A.off[e];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) ve[v * nn + node] = acc[v];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_surface: surface terms, r = S - A; optional RK3 stage and max|r|
+// ---------------------------------------------------------------------------
+struct RKArgs {
+  int stage;          // -1: plain residual, 0..2 RK3 stage
+  double a, b;
+  double* g;          // RK register
+  const double* dt;   // device scalar
+  double* qupd;       // state updated in place
+};
+
+__global__ void __launch_bounds__(kTileNodes) k_surface(LevelArgs A, const double* __restrict__ vol,
+                                                        const double* __restrict__ fst, const double* __restrict__ s,
+                                                        double* __restrict__ r, double* norm, RKArgs rk) {
+  const ElemTile t = A.tiles[blockIdx.x];
+  const int n[3] = {t.n[0], t.n[1], t.n[2]};
+  const int nn = n[0] * n[1] * n[2];
+  const int T = t.count * nn;
+  double lmax = 0.0;
+  double dt = (rk.stage >= 0) ? *rk.dt : 0.0;
+  for (int i = threadIdx.x; i < T; i += blockDim.x) {
+    int le = i / nn, node = i - le * nn;
+    int e = A.tile_elems[t.first + le];
+    int idx[3] = {node % n[0], (node / n[0]) % n[1], node / (n[0] * n[1])};
+    const size_t base = (size_t)5 * A.off[e] + node;
+    double acc[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) acc[v] = vol[base + v * nn];
+    for (int f = 0; f < 2 * A.dim; ++f) {
+      int d, ta, tb, side;
+      face_dirs(f, d, ta, tb, side);
+      const double lw = side ? c_tab.lpw[n[d]][idx[d]] : c_tab.lmw[n[d]][idx[d]];
+      const int64_t p = A.fo[e * 6 + f] + idx[tb] * n[ta] + idx[ta];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) acc[v] += lw * fst[v * A.fn + p];
+    }
+    const double iJ = A.geo[9 * A.nodes + A.off[e] + node];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      double rv = (s ? s[base + v * nn] : 0.0) - acc[v] * iJ;
+      lmax = (rv != rv) ? INFINITY : fmax(lmax, fabs(rv));  // a NaN residual reads as +inf
+      if (rk.stage < 0) {
+        r[base + v * nn] = rv;
+      } else {
+        double gv = (rk.stage == 0 ? 0.0 : rk.a * rk.g[base + v * nn]) + dt * rv;
+        rk.g[base + v * nn] = gv;
+        rk.qupd[base + v * nn] += rk.b * gv;
+      }
+    }
+  }
+  if (norm) {
+    for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(norm, lmax);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_isolated: strong-form element-local operator; r = S - A, optional tau
+// ---------------------------------------------------------------------------
+struct TauArgs {
+  const double* rho;     // chained restriction of the finest isolated residual (or null)
+  double* table;         // K x 3 x 16
+  const int32_t* fine_orders;  // K x 3
+  int dir, slot;
+};
+
+__global__ void __launch_bounds__(kTileNodes) k_isolated(LevelArgs A, Params P, const double* __restrict__ q,
+                                                         const double* __restrict__ s, double* __restrict__ r,
+                                                         TauArgs tau) {
+  extern __shared__ double smem[];
+  const ElemTile t = A.tiles[blockIdx.x];
+  const int n[3] = {t.n[0], t.n[1], t.n[2]};
+  const int nn = n[0] * n[1] * n[2];
+  const int T = t.count * nn;
+  const int dim = A.dim;
+  const Gas G = make_gas(P);
+  double* sD = smem;
+  double* sq = sD + 3 * kNP * kNP;
+  double* sA = sq + 5 * T;
+  double* sG = sA + 15 * T;
+  load_dtables(sD, c_D, n, dim);
+  for (int i = threadIdx.x; i < T; i += blockDim.x) {
+    int le = i / nn, node = i - le * nn;
+    int e = A.tile_elems[t.first + le];
+    const int64_t gn = A.off[e] + node;
+    const double* qe = q + (size_t)5 * A.off[e];
+    double qq[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      qq[v] = qe[v * nn + node];
+      sq[v * T + i] = qq[v];
+    }
+    double ir, u[3], p, Tt;
+    to_prim(qq, G, ir, u, p, Tt);
+    sA[0 * T + i] = u[0];
+    sA[1 * T + i] = u[1];
+    sA[2 * T + i] = u[2];
+    sA[3 * T + i] = Tt;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) sA[(4 + c) * T + i] = A.geo[c * A.nodes + gn];
+  }
+  __syncthreads();
+  const int sd[3] = {1, n[0], n[0] * n[1]};
+  for (int i = threadIdx.x; i < T; i += blockDim.x) {
+    int le = i / nn, node = i - le * nn;
+    int e = A.tile_elems[t.first + le];
+    int idx[3] = {node % n[0], (node / n[0]) % n[1], node / (n[0] * n[1])};
+    double g[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) g[k] = 0.0;
+    for (int d = 0; d < dim; ++d) {
+      const int id = idx[d];
+      const int base = le * nn + node - id * sd[d];
+      const double* Drow = sD + d * kNP * kNP + id * kNP;
+      for (int a = 0; a < n[d]; ++a) {
+        const int la = base + a * sd[d];
+        const double c = Drow[a];
+        const double j0 = c * sA[(4 + d * 3 + 0) * T + la];
+        const double j1 = c * sA[(4 + d * 3 + 1) * T + la];
+        const double j2 = c * sA[(4 + d * 3 + 2) * T + la];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const double uv = sA[v * T + la];
+          g[v * 3 + 0] += j0 * uv;
+          g[v * 3 + 1] += j1 * uv;
+          g[v * 3 + 2] += j2 * uv;
+        }
+      }
+    }
+    const double iJ = A.geo[9 * A.nodes + A.off[e] + node];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) sG[k * T + i] = g[k] * iJ;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < T; i += blockDim.x) {
+    double qq[5], u[3], Tt, Ja[9], gr[12];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) qq[v] = sq[v * T + i];
+    u[0] = sA[0 * T + i];
+    u[1] = sA[1 * T + i];
+    u[2] = sA[2 * T + i];
+    Tt = sA[3 * T + i];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) Ja[c] = sA[(4 + c) * T + i];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) gr[k] = sG[k * T + i];
+    const double p = Tt * qq[0] / G.gM2;
+    const double mu = mu_of_T(Tt, G);
+    double F[15];
+    for (int d = 0; d < dim; ++d) {
+      const double* nv = Ja + 3 * d;
+      const double un = u[0] * nv[0] + u[1] * nv[1] + u[2] * nv[2];
+      double fv[5];
+      visc_flux(u, mu, gr, nv, G, true, fv);
+      F[d * 5 + 0] = qq[0] * un;
+      F[d * 5 + 1] = qq[1] * un + p * nv[0] - G.invRe * fv[1];
+      F[d * 5 + 2] = qq[2] * un + p * nv[1] - G.invRe * fv[2];
+      F[d * 5 + 3] = qq[3] * un + p * nv[2] - G.invRe * fv[3];
+      F[d * 5 + 4] = (qq[4] + p) * un - G.invRe * fv[4];
+    }
+    for (int k = 0; k < 5 * dim; ++k) sA[k * T + i] = F[k];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < T; i += blockDim.x) {
+    int le = i / nn, node = i - le * nn;
+    int e = A.tile_elems[t.first + le];
+    int idx[3] = {node % n[0], (node / n[0]) % n[1], node / (n[0] * n[1])};
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int d = 0; d < dim; ++d) {
+      const int id = idx[d];
+      const int base = le * nn + node - id * sd[d];
+      const double* Drow = sD + d * kNP * kNP + id * kNP;
+      for (int a = 0; a < n[d]; ++a) {
+        const int la = base + a * sd[d];
+        const double c = Drow[a];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) acc[v] += c * sA[(d * 5 + v) * T + la];
+      }
+    }
+    const double iJ = A.geo[9 * A.nodes + A.off[e] + node];
+    const size_t base = (size_t)5 * A.off[e] + node;
+    double tmax = 0.0;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      double rv = (s ? s[base + v * nn] : 0.0) - acc[v] * iJ;
+      if (tau.table) {
+        double tv = tau.rho ? rv - tau.rho[base + v * nn] : rv;
+        tmax = fmax(tmax, fabs(tv));
+      } else {
+        r[base + v * nn] = rv;
+      }
+    }
+    if (tau.table && tau.fine_orders[e * 3 + tau.dir] > tau.slot)
+      atomic_max_nonneg(tau.table + ((size_t)e * 3 + tau.dir) * kTauSlots + tau.slot, tmax);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_cfl: global minimum of the explicit step
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTileNodes) k_cfl(LevelArgs A, Params P, const double* __restrict__ q, double* dtmin) {
+  const ElemTile t = A.tiles[blockIdx.x];
+  const int n[3] = {t.n[0], t.n[1], t.n[2]};
+  const int nn = n[0] * n[1] * n[2];
+  const int T = t.count * nn;
+  const Gas G = make_gas(P);
+  double best = 1e300;
+  for (int i = threadIdx.x; i < T; i += blockDim.x) {
+    int le = i / nn, node = i - le * nn;
+    int e = A.tile_elems[t.first + le];
+    const int64_t gn = A.off[e] + node;
+    const double* qe = q + (size_t)5 * A.off[e];
+    double qq[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) qq[v] = qe[v * nn + node];
+    double ir, u[3], p, Tt;
+    to_prim(qq, G, ir, u, p, Tt);
+    const double c = sqrt(G.g * p * ir);
+    const double vel = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const double nu = mu_of_T(Tt, G) * ir * G.invRe;
+    const double iJ = A.geo[9 * A.nodes + gn];
+    for (int d = 0; d < A.dim; ++d) {
+      const int N = n[d] - 1;
+      if (N <= 0) continue;
+      double j0 = A.geo[(3 * d + 0) * A.nodes + gn], j1 = A.geo[(3 * d + 1) * A.nodes + gn],
+             j2 = A.geo[(3 * d + 2) * A.nodes + gn];
+      double h = 2.0 / (sqrt(j0 * j0 + j1 * j1 + j2 * j2) * iJ);
+      double N2 = (double)N * (double)N;
+      best = fmin(best, G.Ca * h / ((vel + c) * N2));
+      best = fmin(best, G.Cnu * h * h / (nu * N2 * N2));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) atomic_min_pos(dtmin, best);
+}
+
+// ---------------------------------------------------------------------------
+// transfers between order maps: out_e = (T2 x T1 x T0) (in_e - sub_e)
+// ---------------------------------------------------------------------------
+__global__ void k_transfer(int dim, const int32_t* __restrict__ nf, const int32_t* __restrict__ offf,
+                           const int32_t* __restrict__ nt, const int32_t* __restrict__ offt, int nvar,
+                           const double* __restrict__ in, const double* __restrict__ sub, double* __restrict__ out,
+                           int accumulate) {
+  const int e = blockIdx.x;
+  const int f0 = nf[e * 3], f1 = nf[e * 3 + 1], f2 = nf[e * 3 + 2];
+  const int t0 = nt[e * 3], t1 = nt[e * 3 + 1], t2 = nt[e * 3 + 2];
+  const int nnf = f0 * f1 * f2, nnt = t0 * t1 * t2;
+  const double* T0 = c_T + ((size_t)f0 * kNP + t0) * kNP * kNP;
+  const double* T1 = c_T + ((size_t)f1 * kNP + t1) * kNP * kNP;
+  const double* T2 = c_T + ((size_t)f2 * kNP + t2) * kNP * kNP;
+  const double* ie = in + (size_t)nvar * offf[e];
+  const double* se = sub ? sub + (size_t)nvar * offf[e] : nullptr;
+  double* oe = out + (size_t)nvar * offt[e];
+  for (int i = threadIdx.x; i < nnt * nvar; i += blockDim.x) {
+    int v = i / nnt, j = i - v * nnt;
+    int j0 = j % t0, j1 = (j / t0) % t1, j2 = j / (t0 * t1);
+    double acc = 0.0;
+    for (int k2 = 0; k2 < f2; ++k2) {
+      double w2 = T2[j2 * f2 + k2];
+      if (w2 == 0.0) continue;
+      for (int k1 = 0; k1 < f1; ++k1) {
+        double w21 = w2 * T1[j1 * f1 + k1];
+        if (w21 == 0.0) continue;
+        for (int k0 = 0; k0 < f0; ++k0) {
+          int k = (k2 * f1 + k1) * f0 + k0;
+          double x = ie[v * nnf + k];
+          if (se) x -= se[v * nnf + k];
+          acc += w21 * T0[j0 * f0 + k0] * x;
+        }
+      }
+    }
+    if (accumulate)
+      oe[v * nnt + j] += acc;
+    else
+      oe[v * nnt + j] = acc;
+  }
+}
+
+__global__ void k_fill(double* p, double v, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
+}
+__global__ void k_axpby(double* y, double a, const double* x, double b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
+__global__ void k_sub3(double* o, const double* a, const double* b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    o[i] = a[i] - b[i];
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+static size_t vol_smem(const Level* L) {
+  return (size_t)(3 * kNP * kNP + 32 * L->tile_smem_nodes) * sizeof(double);
+}
+
+static int configure_smem() {
+  static int done_dev = -1;
+  int dev = 0;
+  DG_CUDA_TRY(cudaGetDevice(&dev));
+  if (done_dev == dev) return DG_OK;
+  const int big = (int)((3 * kNP * kNP + 32 * kMaxElemNodes) * sizeof(double));
+  DG_CUDA_TRY(cudaFuncSetAttribute(k_volume, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  DG_CUDA_TRY(cudaFuncSetAttribute(k_isolated, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  DG_CUDA_TRY(cudaFuncSetAttribute(k_trace_q, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(5 * kMaxElemNodes * sizeof(double))));
+  done_dev = dev;
+  return DG_OK;
+}
+
+static int grid_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  return (int)std::max<int64_t>(1, b);
+}
+
+int fill(double* p, double v, int64_t n, cudaStream_t st) {
+  k_fill<<<grid_for(n), 256, 0, st>>>(p, v, n);
+  DG_CUDA_TRY(cudaGetLastError());
+  return DG_OK;
+}
+int axpby(double* y, double a, const double* x, double b, int64_t n, cudaStream_t st) {
+  k_axpby<<<grid_for(n), 256, 0, st>>>(y, a, x, b, n);
+  DG_CUDA_TRY(cudaGetLastError());
+  return DG_OK;
+}
+int sub3(double* o, const double* a, const double* b, int64_t n, cudaStream_t st) {
+  k_sub3<<<grid_for(n), 256, 0, st>>>(o, a, b, n);
+  DG_CUDA_TRY(cudaGetLastError());
+  return DG_OK;
+}
+int reset_max(double* d, cudaStream_t st) { return fill(d, 0.0, 1, st); }
+int reset_min(double* d, cudaStream_t st) { return fill(d, 1e300, 1, st); }
+int read_scalar(const double* d, double* h, cudaStream_t st) {
+  DG_CUDA_TRY(cudaMemcpyAsync(h, d, sizeof(double), cudaMemcpyDeviceToHost, st));
+  DG_CUDA_TRY(cudaStreamSynchronize(st));
+  return DG_OK;
+}
+
+int residual(const dg_mesh* m, Level* L, const double* q, const double* s, double* r, bool isolated,
+             cudaStream_t st, double* d_norm, int rk_stage, double* rk_g, const double* d_dt) {
+  int rc = configure_smem();
+  if (rc != DG_OK) return rc;
+  LevelArgs A = largs(L);
+  if (isolated) {
+    TauArgs ta{nullptr, nullptr, nullptr, 0, 0};
+    k_isolated<<<L->n_tiles, kTileNodes, vol_smem(L), st>>>(A, m->prm, q, s, r, ta);
+    DG_CUDA_TRY(cudaGetLastError());
+    return DG_OK;
+  }
+  MortarArgs MA = margs(L);
+  k_trace_q<<<L->n_tiles, kTileNodes, 5 * L->tile_smem_nodes * sizeof(double), st>>>(A, q, L->d_trq);
+  k_mortar<1><<<L->n_mtiles, kMortarTile, 0, st>>>(A, MA, m->prm, L->d_trq, nullptr, L->d_ust);
+  k_volume<<<L->n_tiles, kTileNodes, vol_smem(L), st>>>(A, m->prm, q, L->d_ust, L->d_trg, L->d_vol);
+  k_mortar<2><<<L->n_mtiles, kMortarTile, 0, st>>>(A, MA, m->prm, L->d_trq, L->d_trg, L->d_fst);
+  RKArgs rk;
+  rk.stage = rk_stage;
+  rk.a = (rk_stage == 1) ? -5.0 / 9.0 : (rk_stage == 2 ? -153.0 / 128.0 : 0.0);
+  rk.b = (rk_stage == 0) ? 1.0 / 3.0 : (rk_stage == 1 ? 15.0 / 16.0 : 8.0 / 15.0);
+  rk.g = rk_g;
+  rk.dt = d_dt;
+  rk.qupd = const_cast<double*>(q);
+  k_surface<<<L->n_tiles, kTileNodes, 0, st>>>(A, L->d_vol, L->d_fst, s, r, d_norm, rk);
+  DG_CUDA_TRY(cudaGetLastError());
+  return DG_OK;
+}
+
+int cfl_dt(const dg_mesh* m, Level* L, const double* q, double* d_dt, cudaStream_t st) {
+  int rc = reset_min(d_dt, st);
+  if (rc != DG_OK) return rc;
+  k_cfl<<<L->n_tiles, kTileNodes, 0, st>>>(largs(L), m->prm, q, d_dt);
+  DG_CUDA_TRY(cudaGetLastError());
+  return DG_OK;
+}
+
+int transfer(const dg_mesh* m, const Level* from, const Level* to, int nvar, const double* in, double* out,
+             cudaStream_t st, const double* sub, bool accumulate) {
+  (void)m;
+  k_transfer<<<from->K, 128, 0, st>>>(from->dim, from->d_n, from->d_off, to->d_n, to->d_off, nvar, in, sub, out,
+                                      accumulate ? 1 : 0);
+  DG_CUDA_TRY(cudaGetLastError());
+  return DG_OK;
+}
+
+static int tau_reduce(const Level* L, const double* r, const double* rho, int dir, int slot,
+                      const int32_t* fine_orders, double* table, cudaStream_t st);
+
+int tau_accumulate(const dg_mesh* m, Level* L, const double* q, const double* s, const double* rho, bool isolated,
+                   int dir, int slot, const int32_t* fine_orders_dev, double* d_tau, cudaStream_t st) {
+  int rc = configure_smem();
+  if (rc != DG_OK) return rc;
+  if (!isolated) {
+    // full operator: residual into the level's scratch, then reduce
+    rc = residual(m, L, q, s, L->d_R, false, st, nullptr, -1, nullptr, nullptr);
+    if (rc != DG_OK) return rc;
+    return tau_reduce(L, L->d_R, rho, dir, slot, fine_orders_dev, d_tau, st);
+  }
+  TauArgs ta{rho, d_tau, fine_orders_dev, dir, slot};
+  k_isolated<<<L->n_tiles, kTileNodes, vol_smem(L), st>>>(largs(L), m->prm, q, s, nullptr, ta);
+  DG_CUDA_TRY(cudaGetLastError());
+  return DG_OK;
+}
+
+__global__ void k_tau_reduce(LevelArgs A, const double* __restrict__ r, const double* __restrict__ rho, int dir,
+                             int slot, const int32_t* __restrict__ fine_orders, double* table) {
+  const ElemTile t = A.tiles[blockIdx.x];
+  const int nn = t.n[0] * t.n[1] * t.n[2];
+  const int T = t.count * nn;
+  for (int i = threadIdx.x; i < T; i += blockDim.x) {
+    int le = i / nn, node = i - le * nn;
+    int e = A.tile_elems[t.first + le];
+    const size_t base = (size_t)5 * A.off[e] + node;
+    double tmax = 0.0;
+    for (int v = 0; v < 5; ++v) {
+      double tv = r[base + v * nn] - (rho ? rho[base + v * nn] : 0.0);
+      tmax = fmax(tmax, fabs(tv));
+    }
+    if (fine_orders[e * 3 + dir] > slot) atomic_max_nonneg(table + ((size_t)e * 3 + dir) * kTauSlots + slot, tmax);
+  }
+}
+
+static int tau_reduce(const Level* L, const double* r, const double* rho, int dir, int slot,
+                      const int32_t* fine_orders, double* table, cudaStream_t st) {
+  k_tau_reduce<<<L->n_tiles, kTileNodes, 0, st>>>(largs(L), r, rho, dir, slot, fine_orders, table);
+  DG_CUDA_TRY(cudaGetLastError());
+  return DG_OK;
+}
+
+}  // namespace dg

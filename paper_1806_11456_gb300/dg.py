@@ -1,0 +1,198 @@
+"""Python binding of the C ABI in include/dg.h (argument marshalling only).
+
+Every computation runs in the CUDA library libdgpmg.so; this module loads it
+(failing loudly when it is missing or no CUDA device is present), converts
+torch tensors to device pointers and the current torch stream to a
+cudaStream_t, and maps status codes to exceptions.  State tensors are float64
+CUDA tensors in the element-blocked layout of ``Mesh.layout()``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdgpmg.so")
+
+DG_ISOLATED = 1
+DG_NORM = 2
+TAU_SLOTS = 16
+
+
+class DGError(RuntimeError):
+    pass
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("K", ctypes.c_int32), ("M", ctypes.c_int32),
+                ("xmap", ctypes.POINTER(ctypes.c_double)), ("ftab", ctypes.POINTER(ctypes.c_int32)),
+                ("params", ctypes.c_double * 16)]
+
+
+class MGParams(ctypes.Structure):
+    _fields_ = [("beta1", ctypes.c_int32), ("beta2", ctypes.c_int32), ("beta_c", ctypes.c_int32),
+                ("direction", ctypes.c_int32), ("coarsest", ctypes.c_int32), ("delta_n", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
+
+
+class CycleReport(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("residual_evals", ctypes.c_int32), ("dof_evals", ctypes.c_double),
+                ("rnorm", ctypes.c_double)]
+
+
+class AdaptParams(ctypes.Structure):
+    _fields_ = [("tau_max", ctypes.c_double), ("n_min", ctypes.c_int32), ("n_max", ctypes.c_int32),
+                ("cap", ctypes.c_int32), ("jump_rule", ctypes.c_int32), ("conform_tag", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int32)
+
+EXPORTS = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_layout", "dg_residual", "dg_cfl_dt", "dg_smooth",
+           "dg_pmg_vcycle", "dg_tau_estimate", "dg_adapt", "dg_transfer_state", "dg_last_error"]
+
+
+def lib(path=LIB_PATH):
+    """Load libdgpmg.so (no CUDA call is made here)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise DGError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    L = ctypes.CDLL(path)
+    L.dg_last_error.restype = ctypes.c_char_p
+    L.dg_mesh_create.argtypes = [ctypes.POINTER(MeshDesc), _ip, ctypes.POINTER(_vp)]
+    L.dg_mesh_destroy.argtypes = [_vp]
+    L.dg_mesh_layout.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    L.dg_residual.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, _dp, _vp]
+    L.dg_cfl_dt.argtypes = [_vp, _vp, _dp, _vp]
+    L.dg_smooth.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp]
+    L.dg_pmg_vcycle.argtypes = [_vp, _vp, _vp, ctypes.POINTER(MGParams), ctypes.c_int, ctypes.POINTER(CycleReport), _vp]
+    L.dg_tau_estimate.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _vp]
+    L.dg_adapt.argtypes = [_vp, _dp, ctypes.POINTER(AdaptParams), _ip]
+    L.dg_transfer_state.argtypes = [_vp, _vp, _vp, _vp, _vp]
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != 0:
+        raise DGError(f"dg error {rc}: {lib().dg_last_error().decode()}")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise DGError("state tensors must be contiguous float64 CUDA tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Mesh:
+    """A mesh with an order map: geometry, faces and multigrid levels live on
+    the device inside the library."""
+
+    def __init__(self, mesh, orders, params):
+        import torch
+        if not torch.cuda.is_available():
+            raise DGError("no CUDA device: the DGSEM library has no CPU path")
+        self.dim, self.K, self.M = int(mesh["dim"]), int(mesh["K"]), int(mesh["M"])
+        self._xmap = np.ascontiguousarray(mesh["xmap"], dtype=np.float64)
+        self._ftab = np.ascontiguousarray(mesh["ftab"], dtype=np.int32)
+        self.orders = np.ascontiguousarray(orders, dtype=np.int32)
+        self.params = np.asarray(params, dtype=np.float64)
+        self.mesh = mesh
+        d = MeshDesc()
+        d.dim, d.K, d.M = self.dim, self.K, self.M
+        d.xmap = self._xmap.ctypes.data_as(_dp)
+        d.ftab = self._ftab.ctypes.data_as(_ip)
+        for i in range(16):
+            d.params[i] = float(self.params[i])
+        h = _vp()
+        torch.cuda.current_device()  # make sure the CUDA context exists
+        _check(lib().dg_mesh_create(ctypes.byref(d), self.orders.ctypes.data_as(_ip), ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dg_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def layout(self):
+        n = ctypes.c_int64()
+        off = np.zeros(self.K + 1, dtype=np.int64)
+        _check(lib().dg_mesh_layout(self.h, ctypes.byref(n), off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        return int(n.value), off
+
+    @property
+    def nodes(self):
+        return self.layout()[0]
+
+    def residual(self, q, s=None, r=None, isolated=False, norm=False, stream=None):
+        import torch
+        if r is None:
+            r = torch.empty_like(q)
+        flags = (DG_ISOLATED if isolated else 0) | (DG_NORM if norm else 0)
+        rn = ctypes.c_double(0.0)
+        _check(lib().dg_residual(self.h, _ptr(q), _ptr(s), _ptr(r), flags, ctypes.byref(rn), _stream(stream)))
+        return (r, rn.value) if norm else r
+
+    def cfl_dt(self, q, stream=None):
+        dt = ctypes.c_double()
+        _check(lib().dg_cfl_dt(self.h, _ptr(q), ctypes.byref(dt), _stream(stream)))
+        return dt.value
+
+    def smooth(self, q, s=None, sweeps=1, stream=None):
+        _check(lib().dg_smooth(self.h, _ptr(q), _ptr(s), int(sweeps), _stream(stream)))
+        return q
+
+    def vcycle(self, q, s=None, beta1=3, beta2=3, beta_c=3, direction=-1, coarsest=1, delta_n=1,
+               want_norm=False, stream=None):
+        mg = MGParams()
+        mg.beta1, mg.beta2, mg.beta_c, mg.direction, mg.coarsest, mg.delta_n = \
+            beta1, beta2, beta_c, direction, coarsest, delta_n
+        rep = CycleReport()
+        _check(lib().dg_pmg_vcycle(self.h, _ptr(q), _ptr(s), ctypes.byref(mg), int(bool(want_norm)),
+                                   ctypes.byref(rep), _stream(stream)))
+        return dict(levels=rep.levels, residual_evals=rep.residual_evals, dof_evals=rep.dof_evals,
+                    rnorm=rep.rnorm)
+
+    def tau_estimate(self, q, s=None, dir_mask=7, with_correction=True, isolated=True, stream=None):
+        tab = np.zeros((self.K, 3, TAU_SLOTS))
+        _check(lib().dg_tau_estimate(self.h, _ptr(q), _ptr(s), int(dir_mask), int(bool(with_correction)),
+                                     int(bool(isolated)), tab.ctypes.data_as(_dp), _stream(stream)))
+        return tab
+
+    def adapt(self, tau, tau_max, n_min, n_max, cap=0, jump_rule=0, conform_tag=-1):
+        ap = AdaptParams()
+        ap.tau_max, ap.n_min, ap.n_max, ap.cap, ap.jump_rule, ap.conform_tag = \
+            float(tau_max), n_min, n_max, cap, jump_rule, conform_tag
+        tau = np.ascontiguousarray(tau, dtype=np.float64)
+        out = np.zeros((self.K, 3), dtype=np.int32)
+        _check(lib().dg_adapt(self.h, tau.ctypes.data_as(_dp), ctypes.byref(ap), out.ctypes.data_as(_ip)))
+        return out
+
+    def transfer_state_to(self, other, q_from, q_to=None, stream=None):
+        import torch
+        if q_to is None:
+            q_to = torch.empty(5 * other.nodes, dtype=torch.float64, device=q_from.device)
+        _check(lib().dg_transfer_state(self.h, _ptr(q_from), other.h, _ptr(q_to), _stream(stream)))
+        return q_to

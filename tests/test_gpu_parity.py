@@ -1,0 +1,238 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Tolerance (FP64): |x_gpu - x_oracle|_inf <= 1e-12 * s_x with s_x the
+magnitude of the quantity's terms -- for residuals the oracle's volume term
+max |M^{-1} volume integral| (the residual itself cancels towards zero), for
+states max |Q|, for tau tables the same volume scale of the reference state.
+Both sides round differently (summation order, FMA contraction on the GPU),
+so agreement is to a few hundred ulps of the term magnitudes, far inside the
+bound."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1806_11456_gb300 import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def dg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__ as g
+    g.build()
+    from paper_1806_11456_gb300 import dg as mod
+    return mod
+
+
+def _dev(x):
+    import torch
+    return torch.tensor(np.asarray(x, dtype=np.float64), device="cuda")
+
+
+def _cases():
+    c = {}
+    c["c1_box_N3"] = lambda: syn.config_box_c1()
+    def mixed3d():
+        mesh = syn.periodic_box(3, 2, 2)
+        prm = syn.flow_params(mach=0.3, re=100.0)
+        o = syn.random_orders(mesh["K"], 3, 1, 5, 11)
+        return mesh, o, prm, syn.perturbed_state(mesh, o, prm, 4)
+    c["periodic3d_mortars"] = mixed3d
+    def rotated():
+        mesh = syn.rotate_elements(syn.periodic_box(2, 2, 2), seed=4, frac=0.75)
+        prm = syn.flow_params(mach=0.3, re=50.0)
+        o = syn.random_orders(mesh["K"], 3, 1, 4, 12)
+        return mesh, o, prm, syn.perturbed_state(mesh, o, prm, 5)
+    c["rotated3d_orientations"] = rotated
+    def plate():
+        mesh = syn.box_mesh(np.linspace(-0.2, 1, 6), [0, 0.01, 0.05, 0.12, 0.3],
+                            bc=dict(xmin=1, xmax=2, ymin=lambda i, k: 3 if i < 1 else 4, ymax=1))
+        prm = syn.flow_params(mach=0.2, re=1e4)
+        o = syn.random_orders(mesh["K"], 2, 1, 7, 13)
+        return mesh, o, prm, syn.perturbed_state(mesh, o, prm, 6)
+    c["plate2d_all_bcs"] = plate
+    def single():
+        mesh = syn.box_mesh([0, 1], [0, 2], [0, 0.5], bc=dict(xmin=1, xmax=2, ymin=4, ymax=3, zmin=1, zmax=2))
+        prm = syn.flow_params(mach=0.4, re=30.0)
+        o = np.array([[2, 3, 1]], dtype=np.int32)
+        return mesh, o, prm, syn.perturbed_state(mesh, o, prm, 7)
+    c["single_element_boundaries"] = single
+    def big_tiles():  # elements of more than 256 nodes: one element per CTA
+        mesh = syn.periodic_box(2, 1, 1)
+        prm = syn.flow_params(mach=0.3, re=100.0)
+        o = np.array([[8, 7, 6], [5, 8, 8]], dtype=np.int32)
+        return mesh, o, prm, syn.perturbed_state(mesh, o, prm, 8)
+    c["large_elements"] = big_tiles
+    return c
+
+
+CASES = _cases()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("isolated", [False, True])
+def test_residual_parity(dg, name, isolated):
+    mesh, o, prm, q = CASES[name]()
+    s = syn.random_source(mesh, o, 3)
+    M = dg.Mesh(mesh, o, prm)
+    r = M.residual(_dev(q), _dev(s), isolated=isolated).cpu().numpy()
+    ro = orc.residual(mesh, o, prm, q, s, isolated)
+    scale = orc.volume_scale(mesh, o, prm, q)
+    err = np.max(np.abs(r - ro))
+    assert err <= TOL * scale, (err, scale)
+
+
+def test_residual_norm_and_null_source(dg):
+    mesh, o, prm, q = CASES["periodic3d_mortars"]()
+    M = dg.Mesh(mesh, o, prm)
+    r, rn = M.residual(_dev(q), None, norm=True)
+    ro = orc.residual(mesh, o, prm, q)
+    assert abs(rn - np.max(np.abs(ro))) <= TOL * orc.volume_scale(mesh, o, prm, q)
+
+
+def test_flat_plate_full_size_residual(dg):
+    """The flat-plate workload at full size (60 x 24 elements, N = 7) on a
+    perturbed boundary-layer-like state: every element compared."""
+    mesh = syn.flat_plate_mesh()
+    prm = syn.flow_params(mach=0.2, re=1e5)
+    o = syn.uniform_orders(mesh["K"], 2, 7)
+    q = syn.perturbed_state(mesh, o, prm, 21, amp=0.02)
+    M = dg.Mesh(mesh, o, prm)
+    r = M.residual(_dev(q)).cpu().numpy()
+    ro = orc.residual(mesh, o, prm, q)
+    assert np.max(np.abs(r - ro)) <= TOL * orc.volume_scale(mesh, o, prm, q)
+
+
+@pytest.mark.parametrize("name", ["c1_box_N3", "periodic3d_mortars", "plate2d_all_bcs"])
+def test_cfl_dt_parity(dg, name):
+    mesh, o, prm, q = CASES[name]()
+    M = dg.Mesh(mesh, o, prm)
+    dt = M.cfl_dt(_dev(q))
+    assert abs(dt - orc.cfl_dt(mesh, o, prm, q)) <= 1e-14 * dt
+
+
+@pytest.mark.parametrize("name", ["c1_box_N3", "plate2d_all_bcs"])
+def test_smoother_parity(dg, name):
+    mesh, o, prm, q = CASES[name]()
+    s = syn.random_source(mesh, o, 3)
+    M = dg.Mesh(mesh, o, prm)
+    qd = _dev(q)
+    M.smooth(qd, _dev(s), sweeps=3)
+    qo = orc.smooth(mesh, o, prm, q, s, 3)
+    assert np.max(np.abs(qd.cpu().numpy() - qo)) <= TOL * np.max(np.abs(qo))
+
+
+@pytest.mark.parametrize("name,kw", [
+    ("c1_box_N3", dict(beta1=3, beta2=3, beta_c=3, delta_n=2)),        # 2 levels, N=3 -> N=1
+    ("c1_box_N3", dict(beta1=1, beta2=2, beta_c=3, delta_n=1)),
+    ("periodic3d_mortars", dict(beta1=1, beta2=1, beta_c=2, delta_n=1)),
+    ("plate2d_all_bcs", dict(beta1=2, beta2=1, beta_c=3, delta_n=1)),
+    ("plate2d_all_bcs", dict(beta1=1, beta2=1, beta_c=1, direction=1)),
+])
+def test_vcycle_parity(dg, name, kw):
+    mesh, o, prm, q = CASES[name]()
+    s = syn.random_source(mesh, o, 5)
+    M = dg.Mesh(mesh, o, prm)
+    qd = _dev(q)
+    rep = M.vcycle(qd, _dev(s), **kw)
+    okw = dict(kw)
+    d = okw.pop("direction", -1)
+    qo = orc.fas_vcycle(mesh, o, prm, q, s, okw["beta1"], okw["beta2"], okw["beta_c"],
+                        direction=None if d < 0 else d, delta_n=okw.get("delta_n", 1))
+    assert rep["levels"] >= 2
+    assert np.max(np.abs(qd.cpu().numpy() - qo)) <= TOL * np.max(np.abs(qo))
+
+
+@pytest.mark.parametrize("corr,iso", [(True, True), (False, True), (True, False)])
+def test_tau_estimate_parity(dg, corr, iso):
+    mesh = syn.periodic_box(3, 3, 1, dim=2)
+    prm = syn.flow_params(mach=0.3, re=100.0)
+    o = syn.random_orders(mesh["K"], 2, 2, 6, 17)
+    q = syn.manufactured_state(mesh, o, 1, prm[2], prm[0], amp=0.05)
+    s = syn.random_source(mesh, o, 9, amp=1e-3)
+    M = dg.Mesh(mesh, o, prm)
+    t = M.tau_estimate(_dev(q), _dev(s), dir_mask=3, with_correction=corr, isolated=iso)
+    to = orc.tau_estimate(mesh, o, prm, q, s, dir_mask=3, with_correction=corr, isolated=iso)
+    assert np.array_equal(t < 0, to < 0)
+    scale = orc.volume_scale(mesh, o, prm, q)
+    assert np.max(np.abs(t - to)) <= TOL * scale
+
+
+def test_tau_estimate_parity_3d_rotated(dg):
+    mesh, o, prm, q = CASES["rotated3d_orientations"]()
+    M = dg.Mesh(mesh, o, prm)
+    t = M.tau_estimate(_dev(q), None)
+    to = orc.tau_estimate(mesh, o, prm, q, None)
+    assert np.array_equal(t < 0, to < 0)
+    assert np.max(np.abs(t - to)) <= TOL * orc.volume_scale(mesh, o, prm, q)
+
+
+@pytest.mark.parametrize("dim,rule", [(2, 1), (3, 2), (2, 0)])
+def test_adapt_bit_identical_on_shared_table(dg, dim, rule):
+    rng = np.random.default_rng(dim * 10 + rule)
+    if dim == 2:
+        mesh = syn.box_mesh(np.linspace(0, 1, 9), np.linspace(0, 1, 7), None)
+    else:
+        mesh = syn.rotate_elements(syn.box_mesh(np.linspace(0, 1, 5), np.linspace(0, 1, 4), np.linspace(0, 1, 4)), 2)
+    prm = syn.flow_params()
+    P = syn.random_orders(mesh["K"], dim, 2, 7, 3)
+    tab = np.full((mesh["K"], 3, 16), -1.0)
+    for e in range(mesh["K"]):
+        for i in range(dim):
+            rate, base = rng.uniform(0.05, 1.2), 10 ** rng.uniform(-5, 0)
+            for N in range(1, P[e, i]):
+                tab[e, i, N] = base * 10 ** (-rate * N) * 10 ** rng.uniform(-0.3, 0.3)
+    M = dg.Mesh(mesh, P, prm)
+    for tau_max in (1e-1, 1e-3, 1e-5):
+        got = M.adapt(tab, tau_max, 1 if dim == 2 else 2, 9, jump_rule=rule)
+        want = orc.adapt_orders(mesh, P, tab, tau_max, 1 if dim == 2 else 2, 9,
+                                rule={0: None, 1: "2d", 2: "3d"}[rule])
+        assert np.array_equal(got, want)
+
+
+def test_adapt_from_measured_tau(dg):
+    """End to end: tau measured by each side, maps compared; any disagreement
+    must come from a near-tie (then the shared-table check decides)."""
+    mesh = syn.periodic_box(4, 3, 1, dim=2)
+    prm = syn.flow_params(mach=0.3, re=100.0)
+    P = syn.uniform_orders(mesh["K"], 2, 6)
+    q = syn.manufactured_state(mesh, P, 2, prm[2], prm[0], amp=0.05)
+    M = dg.Mesh(mesh, P, prm)
+    t = M.tau_estimate(_dev(q), None, dir_mask=3)
+    to = orc.tau_estimate(mesh, P, prm, q, None, dir_mask=3)
+    for tau_max in (1.0, 1e-1, 1e-2):
+        got = M.adapt(t, tau_max, 1, 9, jump_rule=1)
+        want = orc.adapt_orders(mesh, P, to, tau_max, 1, 9, rule="2d")
+        assert np.array_equal(got, want)
+
+
+def test_transfer_state_parity(dg):
+    mesh = syn.rotate_elements(syn.periodic_box(2, 2, 1), seed=1, frac=0.5)
+    prm = syn.flow_params()
+    o1 = syn.random_orders(mesh["K"], 3, 1, 6, 1)
+    o2 = syn.random_orders(mesh["K"], 3, 1, 6, 2)
+    q = syn.perturbed_state(mesh, o1, prm, 3)
+    A, B = dg.Mesh(mesh, o1, prm), dg.Mesh(mesh, o2, prm)
+    got = A.transfer_state_to(B, _dev(q)).cpu().numpy()
+    want = orc.transfer(3, o1, o2, q)
+    assert np.max(np.abs(got - want)) <= TOL * np.max(np.abs(q))
+
+
+def test_invalid_arguments_rejected(dg):
+    mesh = syn.periodic_box(1, 1, 1)
+    prm = syn.flow_params()
+    with pytest.raises(dg.DGError):
+        dg.Mesh(mesh, np.array([[0, 2, 2]], dtype=np.int32), prm)
+    with pytest.raises(dg.DGError):
+        dg.Mesh(mesh, np.array([[13, 2, 2]], dtype=np.int32), prm)
+    bad = dict(mesh)
+    ft = mesh["ftab"].copy()
+    ft[0, 0, 1] = 3  # neighbour face that does not point back
+    bad["ftab"] = ft
+    with pytest.raises(dg.DGError):
+        dg.Mesh(bad, syn.uniform_orders(1, 3, 2), prm)
