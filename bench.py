@@ -1,0 +1,302 @@
+"""Benchmark of the DGSEM p-multigrid hot path on GB300.
+
+Workload: the 2D flat-plate boundary-layer mesh, 60 x 24 elements stretched
+toward the wall (first cell 1e-3, ratio 1.15), uniform order N = 7
+(92,160 Gauss nodes, 460,800 degrees of freedom), Mach 0.2, Re_L 1e5, FP64.
+A step is one pass of the whole path on that state: one FAS V-cycle N = 7
+-> 1 (Algorithm 1; RK3 smoothing 2 pre / 2 post / 4 coarsest sweeps, L2
+transfers, CFL step per sweep), the anisotropic isolated tau estimate in both
+directions (chained restrictions, 6 levels each), and the order adaptation
+(tau_max 1e-4, orders in [1, 7], jump limit 1).  The state is freestream plus
+a seeded 1% perturbation.
+
+metric  DOF-residual evaluations per second: the sum over every operator
+        evaluation issued in a step (smoother stages, FAS sources, restricted
+        residuals, tau residuals) of that level's degrees of freedom (5 x
+        nodes), divided by the step's device time.
+e2e     the same through the C ABI with the state in pinned host memory:
+        host->device copy in, step, device->host copy out, all timed.
+L2      a 512 MB buffer is written between timed steps (the state fits in L2).
+
+--impl reference times the oracle (the plain FP64 CPU implementation) on the
+host cores on the same workload and metric: a step is one full-operator
+residual evaluation of the flat-plate state.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "flat_plate_2d_60x24_N7"
+METRIC = "DOF residual evals/s"
+CYCLE = dict(beta1=2, beta2=2, beta_c=4)
+TAU_MAX = 1e-4
+FP64_PEAK_TFLOPS = 4 * 152 * 2.070e9 / 1e12  # 2 DFMA/clk/SM x 152 SMs at 2070 MHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    return ap.parse_args()
+
+
+def workload():
+    from paper_1806_11456_gb300 import synthetic as syn
+    mesh = syn.flat_plate_mesh()
+    prm = syn.flow_params(mach=0.2, re=1e5)
+    orders = syn.uniform_orders(mesh["K"], 2, 7)
+    q = syn.perturbed_state(mesh, orders, prm, seed=7, amp=0.01)
+    return mesh, prm, orders, q
+
+
+def base_config(mesh, orders):
+    nodes = int(np.sum((orders[:, 0] + 1) * (orders[:, 1] + 1)))
+    return {"workload": WORKLOAD, "elements": int(mesh["K"]), "N": 7, "nodes": nodes, "dof": 5 * nodes,
+            "mach": 0.2, "re": 1e5, "step": "V-cycle 7->1 (b1=2,b2=2,bc=4) + tau (2 dirs) + adapt",
+            "l2": "flushed between steps (512 MB write)"}
+
+
+def tau_dof_evals(orders, dim):
+    """DOFs of the operator evaluations of one tau estimate: the reference
+    residual plus one per directional level below the top."""
+    def nodes(o):
+        n = o[:, :dim] + 1
+        return int(np.sum(np.prod(n, axis=1)))
+    total = nodes(orders)
+    for i in range(dim):
+        for lv in range(int(orders[:, i].max()) - 1, 0, -1):
+            o = orders.copy()
+            o[:, i] = np.minimum(o[:, i], lv)
+            total += nodes(o)
+    return 5.0 * total
+
+
+def volume_flops_per_node(dim, n):
+    """Algorithmic FP64 flops per node of the volume kernel (FMA = 2): BR1
+    gradient contraction 27 n per direction, lifting 54 per direction,
+    gradient face traces 48 per direction, nodal viscous + advective
+    contravariant fluxes 68 per direction, divergence 10 n per direction,
+    primitives, viscosity and scalings 34."""
+    return 34 + 37 * dim * n + 170 * dim
+
+
+class ClockSampler:
+    def __init__(self):
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+        except FileNotFoundError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def stop(self, gpu_index=0):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [r for r in self.samples if len(r) >= 9 and r[0] == str(gpu_index)]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    from oracle import oracle as orc
+    mesh, prm, orders, q = workload()
+    dof = 5.0 * orc.nodes_total(orders, 2)
+    for _ in range(args.warmup):
+        orc.residual(mesh, orders, prm, q)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        orc.residual(mesh, orders, prm, q)
+    dt = time.perf_counter() - t0
+    v = dof * args.steps / dt
+    cfg = base_config(mesh, orders)
+    cfg["step"] = "one full-operator residual evaluation (oracle)"
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "DOF/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": cfg,
+           "cpu_baseline": {"value": v, "unit": "DOF/s", "cores": 1, "kind": "oracle",
+                            "sample": f"{args.steps} oracle residual evaluations of the full workload"},
+           "e2e": {"value": v, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def cpu_baseline_sample(mesh, prm, orders, q, budget_s=15.0):
+    from oracle import oracle as orc
+    dof = 5.0 * orc.nodes_total(orders, 2)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        orc.residual(mesh, orders, prm, q)
+        n += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or n >= 40:
+            break
+    return {"value": dof * n / el, "unit": "DOF/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} oracle residual evaluations of the full workload, single thread"}
+
+
+# ---------------------------------------------------------------------------
+# GB300 arm
+# ---------------------------------------------------------------------------
+def run_gb300(args, rank, world):
+    import torch
+    import __graft_entry__ as g
+    from paper_1806_11456_gb300 import dg
+    g.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    mesh, prm, orders, q_np = workload()
+    M = dg.Mesh(mesh, orders, prm)
+    stream = torch.cuda.current_stream()
+    q0 = torch.tensor(q_np, device=dev)
+    q = q0.clone()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    tau_dofs = tau_dof_evals(orders, 2)
+
+    def step(qd):
+        rep = M.vcycle(qd, None, **CYCLE)
+        tau = M.tau_estimate(qd, None, dir_mask=3)
+        M.adapt(tau, TAU_MAX, 1, 7, jump_rule=1)
+        return rep["dof_evals"] + tau_dofs, rep["residual_evals"]
+
+    for _ in range(args.warmup):
+        q.copy_(q0)
+        step(q)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler()
+    clocks.start()
+    total_ms, total_dofs = 0.0, 0.0
+    launches0 = dg.kernel_launches()
+    for _ in range(args.steps):
+        q.copy_(q0)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        dofs, evals = step(q)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        total_dofs += dofs
+    launches = dg.kernel_launches() - launches0
+    torch.cuda.synchronize()
+    clk = clocks.stop(dev.index)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    value = world * total_dofs / (total_ms * 1e-3)
+
+    # e2e through the C ABI with pinned host buffers
+    qh = torch.tensor(q_np).pin_memory()
+    qout = torch.empty_like(qh).pin_memory()
+    qd = torch.empty_like(q0)
+    e2e_ms, e2e_dofs = 0.0, 0.0
+    tau_bytes = mesh["K"] * 3 * 16 * 8
+    for _ in range(max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        qd.copy_(qh, non_blocking=True)
+        dofs, _ = step(qd)
+        qout.copy_(qd, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+        e2e_dofs += dofs
+    e2e = {"value": world * e2e_dofs / (e2e_ms * 1e-3), "unit": "DOF/s",
+           "h2d_bytes_per_step": int(qh.numel() * 8), "d2h_bytes_per_step": int(qout.numel() * 8 + tau_bytes)}
+
+    # dominant kernel: CUDA events around each launch of one residual
+    prof = M.profile_residual(q0, None, iters=50)
+    stages = {k: v for k, v in prof.items() if k != "isolated"}
+    dom = max(stages, key=stages.get)
+    nodes = int(np.sum((orders[:, 0] + 1) * (orders[:, 1] + 1)))
+    flops = volume_flops_per_node(2, 8) * nodes
+    vol_ms = prof["volume"]
+    achieved = flops / (vol_ms * 1e-3) / 1e12
+    residual_ms = sum(stages.values())
+    roof = {"kernel": "k_volume", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "peak_source": "FP64 nominal derived: 2 DFMA/clk/SM x 152 SMs x 2070 MHz",
+            "flops_per_launch": flops, "ms_per_launch": vol_ms, "dominant_stage": dom,
+            "stage_ms": prof, "residual_dof_per_s": 5.0 * nodes / (residual_ms * 1e-3)}
+
+    if rank == 0:
+        cfg = base_config(mesh, orders)
+        out = {"metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": dict(cfg, parallelism=f"replicas{world}"), "e2e": e2e,
+               "gpu_launches": None, "roofline": roof, "clocks": clk}
+        out["gpu_launches"] = int(launches)  # library kernels launched in the timed steps
+        out["cpu_baseline"] = cpu_baseline_sample(mesh, prm, orders, q_np) if world == 1 else None
+        print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    run_gb300(args, rank, world)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -212,6 +212,22 @@ int dg_adapt(const dg_mesh* mesh, const double* tau_host, const dg_adapt_params*
 int dg_transfer_state(const dg_mesh* from, const double* q_from, const dg_mesh* to, double* q_to,
                       void* stream);
 
+/*
+ * dg_profile_residual -- measurement aid: runs `iters` evaluations of the
+ * full residual r = S - A(q) (as dg_residual) with CUDA events recorded on
+ * `stream` between its launches, and writes the mean duration in ms of each
+ * stage to ms_out[0..5]: face traces, mortar pass 1 (BR1 U*), volume (BR1
+ * gradient + flux divergence), mortar pass 2 (Roe + BR1 flux), surface +
+ * residual, and ms_out[5] the isolated operator (one launch).  r is scratch
+ * output.  Synchronises the stream.
+ */
+int dg_profile_residual(dg_mesh* mesh, const double* q, const double* s, double* r, int iters,
+                        double* ms_out, void* stream);
+
+/* dg_kernel_launches -- cumulative number of CUDA kernels this library has
+ * launched in the process (host-side count; a measurement aid). */
+int dg_kernel_launches(int64_t* count);
+
 const char* dg_last_error(void);
 
 #ifdef __cplusplus

@@ -298,6 +298,15 @@ extern "C" {
 
 const char* dg_last_error(void) { return g_err.c_str(); }
 
+int dg_kernel_launches(int64_t* count) {
+  if (!count) {
+    set_error("dg_kernel_launches: null argument");
+    return DG_EINVAL;
+  }
+  *count = (int64_t)launches();
+  return DG_OK;
+}
+
 int dg_mesh_create(const dg_mesh_desc* desc, const int32_t* orders, dg_mesh** out) {
   if (!out) {
     set_error("null output");
@@ -514,6 +523,15 @@ int dg_adapt(const dg_mesh* m, const double* tau_host, const dg_adapt_params* ap
     limit_jumps(m, o, ap->jump_rule, ap->conform_tag);
   std::memcpy(new_orders, o.data(), o.size() * sizeof(int32_t));
   return DG_OK;
+}
+
+int dg_profile_residual(dg_mesh* m, const double* q, const double* s, double* r, int iters, double* ms_out,
+                        void* stream) {
+  if (!m || !q || !r || !ms_out || iters < 1 || q == r) {
+    set_error("dg_profile_residual: bad argument");
+    return DG_EINVAL;
+  }
+  return profile_residual(m, m->fine.get(), q, s, r, iters, ms_out, S(stream));
 }
 
 int dg_transfer_state(const dg_mesh* from, const double* q_from, const dg_mesh* to, double* q_to, void* stream) {

@@ -121,11 +121,6 @@ struct Level {
   ~Level();
 };
 
-struct TransferPlan {  // element-wise transfer between two levels of one mesh
-  int32_t* d_nf = nullptr;  // unused placeholder
-  ~TransferPlan() {}
-};
-
 }  // namespace dg
 
 struct dg_mesh {
@@ -138,7 +133,6 @@ struct dg_mesh {
   std::map<std::vector<int32_t>, std::unique_ptr<dg::Level>> levels;  // coarse levels by order map
   double* d_scalars = nullptr;   // [0] dt, [1] norm, [2..] scratch
   double* d_tau = nullptr;       // K x 3 x 16 tau table
-  double* d_T = nullptr;         // transfer matrices [n_from][n_to][nt*nf]
 };
 
 namespace dg {
@@ -149,9 +143,12 @@ Params make_params(const double* p);
 
 // kernels (dg_kernels.cu)
 int upload_tables();
+unsigned long long launches();
 int residual(const dg_mesh* m, Level* L, const double* q, const double* s, double* r, bool isolated,
              cudaStream_t st, double* d_norm, int rk_stage, double* rk_g, const double* d_dt);
 int cfl_dt(const dg_mesh* m, Level* L, const double* q, double* d_dt, cudaStream_t st);
+int profile_residual(const dg_mesh* m, Level* L, const double* q, const double* s, double* r, int iters,
+                     double* ms_out, cudaStream_t st);
 int transfer(const dg_mesh* m, const Level* from, const Level* to, int nvar, const double* in, double* out,
              cudaStream_t st, const double* sub = nullptr, bool accumulate = false);
 int fill(double* p, double v, int64_t n, cudaStream_t st);

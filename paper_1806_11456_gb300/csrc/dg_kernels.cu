@@ -25,6 +25,7 @@
 // directly from the contravariant velocity).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -39,6 +40,8 @@ __constant__ double* c_D;     // [kNP][kNP][kNP]
 __constant__ double* c_T;     // [kNP][kNP][kNP*kNP] transfer matrices (n_from, n_to)
 
 static double* g_dev_Dhat = nullptr;
+static unsigned long long g_launches = 0;  // kernels launched by this library (host-side count)
+unsigned long long launches() { return g_launches; }
 static double* g_dev_D = nullptr;
 static double* g_dev_T = nullptr;
 static int g_tables_device = -1;
@@ -1019,16 +1022,19 @@ static int grid_for(int64_t n) {
 }
 
 int fill(double* p, double v, int64_t n, cudaStream_t st) {
+  ++g_launches;
   k_fill<<<grid_for(n), 256, 0, st>>>(p, v, n);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
 }
 int axpby(double* y, double a, const double* x, double b, int64_t n, cudaStream_t st) {
+  ++g_launches;
   k_axpby<<<grid_for(n), 256, 0, st>>>(y, a, x, b, n);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
 }
 int sub3(double* o, const double* a, const double* b, int64_t n, cudaStream_t st) {
+  ++g_launches;
   k_sub3<<<grid_for(n), 256, 0, st>>>(o, a, b, n);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
@@ -1048,14 +1054,19 @@ int residual(const dg_mesh* m, Level* L, const double* q, const double* s, doubl
   LevelArgs A = largs(L);
   if (isolated) {
     TauArgs ta{nullptr, nullptr, nullptr, 0, 0};
+    ++g_launches;
     k_isolated<<<L->n_tiles, kTileNodes, vol_smem(L), st>>>(A, m->prm, q, s, r, ta);
     DG_CUDA_TRY(cudaGetLastError());
     return DG_OK;
   }
   MortarArgs MA = margs(L);
+  ++g_launches;
   k_trace_q<<<L->n_tiles, kTileNodes, 5 * L->tile_smem_nodes * sizeof(double), st>>>(A, q, L->d_trq);
+  ++g_launches;
   k_mortar<1><<<L->n_mtiles, kMortarTile, 0, st>>>(A, MA, m->prm, L->d_trq, nullptr, L->d_ust);
+  ++g_launches;
   k_volume<<<L->n_tiles, kTileNodes, vol_smem(L), st>>>(A, m->prm, q, L->d_ust, L->d_trg, L->d_vol);
+  ++g_launches;
   k_mortar<2><<<L->n_mtiles, kMortarTile, 0, st>>>(A, MA, m->prm, L->d_trq, L->d_trg, L->d_fst);
   RKArgs rk;
   rk.stage = rk_stage;
@@ -1064,14 +1075,65 @@ int residual(const dg_mesh* m, Level* L, const double* q, const double* s, doubl
   rk.g = rk_g;
   rk.dt = d_dt;
   rk.qupd = const_cast<double*>(q);
+  ++g_launches;
   k_surface<<<L->n_tiles, kTileNodes, 0, st>>>(A, L->d_vol, L->d_fst, s, r, d_norm, rk);
   DG_CUDA_TRY(cudaGetLastError());
+  return DG_OK;
+}
+
+int profile_residual(const dg_mesh* m, Level* L, const double* q, const double* s, double* r, int iters,
+                     double* ms_out, cudaStream_t st) {
+  int rc = configure_smem();
+  if (rc != DG_OK) return rc;
+  LevelArgs A = largs(L);
+  MortarArgs MA = margs(L);
+  cudaEvent_t ev[7];
+  for (int k = 0; k < 7; ++k) DG_CUDA_TRY(cudaEventCreate(&ev[k]));
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  RKArgs rk;
+  rk.stage = -1;
+  rk.a = rk.b = 0.0;
+  rk.g = nullptr;
+  rk.dt = nullptr;
+  rk.qupd = nullptr;
+  TauArgs ta{nullptr, nullptr, nullptr, 0, 0};
+  for (int it = 0; it < iters; ++it) {
+    cudaEventRecord(ev[0], st);
+    ++g_launches;
+    k_trace_q<<<L->n_tiles, kTileNodes, 5 * L->tile_smem_nodes * sizeof(double), st>>>(A, q, L->d_trq);
+    cudaEventRecord(ev[1], st);
+    ++g_launches;
+    k_mortar<1><<<L->n_mtiles, kMortarTile, 0, st>>>(A, MA, m->prm, L->d_trq, nullptr, L->d_ust);
+    cudaEventRecord(ev[2], st);
+    ++g_launches;
+    k_volume<<<L->n_tiles, kTileNodes, vol_smem(L), st>>>(A, m->prm, q, L->d_ust, L->d_trg, L->d_vol);
+    cudaEventRecord(ev[3], st);
+    ++g_launches;
+    k_mortar<2><<<L->n_mtiles, kMortarTile, 0, st>>>(A, MA, m->prm, L->d_trq, L->d_trg, L->d_fst);
+    cudaEventRecord(ev[4], st);
+    ++g_launches;
+    k_surface<<<L->n_tiles, kTileNodes, 0, st>>>(A, L->d_vol, L->d_fst, s, r, nullptr, rk);
+    cudaEventRecord(ev[5], st);
+    ++g_launches;
+    k_isolated<<<L->n_tiles, kTileNodes, vol_smem(L), st>>>(A, m->prm, q, s, r, ta);
+    cudaEventRecord(ev[6], st);
+    DG_CUDA_TRY(cudaEventSynchronize(ev[6]));
+    for (int k = 0; k < 6; ++k) {
+      float ms = 0.f;
+      DG_CUDA_TRY(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+      acc[k] += ms;
+    }
+  }
+  DG_CUDA_TRY(cudaGetLastError());
+  for (int k = 0; k < 7; ++k) cudaEventDestroy(ev[k]);
+  for (int k = 0; k < 6; ++k) ms_out[k] = acc[k] / std::max(1, iters);
   return DG_OK;
 }
 
 int cfl_dt(const dg_mesh* m, Level* L, const double* q, double* d_dt, cudaStream_t st) {
   int rc = reset_min(d_dt, st);
   if (rc != DG_OK) return rc;
+  ++g_launches;
   k_cfl<<<L->n_tiles, kTileNodes, 0, st>>>(largs(L), m->prm, q, d_dt);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
@@ -1080,6 +1142,7 @@ int cfl_dt(const dg_mesh* m, Level* L, const double* q, double* d_dt, cudaStream
 int transfer(const dg_mesh* m, const Level* from, const Level* to, int nvar, const double* in, double* out,
              cudaStream_t st, const double* sub, bool accumulate) {
   (void)m;
+  ++g_launches;
   k_transfer<<<from->K, 128, 0, st>>>(from->dim, from->d_n, from->d_off, to->d_n, to->d_off, nvar, in, sub, out,
                                       accumulate ? 1 : 0);
   DG_CUDA_TRY(cudaGetLastError());
@@ -1100,6 +1163,7 @@ int tau_accumulate(const dg_mesh* m, Level* L, const double* q, const double* s,
     return tau_reduce(L, L->d_R, rho, dir, slot, fine_orders_dev, d_tau, st);
   }
   TauArgs ta{rho, d_tau, fine_orders_dev, dir, slot};
+  ++g_launches;
   k_isolated<<<L->n_tiles, kTileNodes, vol_smem(L), st>>>(largs(L), m->prm, q, s, nullptr, ta);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
@@ -1125,6 +1189,7 @@ __global__ void k_tau_reduce(LevelArgs A, const double* __restrict__ r, const do
 
 static int tau_reduce(const Level* L, const double* r, const double* rho, int dir, int slot,
                       const int32_t* fine_orders, double* table, cudaStream_t st) {
+  ++g_launches;
   k_tau_reduce<<<L->n_tiles, kTileNodes, 0, st>>>(largs(L), r, rho, dir, slot, fine_orders, table);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;

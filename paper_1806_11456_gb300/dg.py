@@ -54,7 +54,9 @@ _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int32)
 
 EXPORTS = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_layout", "dg_residual", "dg_cfl_dt", "dg_smooth",
-           "dg_pmg_vcycle", "dg_tau_estimate", "dg_adapt", "dg_transfer_state", "dg_last_error"]
+           "dg_pmg_vcycle", "dg_tau_estimate", "dg_adapt", "dg_transfer_state", "dg_profile_residual",
+           "dg_kernel_launches", "dg_last_error"]
+KERNEL_STAGES = ["trace_q", "mortar_u_star", "volume", "mortar_flux", "surface", "isolated"]
 
 
 def lib(path=LIB_PATH):
@@ -76,6 +78,8 @@ def lib(path=LIB_PATH):
     L.dg_tau_estimate.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _vp]
     L.dg_adapt.argtypes = [_vp, _dp, ctypes.POINTER(AdaptParams), _ip]
     L.dg_transfer_state.argtypes = [_vp, _vp, _vp, _vp, _vp]
+    L.dg_profile_residual.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, _dp, _vp]
+    L.dg_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_int64)]
     _lib = L
     return L
 
@@ -98,6 +102,13 @@ def _stream(stream):
     import torch
     s = torch.cuda.current_stream() if stream is None else stream
     return ctypes.c_void_p(s.cuda_stream)
+
+
+def kernel_launches():
+    """Cumulative count of kernels the library has launched in this process."""
+    c = ctypes.c_int64()
+    _check(lib().dg_kernel_launches(ctypes.byref(c)))
+    return int(c.value)
 
 
 class Mesh:
@@ -189,6 +200,15 @@ class Mesh:
         out = np.zeros((self.K, 3), dtype=np.int32)
         _check(lib().dg_adapt(self.h, tau.ctypes.data_as(_dp), ctypes.byref(ap), out.ctypes.data_as(_ip)))
         return out
+
+    def profile_residual(self, q, s=None, iters=20, stream=None):
+        """Mean ms per residual stage (CUDA events on the launching stream)."""
+        import torch
+        r = torch.empty_like(q)
+        ms = np.zeros(6)
+        _check(lib().dg_profile_residual(self.h, _ptr(q), _ptr(s), _ptr(r), int(iters), ms.ctypes.data_as(_dp),
+                                         _stream(stream)))
+        return dict(zip(KERNEL_STAGES, ms.tolist()))
 
     def transfer_state_to(self, other, q_from, q_to=None, stream=None):
         import torch
