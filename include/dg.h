@@ -213,6 +213,34 @@ int dg_transfer_state(const dg_mesh* from, const double* q_from, const dg_mesh* 
                       void* stream);
 
 /*
+ * dg_transfer_noalloc -- the order-map transfer of dg_transfer_state for
+ * callers that cannot allocate device memory at the time of the call (a host
+ * code that hands all device memory to its own pool at start-up, or a caller
+ * recording a CUDA graph): it takes no mesh handle and allocates nothing.
+ * The paper has no counterpart to this entry point; it is a service of this
+ * library.
+ *  dim          2 or 3.
+ *  K            element count, 1 <= K <= 65,536 (larger K: DG_EINVAL with a
+ *               message naming the limit).
+ *  orders_from, orders_to  K x 3 int32 HOST arrays of the two order maps
+ *               (N3 = 0 in 2D); read before the call returns.
+ *  nvar         variables per node (5 for a state).
+ *  in, out      caller-owned DEVICE arrays in the element-blocked layout of
+ *               the two order maps (nvar values per node, variable-major per
+ *               element); out may not alias in.
+ * Per element and direction it applies the L2 projection (order drops), the
+ * interpolation (order rises) or the identity, exactly as dg_transfer_state.
+ * Its per-element records live in one statically reserved device array of
+ * 2 MiB that every GPU loading the library holds until the process exits.
+ * The first call on a device resolves that array's address and writes the
+ * Gauss tables to constant memory (synchronous set-up); make that first call
+ * before any stream capture.  Calls share the array: calls whose work
+ * overlaps on the GPU race, so serialise them (one stream, or events).
+ */
+int dg_transfer_noalloc(int32_t dim, int32_t K, const int32_t* orders_from, const int32_t* orders_to,
+                        int32_t nvar, const double* in, double* out, void* stream);
+
+/*
  * dg_profile_residual -- measurement aid: runs `iters` evaluations of the
  * full residual r = S - A(q) (as dg_residual) with CUDA events recorded on
  * `stream` between its launches, and writes the mean duration in ms of each

@@ -534,6 +534,11 @@ int dg_profile_residual(dg_mesh* m, const double* q, const double* s, double* r,
   return profile_residual(m, m->fine.get(), q, s, r, iters, ms_out, S(stream));
 }
 
+int dg_transfer_noalloc(int32_t dim, int32_t K, const int32_t* orders_from, const int32_t* orders_to,
+                        int32_t nvar, const double* in, double* out, void* stream) {
+  return transfer_noalloc(dim, K, orders_from, orders_to, nvar, in, out, S(stream));
+}
+
 int dg_transfer_state(const dg_mesh* from, const double* q_from, const dg_mesh* to, double* q_to, void* stream) {
   if (!from || !to || !q_from || !q_to || from->K != to->K || from->dim != to->dim) {
     set_error("dg_transfer_state: meshes do not match");

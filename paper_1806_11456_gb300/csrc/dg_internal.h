@@ -158,6 +158,8 @@ int tau_accumulate(const dg_mesh* m, Level* L, const double* q, const double* s,
                    bool isolated, int dir, int order_slot, const int32_t* fine_orders_dev, double* d_tau,
                    cudaStream_t st);
 int read_scalar(const double* d, double* h, cudaStream_t st);
+int transfer_noalloc(int dim, int K, const int32_t* orders_from, const int32_t* orders_to, int nvar,
+                     const double* in, double* out, cudaStream_t st);
 int reset_max(double* d, cudaStream_t st);
 int reset_min(double* d, cudaStream_t st);
 }  // namespace dg

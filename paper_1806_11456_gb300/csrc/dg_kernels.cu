@@ -27,7 +27,10 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <climits>
 #include <cstring>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "dg_internal.h"
@@ -1191,6 +1194,161 @@ static int tau_reduce(const Level* L, const double* r, const double* rho, int di
                       const int32_t* fine_orders, double* table, cudaStream_t st) {
   ++g_launches;
   k_tau_reduce<<<L->n_tiles, kTileNodes, 0, st>>>(largs(L), r, rho, dir, slot, fine_orders, table);
+  DG_CUDA_TRY(cudaGetLastError());
+  return DG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free order-map transfer (dg_transfer_noalloc in dg.h)
+//
+// Some callers cannot allocate device memory when they need a transfer: a
+// host code that reserves all device memory up front in its own pool, or a
+// caller that is recording a CUDA graph.  This variant of k_transfer needs no
+// mesh handle and no library-allocated buffer: its only scratch -- one
+// 8-int record per element (both node-count triples and both node offsets) --
+// lives in the static device array below, and its 1-D projection /
+// interpolation matrices are formed in shared memory from the Gauss nodes in
+// constant memory.  The array is reserved on every GPU that loads the library
+// and stays reserved until the process exits.  Every call shares it, so
+// calls whose kernels overlap on the GPU race; each call rewrites the records
+// of all the elements it uses, so nothing has to start at zero.
+// ---------------------------------------------------------------------------
+constexpr int kNoAllocMaxElems = 65536;  // 65,536 elements -> 2 MiB of records
+constexpr int kNoAllocRec = 8;
+static __device__ __align__(256) int32_t g_noalloc_records[kNoAllocMaxElems * kNoAllocRec];
+
+namespace {
+constexpr int kMaxDevices = 64;
+int32_t* g_noalloc_dev_ptr[kMaxDevices] = {nullptr};
+bool g_noalloc_ready[kMaxDevices] = {false};
+std::mutex g_noalloc_mutex;
+}  // namespace
+
+// l_j(x) on the n Gauss nodes of c_tab, from the product formula
+DEV double noalloc_lagrange(int n, int j, double x) {
+  double v = 1.0;
+  for (int i = 0; i < n; ++i)
+    if (i != j) v *= (x - c_tab.x[n][i]) / (c_tab.x[n][j] - c_tab.x[n][i]);
+  return v;
+}
+
+__global__ void k_transfer_noalloc(int nvar, const int32_t* __restrict__ rec_all, const double* __restrict__ in,
+                                   double* __restrict__ out) {
+  __shared__ double sT[3][kNP * kNP];
+  const int e = blockIdx.x;
+  const int32_t* rec = rec_all + (size_t)e * kNoAllocRec;
+  const int nf[3] = {rec[0], rec[1], rec[2]};
+  const int nt[3] = {rec[3], rec[4], rec[5]};
+  // 1-D matrices: L2 projection when the order drops, interpolation when it
+  // rises, identity when equal
+  for (int d = 0; d < 3; ++d)
+    for (int k = threadIdx.x; k < nt[d] * nf[d]; k += blockDim.x) {
+      int j = k / nf[d], i = k - j * nf[d];
+      double v;
+      if (nt[d] < nf[d])
+        v = c_tab.w[nf[d]][i] * noalloc_lagrange(nt[d], j, c_tab.x[nf[d]][i]) / c_tab.w[nt[d]][j];
+      else if (nt[d] > nf[d])
+        v = noalloc_lagrange(nf[d], i, c_tab.x[nt[d]][j]);
+      else
+        v = (i == j) ? 1.0 : 0.0;
+      sT[d][k] = v;
+    }
+  __syncthreads();
+  const int nnf = nf[0] * nf[1] * nf[2], nnt = nt[0] * nt[1] * nt[2];
+  const double* ie = in + (size_t)nvar * rec[6];
+  double* oe = out + (size_t)nvar * rec[7];
+  for (int i = threadIdx.x; i < nnt * nvar; i += blockDim.x) {
+    int v = i / nnt, j = i - v * nnt;
+    int j0 = j % nt[0], j1 = (j / nt[0]) % nt[1], j2 = j / (nt[0] * nt[1]);
+    double acc = 0.0;
+    for (int k2 = 0; k2 < nf[2]; ++k2)
+      for (int k1 = 0; k1 < nf[1]; ++k1) {
+        double w21 = sT[2][j2 * nf[2] + k2] * sT[1][j1 * nf[1] + k1];
+        for (int k0 = 0; k0 < nf[0]; ++k0)
+          acc += w21 * sT[0][j0 * nf[0] + k0] * ie[v * nnf + (k2 * nf[1] + k1) * nf[0] + k0];
+      }
+    oe[v * nnt + j] = acc;
+  }
+}
+
+// Once per device, with that device current: resolve the static array's
+// device address and make sure the Gauss tables are in constant memory
+// (cudaMemcpyToSymbol writes them; it allocates nothing).
+static int noalloc_setup(int32_t** ptr) {
+  int dev = 0;
+  DG_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("dg_transfer_noalloc: device index out of range");
+    return DG_EINVAL;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ready[dev]) {
+    int32_t* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress((void**)&p, g_noalloc_records);
+    if (e != cudaSuccess || p == nullptr) {
+      set_error(std::string("dg_transfer_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+      return DG_ECUDA;
+    }
+    const Tables1D& T = tables();
+    DevTables h;
+    memset(&h, 0, sizeof(h));
+    for (int n = 1; n < kNP; ++n)
+      for (int j = 0; j < n; ++j) {
+        h.x[n][j] = T.x[n][j];
+        h.w[n][j] = T.w[n][j];
+        h.lm[n][j] = T.lm[n][j];
+        h.lp[n][j] = T.lp[n][j];
+        h.lmw[n][j] = T.lm[n][j] / T.w[n][j];
+        h.lpw[n][j] = T.lp[n][j] / T.w[n][j];
+      }
+    DG_CUDA_TRY(cudaMemcpyToSymbol(c_tab, &h, sizeof(h)));
+    g_noalloc_dev_ptr[dev] = p;
+    g_noalloc_ready[dev] = true;
+  }
+  *ptr = g_noalloc_dev_ptr[dev];
+  return DG_OK;
+}
+
+int transfer_noalloc(int dim, int K, const int32_t* orders_from, const int32_t* orders_to, int nvar,
+                     const double* in, double* out, cudaStream_t st) {
+  if ((dim != 2 && dim != 3) || K < 1 || nvar < 1 || !orders_from || !orders_to || !in || !out) {
+    set_error("dg_transfer_noalloc: bad argument");
+    return DG_EINVAL;
+  }
+  if (K > kNoAllocMaxElems) {
+    set_error("dg_transfer_noalloc: " + std::to_string(K) + " elements exceed the static limit of " +
+              std::to_string(kNoAllocMaxElems));
+    return DG_EINVAL;
+  }
+  std::vector<int32_t> rec((size_t)K * kNoAllocRec);
+  int64_t of = 0, ot = 0;
+  for (int e = 0; e < K; ++e) {
+    int32_t* r = &rec[(size_t)e * kNoAllocRec];
+    for (int d = 0; d < 3; ++d) {
+      int a = orders_from[e * 3 + d], b = orders_to[e * 3 + d];
+      bool active = d < dim;
+      if ((active && (a < 1 || a > kNMax || b < 1 || b > kNMax)) || (!active && (a != 0 || b != 0))) {
+        set_error("dg_transfer_noalloc: order out of range at element " + std::to_string(e));
+        return DG_EINVAL;
+      }
+      r[d] = active ? a + 1 : 1;
+      r[3 + d] = active ? b + 1 : 1;
+    }
+    if (of + (int64_t)r[0] * r[1] * r[2] > INT32_MAX || ot + (int64_t)r[3] * r[4] * r[5] > INT32_MAX) {
+      set_error("dg_transfer_noalloc: node offsets exceed 32 bits");
+      return DG_EINVAL;
+    }
+    r[6] = (int32_t)of;
+    r[7] = (int32_t)ot;
+    of += (int64_t)r[0] * r[1] * r[2];
+    ot += (int64_t)r[3] * r[4] * r[5];
+  }
+  int32_t* dev_rec = nullptr;
+  int rc = noalloc_setup(&dev_rec);
+  if (rc != DG_OK) return rc;
+  DG_CUDA_TRY(cudaMemcpyAsync(dev_rec, rec.data(), rec.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  ++g_launches;
+  k_transfer_noalloc<<<K, 128, 0, st>>>(nvar, dev_rec, in, out);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
 }

@@ -55,7 +55,7 @@ _ip = ctypes.POINTER(ctypes.c_int32)
 
 EXPORTS = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_layout", "dg_residual", "dg_cfl_dt", "dg_smooth",
            "dg_pmg_vcycle", "dg_tau_estimate", "dg_adapt", "dg_transfer_state", "dg_profile_residual",
-           "dg_kernel_launches", "dg_last_error"]
+           "dg_kernel_launches", "dg_transfer_noalloc", "dg_last_error"]
 KERNEL_STAGES = ["trace_q", "mortar_u_star", "volume", "mortar_flux", "surface", "isolated"]
 
 
@@ -80,6 +80,7 @@ def lib(path=LIB_PATH):
     L.dg_transfer_state.argtypes = [_vp, _vp, _vp, _vp, _vp]
     L.dg_profile_residual.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, _dp, _vp]
     L.dg_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_int64)]
+    L.dg_transfer_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, _ip, _ip, ctypes.c_int32, _vp, _vp, _vp]
     _lib = L
     return L
 
