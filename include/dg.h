@@ -104,6 +104,9 @@ int dg_mesh_destroy(dg_mesh* mesh);
  */
 int dg_mesh_layout(const dg_mesh* mesh, int64_t* total_nodes, int64_t* elem_offsets);
 
+/* dg_mesh_orders -- copy the mesh's K x 3 order map to orders_out (host). */
+int dg_mesh_orders(const dg_mesh* mesh, int32_t* orders_out);
+
 /*
  * dg_residual -- r = S - A(Q), A = M^{-1} F(Q) (Sec. 3.1, nonlinRes; F the
  * DGSEM operator of Sec. 2, DiscretNSElem, with Roe and BR1 fluxes and
@@ -139,7 +142,9 @@ typedef struct {
   int32_t direction;  /* -1: isotropic coarsening; 0/1/2: coarsen that reference direction only */
   int32_t coarsest;   /* lowest level order (1 = N_coarse = 1) */
   int32_t delta_n;    /* order drop between consecutive levels (Sec. 3.1 uses 1); <= 0 means 1 */
-  int32_t reserved[2];
+  int32_t graph;      /* 1: capture the cycle's launches as a CUDA graph on the first call with these
+                         arrays and parameters, replay it on later calls (same result) */
+  int32_t reserved;
 } dg_mg_params;
 
 /* What a cycle reports. */
@@ -202,6 +207,52 @@ typedef struct {
  */
 int dg_adapt(const dg_mesh* mesh, const double* tau_host, const dg_adapt_params* ap,
              int32_t* new_orders);
+
+/* Steady-solve parameters (Sec. 3.1.1 cycling, Sec. 3.3.2 adaptation). */
+typedef struct {
+  double tol;              /* stop when max |S - A(Q)| < tol */
+  int32_t max_cycles;      /* V-cycle cap per phase (FMG level, reference solve, final solve) */
+  int32_t fmg;             /* 1: full-multigrid start from order 1, raising one order at a time */
+  double fmg_tol;          /* residual to reach on a FMG level before raising the order (paper: 1e-1) */
+  dg_mg_params mg;         /* cycle used in every phase */
+  int32_t adapt;           /* 1: converge to tau_max/10, estimate tau, adapt once, then converge to tol */
+  int32_t reserved0;
+  dg_adapt_params ap;      /* adaptation parameters (jump rule etc.) */
+} dg_solve_params;
+
+typedef struct {
+  int32_t cycles;          /* V-cycles in all phases */
+  int32_t fmg_cycles;      /* of which on FMG levels below the reference orders */
+  int32_t adapted;         /* 1 if the order map changed */
+  int32_t status;          /* DG_OK, DG_ENOTCONVERGED or DG_EDIVERGED */
+  double rnorm;            /* final max |r| */
+  double rnorm_adapt;      /* max |r| when the tau estimate was taken */
+  double dof_evals;        /* sum over operator evaluations of the level's degrees of freedom */
+  int64_t nodes;           /* nodes of the final mesh */
+} dg_solve_report;
+
+/* Allocator for the state array of an adapted mesh: returns a device pointer
+ * of at least `bytes` bytes that the caller owns, or NULL. */
+typedef void* (*dg_alloc_fn)(size_t bytes, void* ctx);
+
+/*
+ * dg_solve_steady -- steady solve A(Q) = S (Sec. 3.1) with the FAS cycle:
+ * optional full-multigrid start (orders 1, 2, ... each cycled until max |r| <
+ * fmg_tol, then interpolated up; Sec. 3.1.1), V-cycles at the mesh's orders
+ * until max |r| < tol -- or, with adapt = 1, until max |r| < tau_max/10
+ * (Sec. 3.3.2 step 1), then the isolated anisotropic tau estimate, the order
+ * selection and jump rules, a new mesh and the state transferred to it, and
+ * V-cycles until max |r| < tol.
+ *  mesh, q   in/out: on adaptation *mesh is replaced by a new handle (the old
+ *            one is destroyed) and *q by an array obtained from `alloc` (the
+ *            old array stays the caller's).  s must be NULL when adapt = 1.
+ *  alloc     required when adapt = 1.
+ * Returns DG_OK when converged, DG_ENOTCONVERGED when a cycle cap was hit,
+ * DG_EDIVERGED when the residual became NaN/inf; rep is filled in every case.
+ * Synchronises the stream at every residual check.
+ */
+int dg_solve_steady(dg_mesh** mesh, double** q, const double* s, const dg_solve_params* sp, dg_alloc_fn alloc,
+                    void* alloc_ctx, dg_solve_report* rep, void* stream);
 
 /*
  * dg_transfer_state -- move a state between two meshes of the same geometry

@@ -453,3 +453,76 @@ def adapt_orders(mesh, P, ttab, tau_max, n_min, n_max, cap=None, rule="2d", conf
     if rule is None and conform_tag is None:
         return new
     return limit_jumps(mesh, new, rule, conform_tag)
+
+
+# ---------------------------------------------------------------------------
+# steady driver (Sec. 3.1.1 FMG and V-cycling, Sec. 3.3.2 adaptation)
+# ---------------------------------------------------------------------------
+def _max_norm(mesh, orders, prm, q, s):
+    return float(np.max(np.abs(residual(mesh, orders, prm, q, s))))
+
+
+def _cycle_until(mesh, orders, prm, q, s, mg, target, cap):
+    """V-cycles until max|r| < target or `cap` cycles.  Returns (q, cycles,
+    final norm, status) with status 'ok', 'cap' or 'diverged'."""
+    rn = _max_norm(mesh, orders, prm, q, s)
+    c = 0
+    while True:
+        if rn < target:
+            return q, c, rn, "ok"
+        if not math.isfinite(rn):
+            return q, c, rn, "diverged"
+        if c >= cap:
+            return q, c, rn, "cap"
+        q = fas_vcycle(mesh, orders, prm, q, s, mg["beta1"], mg["beta2"], mg["beta_c"],
+                       direction=None if mg.get("direction", -1) < 0 else mg["direction"],
+                       coarsest=mg.get("coarsest", 1), delta_n=mg.get("delta_n", 1))
+        c += 1
+        rn = _max_norm(mesh, orders, prm, q, s)
+
+
+def solve_steady(mesh, orders, prm, q, s, tol, max_cycles, mg, fmg=False, fmg_tol=1e-1, adapt=None):
+    """FMG start from order 1 (each level cycled to fmg_tol, then interpolated
+    up), V-cycles at the reference orders to tol -- or, with `adapt` (dict of
+    select/jump parameters), to tau_max/10, then the isolated tau estimate,
+    the new order map, the state transferred, and V-cycles to tol.
+    Returns (orders, q, report)."""
+    dim = mesh["dim"]
+    rep = dict(cycles=0, fmg_cycles=0, adapted=False)
+    status = "ok"
+    if fmg:
+        top = int(orders[:, :dim].max())
+        prev_o, prev_q = None, None
+        for lv in range(1, top):
+            o = level_orders(orders, lv, dim)
+            ql = transfer(dim, orders, o, q) if prev_o is None else transfer(dim, prev_o, o, prev_q)
+            sl = transfer(dim, orders, o, s) if s is not None else None
+            ql, c, rn, st = _cycle_until(mesh, o, prm, ql, sl, mg, fmg_tol, max_cycles)
+            rep["cycles"] += c
+            rep["fmg_cycles"] += c
+            if st == "diverged":
+                status = st
+                break
+            prev_o, prev_q = o, ql
+        if status == "ok" and prev_o is not None:
+            q = transfer(dim, prev_o, orders, prev_q)
+    rn = float("nan")
+    if status == "ok":
+        target = adapt["tau_max"] / 10.0 if adapt else tol
+        q, c, rn, status = _cycle_until(mesh, orders, prm, q, s, mg, target, max_cycles)
+        rep["cycles"] += c
+    if status == "ok" and adapt:
+        rep["rnorm_adapt"] = rn
+        t = tau_estimate(mesh, orders, prm, q, None, dir_mask=(1 << dim) - 1)
+        rule = {0: None, 1: "2d", 2: "3d"}[adapt.get("jump_rule", 0)]
+        new = adapt_orders(mesh, orders, t, adapt["tau_max"], adapt["n_min"], adapt["n_max"],
+                           cap=adapt.get("cap") or None, rule=rule)
+        if not np.array_equal(new, orders):
+            q = transfer(dim, orders, new, q)
+            orders = new
+            rep["adapted"] = True
+        q, c, rn, status = _cycle_until(mesh, orders, prm, q, None, mg, tol, max_cycles)
+        rep["cycles"] += c
+    rep["rnorm"] = rn
+    rep["status"] = status
+    return orders, q, rep

@@ -132,6 +132,90 @@ static std::vector<int32_t> capped(const std::vector<int32_t>& o, int dim, int l
   return r;
 }
 
+static int level_norm(dg_mesh* m, Level* L, const double* Q, const double* Sv, cudaStream_t st, double* out) {
+  DG_TRY(ensure_work(L));
+  DG_TRY(reset_max(m->d_scalars + 1, st));
+  DG_TRY(residual(m, L, Q, Sv, L->d_R, false, st, m->d_scalars + 1, -1, nullptr, nullptr));
+  return read_scalar(m->d_scalars + 1, out, st);
+}
+
+static std::vector<int32_t> capped(const std::vector<int32_t>& o, int dim, int level, int direction);
+
+// The levels of a cycle whose finest level has orders `top_orders`.
+static int cycle_levels(dg_mesh* m, const std::vector<int32_t>& top_orders, const dg_mg_params& mg,
+                        std::vector<Level*>* lv) {
+  int top = 0;
+  for (int e = 0; e < m->K; ++e)
+    for (int d = 0; d < m->dim; ++d)
+      if (mg.direction < 0 || mg.direction == d) top = std::max(top, (int)top_orders[e * 3 + d]);
+  const int coarsest = std::min((int)mg.coarsest, top);
+  const int dN = mg.delta_n > 0 ? mg.delta_n : 1;
+  lv->clear();
+  for (int l = top; l >= coarsest; l -= dN) {
+    Level* L = get_level(m, capped(top_orders, m->dim, l, mg.direction));
+    if (!L) return DG_ECUDA;
+    DG_TRY(ensure_work(L));
+    lv->push_back(L);
+  }
+  return DG_OK;
+}
+
+// One V-cycle on (Q, Sv) whose finest level has orders `top_orders`.  With
+// mg.graph the launch sequence is captured once per (orders, Q, Sv,
+// parameters) on a library stream and replayed on `st` afterwards.
+static int run_vcycle(dg_mesh* m, const std::vector<int32_t>& top_orders, double* Q, const double* Sv,
+                      const dg_mg_params& mg, cudaStream_t st, int* evals, double* dofs, int* nlev) {
+  Cycle C{m, st, mg, {}, 0, 0.0};
+  DG_TRY(cycle_levels(m, top_orders, mg, &C.lv));
+  *nlev = (int)C.lv.size();
+  if (!mg.graph) {
+    DG_TRY(vcycle_level(C, 0, Q, Sv));
+    *evals = C.evals;
+    *dofs = C.dofs;
+    return DG_OK;
+  }
+  std::string key((const char*)top_orders.data(), top_orders.size() * sizeof(int32_t));
+  const void* ptrs[2] = {Q, Sv};
+  key.append((const char*)ptrs, sizeof(ptrs));
+  key.append((const char*)&mg, sizeof(mg));
+  auto it = m->graphs.find(key);
+  if (it == m->graphs.end()) {
+    DG_TRY(prepare_capture());
+    if (!m->cap_stream) DG_CUDA_TRY(cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking));
+    Cycle G{m, m->cap_stream, mg, C.lv, 0, 0.0};
+    unsigned long long l0 = launches();
+    DG_CUDA_TRY(cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = vcycle_level(G, 0, Q, Sv);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(m->cap_stream, &graph);
+    if (rc != DG_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) {
+      set_error(std::string("V-cycle capture: ") + cudaGetErrorString(e));
+      return DG_ECUDA;
+    }
+    dg_mesh::Graph gr;
+    e = cudaGraphInstantiate(&gr.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      set_error(std::string("V-cycle graph instantiate: ") + cudaGetErrorString(e));
+      return DG_ECUDA;
+    }
+    gr.evals = G.evals;
+    gr.dofs = G.dofs;
+    gr.launches = launches() - l0;
+    add_launches(0ULL - gr.launches);  // captured, not launched
+    it = m->graphs.emplace(key, gr).first;
+  }
+  DG_CUDA_TRY(cudaGraphLaunch(it->second.exec, st));
+  add_launches(it->second.launches);
+  *evals = it->second.evals;
+  *dofs = it->second.dofs;
+  return DG_OK;
+}
+
 // ---------------------------------------------------------------------------
 // adaptation (host, deterministic)
 // ---------------------------------------------------------------------------
@@ -324,13 +408,17 @@ int dg_mesh_create(const dg_mesh_desc* desc, const int32_t* orders, dg_mesh** ou
   m->xmap.assign(desc->xmap, desc->xmap + (size_t)desc->K * npe * 3);
   m->ftab.assign(desc->ftab, desc->ftab + (size_t)desc->K * 24);
   m->prm = make_params(desc->params);
+  std::memcpy(m->raw_params, desc->params, sizeof(m->raw_params));
   m->orders.assign(orders, orders + (size_t)desc->K * 3);
   m->fine.reset(new Level());
   int rc = build_level(m, m->orders, m->fine.get());
   if (rc == DG_OK) {
     cudaError_t e1 = cudaMalloc(&m->d_scalars, 16 * sizeof(double));
     cudaError_t e2 = cudaMalloc(&m->d_tau, (size_t)m->K * 3 * kTauSlots * sizeof(double));
-    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+    cudaError_t e3 = cudaMalloc(&m->d_orders, m->orders.size() * sizeof(int32_t));
+    if (e3 == cudaSuccess)
+      e3 = cudaMemcpy(m->d_orders, m->orders.data(), m->orders.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
       set_error("cudaMalloc failed for mesh scalars");
       rc = DG_ECUDA;
     }
@@ -345,8 +433,11 @@ int dg_mesh_create(const dg_mesh_desc* desc, const int32_t* orders, dg_mesh** ou
 
 int dg_mesh_destroy(dg_mesh* m) {
   if (!m) return DG_OK;
+  for (auto& kv : m->graphs) cudaGraphExecDestroy(kv.second.exec);
+  if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
   if (m->d_scalars) cudaFree(m->d_scalars);
   if (m->d_tau) cudaFree(m->d_tau);
+  if (m->d_orders) cudaFree(m->d_orders);
   delete m;
   return DG_OK;
 }
@@ -359,6 +450,15 @@ int dg_mesh_layout(const dg_mesh* m, int64_t* total_nodes, int64_t* elem_offsets
   if (total_nodes) *total_nodes = m->fine->nodes;
   if (elem_offsets)
     for (int e = 0; e <= m->K; ++e) elem_offsets[e] = m->fine->off[e];
+  return DG_OK;
+}
+
+int dg_mesh_orders(const dg_mesh* m, int32_t* out) {
+  if (!m || !out) {
+    set_error("dg_mesh_orders: null argument");
+    return DG_EINVAL;
+  }
+  std::memcpy(out, m->orders.data(), m->orders.size() * sizeof(int32_t));
   return DG_OK;
 }
 
@@ -417,31 +517,17 @@ int dg_pmg_vcycle(dg_mesh* m, double* q, const double* s, const dg_mg_params* mg
     set_error("dg_pmg_vcycle: bad argument");
     return DG_EINVAL;
   }
-  Cycle C{m, S(stream), *mg, {}, 0, 0.0};
-  int top = 0;
-  for (int e = 0; e < m->K; ++e)
-    for (int d = 0; d < m->dim; ++d)
-      if (mg->direction < 0 || mg->direction == d) top = std::max(top, (int)m->orders[e * 3 + d]);
-  int coarsest = std::min(mg->coarsest, top);
-  const int dN = mg->delta_n > 0 ? mg->delta_n : 1;
-  for (int l = top; l >= coarsest; l -= dN) {
-    Level* L = get_level(m, capped(m->orders, m->dim, l, mg->direction));
-    if (!L) return DG_ECUDA;
-    C.lv.push_back(L);
-  }
-  DG_TRY(vcycle_level(C, 0, q, s));
+  cudaStream_t st = S(stream);
+  int evals = 0;
+  double dofs = 0.0;
+  int nlev = 0;
+  DG_TRY(run_vcycle(m, m->orders, q, s, *mg, st, &evals, &dofs, &nlev));
   double rn = 0.0;
-  if (want_norm) {
-    Level* F = m->fine.get();
-    DG_TRY(ensure_work(F));
-    DG_TRY(reset_max(m->d_scalars + 1, C.st));
-    DG_TRY(residual(m, F, q, s, F->d_R, false, C.st, m->d_scalars + 1, -1, nullptr, nullptr));
-    DG_TRY(read_scalar(m->d_scalars + 1, &rn, C.st));
-  }
+  if (want_norm) DG_TRY(level_norm(m, m->fine.get(), q, s, st, &rn));
   if (rep) {
-    rep->levels = (int32_t)C.lv.size();
-    rep->residual_evals = C.evals;
-    rep->dof_evals = C.dofs;
+    rep->levels = nlev;
+    rep->residual_evals = evals;
+    rep->dof_evals = dofs;
     rep->rnorm = rn;
   }
   return DG_OK;
@@ -460,10 +546,7 @@ int dg_tau_estimate(dg_mesh* m, const double* q, const double* s, int dir_mask, 
   DG_TRY(fill(m->d_tau, 0.0, (int64_t)tsz, st));
   // R^P(q) at the reference orders
   if (with_correction) DG_TRY(residual(m, F, q, s, F->d_R, isolated != 0, st, nullptr, -1, nullptr, nullptr));
-  int32_t* d_fine_orders = nullptr;
-  DG_CUDA_TRY(cudaMalloc(&d_fine_orders, m->orders.size() * sizeof(int32_t)));
-  DG_CUDA_TRY(cudaMemcpyAsync(d_fine_orders, m->orders.data(), m->orders.size() * sizeof(int32_t),
-                              cudaMemcpyHostToDevice, st));
+  const int32_t* d_fine_orders = m->d_orders;
   int rc = DG_OK;
   for (int i = 0; i < m->dim && rc == DG_OK; ++i) {
     if (!((dir_mask >> i) & 1)) continue;
@@ -499,7 +582,6 @@ int dg_tau_estimate(dg_mesh* m, const double* q, const double* s, int dir_mask, 
       rc = DG_ECUDA;
     }
   }
-  cudaFree(d_fine_orders);
   if (rc != DG_OK) return rc;
   for (int e = 0; e < m->K; ++e)
     for (int i = 0; i < 3; ++i)
@@ -532,6 +614,128 @@ int dg_profile_residual(dg_mesh* m, const double* q, const double* s, double* r,
     return DG_EINVAL;
   }
   return profile_residual(m, m->fine.get(), q, s, r, iters, ms_out, S(stream));
+}
+
+// Cycle (Q, Sv) with top orders `o` until max|r| < target or `cap` cycles;
+// *cycles counts them.  Returns DG_OK, DG_ENOTCONVERGED or DG_EDIVERGED.
+static int cycle_until(dg_mesh* m, const std::vector<int32_t>& o, Level* L, double* Q, const double* Sv,
+                       const dg_mg_params& mg, double target, int cap, cudaStream_t st, int* cycles, double* dofs,
+                       double* rn) {
+  DG_TRY(level_norm(m, L, Q, Sv, st, rn));
+  dofs[0] += 5.0 * L->nodes;
+  for (int c = 0; c < cap; ++c) {
+    if (!(*rn < target)) {
+      if (std::isnan(*rn) || std::isinf(*rn)) return DG_EDIVERGED;
+    } else {
+      return DG_OK;
+    }
+    int ev = 0, nl = 0;
+    double dd = 0.0;
+    DG_TRY(run_vcycle(m, o, Q, Sv, mg, st, &ev, &dd, &nl));
+    dofs[0] += dd;
+    (*cycles)++;
+    DG_TRY(level_norm(m, L, Q, Sv, st, rn));
+    dofs[0] += 5.0 * L->nodes;
+  }
+  if (std::isnan(*rn) || std::isinf(*rn)) return DG_EDIVERGED;
+  return (*rn < target) ? DG_OK : DG_ENOTCONVERGED;
+}
+
+int dg_solve_steady(dg_mesh** meshp, double** qp, const double* s, const dg_solve_params* sp, dg_alloc_fn alloc,
+                    void* alloc_ctx, dg_solve_report* rep, void* stream) {
+  if (!meshp || !*meshp || !qp || !*qp || !sp || !rep || sp->max_cycles < 0 || !(sp->tol > 0.0) ||
+      (sp->adapt && (!alloc || s)) || (sp->fmg && !(sp->fmg_tol > 0.0))) {
+    set_error("dg_solve_steady: bad argument (adaptation needs alloc and s == NULL)");
+    return DG_EINVAL;
+  }
+  std::memset(rep, 0, sizeof(*rep));
+  dg_mesh* m = *meshp;
+  double* q = *qp;
+  cudaStream_t st = S(stream);
+  dg_mg_params mg = sp->mg;
+  int rc = DG_OK;
+  double rn = 0.0;
+  // ---- full multigrid ramp (Sec. 3.1.1) ----
+  if (sp->fmg) {
+    int top = 0;
+    for (int e = 0; e < m->K; ++e)
+      for (int d = 0; d < m->dim; ++d) top = std::max(top, (int)m->orders[e * 3 + d]);
+    Level* prev = nullptr;
+    for (int l = 1; l < top; ++l) {
+      std::vector<int32_t> o = capped(m->orders, m->dim, l, -1);
+      Level* L = get_level(m, o);
+      if (!L) return DG_ECUDA;
+      DG_TRY(ensure_work(L));
+      if (!prev)
+        DG_TRY(transfer(m, m->fine.get(), L, 5, q, L->d_Q, st));  // initial state, L2-projected down
+      else
+        DG_TRY(transfer(m, prev, L, 5, prev->d_Q, L->d_Q, st));   // interpolated up
+      if (s) DG_TRY(transfer(m, m->fine.get(), L, 5, s, L->d_S, st));
+      int cyc = 0;
+      rc = cycle_until(m, o, L, L->d_Q, s ? L->d_S : nullptr, mg, sp->fmg_tol, sp->max_cycles, st, &cyc,
+                       &rep->dof_evals, &rn);
+      rep->cycles += cyc;
+      rep->fmg_cycles += cyc;
+      if (rc == DG_EDIVERGED) break;
+      rc = DG_OK;  // a FMG level that stalls still hands its state up
+      prev = L;
+    }
+    if (rc == DG_OK && prev) DG_TRY(transfer(m, prev, m->fine.get(), 5, prev->d_Q, q, st));
+  }
+  // ---- reference orders ----
+  if (rc == DG_OK) {
+    double target = sp->adapt ? sp->ap.tau_max / 10.0 : sp->tol;
+    int cyc = 0;
+    rc = cycle_until(m, m->orders, m->fine.get(), q, s, mg, target, sp->max_cycles, st, &cyc, &rep->dof_evals, &rn);
+    rep->cycles += cyc;
+  }
+  // ---- adaptation (Sec. 3.3.2) ----
+  if (rc == DG_OK && sp->adapt) {
+    rep->rnorm_adapt = rn;
+    std::vector<double> tau((size_t)m->K * 3 * kTauSlots);
+    DG_TRY(dg_tau_estimate(m, q, nullptr, (1 << m->dim) - 1, 1, 1, tau.data(), stream));
+    std::vector<int32_t> no(m->orders.size());
+    DG_TRY(dg_adapt(m, tau.data(), &sp->ap, no.data()));
+    if (no != m->orders) {
+      dg_mesh_desc d;
+      d.dim = m->dim;
+      d.K = m->K;
+      d.M = m->M;
+      d.xmap = m->xmap.data();
+      d.ftab = m->ftab.data();
+      std::memcpy(d.params, m->raw_params, sizeof(d.params));
+      dg_mesh* nm = nullptr;
+      DG_TRY(dg_mesh_create(&d, no.data(), &nm));
+      double* nq = (double*)alloc((size_t)5 * nm->fine->nodes * sizeof(double), alloc_ctx);
+      if (!nq) {
+        dg_mesh_destroy(nm);
+        set_error("dg_solve_steady: allocator returned NULL");
+        return DG_ENOMEM;
+      }
+      rc = transfer(m, m->fine.get(), nm->fine.get(), 5, q, nq, st);
+      if (rc != DG_OK) {
+        dg_mesh_destroy(nm);
+        return rc;
+      }
+      DG_CUDA_TRY(cudaStreamSynchronize(st));
+      dg_mesh_destroy(m);
+      m = nm;
+      q = nq;
+      *meshp = m;
+      *qp = q;
+      rep->adapted = 1;
+    }
+    int cyc = 0;
+    rc = cycle_until(m, m->orders, m->fine.get(), q, nullptr, mg, sp->tol, sp->max_cycles, st, &cyc,
+                     &rep->dof_evals, &rn);
+    rep->cycles += cyc;
+  }
+  rep->rnorm = rn;
+  rep->status = rc;
+  rep->nodes = m->fine->nodes;
+  if (rc != DG_OK) set_error(rc == DG_EDIVERGED ? "dg_solve_steady: residual diverged"
+                                                : "dg_solve_steady: cycle cap reached before the tolerance");
+  return rc;
 }
 
 int dg_transfer_noalloc(int32_t dim, int32_t K, const int32_t* orders_from, const int32_t* orders_to,

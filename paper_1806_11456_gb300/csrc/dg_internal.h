@@ -128,11 +128,21 @@ struct dg_mesh {
   std::vector<double> xmap;
   std::vector<int32_t> ftab;
   dg::Params prm;
+  double raw_params[16];
   std::vector<int32_t> orders;
   std::unique_ptr<dg::Level> fine;
   std::map<std::vector<int32_t>, std::unique_ptr<dg::Level>> levels;  // coarse levels by order map
   double* d_scalars = nullptr;   // [0] dt, [1] norm, [2..] scratch
   double* d_tau = nullptr;       // K x 3 x 16 tau table
+  int32_t* d_orders = nullptr;   // K x 3 orders on the device
+  cudaStream_t cap_stream = nullptr;  // stream used to capture cycle graphs
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    int evals = 0;
+    double dofs = 0.0;
+    unsigned long long launches = 0;
+  };
+  std::map<std::string, Graph> graphs;  // captured V-cycles by (orders, pointers, parameters)
 };
 
 namespace dg {
@@ -144,6 +154,8 @@ Params make_params(const double* p);
 // kernels (dg_kernels.cu)
 int upload_tables();
 unsigned long long launches();
+void add_launches(unsigned long long n);
+int prepare_capture();  // one-time per-device set-up that may not run inside a capture
 int residual(const dg_mesh* m, Level* L, const double* q, const double* s, double* r, bool isolated,
              cudaStream_t st, double* d_norm, int rk_stage, double* rk_g, const double* d_dt);
 int cfl_dt(const dg_mesh* m, Level* L, const double* q, double* d_dt, cudaStream_t st);

@@ -45,6 +45,7 @@ __constant__ double* c_T;     // [kNP][kNP][kNP*kNP] transfer matrices (n_from, 
 static double* g_dev_Dhat = nullptr;
 static unsigned long long g_launches = 0;  // kernels launched by this library (host-side count)
 unsigned long long launches() { return g_launches; }
+void add_launches(unsigned long long n) { g_launches += n; }
 static double* g_dev_D = nullptr;
 static double* g_dev_T = nullptr;
 static int g_tables_device = -1;
@@ -1017,6 +1018,8 @@ static int configure_smem() {
   done_dev = dev;
   return DG_OK;
 }
+
+int prepare_capture() { return configure_smem(); }
 
 static int grid_for(int64_t n) {
   int64_t b = (n + 255) / 256;

@@ -34,7 +34,16 @@ class MeshDesc(ctypes.Structure):
 class MGParams(ctypes.Structure):
     _fields_ = [("beta1", ctypes.c_int32), ("beta2", ctypes.c_int32), ("beta_c", ctypes.c_int32),
                 ("direction", ctypes.c_int32), ("coarsest", ctypes.c_int32), ("delta_n", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("graph", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class SolveReport(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int32), ("fmg_cycles", ctypes.c_int32), ("adapted", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("rnorm", ctypes.c_double), ("rnorm_adapt", ctypes.c_double),
+                ("dof_evals", ctypes.c_double), ("nodes", ctypes.c_int64)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 
 
 class CycleReport(ctypes.Structure):
@@ -48,6 +57,12 @@ class AdaptParams(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 3)]
 
 
+class SolveParams(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_cycles", ctypes.c_int32), ("fmg", ctypes.c_int32),
+                ("fmg_tol", ctypes.c_double), ("mg", MGParams), ("adapt", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("ap", AdaptParams)]
+
+
 _lib = None
 _vp = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -55,7 +70,7 @@ _ip = ctypes.POINTER(ctypes.c_int32)
 
 EXPORTS = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_layout", "dg_residual", "dg_cfl_dt", "dg_smooth",
            "dg_pmg_vcycle", "dg_tau_estimate", "dg_adapt", "dg_transfer_state", "dg_profile_residual",
-           "dg_kernel_launches", "dg_transfer_noalloc", "dg_last_error"]
+           "dg_kernel_launches", "dg_transfer_noalloc", "dg_solve_steady", "dg_mesh_orders", "dg_last_error"]
 KERNEL_STAGES = ["trace_q", "mortar_u_star", "volume", "mortar_flux", "surface", "isolated"]
 
 
@@ -80,6 +95,9 @@ def lib(path=LIB_PATH):
     L.dg_transfer_state.argtypes = [_vp, _vp, _vp, _vp, _vp]
     L.dg_profile_residual.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, _dp, _vp]
     L.dg_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_int64)]
+    L.dg_solve_steady.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp, ctypes.POINTER(SolveParams), ALLOC_FN,
+                                  _vp, ctypes.POINTER(SolveReport), _vp]
+    L.dg_mesh_orders.argtypes = [_vp, _ip]
     L.dg_transfer_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, _ip, _ip, ctypes.c_int32, _vp, _vp, _vp]
     _lib = L
     return L
@@ -177,10 +195,10 @@ class Mesh:
         return q
 
     def vcycle(self, q, s=None, beta1=3, beta2=3, beta_c=3, direction=-1, coarsest=1, delta_n=1,
-               want_norm=False, stream=None):
+               graph=False, want_norm=False, stream=None):
         mg = MGParams()
-        mg.beta1, mg.beta2, mg.beta_c, mg.direction, mg.coarsest, mg.delta_n = \
-            beta1, beta2, beta_c, direction, coarsest, delta_n
+        mg.beta1, mg.beta2, mg.beta_c, mg.direction, mg.coarsest, mg.delta_n, mg.graph = \
+            beta1, beta2, beta_c, direction, coarsest, delta_n, int(bool(graph))
         rep = CycleReport()
         _check(lib().dg_pmg_vcycle(self.h, _ptr(q), _ptr(s), ctypes.byref(mg), int(bool(want_norm)),
                                    ctypes.byref(rep), _stream(stream)))
@@ -210,6 +228,48 @@ class Mesh:
         _check(lib().dg_profile_residual(self.h, _ptr(q), _ptr(s), _ptr(r), int(iters), ms.ctypes.data_as(_dp),
                                          _stream(stream)))
         return dict(zip(KERNEL_STAGES, ms.tolist()))
+
+    def solve_steady(self, q, s=None, tol=1e-10, max_cycles=200, fmg=False, fmg_tol=1e-1, mg=None, adapt=False,
+                     tau_max=1e-4, n_min=1, n_max=7, jump_rule=1, conform_tag=-1, cap=0, stream=None):
+        """Steady solve through dg_solve_steady.  Returns (q, report); with
+        adaptation q is a new tensor on the adapted mesh, which this object
+        then wraps (its orders are updated)."""
+        import torch
+        sp = SolveParams()
+        sp.tol, sp.max_cycles, sp.fmg, sp.fmg_tol, sp.adapt = float(tol), int(max_cycles), int(bool(fmg)), \
+            float(fmg_tol), int(bool(adapt))
+        m = dict(beta1=3, beta2=3, beta_c=6, direction=-1, coarsest=1, delta_n=1, graph=1)
+        m.update(mg or {})
+        for k, v in m.items():
+            setattr(sp.mg, k, int(v))
+        sp.ap.tau_max, sp.ap.n_min, sp.ap.n_max, sp.ap.cap, sp.ap.jump_rule, sp.ap.conform_tag = \
+            float(tau_max), n_min, n_max, cap, jump_rule, conform_tag
+        keep = []
+
+        def _alloc(nbytes, _ctx):
+            t = torch.empty(int(nbytes) // 8, dtype=torch.float64, device=q.device)
+            keep.append(t)
+            return t.data_ptr()
+
+        cb = ALLOC_FN(_alloc)
+        hp = _vp(self.h.value)
+        qp = _vp(q.data_ptr())
+        rep = SolveReport()
+        _ptr(q)
+        rc = lib().dg_solve_steady(ctypes.byref(hp), ctypes.byref(qp), _ptr(s), ctypes.byref(sp), cb, None,
+                                   ctypes.byref(rep), _stream(stream))
+        out = q
+        if rep.adapted:
+            self.h = hp
+            orders = np.zeros((self.K, 3), dtype=np.int32)
+            _check(lib().dg_mesh_orders(self.h, orders.ctypes.data_as(_ip)))
+            self.orders = orders
+            out = keep[-1]
+        report = dict(cycles=rep.cycles, fmg_cycles=rep.fmg_cycles, adapted=bool(rep.adapted), status=rep.status,
+                      rnorm=rep.rnorm, rnorm_adapt=rep.rnorm_adapt, dof_evals=rep.dof_evals, nodes=rep.nodes)
+        if rc not in (0, -4, -5):
+            _check(rc)
+        return out, report
 
     def transfer_state_to(self, other, q_from, q_to=None, stream=None):
         import torch

@@ -28,7 +28,7 @@ import numpy as np
 BC_INTERIOR, BC_FREESTREAM, BC_OUTFLOW, BC_SLIP, BC_WALL = 0, 1, 2, 3, 4
 
 
-def flow_params(mach=0.3, re=100.0, pr=0.72, gamma=1.4, ca=0.4, cnu=0.4):
+def flow_params(mach=0.3, re=100.0, pr=0.72, gamma=1.4, ca=0.2, cnu=0.2):
     """Parameter vector (16 doubles) understood by both implementations.
 
     0 gamma, 1 Pr, 2 Mach, 3 Re, 4 Sutherland constant (110.4 K / 288.15 K),

@@ -236,3 +236,59 @@ def test_invalid_arguments_rejected(dg):
     bad["ftab"] = ft
     with pytest.raises(dg.DGError):
         dg.Mesh(bad, syn.uniform_orders(1, 3, 2), prm)
+
+
+# ---------------------------------------------------------------------------
+# steady driver
+# ---------------------------------------------------------------------------
+def test_solve_steady_fixed_cycles_parity(dg):
+    """FMG ramp + reference phase with unreachable tolerances: both sides run
+    exactly max_cycles cycles per phase; final states compared."""
+    mesh = syn.periodic_box(2, 2, 1, dim=2)
+    prm = syn.flow_params(mach=0.3, re=100.0)
+    o = syn.random_orders(mesh["K"], 2, 2, 4, 31)
+    q = syn.perturbed_state(mesh, o, prm, 3, amp=0.02)
+    s = syn.random_source(mesh, o, 4, amp=1e-3)
+    mg = dict(beta1=1, beta2=1, beta_c=2, direction=-1, coarsest=1, delta_n=1)
+    M = dg.Mesh(mesh, o, prm)
+    qd = _dev(q)
+    qd2, rep = M.solve_steady(qd, _dev(s), tol=1e-30, max_cycles=2, fmg=True, fmg_tol=1e-30, mg=dict(mg, graph=1))
+    o2, qo, repo = orc.solve_steady(mesh, o, prm, q, s, 1e-30, 2, mg, fmg=True, fmg_tol=1e-30)
+    assert rep["status"] == -5 and repo["status"] == "cap"
+    assert rep["cycles"] == repo["cycles"] and rep["fmg_cycles"] == repo["fmg_cycles"]
+    assert np.max(np.abs(qd2.cpu().numpy() - qo)) <= TOL * np.max(np.abs(qo))
+
+
+def test_solve_steady_adaptation_parity(dg):
+    """Reference phase skipped (tau_max large), tau estimate, adaptation to a
+    new mesh, two final cycles: orders and states compared."""
+    mesh = syn.periodic_box(3, 2, 1, dim=2)
+    prm = syn.flow_params(mach=0.3, re=100.0)
+    P = syn.uniform_orders(mesh["K"], 2, 5)
+    q = syn.manufactured_state(mesh, P, 5, prm[2], prm[0], amp=0.05)
+    mg = dict(beta1=1, beta2=1, beta_c=2, direction=-1, coarsest=1, delta_n=1)
+    tau_max = 1e3  # target tau_max / 10 is met at once
+    M = dg.Mesh(mesh, P, prm)
+    qd, rep = M.solve_steady(_dev(q), None, tol=1e-30, max_cycles=2, mg=mg, adapt=True, tau_max=tau_max,
+                             n_min=1, n_max=6, jump_rule=1)
+    ap = dict(tau_max=tau_max, n_min=1, n_max=6, jump_rule=1)
+    oo, qo, repo = orc.solve_steady(mesh, P, prm, q, None, 1e-30, 2, mg, adapt=ap)
+    assert rep["adapted"] == repo["adapted"]
+    assert np.array_equal(M.orders, oo)
+    assert rep["cycles"] == repo["cycles"] == 2
+    assert np.max(np.abs(qd.cpu().numpy() - qo)) <= TOL * np.max(np.abs(qo))
+
+
+def test_graph_replay_matches_direct_launches(dg):
+    mesh, o, prm, q = CASES["plate2d_all_bcs"]()
+    s = syn.random_source(mesh, o, 5)
+    M = dg.Mesh(mesh, o, prm)
+    kw = dict(beta1=2, beta2=1, beta_c=3)
+    qa = _dev(q)
+    sd = _dev(s)
+    M.vcycle(qa, sd, **kw)
+    M.vcycle(qa, sd, **kw)
+    qb = _dev(q)
+    M.vcycle(qb, sd, graph=True, **kw)   # captured
+    M.vcycle(qb, sd, graph=True, **kw)   # replayed
+    assert np.array_equal(qa.cpu().numpy(), qb.cpu().numpy())
