@@ -292,13 +292,13 @@ int dg_transfer_noalloc(int32_t dim, int32_t K, const int32_t* orders_from, cons
                         int32_t nvar, const double* in, double* out, void* stream);
 
 /*
- * dg_profile_residual -- measurement aid: runs `iters` evaluations of the
- * full residual r = S - A(q) (as dg_residual) with CUDA events recorded on
- * `stream` between its launches, and writes the mean duration in ms of each
- * stage to ms_out[0..5]: face traces, mortar pass 1 (BR1 U*), volume (BR1
- * gradient + flux divergence), mortar pass 2 (Roe + BR1 flux), surface +
- * residual, and ms_out[5] the isolated operator (one launch).  r is scratch
- * output.  Synchronises the stream.
+ * dg_profile_residual -- measurement aid: evaluates the full residual
+ * r = S - A(q) once (as dg_residual), then launches each of its stages
+ * `iters` times back to back between two CUDA events recorded on `stream`
+ * and writes the mean duration per launch in ms to ms_out[0..5]: face
+ * traces, mortar pass 1 (BR1 U*), volume (BR1 gradient + flux divergence),
+ * mortar pass 2 (Roe + BR1 flux), surface + residual, and ms_out[5] the
+ * isolated operator.  r receives the residual.  Synchronises the stream.
  */
 int dg_profile_residual(dg_mesh* mesh, const double* q, const double* s, double* r, int iters,
                         double* ms_out, void* stream);

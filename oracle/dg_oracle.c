@@ -324,8 +324,15 @@ static void build_offsets(mesh_t* m) {
   }
 }
 
-/* Mapping x(xi) and dx/dxi_j at reference point xi for element e. */
+/* Mapping x(xi) - o and dx/dxi_j at reference point xi for element e, with
+ * o = shift (NULL: no shift) subtracted from every mapping node first. */
+static void mapping_eval_shift(const mesh_t* m, int e, const double* xi, const double* shift, double* x,
+                               double dx[3][3]);
 static void mapping_eval(const mesh_t* m, int e, const double* xi, double* x, double dx[3][3]) {
+  mapping_eval_shift(m, e, xi, NULL, x, dx);
+}
+static void mapping_eval_shift(const mesh_t* m, int e, const double* xi, const double* shift, double* x,
+                               double dx[3][3]) {
   int M = m->M, Mp = M + 1;
   double eq[OR_NP];
   for (int a = 0; a <= M; ++a) eq[a] = (M == 0) ? 0.0 : -1.0 + 2.0 * a / M;
@@ -345,7 +352,10 @@ static void mapping_eval(const mesh_t* m, int e, const double* xi, double* x, do
     for (int cc = 0; cc <= M; ++cc)
       for (int b = 0; b <= M; ++b)
         for (int a = 0; a <= M; ++a) {
-          const double* p = X + 3 * ((cc * Mp + b) * Mp + a);
+          const double* p0 = X + 3 * ((cc * Mp + b) * Mp + a);
+          double p[3] = {p0[0], p0[1], p0[2]};
+          if (shift)
+            for (int c = 0; c < 3; ++c) p[c] -= shift[c];
           double f = L[0][a] * L[1][b] * L[2][cc];
           double f0 = D[0][a] * L[1][b] * L[2][cc];
           double f1 = L[0][a] * D[1][b] * L[2][cc];
@@ -361,7 +371,10 @@ static void mapping_eval(const mesh_t* m, int e, const double* xi, double* x, do
     /* 2D: x, y from the planar mapping; the extrusion is z = zeta. */
     for (int b = 0; b <= M; ++b)
       for (int a = 0; a <= M; ++a) {
-        const double* p = X + 3 * (b * Mp + a);
+        const double* p0 = X + 3 * (b * Mp + a);
+        double p[3] = {p0[0], p0[1], p0[2]};
+        if (shift)
+          for (int c = 0; c < 2; ++c) p[c] -= shift[c];
         double f = L[0][a] * L[1][b];
         double f0 = D[0][a] * L[1][b];
         double f1 = L[0][a] * D[1][b];
@@ -393,7 +406,10 @@ static void element_metrics(const mesh_t* m, int e, double* Ja, double* J) {
         int nd = (k * n[1] + j) * n[0] + i;
         double xi[3] = {x0[i], x1[j], (m->dim == 3) ? x2[k] : 0.0};
         double x[3], dx[3][3];
-        mapping_eval(m, e, xi, x, dx);
+        /* coordinates relative to the element's first mapping node */
+        mapping_eval_shift(m, e, xi, m->xmap + (size_t)e * (m->dim == 3 ? (m->M + 1) * (m->M + 1) * (m->M + 1)
+                                                                          : (m->M + 1) * (m->M + 1)) * 3,
+                           x, dx);
         for (int c = 0; c < 3; ++c) {
           xs[nd * 3 + c] = x[c];
           for (int jj = 0; jj < 3; ++jj) dxs[nd * 9 + c * 3 + jj] = dx[c][jj];
@@ -419,7 +435,11 @@ static void element_metrics(const mesh_t* m, int e, double* Ja, double* J) {
       }
   if (m->dim == 3) {
     /* For Cartesian component cn (n in the curl formula), with (n,m,l) cyclic:
-     * V = I^N( X_l grad X_m - X_m grad X_l ),  Ja^i_n = -1/2 (curl_xi V)_i. */
+     * V = I^N( X_l grad X_m - X_m grad X_l ),  Ja^i_n = -1/2 (curl_xi V)_i.
+     * X is taken relative to the element's first mapping node o (xs holds
+     * x - o): the extra terms -o_l grad X_m + o_m grad X_l have zero discrete
+     * curl whenever M <= N, and the products no longer cancel large absolute
+     * coordinates. */
     double* V = (double*)malloc(sizeof(double) * nn * 3);
     for (int cn = 0; cn < 3; ++cn) {
       int cm = (cn + 1) % 3, cl = (cn + 2) % 3;

@@ -16,8 +16,9 @@ namespace dg {
 constexpr int kNMax = 12;               // highest polynomial order
 constexpr int kNP = kNMax + 2;          // table stride (n = 1 .. kNMax+1)
 constexpr int kMaxElemNodes = 729;      // 3D element node cap (smem staging)
-constexpr int kTileNodes = 256;         // element-kernel CTA size (threads)
-constexpr int kMortarTile = 256;        // mortar-kernel CTA size (threads)
+constexpr int kTileNodes = 128;         // element-kernel CTA size (threads) and tile target
+constexpr int kMortarTile = 64;         // mortar-kernel CTA size (threads) and tile target
+constexpr int kMortarTileMax = 169;     // a single mortar of 13 x 13 nodes forms its own tile
 constexpr int kTauSlots = 16;           // orders per direction in the tau table
 
 void set_error(const std::string& msg);
@@ -116,6 +117,8 @@ struct Level {
   int n_tiles = 0;
   size_t tile_smem_nodes = 0;           // max nodes of a tile
   double* d_vol = nullptr;              // 5 x nodes volume part
+  bool affine = false;                  // metrics constant within every element
+  std::vector<int32_t> nvec_host;       // K x 3 node counts (host copy)
   // multigrid work arrays (allocated on first use)
   double *d_Q = nullptr, *d_S = nullptr, *d_Q0 = nullptr, *d_G = nullptr, *d_R = nullptr;
   ~Level();

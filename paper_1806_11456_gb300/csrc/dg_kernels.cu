@@ -282,32 +282,45 @@ DEV void face_dirs(int f, int& d, int& ta, int& tb, int& side) {
   tb = (d == 2) ? 1 : 2;
 }
 
+// component k of a 3-vector held in scalars (avoids local-memory arrays)
+DEV int pick(int k, int a0, int a1, int a2) { return k == 0 ? a0 : (k == 1 ? a1 : a2); }
+
 // Interpolate face values (nvar comps, stride fs) of an na x nb face to the
 // mortar point (ia, ib) of an ma x mb rule.
-DEV void face_interp(const double* X, int64_t fs, int na, int nb, int ma, int mb, int ia, int ib, int nvar,
-                     double* out) {
+template <int NVAR>
+DEV void face_interp(const double* X, int64_t fs, int na, int nb, int ma, int mb, int ia, int ib, double* out) {
   if (na == ma && nb == mb) {
     int p = ib * na + ia;
-    for (int v = 0; v < nvar; ++v) out[v] = X[v * fs + p];
+#pragma unroll
+    for (int v = 0; v < NVAR; ++v) out[v] = X[v * fs + p];
     return;
   }
   const double* Ta = c_T + ((size_t)na * kNP + ma) * kNP * kNP + ia * na;
   const double* Tb = c_T + ((size_t)nb * kNP + mb) * kNP * kNP + ib * nb;
-  for (int v = 0; v < nvar; ++v) out[v] = 0.0;
+#pragma unroll
+  for (int v = 0; v < NVAR; ++v) out[v] = 0.0;
   for (int kb = 0; kb < nb; ++kb) {
     double wb = Tb[kb];
     if (wb == 0.0) continue;
     for (int ka = 0; ka < na; ++ka) {
       double wgt = wb * Ta[ka];
       int p = kb * na + ka;
-      for (int v = 0; v < nvar; ++v) out[v] += wgt * X[v * fs + p];
+#pragma unroll
+      for (int v = 0; v < NVAR; ++v) out[v] += wgt * X[v * fs + p];
     }
   }
+}
+
+// Node-count of face f of an element with node counts (n0, n1, n2)
+DEV int face_size(int f, int n0, int n1, int n2) {
+  int d = f >> 1;
+  return d == 0 ? n1 * n2 : (d == 1 ? n0 * n2 : n0 * n1);
 }
 
 // ---------------------------------------------------------------------------
 // k_trace_q: conserved state at every face node of every element
 // ---------------------------------------------------------------------------
+template <int DIM>
 __global__ void __launch_bounds__(kTileNodes) k_trace_q(LevelArgs A, const double* __restrict__ q,
                                                         double* __restrict__ trq) {
   extern __shared__ double smem[];
@@ -324,35 +337,33 @@ __global__ void __launch_bounds__(kTileNodes) k_trace_q(LevelArgs A, const doubl
     for (int v = 0; v < 5; ++v) sq[v * T + i] = qe[v * nn + node];
   }
   __syncthreads();
-  const int nvec[3] = {n0, n1, n2};
-  const int fsz[3] = {n1 * n2, n0 * n2, n0 * n1};
-  const int nfaces = 2 * A.dim;
   int FE = 0;
-  for (int f = 0; f < nfaces; ++f) FE += fsz[f >> 1];
+#pragma unroll
+  for (int f = 0; f < 2 * DIM; ++f) FE += face_size(f, n0, n1, n2);
   for (int i = threadIdx.x; i < t.count * FE; i += blockDim.x) {
     int le = i / FE, r = i - le * FE;
     int f = 0;
-    while (r >= fsz[f >> 1]) {
-      r -= fsz[f >> 1];
+    while (r >= face_size(f, n0, n1, n2)) {
+      r -= face_size(f, n0, n1, n2);
       ++f;
     }
     int d, ta, tb, side;
     face_dirs(f, d, ta, tb, side);
-    int ia = r % nvec[ta], ib = r / nvec[ta];
-    int idx[3];
-    idx[d] = 0;
-    idx[ta] = ia;
-    idx[tb] = ib;
-    int base = (idx[2] * n1 + idx[1]) * n0 + idx[0];
+    const int nta = pick(ta, n0, n1, n2), nd = pick(d, n0, n1, n2);
+    int ia = r % nta, ib = r / nta;
+    int i0 = (d == 0) ? 0 : ia;               // index along x (ta = x unless d == 0)
+    int i1 = (d == 1) ? 0 : (d == 0 ? ia : ib);
+    int i2 = (d == 2) ? 0 : ib;
+    int base = (i2 * n1 + i1) * n0 + i0;
     int sd = (d == 0) ? 1 : (d == 1 ? n0 : n0 * n1);
-    const double* lb = side ? c_tab.lp[nvec[d]] : c_tab.lm[nvec[d]];
+    const double* lb = side ? c_tab.lp[nd] : c_tab.lm[nd];
     int e = A.tile_elems[t.first + le];
     int64_t p = A.fo[e * 6 + f] + r;
     const double* s0 = sq + le * nn + base;
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       double acc = 0.0;
-      for (int k = 0; k < nvec[d]; ++k) acc += lb[k] * s0[v * T + k * sd];
+      for (int k = 0; k < nd; ++k) acc += lb[k] * s0[v * T + k * sd];
       trq[v * A.fn + p] = acc;
     }
   }
@@ -379,79 +390,91 @@ static MortarArgs margs(const Level* L) {
   return a;
 }
 
+// value at one mortar node: U* (PASS 1) or F* S-hat (PASS 2)
 template <int PASS>
-__global__ void __launch_bounds__(kMortarTile) k_mortar(LevelArgs A, MortarArgs MA, Params P,
-                                                        const double* __restrict__ trq,
-                                                        const double* __restrict__ trg, double* __restrict__ out) {
-  constexpr int NV = (PASS == 1) ? 4 : 5;
-  __shared__ double sval[kMortarTile * 5];
-  __shared__ int scum[kMortarTile + 1];
-  const MortarTile mt = MA.tiles[blockIdx.x];
-  const Gas G = make_gas(P);
-  for (int i = threadIdx.x; i < mt.nodes; i += blockDim.x) {
-    const int64_t gp = mt.node_first + i;
-    const MortarDev M = MA.mortars[MA.mnode_mortar[gp]];
-    const int loc = (int)(gp - M.node_off);
-    const int a = loc % M.ma, b = loc / M.ma;
-    int dL, taL, tbL, sL;
-    face_dirs(M.fL, dL, taL, tbL, sL);
-    const int nLa = A.n[M.eL * 3 + taL], nLb = A.n[M.eL * 3 + tbL];
-    const int64_t pL = A.fo[M.eL * 6 + M.fL];
-    double qL[5], qR[5], gL[12], gR[12];
-    face_interp(trq + pL, A.fn, nLa, nLb, M.ma, M.mb, a, b, 5, qL);
-    if (PASS == 2) face_interp(trg + pL, A.fn, nLa, nLb, M.ma, M.mb, a, b, 12, gL);
-    double nS[3] = {MA.mnS[gp], MA.mnS[MA.mnodes + gp], MA.mnS[2 * MA.mnodes + gp]};
-    double S = sqrt(nS[0] * nS[0] + nS[1] * nS[1] + nS[2] * nS[2]);
-    double iS = 1.0 / S;
-    double nu[3] = {nS[0] * iS, nS[1] * iS, nS[2] * iS};
-    if (M.eR >= 0) {
-      int dR, taR, tbR, sR;
-      face_dirs(M.fR, dR, taR, tbR, sR);
-      const int Ra = A.n[M.eR * 3 + taR], Rb = A.n[M.eR * 3 + tbR];
-      const bool sw = M.orient & 1;
-      const int Ma = sw ? M.mb : M.ma, Mb = sw ? M.ma : M.mb;
-      int ia = sw ? b : a, ib = sw ? a : b;
-      if (M.orient & 2) ia = Ma - 1 - ia;
-      if (M.orient & 4) ib = Mb - 1 - ib;
-      const int64_t pR = A.fo[M.eR * 6 + M.fR];
-      face_interp(trq + pR, A.fn, Ra, Rb, Ma, Mb, ia, ib, 5, qR);
-      if (PASS == 2) face_interp(trg + pR, A.fn, Ra, Rb, Ma, Mb, ia, ib, 12, gR);
+DEV void mortar_node_value(const LevelArgs& A, const MortarArgs& MA, const Gas& G, const double* __restrict__ trq,
+                           const double* __restrict__ trg, int64_t gp, double* o) {
+  const MortarDev M = MA.mortars[MA.mnode_mortar[gp]];
+  const int loc = (int)(gp - M.node_off);
+  const int a = loc % M.ma, b = loc / M.ma;
+  int dL, taL, tbL, sL;
+  face_dirs(M.fL, dL, taL, tbL, sL);
+  const int nLa = A.n[M.eL * 3 + taL], nLb = A.n[M.eL * 3 + tbL];
+  const int64_t pL = A.fo[M.eL * 6 + M.fL];
+  double qL[5], qR[5];
+  face_interp<5>(trq + pL, A.fn, nLa, nLb, M.ma, M.mb, a, b, qL);
+  const double nS0 = MA.mnS[gp], nS1 = MA.mnS[MA.mnodes + gp], nS2 = MA.mnS[2 * MA.mnodes + gp];
+  const double S = sqrt(nS0 * nS0 + nS1 * nS1 + nS2 * nS2);
+  const double iS = 1.0 / S;
+  const double nu[3] = {nS0 * iS, nS1 * iS, nS2 * iS};
+  int Ra = 0, Rb = 0, Ma = 0, Mb = 0, ia = 0, ib = 0;
+  int64_t pR = 0;
+  if (M.eR >= 0) {
+    int dR, taR, tbR, sR;
+    face_dirs(M.fR, dR, taR, tbR, sR);
+    Ra = A.n[M.eR * 3 + taR];
+    Rb = A.n[M.eR * 3 + tbR];
+    const bool sw = M.orient & 1;
+    Ma = sw ? M.mb : M.ma;
+    Mb = sw ? M.ma : M.mb;
+    ia = sw ? b : a;
+    ib = sw ? a : b;
+    if (M.orient & 2) ia = Ma - 1 - ia;
+    if (M.orient & 4) ib = Mb - 1 - ib;
+    pR = A.fo[M.eR * 6 + M.fR];
+    face_interp<5>(trq + pR, A.fn, Ra, Rb, Ma, Mb, ia, ib, qR);
+  } else {
+    ghost(M.bc, qL, nu, G, qR);
+  }
+  if (PASS == 1) {
+    double ir, u[3], p, T, u2[3], T2;
+    to_prim(qL, G, ir, u, p, T);
+    to_prim(qR, G, ir, u2, p, T2);
+    o[0] = 0.5 * (u[0] + u2[0]);
+    o[1] = 0.5 * (u[1] + u2[1]);
+    o[2] = 0.5 * (u[2] + u2[2]);
+    o[3] = 0.5 * (T + T2);
+    return;
+  }
+  double f[5];
+  roe(qL, qR, nu, G, f);
+  if (!(M.eR < 0 && M.bc == DG_BC_SLIP)) {
+    double g[12], fv[5];
+    face_interp<12>(trg + pL, A.fn, nLa, nLb, M.ma, M.mb, a, b, g);
+    double ir, u[3], p, T;
+    to_prim(qL, G, ir, u, p, T);
+    const double mu = mu_of_T(T, G);
+    if (M.eR < 0 && M.bc == DG_BC_WALL) {
+      const double z[3] = {0, 0, 0};
+      visc_flux(z, mu, g, nu, G, false, fv);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) f[v] -= G.invRe * fv[v];
     } else {
-      ghost(M.bc, qL, nu, G, qR);
-      if (PASS == 2)
-        for (int k = 0; k < 12; ++k) gR[k] = gL[k];
-    }
-    double* o = sval + i * 5;
-    if (PASS == 1) {
-      double ir, u[3], p, T, u2[3], T2;
-      to_prim(qL, G, ir, u, p, T);
-      to_prim(qR, G, ir, u2, p, T2);
-      o[0] = 0.5 * (u[0] + u2[0]);
-      o[1] = 0.5 * (u[1] + u2[1]);
-      o[2] = 0.5 * (u[2] + u2[2]);
-      o[3] = 0.5 * (T + T2);
-    } else {
-      double fr[5];
-      roe(qL, qR, nu, G, fr);
-      double fv[5] = {0, 0, 0, 0, 0};
-      if (!(M.eR < 0 && M.bc == DG_BC_SLIP)) {
-        double ir, u[3], p, T;
-        to_prim(qL, G, ir, u, p, T);
-        double mu = mu_of_T(T, G);
-        if (M.eR < 0 && M.bc == DG_BC_WALL) {
-          double z[3] = {0, 0, 0};
-          visc_flux(z, mu, gL, nu, G, false, fv);
-        } else {
-          double f1[5], f2[5], ir2, u2[3], p2, T2;
-          visc_flux(u, mu, gL, nu, G, true, f1);
-          to_prim(qR, G, ir2, u2, p2, T2);
-          visc_flux(u2, mu_of_T(T2, G), gR, nu, G, true, f2);
-          for (int v = 0; v < 5; ++v) fv[v] = 0.5 * (f1[v] + f2[v]);
-        }
-      }
-      for (int v = 0; v < 5; ++v) o[v] = S * (fr[v] - G.invRe * fv[v]);
+      visc_flux(u, mu, g, nu, G, true, fv);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) f[v] -= 0.5 * G.invRe * fv[v];
+      if (M.eR >= 0) face_interp<12>(trg + pR, A.fn, Ra, Rb, Ma, Mb, ia, ib, g);  // else: interior gradient
+      to_prim(qR, G, ir, u, p, T);
+      visc_flux(u, mu_of_T(T, G), g, nu, G, true, fv);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) f[v] -= 0.5 * G.invRe * fv[v];
     }
   }
+#pragma unroll
+  for (int v = 0; v < 5; ++v) o[v] = S * f[v];
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(kMortarTile, 8) k_mortar(LevelArgs A, MortarArgs MA, Params P,
+                                                           const double* __restrict__ trq,
+                                                           const double* __restrict__ trg, double* __restrict__ out) {
+  constexpr int NV = (PASS == 1) ? 4 : 5;
+  __shared__ double sval[kMortarTileMax * 5];
+  __shared__ int scum[kMortarTileMax + 1];
+  const MortarTile mt = MA.tiles[blockIdx.x];
+  const Gas G = make_gas(P);
+  for (int i = threadIdx.x; i < mt.nodes; i += blockDim.x)
+    mortar_node_value<PASS>(A, MA, G, trq, trg, mt.node_first + i, sval + i * 5);
   // prefix of projection outputs per mortar in the tile
   if (threadIdx.x == 0) {
     int acc = 0;
@@ -480,13 +503,16 @@ __global__ void __launch_bounds__(kMortarTile) k_mortar(LevelArgs A, MortarArgs 
     int dL, taL, tbL, sL;
     face_dirs(M.fL, dL, taL, tbL, sL);
     const int nLa = A.n[M.eL * 3 + taL], nLb = A.n[M.eL * 3 + tbL];
-    double acc[5] = {0, 0, 0, 0, 0};
+    double acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = 0.0;
     int64_t dst;
     double sgn = 1.0;
     if (r < nLa * nLb) {
       int ka = r % nLa, kb = r / nLa;
       dst = A.fo[M.eL * 6 + M.fL] + r;
       if (M.flags & 1) {
+#pragma unroll
         for (int v = 0; v < NV; ++v) acc[v] = vals[r * 5 + v];
       } else {
         const double* Pa = c_T + ((size_t)M.ma * kNP + nLa) * kNP * kNP + ka * M.ma;
@@ -494,6 +520,7 @@ __global__ void __launch_bounds__(kMortarTile) k_mortar(LevelArgs A, MortarArgs 
         for (int bb = 0; bb < M.mb; ++bb)
           for (int aa = 0; aa < M.ma; ++aa) {
             double wgt = Pa[aa] * Pb[bb];
+#pragma unroll
             for (int v = 0; v < NV; ++v) acc[v] += wgt * vals[(bb * M.ma + aa) * 5 + v];
           }
       }
@@ -516,45 +543,33 @@ __global__ void __launch_bounds__(kMortarTile) k_mortar(LevelArgs A, MortarArgs 
           if (M.orient & 4) ib = Mb - 1 - ib;
           double wgt = Pa[ia] * Pb[ib];
           if (wgt == 0.0) continue;
+#pragma unroll
           for (int v = 0; v < NV; ++v) acc[v] += wgt * vals[(bb * M.ma + aa) * 5 + v];
         }
     }
+#pragma unroll
     for (int v = 0; v < NV; ++v) out[v * A.fn + dst] = sgn * acc[v];
   }
 }
 
 // ---------------------------------------------------------------------------
-// k_volume: BR1 gradient (weak form), gradient traces, flux divergence
+// element kernels: staging, BR1 gradient, fluxes, divergence
 // ---------------------------------------------------------------------------
-struct TileShape {
-  int n[3];
-  int nn, T;
-};
-
-DEV void load_dtables(double* sD, const double* src, const int* n, int dim) {
+DEV void load_dtables(double* sD, const double* src, int n0, int n1, int n2, int dim) {
   // sD[d][i][a] with stride kNP*kNP per direction
-  for (int d = 0; d < dim; ++d)
-    for (int k = threadIdx.x; k < n[d] * n[d]; k += blockDim.x) {
-      int i = k / n[d], a = k - i * n[d];
-      sD[d * kNP * kNP + i * kNP + a] = src[((size_t)n[d] * kNP + i) * kNP + a];
+  for (int d = 0; d < dim; ++d) {
+    const int nd = pick(d, n0, n1, n2);
+    for (int k = threadIdx.x; k < nd * nd; k += blockDim.x) {
+      int i = k / nd, a = k - i * nd;
+      sD[d * kNP * kNP + i * kNP + a] = src[((size_t)nd * kNP + i) * kNP + a];
     }
+  }
 }
 
-__global__ void __launch_bounds__(kTileNodes) k_volume(LevelArgs A, Params P, const double* __restrict__ q,
-                                                       const double* __restrict__ ust, double* __restrict__ trg,
-                                                       double* __restrict__ vol) {
-  extern __shared__ double smem[];
-  const ElemTile t = A.tiles[blockIdx.x];
-  const int n[3] = {t.n[0], t.n[1], t.n[2]};
-  const int nn = n[0] * n[1] * n[2];
-  const int T = t.count * nn;
-  const int dim = A.dim;
-  const Gas G = make_gas(P);
-  double* sD = smem;                          // 3 * kNP * kNP
-  double* sq = sD + 3 * kNP * kNP;            // 5 * T
-  double* sA = sq + 5 * T;                    // 15 * T: U(4) + Ja(9) | Ftilde(15)
-  double* sG = sA + 15 * T;                   // 12 * T
-  load_dtables(sD, c_Dhat, n, dim);
+// Stage the tile: conserved state (sq), primitives u,v,w,T (sA[0..3]) and the
+// nine metric components (sA[4..12]).
+DEV void stage_tile(const LevelArgs& A, const ElemTile& t, int nn, int T, const Gas& G, const double* __restrict__ q,
+                    double* sq, double* sA) {
   for (int i = threadIdx.x; i < T; i += blockDim.x) {
     int le = i / nn, node = i - le * nn;
     int e = A.tile_elems[t.first + le];
@@ -575,22 +590,43 @@ __global__ void __launch_bounds__(kTileNodes) k_volume(LevelArgs A, Params P, co
 #pragma unroll
     for (int c = 0; c < 9; ++c) sA[(4 + c) * T + i] = A.geo[c * A.nodes + gn];
   }
-  __syncthreads();
-  const int sd[3] = {1, n[0], n[0] * n[1]};
-  // ---- gradient ----
-  for (int i = threadIdx.x; i < T; i += blockDim.x) {
-    int le = i / nn, node = i - le * nn;
-    int e = A.tile_elems[t.first + le];
-    int idx[3] = {node % n[0], (node / n[0]) % n[1], node / (n[0] * n[1])};
-    double g[12];
+}
+
+// Volume part of the gradient at node i of the tile: sum_d D^d (Ja^d U).
+// AFFINE: the metrics are constant in the element, so Ja^d is factored out
+// of the contraction (same value, 4 instead of 15 FP64 operations per point).
+template <int DIM, bool AFFINE>
+DEV void gradient_volume(const double* sD, const double* sA, int T, int nn, int i, int n0, int n1, int n2,
+                         double* g) {
+  const int le = i / nn, node = i - le * nn;
+  const int idx0 = node % n0, idx1 = (node / n0) % n1, idx2 = node / (n0 * n1);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) g[k] = 0.0;
-    for (int d = 0; d < dim; ++d) {
-      const int id = idx[d];
-      const int base = le * nn + node - id * sd[d];
-      const double* Drow = sD + d * kNP * kNP + id * kNP;
-      for (int a = 0; a < n[d]; ++a) {
-        const int la = base + a * sd[d];
+  for (int k = 0; k < 12; ++k) g[k] = 0.0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const int id = pick(d, idx0, idx1, idx2), nd = pick(d, n0, n1, n2);
+    const int sd = (d == 0) ? 1 : (d == 1 ? n0 : n0 * n1);
+    const int base = le * nn + node - id * sd;
+    const double* Drow = sD + d * kNP * kNP + id * kNP;
+    if (AFFINE) {
+      double cu[4] = {0, 0, 0, 0};
+      for (int a = 0; a < nd; ++a) {
+        const int la = base + a * sd;
+        const double c = Drow[a];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) cu[v] += c * sA[v * T + la];
+      }
+      const double j0 = sA[(4 + d * 3 + 0) * T + i], j1 = sA[(4 + d * 3 + 1) * T + i],
+                   j2 = sA[(4 + d * 3 + 2) * T + i];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        g[v * 3 + 0] += j0 * cu[v];
+        g[v * 3 + 1] += j1 * cu[v];
+        g[v * 3 + 2] += j2 * cu[v];
+      }
+    } else {
+      for (int a = 0; a < nd; ++a) {
+        const int la = base + a * sd;
         const double c = Drow[a];
         const double j0 = c * sA[(4 + d * 3 + 0) * T + la];
         const double j1 = c * sA[(4 + d * 3 + 1) * T + la];
@@ -604,12 +640,96 @@ __global__ void __launch_bounds__(kTileNodes) k_volume(LevelArgs A, Params P, co
         }
       }
     }
-    // lifting of U* (outward metric already in fnS)
-    for (int f = 0; f < 2 * dim; ++f) {
+  }
+}
+
+// Nodal contravariant fluxes Ftilde^d = Ja^d . (F^a - F^v / Re) of node i,
+// written over its own sA slots (reads its own slots first).
+template <int DIM>
+DEV void nodal_fluxes(const double* sq, double* sA, const double* sG, int T, int i, const Gas& G) {
+  double qq[5], u[3], Ja[3 * DIM], gr[12];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) qq[v] = sq[v * T + i];
+  u[0] = sA[0 * T + i];
+  u[1] = sA[1 * T + i];
+  u[2] = sA[2 * T + i];
+  const double Tt = sA[3 * T + i];
+#pragma unroll
+  for (int c = 0; c < 3 * DIM; ++c) Ja[c] = sA[(4 + c) * T + i];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) gr[k] = sG[k * T + i];
+  const double p = Tt * qq[0] / G.gM2;
+  const double mu = mu_of_T(Tt, G);
+  double F[5 * DIM];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const double* nv = Ja + 3 * d;
+    const double un = u[0] * nv[0] + u[1] * nv[1] + u[2] * nv[2];
+    double fv[5];
+    visc_flux(u, mu, gr, nv, G, true, fv);
+    F[d * 5 + 0] = qq[0] * un;
+    F[d * 5 + 1] = qq[1] * un + p * nv[0] - G.invRe * fv[1];
+    F[d * 5 + 2] = qq[2] * un + p * nv[1] - G.invRe * fv[2];
+    F[d * 5 + 3] = qq[3] * un + p * nv[2] - G.invRe * fv[3];
+    F[d * 5 + 4] = (qq[4] + p) * un - G.invRe * fv[4];
+  }
+#pragma unroll
+  for (int k = 0; k < 5 * DIM; ++k) sA[k * T + i] = F[k];
+}
+
+// sum_d D^d Ftilde^d at node i
+template <int DIM>
+DEV void divergence(const double* sD, const double* sA, int T, int nn, int i, int n0, int n1, int n2, double* acc) {
+  const int le = i / nn, node = i - le * nn;
+  const int idx0 = node % n0, idx1 = (node / n0) % n1, idx2 = node / (n0 * n1);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) acc[v] = 0.0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const int id = pick(d, idx0, idx1, idx2), nd = pick(d, n0, n1, n2);
+    const int sd = (d == 0) ? 1 : (d == 1 ? n0 : n0 * n1);
+    const int base = le * nn + node - id * sd;
+    const double* Drow = sD + d * kNP * kNP + id * kNP;
+    for (int a = 0; a < nd; ++a) {
+      const int la = base + a * sd;
+      const double c = Drow[a];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) acc[v] += c * sA[(d * 5 + v) * T + la];
+    }
+  }
+}
+
+template <int DIM, bool AFFINE>
+__global__ void __launch_bounds__(kTileNodes) k_volume(LevelArgs A, Params P, const double* __restrict__ q,
+                                                       const double* __restrict__ ust, double* __restrict__ trg,
+                                                       double* __restrict__ vol) {
+  extern __shared__ double smem[];
+  const ElemTile t = A.tiles[blockIdx.x];
+  const int n0 = t.n[0], n1 = t.n[1], n2 = t.n[2];
+  const int nn = n0 * n1 * n2;
+  const int T = t.count * nn;
+  const Gas G = make_gas(P);
+  double* sD = smem;                          // 3 * kNP * kNP
+  double* sq = sD + 3 * kNP * kNP;            // 5 * T
+  double* sA = sq + 5 * T;                    // 15 * T: U(4) + Ja(9) | Ftilde(15)
+  double* sG = sA + 15 * T;                   // 12 * T
+  load_dtables(sD, c_Dhat, n0, n1, n2, DIM);
+  stage_tile(A, t, nn, T, G, q, sq, sA);
+  __syncthreads();
+  // ---- gradient: volume part + lifting of U*, times 1/J ----
+  for (int i = threadIdx.x; i < T; i += blockDim.x) {
+    double g[12];
+    gradient_volume<DIM, AFFINE>(sD, sA, T, nn, i, n0, n1, n2, g);
+    const int le = i / nn, node = i - le * nn;
+    const int e = A.tile_elems[t.first + le];
+    const int idx0 = node % n0, idx1 = (node / n0) % n1, idx2 = node / (n0 * n1);
+#pragma unroll
+    for (int f = 0; f < 2 * DIM; ++f) {
       int d, ta, tb, side;
       face_dirs(f, d, ta, tb, side);
-      const double lw = side ? c_tab.lpw[n[d]][idx[d]] : c_tab.lmw[n[d]][idx[d]];
-      const int64_t p = A.fo[e * 6 + f] + idx[tb] * n[ta] + idx[ta];
+      const int nd = pick(d, n0, n1, n2), id = pick(d, idx0, idx1, idx2);
+      const double lw = side ? c_tab.lpw[nd][id] : c_tab.lmw[nd][id];
+      const int64_t p = A.fo[e * 6 + f] + pick(tb, idx0, idx1, idx2) * pick(ta, n0, n1, n2) + pick(ta, idx0, idx1, idx2);
       const double m0 = lw * A.fnS[p], m1 = lw * A.fnS[A.fn + p], m2 = lw * A.fnS[2 * A.fn + p];
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
@@ -626,82 +746,46 @@ __global__ void __launch_bounds__(kTileNodes) k_volume(LevelArgs A, Params P, co
   __syncthreads();
   // ---- gradient face traces ----
   {
-    const int fsz[3] = {n[1] * n[2], n[0] * n[2], n[0] * n[1]};
     int FE = 0;
-    for (int f = 0; f < 2 * dim; ++f) FE += fsz[f >> 1];
+#pragma unroll
+    for (int f = 0; f < 2 * DIM; ++f) FE += face_size(f, n0, n1, n2);
     for (int i = threadIdx.x; i < t.count * FE; i += blockDim.x) {
       int le = i / FE, r = i - le * FE;
       int f = 0;
-      while (r >= fsz[f >> 1]) {
-        r -= fsz[f >> 1];
+      while (r >= face_size(f, n0, n1, n2)) {
+        r -= face_size(f, n0, n1, n2);
         ++f;
       }
       int d, ta, tb, side;
       face_dirs(f, d, ta, tb, side);
-      int ia = r % n[ta], ib = r / n[ta];
-      int idx[3];
-      idx[d] = 0;
-      idx[ta] = ia;
-      idx[tb] = ib;
-      int base = (idx[2] * n[1] + idx[1]) * n[0] + idx[0];
-      const double* lb = side ? c_tab.lp[n[d]] : c_tab.lm[n[d]];
+      const int nta = pick(ta, n0, n1, n2), nd = pick(d, n0, n1, n2);
+      int ia = r % nta, ib = r / nta;
+      int i0 = (d == 0) ? 0 : ia;
+      int i1 = (d == 1) ? 0 : (d == 0 ? ia : ib);
+      int i2 = (d == 2) ? 0 : ib;
+      int base = (i2 * n1 + i1) * n0 + i0;
+      int sdd = (d == 0) ? 1 : (d == 1 ? n0 : n0 * n1);
+      const double* lb = side ? c_tab.lp[nd] : c_tab.lm[nd];
       int e = A.tile_elems[t.first + le];
       int64_t p = A.fo[e * 6 + f] + r;
       const double* s0 = sG + le * nn + base;
+#pragma unroll
       for (int k = 0; k < 12; ++k) {
         double acc = 0.0;
-        for (int j = 0; j < n[d]; ++j) acc += lb[j] * s0[k * T + j * sd[d]];
+        for (int j = 0; j < nd; ++j) acc += lb[j] * s0[k * T + j * sdd];
         trg[k * A.fn + p] = acc;
       }
     }
   }
   // ---- nodal contravariant fluxes (own node only: no cross-node hazard) ----
-  for (int i = threadIdx.x; i < T; i += blockDim.x) {
-    double qq[5], u[3], Tt, Ja[9], gr[12];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) qq[v] = sq[v * T + i];
-    u[0] = sA[0 * T + i];
-    u[1] = sA[1 * T + i];
-    u[2] = sA[2 * T + i];
-    Tt = sA[3 * T + i];
-#pragma unroll
-    for (int c = 0; c < 9; ++c) Ja[c] = sA[(4 + c) * T + i];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) gr[k] = sG[k * T + i];
-    const double p = Tt * qq[0] / G.gM2;
-    const double mu = mu_of_T(Tt, G);
-    double F[15];
-    for (int d = 0; d < dim; ++d) {
-      const double* nv = Ja + 3 * d;
-      const double un = u[0] * nv[0] + u[1] * nv[1] + u[2] * nv[2];
-      double fv[5];
-      visc_flux(u, mu, gr, nv, G, true, fv);
-      F[d * 5 + 0] = qq[0] * un;
-      F[d * 5 + 1] = qq[1] * un + p * nv[0] - G.invRe * fv[1];
-      F[d * 5 + 2] = qq[2] * un + p * nv[1] - G.invRe * fv[2];
-      F[d * 5 + 3] = qq[3] * un + p * nv[2] - G.invRe * fv[3];
-      F[d * 5 + 4] = (qq[4] + p) * un - G.invRe * fv[4];
-    }
-    for (int k = 0; k < 5 * dim; ++k) sA[k * T + i] = F[k];
-  }
+  for (int i = threadIdx.x; i < T; i += blockDim.x) nodal_fluxes<DIM>(sq, sA, sG, T, i, G);
   __syncthreads();
   // ---- weak-form divergence ----
   for (int i = threadIdx.x; i < T; i += blockDim.x) {
-    int le = i / nn, node = i - le * nn;
-    int e = A.tile_elems[t.first + le];
-    int idx[3] = {node % n[0], (node / n[0]) % n[1], node / (n[0] * n[1])};
-    double acc[5] = {0, 0, 0, 0, 0};
-    for (int d = 0; d < dim; ++d) {
-      const int id = idx[d];
-      const int base = le * nn + node - id * sd[d];
-      const double* Drow = sD + d * kNP * kNP + id * kNP;
-      for (int a = 0; a < n[d]; ++a) {
-        const int la = base + a * sd[d];
-        const double c = Drow[a];
-#pragma unroll
-        for (int v = 0; v < 5; ++v) acc[v] += c * sA[(d * 5 + v) * T + la];
-      }
-    }
+    double acc[5];
+    divergence<DIM>(sD, sA, T, nn, i, n0, n1, n2, acc);
+    const int le = i / nn, node = i - le * nn;
+    const int e = A.tile_elems[t.first + le];
     double* ve = vol + (size_t)5 * A.off[e];
 #pragma unroll
     for (int v = 0; v < 5; ++v) ve[v * nn + node] = acc[v];
@@ -719,28 +803,31 @@ struct RKArgs {
   double* qupd;       // state updated in place
 };
 
+template <int DIM>
 __global__ void __launch_bounds__(kTileNodes) k_surface(LevelArgs A, const double* __restrict__ vol,
                                                         const double* __restrict__ fst, const double* __restrict__ s,
                                                         double* __restrict__ r, double* norm, RKArgs rk) {
   const ElemTile t = A.tiles[blockIdx.x];
-  const int n[3] = {t.n[0], t.n[1], t.n[2]};
-  const int nn = n[0] * n[1] * n[2];
+  const int n0 = t.n[0], n1 = t.n[1], n2 = t.n[2];
+  const int nn = n0 * n1 * n2;
   const int T = t.count * nn;
   double lmax = 0.0;
-  double dt = (rk.stage >= 0) ? *rk.dt : 0.0;
+  const double dt = (rk.stage >= 0) ? *rk.dt : 0.0;
   for (int i = threadIdx.x; i < T; i += blockDim.x) {
-    int le = i / nn, node = i - le * nn;
-    int e = A.tile_elems[t.first + le];
-    int idx[3] = {node % n[0], (node / n[0]) % n[1], node / (n[0] * n[1])};
+    const int le = i / nn, node = i - le * nn;
+    const int e = A.tile_elems[t.first + le];
+    const int idx0 = node % n0, idx1 = (node / n0) % n1, idx2 = node / (n0 * n1);
     const size_t base = (size_t)5 * A.off[e] + node;
     double acc[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) acc[v] = vol[base + v * nn];
-    for (int f = 0; f < 2 * A.dim; ++f) {
+#pragma unroll
+    for (int f = 0; f < 2 * DIM; ++f) {
       int d, ta, tb, side;
       face_dirs(f, d, ta, tb, side);
-      const double lw = side ? c_tab.lpw[n[d]][idx[d]] : c_tab.lmw[n[d]][idx[d]];
-      const int64_t p = A.fo[e * 6 + f] + idx[tb] * n[ta] + idx[ta];
+      const int nd = pick(d, n0, n1, n2), id = pick(d, idx0, idx1, idx2);
+      const double lw = side ? c_tab.lpw[nd][id] : c_tab.lmw[nd][id];
+      const int64_t p = A.fo[e * 6 + f] + pick(tb, idx0, idx1, idx2) * pick(ta, n0, n1, n2) + pick(ta, idx0, idx1, idx2);
 #pragma unroll
       for (int v = 0; v < 5; ++v) acc[v] += lw * fst[v * A.fn + p];
     }
@@ -774,119 +861,40 @@ struct TauArgs {
   int dir, slot;
 };
 
+template <int DIM, bool AFFINE>
 __global__ void __launch_bounds__(kTileNodes) k_isolated(LevelArgs A, Params P, const double* __restrict__ q,
                                                          const double* __restrict__ s, double* __restrict__ r,
                                                          TauArgs tau) {
   extern __shared__ double smem[];
   const ElemTile t = A.tiles[blockIdx.x];
-  const int n[3] = {t.n[0], t.n[1], t.n[2]};
-  const int nn = n[0] * n[1] * n[2];
+  const int n0 = t.n[0], n1 = t.n[1], n2 = t.n[2];
+  const int nn = n0 * n1 * n2;
   const int T = t.count * nn;
-  const int dim = A.dim;
   const Gas G = make_gas(P);
   double* sD = smem;
   double* sq = sD + 3 * kNP * kNP;
   double* sA = sq + 5 * T;
   double* sG = sA + 15 * T;
-  load_dtables(sD, c_D, n, dim);
-  for (int i = threadIdx.x; i < T; i += blockDim.x) {
-    int le = i / nn, node = i - le * nn;
-    int e = A.tile_elems[t.first + le];
-    const int64_t gn = A.off[e] + node;
-    const double* qe = q + (size_t)5 * A.off[e];
-    double qq[5];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      qq[v] = qe[v * nn + node];
-      sq[v * T + i] = qq[v];
-    }
-    double ir, u[3], p, Tt;
-    to_prim(qq, G, ir, u, p, Tt);
-    sA[0 * T + i] = u[0];
-    sA[1 * T + i] = u[1];
-    sA[2 * T + i] = u[2];
-    sA[3 * T + i] = Tt;
-#pragma unroll
-    for (int c = 0; c < 9; ++c) sA[(4 + c) * T + i] = A.geo[c * A.nodes + gn];
-  }
+  load_dtables(sD, c_D, n0, n1, n2, DIM);
+  stage_tile(A, t, nn, T, G, q, sq, sA);
   __syncthreads();
-  const int sd[3] = {1, n[0], n[0] * n[1]};
   for (int i = threadIdx.x; i < T; i += blockDim.x) {
-    int le = i / nn, node = i - le * nn;
-    int e = A.tile_elems[t.first + le];
-    int idx[3] = {node % n[0], (node / n[0]) % n[1], node / (n[0] * n[1])};
     double g[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) g[k] = 0.0;
-    for (int d = 0; d < dim; ++d) {
-      const int id = idx[d];
-      const int base = le * nn + node - id * sd[d];
-      const double* Drow = sD + d * kNP * kNP + id * kNP;
-      for (int a = 0; a < n[d]; ++a) {
-        const int la = base + a * sd[d];
-        const double c = Drow[a];
-        const double j0 = c * sA[(4 + d * 3 + 0) * T + la];
-        const double j1 = c * sA[(4 + d * 3 + 1) * T + la];
-        const double j2 = c * sA[(4 + d * 3 + 2) * T + la];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          const double uv = sA[v * T + la];
-          g[v * 3 + 0] += j0 * uv;
-          g[v * 3 + 1] += j1 * uv;
-          g[v * 3 + 2] += j2 * uv;
-        }
-      }
-    }
+    gradient_volume<DIM, AFFINE>(sD, sA, T, nn, i, n0, n1, n2, g);
+    const int le = i / nn, node = i - le * nn;
+    const int e = A.tile_elems[t.first + le];
     const double iJ = A.geo[9 * A.nodes + A.off[e] + node];
 #pragma unroll
     for (int k = 0; k < 12; ++k) sG[k * T + i] = g[k] * iJ;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < T; i += blockDim.x) {
-    double qq[5], u[3], Tt, Ja[9], gr[12];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) qq[v] = sq[v * T + i];
-    u[0] = sA[0 * T + i];
-    u[1] = sA[1 * T + i];
-    u[2] = sA[2 * T + i];
-    Tt = sA[3 * T + i];
-#pragma unroll
-    for (int c = 0; c < 9; ++c) Ja[c] = sA[(4 + c) * T + i];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) gr[k] = sG[k * T + i];
-    const double p = Tt * qq[0] / G.gM2;
-    const double mu = mu_of_T(Tt, G);
-    double F[15];
-    for (int d = 0; d < dim; ++d) {
-      const double* nv = Ja + 3 * d;
-      const double un = u[0] * nv[0] + u[1] * nv[1] + u[2] * nv[2];
-      double fv[5];
-      visc_flux(u, mu, gr, nv, G, true, fv);
-      F[d * 5 + 0] = qq[0] * un;
-      F[d * 5 + 1] = qq[1] * un + p * nv[0] - G.invRe * fv[1];
-      F[d * 5 + 2] = qq[2] * un + p * nv[1] - G.invRe * fv[2];
-      F[d * 5 + 3] = qq[3] * un + p * nv[2] - G.invRe * fv[3];
-      F[d * 5 + 4] = (qq[4] + p) * un - G.invRe * fv[4];
-    }
-    for (int k = 0; k < 5 * dim; ++k) sA[k * T + i] = F[k];
-  }
+  for (int i = threadIdx.x; i < T; i += blockDim.x) nodal_fluxes<DIM>(sq, sA, sG, T, i, G);
   __syncthreads();
   for (int i = threadIdx.x; i < T; i += blockDim.x) {
-    int le = i / nn, node = i - le * nn;
-    int e = A.tile_elems[t.first + le];
-    int idx[3] = {node % n[0], (node / n[0]) % n[1], node / (n[0] * n[1])};
-    double acc[5] = {0, 0, 0, 0, 0};
-    for (int d = 0; d < dim; ++d) {
-      const int id = idx[d];
-      const int base = le * nn + node - id * sd[d];
-      const double* Drow = sD + d * kNP * kNP + id * kNP;
-      for (int a = 0; a < n[d]; ++a) {
-        const int la = base + a * sd[d];
-        const double c = Drow[a];
-#pragma unroll
-        for (int v = 0; v < 5; ++v) acc[v] += c * sA[(d * 5 + v) * T + la];
-      }
-    }
+    double acc[5];
+    divergence<DIM>(sD, sA, T, nn, i, n0, n1, n2, acc);
+    const int le = i / nn, node = i - le * nn;
+    const int e = A.tile_elems[t.first + le];
     const double iJ = A.geo[9 * A.nodes + A.off[e] + node];
     const size_t base = (size_t)5 * A.off[e] + node;
     double tmax = 0.0;
@@ -908,10 +916,11 @@ __global__ void __launch_bounds__(kTileNodes) k_isolated(LevelArgs A, Params P, 
 // ---------------------------------------------------------------------------
 // k_cfl: global minimum of the explicit step
 // ---------------------------------------------------------------------------
+template <int DIM>
 __global__ void __launch_bounds__(kTileNodes) k_cfl(LevelArgs A, Params P, const double* __restrict__ q, double* dtmin) {
   const ElemTile t = A.tiles[blockIdx.x];
-  const int n[3] = {t.n[0], t.n[1], t.n[2]};
-  const int nn = n[0] * n[1] * n[2];
+  const int n0 = t.n[0], n1 = t.n[1], n2 = t.n[2];
+  const int nn = n0 * n1 * n2;
   const int T = t.count * nn;
   const Gas G = make_gas(P);
   double best = 1e300;
@@ -929,8 +938,9 @@ __global__ void __launch_bounds__(kTileNodes) k_cfl(LevelArgs A, Params P, const
     const double vel = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
     const double nu = mu_of_T(Tt, G) * ir * G.invRe;
     const double iJ = A.geo[9 * A.nodes + gn];
-    for (int d = 0; d < A.dim; ++d) {
-      const int N = n[d] - 1;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const int N = pick(d, n0, n1, n2) - 1;
       if (N <= 0) continue;
       double j0 = A.geo[(3 * d + 0) * A.nodes + gn], j1 = A.geo[(3 * d + 1) * A.nodes + gn],
              j2 = A.geo[(3 * d + 2) * A.nodes + gn];
@@ -945,12 +955,27 @@ __global__ void __launch_bounds__(kTileNodes) k_cfl(LevelArgs A, Params P, const
 }
 
 // ---------------------------------------------------------------------------
-// transfers between order maps: out_e = (T2 x T1 x T0) (in_e - sub_e)
+// transfers between order maps: out_e = (T2 x T1 x T0) (in_e - sub_e),
+// sum-factorised through shared memory (one direction per pass, one
+// variable at a time so the buffers stay within 2 x the largest slab)
 // ---------------------------------------------------------------------------
-__global__ void k_transfer(int dim, const int32_t* __restrict__ nf, const int32_t* __restrict__ offf,
-                           const int32_t* __restrict__ nt, const int32_t* __restrict__ offt, int nvar,
-                           const double* __restrict__ in, const double* __restrict__ sub, double* __restrict__ out,
-                           int accumulate) {
+constexpr int kTransferThreads = 128;
+// largest per-variable slab: 3D elements have <= 729 nodes and n <= 13 per
+// direction, so f1*f2 <= 364 and t0 <= 13 bound the x-pass intermediate
+constexpr int kTransferMaxSlab = 4800;
+
+DEV int transfer_slab(int f0, int f1, int f2, int t0, int t1, int t2) {
+  return max(max(f0 * f1 * f2, t0 * t1 * t2), max(f2 * f1 * t0, f2 * t1 * t0));
+}
+
+__global__ void __launch_bounds__(kTransferThreads) k_transfer(const int32_t* __restrict__ nf,
+                                                               const int32_t* __restrict__ offf,
+                                                               const int32_t* __restrict__ nt,
+                                                               const int32_t* __restrict__ offt, int nvar,
+                                                               const double* __restrict__ in,
+                                                               const double* __restrict__ sub,
+                                                               double* __restrict__ out, int accumulate) {
+  extern __shared__ double sbuf[];
   const int e = blockIdx.x;
   const int f0 = nf[e * 3], f1 = nf[e * 3 + 1], f2 = nf[e * 3 + 2];
   const int t0 = nt[e * 3], t1 = nt[e * 3 + 1], t2 = nt[e * 3 + 2];
@@ -958,31 +983,43 @@ __global__ void k_transfer(int dim, const int32_t* __restrict__ nf, const int32_
   const double* T0 = c_T + ((size_t)f0 * kNP + t0) * kNP * kNP;
   const double* T1 = c_T + ((size_t)f1 * kNP + t1) * kNP * kNP;
   const double* T2 = c_T + ((size_t)f2 * kNP + t2) * kNP * kNP;
-  const double* ie = in + (size_t)nvar * offf[e];
-  const double* se = sub ? sub + (size_t)nvar * offf[e] : nullptr;
-  double* oe = out + (size_t)nvar * offt[e];
-  for (int i = threadIdx.x; i < nnt * nvar; i += blockDim.x) {
-    int v = i / nnt, j = i - v * nnt;
-    int j0 = j % t0, j1 = (j / t0) % t1, j2 = j / (t0 * t1);
-    double acc = 0.0;
-    for (int k2 = 0; k2 < f2; ++k2) {
-      double w2 = T2[j2 * f2 + k2];
-      if (w2 == 0.0) continue;
-      for (int k1 = 0; k1 < f1; ++k1) {
-        double w21 = w2 * T1[j1 * f1 + k1];
-        if (w21 == 0.0) continue;
-        for (int k0 = 0; k0 < f0; ++k0) {
-          int k = (k2 * f1 + k1) * f0 + k0;
-          double x = ie[v * nnf + k];
-          if (se) x -= se[v * nnf + k];
-          acc += w21 * T0[j0 * f0 + k0] * x;
-        }
-      }
+  const int maxn = transfer_slab(f0, f1, f2, t0, t1, t2);
+  double* bA = sbuf;
+  double* bB = sbuf + maxn;
+  const int n1x = f2 * f1 * t0, n2y = f2 * t1 * t0;
+  for (int v = 0; v < nvar; ++v) {
+    const double* ie = in + (size_t)nvar * offf[e] + (size_t)v * nnf;
+    const double* se = sub ? sub + (size_t)nvar * offf[e] + (size_t)v * nnf : nullptr;
+    double* oe = out + (size_t)nvar * offt[e] + (size_t)v * nnt;
+    for (int i = threadIdx.x; i < nnf; i += blockDim.x) bA[i] = se ? ie[i] - se[i] : ie[i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < n1x; i += blockDim.x) {  // x pass: [k2][k1][j0]
+      int j0 = i % t0, k12 = i / t0;
+      const double* src = bA + k12 * f0;
+      double acc = 0.0;
+      for (int k0 = 0; k0 < f0; ++k0) acc += T0[j0 * f0 + k0] * src[k0];
+      bB[i] = acc;
     }
-    if (accumulate)
-      oe[v * nnt + j] += acc;
-    else
-      oe[v * nnt + j] = acc;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n2y; i += blockDim.x) {  // y pass: [k2][j1][j0]
+      int j0 = i % t0, j1 = (i / t0) % t1, k2 = i / (t0 * t1);
+      const double* src = bB + k2 * f1 * t0 + j0;
+      double acc = 0.0;
+      for (int k1 = 0; k1 < f1; ++k1) acc += T1[j1 * f1 + k1] * src[k1 * t0];
+      bA[i] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nnt; i += blockDim.x) {  // z pass: [j2][j1][j0]
+      int j01 = i % (t0 * t1), j2 = i / (t0 * t1);
+      const double* src = bA + j01;
+      double acc = 0.0;
+      for (int k2 = 0; k2 < f2; ++k2) acc += T2[j2 * f2 + k2] * src[k2 * t1 * t0];
+      if (accumulate)
+        oe[i] += acc;
+      else
+        oe[i] = acc;
+    }
+    __syncthreads();
   }
 }
 
@@ -1005,16 +1042,26 @@ static size_t vol_smem(const Level* L) {
   return (size_t)(3 * kNP * kNP + 32 * L->tile_smem_nodes) * sizeof(double);
 }
 
+template <int DIM, bool AFF>
+static int set_attrs() {
+  const int big = (int)((3 * kNP * kNP + 32 * kMaxElemNodes) * sizeof(double));
+  DG_CUDA_TRY(cudaFuncSetAttribute(k_volume<DIM, AFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  DG_CUDA_TRY(cudaFuncSetAttribute(k_isolated<DIM, AFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  return DG_OK;
+}
+
 static int configure_smem() {
   static int done_dev = -1;
   int dev = 0;
   DG_CUDA_TRY(cudaGetDevice(&dev));
   if (done_dev == dev) return DG_OK;
-  const int big = (int)((3 * kNP * kNP + 32 * kMaxElemNodes) * sizeof(double));
-  DG_CUDA_TRY(cudaFuncSetAttribute(k_volume, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  DG_CUDA_TRY(cudaFuncSetAttribute(k_isolated, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  DG_CUDA_TRY(cudaFuncSetAttribute(k_trace_q, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)(5 * kMaxElemNodes * sizeof(double))));
+  int rc;
+  if ((rc = set_attrs<2, false>()) != DG_OK) return rc;
+  if ((rc = set_attrs<2, true>()) != DG_OK) return rc;
+  if ((rc = set_attrs<3, false>()) != DG_OK) return rc;
+  if ((rc = set_attrs<3, true>()) != DG_OK) return rc;
+  DG_CUDA_TRY(cudaFuncSetAttribute(k_transfer, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(2 * kTransferMaxSlab * sizeof(double))));
   done_dev = dev;
   return DG_OK;
 }
@@ -1053,6 +1100,64 @@ int read_scalar(const double* d, double* h, cudaStream_t st) {
   return DG_OK;
 }
 
+// ---- per-kernel launch helpers (dimension / affine dispatch) ----
+static void launch_trace(const Level* L, const LevelArgs& A, const double* q, cudaStream_t st) {
+  ++g_launches;
+  const size_t sm = 5 * L->tile_smem_nodes * sizeof(double);
+  if (L->dim == 2)
+    k_trace_q<2><<<L->n_tiles, kTileNodes, sm, st>>>(A, q, L->d_trq);
+  else
+    k_trace_q<3><<<L->n_tiles, kTileNodes, sm, st>>>(A, q, L->d_trq);
+}
+static void launch_volume(const Level* L, const LevelArgs& A, const Params& P, const double* q, cudaStream_t st) {
+  ++g_launches;
+  const size_t sm = vol_smem(L);
+  if (L->dim == 2) {
+    if (L->affine)
+      k_volume<2, true><<<L->n_tiles, kTileNodes, sm, st>>>(A, P, q, L->d_ust, L->d_trg, L->d_vol);
+    else
+      k_volume<2, false><<<L->n_tiles, kTileNodes, sm, st>>>(A, P, q, L->d_ust, L->d_trg, L->d_vol);
+  } else {
+    if (L->affine)
+      k_volume<3, true><<<L->n_tiles, kTileNodes, sm, st>>>(A, P, q, L->d_ust, L->d_trg, L->d_vol);
+    else
+      k_volume<3, false><<<L->n_tiles, kTileNodes, sm, st>>>(A, P, q, L->d_ust, L->d_trg, L->d_vol);
+  }
+}
+template <typename TA>
+static void launch_isolated(const Level* L, const LevelArgs& A, const Params& P, const double* q, const double* s,
+                            double* r, const TA& ta, cudaStream_t st) {
+  ++g_launches;
+  const size_t sm = vol_smem(L);
+  if (L->dim == 2) {
+    if (L->affine)
+      k_isolated<2, true><<<L->n_tiles, kTileNodes, sm, st>>>(A, P, q, s, r, ta);
+    else
+      k_isolated<2, false><<<L->n_tiles, kTileNodes, sm, st>>>(A, P, q, s, r, ta);
+  } else {
+    if (L->affine)
+      k_isolated<3, true><<<L->n_tiles, kTileNodes, sm, st>>>(A, P, q, s, r, ta);
+    else
+      k_isolated<3, false><<<L->n_tiles, kTileNodes, sm, st>>>(A, P, q, s, r, ta);
+  }
+}
+static void launch_surface(const Level* L, const LevelArgs& A, const double* s, double* r, double* norm,
+                           const RKArgs& rk, cudaStream_t st) {
+  ++g_launches;
+  if (L->dim == 2)
+    k_surface<2><<<L->n_tiles, kTileNodes, 0, st>>>(A, L->d_vol, L->d_fst, s, r, norm, rk);
+  else
+    k_surface<3><<<L->n_tiles, kTileNodes, 0, st>>>(A, L->d_vol, L->d_fst, s, r, norm, rk);
+}
+static void launch_mortar(int pass, const Level* L, const LevelArgs& A, const MortarArgs& MA, const Params& P,
+                          cudaStream_t st) {
+  ++g_launches;
+  if (pass == 1)
+    k_mortar<1><<<L->n_mtiles, kMortarTile, 0, st>>>(A, MA, P, L->d_trq, nullptr, L->d_ust);
+  else
+    k_mortar<2><<<L->n_mtiles, kMortarTile, 0, st>>>(A, MA, P, L->d_trq, L->d_trg, L->d_fst);
+}
+
 int residual(const dg_mesh* m, Level* L, const double* q, const double* s, double* r, bool isolated,
              cudaStream_t st, double* d_norm, int rk_stage, double* rk_g, const double* d_dt) {
   int rc = configure_smem();
@@ -1060,20 +1165,15 @@ int residual(const dg_mesh* m, Level* L, const double* q, const double* s, doubl
   LevelArgs A = largs(L);
   if (isolated) {
     TauArgs ta{nullptr, nullptr, nullptr, 0, 0};
-    ++g_launches;
-    k_isolated<<<L->n_tiles, kTileNodes, vol_smem(L), st>>>(A, m->prm, q, s, r, ta);
+    launch_isolated(L, A, m->prm, q, s, r, ta, st);
     DG_CUDA_TRY(cudaGetLastError());
     return DG_OK;
   }
   MortarArgs MA = margs(L);
-  ++g_launches;
-  k_trace_q<<<L->n_tiles, kTileNodes, 5 * L->tile_smem_nodes * sizeof(double), st>>>(A, q, L->d_trq);
-  ++g_launches;
-  k_mortar<1><<<L->n_mtiles, kMortarTile, 0, st>>>(A, MA, m->prm, L->d_trq, nullptr, L->d_ust);
-  ++g_launches;
-  k_volume<<<L->n_tiles, kTileNodes, vol_smem(L), st>>>(A, m->prm, q, L->d_ust, L->d_trg, L->d_vol);
-  ++g_launches;
-  k_mortar<2><<<L->n_mtiles, kMortarTile, 0, st>>>(A, MA, m->prm, L->d_trq, L->d_trg, L->d_fst);
+  launch_trace(L, A, q, st);
+  launch_mortar(1, L, A, MA, m->prm, st);
+  launch_volume(L, A, m->prm, q, st);
+  launch_mortar(2, L, A, MA, m->prm, st);
   RKArgs rk;
   rk.stage = rk_stage;
   rk.a = (rk_stage == 1) ? -5.0 / 9.0 : (rk_stage == 2 ? -153.0 / 128.0 : 0.0);
@@ -1081,21 +1181,21 @@ int residual(const dg_mesh* m, Level* L, const double* q, const double* s, doubl
   rk.g = rk_g;
   rk.dt = d_dt;
   rk.qupd = const_cast<double*>(q);
-  ++g_launches;
-  k_surface<<<L->n_tiles, kTileNodes, 0, st>>>(A, L->d_vol, L->d_fst, s, r, d_norm, rk);
+  launch_surface(L, A, s, r, d_norm, rk, st);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
 }
 
 int profile_residual(const dg_mesh* m, Level* L, const double* q, const double* s, double* r, int iters,
                      double* ms_out, cudaStream_t st) {
-  int rc = configure_smem();
+  // One full evaluation fills every intermediate buffer; then each stage is
+  // launched `iters` times back to back between two events on `st` (each
+  // stage rewrites only its own outputs, so repeats are idempotent) and the
+  // mean duration per launch is reported.
+  int rc = residual(m, L, q, s, r, false, st, nullptr, -1, nullptr, nullptr);
   if (rc != DG_OK) return rc;
   LevelArgs A = largs(L);
   MortarArgs MA = margs(L);
-  cudaEvent_t ev[7];
-  for (int k = 0; k < 7; ++k) DG_CUDA_TRY(cudaEventCreate(&ev[k]));
-  double acc[6] = {0, 0, 0, 0, 0, 0};
   RKArgs rk;
   rk.stage = -1;
   rk.a = rk.b = 0.0;
@@ -1103,36 +1203,30 @@ int profile_residual(const dg_mesh* m, Level* L, const double* q, const double* 
   rk.dt = nullptr;
   rk.qupd = nullptr;
   TauArgs ta{nullptr, nullptr, nullptr, 0, 0};
-  for (int it = 0; it < iters; ++it) {
-    cudaEventRecord(ev[0], st);
-    ++g_launches;
-    k_trace_q<<<L->n_tiles, kTileNodes, 5 * L->tile_smem_nodes * sizeof(double), st>>>(A, q, L->d_trq);
-    cudaEventRecord(ev[1], st);
-    ++g_launches;
-    k_mortar<1><<<L->n_mtiles, kMortarTile, 0, st>>>(A, MA, m->prm, L->d_trq, nullptr, L->d_ust);
-    cudaEventRecord(ev[2], st);
-    ++g_launches;
-    k_volume<<<L->n_tiles, kTileNodes, vol_smem(L), st>>>(A, m->prm, q, L->d_ust, L->d_trg, L->d_vol);
-    cudaEventRecord(ev[3], st);
-    ++g_launches;
-    k_mortar<2><<<L->n_mtiles, kMortarTile, 0, st>>>(A, MA, m->prm, L->d_trq, L->d_trg, L->d_fst);
-    cudaEventRecord(ev[4], st);
-    ++g_launches;
-    k_surface<<<L->n_tiles, kTileNodes, 0, st>>>(A, L->d_vol, L->d_fst, s, r, nullptr, rk);
-    cudaEventRecord(ev[5], st);
-    ++g_launches;
-    k_isolated<<<L->n_tiles, kTileNodes, vol_smem(L), st>>>(A, m->prm, q, s, r, ta);
-    cudaEventRecord(ev[6], st);
-    DG_CUDA_TRY(cudaEventSynchronize(ev[6]));
-    for (int k = 0; k < 6; ++k) {
-      float ms = 0.f;
-      DG_CUDA_TRY(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
-      acc[k] += ms;
+  cudaEvent_t e0, e1;
+  DG_CUDA_TRY(cudaEventCreate(&e0));
+  DG_CUDA_TRY(cudaEventCreate(&e1));
+  for (int k = 0; k < 6; ++k) {
+    DG_CUDA_TRY(cudaEventRecord(e0, st));
+    for (int it = 0; it < iters; ++it) {
+      switch (k) {
+        case 0: launch_trace(L, A, q, st); break;
+        case 1: launch_mortar(1, L, A, MA, m->prm, st); break;
+        case 2: launch_volume(L, A, m->prm, q, st); break;
+        case 3: launch_mortar(2, L, A, MA, m->prm, st); break;
+        case 4: launch_surface(L, A, s, r, nullptr, rk, st); break;
+        default: launch_isolated(L, A, m->prm, q, s, r, ta, st); break;
+      }
     }
+    DG_CUDA_TRY(cudaEventRecord(e1, st));
+    DG_CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    DG_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    ms_out[k] = ms / std::max(1, iters);
   }
   DG_CUDA_TRY(cudaGetLastError());
-  for (int k = 0; k < 7; ++k) cudaEventDestroy(ev[k]);
-  for (int k = 0; k < 6; ++k) ms_out[k] = acc[k] / std::max(1, iters);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   return DG_OK;
 }
 
@@ -1140,7 +1234,10 @@ int cfl_dt(const dg_mesh* m, Level* L, const double* q, double* d_dt, cudaStream
   int rc = reset_min(d_dt, st);
   if (rc != DG_OK) return rc;
   ++g_launches;
-  k_cfl<<<L->n_tiles, kTileNodes, 0, st>>>(largs(L), m->prm, q, d_dt);
+  if (L->dim == 2)
+    k_cfl<2><<<L->n_tiles, kTileNodes, 0, st>>>(largs(L), m->prm, q, d_dt);
+  else
+    k_cfl<3><<<L->n_tiles, kTileNodes, 0, st>>>(largs(L), m->prm, q, d_dt);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
 }
@@ -1148,9 +1245,25 @@ int cfl_dt(const dg_mesh* m, Level* L, const double* q, double* d_dt, cudaStream
 int transfer(const dg_mesh* m, const Level* from, const Level* to, int nvar, const double* in, double* out,
              cudaStream_t st, const double* sub, bool accumulate) {
   (void)m;
+  int rc = configure_smem();
+  if (rc != DG_OK) return rc;
+  // shared memory: two slabs of the largest per-variable intermediate
+  size_t slab = 0;
+  for (int e = 0; e < from->K; ++e) {
+    const int* f = &from->nvec_host[e * 3];
+    const int* t = &to->nvec_host[e * 3];
+    size_t a = std::max((size_t)f[0] * f[1] * f[2], (size_t)t[0] * t[1] * t[2]);
+    size_t b = std::max((size_t)f[2] * f[1] * t[0], (size_t)f[2] * t[1] * t[0]);
+    slab = std::max(slab, std::max(a, b));
+  }
+  if (slab > (size_t)kTransferMaxSlab) {
+    set_error("transfer: element too large for the shared-memory slab");
+    return DG_EINVAL;
+  }
   ++g_launches;
-  k_transfer<<<from->K, 128, 0, st>>>(from->dim, from->d_n, from->d_off, to->d_n, to->d_off, nvar, in, sub, out,
-                                      accumulate ? 1 : 0);
+  k_transfer<<<from->K, kTransferThreads, 2 * slab * sizeof(double), st>>>(from->d_n, from->d_off, to->d_n,
+                                                                          to->d_off, nvar, in, sub, out,
+                                                                          accumulate ? 1 : 0);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
 }
@@ -1169,8 +1282,7 @@ int tau_accumulate(const dg_mesh* m, Level* L, const double* q, const double* s,
     return tau_reduce(L, L->d_R, rho, dir, slot, fine_orders_dev, d_tau, st);
   }
   TauArgs ta{rho, d_tau, fine_orders_dev, dir, slot};
-  ++g_launches;
-  k_isolated<<<L->n_tiles, kTileNodes, vol_smem(L), st>>>(largs(L), m->prm, q, s, nullptr, ta);
+  launch_isolated(L, largs(L), m->prm, q, s, nullptr, ta, st);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
 }

@@ -243,10 +243,19 @@ inline void cross(const double* a, const double* b, double* c) {
 }
 
 // Ja[node][i][c] and J[node] for one element with node counts n[3]
-void element_geometry(const MapEval& ME, const double* X, const int n[3], int dim, std::vector<double>& Ja,
+void element_geometry(const MapEval& ME, const double* Xabs, const int n[3], int dim, std::vector<double>& Ja,
                       std::vector<double>& J) {
   const Tables1D& T = tables();
   int nn = n[0] * n[1] * n[2];
+  // Work with coordinates relative to the element's first mapping node: the
+  // metrics are unchanged (the curl of the discrete gradient of a constant
+  // vanishes when M <= N) and the curl-form products no longer cancel large
+  // absolute coordinates.
+  const int npe = (dim == 3) ? (ME.M + 1) * (ME.M + 1) * (ME.M + 1) : (ME.M + 1) * (ME.M + 1);
+  std::vector<double> Xrel((size_t)npe * 3);
+  for (int a = 0; a < npe; ++a)
+    for (int c = 0; c < 3; ++c) Xrel[a * 3 + c] = Xabs[a * 3 + c] - Xabs[c];
+  const double* X = Xrel.data();
   Ja.assign((size_t)nn * 9, 0.0);
   J.assign(nn, 0.0);
   std::vector<double> xs((size_t)nn * 3), dxs((size_t)nn * 9);
@@ -370,6 +379,7 @@ int build_level(const dg_mesh* m, const std::vector<int32_t>& orders, Level* L) 
   int npe = (dim == 3) ? Mp * Mp * Mp : Mp * Mp;
   std::vector<double> geo((size_t)10 * L->nodes);
   std::vector<std::vector<double>> elemJa(K);
+  bool affine = true;
   for (int e = 0; e < K; ++e) {
     std::vector<double> Ja, J;
     int n[3] = {nvec[e * 3], nvec[e * 3 + 1], nvec[e * 3 + 2]};
@@ -383,8 +393,16 @@ int build_level(const dg_mesh* m, const std::vector<int32_t>& orders, Level* L) 
       for (int c = 0; c < 9; ++c) geo[(size_t)c * L->nodes + L->off[e] + nd] = Ja[nd * 9 + c];
       geo[(size_t)9 * L->nodes + L->off[e] + nd] = 1.0 / J[nd];
     }
+    // affine element: every metric component equal to its value at node 0
+    double scale = 0.0, dev = 0.0;
+    for (int c = 0; c < 9; ++c) scale = std::max(scale, std::fabs(Ja[c]));
+    for (int nd = 1; nd < nn; ++nd)
+      for (int c = 0; c < 9; ++c) dev = std::max(dev, std::fabs(Ja[nd * 9 + c] - Ja[c]));
+    if (dev > 1e-13 * scale) affine = false;
     elemJa[e] = std::move(Ja);
   }
+  L->affine = affine;
+  L->nvec_host = nvec;
   // ---- element-face offsets and own outward face metrics ----
   std::vector<int32_t> fo((size_t)K * 6, 0);
   int64_t acc = 0;

@@ -132,10 +132,13 @@ _PERMS = [(0, 1, 2), (1, 2, 0), (2, 0, 1), (0, 2, 1), (2, 1, 0), (1, 0, 2)]
 
 def rotate_elements(mesh, seed, frac=0.5):
     """Re-label the local reference axes of a random subset of the elements of
-    a 3D box mesh (axis permutations and reversals), keeping the geometry.
-    Face tables and orientation codes are rebuilt from the vertex positions, so
-    neighbouring elements see each other through non-trivial orientations."""
-    assert mesh["dim"] == 3 and mesh["M"] == 1
+    a 3D mesh (axis permutations and reversals), keeping the geometry.  The
+    face table and its orientation codes are rebuilt from the geometry, so
+    neighbouring elements see each other through non-trivial orientations;
+    boundary faces keep their tags."""
+    assert mesh["dim"] == 3
+    M = mesh["M"]
+    Mp = M + 1
     rng = np.random.default_rng(seed)
     K = mesh["K"]
     xmap = mesh["xmap"].copy()
@@ -144,100 +147,181 @@ def rotate_elements(mesh, seed, frac=0.5):
             continue
         perm = _PERMS[rng.integers(len(_PERMS))]
         flips = rng.integers(0, 2, size=3)
-        old = xmap[e].reshape(2, 2, 2, 3)  # [c][b][a]
+        old = xmap[e].reshape(Mp, Mp, Mp, 3)  # [c][b][a]
         new = np.empty_like(old)
-        for c in range(2):
-            for b in range(2):
-                for a in range(2):
-                    loc = [a, b, c]          # new local index along new axes
+        for c in range(Mp):
+            for b in range(Mp):
+                for a in range(Mp):
+                    loc = [a, b, c]          # index along the new axes
                     src = [0, 0, 0]
                     for nd in range(3):      # new axis nd is old axis perm[nd]
                         v = loc[nd]
-                        src[perm[nd]] = 1 - v if flips[nd] else v
+                        src[perm[nd]] = M - v if flips[nd] else v
                     new[c, b, a] = old[src[2], src[1], src[0]]
-        # keep a right-handed frame: odd permutations with an even number of
-        # flips (or vice versa) would invert the element, so flip axis 0 once more
-        det = np.linalg.det(np.stack([new[0, 0, 1] - new[0, 0, 0], new[0, 1, 0] - new[0, 0, 0],
-                                      new[1, 0, 0] - new[0, 0, 0]]))
+        # keep a right-handed frame: reverse the first axis if the relabelling
+        # inverted the element
+        det = np.linalg.det(np.stack([new[0, 0, M] - new[0, 0, 0], new[0, M, 0] - new[0, 0, 0],
+                                      new[M, 0, 0] - new[0, 0, 0]]))
         if det < 0:
             new = new[:, :, ::-1].copy()
-        xmap[e] = new.reshape(8, 3)
+        xmap[e] = new.reshape(Mp ** 3, 3)
+    scale = np.max(np.abs(mesh["xmap"]))
+    old_tags = {}
+    for e in range(K):
+        for f in range(6):
+            if mesh["ftab"][e, f, 0] < 0:
+                old_tags[_corner_key(_face_corners(mesh["xmap"][e], f, M), scale)] = int(mesh["ftab"][e, f, 3])
     out = dict(mesh)
     out["xmap"] = xmap
-    out["ftab"] = _faces_from_vertices(xmap, mesh["ftab"])
+    out["ftab"] = _connect_periodic_aware(mesh, xmap, old_tags, scale)
     return out
 
 
-def _face_vertices(xm, f):
-    """The 4 corner positions of face f of a trilinear element, in the face's
-    (s, t) corner order (-,-), (+,-), (-,+), (+,+)."""
-    v = xm.reshape(2, 2, 2, 3)  # [c][b][a]
+def _connect_periodic_aware(mesh, xmap, old_tags, scale):
+    """Faces of the relabelled mesh.  Geometric matching handles every face
+    pair whose corners coincide; a periodic pair (corners one period apart) is
+    found through the old table: the relabelled face has the corner key of
+    one old face of the same element, whose old neighbour face is located in
+    the neighbour's relabelled faces by its corner key."""
+    M = mesh["M"]
+    K = mesh["K"]
+    xold = mesh["xmap"]
+    ftab = connect_faces(xmap, M, 3, None, tag_of_key=(old_tags, scale), allow_unmatched_keys=True)
+    for e in range(K):
+        for f in range(6):
+            if ftab[e, f, 0] >= 0 or ftab[e, f, 3] != -99:
+                continue
+            A = _face_corners(xmap[e], f, M)
+            key = _corner_key(A, scale)
+            f_old = [g for g in range(6) if _corner_key(_face_corners(xold[e], g, M), scale) == key]
+            assert len(f_old) == 1
+            nb, g_old = mesh["ftab"][e, f_old[0], 0], mesh["ftab"][e, f_old[0], 1]
+            key_nb = _corner_key(_face_corners(xold[nb], g_old, M), scale)
+            g_new = [g for g in range(6) if _corner_key(_face_corners(xmap[nb], g, M), scale) == key_nb]
+            assert len(g_new) == 1
+            B = _face_corners(xmap[nb], g_new[0], M)
+            Bs = B + (A.mean(axis=0) - B.mean(axis=0))  # remove the period
+            ftab[e, f] = (nb, g_new[0], _orientation(A, Bs, scale), 0)
+    return ftab
+
+
+def _orientation(X, Y, scale):
+    for o in range(8):
+        ok = True
+        for bt in range(2):
+            for at in range(2):
+                s_, t_ = 2 * at - 1, 2 * bt - 1
+                s2, t2 = (t_, s_) if (o & 1) else (s_, t_)
+                if o & 2:
+                    s2 = -s2
+                if o & 4:
+                    t2 = -t2
+                ia, ib = (s2 + 1) // 2, (t2 + 1) // 2
+                if np.linalg.norm(X[bt * 2 + at] - Y[ib * 2 + ia]) > 1e-9 * scale:
+                    ok = False
+        if ok:
+            return o
+    raise AssertionError("face corners do not match")
+
+
+# cube faces of the cubed sphere: outward normal n and tangent axes with e1 x e2 = n
+_CUBE_FACES = [((1, 0, 0), (0, 1, 0), (0, 0, 1)), ((-1, 0, 0), (0, 0, 1), (0, 1, 0)),
+               ((0, 1, 0), (0, 0, 1), (1, 0, 0)), ((0, -1, 0), (1, 0, 0), (0, 0, 1)),
+               ((0, 0, 1), (1, 0, 0), (0, 1, 0)), ((0, 0, -1), (0, 1, 0), (1, 0, 0))]
+
+
+def cubed_sphere_mesh(nt, nr, r0=1.0, r1=20.0, M=2, inner_tag=BC_WALL, outer_tag=BC_FREESTREAM):
+    """Equiangular cubed-sphere shell r0 <= r <= r1: 6 patches of nt x nt
+    elements, nr layers with geometric radii r_k = r0 (r1/r0)^(k/nr).  Element
+    axes: (xi, eta) along the patch's equiangular angles, zeta outward.  The
+    mapping of order M interpolates the exact sphere at the equispaced
+    reference nodes; faces are connected by matching corner positions (with
+    the orientation codes this implies across cube edges)."""
+    Mp = M + 1
+    ang = np.linspace(-np.pi / 4, np.pi / 4, nt + 1)
+    rad = r0 * (r1 / r0) ** (np.arange(nr + 1) / nr)
+    ref = np.linspace(0.0, 1.0, Mp)
+    K = 6 * nt * nt * nr
+    xmap = np.zeros((K, Mp ** 3, 3))
+    e = 0
+    for (n, e1, e2) in _CUBE_FACES:
+        n, e1, e2 = np.array(n, float), np.array(e1, float), np.array(e2, float)
+        for k in range(nr):
+            for j in range(nt):
+                for i in range(nt):
+                    for c in range(Mp):
+                        r = rad[k] * (rad[k + 1] / rad[k]) ** ref[c]
+                        for b in range(Mp):
+                            be = ang[j] + (ang[j + 1] - ang[j]) * ref[b]
+                            for a in range(Mp):
+                                al = ang[i] + (ang[i + 1] - ang[i]) * ref[a]
+                                v = n + np.tan(al) * e1 + np.tan(be) * e2
+                                xmap[e, (c * Mp + b) * Mp + a] = r * v / np.linalg.norm(v)
+                    e += 1
+    ftab = connect_faces(xmap, M, 3, lambda cen: inner_tag if np.linalg.norm(cen) < 0.5 * (r0 + rad[1]) else outer_tag)
+    return dict(dim=3, K=K, M=M, xmap=xmap, ftab=ftab)
+
+
+def _face_corners(xm, f, M):
+    """Corner positions of face f of an element with (M+1)^3 mapping nodes,
+    in the face's (s, t) corner order (-,-), (+,-), (-,+), (+,+)."""
+    Mp = M + 1
+    v = xm.reshape(Mp, Mp, Mp, 3)  # [c][b][a]
     d, side = f // 2, f % 2
     ta, tb = [t for t in range(3) if t != d]
     out = []
     for bt in range(2):
         for at in range(2):
             idx = [0, 0, 0]
-            idx[d] = side
-            idx[ta] = at
-            idx[tb] = bt
+            idx[d] = side * M
+            idx[ta] = at * M
+            idx[tb] = bt * M
             out.append(v[idx[2], idx[1], idx[0]])
     return np.array(out)
 
 
-def _faces_from_vertices(xmap, ftab_old):
-    """Rebuild neighbour faces and orientation codes by matching face corners.
-    Periodic neighbours are matched up to the periodic translation: the old
-    table supplies which element pairs touch."""
+def _corner_key(C, scale):
+    return tuple(sorted(tuple(np.round(c / scale, 9)) for c in C))
+
+
+def connect_faces(xmap, M, dim, boundary_tag, tag_of_key=None, allow_unmatched_keys=False):
+    """Face table of a conforming hexahedral mesh from its geometry: faces
+    that share their four corners are neighbours; the orientation code maps
+    one side's face coordinates to the other's.  Unmatched faces get
+    boundary_tag(face centroid), or the tag stored for their corner key (tag
+    -99 marks an unmatched face with no stored tag when allowed)."""
     K = xmap.shape[0]
-    cent = xmap.mean(axis=1)
-    new_tab = np.full_like(ftab_old, -1)
-    new_tab[:, :, 2:] = 0
-
-    # old faces of the axis-aligned box are named by their outward direction;
-    # a re-labelled face is matched to the old one through its centroid
-    def outward_dir(e, f):
-        fv = _face_vertices(xmap[e], f)
-        c = fv.mean(axis=0) - cent[e]
-        d = int(np.argmax(np.abs(c)))
-        return 2 * d + (1 if c[d] > 0 else 0)
-
-    new_of_old = np.zeros((K, 6), dtype=int)
+    ftab = np.full((K, 6, 4), -1, dtype=np.int32)
+    ftab[:, :, 2:] = 0
+    scale = np.max(np.abs(xmap))
+    key_of = {}
+    corners = {}
     for e in range(K):
-        for f in range(6):
-            new_of_old[e, outward_dir(e, f)] = f
-    for e in range(K):
-        for f in range(6):
-            fo = outward_dir(e, f)
-            nb, nbf_old, _, tg = ftab_old[e, fo]
-            if nb < 0:
-                new_tab[e, f] = (-1, -1, 0, tg)
-                continue
-            nbf = new_of_old[nb, nbf_old]
-            A = _face_vertices(xmap[e], f)
-            B = _face_vertices(xmap[nb], nbf)
-            # remove the (periodic) translation between the two faces
-            B = B - B.mean(axis=0) + A.mean(axis=0)
-            code = None
-            for o in range(8):
-                ok = True
-                for bt in range(2):
-                    for at in range(2):
-                        s, t = 2 * at - 1, 2 * bt - 1
-                        s2, t2 = (t, s) if (o & 1) else (s, t)
-                        if o & 2:
-                            s2 = -s2
-                        if o & 4:
-                            t2 = -t2
-                        ia, ib = (s2 + 1) // 2, (t2 + 1) // 2
-                        if np.linalg.norm(A[bt * 2 + at] - B[ib * 2 + ia]) > 1e-9:
-                            ok = False
-                if ok:
-                    code = o
-                    break
-            assert code is not None, "face corners do not match"
-            new_tab[e, f] = (nb, nbf, code, 0)
-    return new_tab
+        for f in range(2 * dim):
+            C = _face_corners(xmap[e], f, M)
+            corners[(e, f)] = C
+            key_of.setdefault(_corner_key(C, scale), []).append((e, f))
+    for key, lst in key_of.items():
+        if len(lst) == 1:
+            e, f = lst[0]
+            if tag_of_key is not None:
+                k2 = _corner_key(corners[(e, f)], tag_of_key[1])
+                if k2 in tag_of_key[0]:
+                    tag = tag_of_key[0][k2]
+                elif allow_unmatched_keys:
+                    tag = -99
+                else:
+                    raise AssertionError("unmatched face without a boundary tag")
+            else:
+                tag = boundary_tag(corners[(e, f)].mean(axis=0))
+            ftab[e, f] = (-1, -1, 0, tag)
+            continue
+        assert len(lst) == 2, "a face shared by more than two elements"
+        (eA, fA), (eB, fB) = lst
+        A, B = corners[(eA, fA)], corners[(eB, fB)]
+        ftab[eA, fA] = (eB, fB, _orientation(A, B, scale), 0)
+        ftab[eB, fB] = (eA, fA, _orientation(B, A, scale), 0)
+    return ftab
 
 
 # --------------------------------------------------------------------------
@@ -385,6 +469,35 @@ def perturbed_state(mesh, orders, prm, seed, amp=0.05):
     return to_blocked(conserved(rho, u, v, w, p, gamma), orders, mesh["dim"])
 
 
+def smooth_state(mesh, orders, prm, seed, amp=0.05, wavelength=5.0):
+    """Freestream plus smooth seeded perturbations of rho, u, v, w, p: each a
+    sum of three plane waves with random directions, wavelength ~ `wavelength`
+    and random phases (resolved by the mesh, unlike per-node noise)."""
+    rng = np.random.default_rng(seed)
+    gamma, mach = prm[0], prm[2]
+    X = node_coordinates(mesh, orders)
+    if mesh["dim"] == 2:
+        X = X.copy()
+        X[:, 2] = 0.0
+
+    def field():
+        out = np.zeros(len(X))
+        for _ in range(3):
+            kdir = rng.normal(size=3)
+            if mesh["dim"] == 2:
+                kdir[2] = 0.0
+            kdir *= 2 * np.pi / wavelength / np.linalg.norm(kdir)
+            out += np.sin(X @ kdir + rng.uniform(0, 2 * np.pi)) / 3.0
+        return out
+
+    rho = 1.0 + amp * field()
+    u = 1.0 + amp * field()
+    v = amp * field()
+    w = amp * field() if mesh["dim"] == 3 else np.zeros(len(X))
+    p = (1.0 + amp * field()) / (gamma * mach * mach)
+    return to_blocked(conserved(rho, u, v, w, p, gamma), orders, mesh["dim"])
+
+
 def random_source(mesh, orders, seed, amp=1e-2):
     rng = np.random.default_rng(seed + 1000)
     nn, off = layout_offsets(orders, mesh["dim"])
@@ -404,6 +517,16 @@ def config_box_c1(seed=0):
     orders = uniform_orders(mesh["K"], 3, 3)
     q = manufactured_state(mesh, orders, seed, prm[2], prm[0])
     return mesh, orders, prm, q
+
+
+def config_sphere_c3(seed=2, nt=12, nr=16):
+    """Cubed-sphere shell r in [1, 20], 6 x nt x nt x nr quadratic hexes
+    (13,824 at nt=12, nr=16), orders uniform in [1, 6]^3 from the seed, Mach
+    0.2, Re 200, no-slip adiabatic sphere, freestream outer boundary."""
+    mesh = cubed_sphere_mesh(nt, nr)
+    prm = flow_params(mach=0.2, re=200.0)
+    orders = random_orders(mesh["K"], 3, 1, 6, seed)
+    return mesh, orders, prm
 
 
 def config_flat_plate_c2(N=7):

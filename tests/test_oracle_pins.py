@@ -178,6 +178,10 @@ MESHES = {
     "rotated3d_mixed": lambda: (syn.rotate_elements(syn.periodic_box(2, 2, 2), seed=4, frac=0.75), 3, 1, 4),
     "plate2d_mixed": lambda: (syn.box_mesh(np.linspace(-0.2, 1, 5), [0, 0.05, 0.12, 0.3],
                                            bc=dict(xmin=1, xmax=2, ymin=3, ymax=1)), 2, 1, 7),
+    # curved quadratic cubed-sphere shell, relabelled axes, conforming N = 4
+    # (M = 2 <= N/2), freestream on both spheres
+    "sphere_curved_rotated": lambda: (syn.rotate_elements(syn.cubed_sphere_mesh(2, 2, inner_tag=1), seed=5, frac=0.6),
+                                      3, 4, 4),
 }
 
 
@@ -189,7 +193,12 @@ def test_free_stream_preservation(name, isolated):
     prm = syn.flow_params(mach=0.3, re=100.0)
     q = syn.freestream_state(mesh, orders, prm)
     r = orc.residual(mesh, orders, prm, q, None, isolated)
-    assert np.max(np.abs(r)) <= 1e-13 * _scale(mesh, orders, prm)
+    # roundoff bound: 1e-13 of the term scale on affine meshes; the curved
+    # shell's metrics are products of coordinates up to r = 20 (J spans four
+    # decades), so its roundoff floor is 1e-12 -- a lost free-stream property
+    # shows at truncation level, many orders above either bound
+    tol = 1e-12 if mesh["M"] > 1 else 1e-13
+    assert np.max(np.abs(r)) <= tol * _scale(mesh, orders, prm)
 
 
 @pytest.mark.parametrize("name", ["periodic3d_mixed", "rotated3d_mixed"])
