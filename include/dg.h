@@ -104,6 +104,20 @@ int dg_mesh_destroy(dg_mesh* mesh);
  */
 int dg_mesh_layout(const dg_mesh* mesh, int64_t* total_nodes, int64_t* elem_offsets);
 
+/* Arithmetic of the operator kernels (dg_set_arithmetic). */
+#define DG_ARITH_FP64 0 /* native FP64 */
+#define DG_ARITH_DF32 1 /* double-float: pairs of FP32 numbers, ~48-bit significands, on the FP32 pipes */
+
+/*
+ * dg_set_arithmetic -- choose how the operator kernels (residual, isolated
+ * residual, tau) evaluate A(Q): DG_ARITH_FP64 (default) or DG_ARITH_DF32.
+ * Memory formats do not change (FP64 state, source and residual arrays) and
+ * the smoother's state update stays FP64; only the arithmetic inside the
+ * operator changes.  Applies to every level of the mesh; cached V-cycle
+ * graphs are dropped.
+ */
+int dg_set_arithmetic(dg_mesh* mesh, int mode);
+
 /* dg_mesh_orders -- copy the mesh's K x 3 order map to orders_out (host). */
 int dg_mesh_orders(const dg_mesh* mesh, int32_t* orders_out);
 

@@ -168,6 +168,7 @@ static int run_vcycle(dg_mesh* m, const std::vector<int32_t>& top_orders, double
   Cycle C{m, st, mg, {}, 0, 0.0};
   DG_TRY(cycle_levels(m, top_orders, mg, &C.lv));
   *nlev = (int)C.lv.size();
+  for (Level* L : C.lv) DG_TRY(prepare_arith(m, L, st));  // never allocate inside a capture
   if (!mg.graph) {
     DG_TRY(vcycle_level(C, 0, Q, Sv));
     *evals = C.evals;
@@ -453,6 +454,19 @@ int dg_mesh_layout(const dg_mesh* m, int64_t* total_nodes, int64_t* elem_offsets
   return DG_OK;
 }
 
+int dg_set_arithmetic(dg_mesh* m, int mode) {
+  if (!m || (mode != DG_ARITH_FP64 && mode != DG_ARITH_DF32)) {
+    set_error("dg_set_arithmetic: bad argument");
+    return DG_EINVAL;
+  }
+  if (m->arith != mode) {
+    for (auto& kv : m->graphs) cudaGraphExecDestroy(kv.second.exec);
+    m->graphs.clear();
+  }
+  m->arith = mode;
+  return DG_OK;
+}
+
 int dg_mesh_orders(const dg_mesh* m, int32_t* out) {
   if (!m || !out) {
     set_error("dg_mesh_orders: null argument");
@@ -706,6 +720,7 @@ int dg_solve_steady(dg_mesh** meshp, double** qp, const double* s, const dg_solv
       std::memcpy(d.params, m->raw_params, sizeof(d.params));
       dg_mesh* nm = nullptr;
       DG_TRY(dg_mesh_create(&d, no.data(), &nm));
+      nm->arith = m->arith;
       double* nq = (double*)alloc((size_t)5 * nm->fine->nodes * sizeof(double), alloc_ctx);
       if (!nq) {
         dg_mesh_destroy(nm);

@@ -118,6 +118,9 @@ struct Level {
   size_t tile_smem_nodes = 0;           // max nodes of a tile
   double* d_vol = nullptr;              // 5 x nodes volume part
   bool affine = false;                  // metrics constant within every element
+  double* d_geo2 = nullptr;             // float-pair copies for the double-float kernels (lazy)
+  double* d_fnS2 = nullptr;
+  double* d_mnS2 = nullptr;
   std::vector<int32_t> nvec_host;       // K x 3 node counts (host copy)
   // multigrid work arrays (allocated on first use)
   double *d_Q = nullptr, *d_S = nullptr, *d_Q0 = nullptr, *d_G = nullptr, *d_R = nullptr;
@@ -128,6 +131,7 @@ struct Level {
 
 struct dg_mesh {
   int dim = 3, K = 0, M = 1;
+  int arith = DG_ARITH_FP64;     // arithmetic of the operator kernels
   std::vector<double> xmap;
   std::vector<int32_t> ftab;
   dg::Params prm;
@@ -159,6 +163,7 @@ int upload_tables();
 unsigned long long launches();
 void add_launches(unsigned long long n);
 int prepare_capture();  // one-time per-device set-up that may not run inside a capture
+int prepare_arith(const dg_mesh* m, Level* L, cudaStream_t st);  // per-level data the arithmetic mode needs
 int residual(const dg_mesh* m, Level* L, const double* q, const double* s, double* r, bool isolated,
              cudaStream_t st, double* d_norm, int rk_stage, double* rk_g, const double* d_dt);
 int cfl_dt(const dg_mesh* m, Level* L, const double* q, double* d_dt, cudaStream_t st);

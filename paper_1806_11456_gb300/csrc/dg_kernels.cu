@@ -33,7 +33,10 @@
 #include <string>
 #include <vector>
 
+#include <type_traits>
+
 #include "dg_internal.h"
+#include "dg_real.h"
 
 namespace dg {
 
@@ -41,6 +44,24 @@ __constant__ DevTables c_tab;
 __constant__ double* c_Dhat;  // [kNP][kNP][kNP]
 __constant__ double* c_D;     // [kNP][kNP][kNP]
 __constant__ double* c_T;     // [kNP][kNP][kNP*kNP] transfer matrices (n_from, n_to)
+
+// the same tables as float pairs (hi, lo) for the double-float kernels
+struct DevTables2 {
+  float2 lm[kNP][kNP], lp[kNP][kNP];
+  float2 lmw[kNP][kNP], lpw[kNP][kNP];
+};
+__constant__ DevTables2 c_tab2;
+__constant__ float2* c_Dhat2;
+__constant__ float2* c_D2;
+__constant__ float2* c_T2;
+static float2* g_dev_Dhat2 = nullptr;
+static float2* g_dev_D2 = nullptr;
+static float2* g_dev_T2 = nullptr;
+
+static float2 split2(double x) {
+  float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
 
 static double* g_dev_Dhat = nullptr;
 static unsigned long long g_launches = 0;  // kernels launched by this library (host-side count)
@@ -88,144 +109,225 @@ int upload_tables() {
   DG_CUDA_TRY(cudaMemcpyToSymbol(c_Dhat, &g_dev_Dhat, sizeof(double*)));
   DG_CUDA_TRY(cudaMemcpyToSymbol(c_D, &g_dev_D, sizeof(double*)));
   DG_CUDA_TRY(cudaMemcpyToSymbol(c_T, &g_dev_T, sizeof(double*)));
+  // float-pair copies
+  DevTables2 h2;
+  memset(&h2, 0, sizeof(h2));
+  for (int n = 1; n < kNP; ++n)
+    for (int j = 0; j < n; ++j) {
+      h2.lm[n][j] = split2(h.lm[n][j]);
+      h2.lp[n][j] = split2(h.lp[n][j]);
+      h2.lmw[n][j] = split2(h.lmw[n][j]);
+      h2.lpw[n][j] = split2(h.lpw[n][j]);
+    }
+  DG_CUDA_TRY(cudaMemcpyToSymbol(c_tab2, &h2, sizeof(h2)));
+  std::vector<float2> Dh2(Dh.size()), Dc2(Dc.size()), Tm2(Tm.size());
+  for (size_t i = 0; i < Dh.size(); ++i) Dh2[i] = split2(Dh[i]);
+  for (size_t i = 0; i < Dc.size(); ++i) Dc2[i] = split2(Dc[i]);
+  for (size_t i = 0; i < Tm.size(); ++i) Tm2[i] = split2(Tm[i]);
+  if (!g_dev_Dhat2) {
+    DG_CUDA_TRY(cudaMalloc(&g_dev_Dhat2, Dh2.size() * sizeof(float2)));
+    DG_CUDA_TRY(cudaMalloc(&g_dev_D2, Dc2.size() * sizeof(float2)));
+    DG_CUDA_TRY(cudaMalloc(&g_dev_T2, Tm2.size() * sizeof(float2)));
+  }
+  DG_CUDA_TRY(cudaMemcpy(g_dev_Dhat2, Dh2.data(), Dh2.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  DG_CUDA_TRY(cudaMemcpy(g_dev_D2, Dc2.data(), Dc2.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  DG_CUDA_TRY(cudaMemcpy(g_dev_T2, Tm2.data(), Tm2.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  DG_CUDA_TRY(cudaMemcpyToSymbol(c_Dhat2, &g_dev_Dhat2, sizeof(float2*)));
+  DG_CUDA_TRY(cudaMemcpyToSymbol(c_D2, &g_dev_D2, sizeof(float2*)));
+  DG_CUDA_TRY(cudaMemcpyToSymbol(c_T2, &g_dev_T2, sizeof(float2*)));
   g_tables_device = dev;
   return DG_OK;
 }
 
 // ---------------------------------------------------------------------------
-// device physics (Appendix A)
+// device physics (Appendix A), generic over the arithmetic type R
 // ---------------------------------------------------------------------------
 #define DEV __device__ __forceinline__
 
-struct Gas {
-  double g1;     // gamma - 1
-  double gM2;    // gamma M^2
-  double Su, Su1;  // Sutherland S and 1 + S
-  double hc;     // 1/((gamma-1) Pr M^2)
-  double invRe;
-  double g;
-  double Ca, Cnu;
-  double qinf[5];
-  double pinf;
+template <typename R>
+DEV R cst(float x);
+template <>
+DEV double cst<double>(float x) {
+  return (double)x;
+}
+template <>
+DEV dd cst<dd>(float x) {
+  return dd(x, 0.0f);
+}
+
+// Gas constants in R (split into float pairs on the host for R = dd).
+template <typename R>
+struct GasT {
+  R g1;      // gamma - 1
+  R gM2;     // gamma M^2
+  R igM2;    // 1 / (gamma M^2)
+  R Su, Su1; // Sutherland S and 1 + S
+  R hc;      // 1/((gamma-1) Pr M^2)
+  R invRe;
+  R two3;    // 2/3
+  R qinf[5];
+  R pinf;
+  R ig1;     // 1/(gamma - 1)
 };
 
-DEV Gas make_gas(const Params& P) {
-  Gas G;
+struct GasD {  // FP64 constants for the CFL kernel
+  double g, g1, gM2, Su, Su1, invRe, Ca, Cnu;
+};
+
+template <typename R>
+R host_r(double x);
+template <>
+double host_r<double>(double x) {
+  return x;
+}
+template <>
+dd host_r<dd>(double x) {
+  dd v;
+  v.hi = (float)x;
+  v.lo = (float)(x - (double)v.hi);
+  return v;
+}
+
+template <typename R>
+GasT<R> make_gas(const Params& P) {
+  GasT<R> G;
+  G.g1 = host_r<R>(P.g - 1.0);
+  G.gM2 = host_r<R>(P.gM2);
+  G.igM2 = host_r<R>(1.0 / P.gM2);
+  G.Su = host_r<R>(P.Su);
+  G.Su1 = host_r<R>(1.0 + P.Su);
+  G.hc = host_r<R>(P.hc);
+  G.invRe = host_r<R>(P.invRe);
+  G.two3 = host_r<R>(2.0 / 3.0);
+  for (int v = 0; v < 5; ++v) G.qinf[v] = host_r<R>(P.qinf[v]);
+  G.pinf = host_r<R>(P.pinf);
+  G.ig1 = host_r<R>(1.0 / (P.g - 1.0));
+  return G;
+}
+
+static GasD make_gas_d(const Params& P) {
+  GasD G;
+  G.g = P.g;
   G.g1 = P.g - 1.0;
   G.gM2 = P.gM2;
   G.Su = P.Su;
   G.Su1 = 1.0 + P.Su;
-  G.hc = P.hc;
   G.invRe = P.invRe;
-  G.g = P.g;
   G.Ca = P.Ca;
   G.Cnu = P.Cnu;
-  for (int v = 0; v < 5; ++v) G.qinf[v] = P.qinf[v];
-  G.pinf = P.pinf;
   return G;
 }
 
 // primitives: 1/rho, velocity, pressure, temperature
-DEV void to_prim(const double* q, const Gas& G, double& ir, double* u, double& p, double& T) {
-  ir = 1.0 / q[0];
+template <typename R>
+DEV void to_prim(const R* q, const GasT<R>& G, R& ir, R* u, R& p, R& T) {
+  ir = cst<R>(1.0f) / q[0];
   u[0] = q[1] * ir;
   u[1] = q[2] * ir;
   u[2] = q[3] * ir;
-  p = G.g1 * (q[4] - 0.5 * (q[1] * u[0] + q[2] * u[1] + q[3] * u[2]));
+  p = G.g1 * (q[4] - cst<R>(0.5f) * (q[1] * u[0] + q[2] * u[1] + q[3] * u[2]));
   T = G.gM2 * p * ir;
 }
 
-DEV double mu_of_T(double T, const Gas& G) { return T * sqrt(T) * G.Su1 / (T + G.Su); }
+template <typename R>
+DEV R mu_of_T(R T, const GasT<R>& G) {
+  return T * sqrt(T) * G.Su1 / (T + G.Su);
+}
 
 // viscous flux (no 1/Re) on vector nv; grad[v*3+c] = d(u,v,w,T)_v / dx_c
-DEV void visc_flux(const double* u, double mu, const double* grad, const double* nv, const Gas& G,
-                   bool heat, double* f) {
-  double div = grad[0] + grad[4] + grad[8];
-  double lam = -2.0 / 3.0 * mu * div;
-  // tau . nv, tau symmetric
-  double t00 = 2.0 * mu * grad[0] + lam, t11 = 2.0 * mu * grad[4] + lam, t22 = 2.0 * mu * grad[8] + lam;
-  double t01 = mu * (grad[1] + grad[3]), t02 = mu * (grad[2] + grad[6]), t12 = mu * (grad[5] + grad[7]);
-  double tn0 = t00 * nv[0] + t01 * nv[1] + t02 * nv[2];
-  double tn1 = t01 * nv[0] + t11 * nv[1] + t12 * nv[2];
-  double tn2 = t02 * nv[0] + t12 * nv[1] + t22 * nv[2];
-  f[0] = 0.0;
+template <typename R>
+DEV void visc_flux(const R* u, R mu, const R* grad, const R* nv, const GasT<R>& G, bool heat, R* f) {
+  const R div = grad[0] + grad[4] + grad[8];
+  const R lam = -(G.two3 * mu * div);
+  const R mu2 = cst<R>(2.0f) * mu;
+  const R t00 = mu2 * grad[0] + lam, t11 = mu2 * grad[4] + lam, t22 = mu2 * grad[8] + lam;
+  const R t01 = mu * (grad[1] + grad[3]), t02 = mu * (grad[2] + grad[6]), t12 = mu * (grad[5] + grad[7]);
+  const R tn0 = t00 * nv[0] + t01 * nv[1] + t02 * nv[2];
+  const R tn1 = t01 * nv[0] + t11 * nv[1] + t12 * nv[2];
+  const R tn2 = t02 * nv[0] + t12 * nv[1] + t22 * nv[2];
+  f[0] = cst<R>(0.0f);
   f[1] = tn0;
   f[2] = tn1;
   f[3] = tn2;
-  double e = u[0] * tn0 + u[1] * tn1 + u[2] * tn2;
+  R e = u[0] * tn0 + u[1] * tn1 + u[2] * tn2;
   if (heat) e += G.hc * mu * (grad[9] * nv[0] + grad[10] * nv[1] + grad[11] * nv[2]);
   f[4] = e;
 }
 
 // Roe flux for unit normal n (textbook averages, five waves, no entropy fix)
-DEV void roe(const double* qL, const double* qR, const double* n, const Gas& G, double* f) {
-  double irL, uL[3], pL, TL, irR, uR[3], pR, TR;
+template <typename R>
+DEV void roe(const R* qL, const R* qR, const R* n, const GasT<R>& G, R* f) {
+  const R half = cst<R>(0.5f);
+  R irL, uL[3], pL, TL, irR, uR[3], pR, TR;
   to_prim(qL, G, irL, uL, pL, TL);
   to_prim(qR, G, irR, uR, pR, TR);
-  double unL = uL[0] * n[0] + uL[1] * n[1] + uL[2] * n[2];
-  double unR = uR[0] * n[0] + uR[1] * n[1] + uR[2] * n[2];
-  double HL = (qL[4] + pL) * irL, HR = (qR[4] + pR) * irR;
-  // central part
-  f[0] = 0.5 * (qL[0] * unL + qR[0] * unR);
-  f[1] = 0.5 * (qL[1] * unL + qR[1] * unR + (pL + pR) * n[0]);
-  f[2] = 0.5 * (qL[2] * unL + qR[2] * unR + (pL + pR) * n[1]);
-  f[3] = 0.5 * (qL[3] * unL + qR[3] * unR + (pL + pR) * n[2]);
-  f[4] = 0.5 * (qL[0] * HL * unL + qR[0] * HR * unR);
-  double sL = sqrt(qL[0]), sR = sqrt(qR[0]);
-  double iw = 1.0 / (sL + sR);
-  double ut[3] = {(sL * uL[0] + sR * uR[0]) * iw, (sL * uL[1] + sR * uR[1]) * iw, (sL * uL[2] + sR * uR[2]) * iw};
-  double Ht = (sL * HL + sR * HR) * iw;
-  double rt = sL * sR;
-  double q2 = ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2];
-  double c2 = G.g1 * (Ht - 0.5 * q2);
-  double ct = sqrt(c2);
-  double ic2 = 1.0 / c2;
-  double unt = ut[0] * n[0] + ut[1] * n[1] + ut[2] * n[2];
-  double dp = pR - pL, dr = qR[0] - qL[0];
-  double du[3] = {uR[0] - uL[0], uR[1] - uL[1], uR[2] - uL[2]};
-  double dun = unR - unL;
-  double a1 = 0.5 * (dp - rt * ct * dun) * ic2;
-  double a5 = 0.5 * (dp + rt * ct * dun) * ic2;
-  double a2 = dr - dp * ic2;
-  double l1 = fabs(unt - ct) * a1, l5 = fabs(unt + ct) * a5, l2 = fabs(unt);
-  double e2 = l2 * a2;
-  // shear part
-  double dt[3] = {du[0] - dun * n[0], du[1] - dun * n[1], du[2] - dun * n[2]};
-  double sh = l2 * rt;
-  double d0 = l1 + l5 + e2;
-  double d1 = l1 * (ut[0] - ct * n[0]) + l5 * (ut[0] + ct * n[0]) + e2 * ut[0] + sh * dt[0];
-  double d2 = l1 * (ut[1] - ct * n[1]) + l5 * (ut[1] + ct * n[1]) + e2 * ut[1] + sh * dt[1];
-  double d3 = l1 * (ut[2] - ct * n[2]) + l5 * (ut[2] + ct * n[2]) + e2 * ut[2] + sh * dt[2];
-  double d4 = l1 * (Ht - unt * ct) + l5 * (Ht + unt * ct) + e2 * 0.5 * q2 +
-              sh * (ut[0] * dt[0] + ut[1] * dt[1] + ut[2] * dt[2]);
-  f[0] -= 0.5 * d0;
-  f[1] -= 0.5 * d1;
-  f[2] -= 0.5 * d2;
-  f[3] -= 0.5 * d3;
-  f[4] -= 0.5 * d4;
+  const R unL = uL[0] * n[0] + uL[1] * n[1] + uL[2] * n[2];
+  const R unR = uR[0] * n[0] + uR[1] * n[1] + uR[2] * n[2];
+  const R HL = (qL[4] + pL) * irL, HR = (qR[4] + pR) * irR;
+  const R pLR = pL + pR;
+  f[0] = half * (qL[0] * unL + qR[0] * unR);
+  f[1] = half * (qL[1] * unL + qR[1] * unR + pLR * n[0]);
+  f[2] = half * (qL[2] * unL + qR[2] * unR + pLR * n[1]);
+  f[3] = half * (qL[3] * unL + qR[3] * unR + pLR * n[2]);
+  f[4] = half * (qL[0] * HL * unL + qR[0] * HR * unR);
+  const R sL = sqrt(qL[0]), sR = sqrt(qR[0]);
+  const R iw = cst<R>(1.0f) / (sL + sR);
+  const R ut0 = (sL * uL[0] + sR * uR[0]) * iw, ut1 = (sL * uL[1] + sR * uR[1]) * iw,
+          ut2 = (sL * uL[2] + sR * uR[2]) * iw;
+  const R Ht = (sL * HL + sR * HR) * iw;
+  const R rt = sL * sR;
+  const R q2 = ut0 * ut0 + ut1 * ut1 + ut2 * ut2;
+  const R c2 = G.g1 * (Ht - half * q2);
+  const R ct = sqrt(c2);
+  const R ic2 = cst<R>(1.0f) / c2;
+  const R unt = ut0 * n[0] + ut1 * n[1] + ut2 * n[2];
+  const R dp = pR - pL, dr = qR[0] - qL[0];
+  const R du0 = uR[0] - uL[0], du1 = uR[1] - uL[1], du2 = uR[2] - uL[2];
+  const R dun = unR - unL;
+  const R rcd = rt * ct * dun;
+  const R a1 = half * (dp - rcd) * ic2;
+  const R a5 = half * (dp + rcd) * ic2;
+  const R a2 = dr - dp * ic2;
+  const R l1 = fabs(unt - ct) * a1, l5 = fabs(unt + ct) * a5, l2 = fabs(unt);
+  const R e2 = l2 * a2;
+  const R dt0 = du0 - dun * n[0], dt1 = du1 - dun * n[1], dt2 = du2 - dun * n[2];
+  const R sh = l2 * rt;
+  const R cn0 = ct * n[0], cn1 = ct * n[1], cn2 = ct * n[2];
+  const R d0 = l1 + l5 + e2;
+  const R d1 = l1 * (ut0 - cn0) + l5 * (ut0 + cn0) + e2 * ut0 + sh * dt0;
+  const R d2 = l1 * (ut1 - cn1) + l5 * (ut1 + cn1) + e2 * ut1 + sh * dt1;
+  const R d3 = l1 * (ut2 - cn2) + l5 * (ut2 + cn2) + e2 * ut2 + sh * dt2;
+  const R uc = unt * ct;
+  const R d4 = l1 * (Ht - uc) + l5 * (Ht + uc) + e2 * half * q2 + sh * (ut0 * dt0 + ut1 * dt1 + ut2 * dt2);
+  f[0] -= half * d0;
+  f[1] -= half * d1;
+  f[2] -= half * d2;
+  f[3] -= half * d3;
+  f[4] -= half * d4;
 }
 
-DEV void ghost(int bc, const double* qi, const double* nu, const Gas& G, double* qg) {
+template <typename R>
+DEV void ghost(int bc, const R* qi, const R* nu, const GasT<R>& G, R* qg) {
   if (bc == DG_BC_FREESTREAM) {
+#pragma unroll
     for (int v = 0; v < 5; ++v) qg[v] = G.qinf[v];
     return;
   }
-  double ir = 1.0 / qi[0];
-  double ke = 0.5 * (qi[1] * qi[1] + qi[2] * qi[2] + qi[3] * qi[3]) * ir;
   if (bc == DG_BC_OUTFLOW) {
+    const R ke = cst<R>(0.5f) * (qi[1] * qi[1] + qi[2] * qi[2] + qi[3] * qi[3]) / qi[0];
     qg[0] = qi[0];
     qg[1] = qi[1];
     qg[2] = qi[2];
     qg[3] = qi[3];
-    qg[4] = G.pinf / G.g1 + ke;
+    qg[4] = G.pinf * G.ig1 + ke;
     return;
   }
   if (bc == DG_BC_SLIP) {
-    double mn = qi[1] * nu[0] + qi[2] * nu[1] + qi[3] * nu[2];
+    const R mn2 = cst<R>(2.0f) * (qi[1] * nu[0] + qi[2] * nu[1] + qi[3] * nu[2]);
     qg[0] = qi[0];
-    qg[1] = qi[1] - 2.0 * mn * nu[0];
-    qg[2] = qi[2] - 2.0 * mn * nu[1];
-    qg[3] = qi[3] - 2.0 * mn * nu[2];
+    qg[1] = qi[1] - mn2 * nu[0];
+    qg[2] = qi[2] - mn2 * nu[1];
+    qg[3] = qi[3] - mn2 * nu[2];
     qg[4] = qi[4];
     return;
   }
@@ -244,24 +346,53 @@ DEV void atomic_min_pos(double* addr, double v) {
   atomicMin(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
+// ---- tables in R ----
+template <typename R>
+struct Tab;
+template <>
+struct Tab<double> {
+  static DEV double lp(int n, int j) { return c_tab.lp[n][j]; }
+  static DEV double lm(int n, int j) { return c_tab.lm[n][j]; }
+  static DEV double lpw(int n, int j) { return c_tab.lpw[n][j]; }
+  static DEV double lmw(int n, int j) { return c_tab.lmw[n][j]; }
+  static DEV const double* Dhat() { return c_Dhat; }
+  static DEV const double* Dcol() { return c_D; }
+  static DEV const double* T() { return c_T; }
+};
+template <>
+struct Tab<dd> {
+  static DEV dd lp(int n, int j) { return dd(c_tab2.lp[n][j].x, c_tab2.lp[n][j].y); }
+  static DEV dd lm(int n, int j) { return dd(c_tab2.lm[n][j].x, c_tab2.lm[n][j].y); }
+  static DEV dd lpw(int n, int j) { return dd(c_tab2.lpw[n][j].x, c_tab2.lpw[n][j].y); }
+  static DEV dd lmw(int n, int j) { return dd(c_tab2.lmw[n][j].x, c_tab2.lmw[n][j].y); }
+  static DEV const float2* Dhat() { return c_Dhat2; }
+  static DEV const float2* Dcol() { return c_D2; }
+  static DEV const float2* T() { return c_T2; }
+};
+
 // ---------------------------------------------------------------------------
 // shared helpers for element tiles
 // ---------------------------------------------------------------------------
-struct LevelArgs {
+template <typename R>
+struct LevelArgsT {
+  using ST = typename Store<R>::T;
   const int32_t* n;
   const int32_t* off;
-  const double* geo;
+  const ST* geo;  // 10 x nodes
   int64_t nodes;
   const int32_t* fo;
   int64_t fn;  // face nodes
-  const double* fnS;
+  const ST* fnS;
   const ElemTile* tiles;
   const int32_t* tile_elems;
   int dim;
 };
 
-static LevelArgs largs(const Level* L) {
-  LevelArgs a;
+template <typename R>
+static LevelArgsT<R> largs(const Level* L);
+template <>
+LevelArgsT<double> largs<double>(const Level* L) {
+  LevelArgsT<double> a;
   a.n = L->d_n;
   a.off = L->d_off;
   a.geo = L->d_geo;
@@ -269,6 +400,21 @@ static LevelArgs largs(const Level* L) {
   a.fo = L->d_fo;
   a.fn = L->face_nodes;
   a.fnS = L->d_fnS;
+  a.tiles = L->d_tiles;
+  a.tile_elems = L->d_tile_elems;
+  a.dim = L->dim;
+  return a;
+}
+template <>
+LevelArgsT<dd> largs<dd>(const Level* L) {
+  LevelArgsT<dd> a;
+  a.n = L->d_n;
+  a.off = L->d_off;
+  a.geo = reinterpret_cast<const float2*>(L->d_geo2);
+  a.nodes = L->nodes;
+  a.fo = L->d_fo;
+  a.fn = L->face_nodes;
+  a.fnS = reinterpret_cast<const float2*>(L->d_fnS2);
   a.tiles = L->d_tiles;
   a.tile_elems = L->d_tile_elems;
   a.dim = L->dim;
@@ -285,28 +431,29 @@ DEV void face_dirs(int f, int& d, int& ta, int& tb, int& side) {
 // component k of a 3-vector held in scalars (avoids local-memory arrays)
 DEV int pick(int k, int a0, int a1, int a2) { return k == 0 ? a0 : (k == 1 ? a1 : a2); }
 
-// Interpolate face values (nvar comps, stride fs) of an na x nb face to the
+// Interpolate face values (NVAR comps, stride fs) of an na x nb face to the
 // mortar point (ia, ib) of an ma x mb rule.
-template <int NVAR>
-DEV void face_interp(const double* X, int64_t fs, int na, int nb, int ma, int mb, int ia, int ib, double* out) {
+template <typename R, int NVAR>
+DEV void face_interp(const typename Store<R>::T* X, int64_t fs, int na, int nb, int ma, int mb, int ia, int ib,
+                     R* out) {
+  using SR = Store<R>;
   if (na == ma && nb == mb) {
     int p = ib * na + ia;
 #pragma unroll
-    for (int v = 0; v < NVAR; ++v) out[v] = X[v * fs + p];
+    for (int v = 0; v < NVAR; ++v) out[v] = SR::get(X, v * fs + p);
     return;
   }
-  const double* Ta = c_T + ((size_t)na * kNP + ma) * kNP * kNP + ia * na;
-  const double* Tb = c_T + ((size_t)nb * kNP + mb) * kNP * kNP + ib * nb;
+  const typename Store<R>::T* Ta = Tab<R>::T() + ((size_t)na * kNP + ma) * kNP * kNP + ia * na;
+  const typename Store<R>::T* Tb = Tab<R>::T() + ((size_t)nb * kNP + mb) * kNP * kNP + ib * nb;
 #pragma unroll
-  for (int v = 0; v < NVAR; ++v) out[v] = 0.0;
+  for (int v = 0; v < NVAR; ++v) out[v] = cst<R>(0.0f);
   for (int kb = 0; kb < nb; ++kb) {
-    double wb = Tb[kb];
-    if (wb == 0.0) continue;
+    const R wb = SR::get(Tb, kb);
     for (int ka = 0; ka < na; ++ka) {
-      double wgt = wb * Ta[ka];
+      const R wgt = wb * SR::get(Ta, ka);
       int p = kb * na + ka;
 #pragma unroll
-      for (int v = 0; v < NVAR; ++v) out[v] += wgt * X[v * fs + p];
+      for (int v = 0; v < NVAR; ++v) out[v] += wgt * SR::get(X, v * fs + p);
     }
   }
 }
@@ -320,21 +467,21 @@ DEV int face_size(int f, int n0, int n1, int n2) {
 // ---------------------------------------------------------------------------
 // k_trace_q: conserved state at every face node of every element
 // ---------------------------------------------------------------------------
-template <int DIM>
-__global__ void __launch_bounds__(kTileNodes) k_trace_q(LevelArgs A, const double* __restrict__ q,
-                                                        double* __restrict__ trq) {
-  extern __shared__ double smem[];
+template <typename R, int DIM>
+__global__ void __launch_bounds__(kTileNodes) k_trace_q(LevelArgsT<R> A, const double* __restrict__ q,
+                                                        typename Store<R>::T* __restrict__ trq) {
+  extern __shared__ double smem_raw[];
+  R* sq = reinterpret_cast<R*>(smem_raw);
   const ElemTile t = A.tiles[blockIdx.x];
   const int n0 = t.n[0], n1 = t.n[1], n2 = t.n[2];
   const int nn = n0 * n1 * n2;
   const int T = t.count * nn;
-  double* sq = smem;
   for (int i = threadIdx.x; i < T; i += blockDim.x) {
     int le = i / nn, node = i - le * nn;
     int e = A.tile_elems[t.first + le];
     const double* qe = q + (size_t)5 * A.off[e];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) sq[v * T + i] = qe[v * nn + node];
+    for (int v = 0; v < 5; ++v) sq[v * T + i] = from_double<R>(qe[v * nn + node]);
   }
   __syncthreads();
   int FE = 0;
@@ -351,20 +498,19 @@ __global__ void __launch_bounds__(kTileNodes) k_trace_q(LevelArgs A, const doubl
     face_dirs(f, d, ta, tb, side);
     const int nta = pick(ta, n0, n1, n2), nd = pick(d, n0, n1, n2);
     int ia = r % nta, ib = r / nta;
-    int i0 = (d == 0) ? 0 : ia;               // index along x (ta = x unless d == 0)
+    int i0 = (d == 0) ? 0 : ia;
     int i1 = (d == 1) ? 0 : (d == 0 ? ia : ib);
     int i2 = (d == 2) ? 0 : ib;
     int base = (i2 * n1 + i1) * n0 + i0;
     int sd = (d == 0) ? 1 : (d == 1 ? n0 : n0 * n1);
-    const double* lb = side ? c_tab.lp[nd] : c_tab.lm[nd];
     int e = A.tile_elems[t.first + le];
     int64_t p = A.fo[e * 6 + f] + r;
-    const double* s0 = sq + le * nn + base;
+    const R* s0 = sq + le * nn + base;
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      double acc = 0.0;
-      for (int k = 0; k < nd; ++k) acc += lb[k] * s0[v * T + k * sd];
-      trq[v * A.fn + p] = acc;
+      R acc = cst<R>(0.0f);
+      for (int k = 0; k < nd; ++k) acc += (side ? Tab<R>::lp(nd, k) : Tab<R>::lm(nd, k)) * s0[v * T + k * sd];
+      Store<R>::put(trq, v * A.fn + p, acc);
     }
   }
 }
@@ -372,28 +518,34 @@ __global__ void __launch_bounds__(kTileNodes) k_trace_q(LevelArgs A, const doubl
 // ---------------------------------------------------------------------------
 // k_mortar<PASS>: PASS 1 = BR1 average U*, PASS 2 = Roe + BR1 viscous flux
 // ---------------------------------------------------------------------------
-struct MortarArgs {
+template <typename R>
+struct MortarArgsT {
   const MortarDev* mortars;
   const int32_t* mnode_mortar;
-  const double* mnS;
+  const typename Store<R>::T* mnS;
   int64_t mnodes;
   const MortarTile* tiles;
 };
 
-static MortarArgs margs(const Level* L) {
-  MortarArgs a;
+template <typename R>
+static MortarArgsT<R> margs(const Level* L) {
+  MortarArgsT<R> a;
   a.mortars = L->d_mortars;
   a.mnode_mortar = L->d_mnode_mortar;
-  a.mnS = L->d_mnS;
+  a.mnS = std::is_same<R, dd>::value ? reinterpret_cast<const typename Store<R>::T*>(L->d_mnS2)
+                                     : reinterpret_cast<const typename Store<R>::T*>(L->d_mnS);
   a.mnodes = L->mortar_nodes;
   a.tiles = L->d_mtiles;
   return a;
 }
 
 // value at one mortar node: U* (PASS 1) or F* S-hat (PASS 2)
-template <int PASS>
-DEV void mortar_node_value(const LevelArgs& A, const MortarArgs& MA, const Gas& G, const double* __restrict__ trq,
-                           const double* __restrict__ trg, int64_t gp, double* o) {
+template <typename R, int PASS>
+DEV void mortar_node_value(const LevelArgsT<R>& A, const MortarArgsT<R>& MA, const GasT<R>& G,
+                           const typename Store<R>::T* __restrict__ trq, const typename Store<R>::T* __restrict__ trg,
+                           int64_t gp, R* o) {
+  using SR = Store<R>;
+  const R half = cst<R>(0.5f);
   const MortarDev M = MA.mortars[MA.mnode_mortar[gp]];
   const int loc = (int)(gp - M.node_off);
   const int a = loc % M.ma, b = loc / M.ma;
@@ -401,12 +553,12 @@ DEV void mortar_node_value(const LevelArgs& A, const MortarArgs& MA, const Gas& 
   face_dirs(M.fL, dL, taL, tbL, sL);
   const int nLa = A.n[M.eL * 3 + taL], nLb = A.n[M.eL * 3 + tbL];
   const int64_t pL = A.fo[M.eL * 6 + M.fL];
-  double qL[5], qR[5];
-  face_interp<5>(trq + pL, A.fn, nLa, nLb, M.ma, M.mb, a, b, qL);
-  const double nS0 = MA.mnS[gp], nS1 = MA.mnS[MA.mnodes + gp], nS2 = MA.mnS[2 * MA.mnodes + gp];
-  const double S = sqrt(nS0 * nS0 + nS1 * nS1 + nS2 * nS2);
-  const double iS = 1.0 / S;
-  const double nu[3] = {nS0 * iS, nS1 * iS, nS2 * iS};
+  R qL[5], qR[5];
+  face_interp<R, 5>(trq + pL, A.fn, nLa, nLb, M.ma, M.mb, a, b, qL);
+  const R nS0 = SR::get(MA.mnS, gp), nS1 = SR::get(MA.mnS, MA.mnodes + gp), nS2 = SR::get(MA.mnS, 2 * MA.mnodes + gp);
+  const R S = sqrt(nS0 * nS0 + nS1 * nS1 + nS2 * nS2);
+  const R iS = cst<R>(1.0f) / S;
+  const R nu[3] = {nS0 * iS, nS1 * iS, nS2 * iS};
   int Ra = 0, Rb = 0, Ma = 0, Mb = 0, ia = 0, ib = 0;
   int64_t pR = 0;
   if (M.eR >= 0) {
@@ -422,60 +574,61 @@ DEV void mortar_node_value(const LevelArgs& A, const MortarArgs& MA, const Gas& 
     if (M.orient & 2) ia = Ma - 1 - ia;
     if (M.orient & 4) ib = Mb - 1 - ib;
     pR = A.fo[M.eR * 6 + M.fR];
-    face_interp<5>(trq + pR, A.fn, Ra, Rb, Ma, Mb, ia, ib, qR);
+    face_interp<R, 5>(trq + pR, A.fn, Ra, Rb, Ma, Mb, ia, ib, qR);
   } else {
     ghost(M.bc, qL, nu, G, qR);
   }
   if (PASS == 1) {
-    double ir, u[3], p, T, u2[3], T2;
+    R ir, u[3], p, T, u2[3], T2;
     to_prim(qL, G, ir, u, p, T);
     to_prim(qR, G, ir, u2, p, T2);
-    o[0] = 0.5 * (u[0] + u2[0]);
-    o[1] = 0.5 * (u[1] + u2[1]);
-    o[2] = 0.5 * (u[2] + u2[2]);
-    o[3] = 0.5 * (T + T2);
+    o[0] = half * (u[0] + u2[0]);
+    o[1] = half * (u[1] + u2[1]);
+    o[2] = half * (u[2] + u2[2]);
+    o[3] = half * (T + T2);
     return;
   }
-  double f[5];
+  R f[5];
   roe(qL, qR, nu, G, f);
   if (!(M.eR < 0 && M.bc == DG_BC_SLIP)) {
-    double g[12], fv[5];
-    face_interp<12>(trg + pL, A.fn, nLa, nLb, M.ma, M.mb, a, b, g);
-    double ir, u[3], p, T;
+    R g[12], fv[5];
+    face_interp<R, 12>(trg + pL, A.fn, nLa, nLb, M.ma, M.mb, a, b, g);
+    R ir, u[3], p, T;
     to_prim(qL, G, ir, u, p, T);
-    const double mu = mu_of_T(T, G);
+    const R mu = mu_of_T(T, G);
     if (M.eR < 0 && M.bc == DG_BC_WALL) {
-      const double z[3] = {0, 0, 0};
+      const R z[3] = {cst<R>(0.0f), cst<R>(0.0f), cst<R>(0.0f)};
       visc_flux(z, mu, g, nu, G, false, fv);
 #pragma unroll
       for (int v = 0; v < 5; ++v) f[v] -= G.invRe * fv[v];
     } else {
+      const R hre = half * G.invRe;
       visc_flux(u, mu, g, nu, G, true, fv);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) f[v] -= 0.5 * G.invRe * fv[v];
-      if (M.eR >= 0) face_interp<12>(trg + pR, A.fn, Ra, Rb, Ma, Mb, ia, ib, g);  // else: interior gradient
+      for (int v = 0; v < 5; ++v) f[v] -= hre * fv[v];
+      if (M.eR >= 0) face_interp<R, 12>(trg + pR, A.fn, Ra, Rb, Ma, Mb, ia, ib, g);  // else: interior gradient
       to_prim(qR, G, ir, u, p, T);
       visc_flux(u, mu_of_T(T, G), g, nu, G, true, fv);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) f[v] -= 0.5 * G.invRe * fv[v];
+      for (int v = 0; v < 5; ++v) f[v] -= hre * fv[v];
     }
   }
 #pragma unroll
   for (int v = 0; v < 5; ++v) o[v] = S * f[v];
 }
 
-template <int PASS>
-__global__ void __launch_bounds__(kMortarTile, 8) k_mortar(LevelArgs A, MortarArgs MA, Params P,
-                                                           const double* __restrict__ trq,
-                                                           const double* __restrict__ trg, double* __restrict__ out) {
+template <typename R, int PASS>
+__global__ void __launch_bounds__(kMortarTile, 8) k_mortar(LevelArgsT<R> A, MortarArgsT<R> MA, GasT<R> G,
+                                                           const typename Store<R>::T* __restrict__ trq,
+                                                           const typename Store<R>::T* __restrict__ trg,
+                                                           typename Store<R>::T* __restrict__ out) {
+  using SR = Store<R>;
   constexpr int NV = (PASS == 1) ? 4 : 5;
-  __shared__ double sval[kMortarTileMax * 5];
+  __shared__ R sval[kMortarTileMax * 5];
   __shared__ int scum[kMortarTileMax + 1];
   const MortarTile mt = MA.tiles[blockIdx.x];
-  const Gas G = make_gas(P);
   for (int i = threadIdx.x; i < mt.nodes; i += blockDim.x)
-    mortar_node_value<PASS>(A, MA, G, trq, trg, mt.node_first + i, sval + i * 5);
-  // prefix of projection outputs per mortar in the tile
+    mortar_node_value<R, PASS>(A, MA, G, trq, trg, mt.node_first + i, sval + i * 5);
   if (threadIdx.x == 0) {
     int acc = 0;
     for (int m = 0; m < mt.count; ++m) {
@@ -499,15 +652,15 @@ __global__ void __launch_bounds__(kMortarTile, 8) k_mortar(LevelArgs A, MortarAr
     while (scum[m + 1] <= i) ++m;
     const MortarDev M = MA.mortars[mt.first + m];
     int r = i - scum[m];
-    const double* vals = sval + (M.node_off - mt.node_first) * 5;
+    const R* vals = sval + (M.node_off - mt.node_first) * 5;
     int dL, taL, tbL, sL;
     face_dirs(M.fL, dL, taL, tbL, sL);
     const int nLa = A.n[M.eL * 3 + taL], nLb = A.n[M.eL * 3 + tbL];
-    double acc[NV];
+    R acc[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+    for (int v = 0; v < NV; ++v) acc[v] = cst<R>(0.0f);
     int64_t dst;
-    double sgn = 1.0;
+    bool neg = false;
     if (r < nLa * nLb) {
       int ka = r % nLa, kb = r / nLa;
       dst = A.fo[M.eL * 6 + M.fL] + r;
@@ -515,11 +668,11 @@ __global__ void __launch_bounds__(kMortarTile, 8) k_mortar(LevelArgs A, MortarAr
 #pragma unroll
         for (int v = 0; v < NV; ++v) acc[v] = vals[r * 5 + v];
       } else {
-        const double* Pa = c_T + ((size_t)M.ma * kNP + nLa) * kNP * kNP + ka * M.ma;
-        const double* Pb = c_T + ((size_t)M.mb * kNP + nLb) * kNP * kNP + kb * M.mb;
+        const typename SR::T* Pa = Tab<R>::T() + ((size_t)M.ma * kNP + nLa) * kNP * kNP + ka * M.ma;
+        const typename SR::T* Pb = Tab<R>::T() + ((size_t)M.mb * kNP + nLb) * kNP * kNP + kb * M.mb;
         for (int bb = 0; bb < M.mb; ++bb)
           for (int aa = 0; aa < M.ma; ++aa) {
-            double wgt = Pa[aa] * Pb[bb];
+            const R wgt = SR::get(Pa, aa) * SR::get(Pb, bb);
 #pragma unroll
             for (int v = 0; v < NV; ++v) acc[v] += wgt * vals[(bb * M.ma + aa) * 5 + v];
           }
@@ -533,91 +686,90 @@ __global__ void __launch_bounds__(kMortarTile, 8) k_mortar(LevelArgs A, MortarAr
       const int Ma = sw ? M.mb : M.ma, Mb = sw ? M.ma : M.mb;
       int ka = r % Ra, kb = r / Ra;
       dst = A.fo[M.eR * 6 + M.fR] + r;
-      if (PASS == 2) sgn = -1.0;
-      const double* Pa = c_T + ((size_t)Ma * kNP + Ra) * kNP * kNP + ka * Ma;
-      const double* Pb = c_T + ((size_t)Mb * kNP + Rb) * kNP * kNP + kb * Mb;
+      neg = (PASS == 2);
+      const typename SR::T* Pa = Tab<R>::T() + ((size_t)Ma * kNP + Ra) * kNP * kNP + ka * Ma;
+      const typename SR::T* Pb = Tab<R>::T() + ((size_t)Mb * kNP + Rb) * kNP * kNP + kb * Mb;
       for (int bb = 0; bb < M.mb; ++bb)
         for (int aa = 0; aa < M.ma; ++aa) {
           int ia = sw ? bb : aa, ib = sw ? aa : bb;
           if (M.orient & 2) ia = Ma - 1 - ia;
           if (M.orient & 4) ib = Mb - 1 - ib;
-          double wgt = Pa[ia] * Pb[ib];
-          if (wgt == 0.0) continue;
+          const R wgt = SR::get(Pa, ia) * SR::get(Pb, ib);
 #pragma unroll
           for (int v = 0; v < NV; ++v) acc[v] += wgt * vals[(bb * M.ma + aa) * 5 + v];
         }
     }
 #pragma unroll
-    for (int v = 0; v < NV; ++v) out[v * A.fn + dst] = sgn * acc[v];
+    for (int v = 0; v < NV; ++v) SR::put(out, v * A.fn + dst, neg ? -acc[v] : acc[v]);
   }
 }
 
 // ---------------------------------------------------------------------------
 // element kernels: staging, BR1 gradient, fluxes, divergence
 // ---------------------------------------------------------------------------
-DEV void load_dtables(double* sD, const double* src, int n0, int n1, int n2, int dim) {
+template <typename R>
+DEV void load_dtables(R* sD, const typename Store<R>::T* src, int n0, int n1, int n2, int dim) {
   // sD[d][i][a] with stride kNP*kNP per direction
   for (int d = 0; d < dim; ++d) {
     const int nd = pick(d, n0, n1, n2);
     for (int k = threadIdx.x; k < nd * nd; k += blockDim.x) {
       int i = k / nd, a = k - i * nd;
-      sD[d * kNP * kNP + i * kNP + a] = src[((size_t)nd * kNP + i) * kNP + a];
+      sD[d * kNP * kNP + i * kNP + a] = Store<R>::get(src, ((size_t)nd * kNP + i) * kNP + a);
     }
   }
 }
 
 // Stage the tile: conserved state (sq), primitives u,v,w,T (sA[0..3]) and the
 // nine metric components (sA[4..12]).
-DEV void stage_tile(const LevelArgs& A, const ElemTile& t, int nn, int T, const Gas& G, const double* __restrict__ q,
-                    double* sq, double* sA) {
+template <typename R>
+DEV void stage_tile(const LevelArgsT<R>& A, const ElemTile& t, int nn, int T, const GasT<R>& G,
+                    const double* __restrict__ q, R* sq, R* sA) {
   for (int i = threadIdx.x; i < T; i += blockDim.x) {
     int le = i / nn, node = i - le * nn;
     int e = A.tile_elems[t.first + le];
     const int64_t gn = A.off[e] + node;
     const double* qe = q + (size_t)5 * A.off[e];
-    double qq[5];
+    R qq[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      qq[v] = qe[v * nn + node];
+      qq[v] = from_double<R>(qe[v * nn + node]);
       sq[v * T + i] = qq[v];
     }
-    double ir, u[3], p, Tt;
+    R ir, u[3], p, Tt;
     to_prim(qq, G, ir, u, p, Tt);
     sA[0 * T + i] = u[0];
     sA[1 * T + i] = u[1];
     sA[2 * T + i] = u[2];
     sA[3 * T + i] = Tt;
 #pragma unroll
-    for (int c = 0; c < 9; ++c) sA[(4 + c) * T + i] = A.geo[c * A.nodes + gn];
+    for (int c = 0; c < 9; ++c) sA[(4 + c) * T + i] = Store<R>::get(A.geo, c * A.nodes + gn);
   }
 }
 
 // Volume part of the gradient at node i of the tile: sum_d D^d (Ja^d U).
 // AFFINE: the metrics are constant in the element, so Ja^d is factored out
-// of the contraction (same value, 4 instead of 15 FP64 operations per point).
-template <int DIM, bool AFFINE>
-DEV void gradient_volume(const double* sD, const double* sA, int T, int nn, int i, int n0, int n1, int n2,
-                         double* g) {
+// of the contraction (same value, 4 instead of 15 operations per point).
+template <typename R, int DIM, bool AFFINE>
+DEV void gradient_volume(const R* sD, const R* sA, int T, int nn, int i, int n0, int n1, int n2, R* g) {
   const int le = i / nn, node = i - le * nn;
   const int idx0 = node % n0, idx1 = (node / n0) % n1, idx2 = node / (n0 * n1);
 #pragma unroll
-  for (int k = 0; k < 12; ++k) g[k] = 0.0;
+  for (int k = 0; k < 12; ++k) g[k] = cst<R>(0.0f);
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
     const int id = pick(d, idx0, idx1, idx2), nd = pick(d, n0, n1, n2);
     const int sd = (d == 0) ? 1 : (d == 1 ? n0 : n0 * n1);
     const int base = le * nn + node - id * sd;
-    const double* Drow = sD + d * kNP * kNP + id * kNP;
+    const R* Drow = sD + d * kNP * kNP + id * kNP;
     if (AFFINE) {
-      double cu[4] = {0, 0, 0, 0};
+      R cu[4] = {cst<R>(0.0f), cst<R>(0.0f), cst<R>(0.0f), cst<R>(0.0f)};
       for (int a = 0; a < nd; ++a) {
         const int la = base + a * sd;
-        const double c = Drow[a];
+        const R c = Drow[a];
 #pragma unroll
         for (int v = 0; v < 4; ++v) cu[v] += c * sA[v * T + la];
       }
-      const double j0 = sA[(4 + d * 3 + 0) * T + i], j1 = sA[(4 + d * 3 + 1) * T + i],
-                   j2 = sA[(4 + d * 3 + 2) * T + i];
+      const R j0 = sA[(4 + d * 3 + 0) * T + i], j1 = sA[(4 + d * 3 + 1) * T + i], j2 = sA[(4 + d * 3 + 2) * T + i];
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         g[v * 3 + 0] += j0 * cu[v];
@@ -627,13 +779,13 @@ DEV void gradient_volume(const double* sD, const double* sA, int T, int nn, int 
     } else {
       for (int a = 0; a < nd; ++a) {
         const int la = base + a * sd;
-        const double c = Drow[a];
-        const double j0 = c * sA[(4 + d * 3 + 0) * T + la];
-        const double j1 = c * sA[(4 + d * 3 + 1) * T + la];
-        const double j2 = c * sA[(4 + d * 3 + 2) * T + la];
+        const R c = Drow[a];
+        const R j0 = c * sA[(4 + d * 3 + 0) * T + la];
+        const R j1 = c * sA[(4 + d * 3 + 1) * T + la];
+        const R j2 = c * sA[(4 + d * 3 + 2) * T + la];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-          const double uv = sA[v * T + la];
+          const R uv = sA[v * T + la];
           g[v * 3 + 0] += j0 * uv;
           g[v * 3 + 1] += j1 * uv;
           g[v * 3 + 2] += j2 * uv;
@@ -645,27 +797,27 @@ DEV void gradient_volume(const double* sD, const double* sA, int T, int nn, int 
 
 // Nodal contravariant fluxes Ftilde^d = Ja^d . (F^a - F^v / Re) of node i,
 // written over its own sA slots (reads its own slots first).
-template <int DIM>
-DEV void nodal_fluxes(const double* sq, double* sA, const double* sG, int T, int i, const Gas& G) {
-  double qq[5], u[3], Ja[3 * DIM], gr[12];
+template <typename R, int DIM>
+DEV void nodal_fluxes(const R* sq, R* sA, const R* sG, int T, int i, const GasT<R>& G) {
+  R qq[5], u[3], Ja[3 * DIM], gr[12];
 #pragma unroll
   for (int v = 0; v < 5; ++v) qq[v] = sq[v * T + i];
   u[0] = sA[0 * T + i];
   u[1] = sA[1 * T + i];
   u[2] = sA[2 * T + i];
-  const double Tt = sA[3 * T + i];
+  const R Tt = sA[3 * T + i];
 #pragma unroll
   for (int c = 0; c < 3 * DIM; ++c) Ja[c] = sA[(4 + c) * T + i];
 #pragma unroll
   for (int k = 0; k < 12; ++k) gr[k] = sG[k * T + i];
-  const double p = Tt * qq[0] / G.gM2;
-  const double mu = mu_of_T(Tt, G);
-  double F[5 * DIM];
+  const R p = Tt * qq[0] * G.igM2;
+  const R mu = mu_of_T(Tt, G);
+  R F[5 * DIM];
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
-    const double* nv = Ja + 3 * d;
-    const double un = u[0] * nv[0] + u[1] * nv[1] + u[2] * nv[2];
-    double fv[5];
+    const R* nv = Ja + 3 * d;
+    const R un = u[0] * nv[0] + u[1] * nv[1] + u[2] * nv[2];
+    R fv[5];
     visc_flux(u, mu, gr, nv, G, true, fv);
     F[d * 5 + 0] = qq[0] * un;
     F[d * 5 + 1] = qq[1] * un + p * nv[0] - G.invRe * fv[1];
@@ -678,48 +830,49 @@ DEV void nodal_fluxes(const double* sq, double* sA, const double* sG, int T, int
 }
 
 // sum_d D^d Ftilde^d at node i
-template <int DIM>
-DEV void divergence(const double* sD, const double* sA, int T, int nn, int i, int n0, int n1, int n2, double* acc) {
+template <typename R, int DIM>
+DEV void divergence(const R* sD, const R* sA, int T, int nn, int i, int n0, int n1, int n2, R* acc) {
   const int le = i / nn, node = i - le * nn;
   const int idx0 = node % n0, idx1 = (node / n0) % n1, idx2 = node / (n0 * n1);
 #pragma unroll
-  for (int v = 0; v < 5; ++v) acc[v] = 0.0;
+  for (int v = 0; v < 5; ++v) acc[v] = cst<R>(0.0f);
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
     const int id = pick(d, idx0, idx1, idx2), nd = pick(d, n0, n1, n2);
     const int sd = (d == 0) ? 1 : (d == 1 ? n0 : n0 * n1);
     const int base = le * nn + node - id * sd;
-    const double* Drow = sD + d * kNP * kNP + id * kNP;
+    const R* Drow = sD + d * kNP * kNP + id * kNP;
     for (int a = 0; a < nd; ++a) {
       const int la = base + a * sd;
-      const double c = Drow[a];
+      const R c = Drow[a];
 #pragma unroll
       for (int v = 0; v < 5; ++v) acc[v] += c * sA[(d * 5 + v) * T + la];
     }
   }
 }
 
-template <int DIM, bool AFFINE>
-__global__ void __launch_bounds__(kTileNodes) k_volume(LevelArgs A, Params P, const double* __restrict__ q,
-                                                       const double* __restrict__ ust, double* __restrict__ trg,
-                                                       double* __restrict__ vol) {
-  extern __shared__ double smem[];
+template <typename R, int DIM, bool AFFINE>
+__global__ void __launch_bounds__(kTileNodes) k_volume(LevelArgsT<R> A, GasT<R> G, const double* __restrict__ q,
+                                                       const typename Store<R>::T* __restrict__ ust,
+                                                       typename Store<R>::T* __restrict__ trg,
+                                                       typename Store<R>::T* __restrict__ vol) {
+  using SR = Store<R>;
+  extern __shared__ double smem_raw[];
   const ElemTile t = A.tiles[blockIdx.x];
   const int n0 = t.n[0], n1 = t.n[1], n2 = t.n[2];
   const int nn = n0 * n1 * n2;
   const int T = t.count * nn;
-  const Gas G = make_gas(P);
-  double* sD = smem;                          // 3 * kNP * kNP
-  double* sq = sD + 3 * kNP * kNP;            // 5 * T
-  double* sA = sq + 5 * T;                    // 15 * T: U(4) + Ja(9) | Ftilde(15)
-  double* sG = sA + 15 * T;                   // 12 * T
-  load_dtables(sD, c_Dhat, n0, n1, n2, DIM);
-  stage_tile(A, t, nn, T, G, q, sq, sA);
+  R* sD = reinterpret_cast<R*>(smem_raw);     // 3 * kNP * kNP
+  R* sq = sD + 3 * kNP * kNP;                  // 5 * T
+  R* sA = sq + 5 * T;                          // 15 * T: U(4) + Ja(9) | Ftilde(15)
+  R* sG = sA + 15 * T;                         // 12 * T
+  load_dtables<R>(sD, Tab<R>::Dhat(), n0, n1, n2, DIM);
+  stage_tile<R>(A, t, nn, T, G, q, sq, sA);
   __syncthreads();
   // ---- gradient: volume part + lifting of U*, times 1/J ----
   for (int i = threadIdx.x; i < T; i += blockDim.x) {
-    double g[12];
-    gradient_volume<DIM, AFFINE>(sD, sA, T, nn, i, n0, n1, n2, g);
+    R g[12];
+    gradient_volume<R, DIM, AFFINE>(sD, sA, T, nn, i, n0, n1, n2, g);
     const int le = i / nn, node = i - le * nn;
     const int e = A.tile_elems[t.first + le];
     const int idx0 = node % n0, idx1 = (node / n0) % n1, idx2 = node / (n0 * n1);
@@ -728,18 +881,18 @@ __global__ void __launch_bounds__(kTileNodes) k_volume(LevelArgs A, Params P, co
       int d, ta, tb, side;
       face_dirs(f, d, ta, tb, side);
       const int nd = pick(d, n0, n1, n2), id = pick(d, idx0, idx1, idx2);
-      const double lw = side ? c_tab.lpw[nd][id] : c_tab.lmw[nd][id];
+      const R lw = side ? Tab<R>::lpw(nd, id) : Tab<R>::lmw(nd, id);
       const int64_t p = A.fo[e * 6 + f] + pick(tb, idx0, idx1, idx2) * pick(ta, n0, n1, n2) + pick(ta, idx0, idx1, idx2);
-      const double m0 = lw * A.fnS[p], m1 = lw * A.fnS[A.fn + p], m2 = lw * A.fnS[2 * A.fn + p];
+      const R m0 = lw * SR::get(A.fnS, p), m1 = lw * SR::get(A.fnS, A.fn + p), m2 = lw * SR::get(A.fnS, 2 * A.fn + p);
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
-        const double us = ust[v * A.fn + p];
+        const R us = SR::get(ust, v * A.fn + p);
         g[v * 3 + 0] += m0 * us;
         g[v * 3 + 1] += m1 * us;
         g[v * 3 + 2] += m2 * us;
       }
     }
-    const double iJ = A.geo[9 * A.nodes + A.off[e] + node];
+    const R iJ = SR::get(A.geo, 9 * A.nodes + A.off[e] + node);
 #pragma unroll
     for (int k = 0; k < 12; ++k) sG[k * T + i] = g[k] * iJ;
   }
@@ -765,30 +918,29 @@ __global__ void __launch_bounds__(kTileNodes) k_volume(LevelArgs A, Params P, co
       int i2 = (d == 2) ? 0 : ib;
       int base = (i2 * n1 + i1) * n0 + i0;
       int sdd = (d == 0) ? 1 : (d == 1 ? n0 : n0 * n1);
-      const double* lb = side ? c_tab.lp[nd] : c_tab.lm[nd];
       int e = A.tile_elems[t.first + le];
       int64_t p = A.fo[e * 6 + f] + r;
-      const double* s0 = sG + le * nn + base;
+      const R* s0 = sG + le * nn + base;
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
-        double acc = 0.0;
-        for (int j = 0; j < nd; ++j) acc += lb[j] * s0[k * T + j * sdd];
-        trg[k * A.fn + p] = acc;
+        R acc = cst<R>(0.0f);
+        for (int j = 0; j < nd; ++j) acc += (side ? Tab<R>::lp(nd, j) : Tab<R>::lm(nd, j)) * s0[k * T + j * sdd];
+        SR::put(trg, k * A.fn + p, acc);
       }
     }
   }
   // ---- nodal contravariant fluxes (own node only: no cross-node hazard) ----
-  for (int i = threadIdx.x; i < T; i += blockDim.x) nodal_fluxes<DIM>(sq, sA, sG, T, i, G);
+  for (int i = threadIdx.x; i < T; i += blockDim.x) nodal_fluxes<R, DIM>(sq, sA, sG, T, i, G);
   __syncthreads();
   // ---- weak-form divergence ----
   for (int i = threadIdx.x; i < T; i += blockDim.x) {
-    double acc[5];
-    divergence<DIM>(sD, sA, T, nn, i, n0, n1, n2, acc);
+    R acc[5];
+    divergence<R, DIM>(sD, sA, T, nn, i, n0, n1, n2, acc);
     const int le = i / nn, node = i - le * nn;
     const int e = A.tile_elems[t.first + le];
-    double* ve = vol + (size_t)5 * A.off[e];
+    const size_t ve = (size_t)5 * A.off[e] + node;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) ve[v * nn + node] = acc[v];
+    for (int v = 0; v < 5; ++v) SR::put(vol, ve + v * nn, acc[v]);
   }
 }
 
@@ -803,10 +955,12 @@ struct RKArgs {
   double* qupd;       // state updated in place
 };
 
-template <int DIM>
-__global__ void __launch_bounds__(kTileNodes) k_surface(LevelArgs A, const double* __restrict__ vol,
-                                                        const double* __restrict__ fst, const double* __restrict__ s,
-                                                        double* __restrict__ r, double* norm, RKArgs rk) {
+template <typename R, int DIM>
+__global__ void __launch_bounds__(kTileNodes) k_surface(LevelArgsT<R> A, const typename Store<R>::T* __restrict__ vol,
+                                                        const typename Store<R>::T* __restrict__ fst,
+                                                        const double* __restrict__ s, double* __restrict__ r,
+                                                        double* norm, RKArgs rk) {
+  using SR = Store<R>;
   const ElemTile t = A.tiles[blockIdx.x];
   const int n0 = t.n[0], n1 = t.n[1], n2 = t.n[2];
   const int nn = n0 * n1 * n2;
@@ -818,23 +972,23 @@ __global__ void __launch_bounds__(kTileNodes) k_surface(LevelArgs A, const doubl
     const int e = A.tile_elems[t.first + le];
     const int idx0 = node % n0, idx1 = (node / n0) % n1, idx2 = node / (n0 * n1);
     const size_t base = (size_t)5 * A.off[e] + node;
-    double acc[5];
+    R acc[5];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) acc[v] = vol[base + v * nn];
+    for (int v = 0; v < 5; ++v) acc[v] = SR::get(vol, base + v * nn);
 #pragma unroll
     for (int f = 0; f < 2 * DIM; ++f) {
       int d, ta, tb, side;
       face_dirs(f, d, ta, tb, side);
       const int nd = pick(d, n0, n1, n2), id = pick(d, idx0, idx1, idx2);
-      const double lw = side ? c_tab.lpw[nd][id] : c_tab.lmw[nd][id];
+      const R lw = side ? Tab<R>::lpw(nd, id) : Tab<R>::lmw(nd, id);
       const int64_t p = A.fo[e * 6 + f] + pick(tb, idx0, idx1, idx2) * pick(ta, n0, n1, n2) + pick(ta, idx0, idx1, idx2);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) acc[v] += lw * fst[v * A.fn + p];
+      for (int v = 0; v < 5; ++v) acc[v] += lw * SR::get(fst, v * A.fn + p);
     }
-    const double iJ = A.geo[9 * A.nodes + A.off[e] + node];
+    const R iJ = SR::get(A.geo, 9 * A.nodes + A.off[e] + node);
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      double rv = (s ? s[base + v * nn] : 0.0) - acc[v] * iJ;
+      const double rv = (s ? s[base + v * nn] : 0.0) - to_double(acc[v] * iJ);
       lmax = (rv != rv) ? INFINITY : fmax(lmax, fabs(rv));  // a NaN residual reads as +inf
       if (rk.stage < 0) {
         r[base + v * nn] = rv;
@@ -861,46 +1015,46 @@ struct TauArgs {
   int dir, slot;
 };
 
-template <int DIM, bool AFFINE>
-__global__ void __launch_bounds__(kTileNodes) k_isolated(LevelArgs A, Params P, const double* __restrict__ q,
+template <typename R, int DIM, bool AFFINE>
+__global__ void __launch_bounds__(kTileNodes) k_isolated(LevelArgsT<R> A, GasT<R> G, const double* __restrict__ q,
                                                          const double* __restrict__ s, double* __restrict__ r,
                                                          TauArgs tau) {
-  extern __shared__ double smem[];
+  using SR = Store<R>;
+  extern __shared__ double smem_raw[];
   const ElemTile t = A.tiles[blockIdx.x];
   const int n0 = t.n[0], n1 = t.n[1], n2 = t.n[2];
   const int nn = n0 * n1 * n2;
   const int T = t.count * nn;
-  const Gas G = make_gas(P);
-  double* sD = smem;
-  double* sq = sD + 3 * kNP * kNP;
-  double* sA = sq + 5 * T;
-  double* sG = sA + 15 * T;
-  load_dtables(sD, c_D, n0, n1, n2, DIM);
-  stage_tile(A, t, nn, T, G, q, sq, sA);
+  R* sD = reinterpret_cast<R*>(smem_raw);
+  R* sq = sD + 3 * kNP * kNP;
+  R* sA = sq + 5 * T;
+  R* sG = sA + 15 * T;
+  load_dtables<R>(sD, Tab<R>::Dcol(), n0, n1, n2, DIM);
+  stage_tile<R>(A, t, nn, T, G, q, sq, sA);
   __syncthreads();
   for (int i = threadIdx.x; i < T; i += blockDim.x) {
-    double g[12];
-    gradient_volume<DIM, AFFINE>(sD, sA, T, nn, i, n0, n1, n2, g);
+    R g[12];
+    gradient_volume<R, DIM, AFFINE>(sD, sA, T, nn, i, n0, n1, n2, g);
     const int le = i / nn, node = i - le * nn;
     const int e = A.tile_elems[t.first + le];
-    const double iJ = A.geo[9 * A.nodes + A.off[e] + node];
+    const R iJ = SR::get(A.geo, 9 * A.nodes + A.off[e] + node);
 #pragma unroll
     for (int k = 0; k < 12; ++k) sG[k * T + i] = g[k] * iJ;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < T; i += blockDim.x) nodal_fluxes<DIM>(sq, sA, sG, T, i, G);
+  for (int i = threadIdx.x; i < T; i += blockDim.x) nodal_fluxes<R, DIM>(sq, sA, sG, T, i, G);
   __syncthreads();
   for (int i = threadIdx.x; i < T; i += blockDim.x) {
-    double acc[5];
-    divergence<DIM>(sD, sA, T, nn, i, n0, n1, n2, acc);
+    R acc[5];
+    divergence<R, DIM>(sD, sA, T, nn, i, n0, n1, n2, acc);
     const int le = i / nn, node = i - le * nn;
     const int e = A.tile_elems[t.first + le];
-    const double iJ = A.geo[9 * A.nodes + A.off[e] + node];
+    const R iJ = SR::get(A.geo, 9 * A.nodes + A.off[e] + node);
     const size_t base = (size_t)5 * A.off[e] + node;
     double tmax = 0.0;
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      double rv = (s ? s[base + v * nn] : 0.0) - acc[v] * iJ;
+      const double rv = (s ? s[base + v * nn] : 0.0) - to_double(acc[v] * iJ);
       if (tau.table) {
         double tv = tau.rho ? rv - tau.rho[base + v * nn] : rv;
         tmax = fmax(tmax, fabs(tv));
@@ -914,15 +1068,15 @@ __global__ void __launch_bounds__(kTileNodes) k_isolated(LevelArgs A, Params P, 
 }
 
 // ---------------------------------------------------------------------------
-// k_cfl: global minimum of the explicit step
+// k_cfl: global minimum of the explicit step (FP64)
 // ---------------------------------------------------------------------------
 template <int DIM>
-__global__ void __launch_bounds__(kTileNodes) k_cfl(LevelArgs A, Params P, const double* __restrict__ q, double* dtmin) {
+__global__ void __launch_bounds__(kTileNodes) k_cfl(LevelArgsT<double> A, GasD G, const double* __restrict__ q,
+                                                    double* dtmin) {
   const ElemTile t = A.tiles[blockIdx.x];
   const int n0 = t.n[0], n1 = t.n[1], n2 = t.n[2];
   const int nn = n0 * n1 * n2;
   const int T = t.count * nn;
-  const Gas G = make_gas(P);
   double best = 1e300;
   for (int i = threadIdx.x; i < T; i += blockDim.x) {
     int le = i / nn, node = i - le * nn;
@@ -932,11 +1086,13 @@ __global__ void __launch_bounds__(kTileNodes) k_cfl(LevelArgs A, Params P, const
     double qq[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) qq[v] = qe[v * nn + node];
-    double ir, u[3], p, Tt;
-    to_prim(qq, G, ir, u, p, Tt);
+    const double ir = 1.0 / qq[0];
+    const double u0 = qq[1] * ir, u1 = qq[2] * ir, u2 = qq[3] * ir;
+    const double p = G.g1 * (qq[4] - 0.5 * (qq[1] * u0 + qq[2] * u1 + qq[3] * u2));
+    const double Tt = G.gM2 * p * ir;
     const double c = sqrt(G.g * p * ir);
-    const double vel = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    const double nu = mu_of_T(Tt, G) * ir * G.invRe;
+    const double vel = sqrt(u0 * u0 + u1 * u1 + u2 * u2);
+    const double nu = Tt * sqrt(Tt) * G.Su1 / (Tt + G.Su) * ir * G.invRe;
     const double iJ = A.geo[9 * A.nodes + gn];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
@@ -1042,11 +1198,11 @@ static size_t vol_smem(const Level* L) {
   return (size_t)(3 * kNP * kNP + 32 * L->tile_smem_nodes) * sizeof(double);
 }
 
-template <int DIM, bool AFF>
+template <typename R, int DIM, bool AFF>
 static int set_attrs() {
   const int big = (int)((3 * kNP * kNP + 32 * kMaxElemNodes) * sizeof(double));
-  DG_CUDA_TRY(cudaFuncSetAttribute(k_volume<DIM, AFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  DG_CUDA_TRY(cudaFuncSetAttribute(k_isolated<DIM, AFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  DG_CUDA_TRY(cudaFuncSetAttribute(k_volume<R, DIM, AFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  DG_CUDA_TRY(cudaFuncSetAttribute(k_isolated<R, DIM, AFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   return DG_OK;
 }
 
@@ -1056,10 +1212,14 @@ static int configure_smem() {
   DG_CUDA_TRY(cudaGetDevice(&dev));
   if (done_dev == dev) return DG_OK;
   int rc;
-  if ((rc = set_attrs<2, false>()) != DG_OK) return rc;
-  if ((rc = set_attrs<2, true>()) != DG_OK) return rc;
-  if ((rc = set_attrs<3, false>()) != DG_OK) return rc;
-  if ((rc = set_attrs<3, true>()) != DG_OK) return rc;
+  if ((rc = set_attrs<double, 2, false>()) != DG_OK) return rc;
+  if ((rc = set_attrs<double, 2, true>()) != DG_OK) return rc;
+  if ((rc = set_attrs<double, 3, false>()) != DG_OK) return rc;
+  if ((rc = set_attrs<double, 3, true>()) != DG_OK) return rc;
+  if ((rc = set_attrs<dd, 2, false>()) != DG_OK) return rc;
+  if ((rc = set_attrs<dd, 2, true>()) != DG_OK) return rc;
+  if ((rc = set_attrs<dd, 3, false>()) != DG_OK) return rc;
+  if ((rc = set_attrs<dd, 3, true>()) != DG_OK) return rc;
   DG_CUDA_TRY(cudaFuncSetAttribute(k_transfer, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)(2 * kTransferMaxSlab * sizeof(double))));
   done_dev = dev;
@@ -1100,80 +1260,113 @@ int read_scalar(const double* d, double* h, cudaStream_t st) {
   return DG_OK;
 }
 
-// ---- per-kernel launch helpers (dimension / affine dispatch) ----
-static void launch_trace(const Level* L, const LevelArgs& A, const double* q, cudaStream_t st) {
-  ++g_launches;
-  const size_t sm = 5 * L->tile_smem_nodes * sizeof(double);
-  if (L->dim == 2)
-    k_trace_q<2><<<L->n_tiles, kTileNodes, sm, st>>>(A, q, L->d_trq);
-  else
-    k_trace_q<3><<<L->n_tiles, kTileNodes, sm, st>>>(A, q, L->d_trq);
-}
-static void launch_volume(const Level* L, const LevelArgs& A, const Params& P, const double* q, cudaStream_t st) {
-  ++g_launches;
-  const size_t sm = vol_smem(L);
-  if (L->dim == 2) {
-    if (L->affine)
-      k_volume<2, true><<<L->n_tiles, kTileNodes, sm, st>>>(A, P, q, L->d_ust, L->d_trg, L->d_vol);
-    else
-      k_volume<2, false><<<L->n_tiles, kTileNodes, sm, st>>>(A, P, q, L->d_ust, L->d_trg, L->d_vol);
-  } else {
-    if (L->affine)
-      k_volume<3, true><<<L->n_tiles, kTileNodes, sm, st>>>(A, P, q, L->d_ust, L->d_trg, L->d_vol);
-    else
-      k_volume<3, false><<<L->n_tiles, kTileNodes, sm, st>>>(A, P, q, L->d_ust, L->d_trg, L->d_vol);
+// float-pair copies of a level's geometry (double-float kernels), made once
+__global__ void k_split(const double* __restrict__ x, float2* __restrict__ y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    const float h = (float)v;
+    y[i] = make_float2(h, (float)(v - (double)h));
   }
 }
-template <typename TA>
-static void launch_isolated(const Level* L, const LevelArgs& A, const Params& P, const double* q, const double* s,
-                            double* r, const TA& ta, cudaStream_t st) {
+static int split_array(const double* x, double** y, int64_t n, cudaStream_t st) {
+  DG_CUDA_TRY(cudaMalloc((void**)y, std::max<int64_t>(1, n) * sizeof(float2)));
   ++g_launches;
-  const size_t sm = vol_smem(L);
-  if (L->dim == 2) {
-    if (L->affine)
-      k_isolated<2, true><<<L->n_tiles, kTileNodes, sm, st>>>(A, P, q, s, r, ta);
-    else
-      k_isolated<2, false><<<L->n_tiles, kTileNodes, sm, st>>>(A, P, q, s, r, ta);
-  } else {
-    if (L->affine)
-      k_isolated<3, true><<<L->n_tiles, kTileNodes, sm, st>>>(A, P, q, s, r, ta);
-    else
-      k_isolated<3, false><<<L->n_tiles, kTileNodes, sm, st>>>(A, P, q, s, r, ta);
-  }
+  k_split<<<grid_for(n), 256, 0, st>>>(x, reinterpret_cast<float2*>(*y), n);
+  DG_CUDA_TRY(cudaGetLastError());
+  return DG_OK;
 }
-static void launch_surface(const Level* L, const LevelArgs& A, const double* s, double* r, double* norm,
-                           const RKArgs& rk, cudaStream_t st) {
-  ++g_launches;
-  if (L->dim == 2)
-    k_surface<2><<<L->n_tiles, kTileNodes, 0, st>>>(A, L->d_vol, L->d_fst, s, r, norm, rk);
-  else
-    k_surface<3><<<L->n_tiles, kTileNodes, 0, st>>>(A, L->d_vol, L->d_fst, s, r, norm, rk);
-}
-static void launch_mortar(int pass, const Level* L, const LevelArgs& A, const MortarArgs& MA, const Params& P,
-                          cudaStream_t st) {
-  ++g_launches;
-  if (pass == 1)
-    k_mortar<1><<<L->n_mtiles, kMortarTile, 0, st>>>(A, MA, P, L->d_trq, nullptr, L->d_ust);
-  else
-    k_mortar<2><<<L->n_mtiles, kMortarTile, 0, st>>>(A, MA, P, L->d_trq, L->d_trg, L->d_fst);
+static int ensure_dd(Level* L, cudaStream_t st) {
+  if (L->d_geo2) return DG_OK;
+  int rc;
+  if ((rc = split_array(L->d_geo, &L->d_geo2, 10 * L->nodes, st)) != DG_OK) return rc;
+  if ((rc = split_array(L->d_fnS, &L->d_fnS2, 3 * L->face_nodes, st)) != DG_OK) return rc;
+  return split_array(L->d_mnS, &L->d_mnS2, 3 * L->mortar_nodes, st);
 }
 
-int residual(const dg_mesh* m, Level* L, const double* q, const double* s, double* r, bool isolated,
-             cudaStream_t st, double* d_norm, int rk_stage, double* rk_g, const double* d_dt) {
-  int rc = configure_smem();
-  if (rc != DG_OK) return rc;
-  LevelArgs A = largs(L);
-  if (isolated) {
-    TauArgs ta{nullptr, nullptr, nullptr, 0, 0};
-    launch_isolated(L, A, m->prm, q, s, r, ta, st);
-    DG_CUDA_TRY(cudaGetLastError());
-    return DG_OK;
+int prepare_arith(const dg_mesh* m, Level* L, cudaStream_t st) {
+  return (m->arith == DG_ARITH_DF32) ? ensure_dd(L, st) : DG_OK;
+}
+
+// ---- per-kernel launch helpers (arithmetic / dimension / affine dispatch) ----
+template <typename R>
+using ST = typename Store<R>::T;
+
+template <typename R>
+static ST<R>* buf(double* p) {
+  return reinterpret_cast<ST<R>*>(p);
+}
+
+template <typename R>
+static void launch_trace(const Level* L, const double* q, cudaStream_t st) {
+  ++g_launches;
+  const size_t sm = 5 * L->tile_smem_nodes * sizeof(double);
+  LevelArgsT<R> A = largs<R>(L);
+  if (L->dim == 2)
+    k_trace_q<R, 2><<<L->n_tiles, kTileNodes, sm, st>>>(A, q, buf<R>(L->d_trq));
+  else
+    k_trace_q<R, 3><<<L->n_tiles, kTileNodes, sm, st>>>(A, q, buf<R>(L->d_trq));
+}
+template <typename R>
+static void launch_volume(const Level* L, const GasT<R>& G, const double* q, cudaStream_t st) {
+  ++g_launches;
+  const size_t sm = vol_smem(L);
+  LevelArgsT<R> A = largs<R>(L);
+  const ST<R>* ust = buf<R>(L->d_ust);
+  ST<R>* trg = buf<R>(L->d_trg);
+  ST<R>* vol = buf<R>(L->d_vol);
+  if (L->dim == 2) {
+    if (L->affine)
+      k_volume<R, 2, true><<<L->n_tiles, kTileNodes, sm, st>>>(A, G, q, ust, trg, vol);
+    else
+      k_volume<R, 2, false><<<L->n_tiles, kTileNodes, sm, st>>>(A, G, q, ust, trg, vol);
+  } else {
+    if (L->affine)
+      k_volume<R, 3, true><<<L->n_tiles, kTileNodes, sm, st>>>(A, G, q, ust, trg, vol);
+    else
+      k_volume<R, 3, false><<<L->n_tiles, kTileNodes, sm, st>>>(A, G, q, ust, trg, vol);
   }
-  MortarArgs MA = margs(L);
-  launch_trace(L, A, q, st);
-  launch_mortar(1, L, A, MA, m->prm, st);
-  launch_volume(L, A, m->prm, q, st);
-  launch_mortar(2, L, A, MA, m->prm, st);
+}
+template <typename R>
+static void launch_isolated(const Level* L, const GasT<R>& G, const double* q, const double* s, double* r,
+                            const TauArgs& ta, cudaStream_t st) {
+  ++g_launches;
+  const size_t sm = vol_smem(L);
+  LevelArgsT<R> A = largs<R>(L);
+  if (L->dim == 2) {
+    if (L->affine)
+      k_isolated<R, 2, true><<<L->n_tiles, kTileNodes, sm, st>>>(A, G, q, s, r, ta);
+    else
+      k_isolated<R, 2, false><<<L->n_tiles, kTileNodes, sm, st>>>(A, G, q, s, r, ta);
+  } else {
+    if (L->affine)
+      k_isolated<R, 3, true><<<L->n_tiles, kTileNodes, sm, st>>>(A, G, q, s, r, ta);
+    else
+      k_isolated<R, 3, false><<<L->n_tiles, kTileNodes, sm, st>>>(A, G, q, s, r, ta);
+  }
+}
+template <typename R>
+static void launch_surface(const Level* L, const double* s, double* r, double* norm, const RKArgs& rk,
+                           cudaStream_t st) {
+  ++g_launches;
+  LevelArgsT<R> A = largs<R>(L);
+  if (L->dim == 2)
+    k_surface<R, 2><<<L->n_tiles, kTileNodes, 0, st>>>(A, buf<R>(L->d_vol), buf<R>(L->d_fst), s, r, norm, rk);
+  else
+    k_surface<R, 3><<<L->n_tiles, kTileNodes, 0, st>>>(A, buf<R>(L->d_vol), buf<R>(L->d_fst), s, r, norm, rk);
+}
+template <typename R>
+static void launch_mortar(int pass, const Level* L, const GasT<R>& G, cudaStream_t st) {
+  ++g_launches;
+  LevelArgsT<R> A = largs<R>(L);
+  MortarArgsT<R> MA = margs<R>(L);
+  if (pass == 1)
+    k_mortar<R, 1><<<L->n_mtiles, kMortarTile, 0, st>>>(A, MA, G, buf<R>(L->d_trq), nullptr, buf<R>(L->d_ust));
+  else
+    k_mortar<R, 2><<<L->n_mtiles, kMortarTile, 0, st>>>(A, MA, G, buf<R>(L->d_trq), buf<R>(L->d_trg),
+                                                        buf<R>(L->d_fst));
+}
+
+static RKArgs rk_args(int rk_stage, double* rk_g, const double* d_dt, const double* q) {
   RKArgs rk;
   rk.stage = rk_stage;
   rk.a = (rk_stage == 1) ? -5.0 / 9.0 : (rk_stage == 2 ? -153.0 / 128.0 : 0.0);
@@ -1181,27 +1374,44 @@ int residual(const dg_mesh* m, Level* L, const double* q, const double* s, doubl
   rk.g = rk_g;
   rk.dt = d_dt;
   rk.qupd = const_cast<double*>(q);
-  launch_surface(L, A, s, r, d_norm, rk, st);
+  return rk;
+}
+
+template <typename R>
+static int residual_t(const dg_mesh* m, Level* L, const double* q, const double* s, double* r, bool isolated,
+                      cudaStream_t st, double* d_norm, int rk_stage, double* rk_g, const double* d_dt) {
+  const GasT<R> G = make_gas<R>(m->prm);
+  if (isolated) {
+    TauArgs ta{nullptr, nullptr, nullptr, 0, 0};
+    launch_isolated<R>(L, G, q, s, r, ta, st);
+    DG_CUDA_TRY(cudaGetLastError());
+    return DG_OK;
+  }
+  launch_trace<R>(L, q, st);
+  launch_mortar<R>(1, L, G, st);
+  launch_volume<R>(L, G, q, st);
+  launch_mortar<R>(2, L, G, st);
+  launch_surface<R>(L, s, r, d_norm, rk_args(rk_stage, rk_g, d_dt, q), st);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
 }
 
-int profile_residual(const dg_mesh* m, Level* L, const double* q, const double* s, double* r, int iters,
-                     double* ms_out, cudaStream_t st) {
-  // One full evaluation fills every intermediate buffer; then each stage is
-  // launched `iters` times back to back between two events on `st` (each
-  // stage rewrites only its own outputs, so repeats are idempotent) and the
-  // mean duration per launch is reported.
-  int rc = residual(m, L, q, s, r, false, st, nullptr, -1, nullptr, nullptr);
+int residual(const dg_mesh* m, Level* L, const double* q, const double* s, double* r, bool isolated,
+             cudaStream_t st, double* d_norm, int rk_stage, double* rk_g, const double* d_dt) {
+  int rc = configure_smem();
   if (rc != DG_OK) return rc;
-  LevelArgs A = largs(L);
-  MortarArgs MA = margs(L);
-  RKArgs rk;
-  rk.stage = -1;
-  rk.a = rk.b = 0.0;
-  rk.g = nullptr;
-  rk.dt = nullptr;
-  rk.qupd = nullptr;
+  if (m->arith == DG_ARITH_DF32) {
+    if ((rc = ensure_dd(L, st)) != DG_OK) return rc;
+    return residual_t<dd>(m, L, q, s, r, isolated, st, d_norm, rk_stage, rk_g, d_dt);
+  }
+  return residual_t<double>(m, L, q, s, r, isolated, st, d_norm, rk_stage, rk_g, d_dt);
+}
+
+template <typename R>
+static int profile_t(const dg_mesh* m, Level* L, const double* q, const double* s, double* r, int iters,
+                     double* ms_out, cudaStream_t st) {
+  const GasT<R> G = make_gas<R>(m->prm);
+  RKArgs rk = rk_args(-1, nullptr, nullptr, nullptr);
   TauArgs ta{nullptr, nullptr, nullptr, 0, 0};
   cudaEvent_t e0, e1;
   DG_CUDA_TRY(cudaEventCreate(&e0));
@@ -1210,12 +1420,12 @@ int profile_residual(const dg_mesh* m, Level* L, const double* q, const double* 
     DG_CUDA_TRY(cudaEventRecord(e0, st));
     for (int it = 0; it < iters; ++it) {
       switch (k) {
-        case 0: launch_trace(L, A, q, st); break;
-        case 1: launch_mortar(1, L, A, MA, m->prm, st); break;
-        case 2: launch_volume(L, A, m->prm, q, st); break;
-        case 3: launch_mortar(2, L, A, MA, m->prm, st); break;
-        case 4: launch_surface(L, A, s, r, nullptr, rk, st); break;
-        default: launch_isolated(L, A, m->prm, q, s, r, ta, st); break;
+        case 0: launch_trace<R>(L, q, st); break;
+        case 1: launch_mortar<R>(1, L, G, st); break;
+        case 2: launch_volume<R>(L, G, q, st); break;
+        case 3: launch_mortar<R>(2, L, G, st); break;
+        case 4: launch_surface<R>(L, s, r, nullptr, rk, st); break;
+        default: launch_isolated<R>(L, G, q, s, r, ta, st); break;
       }
     }
     DG_CUDA_TRY(cudaEventRecord(e1, st));
@@ -1230,14 +1440,27 @@ int profile_residual(const dg_mesh* m, Level* L, const double* q, const double* 
   return DG_OK;
 }
 
+int profile_residual(const dg_mesh* m, Level* L, const double* q, const double* s, double* r, int iters,
+                     double* ms_out, cudaStream_t st) {
+  // One full evaluation fills every intermediate buffer; then each stage is
+  // launched `iters` times back to back between two events on `st` (each
+  // stage rewrites only its own outputs, so repeats are idempotent) and the
+  // mean duration per launch is reported.
+  int rc = residual(m, L, q, s, r, false, st, nullptr, -1, nullptr, nullptr);
+  if (rc != DG_OK) return rc;
+  if (m->arith == DG_ARITH_DF32) return profile_t<dd>(m, L, q, s, r, iters, ms_out, st);
+  return profile_t<double>(m, L, q, s, r, iters, ms_out, st);
+}
+
 int cfl_dt(const dg_mesh* m, Level* L, const double* q, double* d_dt, cudaStream_t st) {
   int rc = reset_min(d_dt, st);
   if (rc != DG_OK) return rc;
   ++g_launches;
+  const GasD G = make_gas_d(m->prm);
   if (L->dim == 2)
-    k_cfl<2><<<L->n_tiles, kTileNodes, 0, st>>>(largs(L), m->prm, q, d_dt);
+    k_cfl<2><<<L->n_tiles, kTileNodes, 0, st>>>(largs<double>(L), G, q, d_dt);
   else
-    k_cfl<3><<<L->n_tiles, kTileNodes, 0, st>>>(largs(L), m->prm, q, d_dt);
+    k_cfl<3><<<L->n_tiles, kTileNodes, 0, st>>>(largs<double>(L), G, q, d_dt);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
 }
@@ -1282,12 +1505,17 @@ int tau_accumulate(const dg_mesh* m, Level* L, const double* q, const double* s,
     return tau_reduce(L, L->d_R, rho, dir, slot, fine_orders_dev, d_tau, st);
   }
   TauArgs ta{rho, d_tau, fine_orders_dev, dir, slot};
-  launch_isolated(L, largs(L), m->prm, q, s, nullptr, ta, st);
+  if (m->arith == DG_ARITH_DF32) {
+    if ((rc = ensure_dd(L, st)) != DG_OK) return rc;
+    launch_isolated<dd>(L, make_gas<dd>(m->prm), q, s, nullptr, ta, st);
+  } else {
+    launch_isolated<double>(L, make_gas<double>(m->prm), q, s, nullptr, ta, st);
+  }
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
 }
 
-__global__ void k_tau_reduce(LevelArgs A, const double* __restrict__ r, const double* __restrict__ rho, int dir,
+__global__ void k_tau_reduce(LevelArgsT<double> A, const double* __restrict__ r, const double* __restrict__ rho, int dir,
                              int slot, const int32_t* __restrict__ fine_orders, double* table) {
   const ElemTile t = A.tiles[blockIdx.x];
   const int nn = t.n[0] * t.n[1] * t.n[2];
@@ -1308,7 +1536,7 @@ __global__ void k_tau_reduce(LevelArgs A, const double* __restrict__ r, const do
 static int tau_reduce(const Level* L, const double* r, const double* rho, int dir, int slot,
                       const int32_t* fine_orders, double* table, cudaStream_t st) {
   ++g_launches;
-  k_tau_reduce<<<L->n_tiles, kTileNodes, 0, st>>>(largs(L), r, rho, dir, slot, fine_orders, table);
+  k_tau_reduce<<<L->n_tiles, kTileNodes, 0, st>>>(largs<double>(L), r, rho, dir, slot, fine_orders, table);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
 }

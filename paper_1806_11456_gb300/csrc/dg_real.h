@@ -1,0 +1,121 @@
+// Arithmetic types of the operator kernels.
+//
+// R = double : native FP64 (2 DFMA per clock per SM on GB300).
+// R = dd     : "double-float", an unevaluated sum hi + lo of two FP32 numbers
+//              (|lo| <= ulp(hi)/2), about 48 significant bits, evaluated on
+//              the FP32 pipes (128 lanes per clock per SM).  Built from the
+//              classical error-free transformations: Knuth's TwoSum, Dekker's
+//              FastTwoSum, and the FMA form of TwoProd (Dekker 1971; Knuth,
+//              TAOCP vol. 2, 4.2.2).  Division and square root take one
+//              Newton/Karp correction on top of the FP32 result.
+// Every kernel loads and stores FP64 in memory; the state update of the
+// smoother stays in FP64.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+namespace dg {
+
+#define DGR __device__ __forceinline__
+
+struct dd {
+  float hi, lo;
+  DGR dd() = default;
+  DGR constexpr dd(float h, float l) : hi(h), lo(l) {}
+  // exact split of a double into a (rounded-to-48-bit) pair
+  DGR explicit dd(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
+};
+
+DGR dd fast_two_sum(float a, float b) {  // requires |a| >= |b|
+  float s = a + b;
+  return dd(s, b - (s - a));
+}
+DGR dd two_sum(float a, float b) {
+  float s = a + b;
+  float bb = s - a;
+  return dd(s, (a - (s - bb)) + (b - bb));
+}
+DGR dd operator+(dd a, dd b) {
+  dd s = two_sum(a.hi, b.hi);
+  float e = s.lo + (a.lo + b.lo);
+  return fast_two_sum(s.hi, e);
+}
+DGR dd operator-(dd a) { return dd(-a.hi, -a.lo); }
+DGR dd operator-(dd a, dd b) { return a + (-b); }
+DGR dd operator*(dd a, dd b) {
+  float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return fast_two_sum(p, e);
+}
+DGR dd operator/(dd a, dd b) {
+  float q1 = a.hi / b.hi;
+  // remainder a - q1 * b, exactly enough for the correction
+  float p = q1 * b.hi;
+  float pe = fmaf(q1, b.hi, -p);
+  dd r = a - dd(p, pe) - dd(q1 * b.lo, 0.0f);
+  float q2 = r.hi / b.hi;
+  return fast_two_sum(q1, q2);
+}
+DGR dd& operator+=(dd& a, dd b) { return a = a + b; }
+DGR dd& operator-=(dd& a, dd b) { return a = a - b; }
+DGR dd& operator*=(dd& a, dd b) { return a = a * b; }
+DGR bool operator<(dd a, dd b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+DGR bool operator>(dd a, dd b) { return b < a; }
+DGR dd sqrt(dd a) {
+  if (a.hi <= 0.0f) return dd(0.0f, 0.0f);
+  float y = sqrtf(a.hi);
+  // Karp: sqrt(a) ~ y + (a - y^2) / (2 y)
+  float p = y * y;
+  float pe = fmaf(y, y, -p);
+  dd r = a - dd(p, pe);
+  return fast_two_sum(y, r.hi / (2.0f * y));
+}
+DGR dd fabs(dd a) { return (a.hi < 0.0f) ? -a : a; }
+DGR dd fmax(dd a, dd b) { return (a < b) ? b : a; }
+// the double versions live in the same namespace, so that the dd overloads
+// above do not hide them
+__host__ __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
+__host__ __device__ __forceinline__ double fabs(double x) { return ::fabs(x); }
+__host__ __device__ __forceinline__ double fmax(double a, double b) { return ::fmax(a, b); }
+__host__ __device__ __forceinline__ double fmin(double a, double b) { return ::fmin(a, b); }
+
+DGR double to_double(dd a) { return (double)a.hi + (double)a.lo; }
+DGR double to_double(double a) { return a; }
+DGR bool is_nan(dd a) { return a.hi != a.hi; }
+
+// ---- uniform helpers for generic kernel code ----
+template <typename R>
+DGR R from_double(double x);
+template <>
+DGR double from_double<double>(double x) {
+  return x;
+}
+template <>
+DGR dd from_double<dd>(double x) {
+  return dd(x);
+}
+
+// storage type of tables for R (double for R = double, float2 for R = dd)
+template <typename R>
+struct Store;
+template <>
+struct Store<double> {
+  using T = double;
+  static DGR double get(const double* p, size_t i) { return p[i]; }
+  static DGR void put(double* p, size_t i, double v) { p[i] = v; }
+};
+template <>
+struct Store<dd> {
+  using T = float2;
+  static DGR dd get(const float2* p, size_t i) {
+    float2 v = p[i];
+    return dd(v.x, v.y);
+  }
+  static DGR void put(float2* p, size_t i, dd v) { p[i] = make_float2(v.hi, v.lo); }
+};
+
+}  // namespace dg

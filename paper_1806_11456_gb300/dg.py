@@ -70,7 +70,9 @@ _ip = ctypes.POINTER(ctypes.c_int32)
 
 EXPORTS = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_layout", "dg_residual", "dg_cfl_dt", "dg_smooth",
            "dg_pmg_vcycle", "dg_tau_estimate", "dg_adapt", "dg_transfer_state", "dg_profile_residual",
-           "dg_kernel_launches", "dg_transfer_noalloc", "dg_solve_steady", "dg_mesh_orders", "dg_last_error"]
+           "dg_kernel_launches", "dg_transfer_noalloc", "dg_solve_steady", "dg_mesh_orders", "dg_set_arithmetic",
+           "dg_last_error"]
+ARITH = {"fp64": 0, "df32": 1}
 KERNEL_STAGES = ["trace_q", "mortar_u_star", "volume", "mortar_flux", "surface", "isolated"]
 
 
@@ -98,6 +100,7 @@ def lib(path=LIB_PATH):
     L.dg_solve_steady.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp, ctypes.POINTER(SolveParams), ALLOC_FN,
                                   _vp, ctypes.POINTER(SolveReport), _vp]
     L.dg_mesh_orders.argtypes = [_vp, _ip]
+    L.dg_set_arithmetic.argtypes = [_vp, ctypes.c_int]
     L.dg_transfer_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, _ip, _ip, ctypes.c_int32, _vp, _vp, _vp]
     _lib = L
     return L
@@ -165,6 +168,13 @@ class Mesh:
             self.close()
         except Exception:
             pass
+
+    def set_arithmetic(self, mode):
+        """'fp64' (native FP64) or 'df32' (double-float pairs on the FP32 pipes)
+        for the operator kernels."""
+        _check(lib().dg_set_arithmetic(self.h, ARITH[mode]))
+        self.arith = mode
+        return self
 
     def layout(self):
         n = ctypes.c_int64()

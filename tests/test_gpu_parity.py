@@ -80,12 +80,16 @@ def _cases():
 CASES = _cases()
 
 
+ARITHS = ["fp64", "df32"]
+
+
+@pytest.mark.parametrize("arith", ARITHS)
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("isolated", [False, True])
-def test_residual_parity(dg, name, isolated):
+def test_residual_parity(dg, name, isolated, arith):
     mesh, o, prm, q = CASES[name]()
     s = syn.random_source(mesh, o, 3)
-    M = dg.Mesh(mesh, o, prm)
+    M = dg.Mesh(mesh, o, prm).set_arithmetic(arith)
     r = M.residual(_dev(q), _dev(s), isolated=isolated).cpu().numpy()
     ro = orc.residual(mesh, o, prm, q, s, isolated)
     scale = orc.volume_scale(mesh, o, prm, q)
@@ -101,14 +105,15 @@ def test_residual_norm_and_null_source(dg):
     assert abs(rn - np.max(np.abs(ro))) <= TOL * orc.volume_scale(mesh, o, prm, q)
 
 
-def test_flat_plate_full_size_residual(dg):
+@pytest.mark.parametrize("arith", ARITHS)
+def test_flat_plate_full_size_residual(dg, arith):
     """The flat-plate workload at full size (60 x 24 elements, N = 7) on a
     perturbed boundary-layer-like state: every element compared."""
     mesh = syn.flat_plate_mesh()
     prm = syn.flow_params(mach=0.2, re=1e5)
     o = syn.uniform_orders(mesh["K"], 2, 7)
     q = syn.perturbed_state(mesh, o, prm, 21, amp=0.02)
-    M = dg.Mesh(mesh, o, prm)
+    M = dg.Mesh(mesh, o, prm).set_arithmetic(arith)
     r = M.residual(_dev(q)).cpu().numpy()
     ro = orc.residual(mesh, o, prm, q)
     assert np.max(np.abs(r - ro)) <= TOL * orc.volume_scale(mesh, o, prm, q)
@@ -141,10 +146,11 @@ def test_smoother_parity(dg, name):
     ("plate2d_all_bcs", dict(beta1=1, beta2=1, beta_c=1, direction=1)),
     ("curved_sphere_mortars", dict(beta1=1, beta2=1, beta_c=1, delta_n=1)),
 ])
-def test_vcycle_parity(dg, name, kw):
+@pytest.mark.parametrize("arith", ARITHS)
+def test_vcycle_parity(dg, name, kw, arith):
     mesh, o, prm, q = CASES[name]()
     s = syn.random_source(mesh, o, 5)
-    M = dg.Mesh(mesh, o, prm)
+    M = dg.Mesh(mesh, o, prm).set_arithmetic(arith)
     qd = _dev(q)
     rep = M.vcycle(qd, _dev(s), **kw)
     okw = dict(kw)
@@ -155,14 +161,15 @@ def test_vcycle_parity(dg, name, kw):
     assert np.max(np.abs(qd.cpu().numpy() - qo)) <= TOL * np.max(np.abs(qo))
 
 
+@pytest.mark.parametrize("arith", ARITHS)
 @pytest.mark.parametrize("corr,iso", [(True, True), (False, True), (True, False)])
-def test_tau_estimate_parity(dg, corr, iso):
+def test_tau_estimate_parity(dg, corr, iso, arith):
     mesh = syn.periodic_box(3, 3, 1, dim=2)
     prm = syn.flow_params(mach=0.3, re=100.0)
     o = syn.random_orders(mesh["K"], 2, 2, 6, 17)
     q = syn.manufactured_state(mesh, o, 1, prm[2], prm[0], amp=0.05)
     s = syn.random_source(mesh, o, 9, amp=1e-3)
-    M = dg.Mesh(mesh, o, prm)
+    M = dg.Mesh(mesh, o, prm).set_arithmetic(arith)
     t = M.tau_estimate(_dev(q), _dev(s), dir_mask=3, with_correction=corr, isolated=iso)
     to = orc.tau_estimate(mesh, o, prm, q, s, dir_mask=3, with_correction=corr, isolated=iso)
     assert np.array_equal(t < 0, to < 0)
@@ -301,7 +308,8 @@ def test_graph_replay_matches_direct_launches(dg):
     assert np.array_equal(qa.cpu().numpy(), qb.cpu().numpy())
 
 
-def test_sphere_full_size_residual(dg):
+@pytest.mark.parametrize("arith", ARITHS)
+def test_sphere_full_size_residual(dg, arith):
     """The cubed-sphere workload at full size: 6 x 12 x 12 x 16 = 13,824
     quadratic hexes, orders uniform in [1, 6]^3 (1.26 M nodes), every node
     compared for the full and the isolated operator, on a smooth perturbed
@@ -311,7 +319,7 @@ def test_sphere_full_size_residual(dg):
     orders.)"""
     mesh, o, prm = syn.config_sphere_c3()
     q = syn.smooth_state(mesh, o, prm, 3)
-    M = dg.Mesh(mesh, o, prm)
+    M = dg.Mesh(mesh, o, prm).set_arithmetic(arith)
     qd = _dev(q)
     scale = orc.volume_scale(mesh, o, prm, q)
     r = M.residual(qd).cpu().numpy()
