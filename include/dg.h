@@ -229,15 +229,17 @@ typedef struct {
   int32_t fmg;             /* 1: full-multigrid start from order 1, raising one order at a time */
   double fmg_tol;          /* residual to reach on a FMG level before raising the order (paper: 1e-1) */
   dg_mg_params mg;         /* cycle used in every phase */
-  int32_t adapt;           /* 1: converge to tau_max/10, estimate tau, adapt once, then converge to tol */
-  int32_t reserved0;
-  dg_adapt_params ap;      /* adaptation parameters (jump rule etc.) */
+  int32_t adapt;           /* 1: converge to tau_max/10, estimate tau, adapt, then converge to tol */
+  int32_t n_stages;        /* multi-stage adaptation (Sec. 3.3.4): 0 = single stage */
+  dg_adapt_params ap;      /* adaptation parameters (jump rule etc.; ap.cap = single-stage cap) */
+  int32_t stage_orders[4]; /* caps of the successive stages P_2 < P_3 < ... (the mesh enters at P_1) */
+  double ref_factor;       /* reference solves converge to ref_factor * tau_max (paper: 1/10; <= 0 means 0.1) */
 } dg_solve_params;
 
 typedef struct {
   int32_t cycles;          /* V-cycles in all phases */
   int32_t fmg_cycles;      /* of which on FMG levels below the reference orders */
-  int32_t adapted;         /* 1 if the order map changed */
+  int32_t adapted;         /* number of adaptations that changed the order map */
   int32_t status;          /* DG_OK, DG_ENOTCONVERGED or DG_EDIVERGED */
   double rnorm;            /* final max |r| */
   double rnorm_adapt;      /* max |r| when the tau estimate was taken */
@@ -256,7 +258,10 @@ typedef void* (*dg_alloc_fn)(size_t bytes, void* ctx);
  * until max |r| < tol -- or, with adapt = 1, until max |r| < tau_max/10
  * (Sec. 3.3.2 step 1), then the isolated anisotropic tau estimate, the order
  * selection and jump rules, a new mesh and the state transferred to it, and
- * V-cycles until max |r| < tol.
+ * V-cycles until max |r| < tol.  With n_stages > 0 the adaptation repeats in
+ * stages (Sec. 3.3.4): stage i caps the new orders at stage_orders[i] and is
+ * the last one when the largest uncapped required order is <= that cap (or
+ * when the stages run out); each stage first converges to tau_max/10.
  *  mesh, q   in/out: on adaptation *mesh is replaced by a new handle (the old
  *            one is destroyed) and *q by an array obtained from `alloc` (the
  *            old array stays the caller's).  s must be NULL when adapt = 1.

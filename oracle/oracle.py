@@ -488,7 +488,7 @@ def solve_steady(mesh, orders, prm, q, s, tol, max_cycles, mg, fmg=False, fmg_to
     the new order map, the state transferred, and V-cycles to tol.
     Returns (orders, q, report)."""
     dim = mesh["dim"]
-    rep = dict(cycles=0, fmg_cycles=0, adapted=False)
+    rep = dict(cycles=0, fmg_cycles=0, adapted=0)
     status = "ok"
     if fmg:
         top = int(orders[:, :dim].max())
@@ -508,21 +508,39 @@ def solve_steady(mesh, orders, prm, q, s, tol, max_cycles, mg, fmg=False, fmg_to
             q = transfer(dim, prev_o, orders, prev_q)
     rn = float("nan")
     if status == "ok":
-        target = adapt["tau_max"] / 10.0 if adapt else tol
+        target = adapt["tau_max"] * adapt.get("ref_factor", 0.1) if adapt else tol
         q, c, rn, status = _cycle_until(mesh, orders, prm, q, s, mg, target, max_cycles)
         rep["cycles"] += c
     if status == "ok" and adapt:
-        rep["rnorm_adapt"] = rn
-        t = tau_estimate(mesh, orders, prm, q, None, dir_mask=(1 << dim) - 1)
+        rep["adapted"] = 0
+        stages = list(adapt.get("stages", ()))
+        nst = max(1, len(stages))
         rule = {0: None, 1: "2d", 2: "3d"}[adapt.get("jump_rule", 0)]
-        new = adapt_orders(mesh, orders, t, adapt["tau_max"], adapt["n_min"], adapt["n_max"],
-                           cap=adapt.get("cap") or None, rule=rule)
-        if not np.array_equal(new, orders):
-            q = transfer(dim, orders, new, q)
-            orders = new
-            rep["adapted"] = True
-        q, c, rn, status = _cycle_until(mesh, orders, prm, q, None, mg, tol, max_cycles)
-        rep["cycles"] += c
+        for st_i in range(nst):
+            if st_i > 0:  # each stage starts from a state converged to tau_max/10
+                q, c, rn, status = _cycle_until(mesh, orders, prm, q, None, mg, adapt["tau_max"] * adapt.get("ref_factor", 0.1),
+                                                max_cycles)
+                rep["cycles"] += c
+                if status != "ok":
+                    break
+            rep["rnorm_adapt"] = rn
+            t = tau_estimate(mesh, orders, prm, q, None, dir_mask=(1 << dim) - 1)
+            cap = stages[st_i] if stages else (adapt.get("cap") or None)
+            last = True
+            if stages:
+                free = adapt_orders(mesh, orders, t, adapt["tau_max"], adapt["n_min"], adapt["n_max"], cap=None,
+                                    rule=rule)
+                last = st_i == nst - 1 or int(free.max()) <= cap
+            new = adapt_orders(mesh, orders, t, adapt["tau_max"], adapt["n_min"], adapt["n_max"], cap=cap, rule=rule)
+            if not np.array_equal(new, orders):
+                q = transfer(dim, orders, new, q)
+                orders = new
+                rep["adapted"] += 1
+            if last:
+                break
+        if status == "ok":
+            q, c, rn, status = _cycle_until(mesh, orders, prm, q, None, mg, tol, max_cycles)
+            rep["cycles"] += c
     rep["rnorm"] = rn
     rep["status"] = status
     return orders, q, rep

@@ -698,52 +698,79 @@ int dg_solve_steady(dg_mesh** meshp, double** qp, const double* s, const dg_solv
   }
   // ---- reference orders ----
   if (rc == DG_OK) {
-    double target = sp->adapt ? sp->ap.tau_max / 10.0 : sp->tol;
+    const double ref = sp->ref_factor > 0.0 ? sp->ref_factor : 0.1;
+    double target = sp->adapt ? sp->ap.tau_max * ref : sp->tol;
     int cyc = 0;
     rc = cycle_until(m, m->orders, m->fine.get(), q, s, mg, target, sp->max_cycles, st, &cyc, &rep->dof_evals, &rn);
     rep->cycles += cyc;
   }
-  // ---- adaptation (Sec. 3.3.2) ----
+  // ---- adaptation (Sec. 3.3.2), possibly in stages (Sec. 3.3.4) ----
   if (rc == DG_OK && sp->adapt) {
-    rep->rnorm_adapt = rn;
-    std::vector<double> tau((size_t)m->K * 3 * kTauSlots);
-    DG_TRY(dg_tau_estimate(m, q, nullptr, (1 << m->dim) - 1, 1, 1, tau.data(), stream));
-    std::vector<int32_t> no(m->orders.size());
-    DG_TRY(dg_adapt(m, tau.data(), &sp->ap, no.data()));
-    if (no != m->orders) {
-      dg_mesh_desc d;
-      d.dim = m->dim;
-      d.K = m->K;
-      d.M = m->M;
-      d.xmap = m->xmap.data();
-      d.ftab = m->ftab.data();
-      std::memcpy(d.params, m->raw_params, sizeof(d.params));
-      dg_mesh* nm = nullptr;
-      DG_TRY(dg_mesh_create(&d, no.data(), &nm));
-      nm->arith = m->arith;
-      double* nq = (double*)alloc((size_t)5 * nm->fine->nodes * sizeof(double), alloc_ctx);
-      if (!nq) {
-        dg_mesh_destroy(nm);
-        set_error("dg_solve_steady: allocator returned NULL");
-        return DG_ENOMEM;
+    const int nst = std::max(1, (int)sp->n_stages);
+    for (int stage = 0; stage < nst && rc == DG_OK; ++stage) {
+      if (stage > 0) {  // every stage starts from a state converged to tau_max/10
+        int cyc = 0;
+        const double ref = sp->ref_factor > 0.0 ? sp->ref_factor : 0.1;
+        rc = cycle_until(m, m->orders, m->fine.get(), q, nullptr, mg, sp->ap.tau_max * ref, sp->max_cycles, st,
+                         &cyc, &rep->dof_evals, &rn);
+        rep->cycles += cyc;
+        if (rc != DG_OK) break;
       }
-      rc = transfer(m, m->fine.get(), nm->fine.get(), 5, q, nq, st);
-      if (rc != DG_OK) {
-        dg_mesh_destroy(nm);
-        return rc;
+      rep->rnorm_adapt = rn;
+      std::vector<double> tau((size_t)m->K * 3 * kTauSlots);
+      DG_TRY(dg_tau_estimate(m, q, nullptr, (1 << m->dim) - 1, 1, 1, tau.data(), stream));
+      dg_adapt_params ap = sp->ap;
+      bool last = true;
+      if (sp->n_stages > 0) {
+        ap.cap = sp->stage_orders[stage];
+        dg_adapt_params un = sp->ap;
+        un.cap = 0;
+        std::vector<int32_t> free_orders(m->orders.size());
+        DG_TRY(dg_adapt(m, tau.data(), &un, free_orders.data()));
+        int need = 0;
+        for (int32_t v : free_orders) need = std::max(need, (int)v);
+        last = (stage == nst - 1) || need <= ap.cap;
       }
-      DG_CUDA_TRY(cudaStreamSynchronize(st));
-      dg_mesh_destroy(m);
-      m = nm;
-      q = nq;
-      *meshp = m;
-      *qp = q;
-      rep->adapted = 1;
+      std::vector<int32_t> no(m->orders.size());
+      DG_TRY(dg_adapt(m, tau.data(), &ap, no.data()));
+      if (no != m->orders) {
+        dg_mesh_desc d;
+        d.dim = m->dim;
+        d.K = m->K;
+        d.M = m->M;
+        d.xmap = m->xmap.data();
+        d.ftab = m->ftab.data();
+        std::memcpy(d.params, m->raw_params, sizeof(d.params));
+        dg_mesh* nm = nullptr;
+        DG_TRY(dg_mesh_create(&d, no.data(), &nm));
+        nm->arith = m->arith;
+        double* nq = (double*)alloc((size_t)5 * nm->fine->nodes * sizeof(double), alloc_ctx);
+        if (!nq) {
+          dg_mesh_destroy(nm);
+          set_error("dg_solve_steady: allocator returned NULL");
+          return DG_ENOMEM;
+        }
+        rc = transfer(m, m->fine.get(), nm->fine.get(), 5, q, nq, st);
+        if (rc != DG_OK) {
+          dg_mesh_destroy(nm);
+          return rc;
+        }
+        DG_CUDA_TRY(cudaStreamSynchronize(st));
+        dg_mesh_destroy(m);
+        m = nm;
+        q = nq;
+        *meshp = m;
+        *qp = q;
+        rep->adapted += 1;
+      }
+      if (last) break;
     }
-    int cyc = 0;
-    rc = cycle_until(m, m->orders, m->fine.get(), q, nullptr, mg, sp->tol, sp->max_cycles, st, &cyc,
-                     &rep->dof_evals, &rn);
-    rep->cycles += cyc;
+    if (rc == DG_OK) {
+      int cyc = 0;
+      rc = cycle_until(m, m->orders, m->fine.get(), q, nullptr, mg, sp->tol, sp->max_cycles, st, &cyc,
+                       &rep->dof_evals, &rn);
+      rep->cycles += cyc;
+    }
   }
   rep->rnorm = rn;
   rep->status = rc;

@@ -60,7 +60,8 @@ class AdaptParams(ctypes.Structure):
 class SolveParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_cycles", ctypes.c_int32), ("fmg", ctypes.c_int32),
                 ("fmg_tol", ctypes.c_double), ("mg", MGParams), ("adapt", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("ap", AdaptParams)]
+                ("n_stages", ctypes.c_int32), ("ap", AdaptParams), ("stage_orders", ctypes.c_int32 * 4),
+                ("ref_factor", ctypes.c_double)]
 
 
 _lib = None
@@ -240,7 +241,8 @@ class Mesh:
         return dict(zip(KERNEL_STAGES, ms.tolist()))
 
     def solve_steady(self, q, s=None, tol=1e-10, max_cycles=200, fmg=False, fmg_tol=1e-1, mg=None, adapt=False,
-                     tau_max=1e-4, n_min=1, n_max=7, jump_rule=1, conform_tag=-1, cap=0, stream=None):
+                     tau_max=1e-4, n_min=1, n_max=7, jump_rule=1, conform_tag=-1, cap=0, stages=(), ref_factor=0.1,
+                     stream=None):
         """Steady solve through dg_solve_steady.  Returns (q, report); with
         adaptation q is a new tensor on the adapted mesh, which this object
         then wraps (its orders are updated)."""
@@ -254,6 +256,12 @@ class Mesh:
             setattr(sp.mg, k, int(v))
         sp.ap.tau_max, sp.ap.n_min, sp.ap.n_max, sp.ap.cap, sp.ap.jump_rule, sp.ap.conform_tag = \
             float(tau_max), n_min, n_max, cap, jump_rule, conform_tag
+        if len(stages) > 4:
+            raise DGError("at most 4 adaptation stages")
+        sp.n_stages = len(stages)
+        sp.ref_factor = float(ref_factor)
+        for i, v in enumerate(stages):
+            sp.stage_orders[i] = int(v)
         keep = []
 
         def _alloc(nbytes, _ctx):
@@ -275,7 +283,7 @@ class Mesh:
             _check(lib().dg_mesh_orders(self.h, orders.ctypes.data_as(_ip)))
             self.orders = orders
             out = keep[-1]
-        report = dict(cycles=rep.cycles, fmg_cycles=rep.fmg_cycles, adapted=bool(rep.adapted), status=rep.status,
+        report = dict(cycles=rep.cycles, fmg_cycles=rep.fmg_cycles, adapted=int(rep.adapted), status=rep.status,
                       rnorm=rep.rnorm, rnorm_adapt=rep.rnorm_adapt, dof_evals=rep.dof_evals, nodes=rep.nodes)
         if rc not in (0, -4, -5):
             _check(rc)

@@ -529,6 +529,15 @@ def config_sphere_c3(seed=2, nt=12, nr=16):
     return mesh, orders, prm
 
 
+def compatible_source(mesh, orders, S, weights_times_J):
+    """Remove from each variable of the source its mean with respect to the
+    given nodal weights w J (node-major over the element-blocked layout): on a
+    periodic domain a steady state exists only for a source of zero integral."""
+    F = from_blocked(S, orders, mesh["dim"])
+    F = F - (F @ weights_times_J / weights_times_J.sum())[:, None]
+    return to_blocked(F, orders, mesh["dim"])
+
+
 def config_flat_plate_c2(N=7):
     """60x24 stretched 2D flat plate, uniform N, freestream start (Mach 0.2, Re 1e5)."""
     mesh = flat_plate_mesh()

@@ -326,3 +326,24 @@ def test_sphere_full_size_residual(dg, arith):
     assert np.max(np.abs(r - orc.residual(mesh, o, prm, q))) <= TOL * scale
     ri = M.residual(qd, isolated=True).cpu().numpy()
     assert np.max(np.abs(ri - orc.residual(mesh, o, prm, q, None, True))) <= TOL * scale
+
+
+def test_solve_steady_multistage_parity(dg):
+    """Two adaptation stages capped at orders 3 then 5 (Sec. 3.3.4): orders and
+    states after two final cycles compared with the oracle's driver."""
+    mesh = syn.periodic_box(3, 2, 1, dim=2)
+    prm = syn.flow_params(mach=0.3, re=100.0)
+    P = syn.uniform_orders(mesh["K"], 2, 4)
+    q = syn.manufactured_state(mesh, P, 6, prm[2], prm[0], amp=0.05)
+    mg = dict(beta1=1, beta2=1, beta_c=2, direction=-1, coarsest=1, delta_n=1)
+    tau_max = 12.0
+    ref = 1e6  # reference solves accept the given state at once: the stage logic is what is compared
+    M = dg.Mesh(mesh, P, prm)
+    qd, rep = M.solve_steady(_dev(q), None, tol=1e-30, max_cycles=2, mg=mg, adapt=True, tau_max=tau_max,
+                             n_min=1, n_max=7, jump_rule=1, stages=(3, 5), ref_factor=ref)
+    ap = dict(tau_max=tau_max, n_min=1, n_max=7, jump_rule=1, stages=(3, 5), ref_factor=ref)
+    oo, qo, repo = orc.solve_steady(mesh, P, prm, q, None, 1e-30, 2, mg, adapt=ap)
+    assert rep["adapted"] == repo["adapted"] >= 2   # both stages changed the map
+    assert np.array_equal(M.orders, oo)
+    assert rep["cycles"] == repo["cycles"]
+    assert np.max(np.abs(qd.cpu().numpy() - qo)) <= TOL * np.max(np.abs(qo))
