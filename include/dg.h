@@ -95,6 +95,31 @@ typedef struct dg_mesh dg_mesh;
  */
 int dg_mesh_create(const dg_mesh_desc* desc, const int32_t* orders, dg_mesh** out);
 
+/*
+ * dg_batch_create -- one handle for `nsolves` independent problems (the
+ * batched form): their elements are concatenated in solve order, each solve
+ * keeping its own flow parameters, explicit time step and residual norm, so
+ * every kernel of the path runs once per launch over the elements of all
+ * solves and each solve advances exactly as it would alone.  Element groups
+ * of equal order triples are shared across solves.  All descriptions must
+ * have the same dim and mapping order M.  The state of solve k occupies the
+ * node range returned by dg_batch_info.  The batch cycles with every call
+ * above (dg_residual, dg_smooth, dg_pmg_vcycle, dg_solve_steady without
+ * adaptation); dg_residual's DG_NORM and the driver's checks take the maximum
+ * over solves, dg_residual_norms gives them per solve.  Not part of the paper:
+ * the batching of independent solves is this library's.
+ *  descs   nsolves descriptions; orders: nsolves pointers to K_k x 3 maps.
+ */
+int dg_batch_create(const dg_mesh_desc* descs, const int32_t* const* orders, int32_t nsolves, dg_mesh** out);
+
+/* dg_batch_info -- number of solves and their node offsets (nsolves + 1
+ * values, host; may be NULL) in the batch layout. */
+int dg_batch_info(const dg_mesh* mesh, int32_t* nsolves, int64_t* solve_node_offsets);
+
+/* dg_residual_norms -- max |S - A(Q)| of every solve of the mesh (host
+ * array of nsolves doubles; 1 for a plain mesh).  Synchronises the stream. */
+int dg_residual_norms(dg_mesh* mesh, const double* q, const double* s, double* norms, void* stream);
+
 /* dg_mesh_destroy -- free the handle and all library-owned device memory. */
 int dg_mesh_destroy(dg_mesh* mesh);
 

@@ -132,11 +132,25 @@ static std::vector<int32_t> capped(const std::vector<int32_t>& o, int dim, int l
   return r;
 }
 
-static int level_norm(dg_mesh* m, Level* L, const double* Q, const double* Sv, cudaStream_t st, double* out) {
+// max |S - A(Q)| per solve slot into norms (host, nslots values); *out gets the max over slots
+static int level_norms(dg_mesh* m, Level* L, const double* Q, const double* Sv, cudaStream_t st, double* norms,
+                       double* out) {
   DG_TRY(ensure_work(L));
-  DG_TRY(reset_max(m->d_scalars + 1, st));
-  DG_TRY(residual(m, L, Q, Sv, L->d_R, false, st, m->d_scalars + 1, -1, nullptr, nullptr));
-  return read_scalar(m->d_scalars + 1, out, st);
+  double* dn = m->d_scalars + m->nslots;
+  DG_TRY(fill(dn, 0.0, m->nslots, st));
+  DG_TRY(residual(m, L, Q, Sv, L->d_R, false, st, dn, -1, nullptr, nullptr));
+  std::vector<double> tmp(m->nslots);
+  double* h = norms ? norms : tmp.data();
+  DG_CUDA_TRY(cudaMemcpyAsync(h, dn, m->nslots * sizeof(double), cudaMemcpyDeviceToHost, st));
+  DG_CUDA_TRY(cudaStreamSynchronize(st));
+  double mx = 0.0;
+  for (int k = 0; k < m->nslots; ++k) mx = (h[k] != h[k]) ? h[k] : std::max(mx, h[k]);
+  if (out) *out = mx;
+  return DG_OK;
+}
+
+static int level_norm(dg_mesh* m, Level* L, const double* Q, const double* Sv, cudaStream_t st, double* out) {
+  return level_norms(m, L, Q, Sv, st, nullptr, out);
 }
 
 static std::vector<int32_t> capped(const std::vector<int32_t>& o, int dim, int level, int direction);
@@ -410,11 +424,17 @@ int dg_mesh_create(const dg_mesh_desc* desc, const int32_t* orders, dg_mesh** ou
   m->ftab.assign(desc->ftab, desc->ftab + (size_t)desc->K * 24);
   m->prm = make_params(desc->params);
   std::memcpy(m->raw_params, desc->params, sizeof(m->raw_params));
+  m->nslots = 1;
+  m->slot_prm.assign(1, m->prm);
+  m->slot_raw.assign(1, std::vector<double>(desc->params, desc->params + 16));
+  m->elem_slot.assign(desc->K, 0);
+  m->slot_elem_off = {0, desc->K};
   m->orders.assign(orders, orders + (size_t)desc->K * 3);
   m->fine.reset(new Level());
   int rc = build_level(m, m->orders, m->fine.get());
+  if (rc == DG_OK) rc = upload_gas(m);
   if (rc == DG_OK) {
-    cudaError_t e1 = cudaMalloc(&m->d_scalars, 16 * sizeof(double));
+    cudaError_t e1 = cudaMalloc(&m->d_scalars, (2 * m->nslots + 16) * sizeof(double));
     cudaError_t e2 = cudaMalloc(&m->d_tau, (size_t)m->K * 3 * kTauSlots * sizeof(double));
     cudaError_t e3 = cudaMalloc(&m->d_orders, m->orders.size() * sizeof(int32_t));
     if (e3 == cudaSuccess)
@@ -432,6 +452,87 @@ int dg_mesh_create(const dg_mesh_desc* desc, const int32_t* orders, dg_mesh** ou
   return DG_OK;
 }
 
+int dg_batch_create(const dg_mesh_desc* descs, const int32_t* const* orders, int32_t nsolves, dg_mesh** out) {
+  if (!descs || !orders || !out || nsolves < 1) {
+    set_error("dg_batch_create: bad argument");
+    return DG_EINVAL;
+  }
+  for (int k = 0; k < nsolves; ++k) {
+    DG_TRY(check_desc(&descs[k], orders[k]));
+    if (descs[k].dim != descs[0].dim || descs[k].M != descs[0].M) {
+      set_error("dg_batch_create: all solves need the same dim and mapping order");
+      return DG_EINVAL;
+    }
+  }
+  DG_TRY(upload_tables());
+  dg_mesh* m = new (std::nothrow) dg_mesh();
+  if (!m) return DG_ENOMEM;
+  const int dim = descs[0].dim, Mp = descs[0].M + 1;
+  const size_t npe = dim == 3 ? (size_t)Mp * Mp * Mp : (size_t)Mp * Mp;
+  m->dim = dim;
+  m->M = descs[0].M;
+  m->nslots = nsolves;
+  m->slot_elem_off.assign(1, 0);
+  for (int k = 0; k < nsolves; ++k) {
+    const dg_mesh_desc& d = descs[k];
+    const int e0 = m->K;
+    m->xmap.insert(m->xmap.end(), d.xmap, d.xmap + (size_t)d.K * npe * 3);
+    for (int i = 0; i < d.K * 24; ++i) {
+      int32_t v = d.ftab[i];
+      if (i % 4 == 0 && v >= 0) v += e0;  // neighbour index into the batch
+      m->ftab.push_back(v);
+    }
+    m->orders.insert(m->orders.end(), orders[k], orders[k] + (size_t)d.K * 3);
+    m->elem_slot.insert(m->elem_slot.end(), d.K, k);
+    m->slot_prm.push_back(make_params(d.params));
+    m->slot_raw.push_back(std::vector<double>(d.params, d.params + 16));
+    m->K += d.K;
+    m->slot_elem_off.push_back(m->K);
+  }
+  m->prm = m->slot_prm[0];
+  std::memcpy(m->raw_params, descs[0].params, sizeof(m->raw_params));
+  m->fine.reset(new Level());
+  int rc = build_level(m, m->orders, m->fine.get());
+  if (rc == DG_OK) rc = upload_gas(m);
+  if (rc == DG_OK) {
+    cudaError_t e1 = cudaMalloc(&m->d_scalars, (2 * m->nslots + 16) * sizeof(double));
+    cudaError_t e2 = cudaMalloc(&m->d_tau, (size_t)m->K * 3 * kTauSlots * sizeof(double));
+    cudaError_t e3 = cudaMalloc(&m->d_orders, m->orders.size() * sizeof(int32_t));
+    if (e3 == cudaSuccess)
+      e3 = cudaMemcpy(m->d_orders, m->orders.data(), m->orders.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+      set_error("cudaMalloc failed for batch scalars");
+      rc = DG_ECUDA;
+    }
+  }
+  if (rc != DG_OK) {
+    dg_mesh_destroy(m);
+    return rc;
+  }
+  *out = m;
+  return DG_OK;
+}
+
+int dg_batch_info(const dg_mesh* m, int32_t* nsolves, int64_t* offs) {
+  if (!m) {
+    set_error("dg_batch_info: null mesh");
+    return DG_EINVAL;
+  }
+  if (nsolves) *nsolves = m->nslots;
+  if (offs)
+    for (int k = 0; k <= m->nslots; ++k) offs[k] = m->fine->off[m->slot_elem_off[k]];
+  return DG_OK;
+}
+
+int dg_residual_norms(dg_mesh* m, const double* q, const double* s, double* norms, void* stream) {
+  if (!m || !q || !norms) {
+    set_error("dg_residual_norms: null argument");
+    return DG_EINVAL;
+  }
+  double mx = 0.0;
+  return level_norms(m, m->fine.get(), q, s, S(stream), norms, &mx);
+}
+
 int dg_mesh_destroy(dg_mesh* m) {
   if (!m) return DG_OK;
   for (auto& kv : m->graphs) cudaGraphExecDestroy(kv.second.exec);
@@ -439,6 +540,9 @@ int dg_mesh_destroy(dg_mesh* m) {
   if (m->d_scalars) cudaFree(m->d_scalars);
   if (m->d_tau) cudaFree(m->d_tau);
   if (m->d_orders) cudaFree(m->d_orders);
+  if (m->d_gas64) cudaFree(m->d_gas64);
+  if (m->d_gas32x2) cudaFree(m->d_gas32x2);
+  if (m->d_gasd) cudaFree(m->d_gasd);
   delete m;
   return DG_OK;
 }
@@ -490,8 +594,8 @@ int dg_residual(dg_mesh* m, const double* q, const double* s, double* r, int fla
   bool iso = flags & DG_ISOLATED;
   double* dnorm = nullptr;
   if (flags & DG_NORM) {
-    dnorm = m->d_scalars + 1;
-    DG_TRY(reset_max(dnorm, st));
+    dnorm = m->d_scalars + m->nslots;
+    DG_TRY(fill(dnorm, 0.0, m->nslots, st));
   }
   DG_TRY(residual(m, m->fine.get(), q, s, r, iso, st, iso ? nullptr : dnorm, -1, nullptr, nullptr));
   if (flags & DG_NORM) {
@@ -500,7 +604,12 @@ int dg_residual(dg_mesh* m, const double* q, const double* s, double* r, int fla
       set_error("DG_NORM with DG_ISOLATED is not supported");
       return DG_EINVAL;
     }
-    DG_TRY(read_scalar(dnorm, rnorm_host, st));
+    std::vector<double> h(m->nslots);
+    DG_CUDA_TRY(cudaMemcpyAsync(h.data(), dnorm, m->nslots * sizeof(double), cudaMemcpyDeviceToHost, st));
+    DG_CUDA_TRY(cudaStreamSynchronize(st));
+    double mx = 0.0;
+    for (double v : h) mx = (v != v) ? v : std::max(mx, v);
+    *rnorm_host = mx;
   }
   return DG_OK;
 }
@@ -664,6 +773,10 @@ int dg_solve_steady(dg_mesh** meshp, double** qp, const double* s, const dg_solv
   }
   std::memset(rep, 0, sizeof(*rep));
   dg_mesh* m = *meshp;
+  if (sp->adapt && m->nslots > 1) {
+    set_error("dg_solve_steady: adaptation of a batch is not supported (adapt each solve)");
+    return DG_EINVAL;
+  }
   double* q = *qp;
   cudaStream_t st = S(stream);
   dg_mg_params mg = sp->mg;

@@ -79,6 +79,10 @@ struct MortarTile {    // one CTA of a mortar kernel
   int32_t node_first, nodes;
 };
 
+struct GasD {  // FP64 constants of the CFL kernel
+  double g, g1, gM2, Su, Su1, invRe, Ca, Cnu;
+};
+
 struct Params {
   double g, Pr, Ma, Re, Su, Ca, Cnu;
   double qinf[5];
@@ -113,6 +117,7 @@ struct Level {
   MortarTile* d_mtiles = nullptr;
   int n_mtiles = 0;
   int32_t* d_tile_elems = nullptr;
+  int32_t* d_slot = nullptr;            // solve slot of each element
   ElemTile* d_tiles = nullptr;
   int n_tiles = 0;
   size_t tile_smem_nodes = 0;           // max nodes of a tile
@@ -134,12 +139,20 @@ struct dg_mesh {
   int arith = DG_ARITH_FP64;     // arithmetic of the operator kernels
   std::vector<double> xmap;
   std::vector<int32_t> ftab;
-  dg::Params prm;
+  dg::Params prm;                // slot 0 (single solves)
   double raw_params[16];
+  int nslots = 1;                // independent solves batched in this mesh
+  std::vector<dg::Params> slot_prm;
+  std::vector<std::vector<double>> slot_raw;  // per-slot raw parameter vectors
+  std::vector<int32_t> elem_slot;             // K
+  std::vector<int32_t> slot_elem_off;         // nslots + 1
+  void* d_gas64 = nullptr;       // per-slot gas constants (FP64)
+  void* d_gas32x2 = nullptr;     // per-slot gas constants (float pairs)
+  dg::GasD* d_gasd = nullptr;    // per-slot CFL constants
   std::vector<int32_t> orders;
   std::unique_ptr<dg::Level> fine;
   std::map<std::vector<int32_t>, std::unique_ptr<dg::Level>> levels;  // coarse levels by order map
-  double* d_scalars = nullptr;   // [0] dt, [1] norm, [2..] scratch
+  double* d_scalars = nullptr;   // [0, nslots) dt per slot, [nslots, 2 nslots) max|r| per slot
   double* d_tau = nullptr;       // K x 3 x 16 tau table
   int32_t* d_orders = nullptr;   // K x 3 orders on the device
   cudaStream_t cap_stream = nullptr;  // stream used to capture cycle graphs
@@ -160,6 +173,7 @@ Params make_params(const double* p);
 
 // kernels (dg_kernels.cu)
 int upload_tables();
+int upload_gas(dg_mesh* m);
 unsigned long long launches();
 void add_launches(unsigned long long n);
 int prepare_capture();  // one-time per-device set-up that may not run inside a capture

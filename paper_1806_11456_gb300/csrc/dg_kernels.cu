@@ -170,9 +170,6 @@ struct GasT {
   R ig1;     // 1/(gamma - 1)
 };
 
-struct GasD {  // FP64 constants for the CFL kernel
-  double g, g1, gM2, Su, Su1, invRe, Ca, Cnu;
-};
 
 template <typename R>
 R host_r(double x);
@@ -339,11 +336,44 @@ DEV void ghost(int bc, const R* qi, const R* nu, const GasT<R>& G, R* qg) {
   qg[4] = qi[4];
 }
 
+// Reduce v into dst[slot] for the active lanes of a warp: one atomic when all
+// participating lanes share a slot (single solves, sorted batches), one per
+// lane otherwise.  Every lane of the warp must call it.
+template <bool MAX>
+DEV void warp_slot_reduce(double* dst, int slot, double v, bool active);
+
 DEV void atomic_max_nonneg(double* addr, double v) {
   atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
 }
 DEV void atomic_min_pos(double* addr, double v) {
   atomicMin(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+template <bool MAX>
+DEV void warp_slot_reduce(double* dst, int slot, double v, bool active) {
+  const unsigned act = __ballot_sync(0xffffffffu, active);
+  if (act == 0u) return;
+  const int lead = __ffs(act) - 1;
+  const int s0 = __shfl_sync(0xffffffffu, slot, lead);
+  const bool uniform = __all_sync(0xffffffffu, !active || slot == s0);
+  if (uniform) {
+    double w = active ? v : (MAX ? 0.0 : 1e300);
+    for (int o = 16; o > 0; o >>= 1) {
+      const double x = __shfl_xor_sync(0xffffffffu, w, o);
+      w = MAX ? fmax(w, x) : fmin(w, x);
+    }
+    if ((int)(threadIdx.x & 31) == lead) {
+      if (MAX)
+        atomic_max_nonneg(dst + s0, w);
+      else
+        atomic_min_pos(dst + s0, w);
+    }
+  } else if (active) {
+    if (MAX)
+      atomic_max_nonneg(dst + slot, v);
+    else
+      atomic_min_pos(dst + slot, v);
+  }
 }
 
 // ---- tables in R ----
@@ -385,6 +415,7 @@ struct LevelArgsT {
   const ST* fnS;
   const ElemTile* tiles;
   const int32_t* tile_elems;
+  const int32_t* slot;  // solve slot of each element (batched meshes; all 0 otherwise)
   int dim;
 };
 
@@ -402,6 +433,7 @@ LevelArgsT<double> largs<double>(const Level* L) {
   a.fnS = L->d_fnS;
   a.tiles = L->d_tiles;
   a.tile_elems = L->d_tile_elems;
+  a.slot = L->d_slot;
   a.dim = L->dim;
   return a;
 }
@@ -417,6 +449,7 @@ LevelArgsT<dd> largs<dd>(const Level* L) {
   a.fnS = reinterpret_cast<const float2*>(L->d_fnS2);
   a.tiles = L->d_tiles;
   a.tile_elems = L->d_tile_elems;
+  a.slot = L->d_slot;
   a.dim = L->dim;
   return a;
 }
@@ -618,7 +651,8 @@ DEV void mortar_node_value(const LevelArgsT<R>& A, const MortarArgsT<R>& MA, con
 }
 
 template <typename R, int PASS>
-__global__ void __launch_bounds__(kMortarTile, 8) k_mortar(LevelArgsT<R> A, MortarArgsT<R> MA, GasT<R> G,
+__global__ void __launch_bounds__(kMortarTile, 8) k_mortar(LevelArgsT<R> A, MortarArgsT<R> MA,
+                                                           const GasT<R>* __restrict__ gas,
                                                            const typename Store<R>::T* __restrict__ trq,
                                                            const typename Store<R>::T* __restrict__ trg,
                                                            typename Store<R>::T* __restrict__ out) {
@@ -627,8 +661,11 @@ __global__ void __launch_bounds__(kMortarTile, 8) k_mortar(LevelArgsT<R> A, Mort
   __shared__ R sval[kMortarTileMax * 5];
   __shared__ int scum[kMortarTileMax + 1];
   const MortarTile mt = MA.tiles[blockIdx.x];
-  for (int i = threadIdx.x; i < mt.nodes; i += blockDim.x)
-    mortar_node_value<R, PASS>(A, MA, G, trq, trg, mt.node_first + i, sval + i * 5);
+  for (int i = threadIdx.x; i < mt.nodes; i += blockDim.x) {
+    const int64_t gp = mt.node_first + i;
+    const GasT<R>& G = gas[A.slot[MA.mortars[MA.mnode_mortar[gp]].eL]];
+    mortar_node_value<R, PASS>(A, MA, G, trq, trg, gp, sval + i * 5);
+  }
   if (threadIdx.x == 0) {
     int acc = 0;
     for (int m = 0; m < mt.count; ++m) {
@@ -722,11 +759,12 @@ DEV void load_dtables(R* sD, const typename Store<R>::T* src, int n0, int n1, in
 // Stage the tile: conserved state (sq), primitives u,v,w,T (sA[0..3]) and the
 // nine metric components (sA[4..12]).
 template <typename R>
-DEV void stage_tile(const LevelArgsT<R>& A, const ElemTile& t, int nn, int T, const GasT<R>& G,
+DEV void stage_tile(const LevelArgsT<R>& A, const ElemTile& t, int nn, int T, const GasT<R>* __restrict__ gas,
                     const double* __restrict__ q, R* sq, R* sA) {
   for (int i = threadIdx.x; i < T; i += blockDim.x) {
     int le = i / nn, node = i - le * nn;
     int e = A.tile_elems[t.first + le];
+    const GasT<R>& G = gas[A.slot[e]];
     const int64_t gn = A.off[e] + node;
     const double* qe = q + (size_t)5 * A.off[e];
     R qq[5];
@@ -852,7 +890,8 @@ DEV void divergence(const R* sD, const R* sA, int T, int nn, int i, int n0, int 
 }
 
 template <typename R, int DIM, bool AFFINE>
-__global__ void __launch_bounds__(kTileNodes) k_volume(LevelArgsT<R> A, GasT<R> G, const double* __restrict__ q,
+__global__ void __launch_bounds__(kTileNodes) k_volume(LevelArgsT<R> A, const GasT<R>* __restrict__ gas,
+                                                       const double* __restrict__ q,
                                                        const typename Store<R>::T* __restrict__ ust,
                                                        typename Store<R>::T* __restrict__ trg,
                                                        typename Store<R>::T* __restrict__ vol) {
@@ -867,7 +906,7 @@ __global__ void __launch_bounds__(kTileNodes) k_volume(LevelArgsT<R> A, GasT<R> 
   R* sA = sq + 5 * T;                          // 15 * T: U(4) + Ja(9) | Ftilde(15)
   R* sG = sA + 15 * T;                         // 12 * T
   load_dtables<R>(sD, Tab<R>::Dhat(), n0, n1, n2, DIM);
-  stage_tile<R>(A, t, nn, T, G, q, sq, sA);
+  stage_tile<R>(A, t, nn, T, gas, q, sq, sA);
   __syncthreads();
   // ---- gradient: volume part + lifting of U*, times 1/J ----
   for (int i = threadIdx.x; i < T; i += blockDim.x) {
@@ -930,7 +969,8 @@ __global__ void __launch_bounds__(kTileNodes) k_volume(LevelArgsT<R> A, GasT<R> 
     }
   }
   // ---- nodal contravariant fluxes (own node only: no cross-node hazard) ----
-  for (int i = threadIdx.x; i < T; i += blockDim.x) nodal_fluxes<R, DIM>(sq, sA, sG, T, i, G);
+  for (int i = threadIdx.x; i < T; i += blockDim.x)
+    nodal_fluxes<R, DIM>(sq, sA, sG, T, i, gas[A.slot[A.tile_elems[t.first + i / nn]]]);
   __syncthreads();
   // ---- weak-form divergence ----
   for (int i = threadIdx.x; i < T; i += blockDim.x) {
@@ -965,43 +1005,46 @@ __global__ void __launch_bounds__(kTileNodes) k_surface(LevelArgsT<R> A, const t
   const int n0 = t.n[0], n1 = t.n[1], n2 = t.n[2];
   const int nn = n0 * n1 * n2;
   const int T = t.count * nn;
-  double lmax = 0.0;
-  const double dt = (rk.stage >= 0) ? *rk.dt : 0.0;
-  for (int i = threadIdx.x; i < T; i += blockDim.x) {
-    const int le = i / nn, node = i - le * nn;
-    const int e = A.tile_elems[t.first + le];
-    const int idx0 = node % n0, idx1 = (node / n0) % n1, idx2 = node / (n0 * n1);
-    const size_t base = (size_t)5 * A.off[e] + node;
-    R acc[5];
+  for (int i0 = 0; i0 < T; i0 += blockDim.x) {  // all lanes iterate together (warp reductions)
+    const int i = i0 + threadIdx.x;
+    const bool active = i < T;
+    double lmax = 0.0;
+    int slot = 0;
+    if (active) {
+      const int le = i / nn, node = i - le * nn;
+      const int e = A.tile_elems[t.first + le];
+      slot = A.slot[e];
+      const int idx0 = node % n0, idx1 = (node / n0) % n1, idx2 = node / (n0 * n1);
+      const size_t base = (size_t)5 * A.off[e] + node;
+      R acc[5];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) acc[v] = SR::get(vol, base + v * nn);
+      for (int v = 0; v < 5; ++v) acc[v] = SR::get(vol, base + v * nn);
 #pragma unroll
-    for (int f = 0; f < 2 * DIM; ++f) {
-      int d, ta, tb, side;
-      face_dirs(f, d, ta, tb, side);
-      const int nd = pick(d, n0, n1, n2), id = pick(d, idx0, idx1, idx2);
-      const R lw = side ? Tab<R>::lpw(nd, id) : Tab<R>::lmw(nd, id);
-      const int64_t p = A.fo[e * 6 + f] + pick(tb, idx0, idx1, idx2) * pick(ta, n0, n1, n2) + pick(ta, idx0, idx1, idx2);
+      for (int f = 0; f < 2 * DIM; ++f) {
+        int d, ta, tb, side;
+        face_dirs(f, d, ta, tb, side);
+        const int nd = pick(d, n0, n1, n2), id = pick(d, idx0, idx1, idx2);
+        const R lw = side ? Tab<R>::lpw(nd, id) : Tab<R>::lmw(nd, id);
+        const int64_t p = A.fo[e * 6 + f] + pick(tb, idx0, idx1, idx2) * pick(ta, n0, n1, n2) + pick(ta, idx0, idx1, idx2);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) acc[v] += lw * SR::get(fst, v * A.fn + p);
-    }
-    const R iJ = SR::get(A.geo, 9 * A.nodes + A.off[e] + node);
+        for (int v = 0; v < 5; ++v) acc[v] += lw * SR::get(fst, v * A.fn + p);
+      }
+      const R iJ = SR::get(A.geo, 9 * A.nodes + A.off[e] + node);
+      const double dt = (rk.stage >= 0) ? rk.dt[slot] : 0.0;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      const double rv = (s ? s[base + v * nn] : 0.0) - to_double(acc[v] * iJ);
-      lmax = (rv != rv) ? INFINITY : fmax(lmax, fabs(rv));  // a NaN residual reads as +inf
-      if (rk.stage < 0) {
-        r[base + v * nn] = rv;
-      } else {
-        double gv = (rk.stage == 0 ? 0.0 : rk.a * rk.g[base + v * nn]) + dt * rv;
-        rk.g[base + v * nn] = gv;
-        rk.qupd[base + v * nn] += rk.b * gv;
+      for (int v = 0; v < 5; ++v) {
+        const double rv = (s ? s[base + v * nn] : 0.0) - to_double(acc[v] * iJ);
+        lmax = (rv != rv) ? INFINITY : fmax(lmax, fabs(rv));  // a NaN residual reads as +inf
+        if (rk.stage < 0) {
+          r[base + v * nn] = rv;
+        } else {
+          double gv = (rk.stage == 0 ? 0.0 : rk.a * rk.g[base + v * nn]) + dt * rv;
+          rk.g[base + v * nn] = gv;
+          rk.qupd[base + v * nn] += rk.b * gv;
+        }
       }
     }
-  }
-  if (norm) {
-    for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
-    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(norm, lmax);
+    if (norm) warp_slot_reduce<true>(norm, slot, lmax, active);
   }
 }
 
@@ -1016,7 +1059,8 @@ struct TauArgs {
 };
 
 template <typename R, int DIM, bool AFFINE>
-__global__ void __launch_bounds__(kTileNodes) k_isolated(LevelArgsT<R> A, GasT<R> G, const double* __restrict__ q,
+__global__ void __launch_bounds__(kTileNodes) k_isolated(LevelArgsT<R> A, const GasT<R>* __restrict__ gas,
+                                                         const double* __restrict__ q,
                                                          const double* __restrict__ s, double* __restrict__ r,
                                                          TauArgs tau) {
   using SR = Store<R>;
@@ -1030,7 +1074,7 @@ __global__ void __launch_bounds__(kTileNodes) k_isolated(LevelArgsT<R> A, GasT<R
   R* sA = sq + 5 * T;
   R* sG = sA + 15 * T;
   load_dtables<R>(sD, Tab<R>::Dcol(), n0, n1, n2, DIM);
-  stage_tile<R>(A, t, nn, T, G, q, sq, sA);
+  stage_tile<R>(A, t, nn, T, gas, q, sq, sA);
   __syncthreads();
   for (int i = threadIdx.x; i < T; i += blockDim.x) {
     R g[12];
@@ -1042,7 +1086,8 @@ __global__ void __launch_bounds__(kTileNodes) k_isolated(LevelArgsT<R> A, GasT<R
     for (int k = 0; k < 12; ++k) sG[k * T + i] = g[k] * iJ;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < T; i += blockDim.x) nodal_fluxes<R, DIM>(sq, sA, sG, T, i, G);
+  for (int i = threadIdx.x; i < T; i += blockDim.x)
+    nodal_fluxes<R, DIM>(sq, sA, sG, T, i, gas[A.slot[A.tile_elems[t.first + i / nn]]]);
   __syncthreads();
   for (int i = threadIdx.x; i < T; i += blockDim.x) {
     R acc[5];
@@ -1071,43 +1116,49 @@ __global__ void __launch_bounds__(kTileNodes) k_isolated(LevelArgsT<R> A, GasT<R
 // k_cfl: global minimum of the explicit step (FP64)
 // ---------------------------------------------------------------------------
 template <int DIM>
-__global__ void __launch_bounds__(kTileNodes) k_cfl(LevelArgsT<double> A, GasD G, const double* __restrict__ q,
-                                                    double* dtmin) {
+__global__ void __launch_bounds__(kTileNodes) k_cfl(LevelArgsT<double> A, const GasD* __restrict__ gasd,
+                                                    const double* __restrict__ q, double* dtmin) {
   const ElemTile t = A.tiles[blockIdx.x];
   const int n0 = t.n[0], n1 = t.n[1], n2 = t.n[2];
   const int nn = n0 * n1 * n2;
   const int T = t.count * nn;
-  double best = 1e300;
-  for (int i = threadIdx.x; i < T; i += blockDim.x) {
-    int le = i / nn, node = i - le * nn;
-    int e = A.tile_elems[t.first + le];
-    const int64_t gn = A.off[e] + node;
-    const double* qe = q + (size_t)5 * A.off[e];
-    double qq[5];
+  for (int i0 = 0; i0 < T; i0 += blockDim.x) {  // all lanes iterate together (warp reductions)
+    const int i = i0 + threadIdx.x;
+    const bool active = i < T;
+    double best = 1e300;
+    int slot = 0;
+    if (active) {
+      int le = i / nn, node = i - le * nn;
+      int e = A.tile_elems[t.first + le];
+      slot = A.slot[e];
+      const GasD G = gasd[slot];
+      const int64_t gn = A.off[e] + node;
+      const double* qe = q + (size_t)5 * A.off[e];
+      double qq[5];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) qq[v] = qe[v * nn + node];
-    const double ir = 1.0 / qq[0];
-    const double u0 = qq[1] * ir, u1 = qq[2] * ir, u2 = qq[3] * ir;
-    const double p = G.g1 * (qq[4] - 0.5 * (qq[1] * u0 + qq[2] * u1 + qq[3] * u2));
-    const double Tt = G.gM2 * p * ir;
-    const double c = sqrt(G.g * p * ir);
-    const double vel = sqrt(u0 * u0 + u1 * u1 + u2 * u2);
-    const double nu = Tt * sqrt(Tt) * G.Su1 / (Tt + G.Su) * ir * G.invRe;
-    const double iJ = A.geo[9 * A.nodes + gn];
+      for (int v = 0; v < 5; ++v) qq[v] = qe[v * nn + node];
+      const double ir = 1.0 / qq[0];
+      const double u0 = qq[1] * ir, u1 = qq[2] * ir, u2 = qq[3] * ir;
+      const double p = G.g1 * (qq[4] - 0.5 * (qq[1] * u0 + qq[2] * u1 + qq[3] * u2));
+      const double Tt = G.gM2 * p * ir;
+      const double c = sqrt(G.g * p * ir);
+      const double vel = sqrt(u0 * u0 + u1 * u1 + u2 * u2);
+      const double nu = Tt * sqrt(Tt) * G.Su1 / (Tt + G.Su) * ir * G.invRe;
+      const double iJ = A.geo[9 * A.nodes + gn];
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      const int N = pick(d, n0, n1, n2) - 1;
-      if (N <= 0) continue;
-      double j0 = A.geo[(3 * d + 0) * A.nodes + gn], j1 = A.geo[(3 * d + 1) * A.nodes + gn],
-             j2 = A.geo[(3 * d + 2) * A.nodes + gn];
-      double h = 2.0 / (sqrt(j0 * j0 + j1 * j1 + j2 * j2) * iJ);
-      double N2 = (double)N * (double)N;
-      best = fmin(best, G.Ca * h / ((vel + c) * N2));
-      best = fmin(best, G.Cnu * h * h / (nu * N2 * N2));
+      for (int d = 0; d < DIM; ++d) {
+        const int N = pick(d, n0, n1, n2) - 1;
+        if (N <= 0) continue;
+        double j0 = A.geo[(3 * d + 0) * A.nodes + gn], j1 = A.geo[(3 * d + 1) * A.nodes + gn],
+               j2 = A.geo[(3 * d + 2) * A.nodes + gn];
+        double h = 2.0 / (sqrt(j0 * j0 + j1 * j1 + j2 * j2) * iJ);
+        double N2 = (double)N * (double)N;
+        best = fmin(best, G.Ca * h / ((vel + c) * N2));
+        best = fmin(best, G.Cnu * h * h / (nu * N2 * N2));
+      }
     }
+    warp_slot_reduce<false>(dtmin, slot, best, active);
   }
-  for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
-  if ((threadIdx.x & 31) == 0) atomic_min_pos(dtmin, best);
 }
 
 // ---------------------------------------------------------------------------
@@ -1283,6 +1334,37 @@ static int ensure_dd(Level* L, cudaStream_t st) {
   return split_array(L->d_mnS, &L->d_mnS2, 3 * L->mortar_nodes, st);
 }
 
+template <typename R>
+static const GasT<R>* gas_table(const dg_mesh* m);
+template <>
+const GasT<double>* gas_table<double>(const dg_mesh* m) {
+  return reinterpret_cast<const GasT<double>*>(m->d_gas64);
+}
+template <>
+const GasT<dd>* gas_table<dd>(const dg_mesh* m) {
+  return reinterpret_cast<const GasT<dd>*>(m->d_gas32x2);
+}
+
+// per-slot gas constants on the device (FP64, float pairs, CFL)
+int upload_gas(dg_mesh* m) {
+  const int S = m->nslots;
+  std::vector<GasT<double>> g64(S);
+  std::vector<GasT<dd>> g2(S);
+  std::vector<GasD> gd(S);
+  for (int k = 0; k < S; ++k) {
+    g64[k] = make_gas<double>(m->slot_prm[k]);
+    g2[k] = make_gas<dd>(m->slot_prm[k]);
+    gd[k] = make_gas_d(m->slot_prm[k]);
+  }
+  DG_CUDA_TRY(cudaMalloc(&m->d_gas64, S * sizeof(GasT<double>)));
+  DG_CUDA_TRY(cudaMalloc(&m->d_gas32x2, S * sizeof(GasT<dd>)));
+  DG_CUDA_TRY(cudaMalloc((void**)&m->d_gasd, S * sizeof(GasD)));
+  DG_CUDA_TRY(cudaMemcpy(m->d_gas64, g64.data(), S * sizeof(GasT<double>), cudaMemcpyHostToDevice));
+  DG_CUDA_TRY(cudaMemcpy(m->d_gas32x2, g2.data(), S * sizeof(GasT<dd>), cudaMemcpyHostToDevice));
+  DG_CUDA_TRY(cudaMemcpy(m->d_gasd, gd.data(), S * sizeof(GasD), cudaMemcpyHostToDevice));
+  return DG_OK;
+}
+
 int prepare_arith(const dg_mesh* m, Level* L, cudaStream_t st) {
   return (m->arith == DG_ARITH_DF32) ? ensure_dd(L, st) : DG_OK;
 }
@@ -1307,7 +1389,7 @@ static void launch_trace(const Level* L, const double* q, cudaStream_t st) {
     k_trace_q<R, 3><<<L->n_tiles, kTileNodes, sm, st>>>(A, q, buf<R>(L->d_trq));
 }
 template <typename R>
-static void launch_volume(const Level* L, const GasT<R>& G, const double* q, cudaStream_t st) {
+static void launch_volume(const Level* L, const GasT<R>* G, const double* q, cudaStream_t st) {
   ++g_launches;
   const size_t sm = vol_smem(L);
   LevelArgsT<R> A = largs<R>(L);
@@ -1327,7 +1409,7 @@ static void launch_volume(const Level* L, const GasT<R>& G, const double* q, cud
   }
 }
 template <typename R>
-static void launch_isolated(const Level* L, const GasT<R>& G, const double* q, const double* s, double* r,
+static void launch_isolated(const Level* L, const GasT<R>* G, const double* q, const double* s, double* r,
                             const TauArgs& ta, cudaStream_t st) {
   ++g_launches;
   const size_t sm = vol_smem(L);
@@ -1355,7 +1437,7 @@ static void launch_surface(const Level* L, const double* s, double* r, double* n
     k_surface<R, 3><<<L->n_tiles, kTileNodes, 0, st>>>(A, buf<R>(L->d_vol), buf<R>(L->d_fst), s, r, norm, rk);
 }
 template <typename R>
-static void launch_mortar(int pass, const Level* L, const GasT<R>& G, cudaStream_t st) {
+static void launch_mortar(int pass, const Level* L, const GasT<R>* G, cudaStream_t st) {
   ++g_launches;
   LevelArgsT<R> A = largs<R>(L);
   MortarArgsT<R> MA = margs<R>(L);
@@ -1380,7 +1462,7 @@ static RKArgs rk_args(int rk_stage, double* rk_g, const double* d_dt, const doub
 template <typename R>
 static int residual_t(const dg_mesh* m, Level* L, const double* q, const double* s, double* r, bool isolated,
                       cudaStream_t st, double* d_norm, int rk_stage, double* rk_g, const double* d_dt) {
-  const GasT<R> G = make_gas<R>(m->prm);
+  const GasT<R>* G = gas_table<R>(m);
   if (isolated) {
     TauArgs ta{nullptr, nullptr, nullptr, 0, 0};
     launch_isolated<R>(L, G, q, s, r, ta, st);
@@ -1410,7 +1492,7 @@ int residual(const dg_mesh* m, Level* L, const double* q, const double* s, doubl
 template <typename R>
 static int profile_t(const dg_mesh* m, Level* L, const double* q, const double* s, double* r, int iters,
                      double* ms_out, cudaStream_t st) {
-  const GasT<R> G = make_gas<R>(m->prm);
+  const GasT<R>* G = gas_table<R>(m);
   RKArgs rk = rk_args(-1, nullptr, nullptr, nullptr);
   TauArgs ta{nullptr, nullptr, nullptr, 0, 0};
   cudaEvent_t e0, e1;
@@ -1453,14 +1535,13 @@ int profile_residual(const dg_mesh* m, Level* L, const double* q, const double* 
 }
 
 int cfl_dt(const dg_mesh* m, Level* L, const double* q, double* d_dt, cudaStream_t st) {
-  int rc = reset_min(d_dt, st);
+  int rc = fill(d_dt, 1e300, m->nslots, st);
   if (rc != DG_OK) return rc;
   ++g_launches;
-  const GasD G = make_gas_d(m->prm);
   if (L->dim == 2)
-    k_cfl<2><<<L->n_tiles, kTileNodes, 0, st>>>(largs<double>(L), G, q, d_dt);
+    k_cfl<2><<<L->n_tiles, kTileNodes, 0, st>>>(largs<double>(L), m->d_gasd, q, d_dt);
   else
-    k_cfl<3><<<L->n_tiles, kTileNodes, 0, st>>>(largs<double>(L), G, q, d_dt);
+    k_cfl<3><<<L->n_tiles, kTileNodes, 0, st>>>(largs<double>(L), m->d_gasd, q, d_dt);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
 }
@@ -1507,9 +1588,9 @@ int tau_accumulate(const dg_mesh* m, Level* L, const double* q, const double* s,
   TauArgs ta{rho, d_tau, fine_orders_dev, dir, slot};
   if (m->arith == DG_ARITH_DF32) {
     if ((rc = ensure_dd(L, st)) != DG_OK) return rc;
-    launch_isolated<dd>(L, make_gas<dd>(m->prm), q, s, nullptr, ta, st);
+    launch_isolated<dd>(L, gas_table<dd>(m), q, s, nullptr, ta, st);
   } else {
-    launch_isolated<double>(L, make_gas<double>(m->prm), q, s, nullptr, ta, st);
+    launch_isolated<double>(L, gas_table<double>(m), q, s, nullptr, ta, st);
   }
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;

@@ -350,7 +350,7 @@ int dev_zeros(double** dst, size_t n) {
 Level::~Level() {
   void* ptrs[] = {d_n,   d_off,   d_geo,       d_fo,    d_fnS,          d_trq,  d_ust,  d_trg,
                   d_fst, d_mortars, d_mnode_mortar, d_mnS, d_mtiles, d_tile_elems, d_tiles, d_vol,
-                  d_Q,   d_S,     d_Q0,        d_G,     d_R,            d_geo2, d_fnS2, d_mnS2};
+                  d_Q,   d_S,     d_Q0,        d_G,     d_R,            d_geo2, d_fnS2, d_mnS2, d_slot};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -559,6 +559,7 @@ int build_level(const dg_mesh* m, const std::vector<int32_t>& orders, Level* L) 
   DG_TRY(dev_upload(&L->d_mnS, mnS));
   DG_TRY(dev_upload(&L->d_mtiles, mtiles));
   DG_TRY(dev_upload(&L->d_tile_elems, tile_elems));
+  DG_TRY(dev_upload(&L->d_slot, m->elem_slot));
   DG_TRY(dev_upload(&L->d_tiles, tiles));
   DG_TRY(dev_zeros(&L->d_trq, (size_t)5 * acc));
   DG_TRY(dev_zeros(&L->d_ust, (size_t)4 * acc));

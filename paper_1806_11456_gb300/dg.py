@@ -72,7 +72,7 @@ _ip = ctypes.POINTER(ctypes.c_int32)
 EXPORTS = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_layout", "dg_residual", "dg_cfl_dt", "dg_smooth",
            "dg_pmg_vcycle", "dg_tau_estimate", "dg_adapt", "dg_transfer_state", "dg_profile_residual",
            "dg_kernel_launches", "dg_transfer_noalloc", "dg_solve_steady", "dg_mesh_orders", "dg_set_arithmetic",
-           "dg_last_error"]
+           "dg_batch_create", "dg_batch_info", "dg_residual_norms", "dg_last_error"]
 ARITH = {"fp64": 0, "df32": 1}
 KERNEL_STAGES = ["trace_q", "mortar_u_star", "volume", "mortar_flux", "surface", "isolated"]
 
@@ -102,6 +102,9 @@ def lib(path=LIB_PATH):
                                   _vp, ctypes.POINTER(SolveReport), _vp]
     L.dg_mesh_orders.argtypes = [_vp, _ip]
     L.dg_set_arithmetic.argtypes = [_vp, ctypes.c_int]
+    L.dg_batch_create.argtypes = [ctypes.POINTER(MeshDesc), ctypes.POINTER(_ip), ctypes.c_int32, ctypes.POINTER(_vp)]
+    L.dg_batch_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]
+    L.dg_residual_norms.argtypes = [_vp, _vp, _vp, _dp, _vp]
     L.dg_transfer_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, _ip, _ip, ctypes.c_int32, _vp, _vp, _vp]
     _lib = L
     return L
@@ -134,9 +137,67 @@ def kernel_launches():
     return int(c.value)
 
 
+def _desc(mesh, params, keep):
+    d = MeshDesc()
+    xmap = np.ascontiguousarray(mesh["xmap"], dtype=np.float64)
+    ftab = np.ascontiguousarray(mesh["ftab"], dtype=np.int32)
+    keep += [xmap, ftab]
+    d.dim, d.K, d.M = int(mesh["dim"]), int(mesh["K"]), int(mesh["M"])
+    d.xmap = xmap.ctypes.data_as(_dp)
+    d.ftab = ftab.ctypes.data_as(_ip)
+    for i in range(16):
+        d.params[i] = float(params[i])
+    return d
+
+
 class Mesh:
     """A mesh with an order map: geometry, faces and multigrid levels live on
     the device inside the library."""
+
+    @classmethod
+    def batch(cls, items):
+        """One handle for several independent solves [(mesh, orders, params),
+        ...] (dg_batch_create).  ``solve_slices()`` gives each solve's range
+        of the batch state vector."""
+        import torch
+        if not torch.cuda.is_available():
+            raise DGError("no CUDA device: the DGSEM library has no CPU path")
+        keep = []
+        descs = (MeshDesc * len(items))()
+        ords = (_ip * len(items))()
+        for k, (mesh, orders, params) in enumerate(items):
+            descs[k] = _desc(mesh, params, keep)
+            o = np.ascontiguousarray(orders, dtype=np.int32)
+            keep.append(o)
+            ords[k] = o.ctypes.data_as(_ip)
+        h = _vp()
+        torch.cuda.current_device()
+        _check(lib().dg_batch_create(descs, ords, len(items), ctypes.byref(h)))
+        self = cls.__new__(cls)
+        self.h = h
+        self.dim = int(items[0][0]["dim"])
+        self.K = sum(int(it[0]["K"]) for it in items)
+        self.M = int(items[0][0]["M"])
+        self.orders = np.concatenate([np.asarray(it[1], dtype=np.int32) for it in items])
+        self.params = np.asarray(items[0][2], dtype=np.float64)
+        self.mesh = None
+        self.arith = "fp64"
+        return self
+
+    def solve_slices(self):
+        """Node offsets of the solves (5 values per node in the state)."""
+        n = ctypes.c_int32()
+        _check(lib().dg_batch_info(self.h, ctypes.byref(n), None))
+        off = np.zeros(n.value + 1, dtype=np.int64)
+        _check(lib().dg_batch_info(self.h, ctypes.byref(n), off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        return off
+
+    def residual_norms(self, q, s=None, stream=None):
+        n = ctypes.c_int32()
+        _check(lib().dg_batch_info(self.h, ctypes.byref(n), None))
+        out = np.zeros(n.value)
+        _check(lib().dg_residual_norms(self.h, _ptr(q), _ptr(s), out.ctypes.data_as(_dp), _stream(stream)))
+        return out
 
     def __init__(self, mesh, orders, params):
         import torch
