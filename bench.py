@@ -42,10 +42,21 @@ TAU_MAX = 1e-4
 FP64_PEAK_TFLOPS = 4 * 152 * 2.070e9 / 1e12  # 2 DFMA/clk/SM x 152 SMs at 2070 MHz
 
 
+def _hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
+HBM_PEAK_GBS = _hbm_peak()
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     return ap.parse_args()
@@ -205,6 +216,136 @@ def time_to_tolerance(dg, torch, dev, tol=1e-10, max_cycles=3000):
     return out
 
 
+def batched_solves(dg, torch, dev, steps=5):
+    """Many independent solves batched into one handle per dimension (one
+    launch per kernel over the elements of all its solves, one CUDA graph per
+    V-cycle), against the same solves run one at a time, each with its own
+    graph, on the same stream.  Workload: 64 solves, half stretched 2D plates
+    and half quadratic cubed-sphere shells, 200-4000 elements, orders uniform
+    in [1, 8]^dim, Mach in [0.1, 0.4] and Re in [1e2, 1e5] log-uniform,
+    freestream start.  A step is one V-cycle 8 -> 1 of every solve."""
+    from paper_1806_11456_gb300 import synthetic as syn
+    t0 = time.time()
+    items = syn.batch_workload_c4()
+    q_np = [syn.freestream_state(m, o, p) for (m, o, p) in items]
+    t_gen = time.time() - t0
+    groups = [[k for k in range(len(items)) if items[k][0]["dim"] == d] for d in (2, 3)]
+    t0 = time.time()
+    handles = [dg.Mesh.batch([items[k] for k in g]) for g in groups]
+    torch.cuda.synchronize()
+    t_setup = time.time() - t0
+    offs = [H.solve_slices() for H in handles]
+    q0 = [torch.tensor(np.concatenate([q_np[k] for k in g]), device=dev) for g in groups]
+    q = [x.clone() for x in q0]
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, n):
+        ms, dofs = 0.0, 0.0
+        for _ in range(n):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            dofs += fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+        return ms / n, dofs / n
+
+    def batch_step():
+        d = 0.0
+        for H, x, x0 in zip(handles, q, q0):
+            x.copy_(x0)
+            d += H.vcycle(x, None, graph=True, **CYCLE)["dof_evals"]
+        return d
+
+    for _ in range(2):
+        batch_step()
+    launches0 = dg.kernel_launches()
+    b_ms, b_dofs = timed(batch_step, steps)
+    b_launches = (dg.kernel_launches() - launches0) // steps
+    batch_once = [x.cpu().numpy() for x in q]
+    norms = np.concatenate([H.residual_norms(x) for H, x in zip(handles, q)])
+    stage = {}
+    for d, H, x0 in zip((2, 3), handles, q0):
+        prof = H.profile_residual(x0, None, iters=5)
+        n_d = int(H.solve_slices()[-1])
+        stage[f"{d}d"] = {"nodes": n_d, "stage_ms": prof,
+                          "residual_dof_per_s": 5.0 * n_d / (sum(v for k, v in prof.items() if k != "isolated") * 1e-3)}
+
+    # the same solves one at a time
+    alone = [dg.Mesh(m, o, p) for (m, o, p) in items]
+    qa0 = [torch.tensor(x, device=dev) for x in q_np]
+    qa = [x.clone() for x in qa0]
+
+    def seq_step():
+        d = 0.0
+        for A, x, x0 in zip(alone, qa, qa0):
+            x.copy_(x0)
+            d += A.vcycle(x, None, graph=True, **CYCLE)["dof_evals"]
+        return d
+
+    for _ in range(2):
+        seq_step()
+    launches0 = dg.kernel_launches()
+    ns = max(2, steps // 2)
+    s_ms, s_dofs = timed(seq_step, ns)
+    s_launches = (dg.kernel_launches() - launches0) // ns
+    same = True
+    for g, off, qb in zip(groups, offs, batch_once):
+        for j, k in enumerate(g):
+            same &= bool(np.array_equal(qb[5 * off[j]:5 * off[j + 1]], qa[k].cpu().numpy()))
+    nodes = int(sum(off[-1] for off in offs))
+    del alone, qa, qa0, handles, q, q0
+    torch.cuda.empty_cache()
+    return {"workload": "64 solves: 32 stretched 2D plates + 32 quadratic cubed-sphere shells, 200-4000 "
+                        "elements, orders U[1,8]^d, Mach U_log[0.1,0.4], Re U_log[1e2,1e5], freestream start",
+            "solves": len(items), "handles": "one per dimension (2D: 32 solves, 3D: 32 solves)",
+            "elements": int(sum(m["K"] for (m, _, _) in items)), "nodes": nodes,
+            "dof": 5 * nodes, "step": "one V-cycle 8->1 (b1=2,b2=2,bc=4) of every solve, CUDA graph per handle",
+            "batched": {"value": b_dofs / (b_ms * 1e-3), "unit": "DOF/s", "ms_per_step": b_ms,
+                        "launches_per_step": int(b_launches)},
+            "one_at_a_time": {"value": s_dofs / (s_ms * 1e-3), "unit": "DOF/s", "ms_per_step": s_ms,
+                              "launches_per_step": int(s_launches)},
+            "speedup": s_ms / b_ms, "bitwise_equal_alone": bool(same), "residual_stages": stage,
+            "finite": bool(np.all(np.isfinite(norms))), "setup_s": t_setup, "generate_s": t_gen}
+
+
+def roofline_sweep(dg, torch, dev):
+    """Residual stages on 3D periodic affine boxes far larger than L2:
+    N = 3, 5, 7 with 64^3, 43^3 and 32^3 elements (16.8-17.2 M Gauss nodes,
+    ~0.7 GB of state, ~5x the 129 MB L2).  The state is freestream times
+    (1 + 1% seeded uniform noise), generated on the device."""
+    from paper_1806_11456_gb300 import synthetic as syn
+    out = []
+    for N, ne in ((3, 64), (5, 43), (7, 32)):
+        mesh = syn.periodic_box(ne, ne, ne)
+        orders = syn.uniform_orders(mesh["K"], 3, N)
+        prm = syn.flow_params(mach=0.3, re=100.0)
+        t0 = time.time()
+        M = dg.Mesh(mesh, orders, prm)
+        torch.cuda.synchronize()
+        setup = time.time() - t0
+        nodes, _ = M.layout()
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(N)
+        nn = (N + 1) ** 3
+        qinf = torch.tensor(prm[7:12], device=dev, dtype=torch.float64)
+        q = (qinf.view(1, 5, 1) * (1.0 + 0.01 * (2 * torch.rand(mesh["K"], 5, nn, device=dev, dtype=torch.float64,
+                                                                 generator=gen) - 1))).reshape(-1)
+        prof = M.profile_residual(q, None, iters=10)
+        res_ms = sum(v for k, v in prof.items() if k != "isolated")
+        flops = volume_flops_per_node(3, N + 1, affine=True) * nodes
+        tf = flops / (prof["volume"] * 1e-3) / 1e12
+        gbs = 80.0 * nodes / (res_ms * 1e-3) / 1e9  # Q in + r out, the residual's algorithmic bytes
+        out.append({"N": N, "elements": int(mesh["K"]), "nodes": int(nodes), "setup_s": setup,
+                    "residual_ms": res_ms, "residual_dof_per_s": 5.0 * nodes / (res_ms * 1e-3),
+                    "k_volume": {"ms": prof["volume"], "tflops": tf, "frac_fp64_nominal": tf / FP64_PEAK_TFLOPS},
+                    "residual_gbs": gbs, "residual_frac_hbm": gbs / HBM_PEAK_GBS, "stage_ms": prof})
+        del M, q
+        torch.cuda.empty_cache()
+    return out
+
+
 def cpu_baseline_sample(mesh, prm, orders, q, budget_s=15.0):
     from oracle import oracle as orc
     dof = 5.0 * orc.nodes_total(orders, 2)
@@ -346,6 +487,8 @@ def run_gb300(args, rank, world):
                "gpu_launches": None, "roofline": roof, "clocks": clk, "df32": df32}
         out["gpu_launches"] = int(launches)  # library kernels launched in the timed steps
         out["time_to_tol"] = time_to_tolerance(dg, torch, dev)
+        out["batched"] = batched_solves(dg, torch, dev)
+        out["roofline_sweep"] = roofline_sweep(dg, torch, dev)
         out["cpu_baseline"] = cpu_baseline_sample(mesh, prm, orders, q_np) if world == 1 else None
         print(json.dumps(out))
 

@@ -46,7 +46,7 @@ def build(force=False):
     with concurrent.futures.ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(_compile, SOURCES))
     if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        subprocess.check_call([_nvcc()] + ARCH + ["-shared", "-o", LIB] + objs + ["-lcudart"])
+        subprocess.check_call([_nvcc()] + ARCH + ["-shared", "-o", LIB] + objs + ["-lcudart", "-Xcompiler", "-pthread"])
     return LIB
 
 

@@ -10,8 +10,10 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <atomic>
 #include <cstring>
 #include <mutex>
+#include <thread>
 
 #include "dg_internal.h"
 
@@ -333,6 +335,24 @@ int dev_upload(T** dst, const std::vector<T>& src) {
   return DG_OK;
 }
 
+// Runs f(begin, end) on contiguous blocks of [0, n) on up to 16 host threads
+// (one block when n is small).  Every f must write only its own block.
+template <class F>
+void parallel_for(int n, F f) {
+  unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  int nt = (int)std::min<unsigned>(std::min(hw, 16u), (unsigned)std::max(1, n / 256));
+  if (nt <= 1) {
+    f(0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t) {
+    int b = (int)((int64_t)n * t / nt), e = (int)((int64_t)n * (t + 1) / nt);
+    th.emplace_back([=, &f] { f(b, e); });
+  }
+  for (auto& x : th) x.join();
+}
+
 int dev_zeros(double** dst, size_t n) {
   DG_CUDA_TRY(cudaMalloc((void**)dst, std::max<size_t>(1, n) * sizeof(double)));
   DG_CUDA_TRY(cudaMemset(*dst, 0, std::max<size_t>(1, n) * sizeof(double)));
@@ -380,28 +400,40 @@ int build_level(const dg_mesh* m, const std::vector<int32_t>& orders, Level* L) 
   int npe = (dim == 3) ? Mp * Mp * Mp : Mp * Mp;
   std::vector<double> geo((size_t)10 * L->nodes);
   std::vector<std::vector<double>> elemJa(K);
-  bool affine = true;
-  for (int e = 0; e < K; ++e) {
-    std::vector<double> Ja, J;
-    int n[3] = {nvec[e * 3], nvec[e * 3 + 1], nvec[e * 3 + 2]};
-    element_geometry(ME, m->xmap.data() + (size_t)e * npe * 3, n, dim, Ja, J);
-    int nn = n[0] * n[1] * n[2];
-    for (int nd = 0; nd < nn; ++nd) {
-      if (!(J[nd] > 0.0)) {
-        set_error("element " + std::to_string(e) + " has a non-positive Jacobian");
-        return DG_EINVAL;
+  std::atomic<int> bad{K};             // smallest element with J <= 0
+  std::atomic<bool> affine_all{true};
+  parallel_for(K, [&](int e0, int e1) {
+    bool affine = true;
+    for (int e = e0; e < e1; ++e) {
+      std::vector<double> Ja, J;
+      int n[3] = {nvec[e * 3], nvec[e * 3 + 1], nvec[e * 3 + 2]};
+      element_geometry(ME, m->xmap.data() + (size_t)e * npe * 3, n, dim, Ja, J);
+      int nn = n[0] * n[1] * n[2];
+      for (int nd = 0; nd < nn; ++nd) {
+        if (!(J[nd] > 0.0)) {
+          int cur = bad.load();
+          while (e < cur && !bad.compare_exchange_weak(cur, e)) {
+          }
+          break;
+        }
+        for (int c = 0; c < 9; ++c) geo[(size_t)c * L->nodes + L->off[e] + nd] = Ja[nd * 9 + c];
+        geo[(size_t)9 * L->nodes + L->off[e] + nd] = 1.0 / J[nd];
       }
-      for (int c = 0; c < 9; ++c) geo[(size_t)c * L->nodes + L->off[e] + nd] = Ja[nd * 9 + c];
-      geo[(size_t)9 * L->nodes + L->off[e] + nd] = 1.0 / J[nd];
+      // affine element: every metric component equal to its value at node 0
+      double scale = 0.0, dev = 0.0;
+      for (int c = 0; c < 9; ++c) scale = std::max(scale, std::fabs(Ja[c]));
+      for (int nd = 1; nd < nn; ++nd)
+        for (int c = 0; c < 9; ++c) dev = std::max(dev, std::fabs(Ja[nd * 9 + c] - Ja[c]));
+      if (dev > 1e-13 * scale) affine = false;
+      elemJa[e] = std::move(Ja);
     }
-    // affine element: every metric component equal to its value at node 0
-    double scale = 0.0, dev = 0.0;
-    for (int c = 0; c < 9; ++c) scale = std::max(scale, std::fabs(Ja[c]));
-    for (int nd = 1; nd < nn; ++nd)
-      for (int c = 0; c < 9; ++c) dev = std::max(dev, std::fabs(Ja[nd * 9 + c] - Ja[c]));
-    if (dev > 1e-13 * scale) affine = false;
-    elemJa[e] = std::move(Ja);
+    if (!affine) affine_all.store(false);
+  });
+  if (bad.load() < K) {
+    set_error("element " + std::to_string(bad.load()) + " has a non-positive Jacobian");
+    return DG_EINVAL;
   }
+  bool affine = affine_all.load();
   L->affine = affine;
   L->nvec_host = nvec;
   // ---- element-face offsets and own outward face metrics ----
@@ -418,29 +450,31 @@ int build_level(const dg_mesh* m, const std::vector<int32_t>& orders, Level* L) 
     }
   L->face_nodes = acc;
   std::vector<double> fnS((size_t)3 * acc);
-  for (int e = 0; e < K; ++e) {
-    const int* n = &nvec[e * 3];
-    for (int f = 0; f < nf; ++f) {
-      int d, ta, tb, side;
-      face_dirs(f, &d, &ta, &tb, &side);
-      const double* lb = side ? T.lp[n[d]] : T.lm[n[d]];
-      double sg = side ? 1.0 : -1.0;
-      for (int ib = 0; ib < n[tb]; ++ib)
-        for (int ia = 0; ia < n[ta]; ++ia) {
-          double v[3] = {0, 0, 0};
-          for (int k = 0; k < n[d]; ++k) {
-            int idx[3];
-            idx[d] = k;
-            idx[ta] = ia;
-            idx[tb] = ib;
-            int nd = (idx[2] * n[1] + idx[1]) * n[0] + idx[0];
-            for (int c = 0; c < 3; ++c) v[c] += lb[k] * elemJa[e][nd * 9 + d * 3 + c];
+  parallel_for(K, [&](int e0, int e1) {
+    for (int e = e0; e < e1; ++e) {
+      const int* n = &nvec[e * 3];
+      for (int f = 0; f < nf; ++f) {
+        int d, ta, tb, side;
+        face_dirs(f, &d, &ta, &tb, &side);
+        const double* lb = side ? T.lp[n[d]] : T.lm[n[d]];
+        double sg = side ? 1.0 : -1.0;
+        for (int ib = 0; ib < n[tb]; ++ib)
+          for (int ia = 0; ia < n[ta]; ++ia) {
+            double v[3] = {0, 0, 0};
+            for (int k = 0; k < n[d]; ++k) {
+              int idx[3];
+              idx[d] = k;
+              idx[ta] = ia;
+              idx[tb] = ib;
+              int nd = (idx[2] * n[1] + idx[1]) * n[0] + idx[0];
+              for (int c = 0; c < 3; ++c) v[c] += lb[k] * elemJa[e][nd * 9 + d * 3 + c];
+            }
+            int64_t p = fo[e * 6 + f] + ib * n[ta] + ia;
+            for (int c = 0; c < 3; ++c) fnS[(size_t)c * acc + p] = sg * v[c];
           }
-          int64_t p = fo[e * 6 + f] + ib * n[ta] + ia;
-          for (int c = 0; c < 3; ++c) fnS[(size_t)c * acc + p] = sg * v[c];
-        }
+      }
     }
-  }
+  });
   // ---- mortars ----
   std::vector<MortarDev> mortars;
   std::vector<double> mnS;

@@ -545,3 +545,32 @@ def config_flat_plate_c2(N=7):
     orders = uniform_orders(mesh["K"], 2, N)
     q = freestream_state(mesh, orders, prm)
     return mesh, orders, prm, q
+
+
+def batch_workload_c4(seed=3, nsolves=64, kmin=200, kmax=4000, nmax=8, sphere_M=2):
+    """Many independent steady solves: half stretched 2D plate-type meshes,
+    half cubed-sphere shells.  Element counts log-uniform in [kmin, kmax],
+    orders i.i.d. uniform in [1, nmax]^dim, Mach log-uniform in [0.1, 0.4],
+    Re log-uniform in [1e2, 1e5].  Returns [(mesh, orders, params), ...]."""
+    rng = np.random.default_rng(seed)
+    items, shells = [], {}
+    for k in range(nsolves):
+        target = float(np.exp(rng.uniform(np.log(kmin), np.log(kmax))))
+        mach = float(np.exp(rng.uniform(np.log(0.1), np.log(0.4))))
+        re = float(np.exp(rng.uniform(np.log(1e2), np.log(1e5))))
+        if k % 2 == 0:
+            # plate-type: nx : ny = 5 : 2 as in the 60 x 24 plate
+            ny = max(2, int(round(np.sqrt(target / 2.5))))
+            nx = max(2, int(round(target / ny)))
+            mesh = flat_plate_mesh(nx=nx, ny=ny, dy0=float(10 ** rng.uniform(-3, -2)), ratio=1.15)
+            orders = random_orders(mesh["K"], 2, 1, nmax, seed * 1000 + k)
+        else:
+            # shell: 6 nt^2 nr elements with nr ~ 4/3 nt as in 6 x 12 x 12 x 16
+            nt = max(1, int(round((target / 8.0) ** (1.0 / 3.0))))
+            nr = max(2, int(round(target / (6.0 * nt * nt))))
+            if (nt, nr) not in shells:  # same shape, same mesh: built once
+                shells[(nt, nr)] = cubed_sphere_mesh(nt, nr, M=sphere_M)
+            mesh = shells[(nt, nr)]
+            orders = random_orders(mesh["K"], 3, 1, nmax, seed * 1000 + k)
+        items.append((mesh, orders, flow_params(mach=mach, re=re)))
+    return items
