@@ -17,6 +17,8 @@ constexpr int kNMax = 12;               // highest polynomial order
 constexpr int kNP = kNMax + 2;          // table stride (n = 1 .. kNMax+1)
 constexpr int kMaxElemNodes = 729;      // 3D element node cap (smem staging)
 constexpr int kTileNodes = 128;         // element-kernel CTA size (threads) and tile target
+constexpr int kVolThreads = 512;        // launch bound of the element-tile kernels with staged tiles
+constexpr int kTileClasses = 3;         // tiles of <= 128, <= 256 and more nodes (one element)
 constexpr int kMortarTile = 64;         // mortar-kernel CTA size (threads) and tile target
 constexpr int kMortarTileMax = 169;     // a single mortar of 13 x 13 nodes forms its own tile
 constexpr int kTauSlots = 16;           // orders per direction in the tau table
@@ -72,11 +74,14 @@ struct MortarDev {     // one mortar (a face pair or a boundary face)
   int32_t ma, mb;      // mortar nodes per tangential direction (L frame)
   int32_t node_off;    // first mortar node
   int32_t flags;       // bit0: both sides conforming with the mortar
+  int32_t out_off;     // first of its face nodes (L side, then R side) within its tile
+  int32_t pad;
 };
 
 struct MortarTile {    // one CTA of a mortar kernel
   int32_t first, count;     // mortars
   int32_t node_first, nodes;
+  int32_t outs;             // face nodes written (both sides of every mortar)
 };
 
 struct GasD {  // FP64 constants of the CFL kernel
@@ -121,6 +126,8 @@ struct Level {
   ElemTile* d_tiles = nullptr;
   int n_tiles = 0;
   size_t tile_smem_nodes = 0;           // max nodes of a tile
+  int tile_class_end[kTileClasses] = {0, 0, 0};    // tiles are ordered by class; cumulative ends
+  int tile_class_nodes[kTileClasses] = {0, 0, 0};  // max nodes of a tile of each class
   double* d_vol = nullptr;              // 5 x nodes volume part
   bool affine = false;                  // metrics constant within every element
   double* d_geo2 = nullptr;             // float-pair copies for the double-float kernels (lazy)

@@ -466,6 +466,9 @@ DEV int pick(int k, int a0, int a1, int a2) { return k == 0 ? a0 : (k == 1 ? a1 
 
 // Interpolate face values (NVAR comps, stride fs) of an na x nb face to the
 // mortar point (ia, ib) of an ma x mb rule.
+// Value at mortar node (ia, ib) (face frame of the trace) of a face trace with
+// na x nb nodes, interpolated to ma x mb mortar nodes.  A direction in which
+// the face already has the mortar's order is the identity and is skipped.
 template <typename R, int NVAR>
 DEV void face_interp(const typename Store<R>::T* X, int64_t fs, int na, int nb, int ma, int mb, int ia, int ib,
                      R* out) {
@@ -478,12 +481,15 @@ DEV void face_interp(const typename Store<R>::T* X, int64_t fs, int na, int nb, 
   }
   const typename Store<R>::T* Ta = Tab<R>::T() + ((size_t)na * kNP + ma) * kNP * kNP + ia * na;
   const typename Store<R>::T* Tb = Tab<R>::T() + ((size_t)nb * kNP + mb) * kNP * kNP + ib * nb;
+  const bool ida = (na == ma), idb = (nb == mb);
+  const int a0 = ida ? ia : 0, a1 = ida ? ia + 1 : na;
+  const int b0 = idb ? ib : 0, b1 = idb ? ib + 1 : nb;
 #pragma unroll
   for (int v = 0; v < NVAR; ++v) out[v] = cst<R>(0.0f);
-  for (int kb = 0; kb < nb; ++kb) {
-    const R wb = SR::get(Tb, kb);
-    for (int ka = 0; ka < na; ++ka) {
-      const R wgt = wb * SR::get(Ta, ka);
+  for (int kb = b0; kb < b1; ++kb) {
+    const R wb = idb ? cst<R>(1.0f) : SR::get(Tb, kb);
+    for (int ka = a0; ka < a1; ++ka) {
+      const R wgt = ida ? wb : wb * SR::get(Ta, ka);
       int p = kb * na + ka;
 #pragma unroll
       for (int v = 0; v < NVAR; ++v) out[v] += wgt * SR::get(X, v * fs + p);
@@ -650,6 +656,37 @@ DEV void mortar_node_value(const LevelArgsT<R>& A, const MortarArgsT<R>& MA, con
   for (int v = 0; v < 5; ++v) o[v] = S * f[v];
 }
 
+// L2 projection of mortar values (ma x mb nodes in the mortar's L frame,
+// stride 5 per node) onto face node (ka, kb) of a side with na x nb nodes.
+// (Ma, Mb) are the mortar's node counts in that side's frame and `orient`
+// the face orientation code from the L frame to it (0 for the L side).  A
+// direction in which the side has the mortar's order is the identity.
+template <typename R, int NV>
+DEV void mortar_project(const R* vals, int ma, int mb, int Ma, int Mb, int orient, int na, int nb, int ka, int kb,
+                        R* acc) {
+  using SR = Store<R>;
+  const bool ida = (na == Ma), idb = (nb == Mb);
+  const typename SR::T* Pa = Tab<R>::T() + ((size_t)Ma * kNP + na) * kNP * kNP + ka * Ma;
+  const typename SR::T* Pb = Tab<R>::T() + ((size_t)Mb * kNP + nb) * kNP * kNP + kb * Mb;
+  const int a0 = ida ? ka : 0, a1 = ida ? ka + 1 : Ma;
+  const int b0 = idb ? kb : 0, b1 = idb ? kb + 1 : Mb;
+  const bool sw = orient & 1;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = cst<R>(0.0f);
+  for (int ib = b0; ib < b1; ++ib) {
+    const R wb = idb ? cst<R>(1.0f) : SR::get(Pb, ib);
+    const int jb = (orient & 4) ? Mb - 1 - ib : ib;
+    for (int ia = a0; ia < a1; ++ia) {
+      const R wgt = ida ? wb : wb * SR::get(Pa, ia);
+      const int ja = (orient & 2) ? Ma - 1 - ia : ia;
+      const int aa = sw ? jb : ja, bb = sw ? ja : jb;  // back to the L frame
+      const R* x = vals + (bb * ma + aa) * 5;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] += wgt * x[v];
+    }
+  }
+}
+
 template <typename R, int PASS>
 __global__ void __launch_bounds__(kMortarTile, 8) k_mortar(LevelArgsT<R> A, MortarArgsT<R> MA,
                                                            const GasT<R>* __restrict__ gas,
@@ -666,75 +703,39 @@ __global__ void __launch_bounds__(kMortarTile, 8) k_mortar(LevelArgsT<R> A, Mort
     const GasT<R>& G = gas[A.slot[MA.mortars[MA.mnode_mortar[gp]].eL]];
     mortar_node_value<R, PASS>(A, MA, G, trq, trg, gp, sval + i * 5);
   }
-  if (threadIdx.x == 0) {
-    int acc = 0;
-    for (int m = 0; m < mt.count; ++m) {
-      const MortarDev M = MA.mortars[mt.first + m];
-      int dL, taL, tbL, sL;
-      face_dirs(M.fL, dL, taL, tbL, sL);
-      scum[m] = acc;
-      acc += A.n[M.eL * 3 + taL] * A.n[M.eL * 3 + tbL];
-      if (M.eR >= 0) {
-        int dR, taR, tbR, sR;
-        face_dirs(M.fR, dR, taR, tbR, sR);
-        acc += A.n[M.eR * 3 + taR] * A.n[M.eR * 3 + tbR];
-      }
-    }
-    scum[mt.count] = acc;
-  }
+  for (int m = threadIdx.x; m < mt.count; m += blockDim.x) scum[m] = MA.mortars[mt.first + m].out_off;
+  if (threadIdx.x == 0) scum[mt.count] = mt.outs;
   __syncthreads();
-  const int total = scum[mt.count];
-  for (int i = threadIdx.x; i < total; i += blockDim.x) {
-    int m = 0;
-    while (scum[m + 1] <= i) ++m;
-    const MortarDev M = MA.mortars[mt.first + m];
-    int r = i - scum[m];
+  // L2 projection of the mortar values back onto each side's face nodes
+  for (int i = threadIdx.x; i < mt.outs; i += blockDim.x) {
+    int lo = 0, hi = mt.count - 1;  // the mortar whose outputs hold i
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (scum[mid] <= i) lo = mid;
+      else hi = mid - 1;
+    }
+    const MortarDev M = MA.mortars[mt.first + lo];
+    int r = i - scum[lo];
     const R* vals = sval + (M.node_off - mt.node_first) * 5;
     int dL, taL, tbL, sL;
     face_dirs(M.fL, dL, taL, tbL, sL);
     const int nLa = A.n[M.eL * 3 + taL], nLb = A.n[M.eL * 3 + tbL];
     R acc[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] = cst<R>(0.0f);
     int64_t dst;
     bool neg = false;
     if (r < nLa * nLb) {
-      int ka = r % nLa, kb = r / nLa;
       dst = A.fo[M.eL * 6 + M.fL] + r;
-      if (M.flags & 1) {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) acc[v] = vals[r * 5 + v];
-      } else {
-        const typename SR::T* Pa = Tab<R>::T() + ((size_t)M.ma * kNP + nLa) * kNP * kNP + ka * M.ma;
-        const typename SR::T* Pb = Tab<R>::T() + ((size_t)M.mb * kNP + nLb) * kNP * kNP + kb * M.mb;
-        for (int bb = 0; bb < M.mb; ++bb)
-          for (int aa = 0; aa < M.ma; ++aa) {
-            const R wgt = SR::get(Pa, aa) * SR::get(Pb, bb);
-#pragma unroll
-            for (int v = 0; v < NV; ++v) acc[v] += wgt * vals[(bb * M.ma + aa) * 5 + v];
-          }
-      }
+      mortar_project<R, NV>(vals, M.ma, M.mb, M.ma, M.mb, 0, nLa, nLb, r % nLa, r / nLa, acc);
     } else {
       r -= nLa * nLb;
       int dR, taR, tbR, sR;
       face_dirs(M.fR, dR, taR, tbR, sR);
       const int Ra = A.n[M.eR * 3 + taR], Rb = A.n[M.eR * 3 + tbR];
       const bool sw = M.orient & 1;
-      const int Ma = sw ? M.mb : M.ma, Mb = sw ? M.ma : M.mb;
-      int ka = r % Ra, kb = r / Ra;
       dst = A.fo[M.eR * 6 + M.fR] + r;
       neg = (PASS == 2);
-      const typename SR::T* Pa = Tab<R>::T() + ((size_t)Ma * kNP + Ra) * kNP * kNP + ka * Ma;
-      const typename SR::T* Pb = Tab<R>::T() + ((size_t)Mb * kNP + Rb) * kNP * kNP + kb * Mb;
-      for (int bb = 0; bb < M.mb; ++bb)
-        for (int aa = 0; aa < M.ma; ++aa) {
-          int ia = sw ? bb : aa, ib = sw ? aa : bb;
-          if (M.orient & 2) ia = Ma - 1 - ia;
-          if (M.orient & 4) ib = Mb - 1 - ib;
-          const R wgt = SR::get(Pa, ia) * SR::get(Pb, ib);
-#pragma unroll
-          for (int v = 0; v < NV; ++v) acc[v] += wgt * vals[(bb * M.ma + aa) * 5 + v];
-        }
+      mortar_project<R, NV>(vals, M.ma, M.mb, sw ? M.mb : M.ma, sw ? M.ma : M.mb, M.orient, Ra, Rb, r % Ra, r / Ra,
+                            acc);
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v) SR::put(out, v * A.fn + dst, neg ? -acc[v] : acc[v]);
@@ -889,15 +890,18 @@ DEV void divergence(const R* sD, const R* sA, int T, int nn, int i, int n0, int 
   }
 }
 
+// Register caps: 96 in 2D keeps five 128-thread CTAs per SM (a 100-register
+// build rounds to 104 and fits only four); 104 in 3D, 128 for the isolated
+// kernel in 3D (it spills at 104).
 template <typename R, int DIM, bool AFFINE>
-__global__ void __launch_bounds__(kTileNodes) k_volume(LevelArgsT<R> A, const GasT<R>* __restrict__ gas,
-                                                       const double* __restrict__ q,
-                                                       const typename Store<R>::T* __restrict__ ust,
-                                                       typename Store<R>::T* __restrict__ trg,
-                                                       typename Store<R>::T* __restrict__ vol) {
+__global__ void __launch_bounds__(kVolThreads) __maxnreg__(DIM == 2 ? 96 : 104) k_volume(LevelArgsT<R> A, int tile0, const GasT<R>* __restrict__ gas,
+                                                        const double* __restrict__ q,
+                                                        const typename Store<R>::T* __restrict__ ust,
+                                                        typename Store<R>::T* __restrict__ trg,
+                                                        typename Store<R>::T* __restrict__ vol) {
   using SR = Store<R>;
   extern __shared__ double smem_raw[];
-  const ElemTile t = A.tiles[blockIdx.x];
+  const ElemTile t = A.tiles[tile0 + blockIdx.x];
   const int n0 = t.n[0], n1 = t.n[1], n2 = t.n[2];
   const int nn = n0 * n1 * n2;
   const int T = t.count * nn;
@@ -1059,13 +1063,13 @@ struct TauArgs {
 };
 
 template <typename R, int DIM, bool AFFINE>
-__global__ void __launch_bounds__(kTileNodes) k_isolated(LevelArgsT<R> A, const GasT<R>* __restrict__ gas,
-                                                         const double* __restrict__ q,
-                                                         const double* __restrict__ s, double* __restrict__ r,
-                                                         TauArgs tau) {
+__global__ void __launch_bounds__(kVolThreads) __maxnreg__(DIM == 2 ? 96 : 128) k_isolated(LevelArgsT<R> A, int tile0, const GasT<R>* __restrict__ gas,
+                                                          const double* __restrict__ q,
+                                                          const double* __restrict__ s, double* __restrict__ r,
+                                                          TauArgs tau) {
   using SR = Store<R>;
   extern __shared__ double smem_raw[];
-  const ElemTile t = A.tiles[blockIdx.x];
+  const ElemTile t = A.tiles[tile0 + blockIdx.x];
   const int n0 = t.n[0], n1 = t.n[1], n2 = t.n[2];
   const int nn = n0 * n1 * n2;
   const int T = t.count * nn;
@@ -1245,10 +1249,6 @@ __global__ void k_sub3(double* o, const double* a, const double* b, int64_t n) {
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
-static size_t vol_smem(const Level* L) {
-  return (size_t)(3 * kNP * kNP + 32 * L->tile_smem_nodes) * sizeof(double);
-}
-
 template <typename R, int DIM, bool AFF>
 static int set_attrs() {
   const int big = (int)((3 * kNP * kNP + 32 * kMaxElemNodes) * sizeof(double));
@@ -1388,43 +1388,60 @@ static void launch_trace(const Level* L, const double* q, cudaStream_t st) {
   else
     k_trace_q<R, 3><<<L->n_tiles, kTileNodes, sm, st>>>(A, q, buf<R>(L->d_trq));
 }
+// The staged element kernels run once per tile class: tiles of <= 128 nodes
+// with 128 threads, <= 256 with 256, larger (one element of up to 729 nodes)
+// with 512, each class with the shared memory of its own largest tile.
+template <typename F>
+static void for_tile_classes(const Level* L, F launch) {
+  static const int threads[kTileClasses] = {kTileNodes, 2 * kTileNodes, kVolThreads};
+  int begin = 0;
+  for (int c = 0; c < kTileClasses; ++c) {
+    const int end = L->tile_class_end[c];
+    if (end > begin) {
+      ++g_launches;
+      launch(begin, end - begin, threads[c], (size_t)(3 * kNP * kNP + 32 * L->tile_class_nodes[c]) * sizeof(double));
+    }
+    begin = end;
+  }
+}
+
 template <typename R>
 static void launch_volume(const Level* L, const GasT<R>* G, const double* q, cudaStream_t st) {
-  ++g_launches;
-  const size_t sm = vol_smem(L);
   LevelArgsT<R> A = largs<R>(L);
   const ST<R>* ust = buf<R>(L->d_ust);
   ST<R>* trg = buf<R>(L->d_trg);
   ST<R>* vol = buf<R>(L->d_vol);
-  if (L->dim == 2) {
-    if (L->affine)
-      k_volume<R, 2, true><<<L->n_tiles, kTileNodes, sm, st>>>(A, G, q, ust, trg, vol);
-    else
-      k_volume<R, 2, false><<<L->n_tiles, kTileNodes, sm, st>>>(A, G, q, ust, trg, vol);
-  } else {
-    if (L->affine)
-      k_volume<R, 3, true><<<L->n_tiles, kTileNodes, sm, st>>>(A, G, q, ust, trg, vol);
-    else
-      k_volume<R, 3, false><<<L->n_tiles, kTileNodes, sm, st>>>(A, G, q, ust, trg, vol);
-  }
+  for_tile_classes(L, [&](int t0, int nt, int th, size_t sm) {
+    if (L->dim == 2) {
+      if (L->affine)
+        k_volume<R, 2, true><<<nt, th, sm, st>>>(A, t0, G, q, ust, trg, vol);
+      else
+        k_volume<R, 2, false><<<nt, th, sm, st>>>(A, t0, G, q, ust, trg, vol);
+    } else {
+      if (L->affine)
+        k_volume<R, 3, true><<<nt, th, sm, st>>>(A, t0, G, q, ust, trg, vol);
+      else
+        k_volume<R, 3, false><<<nt, th, sm, st>>>(A, t0, G, q, ust, trg, vol);
+    }
+  });
 }
 template <typename R>
 static void launch_isolated(const Level* L, const GasT<R>* G, const double* q, const double* s, double* r,
                             const TauArgs& ta, cudaStream_t st) {
-  ++g_launches;
-  const size_t sm = vol_smem(L);
   LevelArgsT<R> A = largs<R>(L);
-  if (L->dim == 2) {
-    if (L->affine)
-      k_isolated<R, 2, true><<<L->n_tiles, kTileNodes, sm, st>>>(A, G, q, s, r, ta);
-    else
-      k_isolated<R, 2, false><<<L->n_tiles, kTileNodes, sm, st>>>(A, G, q, s, r, ta);
-  } else {
-    if (L->affine)
-      k_isolated<R, 3, true><<<L->n_tiles, kTileNodes, sm, st>>>(A, G, q, s, r, ta);
-    else
-      k_isolated<R, 3, false><<<L->n_tiles, kTileNodes, sm, st>>>(A, G, q, s, r, ta);
-  }
+  for_tile_classes(L, [&](int t0, int nt, int th, size_t sm) {
+    if (L->dim == 2) {
+      if (L->affine)
+        k_isolated<R, 2, true><<<nt, th, sm, st>>>(A, t0, G, q, s, r, ta);
+      else
+        k_isolated<R, 2, false><<<nt, th, sm, st>>>(A, t0, G, q, s, r, ta);
+    } else {
+      if (L->affine)
+        k_isolated<R, 3, true><<<nt, th, sm, st>>>(A, t0, G, q, s, r, ta);
+      else
+        k_isolated<R, 3, false><<<nt, th, sm, st>>>(A, t0, G, q, s, r, ta);
+    }
+  });
 }
 template <typename R>
 static void launch_surface(const Level* L, const double* s, double* r, double* norm, const RKArgs& rk,

@@ -508,6 +508,8 @@ int build_level(const dg_mesh* m, const std::vector<int32_t>& orders, Level* L) 
       M.ma = ma; M.mb = mb;
       M.node_off = (int32_t)mnodes;
       M.flags = conf ? 1 : 0;
+      M.out_off = 0;  // set with the tiles
+      M.pad = 0;
       mortars.push_back(M);
       // mortar-node metric: L face metric interpolated to the mortar nodes
       std::vector<double> Ia((size_t)ma * nLa), Ib((size_t)mb * nLb);
@@ -532,22 +534,33 @@ int build_level(const dg_mesh* m, const std::vector<int32_t>& orders, Level* L) 
   mnS.assign((size_t)3 * mnodes, 0.0);
   for (int64_t p = 0; p < mnodes; ++p)
     for (int c = 0; c < 3; ++c) mnS[(size_t)c * mnodes + p] = mgeo[p][c];
-  // mortar tiles: whole mortars, at most kMortarTile nodes each
+  // mortar tiles: whole mortars, at most kMortarTile nodes each; every
+  // mortar records where its face nodes start among the tile's outputs
   std::vector<MortarTile> mtiles;
   {
-    MortarTile cur{0, 0, 0, 0};
+    MortarTile cur{0, 0, 0, 0, 0};
     for (int i = 0; i < (int)mortars.size(); ++i) {
-      int sz = mortars[i].ma * mortars[i].mb;
+      MortarDev& M = mortars[i];
+      int sz = M.ma * M.mb;
       if (cur.count > 0 && cur.nodes + sz > kMortarTile) {
         mtiles.push_back(cur);
-        cur = MortarTile{i, 0, mortars[i].node_off, 0};
+        cur = MortarTile{i, 0, M.node_off, 0, 0};
       }
       if (cur.count == 0) {
         cur.first = i;
-        cur.node_first = mortars[i].node_off;
+        cur.node_first = M.node_off;
       }
+      int d, ta, tb, side;
+      face_dirs(M.fL, &d, &ta, &tb, &side);
+      int outs = nvec[M.eL * 3 + ta] * nvec[M.eL * 3 + tb];
+      if (M.eR >= 0) {
+        face_dirs(M.fR, &d, &ta, &tb, &side);
+        outs += nvec[M.eR * 3 + ta] * nvec[M.eR * 3 + tb];
+      }
+      M.out_off = cur.outs;
       cur.count++;
       cur.nodes += sz;
+      cur.outs += outs;
     }
     if (cur.count > 0) mtiles.push_back(cur);
   }
@@ -579,6 +592,21 @@ int build_level(const dg_mesh* m, const std::vector<int32_t>& orders, Level* L) 
       max_nodes = std::max(max_nodes, (size_t)t.count * nn);
     }
   }
+  // launch classes by tile size (the staged kernels size their shared memory
+  // and threads per class): <= 128 nodes, <= 256, larger
+  auto tile_class = [](const ElemTile& t) {
+    const int T = t.count * t.n[0] * t.n[1] * t.n[2];
+    return T <= kTileNodes ? 0 : (T <= 2 * kTileNodes ? 1 : 2);
+  };
+  std::stable_sort(tiles.begin(), tiles.end(),
+                   [&](const ElemTile& a, const ElemTile& b) { return tile_class(a) < tile_class(b); });
+  for (int c = 0; c < kTileClasses; ++c) L->tile_class_end[c] = L->tile_class_nodes[c] = 0;
+  for (const ElemTile& t : tiles) {
+    const int c = tile_class(t);
+    L->tile_class_end[c]++;
+    L->tile_class_nodes[c] = std::max(L->tile_class_nodes[c], t.count * t.n[0] * t.n[1] * t.n[2]);
+  }
+  for (int c = 1; c < kTileClasses; ++c) L->tile_class_end[c] += L->tile_class_end[c - 1];
   L->n_tiles = (int)tiles.size();
   L->tile_smem_nodes = max_nodes;
   // ---- upload ----

@@ -22,7 +22,7 @@ namespace dg {
 
 struct dd {
   float hi, lo;
-  DGR dd() = default;
+  dd() = default;
   DGR constexpr dd(float h, float l) : hi(h), lo(l) {}
   // exact split of a double into a (rounded-to-48-bit) pair
   DGR explicit dd(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
