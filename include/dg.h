@@ -182,8 +182,16 @@ typedef struct {
   int32_t coarsest;   /* lowest level order (1 = N_coarse = 1) */
   int32_t delta_n;    /* order drop between consecutive levels (Sec. 3.1 uses 1); <= 0 means 1 */
   int32_t graph;      /* 1: capture the cycle's launches as a CUDA graph on the first call with these
-                         arrays and parameters, replay it on later calls (same result) */
-  int32_t reserved;
+                         arrays and parameters, replay it on later calls (same result); ignored
+                         when control > 0 (the sweep counts are then decided on the host) */
+  int32_t control;    /* 0: fixed sweep counts.  n > 0: residual-based smoothing of Sec. 3.1.2 on
+                         every level above the coarsest, at most n blocks per rule: pre-smoothing
+                         repeats blocks of beta1 sweeps until max|r^P| < eta max|I r^P| (r^P the
+                         level's residual, I the restriction to the next coarser level), post-
+                         smoothing repeats blocks of beta2 sweeps until max|r| is no larger than
+                         after the pre-smoothing.  Decided per solve of a batch (a solve that
+                         meets its rule is not advanced by the other solves' extra blocks). */
+  double eta;         /* pre-smoothing threshold of the rule above (the paper uses 1.1); <= 0: 1.1 */
 } dg_mg_params;
 
 /* What a cycle reports. */

@@ -210,14 +210,25 @@ def n_levels(orders, dim, direction=None):
 # ---------------------------------------------------------------------------
 # FAS V-cycle (Algorithm 1)
 # ---------------------------------------------------------------------------
-def fas_vcycle(mesh, orders, prm, q, s, beta1, beta2, beta_c, direction=None, coarsest=1, delta_n=1):
+def fas_vcycle(mesh, orders, prm, q, s, beta1, beta2, beta_c, direction=None, coarsest=1, delta_n=1,
+               control=0, eta=1.1):
     """One FAS V-cycle from the finest level (orders) down to level `coarsest`,
     the order dropping by delta_n per level (Sec. 3.1 uses 1).
 
     Follows Algorithm 1 with the sign of eq FASIterError (eps = Q - Q0).  At the
     finest level S is the physical source; below it S = A(Q0) + r (eq
     FAScoarseSource).  The coarsest level runs a single block of beta_c sweeps
-    in place of pre + post smoothing.  Returns the new finest-level Q."""
+    in place of pre + post smoothing.  Returns the new finest-level Q.
+
+    control > 0 applies the residual-based smoothing design of Sec. 3.1.2 on
+    every level above the coarsest, with at most `control` blocks per rule:
+    pre-smoothing repeats blocks of beta1 sweeps until the level's residual
+    is below eta times its restriction to the next coarser level,
+    max|r^P| < eta max|I r^P| (P the level, N = P - dN the coarser one, as in
+    the FAS equations; eta = 1.1 in the paper), i.e. until what is left is
+    mostly representable on the coarser level; post-smoothing repeats blocks
+    of beta2 sweeps until max|r| is no larger than it was after the
+    pre-smoothing."""
     dim = mesh["dim"]
     top = n_levels(orders, dim, direction)
     seq = [top]
@@ -237,13 +248,27 @@ def fas_vcycle(mesh, orders, prm, q, s, beta1, beta2, beta_c, direction=None, co
         if level == bottom:
             q = smooth(mesh, o, prm, q, S, beta_c)
         else:
-            q = smooth(mesh, o, prm, q, S, beta1)
             oc = lv_orders[below[level]]
+            blocks = 0
+            while True:  # pre-smoothing
+                q = smooth(mesh, o, prm, q, S, beta1)
+                blocks += 1
+                r = residual(mesh, o, prm, q, S)
+                rc = transfer(dim, o, oc, r)
+                if control <= 0 or blocks >= control or np.max(np.abs(r)) < eta * np.max(np.abs(rc)):
+                    break
+            r_pre = np.max(np.abs(r))
             qc = transfer(dim, o, oc, q)
-            rc = transfer(dim, o, oc, residual(mesh, o, prm, q, S))
             epsc = cycle(below[level], qc, rc, False)
             q = q + transfer(dim, oc, o, epsc)
-            q = smooth(mesh, o, prm, q, S, beta2)
+            blocks = 0
+            while True:  # post-smoothing
+                q = smooth(mesh, o, prm, q, S, beta2)
+                blocks += 1
+                if control <= 0 or blocks >= control:
+                    break
+                if np.max(np.abs(residual(mesh, o, prm, q, S))) <= r_pre:
+                    break
         if finest:
             return q
         return q - q0

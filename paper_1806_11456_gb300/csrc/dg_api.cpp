@@ -77,10 +77,14 @@ struct Cycle {
   double dofs = 0.0;
 };
 
-static int smooth_level(Cycle& C, Level* L, double* Q, const double* Sv, int sweeps) {
+// `sweeps` RK3 sweeps; with a mask (per slot 1/0, device) the slots whose
+// mask is 0 get dt = 0 and are left unchanged.
+static int smooth_level(Cycle& C, Level* L, double* Q, const double* Sv, int sweeps,
+                        const double* mask = nullptr) {
   DG_TRY(ensure_work(L));
   for (int k = 0; k < sweeps; ++k) {
     DG_TRY(cfl_dt(C.m, L, Q, C.m->d_scalars, C.st));
+    if (mask) DG_TRY(mask_dt(C.m, C.m->d_scalars, mask, C.st));
     for (int stage = 0; stage < 3; ++stage) {
       DG_TRY(residual(C.m, L, Q, Sv, nullptr, false, C.st, nullptr, stage, L->d_G, C.m->d_scalars));
       C.evals++;
@@ -107,18 +111,78 @@ static int vcycle_level(Cycle& C, size_t k, double* Qf, const double* Sf) {
   }
   if (k + 1 == C.lv.size()) {
     DG_TRY(smooth_level(C, L, Q, Sv, C.mg.beta_c));
-  } else {
-    DG_TRY(smooth_level(C, L, Q, Sv, C.mg.beta1));
-    DG_TRY(residual(C.m, L, Q, Sv, L->d_R, false, C.st, nullptr, -1, nullptr, nullptr));
+    return DG_OK;
+  }
+  Level* Cc = C.lv[k + 1];
+  DG_TRY(ensure_work(Cc));
+  // Residual-based smoothing (Sec. 3.1.2), decided per solve slot on the host:
+  // d_scalars holds per slot [2n, 3n) max|r^P|, [3n, 4n) max|I r^P|, [4n, 5n)
+  // the mask of the slots still smoothing.
+  const int ns = C.m->nslots;
+  const bool ctl = C.mg.control > 0;
+  const double eta = C.mg.eta > 0.0 ? C.mg.eta : 1.1;
+  double* dN = C.m->d_scalars + 2 * ns;
+  double* dP = C.m->d_scalars + 3 * ns;
+  double* dmask = C.m->d_scalars + 4 * ns;
+  std::vector<double> h(2 * ns), rpre(ns, 0.0);
+  std::vector<char> done(ns, 0);
+  const double* mask = nullptr;
+  // hold the slots that are done for the next block (none while all still run)
+  auto hold_done = [&]() -> int {
+    std::vector<double> hm(ns);
+    for (int j = 0; j < ns; ++j) hm[j] = done[j] ? 0.0 : 1.0;
+    DG_CUDA_TRY(cudaMemcpyAsync(dmask, hm.data(), ns * sizeof(double), cudaMemcpyHostToDevice, C.st));
+    DG_CUDA_TRY(cudaStreamSynchronize(C.st));
+    mask = dmask;
+    return DG_OK;
+  };
+  // pre-smoothing: blocks of beta1 sweeps until max|r^P| < eta max|I r^P|
+  for (int blk = 1;; ++blk) {
+    DG_TRY(smooth_level(C, L, Q, Sv, C.mg.beta1, mask));
+    if (ctl) DG_TRY(fill(dN, 0.0, ns, C.st));
+    DG_TRY(residual(C.m, L, Q, Sv, L->d_R, false, C.st, ctl ? dN : nullptr, -1, nullptr, nullptr));
     C.evals++;
     C.dofs += 5.0 * L->nodes;
-    Level* Cc = C.lv[k + 1];
-    DG_TRY(ensure_work(Cc));
-    DG_TRY(transfer(C.m, L, Cc, 5, Q, Cc->d_Q, C.st));
     DG_TRY(transfer(C.m, L, Cc, 5, L->d_R, Cc->d_S, C.st));
-    DG_TRY(vcycle_level(C, k + 1, nullptr, nullptr));
-    DG_TRY(transfer(C.m, Cc, L, 5, Cc->d_Q, Q, C.st, Cc->d_Q0, true));
-    DG_TRY(smooth_level(C, L, Q, Sv, C.mg.beta2));
+    if (!ctl) break;
+    DG_TRY(slot_maxabs(C.m, Cc, Cc->d_S, dP, C.st));
+    DG_CUDA_TRY(cudaMemcpyAsync(h.data(), dN, 2 * ns * sizeof(double), cudaMemcpyDeviceToHost, C.st));
+    DG_CUDA_TRY(cudaStreamSynchronize(C.st));
+    bool all = true, any = false;
+    for (int j = 0; j < ns; ++j) {
+      if (!done[j]) {
+        rpre[j] = h[j];
+        if (h[j] < eta * h[ns + j] || blk >= C.mg.control) done[j] = 1;
+      }
+      all = all && done[j];
+      any = any || done[j];
+    }
+    if (all) break;
+    if (any) DG_TRY(hold_done());
+  }
+  DG_TRY(transfer(C.m, L, Cc, 5, Q, Cc->d_Q, C.st));
+  DG_TRY(vcycle_level(C, k + 1, nullptr, nullptr));
+  DG_TRY(transfer(C.m, Cc, L, 5, Cc->d_Q, Q, C.st, Cc->d_Q0, true));
+  // post-smoothing: blocks of beta2 sweeps until max|r| <= its value after the pre-smoothing
+  std::fill(done.begin(), done.end(), 0);
+  mask = nullptr;
+  for (int blk = 1;; ++blk) {
+    DG_TRY(smooth_level(C, L, Q, Sv, C.mg.beta2, mask));
+    if (!ctl || blk >= C.mg.control) break;
+    DG_TRY(fill(dN, 0.0, ns, C.st));
+    DG_TRY(residual(C.m, L, Q, Sv, L->d_R, false, C.st, dN, -1, nullptr, nullptr));
+    C.evals++;
+    C.dofs += 5.0 * L->nodes;
+    DG_CUDA_TRY(cudaMemcpyAsync(h.data(), dN, ns * sizeof(double), cudaMemcpyDeviceToHost, C.st));
+    DG_CUDA_TRY(cudaStreamSynchronize(C.st));
+    bool all = true, any = false;
+    for (int j = 0; j < ns; ++j) {
+      if (!done[j] && h[j] <= rpre[j]) done[j] = 1;
+      all = all && done[j];
+      any = any || done[j];
+    }
+    if (all) break;
+    if (any) DG_TRY(hold_done());
   }
   return DG_OK;
 }
@@ -183,7 +247,7 @@ static int run_vcycle(dg_mesh* m, const std::vector<int32_t>& top_orders, double
   DG_TRY(cycle_levels(m, top_orders, mg, &C.lv));
   *nlev = (int)C.lv.size();
   for (Level* L : C.lv) DG_TRY(prepare_arith(m, L, st));  // never allocate inside a capture
-  if (!mg.graph) {
+  if (!mg.graph || mg.control > 0) {  // controlled sweep counts are decided on the host
     DG_TRY(vcycle_level(C, 0, Q, Sv));
     *evals = C.evals;
     *dofs = C.dofs;
@@ -434,7 +498,7 @@ int dg_mesh_create(const dg_mesh_desc* desc, const int32_t* orders, dg_mesh** ou
   int rc = build_level(m, m->orders, m->fine.get());
   if (rc == DG_OK) rc = upload_gas(m);
   if (rc == DG_OK) {
-    cudaError_t e1 = cudaMalloc(&m->d_scalars, (2 * m->nslots + 16) * sizeof(double));
+    cudaError_t e1 = cudaMalloc(&m->d_scalars, (5 * m->nslots + 16) * sizeof(double));
     cudaError_t e2 = cudaMalloc(&m->d_tau, (size_t)m->K * 3 * kTauSlots * sizeof(double));
     cudaError_t e3 = cudaMalloc(&m->d_orders, m->orders.size() * sizeof(int32_t));
     if (e3 == cudaSuccess)
@@ -495,7 +559,7 @@ int dg_batch_create(const dg_mesh_desc* descs, const int32_t* const* orders, int
   int rc = build_level(m, m->orders, m->fine.get());
   if (rc == DG_OK) rc = upload_gas(m);
   if (rc == DG_OK) {
-    cudaError_t e1 = cudaMalloc(&m->d_scalars, (2 * m->nslots + 16) * sizeof(double));
+    cudaError_t e1 = cudaMalloc(&m->d_scalars, (5 * m->nslots + 16) * sizeof(double));
     cudaError_t e2 = cudaMalloc(&m->d_tau, (size_t)m->K * 3 * kTauSlots * sizeof(double));
     cudaError_t e3 = cudaMalloc(&m->d_orders, m->orders.size() * sizeof(int32_t));
     if (e3 == cudaSuccess)
@@ -636,7 +700,8 @@ int dg_smooth(dg_mesh* m, double* q, const double* s, int sweeps, void* stream) 
 int dg_pmg_vcycle(dg_mesh* m, double* q, const double* s, const dg_mg_params* mg, int want_norm,
                   dg_cycle_report* rep, void* stream) {
   if (!m || !q || !mg || mg->beta1 < 0 || mg->beta2 < 0 || mg->beta_c < 0 || mg->coarsest < 1 ||
-      mg->direction < -1 || mg->direction >= m->dim) {
+      mg->direction < -1 || mg->direction >= m->dim || mg->control < 0 ||
+      (mg->control > 0 && (mg->beta1 < 1 || mg->beta2 < 1))) {
     set_error("dg_pmg_vcycle: bad argument");
     return DG_EINVAL;
   }

@@ -159,7 +159,8 @@ struct dg_mesh {
   std::vector<int32_t> orders;
   std::unique_ptr<dg::Level> fine;
   std::map<std::vector<int32_t>, std::unique_ptr<dg::Level>> levels;  // coarse levels by order map
-  double* d_scalars = nullptr;   // [0, nslots) dt per slot, [nslots, 2 nslots) max|r| per slot
+  double* d_scalars = nullptr;   // per slot: [0, n) dt, [n, 2n) max|r|, [2n, 3n) and [3n, 4n) the
+                                 // smoothing-control norms, [4n, 5n) 1/0 smoothing mask (n = nslots)
   double* d_tau = nullptr;       // K x 3 x 16 tau table
   int32_t* d_orders = nullptr;   // K x 3 orders on the device
   cudaStream_t cap_stream = nullptr;  // stream used to capture cycle graphs
@@ -192,6 +193,10 @@ int profile_residual(const dg_mesh* m, Level* L, const double* q, const double* 
                      double* ms_out, cudaStream_t st);
 int transfer(const dg_mesh* m, const Level* from, const Level* to, int nvar, const double* in, double* out,
              cudaStream_t st, const double* sub = nullptr, bool accumulate = false);
+// max |x| per solve slot over a level vector (out zeroed here; device)
+int slot_maxabs(const dg_mesh* m, const Level* L, const double* x, double* out, cudaStream_t st);
+// dt[k] = 0 where mask[k] == 0 (nslots entries, device)
+int mask_dt(const dg_mesh* m, double* dt, const double* mask, cudaStream_t st);
 int fill(double* p, double v, int64_t n, cudaStream_t st);
 int axpby(double* y, double a, const double* x, double b, int64_t n, cudaStream_t st);  // y = a x + b y
 int sub3(double* out, const double* a, const double* b, int64_t n, cudaStream_t st);    // out = a - b

@@ -1041,7 +1041,7 @@ __global__ void __launch_bounds__(kTileNodes) k_surface(LevelArgsT<R> A, const t
         lmax = (rv != rv) ? INFINITY : fmax(lmax, fabs(rv));  // a NaN residual reads as +inf
         if (rk.stage < 0) {
           r[base + v * nn] = rv;
-        } else {
+        } else if (dt != 0.0) {  // dt = 0: the solve is held (smoothing control)
           double gv = (rk.stage == 0 ? 0.0 : rk.a * rk.g[base + v * nn]) + dt * rv;
           rk.g[base + v * nn] = gv;
           rk.qupd[base + v * nn] += rk.b * gv;
@@ -1279,10 +1279,59 @@ static int configure_smem() {
 
 int prepare_capture() { return configure_smem(); }
 
+// max |x| over the nodes and 5 variables of every solve slot (x in the
+// level's layout) into out[slot]; out must be zeroed first
+__global__ void __launch_bounds__(kTileNodes) k_slot_maxabs(LevelArgsT<double> A, const double* __restrict__ x,
+                                                            double* out) {
+  const ElemTile t = A.tiles[blockIdx.x];
+  const int nn = t.n[0] * t.n[1] * t.n[2];
+  const int T = t.count * nn;
+  for (int i0 = 0; i0 < T; i0 += blockDim.x) {  // all lanes iterate together (warp reductions)
+    const int i = i0 + threadIdx.x;
+    const bool active = i < T;
+    double m = 0.0;
+    int slot = 0;
+    if (active) {
+      const int le = i / nn, node = i - le * nn;
+      const int e = A.tile_elems[t.first + le];
+      slot = A.slot[e];
+      const size_t base = (size_t)5 * A.off[e] + node;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double a = x[base + v * nn];
+        m = (a != a) ? INFINITY : fmax(m, fabs(a));
+      }
+    }
+    warp_slot_reduce<true>(out, slot, m, active);
+  }
+}
+
+// dt[k] = 0 for every slot k whose mask is 0 (k_surface then leaves it unchanged)
+__global__ void k_mask_dt(double* dt, const double* mask, int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n && mask[k] == 0.0) dt[k] = 0.0;
+}
+
 static int grid_for(int64_t n) {
   int64_t b = (n + 255) / 256;
   if (b > 152 * 16) b = 152 * 16;
   return (int)std::max<int64_t>(1, b);
+}
+
+int slot_maxabs(const dg_mesh* m, const Level* L, const double* x, double* out, cudaStream_t st) {
+  const int rc = fill(out, 0.0, m->nslots, st);
+  if (rc != DG_OK) return rc;
+  ++g_launches;
+  k_slot_maxabs<<<L->n_tiles, kTileNodes, 0, st>>>(largs<double>(L), x, out);
+  DG_CUDA_TRY(cudaGetLastError());
+  return DG_OK;
+}
+
+int mask_dt(const dg_mesh* m, double* dt, const double* mask, cudaStream_t st) {
+  ++g_launches;
+  k_mask_dt<<<(m->nslots + 127) / 128, 128, 0, st>>>(dt, mask, m->nslots);
+  DG_CUDA_TRY(cudaGetLastError());
+  return DG_OK;
 }
 
 int fill(double* p, double v, int64_t n, cudaStream_t st) {

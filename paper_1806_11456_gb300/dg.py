@@ -34,7 +34,7 @@ class MeshDesc(ctypes.Structure):
 class MGParams(ctypes.Structure):
     _fields_ = [("beta1", ctypes.c_int32), ("beta2", ctypes.c_int32), ("beta_c", ctypes.c_int32),
                 ("direction", ctypes.c_int32), ("coarsest", ctypes.c_int32), ("delta_n", ctypes.c_int32),
-                ("graph", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("graph", ctypes.c_int32), ("control", ctypes.c_int32), ("eta", ctypes.c_double)]
 
 
 class SolveReport(ctypes.Structure):
@@ -267,10 +267,11 @@ class Mesh:
         return q
 
     def vcycle(self, q, s=None, beta1=3, beta2=3, beta_c=3, direction=-1, coarsest=1, delta_n=1,
-               graph=False, want_norm=False, stream=None):
+               graph=False, want_norm=False, control=0, eta=1.1, stream=None):
         mg = MGParams()
         mg.beta1, mg.beta2, mg.beta_c, mg.direction, mg.coarsest, mg.delta_n, mg.graph = \
             beta1, beta2, beta_c, direction, coarsest, delta_n, int(bool(graph))
+        mg.control, mg.eta = int(control), float(eta)
         rep = CycleReport()
         _check(lib().dg_pmg_vcycle(self.h, _ptr(q), _ptr(s), ctypes.byref(mg), int(bool(want_norm)),
                                    ctypes.byref(rep), _stream(stream)))
@@ -311,10 +312,10 @@ class Mesh:
         sp = SolveParams()
         sp.tol, sp.max_cycles, sp.fmg, sp.fmg_tol, sp.adapt = float(tol), int(max_cycles), int(bool(fmg)), \
             float(fmg_tol), int(bool(adapt))
-        m = dict(beta1=3, beta2=3, beta_c=6, direction=-1, coarsest=1, delta_n=1, graph=1)
+        m = dict(beta1=3, beta2=3, beta_c=6, direction=-1, coarsest=1, delta_n=1, graph=1, control=0, eta=1.1)
         m.update(mg or {})
         for k, v in m.items():
-            setattr(sp.mg, k, int(v))
+            setattr(sp.mg, k, float(v) if k == "eta" else int(v))
         sp.ap.tau_max, sp.ap.n_min, sp.ap.n_max, sp.ap.cap, sp.ap.jump_rule, sp.ap.conform_tag = \
             float(tau_max), n_min, n_max, cap, jump_rule, conform_tag
         if len(stages) > 4:

@@ -347,3 +347,38 @@ def test_solve_steady_multistage_parity(dg):
     assert np.array_equal(M.orders, oo)
     assert rep["cycles"] == repo["cycles"]
     assert np.max(np.abs(qd.cpu().numpy() - qo)) <= TOL * np.max(np.abs(qo))
+
+
+def _control_case(N, seed):
+    mesh = syn.box_mesh(np.linspace(-0.2, 1, 5), [0, 0.05, 0.12, 0.3], bc=dict(xmin=1, xmax=2, ymin=4, ymax=1))
+    o = syn.uniform_orders(mesh["K"], 2, N)
+    prm = syn.flow_params(mach=0.3, re=100.0)
+    return mesh, o, prm, syn.perturbed_state(mesh, o, prm, seed, amp=0.05)
+
+
+# (3, 2, 1.5): pre-smoothing stops after 3 blocks; (2, 2, 3.0): post after 2;
+# (3, 0, 1.1): both rules run to the cap of 6 blocks (pinned on the CPU)
+@pytest.mark.parametrize("arith", ARITHS)
+@pytest.mark.parametrize("N,seed,eta,coarsest", [(3, 2, 1.5, 2), (2, 2, 3.0, 1), (3, 0, 1.1, 2), (3, 2, 1.5, 1)])
+def test_vcycle_smoothing_control_parity(dg, N, seed, eta, coarsest, arith):
+    mesh, o, prm, q = _control_case(N, seed)
+    M = dg.Mesh(mesh, o, prm).set_arithmetic(arith)
+    qd = _dev(q)
+    M.vcycle(qd, None, 1, 1, 2, coarsest=coarsest, control=6, eta=eta, graph=True)
+    qo = orc.fas_vcycle(mesh, o, prm, q, None, 1, 1, 2, coarsest=coarsest, control=6, eta=eta)
+    assert np.max(np.abs(qd.cpu().numpy() - qo)) <= TOL * np.max(np.abs(qo))
+
+
+def test_smoothing_control_per_solve_in_a_batch(dg):
+    # three solves whose rules stop after different block counts: each must
+    # come out of the batched cycle exactly as it does alone
+    items = [_control_case(3, seed) for seed in (2, 0, 1)]
+    B = dg.Mesh.batch([(m, o, p) for (m, o, p, _) in items])
+    off = B.solve_slices()
+    qb = _dev(np.concatenate([q for (*_, q) in items]))
+    B.vcycle(qb, None, 1, 1, 2, control=6, eta=1.5)
+    qbn = qb.cpu().numpy()
+    for k, (m, o, p, q) in enumerate(items):
+        qa = _dev(q)
+        dg.Mesh(m, o, p).vcycle(qa, None, 1, 1, 2, control=6, eta=1.5)
+        assert np.array_equal(qbn[5 * off[k]:5 * off[k + 1]], qa.cpu().numpy()), k

@@ -541,3 +541,42 @@ def test_jump_rules_fix_point():
                 for i in range(3):
                     assert lim3[e, i] >= (2 * lim3[nb, m[i]]) // 3
     del rng
+
+
+# ---------------------------------------------------------------------------
+# residual-based smoothing control (Sec. 3.1.2), by brute force
+# ---------------------------------------------------------------------------
+def _control_counts(mesh, o, prm, q, cap, eta):
+    """Blocks of one sweep each that the two rules of Sec. 3.1.2 take on a
+    two-level cycle, found with the oracle's primitives: pre-smoothing stops
+    at the first block with max|r^P| < eta max|I r^P|, post-smoothing at the
+    first block whose residual is no larger than after the pre-smoothing."""
+    dim = mesh["dim"]
+    top = orc.n_levels(o, dim, None)
+    oc = orc.level_orders(o, top - 1, dim, None)
+    qb, pre = q.copy(), 0
+    while True:
+        qb = orc.smooth(mesh, o, prm, qb, None, 1)
+        pre += 1
+        r = orc.residual(mesh, o, prm, qb, None)
+        if pre >= cap or np.max(np.abs(r)) < eta * np.max(np.abs(orc.transfer(dim, o, oc, r))):
+            break
+    r_pre = np.max(np.abs(r))
+    for post in range(1, cap + 1):
+        qj = orc.fas_vcycle(mesh, o, prm, q, None, pre, post, 2, coarsest=top - 1)
+        if np.max(np.abs(orc.residual(mesh, o, prm, qj, None))) <= r_pre:
+            break
+    return pre, post
+
+
+@pytest.mark.parametrize("N,seed,eta,expect", [(3, 2, 1.5, (3, 1)), (2, 2, 3.0, (1, 2)), (3, 0, 1.1, (6, 6))])
+def test_smoothing_control_follows_the_two_rules(N, seed, eta, expect):
+    mesh = syn.box_mesh(np.linspace(-0.2, 1, 5), [0, 0.05, 0.12, 0.3], bc=dict(xmin=1, xmax=2, ymin=4, ymax=1))
+    o = syn.uniform_orders(mesh["K"], 2, N)
+    prm = syn.flow_params(mach=0.3, re=100.0)
+    q = syn.perturbed_state(mesh, o, prm, seed, amp=0.05)
+    pre, post = _control_counts(mesh, o, prm, q, 6, eta)
+    assert (pre, post) == expect  # the case exercises the rule it is meant to
+    got = orc.fas_vcycle(mesh, o, prm, q, None, 1, 1, 2, coarsest=N - 1, control=6, eta=eta)
+    fixed = orc.fas_vcycle(mesh, o, prm, q, None, pre, post, 2, coarsest=N - 1)
+    assert np.array_equal(got, fixed)
