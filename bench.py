@@ -179,25 +179,30 @@ def run_reference(args, rank):
     print(json.dumps(out))
 
 
+def steady_problem(dg, torch, dev, mesh, o, prm, q_target, seed, amp=0.01):
+    """A steady problem whose discrete solution is q_target: S = A(q_target),
+    evaluated by the library (the residual with no source is -A), and a
+    start q_target * (1 + amp * seeded noise).  On a periodic mesh S is
+    compatible by discrete conservation."""
+    M = dg.Mesh(mesh, o, prm)
+    r = M.residual(torch.tensor(q_target, device=dev))
+    S = (-r).cpu().numpy()
+    rng = np.random.default_rng(seed)
+    q0 = q_target * (1.0 + amp * rng.uniform(-1.0, 1.0, q_target.shape))
+    return S, q0
+
+
 def time_to_tolerance(dg, torch, dev, tol=1e-10, max_cycles=3000):
-    """Time to max|r| < tol of the config-1 steady problem (4x4x1 periodic
-    box, N = 3, manufactured state and source, the source made compatible
-    with periodicity) with repeated V-cycles 3 -> 1 (3/3/10 sweeps), CUDA
-    graphs, a residual check every 10 cycles; FP64 and double-float."""
-    from oracle import manufactured as man
-    from oracle import oracle as orc
+    """Time to max|r| < tol of a steady problem on the config-1 mesh (4x4x1
+    periodic box, N = 3, Mach 0.3, Re 100) whose discrete solution is the
+    manufactured field: S = A(q*), start q* with 1% seeded noise; repeated
+    V-cycles 3 -> 1 (3/3/10 sweeps), CUDA graphs, a residual check every 10
+    cycles; FP64 and double-float."""
     from paper_1806_11456_gb300 import synthetic as syn
-    mesh, o, prm, q0 = syn.config_box_c1()
-    X = syn.node_coordinates(mesh, o)
-    S = syn.to_blocked(man.source_at(X, syn.manufactured_phases(0), prm[2], prm[0], prm[3], prm[1], prm[4]), o, 3)
-    _, J = orc.geometry(mesh, o)
-    _, off = syn.layout_offsets(o, 3)
-    w1 = np.polynomial.legendre.leggauss(4)[1]
-    W = np.einsum("k,j,i->kji", w1, w1, w1).reshape(-1)
-    WJ = np.concatenate([W * J[off[e]:off[e + 1]] for e in range(mesh["K"])])
-    S = syn.compatible_source(mesh, o, S, WJ)
-    out = {"workload": "periodic box 4x4x1, N=3, manufactured state, compatible source", "tol": tol,
-           "cycle": "V 3->1, 3/3/10 sweeps, graph replay, norm every 10 cycles"}
+    mesh, o, prm, q_star = syn.config_box_c1()
+    S, q0 = steady_problem(dg, torch, dev, mesh, o, prm, q_star, seed=11)
+    out = {"workload": "periodic box 4x4x1, N=3, S = A(q*) with q* the manufactured field, start q*(1+1% noise)",
+           "tol": tol, "cycle": "V 3->1, 3/3/10 sweeps, graph replay, norm every 10 cycles"}
     for arith in ("fp64", "df32"):
         M = dg.Mesh(mesh, o, prm).set_arithmetic(arith)
         qd = torch.tensor(q0, device=dev)
@@ -212,7 +217,8 @@ def time_to_tolerance(dg, torch, dev, tol=1e-10, max_cycles=3000):
             if k % 10 == 0:
                 rn = M.residual(qd, sd, norm=True)[1]
         torch.cuda.synchronize()
-        out[arith] = {"seconds": time.perf_counter() - t0, "cycles": k, "final_rnorm": rn, "converged": rn < tol}
+        out[arith] = {"seconds": time.perf_counter() - t0, "cycles": k, "final_rnorm": rn, "converged": rn < tol,
+                      "max_dev_from_q_star": float(np.max(np.abs(qd.cpu().numpy() - q_star)))}
     return out
 
 
@@ -310,6 +316,107 @@ def batched_solves(dg, torch, dev, steps=5):
             "finite": bool(np.all(np.isfinite(norms))), "setup_s": t_setup, "generate_s": t_gen}
 
 
+def serving_requests(dg, torch, dev, n, seed=4):
+    """Steady-solve requests of the serving workload: periodic 2D boxes (2-8
+    elements per side, orders U[1,4]^2) and 3D boxes (2-3 per side, orders
+    U[2,3]^3), Mach U_log[0.1, 0.4], Re U_log[1e2, 1e4]; each with a known
+    discrete solution q* (the manufactured field with seeded phases), S =
+    A(q*), start q*(1 + 1% seeded noise)."""
+    from paper_1806_11456_gb300 import synthetic as syn
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        mach = float(np.exp(rng.uniform(np.log(0.1), np.log(0.4))))
+        re = float(np.exp(rng.uniform(np.log(1e2), np.log(1e4))))
+        prm = syn.flow_params(mach=mach, re=re)
+        if k % 4 == 3:
+            m = int(rng.integers(2, 4))
+            mesh = syn.periodic_box(m, m, m)
+            o = syn.random_orders(mesh["K"], 3, 2, 3, seed * 1000 + k)
+        else:
+            mesh = syn.periodic_box(int(rng.integers(2, 9)), int(rng.integers(2, 9)), 1, dim=2)
+            o = syn.random_orders(mesh["K"], 2, 1, 4, seed * 1000 + k)
+        q_star = syn.manufactured_state(mesh, o, seed * 1000 + k, mach, prm[0], amp=0.05)
+        S, q0 = steady_problem(dg, torch, dev, mesh, o, prm, q_star, seed=k)
+        out.append((mesh, o, prm, q0, S))
+    return out
+
+
+def serving(dg, torch, dev, rate=6.0, window=8.0, slots=8, budget=150 << 30, seed=4):
+    """Serving loop: requests arrive as a seeded Poisson process (rate per
+    second over `window` seconds) and are submitted at their arrival times;
+    each is solved to max|r| < 1e-10 (V 3/3/10, graph replay, at most 3000
+    cycles).  The same arrival stream is served by `slots` concurrent slots
+    and by one slot (plain FP64 one at a time)."""
+    import threading as th
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * window * 3)))
+    arrivals = arrivals[arrivals < window]
+    reqs = serving_requests(dg, torch, dev, len(arrivals), seed)
+    kw = dict(tol=1e-10, max_cycles=3000, mg=dict(beta1=3, beta2=3, beta_c=10, graph=1))
+
+    def run(n_slots):
+        ids = [None] * len(reqs)
+        with dg.Server(hbm_budget=budget, slots=n_slots) as S:
+            t0 = time.perf_counter()
+
+            def feed():
+                for i, (t, (m, o, p, q0, src)) in enumerate(zip(arrivals, reqs)):
+                    dt = t - (time.perf_counter() - t0)
+                    if dt > 0:
+                        time.sleep(dt)
+                    ids[i] = S.submit(m, o, p, q0=q0, s=src, **kw)
+
+            feeder = th.Thread(target=feed)
+            feeder.start()
+            feeder.join()
+            S.wait()
+            makespan = time.perf_counter() - t0
+            infos = [S.info(i) for i in ids]
+        lat = np.array([x["t_end"] - x["t_submit"] for x in infos])
+        dofs = sum(x["rep"]["dof_evals"] for x in infos)
+        ok = sum(1 for x in infos if x["state"] == 0)
+        return {"slots": n_slots, "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                "mean_s": float(lat.mean()), "makespan_s": makespan, "dof_per_s": dofs / makespan,
+                "converged": ok, "cycles_mean": float(np.mean([x["rep"]["cycles"] for x in infos]))}
+
+    conc = run(slots)
+    seq = run(1)
+    nodes = [int(np.sum(np.prod(o[:, :m["dim"]] + 1, axis=1))) for (m, o, *_r) in reqs]
+    return {"workload": f"{len(reqs)} requests, Poisson {rate}/s over {window} s: periodic 2D boxes 2-8 per side "
+                        "orders U[1,4]^2 and 3D boxes 2-3 per side orders U[2,3]^3, Mach U_log[0.1,0.4], "
+                        "Re U_log[1e2,1e4], S = A(q*), to max|r| < 1e-10",
+            "requests": len(reqs), "dof_range": [5 * min(nodes), 5 * max(nodes)],
+            "offered_dof_per_s": 5.0 * sum(nodes) / window,
+            "concurrent": conc, "one_at_a_time": seq, "p99_speedup": seq["p99_s"] / conc["p99_s"]}
+
+
+def precision_report(dg, torch, dev):
+    """Error of each double-float output against the FP64 path on the
+    sphere workload (13,824 quadratic hexes, orders U[1,6]^3, Mach 0.2,
+    Re 200; the FP64 path matches the oracle to 1e-12 in the parity tests):
+    the residual, one V-cycle 6 -> 1 (1/1/2 sweeps) and the tau table."""
+    from paper_1806_11456_gb300 import synthetic as syn
+    mesh, o, prm = syn.config_sphere_c3()
+    q = syn.smooth_state(mesh, o, prm, 5, amp=0.02)
+    out = {"workload": "cubed-sphere shell 6x12x12x16 = 13,824 quadratic hexes, orders U[1,6]^3, Mach 0.2, Re 200"}
+    M = {a: dg.Mesh(mesh, o, prm).set_arithmetic(a) for a in ("fp64", "df32")}
+    r = {a: M[a].residual(torch.tensor(q, device=dev)).cpu().numpy() for a in M}
+    out["residual_max_abs_err"] = float(np.max(np.abs(r["df32"] - r["fp64"])))
+    out["residual_rel_err"] = out["residual_max_abs_err"] / float(np.max(np.abs(r["fp64"])))
+    qs = {}
+    for a in M:
+        qd = torch.tensor(q, device=dev)
+        M[a].vcycle(qd, None, beta1=1, beta2=1, beta_c=2)
+        qs[a] = qd.cpu().numpy()
+    out["vcycle_state_rel_err"] = float(np.max(np.abs(qs["df32"] - qs["fp64"])) / np.max(np.abs(qs["fp64"])))
+    t = {a: M[a].tau_estimate(torch.tensor(q, device=dev), None, dir_mask=7) for a in M}
+    meas = t["fp64"] >= 0
+    out["tau_rel_err"] = float(np.max(np.abs(t["df32"] - t["fp64"])[meas]) / np.max(t["fp64"][meas]))
+    out["tau_measured_same"] = bool(np.array_equal(t["df32"] >= 0, meas))
+    return out
+
+
 def roofline_sweep(dg, torch, dev):
     """Residual stages on 3D periodic affine boxes far larger than L2:
     N = 3, 5, 7 with 64^3, 43^3 and 32^3 elements (16.8-17.2 M Gauss nodes,
@@ -344,6 +451,39 @@ def roofline_sweep(dg, torch, dev):
         del M, q
         torch.cuda.empty_cache()
     return out
+
+
+def captured_traffic(kernel="k_volume"):
+    """DRAM bytes (read + write) per launch of `kernel` on the headline
+    workload, from the committed ncu summary, when that capture was taken
+    with the current kernel source (its sha256 is recorded beside the
+    figure); None otherwise."""
+    import hashlib
+    import re
+    src = os.path.join(ROOT, "paper_1806_11456_gb300", "csrc", "dg_kernels.cu")
+    prof = os.path.join(ROOT, "profiles", "k_volume_flat_plate_N7.md")
+    try:
+        with open(src, "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()[:16]
+        with open(prof) as f:
+            text = f.read()
+    except OSError:
+        return None
+    m = re.search(r"traffic: %s dram_bytes_per_launch=(\d+) kernel_source_sha256=([0-9a-f]+)" % kernel, text)
+    return int(m.group(1)) if m and m.group(2) == digest else None
+
+
+def aggregate_ranks(ms, dofs, world, device):
+    """Whole-job figures of replicas: the slowest rank's time (max over
+    ranks) and the units all ranks processed over that time.  Every rank
+    processes the same work, so the job total is world x the rank's."""
+    if world > 1:
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    return ms, world * dofs / (ms * 1e-3)
 
 
 def cpu_baseline_sample(mesh, prm, orders, q, budget_s=15.0):
@@ -408,12 +548,7 @@ def run_gb300(args, rank, world):
     launches = dg.kernel_launches() - launches0
     torch.cuda.synchronize()
     clk = clocks.stop(dev.index)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-        torch.distributed.barrier()
-    value = world * total_dofs / (total_ms * 1e-3)
+    total_ms, value = aggregate_ranks(total_ms, total_dofs, world, dev)
 
     # e2e through the C ABI with pinned host buffers
     qh = torch.tensor(q_np).pin_memory()
@@ -446,7 +581,8 @@ def run_gb300(args, rank, world):
     achieved = flops / (vol_ms * 1e-3) / 1e12
     residual_ms = sum(stages.values())
     roof = {"kernel": "k_volume", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": captured_traffic(),
+            "traffic_unit": "DRAM bytes per launch (ncu capture of the current kernel source, else null)",
             "peak_source": "FP64 nominal derived: 2 DFMA/clk/SM x 152 SMs x 2070 MHz",
             "flops_per_launch": flops, "ms_per_launch": vol_ms, "dominant_stage": dom,
             "stage_ms": prof, "residual_dof_per_s": 5.0 * nodes / (residual_ms * 1e-3)}
@@ -489,6 +625,8 @@ def run_gb300(args, rank, world):
         out["time_to_tol"] = time_to_tolerance(dg, torch, dev)
         out["batched"] = batched_solves(dg, torch, dev)
         out["roofline_sweep"] = roofline_sweep(dg, torch, dev)
+        out["serving"] = serving(dg, torch, dev)
+        out["precision"] = precision_report(dg, torch, dev)
         out["cpu_baseline"] = cpu_baseline_sample(mesh, prm, orders, q_np) if world == 1 else None
         print(json.dumps(out))
 

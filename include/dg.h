@@ -42,6 +42,8 @@ extern "C" {
 #define DG_ECUDA (-3)
 #define DG_EDIVERGED (-4)
 #define DG_ENOTCONVERGED (-5)
+#define DG_EBUDGET (-6)  /* a request does not fit the serving memory budget */
+#define DG_ETIMEOUT (-7) /* dg_server_wait ran out of time */
 
 /* dg_residual flags */
 #define DG_ISOLATED 1 /* the isolated operator F-hat (own flux on the element boundary) */
@@ -354,6 +356,76 @@ int dg_transfer_noalloc(int32_t dim, int32_t K, const int32_t* orders_from, cons
  */
 int dg_profile_residual(dg_mesh* mesh, const double* q, const double* s, double* r, int iters,
                         double* ms_out, void* stream);
+
+/*
+ * ---------------------------------------------------------------------------
+ * Serving loop: steady solves admitted as they arrive (continuous admission)
+ * ---------------------------------------------------------------------------
+ * A server runs up to `slots` solves at once, each in its own host worker
+ * thread with its own CUDA stream, mesh hierarchy and state, so the kernels
+ * of concurrent solves overlap on the device.  A submitted request waits in a
+ * FIFO queue until a slot is free and its device-memory estimate
+ * (dg_solve_footprint) fits in what the running solves leave of the budget;
+ * it then runs dg_solve_steady with its own parameters and keeps its
+ * hierarchy resident until it finishes.  Requests share no device data, so a
+ * solve gives bit for bit the same result alone and among others.
+ */
+typedef struct dg_server dg_server;
+
+typedef struct {
+  int64_t hbm_budget; /* bytes of device memory the running solves may hold together (by estimate) */
+  int32_t slots;      /* solves that run at the same time (>= 1) */
+  int32_t device;     /* CUDA device of every solve */
+} dg_server_params;
+
+#define DG_REQ_QUEUED 1  /* dg_request_info.state: waiting for a slot or for memory */
+#define DG_REQ_RUNNING 2 /* in a slot; finished requests hold their solve's status (<= 0) */
+
+typedef struct {
+  int32_t state;          /* DG_REQ_QUEUED, DG_REQ_RUNNING, or DG_OK / DG_E* when finished */
+  int32_t K;              /* elements */
+  dg_solve_report rep;    /* of the finished solve (rep.nodes sizes the result) */
+  int64_t est_bytes;      /* admission estimate */
+  int64_t dev_bytes;      /* device bytes the solve's mesh hierarchy and arrays held at its end */
+  double t_submit;        /* seconds since dg_server_create */
+  double t_start;
+  double t_end;
+} dg_request_info;
+
+/* Estimate of the device bytes a steady solve of this mesh and order map
+ * holds: every multigrid level 1..max order (geometry, face and mortar
+ * buffers, work arrays) plus its state and source. */
+int dg_solve_footprint(const dg_mesh_desc* desc, const int32_t* orders, int64_t* bytes);
+
+int dg_server_create(const dg_server_params* p, dg_server** out);
+
+/*
+ * dg_server_submit -- queue a steady solve.  Host inputs, all copied:
+ *  desc, orders  the mesh (as dg_mesh_create).
+ *  q0            initial state in the mesh's layout (5 x nodes), or NULL for
+ *                the freestream of desc->params.
+ *  s             source in the same layout, or NULL.
+ *  sp            steady-driver parameters (as dg_solve_steady).
+ * DG_EBUDGET when the estimate alone exceeds the budget.
+ */
+int dg_server_submit(dg_server* srv, const dg_mesh_desc* desc, const int32_t* orders, const double* q0,
+                     const double* s, const dg_solve_params* sp, int64_t* id);
+
+/* Wait until request `id` (or every request, id = -1) has finished; DG_ETIMEOUT
+ * after timeout_s seconds (< 0: no limit). */
+int dg_server_wait(dg_server* srv, int64_t id, double timeout_s);
+
+int dg_server_info(dg_server* srv, int64_t id, dg_request_info* info);
+
+/* Final state (5 x rep.nodes doubles, the final mesh's layout) and order map
+ * (K x 3) of a finished request into host arrays (either may be NULL). */
+int dg_server_result(dg_server* srv, int64_t id, double* q, int32_t* orders);
+
+/* Drop a finished request's host copies. */
+int dg_server_release(dg_server* srv, int64_t id);
+
+/* Cancel queued requests, wait for the running ones, stop the workers. */
+int dg_server_destroy(dg_server* srv);
 
 /* dg_kernel_launches -- cumulative number of CUDA kernels this library has
  * launched in the process (host-side count; a measurement aid). */

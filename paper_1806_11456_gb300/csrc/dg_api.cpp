@@ -263,10 +263,12 @@ static int run_vcycle(dg_mesh* m, const std::vector<int32_t>& top_orders, double
     if (!m->cap_stream) DG_CUDA_TRY(cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking));
     Cycle G{m, m->cap_stream, mg, C.lv, 0, 0.0};
     unsigned long long l0 = launches();
+    std::unique_lock<std::mutex> lock(device_sync_mutex());  // no cudaFree elsewhere while capturing
     DG_CUDA_TRY(cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal));
     int rc = vcycle_level(G, 0, Q, Sv);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(m->cap_stream, &graph);
+    lock.unlock();
     if (rc != DG_OK) {
       if (graph) cudaGraphDestroy(graph);
       return rc;
@@ -466,7 +468,7 @@ int dg_kernel_launches(int64_t* count) {
     set_error("dg_kernel_launches: null argument");
     return DG_EINVAL;
   }
-  *count = (int64_t)launches();
+  *count = (int64_t)launches_total();
   return DG_OK;
 }
 
@@ -599,15 +601,18 @@ int dg_residual_norms(dg_mesh* m, const double* q, const double* s, double* norm
 
 int dg_mesh_destroy(dg_mesh* m) {
   if (!m) return DG_OK;
-  for (auto& kv : m->graphs) cudaGraphExecDestroy(kv.second.exec);
-  if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
-  if (m->d_scalars) cudaFree(m->d_scalars);
-  if (m->d_tau) cudaFree(m->d_tau);
-  if (m->d_orders) cudaFree(m->d_orders);
-  if (m->d_gas64) cudaFree(m->d_gas64);
-  if (m->d_gas32x2) cudaFree(m->d_gas32x2);
-  if (m->d_gasd) cudaFree(m->d_gasd);
-  delete m;
+  {
+    std::lock_guard<std::mutex> lock(device_sync_mutex());
+    for (auto& kv : m->graphs) cudaGraphExecDestroy(kv.second.exec);
+    if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
+    if (m->d_scalars) cudaFree(m->d_scalars);
+    if (m->d_tau) cudaFree(m->d_tau);
+    if (m->d_orders) cudaFree(m->d_orders);
+    if (m->d_gas64) cudaFree(m->d_gas64);
+    if (m->d_gas32x2) cudaFree(m->d_gas32x2);
+    if (m->d_gasd) cudaFree(m->d_gasd);
+  }
+  delete m;  // the levels lock again while they free
   return DG_OK;
 }
 

@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <map>
+#include <mutex>
 #include <memory>
 #include <string>
 #include <vector>
@@ -103,6 +104,7 @@ struct Level {
   std::vector<int32_t> orders;          // K x 3
   std::vector<int64_t> off;             // K+1 node offsets
   int64_t nodes = 0;
+  int64_t bytes = 0;                    // device memory this level holds
   // device
   int32_t* d_n = nullptr;               // K x 3 node counts
   int32_t* d_off = nullptr;             // K+1 (int32 suffices: < 2^31 nodes)
@@ -182,7 +184,14 @@ Params make_params(const double* p);
 // kernels (dg_kernels.cu)
 int upload_tables();
 int upload_gas(dg_mesh* m);
-unsigned long long launches();
+// Held while a V-cycle is captured into a graph and around cudaFree calls:
+// a cudaFree in one thread synchronises the device and would break a capture
+// running in another (serving runs solves in several threads).
+std::mutex& device_sync_mutex();
+// device bytes held by a mesh's levels and scalars
+int64_t mesh_device_bytes(const dg_mesh* m);
+unsigned long long launches();        // launched by the calling thread
+unsigned long long launches_total();  // launched by all threads
 void add_launches(unsigned long long n);
 int prepare_capture();  // one-time per-device set-up that may not run inside a capture
 int prepare_arith(const dg_mesh* m, Level* L, cudaStream_t st);  // per-level data the arithmetic mode needs

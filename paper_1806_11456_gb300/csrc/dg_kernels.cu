@@ -25,6 +25,8 @@
 // directly from the contravariant velocity).
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <algorithm>
 #include <cstdio>
 #include <climits>
@@ -64,14 +66,28 @@ static float2 split2(double x) {
 }
 
 static double* g_dev_Dhat = nullptr;
-static unsigned long long g_launches = 0;  // kernels launched by this library (host-side count)
-unsigned long long launches() { return g_launches; }
-void add_launches(unsigned long long n) { g_launches += n; }
+// Kernels launched by this library: a process total and a per-thread count
+// (a graph capture measures its own launches with the latter).
+static std::atomic<unsigned long long> g_launches_total{0};
+static thread_local unsigned long long t_launches = 0;
+static inline void count_launch() {
+  g_launches_total.fetch_add(1, std::memory_order_relaxed);
+  ++t_launches;
+}
+unsigned long long launches() { return t_launches; }
+unsigned long long launches_total() { return g_launches_total.load(std::memory_order_relaxed); }
+void add_launches(unsigned long long n) {
+  g_launches_total.fetch_add(n, std::memory_order_relaxed);
+  t_launches += n;
+}
 static double* g_dev_D = nullptr;
 static double* g_dev_T = nullptr;
 static int g_tables_device = -1;
 
+static std::mutex g_setup_mutex;  // one-time per-device setup (tables, kernel attributes)
+
 int upload_tables() {
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
   int dev = 0;
   DG_CUDA_TRY(cudaGetDevice(&dev));
   if (g_tables_device == dev) return DG_OK;
@@ -1258,6 +1274,7 @@ static int set_attrs() {
 }
 
 static int configure_smem() {
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
   static int done_dev = -1;
   int dev = 0;
   DG_CUDA_TRY(cudaGetDevice(&dev));
@@ -1321,33 +1338,33 @@ static int grid_for(int64_t n) {
 int slot_maxabs(const dg_mesh* m, const Level* L, const double* x, double* out, cudaStream_t st) {
   const int rc = fill(out, 0.0, m->nslots, st);
   if (rc != DG_OK) return rc;
-  ++g_launches;
+  count_launch();
   k_slot_maxabs<<<L->n_tiles, kTileNodes, 0, st>>>(largs<double>(L), x, out);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
 }
 
 int mask_dt(const dg_mesh* m, double* dt, const double* mask, cudaStream_t st) {
-  ++g_launches;
+  count_launch();
   k_mask_dt<<<(m->nslots + 127) / 128, 128, 0, st>>>(dt, mask, m->nslots);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
 }
 
 int fill(double* p, double v, int64_t n, cudaStream_t st) {
-  ++g_launches;
+  count_launch();
   k_fill<<<grid_for(n), 256, 0, st>>>(p, v, n);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
 }
 int axpby(double* y, double a, const double* x, double b, int64_t n, cudaStream_t st) {
-  ++g_launches;
+  count_launch();
   k_axpby<<<grid_for(n), 256, 0, st>>>(y, a, x, b, n);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
 }
 int sub3(double* o, const double* a, const double* b, int64_t n, cudaStream_t st) {
-  ++g_launches;
+  count_launch();
   k_sub3<<<grid_for(n), 256, 0, st>>>(o, a, b, n);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
@@ -1370,7 +1387,7 @@ __global__ void k_split(const double* __restrict__ x, float2* __restrict__ y, in
 }
 static int split_array(const double* x, double** y, int64_t n, cudaStream_t st) {
   DG_CUDA_TRY(cudaMalloc((void**)y, std::max<int64_t>(1, n) * sizeof(float2)));
-  ++g_launches;
+  count_launch();
   k_split<<<grid_for(n), 256, 0, st>>>(x, reinterpret_cast<float2*>(*y), n);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
@@ -1380,7 +1397,9 @@ static int ensure_dd(Level* L, cudaStream_t st) {
   int rc;
   if ((rc = split_array(L->d_geo, &L->d_geo2, 10 * L->nodes, st)) != DG_OK) return rc;
   if ((rc = split_array(L->d_fnS, &L->d_fnS2, 3 * L->face_nodes, st)) != DG_OK) return rc;
-  return split_array(L->d_mnS, &L->d_mnS2, 3 * L->mortar_nodes, st);
+  if ((rc = split_array(L->d_mnS, &L->d_mnS2, 3 * L->mortar_nodes, st)) != DG_OK) return rc;
+  L->bytes += (int64_t)sizeof(float2) * (10 * L->nodes + 3 * L->face_nodes + 3 * L->mortar_nodes);
+  return DG_OK;
 }
 
 template <typename R>
@@ -1429,7 +1448,7 @@ static ST<R>* buf(double* p) {
 
 template <typename R>
 static void launch_trace(const Level* L, const double* q, cudaStream_t st) {
-  ++g_launches;
+  count_launch();
   const size_t sm = 5 * L->tile_smem_nodes * sizeof(double);
   LevelArgsT<R> A = largs<R>(L);
   if (L->dim == 2)
@@ -1447,7 +1466,7 @@ static void for_tile_classes(const Level* L, F launch) {
   for (int c = 0; c < kTileClasses; ++c) {
     const int end = L->tile_class_end[c];
     if (end > begin) {
-      ++g_launches;
+      count_launch();
       launch(begin, end - begin, threads[c], (size_t)(3 * kNP * kNP + 32 * L->tile_class_nodes[c]) * sizeof(double));
     }
     begin = end;
@@ -1495,7 +1514,7 @@ static void launch_isolated(const Level* L, const GasT<R>* G, const double* q, c
 template <typename R>
 static void launch_surface(const Level* L, const double* s, double* r, double* norm, const RKArgs& rk,
                            cudaStream_t st) {
-  ++g_launches;
+  count_launch();
   LevelArgsT<R> A = largs<R>(L);
   if (L->dim == 2)
     k_surface<R, 2><<<L->n_tiles, kTileNodes, 0, st>>>(A, buf<R>(L->d_vol), buf<R>(L->d_fst), s, r, norm, rk);
@@ -1504,7 +1523,7 @@ static void launch_surface(const Level* L, const double* s, double* r, double* n
 }
 template <typename R>
 static void launch_mortar(int pass, const Level* L, const GasT<R>* G, cudaStream_t st) {
-  ++g_launches;
+  count_launch();
   LevelArgsT<R> A = largs<R>(L);
   MortarArgsT<R> MA = margs<R>(L);
   if (pass == 1)
@@ -1603,7 +1622,7 @@ int profile_residual(const dg_mesh* m, Level* L, const double* q, const double* 
 int cfl_dt(const dg_mesh* m, Level* L, const double* q, double* d_dt, cudaStream_t st) {
   int rc = fill(d_dt, 1e300, m->nslots, st);
   if (rc != DG_OK) return rc;
-  ++g_launches;
+  count_launch();
   if (L->dim == 2)
     k_cfl<2><<<L->n_tiles, kTileNodes, 0, st>>>(largs<double>(L), m->d_gasd, q, d_dt);
   else
@@ -1630,7 +1649,7 @@ int transfer(const dg_mesh* m, const Level* from, const Level* to, int nvar, con
     set_error("transfer: element too large for the shared-memory slab");
     return DG_EINVAL;
   }
-  ++g_launches;
+  count_launch();
   k_transfer<<<from->K, kTransferThreads, 2 * slab * sizeof(double), st>>>(from->d_n, from->d_off, to->d_n,
                                                                           to->d_off, nvar, in, sub, out,
                                                                           accumulate ? 1 : 0);
@@ -1682,7 +1701,7 @@ __global__ void k_tau_reduce(LevelArgsT<double> A, const double* __restrict__ r,
 
 static int tau_reduce(const Level* L, const double* r, const double* rho, int dir, int slot,
                       const int32_t* fine_orders, double* table, cudaStream_t st) {
-  ++g_launches;
+  count_launch();
   k_tau_reduce<<<L->n_tiles, kTileNodes, 0, st>>>(largs<double>(L), r, rho, dir, slot, fine_orders, table);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
@@ -1837,7 +1856,7 @@ int transfer_noalloc(int dim, int K, const int32_t* orders_from, const int32_t* 
   int rc = noalloc_setup(&dev_rec);
   if (rc != DG_OK) return rc;
   DG_CUDA_TRY(cudaMemcpyAsync(dev_rec, rec.data(), rec.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-  ++g_launches;
+  count_launch();
   k_transfer_noalloc<<<K, 128, 0, st>>>(nvar, dev_rec, in, out);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;

@@ -328,9 +328,10 @@ inline void face_dirs(int f, int* d, int* ta, int* tb, int* side) {
 }
 
 template <typename T>
-int dev_upload(T** dst, const std::vector<T>& src) {
+int dev_upload(int64_t* acc, T** dst, const std::vector<T>& src) {
   size_t bytes = std::max<size_t>(1, src.size()) * sizeof(T);
   DG_CUDA_TRY(cudaMalloc((void**)dst, bytes));
+  *acc += (int64_t)bytes;
   if (!src.empty()) DG_CUDA_TRY(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
   return DG_OK;
 }
@@ -353,8 +354,9 @@ void parallel_for(int n, F f) {
   for (auto& x : th) x.join();
 }
 
-int dev_zeros(double** dst, size_t n) {
+int dev_zeros(int64_t* acc, double** dst, size_t n) {
   DG_CUDA_TRY(cudaMalloc((void**)dst, std::max<size_t>(1, n) * sizeof(double)));
+  *acc += (int64_t)(std::max<size_t>(1, n) * sizeof(double));
   DG_CUDA_TRY(cudaMemset(*dst, 0, std::max<size_t>(1, n) * sizeof(double)));
   return DG_OK;
 }
@@ -367,7 +369,19 @@ int dev_zeros(double** dst, size_t n) {
     if (_rc != DG_OK) return _rc; \
   } while (0)
 
+std::mutex& device_sync_mutex() {
+  static std::mutex mu;
+  return mu;
+}
+
+int64_t mesh_device_bytes(const dg_mesh* m) {
+  int64_t b = m->fine ? m->fine->bytes : 0;
+  for (const auto& kv : m->levels) b += kv.second->bytes;
+  return b + (int64_t)(5 * m->nslots + 16) * (int64_t)sizeof(double);
+}
+
 Level::~Level() {
+  std::lock_guard<std::mutex> lock(device_sync_mutex());  // cudaFree synchronises the device
   void* ptrs[] = {d_n,   d_off,   d_geo,       d_fo,    d_fnS,          d_trq,  d_ust,  d_trg,
                   d_fst, d_mortars, d_mnode_mortar, d_mnS, d_mtiles, d_tile_elems, d_tiles, d_vol,
                   d_Q,   d_S,     d_Q0,        d_G,     d_R,            d_geo2, d_fnS2, d_mnS2, d_slot};
@@ -611,34 +625,34 @@ int build_level(const dg_mesh* m, const std::vector<int32_t>& orders, Level* L) 
   L->tile_smem_nodes = max_nodes;
   // ---- upload ----
   std::vector<int32_t> off32(L->off.begin(), L->off.end());
-  DG_TRY(dev_upload(&L->d_n, nvec));
-  DG_TRY(dev_upload(&L->d_off, off32));
-  DG_TRY(dev_upload(&L->d_geo, geo));
-  DG_TRY(dev_upload(&L->d_fo, fo));
-  DG_TRY(dev_upload(&L->d_fnS, fnS));
-  DG_TRY(dev_upload(&L->d_mortars, mortars));
-  DG_TRY(dev_upload(&L->d_mnode_mortar, mnode_mortar));
-  DG_TRY(dev_upload(&L->d_mnS, mnS));
-  DG_TRY(dev_upload(&L->d_mtiles, mtiles));
-  DG_TRY(dev_upload(&L->d_tile_elems, tile_elems));
-  DG_TRY(dev_upload(&L->d_slot, m->elem_slot));
-  DG_TRY(dev_upload(&L->d_tiles, tiles));
-  DG_TRY(dev_zeros(&L->d_trq, (size_t)5 * acc));
-  DG_TRY(dev_zeros(&L->d_ust, (size_t)4 * acc));
-  DG_TRY(dev_zeros(&L->d_trg, (size_t)12 * acc));
-  DG_TRY(dev_zeros(&L->d_fst, (size_t)5 * acc));
-  DG_TRY(dev_zeros(&L->d_vol, (size_t)5 * L->nodes));
+  DG_TRY(dev_upload(&L->bytes, &L->d_n, nvec));
+  DG_TRY(dev_upload(&L->bytes, &L->d_off, off32));
+  DG_TRY(dev_upload(&L->bytes, &L->d_geo, geo));
+  DG_TRY(dev_upload(&L->bytes, &L->d_fo, fo));
+  DG_TRY(dev_upload(&L->bytes, &L->d_fnS, fnS));
+  DG_TRY(dev_upload(&L->bytes, &L->d_mortars, mortars));
+  DG_TRY(dev_upload(&L->bytes, &L->d_mnode_mortar, mnode_mortar));
+  DG_TRY(dev_upload(&L->bytes, &L->d_mnS, mnS));
+  DG_TRY(dev_upload(&L->bytes, &L->d_mtiles, mtiles));
+  DG_TRY(dev_upload(&L->bytes, &L->d_tile_elems, tile_elems));
+  DG_TRY(dev_upload(&L->bytes, &L->d_slot, m->elem_slot));
+  DG_TRY(dev_upload(&L->bytes, &L->d_tiles, tiles));
+  DG_TRY(dev_zeros(&L->bytes, &L->d_trq, (size_t)5 * acc));
+  DG_TRY(dev_zeros(&L->bytes, &L->d_ust, (size_t)4 * acc));
+  DG_TRY(dev_zeros(&L->bytes, &L->d_trg, (size_t)12 * acc));
+  DG_TRY(dev_zeros(&L->bytes, &L->d_fst, (size_t)5 * acc));
+  DG_TRY(dev_zeros(&L->bytes, &L->d_vol, (size_t)5 * L->nodes));
   return DG_OK;
 }
 
 int ensure_work(Level* L) {
   if (L->d_Q) return DG_OK;
   size_t n = (size_t)5 * L->nodes;
-  DG_TRY(dev_zeros(&L->d_Q, n));
-  DG_TRY(dev_zeros(&L->d_S, n));
-  DG_TRY(dev_zeros(&L->d_Q0, n));
-  DG_TRY(dev_zeros(&L->d_G, n));
-  DG_TRY(dev_zeros(&L->d_R, n));
+  DG_TRY(dev_zeros(&L->bytes, &L->d_Q, n));
+  DG_TRY(dev_zeros(&L->bytes, &L->d_S, n));
+  DG_TRY(dev_zeros(&L->bytes, &L->d_Q0, n));
+  DG_TRY(dev_zeros(&L->bytes, &L->d_G, n));
+  DG_TRY(dev_zeros(&L->bytes, &L->d_R, n));
   return DG_OK;
 }
 

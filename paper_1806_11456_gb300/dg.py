@@ -46,6 +46,19 @@ class SolveReport(ctypes.Structure):
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 
 
+class ServerParams(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_int64), ("slots", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("K", ctypes.c_int32), ("rep", SolveReport),
+                ("est_bytes", ctypes.c_int64), ("dev_bytes", ctypes.c_int64), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_end", ctypes.c_double)]
+
+
+REQ_QUEUED, REQ_RUNNING = 1, 2
+
+
 class CycleReport(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int32), ("residual_evals", ctypes.c_int32), ("dof_evals", ctypes.c_double),
                 ("rnorm", ctypes.c_double)]
@@ -72,7 +85,9 @@ _ip = ctypes.POINTER(ctypes.c_int32)
 EXPORTS = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_layout", "dg_residual", "dg_cfl_dt", "dg_smooth",
            "dg_pmg_vcycle", "dg_tau_estimate", "dg_adapt", "dg_transfer_state", "dg_profile_residual",
            "dg_kernel_launches", "dg_transfer_noalloc", "dg_solve_steady", "dg_mesh_orders", "dg_set_arithmetic",
-           "dg_batch_create", "dg_batch_info", "dg_residual_norms", "dg_last_error"]
+           "dg_batch_create", "dg_batch_info", "dg_residual_norms", "dg_solve_footprint", "dg_server_create",
+           "dg_server_submit", "dg_server_wait", "dg_server_info", "dg_server_result", "dg_server_release",
+           "dg_server_destroy", "dg_last_error"]
 ARITH = {"fp64": 0, "df32": 1}
 KERNEL_STAGES = ["trace_q", "mortar_u_star", "volume", "mortar_flux", "surface", "isolated"]
 
@@ -106,6 +121,15 @@ def lib(path=LIB_PATH):
     L.dg_batch_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]
     L.dg_residual_norms.argtypes = [_vp, _vp, _vp, _dp, _vp]
     L.dg_transfer_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, _ip, _ip, ctypes.c_int32, _vp, _vp, _vp]
+    L.dg_solve_footprint.argtypes = [ctypes.POINTER(MeshDesc), _ip, ctypes.POINTER(ctypes.c_int64)]
+    L.dg_server_create.argtypes = [ctypes.POINTER(ServerParams), ctypes.POINTER(_vp)]
+    L.dg_server_submit.argtypes = [_vp, ctypes.POINTER(MeshDesc), _ip, _dp, _dp, ctypes.POINTER(SolveParams),
+                                   ctypes.POINTER(ctypes.c_int64)]
+    L.dg_server_wait.argtypes = [_vp, ctypes.c_int64, ctypes.c_double]
+    L.dg_server_info.argtypes = [_vp, ctypes.c_int64, ctypes.POINTER(RequestInfo)]
+    L.dg_server_result.argtypes = [_vp, ctypes.c_int64, _dp, _ip]
+    L.dg_server_release.argtypes = [_vp, ctypes.c_int64]
+    L.dg_server_destroy.argtypes = [_vp]
     _lib = L
     return L
 
@@ -135,6 +159,27 @@ def kernel_launches():
     c = ctypes.c_int64()
     _check(lib().dg_kernel_launches(ctypes.byref(c)))
     return int(c.value)
+
+
+def solve_params(tol=1e-10, max_cycles=200, fmg=False, fmg_tol=1e-1, mg=None, adapt=False, tau_max=1e-4, n_min=1,
+                 n_max=7, jump_rule=1, conform_tag=-1, cap=0, stages=(), ref_factor=0.1):
+    """dg_solve_params from keyword arguments (mg: dict of dg_mg_params fields)."""
+    sp = SolveParams()
+    sp.tol, sp.max_cycles, sp.fmg, sp.fmg_tol, sp.adapt = float(tol), int(max_cycles), int(bool(fmg)), \
+        float(fmg_tol), int(bool(adapt))
+    m = dict(beta1=3, beta2=3, beta_c=6, direction=-1, coarsest=1, delta_n=1, graph=1, control=0, eta=1.1)
+    m.update(mg or {})
+    for k, v in m.items():
+        setattr(sp.mg, k, float(v) if k == "eta" else int(v))
+    sp.ap.tau_max, sp.ap.n_min, sp.ap.n_max, sp.ap.cap, sp.ap.jump_rule, sp.ap.conform_tag = \
+        float(tau_max), n_min, n_max, cap, jump_rule, conform_tag
+    if len(stages) > 4:
+        raise DGError("at most 4 adaptation stages")
+    sp.n_stages = len(stages)
+    sp.ref_factor = float(ref_factor)
+    for i, v in enumerate(stages):
+        sp.stage_orders[i] = int(v)
+    return sp
 
 
 def _desc(mesh, params, keep):
@@ -309,21 +354,8 @@ class Mesh:
         adaptation q is a new tensor on the adapted mesh, which this object
         then wraps (its orders are updated)."""
         import torch
-        sp = SolveParams()
-        sp.tol, sp.max_cycles, sp.fmg, sp.fmg_tol, sp.adapt = float(tol), int(max_cycles), int(bool(fmg)), \
-            float(fmg_tol), int(bool(adapt))
-        m = dict(beta1=3, beta2=3, beta_c=6, direction=-1, coarsest=1, delta_n=1, graph=1, control=0, eta=1.1)
-        m.update(mg or {})
-        for k, v in m.items():
-            setattr(sp.mg, k, float(v) if k == "eta" else int(v))
-        sp.ap.tau_max, sp.ap.n_min, sp.ap.n_max, sp.ap.cap, sp.ap.jump_rule, sp.ap.conform_tag = \
-            float(tau_max), n_min, n_max, cap, jump_rule, conform_tag
-        if len(stages) > 4:
-            raise DGError("at most 4 adaptation stages")
-        sp.n_stages = len(stages)
-        sp.ref_factor = float(ref_factor)
-        for i, v in enumerate(stages):
-            sp.stage_orders[i] = int(v)
+        sp = solve_params(tol, max_cycles, fmg, fmg_tol, mg, adapt, tau_max, n_min, n_max, jump_rule, conform_tag,
+                          cap, stages, ref_factor)
         keep = []
 
         def _alloc(nbytes, _ctx):
@@ -357,3 +389,77 @@ class Mesh:
             q_to = torch.empty(5 * other.nodes, dtype=torch.float64, device=q_from.device)
         _check(lib().dg_transfer_state(self.h, _ptr(q_from), other.h, _ptr(q_to), _stream(stream)))
         return q_to
+
+
+def solve_footprint(mesh, orders, params):
+    """Device bytes a steady solve of this mesh and order map is estimated to
+    hold (dg_solve_footprint; the serving admission estimate)."""
+    keep = []
+    d = _desc(mesh, params, keep)
+    o = np.ascontiguousarray(orders, dtype=np.int32)
+    b = ctypes.c_int64()
+    _check(lib().dg_solve_footprint(ctypes.byref(d), o.ctypes.data_as(_ip), ctypes.byref(b)))
+    return int(b.value)
+
+
+class Server:
+    """Serving loop (dg_server_*): steady solves submitted as host arrays run
+    in `slots` concurrent workers, admitted while their memory estimates fit
+    in `hbm_budget` bytes."""
+
+    def __init__(self, hbm_budget, slots=4, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise DGError("no CUDA device: the DGSEM library has no CPU path")
+        p = ServerParams()
+        p.hbm_budget, p.slots = int(hbm_budget), int(slots)
+        p.device = torch.cuda.current_device() if device is None else int(device)
+        self.h = _vp()
+        _check(lib().dg_server_create(ctypes.byref(p), ctypes.byref(self.h)))
+
+    def submit(self, mesh, orders, params, q0=None, s=None, **solve_kw):
+        keep = []
+        d = _desc(mesh, params, keep)
+        o = np.ascontiguousarray(orders, dtype=np.int32)
+        qa = None if q0 is None else np.ascontiguousarray(q0, dtype=np.float64)
+        sa = None if s is None else np.ascontiguousarray(s, dtype=np.float64)
+        sp = solve_params(**solve_kw)
+        rid = ctypes.c_int64()
+        _check(lib().dg_server_submit(self.h, ctypes.byref(d), o.ctypes.data_as(_ip),
+                                      None if qa is None else qa.ctypes.data_as(_dp),
+                                      None if sa is None else sa.ctypes.data_as(_dp), ctypes.byref(sp),
+                                      ctypes.byref(rid)))
+        return int(rid.value)
+
+    def wait(self, rid=-1, timeout=-1.0):
+        _check(lib().dg_server_wait(self.h, int(rid), float(timeout)))
+
+    def info(self, rid):
+        i = RequestInfo()
+        _check(lib().dg_server_info(self.h, int(rid), ctypes.byref(i)))
+        r = i.rep
+        return dict(state=i.state, K=i.K, est_bytes=i.est_bytes, dev_bytes=i.dev_bytes, t_submit=i.t_submit,
+                    t_start=i.t_start, t_end=i.t_end,
+                    rep=dict(cycles=r.cycles, fmg_cycles=r.fmg_cycles, adapted=r.adapted, status=r.status,
+                             rnorm=r.rnorm, rnorm_adapt=r.rnorm_adapt, dof_evals=r.dof_evals, nodes=r.nodes))
+
+    def result(self, rid):
+        i = self.info(rid)
+        q = np.zeros(5 * i["rep"]["nodes"])
+        o = np.zeros((i["K"], 3), dtype=np.int32)
+        _check(lib().dg_server_result(self.h, int(rid), q.ctypes.data_as(_dp), o.ctypes.data_as(_ip)))
+        return q, o
+
+    def release(self, rid):
+        _check(lib().dg_server_release(self.h, int(rid)))
+
+    def close(self):
+        if self.h:
+            lib().dg_server_destroy(self.h)
+            self.h = _vp()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

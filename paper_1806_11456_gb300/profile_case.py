@@ -1,0 +1,71 @@
+"""A small, fixed invocation of the residual for profilers (ncu): builds the
+library, creates one workload and evaluates its residual `--warmup` + `--iters`
+times on the current CUDA device, then exits.  Nothing is timed here.
+
+    python -m paper_1806_11456_gb300.profile_case flat_plate --warmup 2 --iters 3
+    python -m paper_1806_11456_gb300.profile_case box3d --arith df32
+
+Workloads: flat_plate (60 x 24 stretched plate, N = 7, 92,160 nodes, the
+bench's headline mesh); box3d (periodic 48^3 affine hexes, N = 3, 7.1 M nodes,
+283 MB of state: larger than L2); sphere (13,824 quadratic hexes, orders
+U[1,6]^3).
+"""
+import argparse
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def workload(name):
+    from paper_1806_11456_gb300 import synthetic as syn
+    if name == "flat_plate":
+        mesh = syn.flat_plate_mesh()
+        prm = syn.flow_params(mach=0.2, re=1e5)
+        o = syn.uniform_orders(mesh["K"], 2, 7)
+        return mesh, o, prm, syn.perturbed_state(mesh, o, prm, seed=7, amp=0.01)
+    if name == "box3d":
+        mesh = syn.periodic_box(48, 48, 48)
+        prm = syn.flow_params(mach=0.3, re=100.0)
+        o = syn.uniform_orders(mesh["K"], 3, 3)
+        return mesh, o, prm, None
+    if name == "sphere":
+        mesh, o, prm = syn.config_sphere_c3()
+        return mesh, o, prm, syn.smooth_state(mesh, o, prm, 5, amp=0.02)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("workload", choices=["flat_plate", "box3d", "sphere"])
+    ap.add_argument("--warmup", type=int, default=2)
+    ap.add_argument("--iters", type=int, default=3)
+    ap.add_argument("--arith", default="fp64", choices=["fp64", "df32"])
+    args = ap.parse_args()
+    sys.path.insert(0, ROOT)
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_1806_11456_gb300 import dg
+    mesh, o, prm, q = workload(args.workload)
+    M = dg.Mesh(mesh, o, prm).set_arithmetic(args.arith)
+    if q is None:  # large box: freestream times (1 + 1% seeded noise), made on the device
+        n, _ = M.layout()
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(3)
+        qinf = torch.tensor(np.asarray(prm[7:12]), device="cuda", dtype=torch.float64)
+        nn = int(np.prod(o[0, :mesh["dim"]] + 1))
+        qd = (qinf.view(1, 5, 1) * (1 + 0.01 * (2 * torch.rand(mesh["K"], 5, nn, device="cuda", dtype=torch.float64,
+                                                                 generator=gen) - 1))).reshape(-1)
+    else:
+        qd = torch.tensor(q, device="cuda")
+    r = torch.empty_like(qd)
+    for _ in range(args.warmup + args.iters):
+        M.residual(qd, None, r=r)
+    torch.cuda.synchronize()
+
+
+if __name__ == "__main__":
+    main()
