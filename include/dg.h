@@ -427,6 +427,22 @@ int dg_server_release(dg_server* srv, int64_t id);
 /* Cancel queued requests, wait for the running ones, stop the workers. */
 int dg_server_destroy(dg_server* srv);
 
+/*
+ * dg_set_autotune -- with on != 0, choose each multigrid level's element CTA
+ * tiles by timing: for every packing of small elements (64, 128 or 256 nodes
+ * per CTA) and every launch class (tiles of <= 128, <= 256, <= 729 nodes),
+ * the volume kernel is timed with two CTA sizes on a freestream state, and
+ * the fastest packing and sizes are kept.  Levels that exist are tuned now
+ * (synchronises the stream; captured V-cycle graphs are dropped), later ones
+ * when they are built.  Results do not change: every node's arithmetic is
+ * the same whatever CTA computes it.  on = 0 keeps the current tiles.
+ */
+int dg_set_autotune(dg_mesh* mesh, int on, void* stream);
+
+/* dg_mesh_tuning -- the finest level's tiles: out[0] nodes per CTA for small
+ * elements, out[1..3] CTA sizes of the three launch classes. */
+int dg_mesh_tuning(const dg_mesh* mesh, int32_t* out);
+
 /* dg_kernel_launches -- cumulative number of CUDA kernels this library has
  * launched in the process (host-side count; a measurement aid). */
 int dg_kernel_launches(int64_t* count);

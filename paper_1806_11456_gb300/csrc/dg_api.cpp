@@ -616,6 +616,34 @@ int dg_mesh_destroy(dg_mesh* m) {
   return DG_OK;
 }
 
+int dg_set_autotune(dg_mesh* m, int on, void* stream) {
+  if (!m) {
+    set_error("dg_set_autotune: null mesh");
+    return DG_EINVAL;
+  }
+  m->autotune = on != 0;
+  if (!m->autotune) return DG_OK;
+  {
+    std::lock_guard<std::mutex> lock(device_sync_mutex());
+    for (auto& kv : m->graphs) cudaGraphExecDestroy(kv.second.exec);  // they hold the old tile lists
+  }
+  m->graphs.clear();
+  cudaStream_t st = S(stream);
+  DG_TRY(tune_level(m, m->fine.get(), st));
+  for (auto& kv : m->levels) DG_TRY(tune_level(m, kv.second.get(), st));
+  return DG_OK;
+}
+
+int dg_mesh_tuning(const dg_mesh* m, int32_t* out) {
+  if (!m || !out) {
+    set_error("dg_mesh_tuning: bad argument");
+    return DG_EINVAL;
+  }
+  out[0] = m->fine->pack;
+  for (int c = 0; c < kTileClasses; ++c) out[1 + c] = m->fine->class_threads[c];
+  return DG_OK;
+}
+
 int dg_mesh_layout(const dg_mesh* m, int64_t* total_nodes, int64_t* elem_offsets) {
   if (!m) {
     set_error("null mesh");

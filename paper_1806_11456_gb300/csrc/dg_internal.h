@@ -128,6 +128,9 @@ struct Level {
   ElemTile* d_tiles = nullptr;
   int n_tiles = 0;
   size_t tile_smem_nodes = 0;           // max nodes of a tile
+  int pack = kTileNodes;                           // tile target for small elements (nodes)
+  int class_threads[kTileClasses] = {kTileNodes, 2 * kTileNodes, kVolThreads};  // per launch class
+  bool tuned = false;                              // pack and threads chosen by timing
   int tile_class_end[kTileClasses] = {0, 0, 0};    // tiles are ordered by class; cumulative ends
   int tile_class_nodes[kTileClasses] = {0, 0, 0};  // max nodes of a tile of each class
   double* d_vol = nullptr;              // 5 x nodes volume part
@@ -153,6 +156,7 @@ struct dg_mesh {
   int nslots = 1;                // independent solves batched in this mesh
   std::vector<dg::Params> slot_prm;
   std::vector<std::vector<double>> slot_raw;  // per-slot raw parameter vectors
+  bool autotune = false;                       // tune every level's tiles when it is built
   std::vector<int32_t> elem_slot;             // K
   std::vector<int32_t> slot_elem_off;         // nslots + 1
   void* d_gas64 = nullptr;       // per-slot gas constants (FP64)
@@ -179,6 +183,11 @@ namespace dg {
 int build_level(const dg_mesh* m, const std::vector<int32_t>& orders, Level* L);
 Level* get_level(dg_mesh* m, const std::vector<int32_t>& orders);
 int ensure_work(Level* L);
+// (re)build a level's element tile lists with `pack` nodes per tile for small elements
+int build_tiles(Level* L, int pack);
+// time the staged element kernels over tile packings and class thread counts and
+// keep the fastest (results do not change: the per-node arithmetic is the same)
+int tune_level(dg_mesh* m, Level* L, cudaStream_t st);
 Params make_params(const double* p);
 
 // kernels (dg_kernels.cu)

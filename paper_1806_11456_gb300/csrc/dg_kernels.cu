@@ -1460,21 +1460,22 @@ static void launch_trace(const Level* L, const double* q, cudaStream_t st) {
 // with 128 threads, <= 256 with 256, larger (one element of up to 729 nodes)
 // with 512, each class with the shared memory of its own largest tile.
 template <typename F>
-static void for_tile_classes(const Level* L, F launch) {
-  static const int threads[kTileClasses] = {kTileNodes, 2 * kTileNodes, kVolThreads};
+static void for_tile_classes(const Level* L, F launch, int only = -1, int threads_override = 0) {
   int begin = 0;
   for (int c = 0; c < kTileClasses; ++c) {
     const int end = L->tile_class_end[c];
-    if (end > begin) {
+    if (end > begin && (only < 0 || only == c)) {
       count_launch();
-      launch(begin, end - begin, threads[c], (size_t)(3 * kNP * kNP + 32 * L->tile_class_nodes[c]) * sizeof(double));
+      const int th = threads_override > 0 ? threads_override : L->class_threads[c];
+      launch(begin, end - begin, th, (size_t)(3 * kNP * kNP + 32 * L->tile_class_nodes[c]) * sizeof(double));
     }
     begin = end;
   }
 }
 
 template <typename R>
-static void launch_volume(const Level* L, const GasT<R>* G, const double* q, cudaStream_t st) {
+static void launch_volume(const Level* L, const GasT<R>* G, const double* q, cudaStream_t st, int only = -1,
+                          int threads_override = 0) {
   LevelArgsT<R> A = largs<R>(L);
   const ST<R>* ust = buf<R>(L->d_ust);
   ST<R>* trg = buf<R>(L->d_trg);
@@ -1491,7 +1492,7 @@ static void launch_volume(const Level* L, const GasT<R>* G, const double* q, cud
       else
         k_volume<R, 3, false><<<nt, th, sm, st>>>(A, t0, G, q, ust, trg, vol);
     }
-  });
+  }, only, threads_override);
 }
 template <typename R>
 static void launch_isolated(const Level* L, const GasT<R>* G, const double* q, const double* s, double* r,
@@ -1605,6 +1606,94 @@ static int profile_t(const dg_mesh* m, Level* L, const double* q, const double* 
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return DG_OK;
+}
+
+// scratch state for tuning: every node at its solve's freestream
+__global__ void __launch_bounds__(kTileNodes) k_fill_freestream(LevelArgsT<double> A, const double* __restrict__ qinf,
+                                                                double* __restrict__ q) {
+  const ElemTile t = A.tiles[blockIdx.x];
+  const int nn = t.n[0] * t.n[1] * t.n[2];
+  for (int i = threadIdx.x; i < t.count * nn; i += blockDim.x) {
+    const int le = i / nn, node = i - le * nn;
+    const int e = A.tile_elems[t.first + le];
+    const size_t base = (size_t)5 * A.off[e] + node;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) q[base + v * nn] = qinf[A.slot[e] * 5 + v];
+  }
+}
+
+template <typename R>
+static int tune_t(dg_mesh* m, Level* L, const double* q, cudaStream_t st) {
+  static const int packs[3] = {64, 128, 256};
+  static const int options[kTileClasses][2] = {{64, 128}, {128, 256}, {256, 512}};
+  const GasT<R>* G = gas_table<R>(m);
+  cudaEvent_t e0, e1;
+  DG_CUDA_TRY(cudaEventCreate(&e0));
+  DG_CUDA_TRY(cudaEventCreate(&e1));
+  double best_total = 1e300;
+  int best_pack = L->pack, best_threads[kTileClasses] = {L->class_threads[0], L->class_threads[1],
+                                                         L->class_threads[2]};
+  int rc = DG_OK;
+  for (int pk : packs) {
+    if ((rc = build_tiles(L, pk)) != DG_OK) break;
+    double total = 0.0;
+    int th_c[kTileClasses] = {kTileNodes, 2 * kTileNodes, kVolThreads};
+    for (int c = 0; c < kTileClasses; ++c) {
+      const int begin = c ? L->tile_class_end[c - 1] : 0;
+      if (L->tile_class_end[c] == begin) continue;
+      double best_c = 1e300;
+      for (int th : options[c]) {
+        launch_volume<R>(L, G, q, st, c, th);  // warm-up
+        DG_CUDA_TRY(cudaEventRecord(e0, st));
+        for (int k = 0; k < 5; ++k) launch_volume<R>(L, G, q, st, c, th);
+        DG_CUDA_TRY(cudaEventRecord(e1, st));
+        DG_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        DG_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_c) {
+          best_c = ms;
+          th_c[c] = th;
+        }
+      }
+      total += best_c;
+    }
+    if (total < best_total) {
+      best_total = total;
+      best_pack = pk;
+      for (int c = 0; c < kTileClasses; ++c) best_threads[c] = th_c[c];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != DG_OK) return rc;
+  if (L->pack != best_pack && (rc = build_tiles(L, best_pack)) != DG_OK) return rc;
+  for (int c = 0; c < kTileClasses; ++c) L->class_threads[c] = best_threads[c];
+  L->tuned = true;
+  return DG_OK;
+}
+
+int tune_level(dg_mesh* m, Level* L, cudaStream_t st) {
+  int rc = configure_smem();
+  if (rc != DG_OK) return rc;
+  if ((rc = prepare_arith(m, L, st)) != DG_OK) return rc;
+  std::vector<double> qinf((size_t)5 * m->nslots);
+  for (int k = 0; k < m->nslots; ++k)
+    for (int v = 0; v < 5; ++v) qinf[k * 5 + v] = m->slot_raw[k][7 + v];
+  double *q = nullptr, *dq = nullptr;
+  DG_CUDA_TRY(cudaMalloc(&q, (size_t)5 * L->nodes * sizeof(double)));
+  DG_CUDA_TRY(cudaMalloc(&dq, qinf.size() * sizeof(double)));
+  DG_CUDA_TRY(cudaMemcpyAsync(dq, qinf.data(), qinf.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  count_launch();
+  k_fill_freestream<<<L->n_tiles, kTileNodes, 0, st>>>(largs<double>(L), dq, q);
+  DG_CUDA_TRY(cudaGetLastError());
+  rc = (m->arith == DG_ARITH_DF32) ? tune_t<dd>(m, L, q, st) : tune_t<double>(m, L, q, st);
+  DG_CUDA_TRY(cudaStreamSynchronize(st));
+  {
+    std::lock_guard<std::mutex> lock(device_sync_mutex());
+    cudaFree(q);
+    cudaFree(dq);
+  }
+  return rc;
 }
 
 int profile_residual(const dg_mesh* m, Level* L, const double* q, const double* s, double* r, int iters,

@@ -389,6 +389,70 @@ Level::~Level() {
     if (p) cudaFree(p);
 }
 
+// CTA work lists of a level: whole elements of one order triple per tile,
+// `pack` nodes per tile at most for elements that fit (one element per tile
+// otherwise), ordered by launch class: tiles of <= 128 nodes, <= 256, larger.
+// Replaces any earlier lists of the level (graphs captured with them must be
+// dropped by the caller).
+int build_tiles(Level* L, int pack) {
+  const int K = L->K;
+  const std::vector<int32_t>& nvec = L->nvec_host;
+  std::map<std::array<int, 3>, std::vector<int32_t>> groups;
+  for (int e = 0; e < K; ++e) groups[{nvec[e * 3], nvec[e * 3 + 1], nvec[e * 3 + 2]}].push_back(e);
+  std::vector<int32_t> tile_elems;
+  std::vector<ElemTile> tiles;
+  size_t max_nodes = 0;
+  for (auto& kv : groups) {
+    int nn = kv.first[0] * kv.first[1] * kv.first[2];
+    if (nn > kMaxElemNodes) {
+      set_error("element with more than 729 nodes");
+      return DG_EINVAL;
+    }
+    int per = std::max(1, pack / nn);
+    const auto& els = kv.second;
+    for (size_t i = 0; i < els.size(); i += per) {
+      ElemTile t;
+      t.first = (int32_t)tile_elems.size();
+      t.count = (int32_t)std::min<size_t>(per, els.size() - i);
+      t.n[0] = (int16_t)kv.first[0];
+      t.n[1] = (int16_t)kv.first[1];
+      t.n[2] = (int16_t)kv.first[2];
+      t.pad = 0;
+      for (int c = 0; c < t.count; ++c) tile_elems.push_back(els[i + c]);
+      tiles.push_back(t);
+      max_nodes = std::max(max_nodes, (size_t)t.count * nn);
+    }
+  }
+  auto tile_class = [](const ElemTile& t) {
+    const int T = t.count * t.n[0] * t.n[1] * t.n[2];
+    return T <= kTileNodes ? 0 : (T <= 2 * kTileNodes ? 1 : 2);
+  };
+  std::stable_sort(tiles.begin(), tiles.end(),
+                   [&](const ElemTile& a, const ElemTile& b) { return tile_class(a) < tile_class(b); });
+  for (int c = 0; c < kTileClasses; ++c) L->tile_class_end[c] = L->tile_class_nodes[c] = 0;
+  for (const ElemTile& t : tiles) {
+    const int c = tile_class(t);
+    L->tile_class_end[c]++;
+    L->tile_class_nodes[c] = std::max(L->tile_class_nodes[c], t.count * t.n[0] * t.n[1] * t.n[2]);
+  }
+  for (int c = 1; c < kTileClasses; ++c) L->tile_class_end[c] += L->tile_class_end[c - 1];
+  {
+    std::lock_guard<std::mutex> lock(device_sync_mutex());
+    if (L->d_tiles) cudaFree(L->d_tiles);
+    if (L->d_tile_elems) cudaFree(L->d_tile_elems);
+  }
+  L->d_tiles = nullptr;
+  L->d_tile_elems = nullptr;
+  int64_t scratch = 0;  // the lists' bytes are counted once, at the first build
+  int64_t* acc = (L->n_tiles == 0) ? &L->bytes : &scratch;
+  DG_TRY(dev_upload(acc, &L->d_tile_elems, tile_elems));
+  DG_TRY(dev_upload(acc, &L->d_tiles, tiles));
+  L->n_tiles = (int)tiles.size();
+  L->tile_smem_nodes = max_nodes;
+  L->pack = pack;
+  return DG_OK;
+}
+
 int build_level(const dg_mesh* m, const std::vector<int32_t>& orders, Level* L) {
   const Tables1D& T = tables();
   const int dim = m->dim, K = m->K;
@@ -579,50 +643,6 @@ int build_level(const dg_mesh* m, const std::vector<int32_t>& orders, Level* L) 
     if (cur.count > 0) mtiles.push_back(cur);
   }
   L->n_mtiles = (int)mtiles.size();
-  // ---- element tiles grouped by node counts ----
-  std::map<std::array<int, 3>, std::vector<int32_t>> groups;
-  for (int e = 0; e < K; ++e) groups[{nvec[e * 3], nvec[e * 3 + 1], nvec[e * 3 + 2]}].push_back(e);
-  std::vector<int32_t> tile_elems;
-  std::vector<ElemTile> tiles;
-  size_t max_nodes = 0;
-  for (auto& kv : groups) {
-    int nn = kv.first[0] * kv.first[1] * kv.first[2];
-    if (nn > kMaxElemNodes) {
-      set_error("element with more than 729 nodes");
-      return DG_EINVAL;
-    }
-    int per = std::max(1, kTileNodes / nn);
-    const auto& els = kv.second;
-    for (size_t i = 0; i < els.size(); i += per) {
-      ElemTile t;
-      t.first = (int32_t)tile_elems.size();
-      t.count = (int32_t)std::min<size_t>(per, els.size() - i);
-      t.n[0] = (int16_t)kv.first[0];
-      t.n[1] = (int16_t)kv.first[1];
-      t.n[2] = (int16_t)kv.first[2];
-      t.pad = 0;
-      for (int c = 0; c < t.count; ++c) tile_elems.push_back(els[i + c]);
-      tiles.push_back(t);
-      max_nodes = std::max(max_nodes, (size_t)t.count * nn);
-    }
-  }
-  // launch classes by tile size (the staged kernels size their shared memory
-  // and threads per class): <= 128 nodes, <= 256, larger
-  auto tile_class = [](const ElemTile& t) {
-    const int T = t.count * t.n[0] * t.n[1] * t.n[2];
-    return T <= kTileNodes ? 0 : (T <= 2 * kTileNodes ? 1 : 2);
-  };
-  std::stable_sort(tiles.begin(), tiles.end(),
-                   [&](const ElemTile& a, const ElemTile& b) { return tile_class(a) < tile_class(b); });
-  for (int c = 0; c < kTileClasses; ++c) L->tile_class_end[c] = L->tile_class_nodes[c] = 0;
-  for (const ElemTile& t : tiles) {
-    const int c = tile_class(t);
-    L->tile_class_end[c]++;
-    L->tile_class_nodes[c] = std::max(L->tile_class_nodes[c], t.count * t.n[0] * t.n[1] * t.n[2]);
-  }
-  for (int c = 1; c < kTileClasses; ++c) L->tile_class_end[c] += L->tile_class_end[c - 1];
-  L->n_tiles = (int)tiles.size();
-  L->tile_smem_nodes = max_nodes;
   // ---- upload ----
   std::vector<int32_t> off32(L->off.begin(), L->off.end());
   DG_TRY(dev_upload(&L->bytes, &L->d_n, nvec));
@@ -634,9 +654,8 @@ int build_level(const dg_mesh* m, const std::vector<int32_t>& orders, Level* L) 
   DG_TRY(dev_upload(&L->bytes, &L->d_mnode_mortar, mnode_mortar));
   DG_TRY(dev_upload(&L->bytes, &L->d_mnS, mnS));
   DG_TRY(dev_upload(&L->bytes, &L->d_mtiles, mtiles));
-  DG_TRY(dev_upload(&L->bytes, &L->d_tile_elems, tile_elems));
   DG_TRY(dev_upload(&L->bytes, &L->d_slot, m->elem_slot));
-  DG_TRY(dev_upload(&L->bytes, &L->d_tiles, tiles));
+  DG_TRY(build_tiles(L, kTileNodes));
   DG_TRY(dev_zeros(&L->bytes, &L->d_trq, (size_t)5 * acc));
   DG_TRY(dev_zeros(&L->bytes, &L->d_ust, (size_t)4 * acc));
   DG_TRY(dev_zeros(&L->bytes, &L->d_trg, (size_t)12 * acc));
@@ -662,6 +681,7 @@ Level* get_level(dg_mesh* m, const std::vector<int32_t>& orders) {
   if (it != m->levels.end()) return it->second.get();
   std::unique_ptr<Level> L(new Level());
   if (build_level(m, orders, L.get()) != DG_OK) return nullptr;
+  if (m->autotune && tune_level(m, L.get(), nullptr) != DG_OK) return nullptr;
   Level* raw = L.get();
   m->levels.emplace(orders, std::move(L));
   return raw;

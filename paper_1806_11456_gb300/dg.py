@@ -87,7 +87,7 @@ EXPORTS = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_layout", "dg_residual",
            "dg_kernel_launches", "dg_transfer_noalloc", "dg_solve_steady", "dg_mesh_orders", "dg_set_arithmetic",
            "dg_batch_create", "dg_batch_info", "dg_residual_norms", "dg_solve_footprint", "dg_server_create",
            "dg_server_submit", "dg_server_wait", "dg_server_info", "dg_server_result", "dg_server_release",
-           "dg_server_destroy", "dg_last_error"]
+           "dg_server_destroy", "dg_set_autotune", "dg_mesh_tuning", "dg_last_error"]
 ARITH = {"fp64": 0, "df32": 1}
 KERNEL_STAGES = ["trace_q", "mortar_u_star", "volume", "mortar_flux", "surface", "isolated"]
 
@@ -121,6 +121,8 @@ def lib(path=LIB_PATH):
     L.dg_batch_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]
     L.dg_residual_norms.argtypes = [_vp, _vp, _vp, _dp, _vp]
     L.dg_transfer_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, _ip, _ip, ctypes.c_int32, _vp, _vp, _vp]
+    L.dg_set_autotune.argtypes = [_vp, ctypes.c_int, _vp]
+    L.dg_mesh_tuning.argtypes = [_vp, _ip]
     L.dg_solve_footprint.argtypes = [ctypes.POINTER(MeshDesc), _ip, ctypes.POINTER(ctypes.c_int64)]
     L.dg_server_create.argtypes = [ctypes.POINTER(ServerParams), ctypes.POINTER(_vp)]
     L.dg_server_submit.argtypes = [_vp, ctypes.POINTER(MeshDesc), _ip, _dp, _dp, ctypes.POINTER(SolveParams),
@@ -275,6 +277,17 @@ class Mesh:
             self.close()
         except Exception:
             pass
+
+    def set_autotune(self, on=True, stream=None):
+        """Choose the element tiles of every level by timing (dg_set_autotune)."""
+        _check(lib().dg_set_autotune(self.h, int(bool(on)), _stream(stream)))
+        return self
+
+    def tuning(self):
+        """Finest level's tiles: nodes per CTA for small elements, CTA sizes per class."""
+        out = np.zeros(4, dtype=np.int32)
+        _check(lib().dg_mesh_tuning(self.h, out.ctypes.data_as(_ip)))
+        return dict(pack=int(out[0]), class_threads=[int(x) for x in out[1:]])
 
     def set_arithmetic(self, mode):
         """'fp64' (native FP64) or 'df32' (double-float pairs on the FP32 pipes)

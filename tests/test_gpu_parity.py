@@ -382,3 +382,31 @@ def test_smoothing_control_per_solve_in_a_batch(dg):
         qa = _dev(q)
         dg.Mesh(m, o, p).vcycle(qa, None, 1, 1, 2, control=6, eta=1.5)
         assert np.array_equal(qbn[5 * off[k]:5 * off[k + 1]], qa.cpu().numpy()), k
+
+
+@pytest.mark.parametrize("kind", ["plate2d", "mixed3d", "sphere"])
+def test_autotuned_tiles_give_the_same_bits(dg, kind):
+    # inputs whose first V-cycle stays finite (checked with the oracle)
+    if kind == "plate2d":
+        mesh = syn.flat_plate_mesh(nx=20, ny=8, dy0=0.01)
+        o = syn.random_orders(mesh["K"], 2, 1, 5, 41)
+    elif kind == "mixed3d":
+        mesh = syn.rotate_elements(syn.periodic_box(3, 3, 2), seed=6, frac=0.5)
+        o = syn.random_orders(mesh["K"], 3, 1, 6, 41)
+    else:
+        mesh = syn.cubed_sphere_mesh(2, 2, M=1)
+        o = syn.random_orders(mesh["K"], 3, 2, 5, 41)
+    prm = syn.flow_params(mach=0.3, re=100.0)
+    q = syn.smooth_state(mesh, o, prm, 9, amp=0.01)
+    A = dg.Mesh(mesh, o, prm)
+    B = dg.Mesh(mesh, o, prm).set_autotune(True)
+    t = B.tuning()
+    assert t["pack"] in (64, 128, 256) and all(x in (64, 128, 256, 512) for x in t["class_threads"])
+    for iso in (False, True):
+        assert np.array_equal(A.residual(_dev(q), isolated=iso).cpu().numpy(),
+                              B.residual(_dev(q), isolated=iso).cpu().numpy())
+    qa, qb = _dev(q), _dev(q)
+    A.vcycle(qa, None, 1, 1, 2, graph=True)
+    B.vcycle(qb, None, 1, 1, 2, graph=True)  # coarse levels built and tuned here
+    qa, qb = qa.cpu().numpy(), qb.cpu().numpy()
+    assert np.all(np.isfinite(qa)) and np.array_equal(qa, qb)
