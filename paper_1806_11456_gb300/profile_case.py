@@ -8,7 +8,8 @@ times on the current CUDA device, then exits.  Nothing is timed here.
 Workloads: flat_plate (60 x 24 stretched plate, N = 7, 92,160 nodes, the
 bench's headline mesh); box3d (periodic 48^3 affine hexes, N = 3, 7.1 M nodes,
 283 MB of state: larger than L2); sphere (13,824 quadratic hexes, orders
-U[1,6]^3).
+U[1,6]^3); tiny3d (periodic 3^3 box, N = 2: a serving-sized request).
+--vcycles runs V-cycles instead of residuals.
 """
 import argparse
 import os
@@ -31,6 +32,11 @@ def workload(name):
         prm = syn.flow_params(mach=0.3, re=100.0)
         o = syn.uniform_orders(mesh["K"], 3, 3)
         return mesh, o, prm, None
+    if name == "tiny3d":
+        mesh = syn.periodic_box(3, 3, 3)
+        prm = syn.flow_params(mach=0.3, re=100.0)
+        o = syn.uniform_orders(mesh["K"], 3, 2)
+        return mesh, o, prm, syn.manufactured_state(mesh, o, 1, prm[2], prm[0], amp=0.05)
     if name == "sphere":
         mesh, o, prm = syn.config_sphere_c3()
         return mesh, o, prm, syn.smooth_state(mesh, o, prm, 5, amp=0.02)
@@ -39,10 +45,12 @@ def workload(name):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("workload", choices=["flat_plate", "box3d", "sphere"])
+    ap.add_argument("workload", choices=["flat_plate", "box3d", "sphere", "tiny3d"])
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--arith", default="fp64", choices=["fp64", "df32"])
+    ap.add_argument("--vcycles", action="store_true",
+                    help="run V-cycles (3/3/10 sweeps, graph replay) instead of residual evaluations")
     args = ap.parse_args()
     sys.path.insert(0, ROOT)
     import torch
@@ -63,7 +71,10 @@ def main():
         qd = torch.tensor(q, device="cuda")
     r = torch.empty_like(qd)
     for _ in range(args.warmup + args.iters):
-        M.residual(qd, None, r=r)
+        if args.vcycles:
+            M.vcycle(qd, None, beta1=3, beta2=3, beta_c=10, graph=True)
+        else:
+            M.residual(qd, None, r=r)
     torch.cuda.synchronize()
 
 
