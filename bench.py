@@ -186,12 +186,13 @@ def run_reference(args, rank):
 def steady_problem(dg, torch, dev, mesh, o, prm, q_target, seed, amp=0.01):
     """A steady problem whose discrete solution is q_target: S = A(q_target),
     evaluated by the library (the residual with no source is -A), and a
-    start q_target + amp * |q_target| * noise.  On a periodic mesh the
+    start q_target + amp * |q_target| * w with w a smooth periodic wave
+    sin(2 pi (x + 2y + 3z) + phase_v), seeded phases.  On a periodic mesh the
     pseudo-time iteration conserves the discrete totals of the five
-    variables, so the noise is made of zero weighted mean per variable
-    (Gauss weights; the meshes here have equal elements and one order map
-    per element count), else the start's totals would admit no steady state
-    with this source."""
+    variables, so w is given zero weighted mean per variable (Gauss weights;
+    the meshes here have equal elements).  Per-node noise as the start does
+    not converge to 1e-10 with the fixed-count cycle on these boxes (it
+    stalls near 1e-5), a smooth perturbation does in a few hundred cycles."""
     from paper_1806_11456_gb300 import synthetic as syn
     M = dg.Mesh(mesh, o, prm)
     r = M.residual(torch.tensor(q_target, device=dev))
@@ -206,23 +207,25 @@ def steady_problem(dg, torch, dev, mesh, o, prm, q_target, seed, amp=0.01):
             w = np.multiply.outer(np.polynomial.legendre.leggauss(int(o[e, d]) + 1)[1], w)
         W.append(w.reshape(-1))
     W = np.concatenate(W)
-    noise = rng.uniform(-1.0, 1.0, (5, off[-1]))
-    noise -= (noise @ W / W.sum())[:, None]
+    X = syn.node_coordinates(mesh, o)
+    phase = rng.uniform(0.0, 2.0 * np.pi, 5)
+    wave = np.stack([np.sin(2.0 * np.pi * (X[:, 0] + 2.0 * X[:, 1] + 3.0 * X[:, 2]) + phase[v]) for v in range(5)])
+    wave -= (wave @ W / W.sum())[:, None]
     scale = np.abs(syn.from_blocked(q_target, o, dim)).max(axis=1)[:, None]
-    q0 = q_target + amp * syn.to_blocked(noise * scale, o, dim)
+    q0 = q_target + amp * syn.to_blocked(wave * scale, o, dim)
     return S, q0
 
 
 def time_to_tolerance(dg, torch, dev, tol=1e-10, max_cycles=3000):
     """Time to max|r| < tol of a steady problem on the config-1 mesh (4x4x1
     periodic box, N = 3, Mach 0.3, Re 100) whose discrete solution is the
-    manufactured field: S = A(q*), start q* plus 1% zero-mean noise; repeated
+    manufactured field: S = A(q*), start q* plus a 1% smooth zero-mean wave; repeated
     V-cycles 3 -> 1 (3/3/10 sweeps), CUDA graphs, a residual check every 10
     cycles; FP64 and double-float."""
     from paper_1806_11456_gb300 import synthetic as syn
     mesh, o, prm, q_star = syn.config_box_c1()
     S, q0 = steady_problem(dg, torch, dev, mesh, o, prm, q_star, seed=11)
-    out = {"workload": "periodic box 4x4x1, N=3, S = A(q*) with q* the manufactured field, start q* + 1% zero-mean noise",
+    out = {"workload": "periodic box 4x4x1, N=3, S = A(q*) with q* the manufactured field, start q* + 1% smooth zero-mean wave",
            "tol": tol, "cycle": "V 3->1, 3/3/10 sweeps, graph replay, norm every 10 cycles"}
     for arith in ("fp64", "df32"):
         M = dg.Mesh(mesh, o, prm).set_arithmetic(arith)
@@ -343,7 +346,7 @@ def serving_requests(dg, torch, dev, n, seed=4):
     N = 2), Mach U[0.25, 0.4], Re U_log[50, 200] (problems the fixed-count
     FAS cycle converges to 1e-10 in ~10^3 cycles); each with a known discrete
     solution q* (the manufactured field with seeded phases), S = A(q*), start
-    q*(1 + 1% seeded noise)."""
+    q* plus a 1% smooth zero-mean wave."""
     from paper_1806_11456_gb300 import synthetic as syn
     rng = np.random.default_rng(seed)
     out = []
@@ -375,7 +378,7 @@ def serving(dg, torch, dev, rate=4.0, window=4.0, slots=8, budget=150 << 30, see
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * window * 3)))
     arrivals = arrivals[arrivals < window]
     reqs = serving_requests(dg, torch, dev, len(arrivals), seed)
-    kw = dict(tol=1e-10, max_cycles=1500, mg=dict(beta1=3, beta2=3, beta_c=10, graph=1))
+    kw = dict(tol=1e-10, max_cycles=1500, check_every=10, mg=dict(beta1=3, beta2=3, beta_c=10, graph=1))
 
     def run(n_slots):
         ids = [None] * len(reqs)
@@ -407,7 +410,7 @@ def serving(dg, torch, dev, rate=4.0, window=4.0, slots=8, budget=150 << 30, see
     nodes = [int(np.sum(np.prod(o[:, :m["dim"]] + 1, axis=1))) for (m, o, *_r) in reqs]
     return {"workload": f"{len(reqs)} requests, Poisson {rate}/s over {window} s: periodic 2D boxes 2-6 per side "
                         "N in {2,3} and 3D boxes 3 per side N = 2, Mach U[0.25,0.4], Re U_log[50,200], "
-                        "S = A(q*), to max|r| < 1e-10 (at most 1500 V-cycles 3/3/10)",
+                        "S = A(q*), to max|r| < 1e-10 (at most 1500 V-cycles 3/3/10, residual checked every 10)",
             "requests": len(reqs), "dof_range": [5 * min(nodes), 5 * max(nodes)],
             "offered_dof_per_s": 5.0 * sum(nodes) / window,
             "concurrent": conc, "one_at_a_time": seq, "p99_speedup": seq["p99_s"] / conc["p99_s"]}

@@ -269,6 +269,9 @@ typedef struct {
   dg_adapt_params ap;      /* adaptation parameters (jump rule etc.; ap.cap = single-stage cap) */
   int32_t stage_orders[4]; /* caps of the successive stages P_2 < P_3 < ... (the mesh enters at P_1) */
   double ref_factor;       /* reference solves converge to ref_factor * tau_max (paper: 1/10; <= 0 means 0.1) */
+  int32_t check_every;     /* residual checked after every k-th V-cycle (<= 1: every cycle); a phase
+                              may run up to k - 1 cycles past its target */
+  int32_t reserved;
 } dg_solve_params;
 
 typedef struct {

@@ -841,20 +841,23 @@ int dg_profile_residual(dg_mesh* m, const double* q, const double* s, double* r,
 // *cycles counts them.  Returns DG_OK, DG_ENOTCONVERGED or DG_EDIVERGED.
 static int cycle_until(dg_mesh* m, const std::vector<int32_t>& o, Level* L, double* Q, const double* Sv,
                        const dg_mg_params& mg, double target, int cap, cudaStream_t st, int* cycles, double* dofs,
-                       double* rn) {
+                       double* rn, int every = 1) {
   DG_TRY(level_norm(m, L, Q, Sv, st, rn));
   dofs[0] += 5.0 * L->nodes;
-  for (int c = 0; c < cap; ++c) {
+  every = std::max(1, every);
+  for (int c = 0; c < cap;) {
     if (!(*rn < target)) {
       if (std::isnan(*rn) || std::isinf(*rn)) return DG_EDIVERGED;
     } else {
       return DG_OK;
     }
-    int ev = 0, nl = 0;
-    double dd = 0.0;
-    DG_TRY(run_vcycle(m, o, Q, Sv, mg, st, &ev, &dd, &nl));
-    dofs[0] += dd;
-    (*cycles)++;
+    for (int k = 0; k < every && c < cap; ++k, ++c) {
+      int ev = 0, nl = 0;
+      double dd = 0.0;
+      DG_TRY(run_vcycle(m, o, Q, Sv, mg, st, &ev, &dd, &nl));
+      dofs[0] += dd;
+      (*cycles)++;
+    }
     DG_TRY(level_norm(m, L, Q, Sv, st, rn));
     dofs[0] += 5.0 * L->nodes;
   }
@@ -898,7 +901,7 @@ int dg_solve_steady(dg_mesh** meshp, double** qp, const double* s, const dg_solv
       if (s) DG_TRY(transfer(m, m->fine.get(), L, 5, s, L->d_S, st));
       int cyc = 0;
       rc = cycle_until(m, o, L, L->d_Q, s ? L->d_S : nullptr, mg, sp->fmg_tol, sp->max_cycles, st, &cyc,
-                       &rep->dof_evals, &rn);
+                       &rep->dof_evals, &rn, sp->check_every);
       rep->cycles += cyc;
       rep->fmg_cycles += cyc;
       if (rc == DG_EDIVERGED) break;
@@ -912,7 +915,7 @@ int dg_solve_steady(dg_mesh** meshp, double** qp, const double* s, const dg_solv
     const double ref = sp->ref_factor > 0.0 ? sp->ref_factor : 0.1;
     double target = sp->adapt ? sp->ap.tau_max * ref : sp->tol;
     int cyc = 0;
-    rc = cycle_until(m, m->orders, m->fine.get(), q, s, mg, target, sp->max_cycles, st, &cyc, &rep->dof_evals, &rn);
+    rc = cycle_until(m, m->orders, m->fine.get(), q, s, mg, target, sp->max_cycles, st, &cyc, &rep->dof_evals, &rn, sp->check_every);
     rep->cycles += cyc;
   }
   // ---- adaptation (Sec. 3.3.2), possibly in stages (Sec. 3.3.4) ----
@@ -923,7 +926,7 @@ int dg_solve_steady(dg_mesh** meshp, double** qp, const double* s, const dg_solv
         int cyc = 0;
         const double ref = sp->ref_factor > 0.0 ? sp->ref_factor : 0.1;
         rc = cycle_until(m, m->orders, m->fine.get(), q, nullptr, mg, sp->ap.tau_max * ref, sp->max_cycles, st,
-                         &cyc, &rep->dof_evals, &rn);
+                         &cyc, &rep->dof_evals, &rn, sp->check_every);
         rep->cycles += cyc;
         if (rc != DG_OK) break;
       }
@@ -979,7 +982,7 @@ int dg_solve_steady(dg_mesh** meshp, double** qp, const double* s, const dg_solv
     if (rc == DG_OK) {
       int cyc = 0;
       rc = cycle_until(m, m->orders, m->fine.get(), q, nullptr, mg, sp->tol, sp->max_cycles, st, &cyc,
-                       &rep->dof_evals, &rn);
+                       &rep->dof_evals, &rn, sp->check_every);
       rep->cycles += cyc;
     }
   }

@@ -108,3 +108,12 @@ def test_footprint_bounds_the_memory_held(dg):
             info = S.info(rid)
             assert info["dev_bytes"] > 0
             assert info["dev_bytes"] <= info["est_bytes"] <= 4 * info["dev_bytes"] + (2 << 20), info
+
+
+def test_check_every_runs_whole_groups_of_cycles(dg):
+    m, o, p, q, s = _requests(1, 5)[0]
+    kw = dict(tol=1e-30, max_cycles=7, mg=MG)
+    qa, _, rep1 = _alone(dg, m, o, p, q, s, **kw)
+    qb, _, rep5 = _alone(dg, m, o, p, q, s, check_every=5, **kw)
+    assert rep1["cycles"] == rep5["cycles"] == 7  # the cap still bounds the phase
+    assert np.array_equal(qa, qb)                 # same cycles, fewer residual checks
