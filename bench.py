@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--c2-solve", action="store_true",
+                    help="also run the steady driver with adaptation on the flat plate (several minutes)")
     ap.add_argument("--mg-compare", type=int, default=0, metavar="CYCLES",
                     help="also compare isotropic and anisotropic V-cycles on the flat plate for CYCLES cycles "
                          "(about a second per cycle; off by default)")
@@ -187,7 +189,8 @@ def steady_problem(dg, torch, dev, mesh, o, prm, q_target, seed, amp=0.01):
     """A steady problem whose discrete solution is q_target: S = A(q_target),
     evaluated by the library (the residual with no source is -A), and a
     start q_target + amp * |q_target| * w with w a smooth periodic wave
-    sin(2 pi (x + 2y + 3z) + phase_v), seeded phases.  On a periodic mesh the
+    sin(2 pi (x + 2y) + phase_v), seeded phases (resolved on every mesh here,
+    including the one-element-thick 4x4x1 box).  On a periodic mesh the
     pseudo-time iteration conserves the discrete totals of the five
     variables, so w is given zero weighted mean per variable (Gauss weights;
     the meshes here have equal elements).  Per-node noise as the start does
@@ -209,7 +212,7 @@ def steady_problem(dg, torch, dev, mesh, o, prm, q_target, seed, amp=0.01):
     W = np.concatenate(W)
     X = syn.node_coordinates(mesh, o)
     phase = rng.uniform(0.0, 2.0 * np.pi, 5)
-    wave = np.stack([np.sin(2.0 * np.pi * (X[:, 0] + 2.0 * X[:, 1] + 3.0 * X[:, 2]) + phase[v]) for v in range(5)])
+    wave = np.stack([np.sin(2.0 * np.pi * (X[:, 0] + 2.0 * X[:, 1]) + phase[v]) for v in range(5)])
     wave -= (wave @ W / W.sum())[:, None]
     scale = np.abs(syn.from_blocked(q_target, o, dim)).max(axis=1)[:, None]
     q0 = q_target + amp * syn.to_blocked(wave * scale, o, dim)
@@ -440,6 +443,32 @@ def precision_report(dg, torch, dev):
     out["tau_rel_err"] = float(np.max(np.abs(t["df32"] - t["fp64"])[meas]) / np.max(t["fp64"][meas]))
     out["tau_measured_same"] = bool(np.array_equal(t["df32"] >= 0, meas))
     return out
+
+
+def c2_solve(dg, torch, dev, tau_max=1e-2, tol=1e-6, max_cycles=400):
+    """The steady driver with adaptation on the flat plate (60x24, N = 7,
+    Mach 0.2, Re 1e5, freestream start): controlled V-cycles (100/100/400,
+    eta 1.1, at most 10 blocks per rule) to tau_max/10, the anisotropic
+    isolated tau estimate, adaptation to orders in [1, 7]^2 (jump limit
+    1), V-cycles on the adapted mesh to tol.  tau_max and tol are looser
+    than the paper's 1e-4 and 1e-10 so the run fits in minutes."""
+    from paper_1806_11456_gb300 import synthetic as syn
+    mesh = syn.flat_plate_mesh()
+    prm = syn.flow_params(mach=0.2, re=1e5)
+    o = syn.uniform_orders(mesh["K"], 2, 7)
+    M = dg.Mesh(mesh, o, prm)
+    q = torch.tensor(syn.freestream_state(mesh, o, prm), device=dev)
+    t0 = time.perf_counter()
+    q2, rep = M.solve_steady(q, None, tol=tol, max_cycles=max_cycles, adapt=True, tau_max=tau_max, n_min=1,
+                             n_max=7, jump_rule=1,
+                             mg=dict(beta1=100, beta2=100, beta_c=400, control=10, eta=1.1, graph=0))
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    hist = {}
+    for nx, ny in M.orders[:, :2]:
+        hist[f"{nx},{ny}"] = hist.get(f"{nx},{ny}", 0) + 1
+    return {"workload": "flat plate 60x24, N = 7 start, freestream", "tau_max": tau_max, "tol": tol,
+            "seconds": secs, "report": rep, "nodes_before": int(mesh["K"] * 64), "orders_histogram": hist}
 
 
 def mg_compare(dg, torch, dev, cycles):
@@ -690,6 +719,8 @@ def run_gb300(args, rank, world):
         out["roofline_sweep"] = roofline_sweep(dg, torch, dev)
         out["serving"] = serving(dg, torch, dev)
         out["precision"] = precision_report(dg, torch, dev)
+        if args.c2_solve:
+            out["c2_solve"] = c2_solve(dg, torch, dev)
         if args.mg_compare > 0:
             out["mg_compare"] = mg_compare(dg, torch, dev, args.mg_compare)
         out["cpu_baseline"] = cpu_baseline_sample(mesh, prm, orders, q_np) if world == 1 else None

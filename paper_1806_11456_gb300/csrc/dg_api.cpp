@@ -82,11 +82,20 @@ struct Cycle {
 static int smooth_level(Cycle& C, Level* L, double* Q, const double* Sv, int sweeps,
                         const double* mask = nullptr) {
   DG_TRY(ensure_work(L));
+  // The sweeps alternate two per-slot dt buffers: the last stage of a sweep
+  // reduces the next sweep's dt from the state it produces, so only the
+  // block's first sweep launches the CFL kernel; likewise every stage's
+  // surface kernel writes the traces of the state it updates, so only the
+  // block's first stage computes them from Q.
+  double* dtb[2] = {C.m->d_scalars, C.m->d_scalars + 5 * C.m->nslots};
+  if (sweeps > 0) DG_TRY(cfl_dt(C.m, L, Q, dtb[0], C.st));
   for (int k = 0; k < sweeps; ++k) {
-    DG_TRY(cfl_dt(C.m, L, Q, C.m->d_scalars, C.st));
-    if (mask) DG_TRY(mask_dt(C.m, C.m->d_scalars, mask, C.st));
+    double* dt = dtb[k & 1];
+    double* dt_next = (k + 1 < sweeps) ? dtb[(k + 1) & 1] : nullptr;
+    if (mask) DG_TRY(mask_dt(C.m, dt, mask, C.st));
     for (int stage = 0; stage < 3; ++stage) {
-      DG_TRY(residual(C.m, L, Q, Sv, nullptr, false, C.st, nullptr, stage, L->d_G, C.m->d_scalars));
+      const int tf = kTracesNext | ((k > 0 || stage > 0) ? kTracesCurrent : 0);
+      DG_TRY(residual(C.m, L, Q, Sv, nullptr, false, C.st, nullptr, stage, L->d_G, dt, tf, dt_next));
       C.evals++;
       C.dofs += 5.0 * L->nodes;
     }
@@ -500,7 +509,7 @@ int dg_mesh_create(const dg_mesh_desc* desc, const int32_t* orders, dg_mesh** ou
   int rc = build_level(m, m->orders, m->fine.get());
   if (rc == DG_OK) rc = upload_gas(m);
   if (rc == DG_OK) {
-    cudaError_t e1 = cudaMalloc(&m->d_scalars, (5 * m->nslots + 16) * sizeof(double));
+    cudaError_t e1 = cudaMalloc(&m->d_scalars, (6 * m->nslots + 16) * sizeof(double));
     cudaError_t e2 = cudaMalloc(&m->d_tau, (size_t)m->K * 3 * kTauSlots * sizeof(double));
     cudaError_t e3 = cudaMalloc(&m->d_orders, m->orders.size() * sizeof(int32_t));
     if (e3 == cudaSuccess)
@@ -561,7 +570,7 @@ int dg_batch_create(const dg_mesh_desc* descs, const int32_t* const* orders, int
   int rc = build_level(m, m->orders, m->fine.get());
   if (rc == DG_OK) rc = upload_gas(m);
   if (rc == DG_OK) {
-    cudaError_t e1 = cudaMalloc(&m->d_scalars, (5 * m->nslots + 16) * sizeof(double));
+    cudaError_t e1 = cudaMalloc(&m->d_scalars, (6 * m->nslots + 16) * sizeof(double));
     cudaError_t e2 = cudaMalloc(&m->d_tau, (size_t)m->K * 3 * kTauSlots * sizeof(double));
     cudaError_t e3 = cudaMalloc(&m->d_orders, m->orders.size() * sizeof(int32_t));
     if (e3 == cudaSuccess)

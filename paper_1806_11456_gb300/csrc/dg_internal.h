@@ -166,7 +166,8 @@ struct dg_mesh {
   std::unique_ptr<dg::Level> fine;
   std::map<std::vector<int32_t>, std::unique_ptr<dg::Level>> levels;  // coarse levels by order map
   double* d_scalars = nullptr;   // per slot: [0, n) dt, [n, 2n) max|r|, [2n, 3n) and [3n, 4n) the
-                                 // smoothing-control norms, [4n, 5n) 1/0 smoothing mask (n = nslots)
+                                 // smoothing-control norms, [4n, 5n) 1/0 smoothing mask, [5n, 6n) the
+                                 // alternate dt of every other sweep (n = nslots)
   double* d_tau = nullptr;       // K x 3 x 16 tau table
   int32_t* d_orders = nullptr;   // K x 3 orders on the device
   cudaStream_t cap_stream = nullptr;  // stream used to capture cycle graphs
@@ -204,8 +205,17 @@ unsigned long long launches_total();  // launched by all threads
 void add_launches(unsigned long long n);
 int prepare_capture();  // one-time per-device set-up that may not run inside a capture
 int prepare_arith(const dg_mesh* m, Level* L, cudaStream_t st);  // per-level data the arithmetic mode needs
+// trace_flags for residual(): the face traces of q are already in the level's
+// buffer (skip computing them) / an RK stage also writes the traces of the
+// updated state there (the next stage then passes kTracesCurrent)
+constexpr int kTracesCurrent = 1;
+constexpr int kTracesNext = 2;
+// dt_next (RK stages only): the next sweep's per-slot time step, reset by
+// stage 1 and reduced from the updated state by stage 2 (what cfl_dt would
+// compute from that state)
 int residual(const dg_mesh* m, Level* L, const double* q, const double* s, double* r, bool isolated,
-             cudaStream_t st, double* d_norm, int rk_stage, double* rk_g, const double* d_dt);
+             cudaStream_t st, double* d_norm, int rk_stage, double* rk_g, const double* d_dt,
+             int trace_flags = 0, double* dt_next = nullptr);
 int cfl_dt(const dg_mesh* m, Level* L, const double* q, double* d_dt, cudaStream_t st);
 int profile_residual(const dg_mesh* m, Level* L, const double* q, const double* s, double* r, int iters,
                      double* ms_out, cudaStream_t st);

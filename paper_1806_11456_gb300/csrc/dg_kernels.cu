@@ -522,23 +522,14 @@ DEV int face_size(int f, int n0, int n1, int n2) {
 // ---------------------------------------------------------------------------
 // k_trace_q: conserved state at every face node of every element
 // ---------------------------------------------------------------------------
+// Conserved state at every face node of the tile's elements from the staged
+// state sq (5 x T, variable-major): interpolation to xi_d = -1 / +1 along
+// the face's normal direction.
 template <typename R, int DIM>
-__global__ void __launch_bounds__(kTileNodes) k_trace_q(LevelArgsT<R> A, const double* __restrict__ q,
-                                                        typename Store<R>::T* __restrict__ trq) {
-  extern __shared__ double smem_raw[];
-  R* sq = reinterpret_cast<R*>(smem_raw);
-  const ElemTile t = A.tiles[blockIdx.x];
+DEV void write_face_traces(const LevelArgsT<R>& A, const ElemTile& t, const R* sq, int T,
+                           typename Store<R>::T* __restrict__ trq) {
   const int n0 = t.n[0], n1 = t.n[1], n2 = t.n[2];
   const int nn = n0 * n1 * n2;
-  const int T = t.count * nn;
-  for (int i = threadIdx.x; i < T; i += blockDim.x) {
-    int le = i / nn, node = i - le * nn;
-    int e = A.tile_elems[t.first + le];
-    const double* qe = q + (size_t)5 * A.off[e];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) sq[v * T + i] = from_double<R>(qe[v * nn + node]);
-  }
-  __syncthreads();
   int FE = 0;
 #pragma unroll
   for (int f = 0; f < 2 * DIM; ++f) FE += face_size(f, n0, n1, n2);
@@ -568,6 +559,25 @@ __global__ void __launch_bounds__(kTileNodes) k_trace_q(LevelArgsT<R> A, const d
       Store<R>::put(trq, v * A.fn + p, acc);
     }
   }
+}
+
+template <typename R, int DIM>
+__global__ void __launch_bounds__(kTileNodes) k_trace_q(LevelArgsT<R> A, const double* __restrict__ q,
+                                                        typename Store<R>::T* __restrict__ trq) {
+  extern __shared__ double smem_raw[];
+  R* sq = reinterpret_cast<R*>(smem_raw);
+  const ElemTile t = A.tiles[blockIdx.x];
+  const int nn = t.n[0] * t.n[1] * t.n[2];
+  const int T = t.count * nn;
+  for (int i = threadIdx.x; i < T; i += blockDim.x) {
+    int le = i / nn, node = i - le * nn;
+    int e = A.tile_elems[t.first + le];
+    const double* qe = q + (size_t)5 * A.off[e];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sq[v * T + i] = from_double<R>(qe[v * nn + node]);
+  }
+  __syncthreads();
+  write_face_traces<R, DIM>(A, t, sq, T, trq);
 }
 
 // ---------------------------------------------------------------------------
@@ -1007,12 +1017,48 @@ __global__ void __launch_bounds__(kVolThreads) __maxnreg__(DIM == 2 ? 96 : 104) 
 // ---------------------------------------------------------------------------
 // k_surface: surface terms, r = S - A; optional RK3 stage and max|r|
 // ---------------------------------------------------------------------------
+// CFL limit of Sec. 2 at one node: min over directions d with N_d > 0 of
+// C_a h_d / ((|v| + c) N_d^2) and C_nu h_d^2 / (nu N_d^4), h_d = 2 / |a^d|,
+// from the conserved state qq and the FP64 geometry (geo, SoA over nodes).
+template <int DIM>
+DEV double node_dt(const GasD& G, const double* qq, const double* __restrict__ geo, int64_t nodes, int64_t gn,
+                   int n0, int n1, int n2) {
+  double best = 1e300;
+  const double ir = 1.0 / qq[0];
+  const double u0 = qq[1] * ir, u1 = qq[2] * ir, u2 = qq[3] * ir;
+  const double p = G.g1 * (qq[4] - 0.5 * (qq[1] * u0 + qq[2] * u1 + qq[3] * u2));
+  const double Tt = G.gM2 * p * ir;
+  const double c = sqrt(G.g * p * ir);
+  const double vel = sqrt(u0 * u0 + u1 * u1 + u2 * u2);
+  const double nu = Tt * sqrt(Tt) * G.Su1 / (Tt + G.Su) * ir * G.invRe;
+  const double iJ = geo[9 * nodes + gn];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const int N = pick(d, n0, n1, n2) - 1;
+    if (N <= 0) continue;
+    double j0 = geo[(3 * d + 0) * nodes + gn], j1 = geo[(3 * d + 1) * nodes + gn],
+           j2 = geo[(3 * d + 2) * nodes + gn];
+    double h = 2.0 / (sqrt(j0 * j0 + j1 * j1 + j2 * j2) * iJ);
+    double N2 = (double)N * (double)N;
+    best = fmin(best, G.Ca * h / ((vel + c) * N2));
+    best = fmin(best, G.Cnu * h * h / (nu * N2 * N2));
+  }
+  return best;
+}
+
 struct RKArgs {
   int stage;          // -1: plain residual, 0..2 RK3 stage
   double a, b;
   double* g;          // RK register
   const double* dt;   // device scalar
   double* qupd;       // state updated in place
+  void* trq_next;     // if set: face traces of the updated state (the next stage's traces)
+  // if set: the next sweep's time step per slot, reset in stage 1 and reduced
+  // from the updated state in stage 2 (the work of k_cfl on that state)
+  double* dt_next;
+  const GasD* gasd;
+  const double* geo64;  // FP64 geometry (the dt must not depend on the arithmetic mode)
+  int nslots;
 };
 
 template <typename R, int DIM>
@@ -1021,14 +1067,20 @@ __global__ void __launch_bounds__(kTileNodes) k_surface(LevelArgsT<R> A, const t
                                                         const double* __restrict__ s, double* __restrict__ r,
                                                         double* norm, RKArgs rk) {
   using SR = Store<R>;
+  extern __shared__ double smem_raw[];
+  R* sq = reinterpret_cast<R*>(smem_raw);  // updated state (5 x T) when rk.trq_next is set
+  const bool traces = rk.stage >= 0 && rk.trq_next != nullptr;
   const ElemTile t = A.tiles[blockIdx.x];
+  if (rk.dt_next && rk.stage == 1 && blockIdx.x == 0)
+    for (int k = threadIdx.x; k < rk.nslots; k += blockDim.x) rk.dt_next[k] = 1e300;
+  const bool cfl = rk.dt_next && rk.stage == 2;
   const int n0 = t.n[0], n1 = t.n[1], n2 = t.n[2];
   const int nn = n0 * n1 * n2;
   const int T = t.count * nn;
   for (int i0 = 0; i0 < T; i0 += blockDim.x) {  // all lanes iterate together (warp reductions)
     const int i = i0 + threadIdx.x;
     const bool active = i < T;
-    double lmax = 0.0;
+    double lmax = 0.0, best = 1e300;
     int slot = 0;
     if (active) {
       const int le = i / nn, node = i - le * nn;
@@ -1051,20 +1103,33 @@ __global__ void __launch_bounds__(kTileNodes) k_surface(LevelArgsT<R> A, const t
       }
       const R iJ = SR::get(A.geo, 9 * A.nodes + A.off[e] + node);
       const double dt = (rk.stage >= 0) ? rk.dt[slot] : 0.0;
+      double qnew[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         const double rv = (s ? s[base + v * nn] : 0.0) - to_double(acc[v] * iJ);
         lmax = (rv != rv) ? INFINITY : fmax(lmax, fabs(rv));  // a NaN residual reads as +inf
         if (rk.stage < 0) {
           r[base + v * nn] = rv;
-        } else if (dt != 0.0) {  // dt = 0: the solve is held (smoothing control)
-          double gv = (rk.stage == 0 ? 0.0 : rk.a * rk.g[base + v * nn]) + dt * rv;
-          rk.g[base + v * nn] = gv;
-          rk.qupd[base + v * nn] += rk.b * gv;
+        } else {
+          double qn = rk.qupd[base + v * nn];
+          if (dt != 0.0) {  // dt = 0: the solve is held (smoothing control)
+            double gv = (rk.stage == 0 ? 0.0 : rk.a * rk.g[base + v * nn]) + dt * rv;
+            rk.g[base + v * nn] = gv;
+            qn += rk.b * gv;
+            rk.qupd[base + v * nn] = qn;
+          }
+          if (traces) sq[v * T + i] = from_double<R>(qn);
+          qnew[v] = qn;
         }
       }
+      if (cfl) best = node_dt<DIM>(rk.gasd[slot], qnew, rk.geo64, A.nodes, A.off[e] + node, n0, n1, n2);
     }
     if (norm) warp_slot_reduce<true>(norm, slot, lmax, active);
+    if (cfl) warp_slot_reduce<false>(rk.dt_next, slot, best, active);
+  }
+  if (traces) {
+    __syncthreads();
+    write_face_traces<R, DIM>(A, t, sq, T, static_cast<typename Store<R>::T*>(rk.trq_next));
   }
 }
 
@@ -1151,31 +1216,11 @@ __global__ void __launch_bounds__(kTileNodes) k_cfl(LevelArgsT<double> A, const 
       int le = i / nn, node = i - le * nn;
       int e = A.tile_elems[t.first + le];
       slot = A.slot[e];
-      const GasD G = gasd[slot];
-      const int64_t gn = A.off[e] + node;
       const double* qe = q + (size_t)5 * A.off[e];
       double qq[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) qq[v] = qe[v * nn + node];
-      const double ir = 1.0 / qq[0];
-      const double u0 = qq[1] * ir, u1 = qq[2] * ir, u2 = qq[3] * ir;
-      const double p = G.g1 * (qq[4] - 0.5 * (qq[1] * u0 + qq[2] * u1 + qq[3] * u2));
-      const double Tt = G.gM2 * p * ir;
-      const double c = sqrt(G.g * p * ir);
-      const double vel = sqrt(u0 * u0 + u1 * u1 + u2 * u2);
-      const double nu = Tt * sqrt(Tt) * G.Su1 / (Tt + G.Su) * ir * G.invRe;
-      const double iJ = A.geo[9 * A.nodes + gn];
-#pragma unroll
-      for (int d = 0; d < DIM; ++d) {
-        const int N = pick(d, n0, n1, n2) - 1;
-        if (N <= 0) continue;
-        double j0 = A.geo[(3 * d + 0) * A.nodes + gn], j1 = A.geo[(3 * d + 1) * A.nodes + gn],
-               j2 = A.geo[(3 * d + 2) * A.nodes + gn];
-        double h = 2.0 / (sqrt(j0 * j0 + j1 * j1 + j2 * j2) * iJ);
-        double N2 = (double)N * (double)N;
-        best = fmin(best, G.Ca * h / ((vel + c) * N2));
-        best = fmin(best, G.Cnu * h * h / (nu * N2 * N2));
-      }
+      best = node_dt<DIM>(gasd[slot], qq, A.geo, A.nodes, A.off[e] + node, n0, n1, n2);
     }
     warp_slot_reduce<false>(dtmin, slot, best, active);
   }
@@ -1517,10 +1562,11 @@ static void launch_surface(const Level* L, const double* s, double* r, double* n
                            cudaStream_t st) {
   count_launch();
   LevelArgsT<R> A = largs<R>(L);
+  const size_t sm = rk.trq_next ? 5 * L->tile_smem_nodes * sizeof(double) : 0;
   if (L->dim == 2)
-    k_surface<R, 2><<<L->n_tiles, kTileNodes, 0, st>>>(A, buf<R>(L->d_vol), buf<R>(L->d_fst), s, r, norm, rk);
+    k_surface<R, 2><<<L->n_tiles, kTileNodes, sm, st>>>(A, buf<R>(L->d_vol), buf<R>(L->d_fst), s, r, norm, rk);
   else
-    k_surface<R, 3><<<L->n_tiles, kTileNodes, 0, st>>>(A, buf<R>(L->d_vol), buf<R>(L->d_fst), s, r, norm, rk);
+    k_surface<R, 3><<<L->n_tiles, kTileNodes, sm, st>>>(A, buf<R>(L->d_vol), buf<R>(L->d_fst), s, r, norm, rk);
 }
 template <typename R>
 static void launch_mortar(int pass, const Level* L, const GasT<R>* G, cudaStream_t st) {
@@ -1542,12 +1588,18 @@ static RKArgs rk_args(int rk_stage, double* rk_g, const double* d_dt, const doub
   rk.g = rk_g;
   rk.dt = d_dt;
   rk.qupd = const_cast<double*>(q);
+  rk.trq_next = nullptr;
+  rk.dt_next = nullptr;
+  rk.gasd = nullptr;
+  rk.geo64 = nullptr;
+  rk.nslots = 0;
   return rk;
 }
 
 template <typename R>
 static int residual_t(const dg_mesh* m, Level* L, const double* q, const double* s, double* r, bool isolated,
-                      cudaStream_t st, double* d_norm, int rk_stage, double* rk_g, const double* d_dt) {
+                      cudaStream_t st, double* d_norm, int rk_stage, double* rk_g, const double* d_dt,
+                      int trace_flags, double* dt_next) {
   const GasT<R>* G = gas_table<R>(m);
   if (isolated) {
     TauArgs ta{nullptr, nullptr, nullptr, 0, 0};
@@ -1555,24 +1607,33 @@ static int residual_t(const dg_mesh* m, Level* L, const double* q, const double*
     DG_CUDA_TRY(cudaGetLastError());
     return DG_OK;
   }
-  launch_trace<R>(L, q, st);
+  if (!(trace_flags & kTracesCurrent)) launch_trace<R>(L, q, st);
   launch_mortar<R>(1, L, G, st);
   launch_volume<R>(L, G, q, st);
   launch_mortar<R>(2, L, G, st);
-  launch_surface<R>(L, s, r, d_norm, rk_args(rk_stage, rk_g, d_dt, q), st);
+  RKArgs rk = rk_args(rk_stage, rk_g, d_dt, q);
+  if (rk_stage >= 0 && (trace_flags & kTracesNext)) rk.trq_next = buf<R>(L->d_trq);
+  if (rk_stage >= 0 && dt_next) {
+    rk.dt_next = dt_next;
+    rk.gasd = m->d_gasd;
+    rk.geo64 = L->d_geo;
+    rk.nslots = m->nslots;
+  }
+  launch_surface<R>(L, s, r, d_norm, rk, st);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
 }
 
 int residual(const dg_mesh* m, Level* L, const double* q, const double* s, double* r, bool isolated,
-             cudaStream_t st, double* d_norm, int rk_stage, double* rk_g, const double* d_dt) {
+             cudaStream_t st, double* d_norm, int rk_stage, double* rk_g, const double* d_dt, int trace_flags,
+             double* dt_next) {
   int rc = configure_smem();
   if (rc != DG_OK) return rc;
   if (m->arith == DG_ARITH_DF32) {
     if ((rc = ensure_dd(L, st)) != DG_OK) return rc;
-    return residual_t<dd>(m, L, q, s, r, isolated, st, d_norm, rk_stage, rk_g, d_dt);
+    return residual_t<dd>(m, L, q, s, r, isolated, st, d_norm, rk_stage, rk_g, d_dt, trace_flags, dt_next);
   }
-  return residual_t<double>(m, L, q, s, r, isolated, st, d_norm, rk_stage, rk_g, d_dt);
+  return residual_t<double>(m, L, q, s, r, isolated, st, d_norm, rk_stage, rk_g, d_dt, trace_flags, dt_next);
 }
 
 template <typename R>

@@ -410,3 +410,19 @@ def test_autotuned_tiles_give_the_same_bits(dg, kind):
     B.vcycle(qb, None, 1, 1, 2, graph=True)  # coarse levels built and tuned here
     qa, qb = qa.cpu().numpy(), qb.cpu().numpy()
     assert np.all(np.isfinite(qa)) and np.array_equal(qa, qb)
+
+
+@pytest.mark.parametrize("arith", ARITHS)
+@pytest.mark.parametrize("name", ["plate2d_all_bcs", "periodic3d_mortars"])
+def test_fused_traces_and_time_step_give_the_same_bits(dg, name, arith):
+    """Sweeps after the first take their face traces and time step from the
+    previous stage's surface kernel; one sweep per call computes them the
+    plain way (trace and CFL kernels).  Both must give the same bits."""
+    mesh, o, prm, q = CASES[name]()
+    s = syn.random_source(mesh, o, 3)
+    M = dg.Mesh(mesh, o, prm).set_arithmetic(arith)
+    qa, qb = _dev(q), _dev(q)
+    M.smooth(qa, _dev(s), sweeps=4)
+    for _ in range(4):
+        M.smooth(qb, _dev(s), sweeps=1)
+    assert np.array_equal(qa.cpu().numpy(), qb.cpu().numpy())
