@@ -634,6 +634,23 @@ def run_gb300(args, rank, world):
     clk = clocks.stop(dev.index)
     total_ms, value = aggregate_ranks(total_ms, total_dofs, world, dev)
 
+    # where a step's time goes (separate pass, CUDA events around each part)
+    parts = {"vcycle": 0.0, "tau": 0.0, "adapt": 0.0}
+    for _ in range(10):
+        q.copy_(q0)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        M.vcycle(q, None, graph=True, **CYCLE)
+        ev[1].record(stream)
+        tau = M.tau_estimate(q, None, dir_mask=3)
+        ev[2].record(stream)
+        M.adapt(tau, TAU_MAX, 1, 7, jump_rule=1)
+        ev[3].record(stream)
+        ev[3].synchronize()
+        for k, name in enumerate(("vcycle", "tau", "adapt")):
+            parts[name] += ev[k].elapsed_time(ev[k + 1]) / 10
+
     # e2e through the C ABI with pinned host buffers
     qh = torch.tensor(q_np).pin_memory()
     qout = torch.empty_like(qh).pin_memory()
@@ -712,7 +729,8 @@ def run_gb300(args, rank, world):
                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                "config": dict(cfg, parallelism=f"replicas{world}"), "e2e": e2e,
-               "gpu_launches": None, "roofline": roof, "clocks": clk, "df32": df32, "autotune": autotune}
+               "gpu_launches": None, "roofline": roof, "clocks": clk, "step_ms_parts": parts, "df32": df32,
+               "autotune": autotune}
         out["gpu_launches"] = int(launches)  # library kernels launched in the timed steps
         out["time_to_tol"] = time_to_tolerance(dg, torch, dev)
         out["batched"] = batched_solves(dg, torch, dev)

@@ -50,3 +50,21 @@ def test_footprint_is_host_logic_and_grows_with_orders():
     assert 0 < small < large
     m3 = syn.periodic_box(3, 3, 3)
     assert dg.solve_footprint(m3, syn.uniform_orders(m3["K"], 3, 4), prm) > large
+
+
+def test_server_rejects_bad_parameters_without_touching_the_device():
+    import ctypes
+    import __graft_entry__ as g
+    g.build()
+    from paper_1806_11456_gb300 import dg
+    L = dg.lib()
+    h = ctypes.c_void_p()
+    for budget, slots in ((1 << 30, 0), (0, 2), (1 << 30, 1000)):
+        p = dg.ServerParams()
+        p.hbm_budget, p.slots, p.device = budget, slots, 0
+        assert L.dg_server_create(ctypes.byref(p), ctypes.byref(h)) == -1  # DG_EINVAL
+    rid = ctypes.c_int64()
+    sp = dg.solve_params()
+    assert L.dg_server_submit(None, None, None, None, None, ctypes.byref(sp), ctypes.byref(rid)) == -1
+    assert L.dg_server_wait(None, -1, 0.0) == -1
+    assert L.dg_server_destroy(None) == 0
