@@ -220,13 +220,13 @@ def steady_problem(dg, torch, dev, mesh, o, prm, q_target, seed, amp=0.01):
 
 
 def time_to_tolerance(dg, torch, dev, tol=1e-10, max_cycles=3000):
-    """Time to max|r| < tol of a steady problem on the config-1 mesh (4x4x1
-    periodic box, N = 3, Mach 0.3, Re 100) whose discrete solution is the
-    manufactured field: S = A(q*), start q* plus a 1% smooth zero-mean wave; repeated
+    """Time to max|r| < tol of a steady problem on the 4x4x1 periodic unit box
+    (N = 3, Mach 0.3, Re 100) whose discrete solution is the manufactured
+    field: S = A(q*), start q* plus a 1% smooth zero-mean wave; repeated
     V-cycles 3 -> 1 (3/3/10 sweeps), CUDA graphs, a residual check every 10
     cycles; FP64 and double-float."""
     from paper_1806_11456_gb300 import synthetic as syn
-    mesh, o, prm, q_star = syn.config_box_c1()
+    mesh, o, prm, q_star = syn.manufactured_box_4x4x1()
     S, q0 = steady_problem(dg, torch, dev, mesh, o, prm, q_star, seed=11)
     out = {"workload": "periodic box 4x4x1, N=3, S = A(q*) with q* the manufactured field, start q* + 1% smooth zero-mean wave",
            "tol": tol, "cycle": "V 3->1, 3/3/10 sweeps, graph replay, norm every 10 cycles"}
@@ -259,7 +259,7 @@ def batched_solves(dg, torch, dev, steps=5):
     freestream start.  A step is one V-cycle 8 -> 1 of every solve."""
     from paper_1806_11456_gb300 import synthetic as syn
     t0 = time.time()
-    items = syn.batch_workload_c4()
+    items = syn.batch_workload_64()
     q_np = [syn.freestream_state(m, o, p) for (m, o, p) in items]
     t_gen = time.time() - t0
     groups = [[k for k in range(len(items)) if items[k][0]["dim"] == d] for d in (2, 3)]
@@ -425,7 +425,7 @@ def precision_report(dg, torch, dev):
     Re 200; the FP64 path matches the oracle to 1e-12 in the parity tests):
     the residual, one V-cycle 6 -> 1 (1/1/2 sweeps) and the tau table."""
     from paper_1806_11456_gb300 import synthetic as syn
-    mesh, o, prm = syn.config_sphere_c3()
+    mesh, o, prm = syn.sphere_shell_13824()
     q = syn.smooth_state(mesh, o, prm, 5, amp=0.02)
     out = {"workload": "cubed-sphere shell 6x12x12x16 = 13,824 quadratic hexes, orders U[1,6]^3, Mach 0.2, Re 200"}
     M = {a: dg.Mesh(mesh, o, prm).set_arithmetic(a) for a in ("fp64", "df32")}

@@ -38,7 +38,7 @@ def workload(name):
         o = syn.uniform_orders(mesh["K"], 3, 2)
         return mesh, o, prm, syn.manufactured_state(mesh, o, 1, prm[2], prm[0], amp=0.05)
     if name == "sphere":
-        mesh, o, prm = syn.config_sphere_c3()
+        mesh, o, prm = syn.sphere_shell_13824()
         return mesh, o, prm, syn.smooth_state(mesh, o, prm, 5, amp=0.02)
     raise SystemExit(f"unknown workload {name}")
 

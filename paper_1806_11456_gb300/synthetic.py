@@ -510,7 +510,7 @@ def random_source(mesh, orders, seed, amp=1e-2):
 # --------------------------------------------------------------------------
 # named workloads
 # --------------------------------------------------------------------------
-def config_box_c1(seed=0):
+def manufactured_box_4x4x1(seed=0):
     """4x4x1 periodic unit box, N=3, manufactured state (Mach 0.3, Re 100)."""
     mesh = periodic_box(4, 4, 1)
     prm = flow_params(mach=0.3, re=100.0)
@@ -519,7 +519,7 @@ def config_box_c1(seed=0):
     return mesh, orders, prm, q
 
 
-def config_sphere_c3(seed=2, nt=12, nr=16):
+def sphere_shell_13824(seed=2, nt=12, nr=16):
     """Cubed-sphere shell r in [1, 20], 6 x nt x nt x nr quadratic hexes
     (13,824 at nt=12, nr=16), orders uniform in [1, 6]^3 from the seed, Mach
     0.2, Re 200, no-slip adiabatic sphere, freestream outer boundary."""
@@ -538,7 +538,7 @@ def compatible_source(mesh, orders, S, weights_times_J):
     return to_blocked(F, orders, mesh["dim"])
 
 
-def config_flat_plate_c2(N=7):
+def flat_plate_60x24(N=7):
     """60x24 stretched 2D flat plate, uniform N, freestream start (Mach 0.2, Re 1e5)."""
     mesh = flat_plate_mesh()
     prm = flow_params(mach=0.2, re=1e5)
@@ -547,7 +547,7 @@ def config_flat_plate_c2(N=7):
     return mesh, orders, prm, q
 
 
-def batch_workload_c4(seed=3, nsolves=64, kmin=200, kmax=4000, nmax=8, sphere_M=2):
+def batch_workload_64(seed=3, nsolves=64, kmin=200, kmax=4000, nmax=8, sphere_M=2):
     """Many independent steady solves: half stretched 2D plate-type meshes,
     half cubed-sphere shells.  Element counts log-uniform in [kmin, kmax],
     orders i.i.d. uniform in [1, nmax]^dim, Mach log-uniform in [0.1, 0.4],

@@ -36,7 +36,7 @@ def _dev(x):
 
 def _cases():
     c = {}
-    c["c1_box_N3"] = lambda: syn.config_box_c1()
+    c["box4x4x1_N3"] = lambda: syn.manufactured_box_4x4x1()
     def mixed3d():
         mesh = syn.periodic_box(3, 2, 2)
         prm = syn.flow_params(mach=0.3, re=100.0)
@@ -119,7 +119,7 @@ def test_flat_plate_full_size_residual(dg, arith):
     assert np.max(np.abs(r - ro)) <= TOL * orc.volume_scale(mesh, o, prm, q)
 
 
-@pytest.mark.parametrize("name", ["c1_box_N3", "periodic3d_mortars", "plate2d_all_bcs", "curved_sphere_mortars"])
+@pytest.mark.parametrize("name", ["box4x4x1_N3", "periodic3d_mortars", "plate2d_all_bcs", "curved_sphere_mortars"])
 def test_cfl_dt_parity(dg, name):
     mesh, o, prm, q = CASES[name]()
     M = dg.Mesh(mesh, o, prm)
@@ -127,7 +127,7 @@ def test_cfl_dt_parity(dg, name):
     assert abs(dt - orc.cfl_dt(mesh, o, prm, q)) <= 1e-14 * dt
 
 
-@pytest.mark.parametrize("name", ["c1_box_N3", "plate2d_all_bcs"])
+@pytest.mark.parametrize("name", ["box4x4x1_N3", "plate2d_all_bcs"])
 def test_smoother_parity(dg, name):
     mesh, o, prm, q = CASES[name]()
     s = syn.random_source(mesh, o, 3)
@@ -139,8 +139,8 @@ def test_smoother_parity(dg, name):
 
 
 @pytest.mark.parametrize("name,kw", [
-    ("c1_box_N3", dict(beta1=3, beta2=3, beta_c=3, delta_n=2)),        # 2 levels, N=3 -> N=1
-    ("c1_box_N3", dict(beta1=1, beta2=2, beta_c=3, delta_n=1)),
+    ("box4x4x1_N3", dict(beta1=3, beta2=3, beta_c=3, delta_n=2)),        # 2 levels, N=3 -> N=1
+    ("box4x4x1_N3", dict(beta1=1, beta2=2, beta_c=3, delta_n=1)),
     ("periodic3d_mortars", dict(beta1=1, beta2=1, beta_c=2, delta_n=1)),
     ("plate2d_all_bcs", dict(beta1=2, beta2=1, beta_c=3, delta_n=1)),
     ("plate2d_all_bcs", dict(beta1=1, beta2=1, beta_c=1, direction=1)),
@@ -317,7 +317,7 @@ def test_sphere_full_size_residual(dg, arith):
     through the high-order derivative operators to a few 1e-12 of the term
     scale on both sides; the small cases above keep white noise at lower
     orders.)"""
-    mesh, o, prm = syn.config_sphere_c3()
+    mesh, o, prm = syn.sphere_shell_13824()
     q = syn.smooth_state(mesh, o, prm, 3)
     M = dg.Mesh(mesh, o, prm).set_arithmetic(arith)
     qd = _dev(q)
