@@ -614,6 +614,8 @@ int dg_mesh_destroy(dg_mesh* m) {
     std::lock_guard<std::mutex> lock(device_sync_mutex());
     for (auto& kv : m->graphs) cudaGraphExecDestroy(kv.second.exec);
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
+    for (cudaStream_t t : m->tau_st)
+      if (t) cudaStreamDestroy(t);
     if (m->d_scalars) cudaFree(m->d_scalars);
     if (m->d_tau) cudaFree(m->d_tau);
     if (m->d_orders) cudaFree(m->d_orders);
@@ -777,9 +779,23 @@ int dg_tau_estimate(dg_mesh* m, const double* q, const double* s, int dir_mask, 
   // R^P(q) at the reference orders
   if (with_correction) DG_TRY(residual(m, F, q, s, F->d_R, isolated != 0, st, nullptr, -1, nullptr, nullptr));
   const int32_t* d_fine_orders = m->d_orders;
+  // The directions are independent (their levels, buffers and table slots
+  // differ): each runs on its own stream, forked from and joined back to st.
+  cudaEvent_t ev_fork = nullptr, ev_join[3] = {nullptr, nullptr, nullptr};
+  DG_CUDA_TRY(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+  DG_CUDA_TRY(cudaEventRecord(ev_fork, st));
   int rc = DG_OK;
   for (int i = 0; i < m->dim && rc == DG_OK; ++i) {
     if (!((dir_mask >> i) & 1)) continue;
+    if (!m->tau_st[i] && cudaStreamCreateWithFlags(&m->tau_st[i], cudaStreamNonBlocking) != cudaSuccess) {
+      rc = DG_ECUDA;
+      break;
+    }
+    cudaStream_t sti = m->tau_st[i];
+    if (cudaStreamWaitEvent(sti, ev_fork, 0) != cudaSuccess) {
+      rc = DG_ECUDA;
+      break;
+    }
     int top = 0;
     for (int e = 0; e < m->K; ++e) top = std::max(top, (int)m->orders[e * 3 + i]);
     Level* prev = F;
@@ -793,17 +809,23 @@ int dg_tau_estimate(dg_mesh* m, const double* q, const double* s, int dir_mask, 
         break;
       }
       if ((rc = ensure_work(Ll)) != DG_OK) break;
-      if ((rc = transfer(m, prev, Ll, 5, Qp, Ll->d_Q, st)) != DG_OK) break;
-      if (s && (rc = transfer(m, prev, Ll, 5, Sp, Ll->d_S, st)) != DG_OK) break;
-      if (Rp && (rc = transfer(m, prev, Ll, 5, Rp, Ll->d_G, st)) != DG_OK) break;
+      if ((rc = transfer(m, prev, Ll, 5, Qp, Ll->d_Q, sti)) != DG_OK) break;
+      if (s && (rc = transfer(m, prev, Ll, 5, Sp, Ll->d_S, sti)) != DG_OK) break;
+      if (Rp && (rc = transfer(m, prev, Ll, 5, Rp, Ll->d_G, sti)) != DG_OK) break;
       rc = tau_accumulate(m, Ll, Ll->d_Q, s ? Ll->d_S : nullptr, Rp ? Ll->d_G : nullptr, isolated != 0, i, l,
-                          d_fine_orders, m->d_tau, st);
+                          d_fine_orders, m->d_tau, sti);
       prev = Ll;
       Qp = Ll->d_Q;
       Sp = Ll->d_S;
       Rp = Rp ? Ll->d_G : nullptr;
     }
+    if (cudaEventCreateWithFlags(&ev_join[i], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(ev_join[i], sti) != cudaSuccess || cudaStreamWaitEvent(st, ev_join[i], 0) != cudaSuccess)
+      rc = DG_ECUDA;
   }
+  cudaEventDestroy(ev_fork);
+  for (cudaEvent_t e : ev_join)
+    if (e) cudaEventDestroy(e);
   if (rc == DG_OK) {
     cudaError_t e = cudaMemcpyAsync(tau_host, m->d_tau, tsz * sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -171,6 +171,7 @@ struct dg_mesh {
   double* d_tau = nullptr;       // K x 3 x 16 tau table
   int32_t* d_orders = nullptr;   // K x 3 orders on the device
   cudaStream_t cap_stream = nullptr;  // stream used to capture cycle graphs
+  cudaStream_t tau_st[3] = {nullptr, nullptr, nullptr};  // one per direction of the tau estimate
   struct Graph {
     cudaGraphExec_t exec = nullptr;
     int evals = 0;
