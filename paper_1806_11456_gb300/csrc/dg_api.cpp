@@ -325,20 +325,22 @@ static DirFit fit_dir(const double* t, int P) {
   DirFit F;
   F.P = P;
   F.t = t;
-  std::vector<double> xs, ys;
-  for (int N = 1; N < P; ++N)
+  double xs[kTauSlots], ys[kTauSlots];
+  int np = 0;
+  for (int N = 1; N < P && N < kTauSlots; ++N)
     if (t[N] > 0.0) {
-      xs.push_back((double)N);
-      ys.push_back(std::log10(t[N]));
+      xs[np] = (double)N;
+      ys[np] = std::log10(t[N]);
+      ++np;
     }
-  if (xs.size() >= 2) {
+  if (np >= 2) {
     double sx = 0.0, sy = 0.0;
-    for (double x : xs) sx += x;
-    for (double y : ys) sy += y;
-    double xm = sx / xs.size(), ym = sy / ys.size();
+    for (int k = 0; k < np; ++k) sx += xs[k];
+    for (int k = 0; k < np; ++k) sy += ys[k];
+    double xm = sx / np, ym = sy / np;
     double sxx = 0.0, sxy = 0.0;
-    for (double x : xs) sxx += (x - xm) * (x - xm);
-    for (size_t k = 0; k < xs.size(); ++k) sxy += (xs[k] - xm) * (ys[k] - ym);
+    for (int k = 0; k < np; ++k) sxx += (xs[k] - xm) * (xs[k] - xm);
+    for (int k = 0; k < np; ++k) sxy += (xs[k] - xm) * (ys[k] - ym);
     double b = sxy / sxx;
     if (b < 0.0) {
       F.has_slope = true;
@@ -356,6 +358,12 @@ static void select_element(const double* tab /* 3 x 16 */, const int32_t* P, con
   if (ap.cap > 0) hi = std::min(hi, (int)ap.cap);
   DirFit F[3];
   for (int i = 0; i < dim; ++i) F[i] = fit_dir(tab + i * kTauSlots, P[i]);
+  // each direction's estimate over the candidate range, evaluated once
+  double tab_at[3][kTauSlots + 1];
+  const int top = std::max(hi, 1);
+  for (int i = 0; i < dim; ++i)
+    for (int N = 0; N <= top && N <= kTauSlots; ++N) tab_at[i][N] = F[i].at(N);
+  auto at = [&](int i, int N) { return N <= kTauSlots ? tab_at[i][N] : F[i].at(N); };
   auto search = [&](const int* lo, const int* up, int32_t* best) -> bool {
     bool found = false;
     long bestdof = 0;
@@ -367,7 +375,7 @@ static void select_element(const double* tab /* 3 x 16 */, const int32_t* P, con
     while (true) {
       for (int i = 0; i < dim; ++i) N[i] = cur[i];
       double tv = 0.0;
-      for (int i = 0; i < dim; ++i) tv += F[i].at(N[i]);
+      for (int i = 0; i < dim; ++i) tv += at(i, N[i]);
       if (tv < ap.tau_max) {
         long dof = 1;
         for (int i = 0; i < dim; ++i) dof *= (N[i] + 1);
