@@ -508,7 +508,7 @@ DEV void face_interp(const typename Store<R>::T* X, int64_t fs, int na, int nb, 
       const R wgt = ida ? wb : wb * SR::get(Ta, ka);
       int p = kb * na + ka;
 #pragma unroll
-      for (int v = 0; v < NVAR; ++v) out[v] += wgt * SR::get(X, v * fs + p);
+      for (int v = 0; v < NVAR; ++v) out[v] = madd(out[v], wgt, SR::get(X, v * fs + p));
     }
   }
 }
@@ -555,7 +555,7 @@ DEV void write_face_traces(const LevelArgsT<R>& A, const ElemTile& t, const R* s
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       R acc = cst<R>(0.0f);
-      for (int k = 0; k < nd; ++k) acc += (side ? Tab<R>::lp(nd, k) : Tab<R>::lm(nd, k)) * s0[v * T + k * sd];
+      for (int k = 0; k < nd; ++k) acc = madd(acc, (side ? Tab<R>::lp(nd, k) : Tab<R>::lm(nd, k)), s0[v * T + k * sd]);
       Store<R>::put(trq, v * A.fn + p, acc);
     }
   }
@@ -708,7 +708,7 @@ DEV void mortar_project(const R* vals, int ma, int mb, int Ma, int Mb, int orien
       const int aa = sw ? jb : ja, bb = sw ? ja : jb;  // back to the L frame
       const R* x = vals + (bb * ma + aa) * 5;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) acc[v] += wgt * x[v];
+      for (int v = 0; v < NV; ++v) acc[v] = madd(acc[v], wgt, x[v]);
     }
   }
 }
@@ -832,14 +832,14 @@ DEV void gradient_volume(const R* sD, const R* sA, int T, int nn, int i, int n0,
         const int la = base + a * sd;
         const R c = Drow[a];
 #pragma unroll
-        for (int v = 0; v < 4; ++v) cu[v] += c * sA[v * T + la];
+        for (int v = 0; v < 4; ++v) cu[v] = madd(cu[v], c, sA[v * T + la]);
       }
       const R j0 = sA[(4 + d * 3 + 0) * T + i], j1 = sA[(4 + d * 3 + 1) * T + i], j2 = sA[(4 + d * 3 + 2) * T + i];
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
-        g[v * 3 + 0] += j0 * cu[v];
-        g[v * 3 + 1] += j1 * cu[v];
-        g[v * 3 + 2] += j2 * cu[v];
+        g[v * 3 + 0] = madd(g[v * 3 + 0], j0, cu[v]);
+        g[v * 3 + 1] = madd(g[v * 3 + 1], j1, cu[v]);
+        g[v * 3 + 2] = madd(g[v * 3 + 2], j2, cu[v]);
       }
     } else {
       for (int a = 0; a < nd; ++a) {
@@ -851,9 +851,9 @@ DEV void gradient_volume(const R* sD, const R* sA, int T, int nn, int i, int n0,
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           const R uv = sA[v * T + la];
-          g[v * 3 + 0] += j0 * uv;
-          g[v * 3 + 1] += j1 * uv;
-          g[v * 3 + 2] += j2 * uv;
+          g[v * 3 + 0] = madd(g[v * 3 + 0], j0, uv);
+          g[v * 3 + 1] = madd(g[v * 3 + 1], j1, uv);
+          g[v * 3 + 2] = madd(g[v * 3 + 2], j2, uv);
         }
       }
     }
@@ -911,7 +911,7 @@ DEV void divergence(const R* sD, const R* sA, int T, int nn, int i, int n0, int 
       const int la = base + a * sd;
       const R c = Drow[a];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) acc[v] += c * sA[(d * 5 + v) * T + la];
+      for (int v = 0; v < 5; ++v) acc[v] = madd(acc[v], c, sA[(d * 5 + v) * T + la]);
     }
   }
 }
@@ -956,9 +956,9 @@ __global__ void __launch_bounds__(kVolThreads) __maxnreg__(DIM == 2 ? 96 : 104) 
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         const R us = SR::get(ust, v * A.fn + p);
-        g[v * 3 + 0] += m0 * us;
-        g[v * 3 + 1] += m1 * us;
-        g[v * 3 + 2] += m2 * us;
+        g[v * 3 + 0] = madd(g[v * 3 + 0], m0, us);
+        g[v * 3 + 1] = madd(g[v * 3 + 1], m1, us);
+        g[v * 3 + 2] = madd(g[v * 3 + 2], m2, us);
       }
     }
     const R iJ = SR::get(A.geo, 9 * A.nodes + A.off[e] + node);
@@ -993,7 +993,7 @@ __global__ void __launch_bounds__(kVolThreads) __maxnreg__(DIM == 2 ? 96 : 104) 
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
         R acc = cst<R>(0.0f);
-        for (int j = 0; j < nd; ++j) acc += (side ? Tab<R>::lp(nd, j) : Tab<R>::lm(nd, j)) * s0[k * T + j * sdd];
+        for (int j = 0; j < nd; ++j) acc = madd(acc, (side ? Tab<R>::lp(nd, j) : Tab<R>::lm(nd, j)), s0[k * T + j * sdd]);
         SR::put(trg, k * A.fn + p, acc);
       }
     }
@@ -1099,7 +1099,7 @@ __global__ void __launch_bounds__(kTileNodes) k_surface(LevelArgsT<R> A, const t
         const R lw = side ? Tab<R>::lpw(nd, id) : Tab<R>::lmw(nd, id);
         const int64_t p = A.fo[e * 6 + f] + pick(tb, idx0, idx1, idx2) * pick(ta, n0, n1, n2) + pick(ta, idx0, idx1, idx2);
 #pragma unroll
-        for (int v = 0; v < 5; ++v) acc[v] += lw * SR::get(fst, v * A.fn + p);
+        for (int v = 0; v < 5; ++v) acc[v] = madd(acc[v], lw, SR::get(fst, v * A.fn + p));
       }
       const R iJ = SR::get(A.geo, 9 * A.nodes + A.off[e] + node);
       const double dt = (rk.stage >= 0) ? rk.dt[slot] : 0.0;
