@@ -433,9 +433,10 @@ int dg_server_destroy(dg_server* srv);
 /*
  * dg_set_autotune -- with on != 0, choose each multigrid level's element CTA
  * tiles by timing: for every packing of small elements (64, 128 or 256 nodes
- * per CTA) and every launch class (tiles of <= 128, <= 256, <= 729 nodes),
- * the volume kernel is timed with two CTA sizes on a freestream state, and
- * the fastest packing and sizes are kept.  Levels that exist are tuned now
+ * per CTA) the volume kernel of every launch class (tiles of <= 128, <= 256,
+ * <= 729 nodes) is timed with two CTA sizes on a freestream state, the
+ * faster size kept, and the packings are compared on the time of the whole
+ * residual (the other tile kernels see the same tiles); the fastest is kept.  Levels that exist are tuned now
  * (synchronises the stream; captured V-cycle graphs are dropped), later ones
  * when they are built.  Results do not change: every node's arithmetic is
  * the same whatever CTA computes it.  on = 0 keeps the current tiles.

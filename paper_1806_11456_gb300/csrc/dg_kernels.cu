@@ -1684,6 +1684,11 @@ __global__ void __launch_bounds__(kTileNodes) k_fill_freestream(LevelArgsT<doubl
 }
 
 template <typename R>
+static int residual_t(const dg_mesh* m, Level* L, const double* q, const double* s, double* r, bool isolated,
+                      cudaStream_t st, double* d_norm, int rk_stage, double* rk_g, const double* d_dt,
+                      int trace_flags, double* dt_next);
+
+template <typename R>
 static int tune_t(dg_mesh* m, Level* L, const double* q, cudaStream_t st) {
   static const int packs[3] = {64, 128, 256};
   static const int options[kTileClasses][2] = {{64, 128}, {128, 256}, {256, 512}};
@@ -1697,7 +1702,6 @@ static int tune_t(dg_mesh* m, Level* L, const double* q, cudaStream_t st) {
   int rc = DG_OK;
   for (int pk : packs) {
     if ((rc = build_tiles(L, pk)) != DG_OK) break;
-    double total = 0.0;
     int th_c[kTileClasses] = {kTileNodes, 2 * kTileNodes, kVolThreads};
     for (int c = 0; c < kTileClasses; ++c) {
       const int begin = c ? L->tile_class_end[c - 1] : 0;
@@ -1716,8 +1720,24 @@ static int tune_t(dg_mesh* m, Level* L, const double* q, cudaStream_t st) {
           th_c[c] = th;
         }
       }
-      total += best_c;
     }
+    // packings are compared on the whole residual: the other tile kernels
+    // (traces, surface) see the same tiles
+    for (int c = 0; c < kTileClasses; ++c) L->class_threads[c] = th_c[c];
+    if ((rc = residual_t<R>(m, L, q, nullptr, L->d_R, false, st, nullptr, -1, nullptr, nullptr, 0, nullptr)) !=
+        DG_OK)
+      break;
+    DG_CUDA_TRY(cudaEventRecord(e0, st));
+    for (int k = 0; k < 5; ++k)
+      if ((rc = residual_t<R>(m, L, q, nullptr, L->d_R, false, st, nullptr, -1, nullptr, nullptr, 0, nullptr)) !=
+          DG_OK)
+        break;
+    if (rc != DG_OK) break;
+    DG_CUDA_TRY(cudaEventRecord(e1, st));
+    DG_CUDA_TRY(cudaEventSynchronize(e1));
+    float ms_res = 0.f;
+    DG_CUDA_TRY(cudaEventElapsedTime(&ms_res, e0, e1));
+    const double total = ms_res;
     if (total < best_total) {
       best_total = total;
       best_pack = pk;
@@ -1736,6 +1756,7 @@ static int tune_t(dg_mesh* m, Level* L, const double* q, cudaStream_t st) {
 int tune_level(dg_mesh* m, Level* L, cudaStream_t st) {
   int rc = configure_smem();
   if (rc != DG_OK) return rc;
+  if ((rc = ensure_work(L)) != DG_OK) return rc;
   if ((rc = prepare_arith(m, L, st)) != DG_OK) return rc;
   std::vector<double> qinf((size_t)5 * m->nslots);
   for (int k = 0; k < m->nslots; ++k)
