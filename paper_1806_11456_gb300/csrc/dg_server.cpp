@@ -13,6 +13,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <exception>
 #include <memory>
 #include <mutex>
 #include <thread>
@@ -219,7 +220,11 @@ void worker(dg_server* S) {
       r->state = DG_REQ_RUNNING;
       r->t_start = seconds_since(S->t0);
     }
-    run_request(*r, st);
+    try {
+      run_request(*r, st);
+    } catch (const std::exception&) {  // host allocation failure: the request fails, the server lives
+      r->state = DG_ENOMEM;
+    }
     {
       std::lock_guard<std::mutex> lk(S->mu);
       S->used -= r->est;
@@ -266,8 +271,21 @@ int dg_server_create(const dg_server_params* p, dg_server** out) {
   return DG_OK;
 }
 
+static int submit_impl(dg_server* S, const dg_mesh_desc* desc, const int32_t* orders, const double* q0,
+                       const double* s, const dg_solve_params* sp, int64_t* id);
+
 int dg_server_submit(dg_server* S, const dg_mesh_desc* desc, const int32_t* orders, const double* q0,
                      const double* s, const dg_solve_params* sp, int64_t* id) {
+  try {
+    return submit_impl(S, desc, orders, q0, s, sp, id);
+  } catch (const std::exception&) {
+    set_error("dg_server_submit: out of host memory");
+    return DG_ENOMEM;
+  }
+}
+
+static int submit_impl(dg_server* S, const dg_mesh_desc* desc, const int32_t* orders, const double* q0,
+                       const double* s, const dg_solve_params* sp, int64_t* id) {
   if (!S || !desc || !orders || !sp || !id || desc->K <= 0 || (desc->dim != 2 && desc->dim != 3) ||
       desc->M < 1 || !desc->xmap || !desc->ftab || (sp->adapt && s)) {
     set_error("dg_server_submit: bad argument");
