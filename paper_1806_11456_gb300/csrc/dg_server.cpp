@@ -159,7 +159,9 @@ void run_request(Request& r, cudaStream_t st) {
   d.ftab = r.ftab.data();
   std::memcpy(d.params, r.params, sizeof(d.params));
   int rc = dg_mesh_create(&d, r.orders.data(), &m);
+  if (rc == DG_OK && r.sp.arith != DG_ARITH_FP64) rc = dg_set_arithmetic(m, r.sp.arith);
   if (rc != DG_OK) {
+    if (m) dg_mesh_destroy(m);
     r.state = rc;
     return;
   }

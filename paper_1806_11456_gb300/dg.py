@@ -74,7 +74,7 @@ class SolveParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_cycles", ctypes.c_int32), ("fmg", ctypes.c_int32),
                 ("fmg_tol", ctypes.c_double), ("mg", MGParams), ("adapt", ctypes.c_int32),
                 ("n_stages", ctypes.c_int32), ("ap", AdaptParams), ("stage_orders", ctypes.c_int32 * 4),
-                ("ref_factor", ctypes.c_double), ("check_every", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("ref_factor", ctypes.c_double), ("check_every", ctypes.c_int32), ("arith", ctypes.c_int32)]
 
 
 _lib = None
@@ -164,7 +164,7 @@ def kernel_launches():
 
 
 def solve_params(tol=1e-10, max_cycles=200, fmg=False, fmg_tol=1e-1, mg=None, adapt=False, tau_max=1e-4, n_min=1,
-                 n_max=7, jump_rule=1, conform_tag=-1, cap=0, stages=(), ref_factor=0.1, check_every=1):
+                 n_max=7, jump_rule=1, conform_tag=-1, cap=0, stages=(), ref_factor=0.1, check_every=1, arith="fp64"):
     """dg_solve_params from keyword arguments (mg: dict of dg_mg_params fields)."""
     sp = SolveParams()
     sp.tol, sp.max_cycles, sp.fmg, sp.fmg_tol, sp.adapt = float(tol), int(max_cycles), int(bool(fmg)), \
@@ -182,6 +182,7 @@ def solve_params(tol=1e-10, max_cycles=200, fmg=False, fmg_tol=1e-1, mg=None, ad
     for i, v in enumerate(stages):
         sp.stage_orders[i] = int(v)
     sp.check_every = int(check_every)
+    sp.arith = ARITH[arith]
     return sp
 
 

@@ -117,3 +117,18 @@ def test_check_every_runs_whole_groups_of_cycles(dg):
     qb, _, rep5 = _alone(dg, m, o, p, q, s, check_every=5, **kw)
     assert rep1["cycles"] == rep5["cycles"] == 7  # the cap still bounds the phase
     assert np.array_equal(qa, qb)                 # same cycles, fewer residual checks
+
+
+def test_double_float_requests_equal_alone(dg):
+    reqs = _requests(3, 6)
+    kw = dict(tol=1e-30, max_cycles=3, mg=MG, arith="df32")
+    with dg.Server(hbm_budget=8 << 30, slots=3) as S:
+        ids = [S.submit(m, o, p, q0=q, s=s, **kw) for (m, o, p, q, s) in reqs]
+        S.wait()
+        for rid, (m, o, p, q, s) in zip(ids, reqs):
+            qs, _ = S.result(rid)
+            import torch
+            M = dg.Mesh(m, o, p).set_arithmetic("df32")
+            qd, _ = M.solve_steady(torch.tensor(q, device="cuda"), torch.tensor(s, device="cuda"),
+                                   tol=1e-30, max_cycles=3, mg=MG)
+            assert np.array_equal(qs, qd.cpu().numpy())
