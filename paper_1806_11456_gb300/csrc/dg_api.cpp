@@ -4,6 +4,7 @@
 #include <array>
 #include <cmath>
 #include <cstring>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -476,404 +477,455 @@ static void limit_jumps(const dg_mesh* m, std::vector<int32_t>& o, int rule, int
 
 using namespace dg;
 
+// A C++ exception never leaves the C ABI: a host allocation failure comes back
+// as DG_ENOMEM, anything else as DG_EINVAL with its message.
+template <class F>
+static int guarded(F&& f) {
+  try {
+    return f();
+  } catch (const std::bad_alloc&) {
+    set_error("out of host memory");
+    return DG_ENOMEM;
+  } catch (const std::exception& e) {
+    set_error(std::string("internal error: ") + e.what());
+    return DG_EINVAL;
+  }
+}
+
 extern "C" {
 
 const char* dg_last_error(void) { return g_err.c_str(); }
 
 int dg_kernel_launches(int64_t* count) {
-  if (!count) {
-    set_error("dg_kernel_launches: null argument");
-    return DG_EINVAL;
-  }
-  *count = (int64_t)launches_total();
-  return DG_OK;
+  return guarded([&]() -> int {
+    if (!count) {
+      set_error("dg_kernel_launches: null argument");
+      return DG_EINVAL;
+    }
+    *count = (int64_t)launches_total();
+    return DG_OK;
+  });
 }
 
 int dg_mesh_create(const dg_mesh_desc* desc, const int32_t* orders, dg_mesh** out) {
-  if (!out) {
-    set_error("null output");
-    return DG_EINVAL;
-  }
-  DG_TRY(check_desc(desc, orders));
-  DG_TRY(upload_tables());
-  dg_mesh* m = new (std::nothrow) dg_mesh();
-  if (!m) return DG_ENOMEM;
-  m->dim = desc->dim;
-  m->K = desc->K;
-  m->M = desc->M;
-  int Mp = desc->M + 1;
-  size_t npe = desc->dim == 3 ? (size_t)Mp * Mp * Mp : (size_t)Mp * Mp;
-  m->xmap.assign(desc->xmap, desc->xmap + (size_t)desc->K * npe * 3);
-  m->ftab.assign(desc->ftab, desc->ftab + (size_t)desc->K * 24);
-  m->prm = make_params(desc->params);
-  std::memcpy(m->raw_params, desc->params, sizeof(m->raw_params));
-  m->nslots = 1;
-  m->slot_prm.assign(1, m->prm);
-  m->slot_raw.assign(1, std::vector<double>(desc->params, desc->params + 16));
-  m->elem_slot.assign(desc->K, 0);
-  m->slot_elem_off = {0, desc->K};
-  m->orders.assign(orders, orders + (size_t)desc->K * 3);
-  m->fine.reset(new Level());
-  int rc = build_level(m, m->orders, m->fine.get());
-  if (rc == DG_OK) rc = upload_gas(m);
-  if (rc == DG_OK) {
-    cudaError_t e1 = cudaMalloc(&m->d_scalars, (6 * m->nslots + 16) * sizeof(double));
-    cudaError_t e2 = cudaMalloc(&m->d_tau, (size_t)m->K * 3 * kTauSlots * sizeof(double));
-    cudaError_t e3 = cudaMalloc(&m->d_orders, m->orders.size() * sizeof(int32_t));
-    if (e3 == cudaSuccess)
-      e3 = cudaMemcpy(m->d_orders, m->orders.data(), m->orders.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
-      set_error("cudaMalloc failed for mesh scalars");
-      rc = DG_ECUDA;
+  return guarded([&]() -> int {
+    if (!out) {
+      set_error("null output");
+      return DG_EINVAL;
     }
-  }
-  if (rc != DG_OK) {
-    dg_mesh_destroy(m);
-    return rc;
-  }
-  *out = m;
-  return DG_OK;
+    DG_TRY(check_desc(desc, orders));
+    DG_TRY(upload_tables());
+    dg_mesh* m = new (std::nothrow) dg_mesh();
+    if (!m) return DG_ENOMEM;
+    m->dim = desc->dim;
+    m->K = desc->K;
+    m->M = desc->M;
+    int Mp = desc->M + 1;
+    size_t npe = desc->dim == 3 ? (size_t)Mp * Mp * Mp : (size_t)Mp * Mp;
+    m->xmap.assign(desc->xmap, desc->xmap + (size_t)desc->K * npe * 3);
+    m->ftab.assign(desc->ftab, desc->ftab + (size_t)desc->K * 24);
+    m->prm = make_params(desc->params);
+    std::memcpy(m->raw_params, desc->params, sizeof(m->raw_params));
+    m->nslots = 1;
+    m->slot_prm.assign(1, m->prm);
+    m->slot_raw.assign(1, std::vector<double>(desc->params, desc->params + 16));
+    m->elem_slot.assign(desc->K, 0);
+    m->slot_elem_off = {0, desc->K};
+    m->orders.assign(orders, orders + (size_t)desc->K * 3);
+    m->fine.reset(new Level());
+    int rc = build_level(m, m->orders, m->fine.get());
+    if (rc == DG_OK) rc = upload_gas(m);
+    if (rc == DG_OK) {
+      cudaError_t e1 = cudaMalloc(&m->d_scalars, (6 * m->nslots + 16) * sizeof(double));
+      cudaError_t e2 = cudaMalloc(&m->d_tau, (size_t)m->K * 3 * kTauSlots * sizeof(double));
+      cudaError_t e3 = cudaMalloc(&m->d_orders, m->orders.size() * sizeof(int32_t));
+      if (e3 == cudaSuccess)
+        e3 = cudaMemcpy(m->d_orders, m->orders.data(), m->orders.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+      if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+        set_error("cudaMalloc failed for mesh scalars");
+        rc = DG_ECUDA;
+      }
+    }
+    if (rc != DG_OK) {
+      dg_mesh_destroy(m);
+      return rc;
+    }
+    *out = m;
+    return DG_OK;
+  });
 }
 
 int dg_batch_create(const dg_mesh_desc* descs, const int32_t* const* orders, int32_t nsolves, dg_mesh** out) {
-  if (!descs || !orders || !out || nsolves < 1) {
-    set_error("dg_batch_create: bad argument");
-    return DG_EINVAL;
-  }
-  for (int k = 0; k < nsolves; ++k) {
-    DG_TRY(check_desc(&descs[k], orders[k]));
-    if (descs[k].dim != descs[0].dim || descs[k].M != descs[0].M) {
-      set_error("dg_batch_create: all solves need the same dim and mapping order");
+  return guarded([&]() -> int {
+    if (!descs || !orders || !out || nsolves < 1) {
+      set_error("dg_batch_create: bad argument");
       return DG_EINVAL;
     }
-  }
-  DG_TRY(upload_tables());
-  dg_mesh* m = new (std::nothrow) dg_mesh();
-  if (!m) return DG_ENOMEM;
-  const int dim = descs[0].dim, Mp = descs[0].M + 1;
-  const size_t npe = dim == 3 ? (size_t)Mp * Mp * Mp : (size_t)Mp * Mp;
-  m->dim = dim;
-  m->M = descs[0].M;
-  m->nslots = nsolves;
-  m->slot_elem_off.assign(1, 0);
-  for (int k = 0; k < nsolves; ++k) {
-    const dg_mesh_desc& d = descs[k];
-    const int e0 = m->K;
-    m->xmap.insert(m->xmap.end(), d.xmap, d.xmap + (size_t)d.K * npe * 3);
-    for (int i = 0; i < d.K * 24; ++i) {
-      int32_t v = d.ftab[i];
-      if (i % 4 == 0 && v >= 0) v += e0;  // neighbour index into the batch
-      m->ftab.push_back(v);
+    for (int k = 0; k < nsolves; ++k) {
+      DG_TRY(check_desc(&descs[k], orders[k]));
+      if (descs[k].dim != descs[0].dim || descs[k].M != descs[0].M) {
+        set_error("dg_batch_create: all solves need the same dim and mapping order");
+        return DG_EINVAL;
+      }
     }
-    m->orders.insert(m->orders.end(), orders[k], orders[k] + (size_t)d.K * 3);
-    m->elem_slot.insert(m->elem_slot.end(), d.K, k);
-    m->slot_prm.push_back(make_params(d.params));
-    m->slot_raw.push_back(std::vector<double>(d.params, d.params + 16));
-    m->K += d.K;
-    m->slot_elem_off.push_back(m->K);
-  }
-  m->prm = m->slot_prm[0];
-  std::memcpy(m->raw_params, descs[0].params, sizeof(m->raw_params));
-  m->fine.reset(new Level());
-  int rc = build_level(m, m->orders, m->fine.get());
-  if (rc == DG_OK) rc = upload_gas(m);
-  if (rc == DG_OK) {
-    cudaError_t e1 = cudaMalloc(&m->d_scalars, (6 * m->nslots + 16) * sizeof(double));
-    cudaError_t e2 = cudaMalloc(&m->d_tau, (size_t)m->K * 3 * kTauSlots * sizeof(double));
-    cudaError_t e3 = cudaMalloc(&m->d_orders, m->orders.size() * sizeof(int32_t));
-    if (e3 == cudaSuccess)
-      e3 = cudaMemcpy(m->d_orders, m->orders.data(), m->orders.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
-      set_error("cudaMalloc failed for batch scalars");
-      rc = DG_ECUDA;
+    DG_TRY(upload_tables());
+    dg_mesh* m = new (std::nothrow) dg_mesh();
+    if (!m) return DG_ENOMEM;
+    const int dim = descs[0].dim, Mp = descs[0].M + 1;
+    const size_t npe = dim == 3 ? (size_t)Mp * Mp * Mp : (size_t)Mp * Mp;
+    m->dim = dim;
+    m->M = descs[0].M;
+    m->nslots = nsolves;
+    m->slot_elem_off.assign(1, 0);
+    for (int k = 0; k < nsolves; ++k) {
+      const dg_mesh_desc& d = descs[k];
+      const int e0 = m->K;
+      m->xmap.insert(m->xmap.end(), d.xmap, d.xmap + (size_t)d.K * npe * 3);
+      for (int i = 0; i < d.K * 24; ++i) {
+        int32_t v = d.ftab[i];
+        if (i % 4 == 0 && v >= 0) v += e0;  // neighbour index into the batch
+        m->ftab.push_back(v);
+      }
+      m->orders.insert(m->orders.end(), orders[k], orders[k] + (size_t)d.K * 3);
+      m->elem_slot.insert(m->elem_slot.end(), d.K, k);
+      m->slot_prm.push_back(make_params(d.params));
+      m->slot_raw.push_back(std::vector<double>(d.params, d.params + 16));
+      m->K += d.K;
+      m->slot_elem_off.push_back(m->K);
     }
-  }
-  if (rc != DG_OK) {
-    dg_mesh_destroy(m);
-    return rc;
-  }
-  *out = m;
-  return DG_OK;
+    m->prm = m->slot_prm[0];
+    std::memcpy(m->raw_params, descs[0].params, sizeof(m->raw_params));
+    m->fine.reset(new Level());
+    int rc = build_level(m, m->orders, m->fine.get());
+    if (rc == DG_OK) rc = upload_gas(m);
+    if (rc == DG_OK) {
+      cudaError_t e1 = cudaMalloc(&m->d_scalars, (6 * m->nslots + 16) * sizeof(double));
+      cudaError_t e2 = cudaMalloc(&m->d_tau, (size_t)m->K * 3 * kTauSlots * sizeof(double));
+      cudaError_t e3 = cudaMalloc(&m->d_orders, m->orders.size() * sizeof(int32_t));
+      if (e3 == cudaSuccess)
+        e3 = cudaMemcpy(m->d_orders, m->orders.data(), m->orders.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+      if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+        set_error("cudaMalloc failed for batch scalars");
+        rc = DG_ECUDA;
+      }
+    }
+    if (rc != DG_OK) {
+      dg_mesh_destroy(m);
+      return rc;
+    }
+    *out = m;
+    return DG_OK;
+  });
 }
 
 int dg_batch_info(const dg_mesh* m, int32_t* nsolves, int64_t* offs) {
-  if (!m) {
-    set_error("dg_batch_info: null mesh");
-    return DG_EINVAL;
-  }
-  if (nsolves) *nsolves = m->nslots;
-  if (offs)
-    for (int k = 0; k <= m->nslots; ++k) offs[k] = m->fine->off[m->slot_elem_off[k]];
-  return DG_OK;
+  return guarded([&]() -> int {
+    if (!m) {
+      set_error("dg_batch_info: null mesh");
+      return DG_EINVAL;
+    }
+    if (nsolves) *nsolves = m->nslots;
+    if (offs)
+      for (int k = 0; k <= m->nslots; ++k) offs[k] = m->fine->off[m->slot_elem_off[k]];
+    return DG_OK;
+  });
 }
 
 int dg_residual_norms(dg_mesh* m, const double* q, const double* s, double* norms, void* stream) {
-  if (!m || !q || !norms) {
-    set_error("dg_residual_norms: null argument");
-    return DG_EINVAL;
-  }
-  double mx = 0.0;
-  return level_norms(m, m->fine.get(), q, s, S(stream), norms, &mx);
+  return guarded([&]() -> int {
+    if (!m || !q || !norms) {
+      set_error("dg_residual_norms: null argument");
+      return DG_EINVAL;
+    }
+    double mx = 0.0;
+    return level_norms(m, m->fine.get(), q, s, S(stream), norms, &mx);
+  });
 }
 
 int dg_mesh_destroy(dg_mesh* m) {
-  if (!m) return DG_OK;
-  {
-    std::lock_guard<std::mutex> lock(device_sync_mutex());
-    for (auto& kv : m->graphs) cudaGraphExecDestroy(kv.second.exec);
-    if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
-    for (cudaStream_t t : m->tau_st)
-      if (t) cudaStreamDestroy(t);
-    if (m->d_scalars) cudaFree(m->d_scalars);
-    if (m->d_tau) cudaFree(m->d_tau);
-    if (m->d_orders) cudaFree(m->d_orders);
-    if (m->d_gas64) cudaFree(m->d_gas64);
-    if (m->d_gas32x2) cudaFree(m->d_gas32x2);
-    if (m->d_gasd) cudaFree(m->d_gasd);
-  }
-  delete m;  // the levels lock again while they free
-  return DG_OK;
+  return guarded([&]() -> int {
+    if (!m) return DG_OK;
+    {
+      std::lock_guard<std::mutex> lock(device_sync_mutex());
+      for (auto& kv : m->graphs) cudaGraphExecDestroy(kv.second.exec);
+      if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
+      for (cudaStream_t t : m->tau_st)
+        if (t) cudaStreamDestroy(t);
+      if (m->d_scalars) cudaFree(m->d_scalars);
+      if (m->d_tau) cudaFree(m->d_tau);
+      if (m->d_orders) cudaFree(m->d_orders);
+      if (m->d_gas64) cudaFree(m->d_gas64);
+      if (m->d_gas32x2) cudaFree(m->d_gas32x2);
+      if (m->d_gasd) cudaFree(m->d_gasd);
+    }
+    delete m;  // the levels lock again while they free
+    return DG_OK;
+  });
 }
 
 int dg_set_autotune(dg_mesh* m, int on, void* stream) {
-  if (!m) {
-    set_error("dg_set_autotune: null mesh");
-    return DG_EINVAL;
-  }
-  m->autotune = on != 0;
-  if (!m->autotune) return DG_OK;
-  {
-    std::lock_guard<std::mutex> lock(device_sync_mutex());
-    for (auto& kv : m->graphs) cudaGraphExecDestroy(kv.second.exec);  // they hold the old tile lists
-  }
-  m->graphs.clear();
-  cudaStream_t st = S(stream);
-  DG_TRY(tune_level(m, m->fine.get(), st));
-  for (auto& kv : m->levels) DG_TRY(tune_level(m, kv.second.get(), st));
-  return DG_OK;
+  return guarded([&]() -> int {
+    if (!m) {
+      set_error("dg_set_autotune: null mesh");
+      return DG_EINVAL;
+    }
+    m->autotune = on != 0;
+    if (!m->autotune) return DG_OK;
+    {
+      std::lock_guard<std::mutex> lock(device_sync_mutex());
+      for (auto& kv : m->graphs) cudaGraphExecDestroy(kv.second.exec);  // they hold the old tile lists
+    }
+    m->graphs.clear();
+    cudaStream_t st = S(stream);
+    DG_TRY(tune_level(m, m->fine.get(), st));
+    for (auto& kv : m->levels) DG_TRY(tune_level(m, kv.second.get(), st));
+    return DG_OK;
+  });
 }
 
 int dg_mesh_tuning(const dg_mesh* m, int32_t* out) {
-  if (!m || !out) {
-    set_error("dg_mesh_tuning: bad argument");
-    return DG_EINVAL;
-  }
-  out[0] = m->fine->pack;
-  for (int c = 0; c < kTileClasses; ++c) out[1 + c] = m->fine->class_threads[c];
-  return DG_OK;
+  return guarded([&]() -> int {
+    if (!m || !out) {
+      set_error("dg_mesh_tuning: bad argument");
+      return DG_EINVAL;
+    }
+    out[0] = m->fine->pack;
+    for (int c = 0; c < kTileClasses; ++c) out[1 + c] = m->fine->class_threads[c];
+    return DG_OK;
+  });
 }
 
 int dg_mesh_layout(const dg_mesh* m, int64_t* total_nodes, int64_t* elem_offsets) {
-  if (!m) {
-    set_error("null mesh");
-    return DG_EINVAL;
-  }
-  if (total_nodes) *total_nodes = m->fine->nodes;
-  if (elem_offsets)
-    for (int e = 0; e <= m->K; ++e) elem_offsets[e] = m->fine->off[e];
-  return DG_OK;
+  return guarded([&]() -> int {
+    if (!m) {
+      set_error("null mesh");
+      return DG_EINVAL;
+    }
+    if (total_nodes) *total_nodes = m->fine->nodes;
+    if (elem_offsets)
+      for (int e = 0; e <= m->K; ++e) elem_offsets[e] = m->fine->off[e];
+    return DG_OK;
+  });
 }
 
 int dg_set_arithmetic(dg_mesh* m, int mode) {
-  if (!m || (mode != DG_ARITH_FP64 && mode != DG_ARITH_DF32)) {
-    set_error("dg_set_arithmetic: bad argument");
-    return DG_EINVAL;
-  }
-  if (m->arith != mode) {
-    for (auto& kv : m->graphs) cudaGraphExecDestroy(kv.second.exec);
-    m->graphs.clear();
-  }
-  m->arith = mode;
-  return DG_OK;
+  return guarded([&]() -> int {
+    if (!m || (mode != DG_ARITH_FP64 && mode != DG_ARITH_DF32)) {
+      set_error("dg_set_arithmetic: bad argument");
+      return DG_EINVAL;
+    }
+    if (m->arith != mode) {
+      for (auto& kv : m->graphs) cudaGraphExecDestroy(kv.second.exec);
+      m->graphs.clear();
+    }
+    m->arith = mode;
+    return DG_OK;
+  });
 }
 
 int dg_mesh_orders(const dg_mesh* m, int32_t* out) {
-  if (!m || !out) {
-    set_error("dg_mesh_orders: null argument");
-    return DG_EINVAL;
-  }
-  std::memcpy(out, m->orders.data(), m->orders.size() * sizeof(int32_t));
-  return DG_OK;
+  return guarded([&]() -> int {
+    if (!m || !out) {
+      set_error("dg_mesh_orders: null argument");
+      return DG_EINVAL;
+    }
+    std::memcpy(out, m->orders.data(), m->orders.size() * sizeof(int32_t));
+    return DG_OK;
+  });
 }
 
 int dg_residual(dg_mesh* m, const double* q, const double* s, double* r, int flags, double* rnorm_host,
                 void* stream) {
-  if (!m || !q || !r || q == r) {
-    set_error("dg_residual: null or aliased arrays");
-    return DG_EINVAL;
-  }
-  if ((flags & DG_NORM) && !rnorm_host) {
-    set_error("dg_residual: DG_NORM needs rnorm_host");
-    return DG_EINVAL;
-  }
-  cudaStream_t st = S(stream);
-  bool iso = flags & DG_ISOLATED;
-  double* dnorm = nullptr;
-  if (flags & DG_NORM) {
-    dnorm = m->d_scalars + m->nslots;
-    DG_TRY(fill(dnorm, 0.0, m->nslots, st));
-  }
-  DG_TRY(residual(m, m->fine.get(), q, s, r, iso, st, iso ? nullptr : dnorm, -1, nullptr, nullptr));
-  if (flags & DG_NORM) {
-    if (iso) {
-      // norm of the isolated residual: reduce it with the tau reduction over one slot
-      set_error("DG_NORM with DG_ISOLATED is not supported");
+  return guarded([&]() -> int {
+    if (!m || !q || !r || q == r) {
+      set_error("dg_residual: null or aliased arrays");
       return DG_EINVAL;
     }
-    std::vector<double> h(m->nslots);
-    DG_CUDA_TRY(cudaMemcpyAsync(h.data(), dnorm, m->nslots * sizeof(double), cudaMemcpyDeviceToHost, st));
-    DG_CUDA_TRY(cudaStreamSynchronize(st));
-    double mx = 0.0;
-    for (double v : h) mx = (v != v) ? v : std::max(mx, v);
-    *rnorm_host = mx;
-  }
-  return DG_OK;
+    if ((flags & DG_NORM) && !rnorm_host) {
+      set_error("dg_residual: DG_NORM needs rnorm_host");
+      return DG_EINVAL;
+    }
+    cudaStream_t st = S(stream);
+    bool iso = flags & DG_ISOLATED;
+    double* dnorm = nullptr;
+    if (flags & DG_NORM) {
+      dnorm = m->d_scalars + m->nslots;
+      DG_TRY(fill(dnorm, 0.0, m->nslots, st));
+    }
+    DG_TRY(residual(m, m->fine.get(), q, s, r, iso, st, iso ? nullptr : dnorm, -1, nullptr, nullptr));
+    if (flags & DG_NORM) {
+      if (iso) {
+        // norm of the isolated residual: reduce it with the tau reduction over one slot
+        set_error("DG_NORM with DG_ISOLATED is not supported");
+        return DG_EINVAL;
+      }
+      std::vector<double> h(m->nslots);
+      DG_CUDA_TRY(cudaMemcpyAsync(h.data(), dnorm, m->nslots * sizeof(double), cudaMemcpyDeviceToHost, st));
+      DG_CUDA_TRY(cudaStreamSynchronize(st));
+      double mx = 0.0;
+      for (double v : h) mx = (v != v) ? v : std::max(mx, v);
+      *rnorm_host = mx;
+    }
+    return DG_OK;
+  });
 }
 
 int dg_cfl_dt(dg_mesh* m, const double* q, double* dt, void* stream) {
-  if (!m || !q || !dt) {
-    set_error("dg_cfl_dt: null argument");
-    return DG_EINVAL;
-  }
-  cudaStream_t st = S(stream);
-  DG_TRY(cfl_dt(m, m->fine.get(), q, m->d_scalars, st));
-  return read_scalar(m->d_scalars, dt, st);
+  return guarded([&]() -> int {
+    if (!m || !q || !dt) {
+      set_error("dg_cfl_dt: null argument");
+      return DG_EINVAL;
+    }
+    cudaStream_t st = S(stream);
+    DG_TRY(cfl_dt(m, m->fine.get(), q, m->d_scalars, st));
+    return read_scalar(m->d_scalars, dt, st);
+  });
 }
 
 int dg_smooth(dg_mesh* m, double* q, const double* s, int sweeps, void* stream) {
-  if (!m || !q || sweeps < 0) {
-    set_error("dg_smooth: bad argument");
-    return DG_EINVAL;
-  }
-  Cycle C{m, S(stream), dg_mg_params{}, {}, 0, 0.0};
-  return smooth_level(C, m->fine.get(), q, s, sweeps);
+  return guarded([&]() -> int {
+    if (!m || !q || sweeps < 0) {
+      set_error("dg_smooth: bad argument");
+      return DG_EINVAL;
+    }
+    Cycle C{m, S(stream), dg_mg_params{}, {}, 0, 0.0};
+    return smooth_level(C, m->fine.get(), q, s, sweeps);
+  });
 }
 
 int dg_pmg_vcycle(dg_mesh* m, double* q, const double* s, const dg_mg_params* mg, int want_norm,
                   dg_cycle_report* rep, void* stream) {
-  if (!m || !q || !mg || mg->beta1 < 0 || mg->beta2 < 0 || mg->beta_c < 0 || mg->coarsest < 1 ||
-      mg->direction < -1 || mg->direction >= m->dim || mg->control < 0 ||
-      (mg->control > 0 && (mg->beta1 < 1 || mg->beta2 < 1))) {
-    set_error("dg_pmg_vcycle: bad argument");
-    return DG_EINVAL;
-  }
-  cudaStream_t st = S(stream);
-  int evals = 0;
-  double dofs = 0.0;
-  int nlev = 0;
-  DG_TRY(run_vcycle(m, m->orders, q, s, *mg, st, &evals, &dofs, &nlev));
-  double rn = 0.0;
-  if (want_norm) DG_TRY(level_norm(m, m->fine.get(), q, s, st, &rn));
-  if (rep) {
-    rep->levels = nlev;
-    rep->residual_evals = evals;
-    rep->dof_evals = dofs;
-    rep->rnorm = rn;
-  }
-  return DG_OK;
+  return guarded([&]() -> int {
+    if (!m || !q || !mg || mg->beta1 < 0 || mg->beta2 < 0 || mg->beta_c < 0 || mg->coarsest < 1 ||
+        mg->direction < -1 || mg->direction >= m->dim || mg->control < 0 ||
+        (mg->control > 0 && (mg->beta1 < 1 || mg->beta2 < 1))) {
+      set_error("dg_pmg_vcycle: bad argument");
+      return DG_EINVAL;
+    }
+    cudaStream_t st = S(stream);
+    int evals = 0;
+    double dofs = 0.0;
+    int nlev = 0;
+    DG_TRY(run_vcycle(m, m->orders, q, s, *mg, st, &evals, &dofs, &nlev));
+    double rn = 0.0;
+    if (want_norm) DG_TRY(level_norm(m, m->fine.get(), q, s, st, &rn));
+    if (rep) {
+      rep->levels = nlev;
+      rep->residual_evals = evals;
+      rep->dof_evals = dofs;
+      rep->rnorm = rn;
+    }
+    return DG_OK;
+  });
 }
 
 int dg_tau_estimate(dg_mesh* m, const double* q, const double* s, int dir_mask, int with_correction, int isolated,
                     double* tau_host, void* stream) {
-  if (!m || !q || !tau_host) {
-    set_error("dg_tau_estimate: null argument");
-    return DG_EINVAL;
-  }
-  cudaStream_t st = S(stream);
-  Level* F = m->fine.get();
-  DG_TRY(ensure_work(F));
-  const size_t tsz = (size_t)m->K * 3 * kTauSlots;
-  DG_TRY(fill(m->d_tau, 0.0, (int64_t)tsz, st));
-  // R^P(q) at the reference orders
-  if (with_correction) DG_TRY(residual(m, F, q, s, F->d_R, isolated != 0, st, nullptr, -1, nullptr, nullptr));
-  const int32_t* d_fine_orders = m->d_orders;
-  // The directions are independent (their levels, buffers and table slots
-  // differ): each runs on its own stream, forked from and joined back to st.
-  cudaEvent_t ev_fork = nullptr, ev_join[3] = {nullptr, nullptr, nullptr};
-  DG_CUDA_TRY(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
-  DG_CUDA_TRY(cudaEventRecord(ev_fork, st));
-  int rc = DG_OK;
-  for (int i = 0; i < m->dim && rc == DG_OK; ++i) {
-    if (!((dir_mask >> i) & 1)) continue;
-    if (!m->tau_st[i] && cudaStreamCreateWithFlags(&m->tau_st[i], cudaStreamNonBlocking) != cudaSuccess) {
-      rc = DG_ECUDA;
-      break;
+  return guarded([&]() -> int {
+    if (!m || !q || !tau_host) {
+      set_error("dg_tau_estimate: null argument");
+      return DG_EINVAL;
     }
-    cudaStream_t sti = m->tau_st[i];
-    if (cudaStreamWaitEvent(sti, ev_fork, 0) != cudaSuccess) {
-      rc = DG_ECUDA;
-      break;
-    }
-    int top = 0;
-    for (int e = 0; e < m->K; ++e) top = std::max(top, (int)m->orders[e * 3 + i]);
-    Level* prev = F;
-    const double* Qp = q;
-    const double* Sp = s;
-    const double* Rp = with_correction ? F->d_R : nullptr;
-    for (int l = top - 1; l >= 1 && rc == DG_OK; --l) {
-      Level* Ll = get_level(m, capped(m->orders, m->dim, l, i));
-      if (!Ll) {
+    cudaStream_t st = S(stream);
+    Level* F = m->fine.get();
+    DG_TRY(ensure_work(F));
+    const size_t tsz = (size_t)m->K * 3 * kTauSlots;
+    DG_TRY(fill(m->d_tau, 0.0, (int64_t)tsz, st));
+    // R^P(q) at the reference orders
+    if (with_correction) DG_TRY(residual(m, F, q, s, F->d_R, isolated != 0, st, nullptr, -1, nullptr, nullptr));
+    const int32_t* d_fine_orders = m->d_orders;
+    // The directions are independent (their levels, buffers and table slots
+    // differ): each runs on its own stream, forked from and joined back to st.
+    cudaEvent_t ev_fork = nullptr, ev_join[3] = {nullptr, nullptr, nullptr};
+    DG_CUDA_TRY(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+    DG_CUDA_TRY(cudaEventRecord(ev_fork, st));
+    int rc = DG_OK;
+    for (int i = 0; i < m->dim && rc == DG_OK; ++i) {
+      if (!((dir_mask >> i) & 1)) continue;
+      if (!m->tau_st[i] && cudaStreamCreateWithFlags(&m->tau_st[i], cudaStreamNonBlocking) != cudaSuccess) {
         rc = DG_ECUDA;
         break;
       }
-      if ((rc = ensure_work(Ll)) != DG_OK) break;
-      if ((rc = transfer(m, prev, Ll, 5, Qp, Ll->d_Q, sti)) != DG_OK) break;
-      if (s && (rc = transfer(m, prev, Ll, 5, Sp, Ll->d_S, sti)) != DG_OK) break;
-      if (Rp && (rc = transfer(m, prev, Ll, 5, Rp, Ll->d_G, sti)) != DG_OK) break;
-      rc = tau_accumulate(m, Ll, Ll->d_Q, s ? Ll->d_S : nullptr, Rp ? Ll->d_G : nullptr, isolated != 0, i, l,
-                          d_fine_orders, m->d_tau, sti);
-      prev = Ll;
-      Qp = Ll->d_Q;
-      Sp = Ll->d_S;
-      Rp = Rp ? Ll->d_G : nullptr;
-    }
-    if (cudaEventCreateWithFlags(&ev_join[i], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventRecord(ev_join[i], sti) != cudaSuccess || cudaStreamWaitEvent(st, ev_join[i], 0) != cudaSuccess)
-      rc = DG_ECUDA;
-  }
-  cudaEventDestroy(ev_fork);
-  for (cudaEvent_t e : ev_join)
-    if (e) cudaEventDestroy(e);
-  if (rc == DG_OK) {
-    cudaError_t e = cudaMemcpyAsync(tau_host, m->d_tau, tsz * sizeof(double), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) {
-      set_error(std::string("tau copy: ") + cudaGetErrorString(e));
-      rc = DG_ECUDA;
-    }
-  }
-  if (rc != DG_OK) return rc;
-  for (int e = 0; e < m->K; ++e)
-    for (int i = 0; i < 3; ++i)
-      for (int N = 0; N < kTauSlots; ++N) {
-        bool measured = i < m->dim && ((dir_mask >> i) & 1) && N >= 1 && N < m->orders[e * 3 + i];
-        if (!measured) tau_host[((size_t)e * 3 + i) * kTauSlots + N] = -1.0;
+      cudaStream_t sti = m->tau_st[i];
+      if (cudaStreamWaitEvent(sti, ev_fork, 0) != cudaSuccess) {
+        rc = DG_ECUDA;
+        break;
       }
-  return DG_OK;
+      int top = 0;
+      for (int e = 0; e < m->K; ++e) top = std::max(top, (int)m->orders[e * 3 + i]);
+      Level* prev = F;
+      const double* Qp = q;
+      const double* Sp = s;
+      const double* Rp = with_correction ? F->d_R : nullptr;
+      for (int l = top - 1; l >= 1 && rc == DG_OK; --l) {
+        Level* Ll = get_level(m, capped(m->orders, m->dim, l, i));
+        if (!Ll) {
+          rc = DG_ECUDA;
+          break;
+        }
+        if ((rc = ensure_work(Ll)) != DG_OK) break;
+        if ((rc = transfer(m, prev, Ll, 5, Qp, Ll->d_Q, sti)) != DG_OK) break;
+        if (s && (rc = transfer(m, prev, Ll, 5, Sp, Ll->d_S, sti)) != DG_OK) break;
+        if (Rp && (rc = transfer(m, prev, Ll, 5, Rp, Ll->d_G, sti)) != DG_OK) break;
+        rc = tau_accumulate(m, Ll, Ll->d_Q, s ? Ll->d_S : nullptr, Rp ? Ll->d_G : nullptr, isolated != 0, i, l,
+                            d_fine_orders, m->d_tau, sti);
+        prev = Ll;
+        Qp = Ll->d_Q;
+        Sp = Ll->d_S;
+        Rp = Rp ? Ll->d_G : nullptr;
+      }
+      if (cudaEventCreateWithFlags(&ev_join[i], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventRecord(ev_join[i], sti) != cudaSuccess || cudaStreamWaitEvent(st, ev_join[i], 0) != cudaSuccess)
+        rc = DG_ECUDA;
+    }
+    cudaEventDestroy(ev_fork);
+    for (cudaEvent_t e : ev_join)
+      if (e) cudaEventDestroy(e);
+    if (rc == DG_OK) {
+      cudaError_t e = cudaMemcpyAsync(tau_host, m->d_tau, tsz * sizeof(double), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) {
+        set_error(std::string("tau copy: ") + cudaGetErrorString(e));
+        rc = DG_ECUDA;
+      }
+    }
+    if (rc != DG_OK) return rc;
+    for (int e = 0; e < m->K; ++e)
+      for (int i = 0; i < 3; ++i)
+        for (int N = 0; N < kTauSlots; ++N) {
+          bool measured = i < m->dim && ((dir_mask >> i) & 1) && N >= 1 && N < m->orders[e * 3 + i];
+          if (!measured) tau_host[((size_t)e * 3 + i) * kTauSlots + N] = -1.0;
+        }
+    return DG_OK;
+  });
 }
 
 int dg_adapt(const dg_mesh* m, const double* tau_host, const dg_adapt_params* ap, int32_t* new_orders) {
-  if (!m || !tau_host || !ap || !new_orders || ap->n_min < 1 || ap->n_max > kNMax || ap->n_min > ap->n_max ||
-      ap->n_max >= kTauSlots) {
-    set_error("dg_adapt: bad argument");
-    return DG_EINVAL;
-  }
-  std::vector<int32_t> o((size_t)m->K * 3, 0);
-  for (int e = 0; e < m->K; ++e)
-    select_element(tau_host + (size_t)e * 3 * kTauSlots, &m->orders[e * 3], *ap, m->dim, &o[e * 3]);
-  if (ap->jump_rule == 1 || ap->jump_rule == 2 || ap->conform_tag >= 0)
-    limit_jumps(m, o, ap->jump_rule, ap->conform_tag);
-  std::memcpy(new_orders, o.data(), o.size() * sizeof(int32_t));
-  return DG_OK;
+  return guarded([&]() -> int {
+    if (!m || !tau_host || !ap || !new_orders || ap->n_min < 1 || ap->n_max > kNMax || ap->n_min > ap->n_max ||
+        ap->n_max >= kTauSlots) {
+      set_error("dg_adapt: bad argument");
+      return DG_EINVAL;
+    }
+    std::vector<int32_t> o((size_t)m->K * 3, 0);
+    for (int e = 0; e < m->K; ++e)
+      select_element(tau_host + (size_t)e * 3 * kTauSlots, &m->orders[e * 3], *ap, m->dim, &o[e * 3]);
+    if (ap->jump_rule == 1 || ap->jump_rule == 2 || ap->conform_tag >= 0)
+      limit_jumps(m, o, ap->jump_rule, ap->conform_tag);
+    std::memcpy(new_orders, o.data(), o.size() * sizeof(int32_t));
+    return DG_OK;
+  });
 }
 
 int dg_profile_residual(dg_mesh* m, const double* q, const double* s, double* r, int iters, double* ms_out,
                         void* stream) {
-  if (!m || !q || !r || !ms_out || iters < 1 || q == r) {
-    set_error("dg_profile_residual: bad argument");
-    return DG_EINVAL;
-  }
-  return profile_residual(m, m->fine.get(), q, s, r, iters, ms_out, S(stream));
+  return guarded([&]() -> int {
+    if (!m || !q || !r || !ms_out || iters < 1 || q == r) {
+      set_error("dg_profile_residual: bad argument");
+      return DG_EINVAL;
+    }
+    return profile_residual(m, m->fine.get(), q, s, r, iters, ms_out, S(stream));
+  });
 }
 
 // Cycle (Q, Sv) with top orders `o` until max|r| < target or `cap` cycles;
@@ -906,144 +958,150 @@ static int cycle_until(dg_mesh* m, const std::vector<int32_t>& o, Level* L, doub
 
 int dg_solve_steady(dg_mesh** meshp, double** qp, const double* s, const dg_solve_params* sp, dg_alloc_fn alloc,
                     void* alloc_ctx, dg_solve_report* rep, void* stream) {
-  if (!meshp || !*meshp || !qp || !*qp || !sp || !rep || sp->max_cycles < 0 || !(sp->tol > 0.0) ||
-      (sp->adapt && (!alloc || s)) || (sp->fmg && !(sp->fmg_tol > 0.0))) {
-    set_error("dg_solve_steady: bad argument (adaptation needs alloc and s == NULL)");
-    return DG_EINVAL;
-  }
-  std::memset(rep, 0, sizeof(*rep));
-  dg_mesh* m = *meshp;
-  if (sp->adapt && m->nslots > 1) {
-    set_error("dg_solve_steady: adaptation of a batch is not supported (adapt each solve)");
-    return DG_EINVAL;
-  }
-  double* q = *qp;
-  cudaStream_t st = S(stream);
-  dg_mg_params mg = sp->mg;
-  int rc = DG_OK;
-  double rn = 0.0;
-  // ---- full multigrid ramp (Sec. 3.1.1) ----
-  if (sp->fmg) {
-    int top = 0;
-    for (int e = 0; e < m->K; ++e)
-      for (int d = 0; d < m->dim; ++d) top = std::max(top, (int)m->orders[e * 3 + d]);
-    Level* prev = nullptr;
-    for (int l = 1; l < top; ++l) {
-      std::vector<int32_t> o = capped(m->orders, m->dim, l, -1);
-      Level* L = get_level(m, o);
-      if (!L) return DG_ECUDA;
-      DG_TRY(ensure_work(L));
-      if (!prev)
-        DG_TRY(transfer(m, m->fine.get(), L, 5, q, L->d_Q, st));  // initial state, L2-projected down
-      else
-        DG_TRY(transfer(m, prev, L, 5, prev->d_Q, L->d_Q, st));   // interpolated up
-      if (s) DG_TRY(transfer(m, m->fine.get(), L, 5, s, L->d_S, st));
-      int cyc = 0;
-      rc = cycle_until(m, o, L, L->d_Q, s ? L->d_S : nullptr, mg, sp->fmg_tol, sp->max_cycles, st, &cyc,
-                       &rep->dof_evals, &rn, sp->check_every);
-      rep->cycles += cyc;
-      rep->fmg_cycles += cyc;
-      if (rc == DG_EDIVERGED) break;
-      rc = DG_OK;  // a FMG level that stalls still hands its state up
-      prev = L;
+  return guarded([&]() -> int {
+    if (!meshp || !*meshp || !qp || !*qp || !sp || !rep || sp->max_cycles < 0 || !(sp->tol > 0.0) ||
+        (sp->adapt && (!alloc || s)) || (sp->fmg && !(sp->fmg_tol > 0.0))) {
+      set_error("dg_solve_steady: bad argument (adaptation needs alloc and s == NULL)");
+      return DG_EINVAL;
     }
-    if (rc == DG_OK && prev) DG_TRY(transfer(m, prev, m->fine.get(), 5, prev->d_Q, q, st));
-  }
-  // ---- reference orders ----
-  if (rc == DG_OK) {
-    const double ref = sp->ref_factor > 0.0 ? sp->ref_factor : 0.1;
-    double target = sp->adapt ? sp->ap.tau_max * ref : sp->tol;
-    int cyc = 0;
-    rc = cycle_until(m, m->orders, m->fine.get(), q, s, mg, target, sp->max_cycles, st, &cyc, &rep->dof_evals, &rn, sp->check_every);
-    rep->cycles += cyc;
-  }
-  // ---- adaptation (Sec. 3.3.2), possibly in stages (Sec. 3.3.4) ----
-  if (rc == DG_OK && sp->adapt) {
-    const int nst = std::max(1, (int)sp->n_stages);
-    for (int stage = 0; stage < nst && rc == DG_OK; ++stage) {
-      if (stage > 0) {  // every stage starts from a state converged to tau_max/10
+    std::memset(rep, 0, sizeof(*rep));
+    dg_mesh* m = *meshp;
+    if (sp->adapt && m->nslots > 1) {
+      set_error("dg_solve_steady: adaptation of a batch is not supported (adapt each solve)");
+      return DG_EINVAL;
+    }
+    double* q = *qp;
+    cudaStream_t st = S(stream);
+    dg_mg_params mg = sp->mg;
+    int rc = DG_OK;
+    double rn = 0.0;
+    // ---- full multigrid ramp (Sec. 3.1.1) ----
+    if (sp->fmg) {
+      int top = 0;
+      for (int e = 0; e < m->K; ++e)
+        for (int d = 0; d < m->dim; ++d) top = std::max(top, (int)m->orders[e * 3 + d]);
+      Level* prev = nullptr;
+      for (int l = 1; l < top; ++l) {
+        std::vector<int32_t> o = capped(m->orders, m->dim, l, -1);
+        Level* L = get_level(m, o);
+        if (!L) return DG_ECUDA;
+        DG_TRY(ensure_work(L));
+        if (!prev)
+          DG_TRY(transfer(m, m->fine.get(), L, 5, q, L->d_Q, st));  // initial state, L2-projected down
+        else
+          DG_TRY(transfer(m, prev, L, 5, prev->d_Q, L->d_Q, st));   // interpolated up
+        if (s) DG_TRY(transfer(m, m->fine.get(), L, 5, s, L->d_S, st));
         int cyc = 0;
-        const double ref = sp->ref_factor > 0.0 ? sp->ref_factor : 0.1;
-        rc = cycle_until(m, m->orders, m->fine.get(), q, nullptr, mg, sp->ap.tau_max * ref, sp->max_cycles, st,
-                         &cyc, &rep->dof_evals, &rn, sp->check_every);
+        rc = cycle_until(m, o, L, L->d_Q, s ? L->d_S : nullptr, mg, sp->fmg_tol, sp->max_cycles, st, &cyc,
+                         &rep->dof_evals, &rn, sp->check_every);
         rep->cycles += cyc;
-        if (rc != DG_OK) break;
+        rep->fmg_cycles += cyc;
+        if (rc == DG_EDIVERGED) break;
+        rc = DG_OK;  // a FMG level that stalls still hands its state up
+        prev = L;
       }
-      rep->rnorm_adapt = rn;
-      std::vector<double> tau((size_t)m->K * 3 * kTauSlots);
-      DG_TRY(dg_tau_estimate(m, q, nullptr, (1 << m->dim) - 1, 1, 1, tau.data(), stream));
-      dg_adapt_params ap = sp->ap;
-      bool last = true;
-      if (sp->n_stages > 0) {
-        ap.cap = sp->stage_orders[stage];
-        dg_adapt_params un = sp->ap;
-        un.cap = 0;
-        std::vector<int32_t> free_orders(m->orders.size());
-        DG_TRY(dg_adapt(m, tau.data(), &un, free_orders.data()));
-        int need = 0;
-        for (int32_t v : free_orders) need = std::max(need, (int)v);
-        last = (stage == nst - 1) || need <= ap.cap;
-      }
-      std::vector<int32_t> no(m->orders.size());
-      DG_TRY(dg_adapt(m, tau.data(), &ap, no.data()));
-      if (no != m->orders) {
-        dg_mesh_desc d;
-        d.dim = m->dim;
-        d.K = m->K;
-        d.M = m->M;
-        d.xmap = m->xmap.data();
-        d.ftab = m->ftab.data();
-        std::memcpy(d.params, m->raw_params, sizeof(d.params));
-        dg_mesh* nm = nullptr;
-        DG_TRY(dg_mesh_create(&d, no.data(), &nm));
-        nm->arith = m->arith;
-        double* nq = (double*)alloc((size_t)5 * nm->fine->nodes * sizeof(double), alloc_ctx);
-        if (!nq) {
-          dg_mesh_destroy(nm);
-          set_error("dg_solve_steady: allocator returned NULL");
-          return DG_ENOMEM;
-        }
-        rc = transfer(m, m->fine.get(), nm->fine.get(), 5, q, nq, st);
-        if (rc != DG_OK) {
-          dg_mesh_destroy(nm);
-          return rc;
-        }
-        DG_CUDA_TRY(cudaStreamSynchronize(st));
-        dg_mesh_destroy(m);
-        m = nm;
-        q = nq;
-        *meshp = m;
-        *qp = q;
-        rep->adapted += 1;
-      }
-      if (last) break;
+      if (rc == DG_OK && prev) DG_TRY(transfer(m, prev, m->fine.get(), 5, prev->d_Q, q, st));
     }
+    // ---- reference orders ----
     if (rc == DG_OK) {
+      const double ref = sp->ref_factor > 0.0 ? sp->ref_factor : 0.1;
+      double target = sp->adapt ? sp->ap.tau_max * ref : sp->tol;
       int cyc = 0;
-      rc = cycle_until(m, m->orders, m->fine.get(), q, nullptr, mg, sp->tol, sp->max_cycles, st, &cyc,
-                       &rep->dof_evals, &rn, sp->check_every);
+      rc = cycle_until(m, m->orders, m->fine.get(), q, s, mg, target, sp->max_cycles, st, &cyc, &rep->dof_evals, &rn, sp->check_every);
       rep->cycles += cyc;
     }
-  }
-  rep->rnorm = rn;
-  rep->status = rc;
-  rep->nodes = m->fine->nodes;
-  if (rc != DG_OK) set_error(rc == DG_EDIVERGED ? "dg_solve_steady: residual diverged"
-                                                : "dg_solve_steady: cycle cap reached before the tolerance");
-  return rc;
+    // ---- adaptation (Sec. 3.3.2), possibly in stages (Sec. 3.3.4) ----
+    if (rc == DG_OK && sp->adapt) {
+      const int nst = std::max(1, (int)sp->n_stages);
+      for (int stage = 0; stage < nst && rc == DG_OK; ++stage) {
+        if (stage > 0) {  // every stage starts from a state converged to tau_max/10
+          int cyc = 0;
+          const double ref = sp->ref_factor > 0.0 ? sp->ref_factor : 0.1;
+          rc = cycle_until(m, m->orders, m->fine.get(), q, nullptr, mg, sp->ap.tau_max * ref, sp->max_cycles, st,
+                           &cyc, &rep->dof_evals, &rn, sp->check_every);
+          rep->cycles += cyc;
+          if (rc != DG_OK) break;
+        }
+        rep->rnorm_adapt = rn;
+        std::vector<double> tau((size_t)m->K * 3 * kTauSlots);
+        DG_TRY(dg_tau_estimate(m, q, nullptr, (1 << m->dim) - 1, 1, 1, tau.data(), stream));
+        dg_adapt_params ap = sp->ap;
+        bool last = true;
+        if (sp->n_stages > 0) {
+          ap.cap = sp->stage_orders[stage];
+          dg_adapt_params un = sp->ap;
+          un.cap = 0;
+          std::vector<int32_t> free_orders(m->orders.size());
+          DG_TRY(dg_adapt(m, tau.data(), &un, free_orders.data()));
+          int need = 0;
+          for (int32_t v : free_orders) need = std::max(need, (int)v);
+          last = (stage == nst - 1) || need <= ap.cap;
+        }
+        std::vector<int32_t> no(m->orders.size());
+        DG_TRY(dg_adapt(m, tau.data(), &ap, no.data()));
+        if (no != m->orders) {
+          dg_mesh_desc d;
+          d.dim = m->dim;
+          d.K = m->K;
+          d.M = m->M;
+          d.xmap = m->xmap.data();
+          d.ftab = m->ftab.data();
+          std::memcpy(d.params, m->raw_params, sizeof(d.params));
+          dg_mesh* nm = nullptr;
+          DG_TRY(dg_mesh_create(&d, no.data(), &nm));
+          nm->arith = m->arith;
+          double* nq = (double*)alloc((size_t)5 * nm->fine->nodes * sizeof(double), alloc_ctx);
+          if (!nq) {
+            dg_mesh_destroy(nm);
+            set_error("dg_solve_steady: allocator returned NULL");
+            return DG_ENOMEM;
+          }
+          rc = transfer(m, m->fine.get(), nm->fine.get(), 5, q, nq, st);
+          if (rc != DG_OK) {
+            dg_mesh_destroy(nm);
+            return rc;
+          }
+          DG_CUDA_TRY(cudaStreamSynchronize(st));
+          dg_mesh_destroy(m);
+          m = nm;
+          q = nq;
+          *meshp = m;
+          *qp = q;
+          rep->adapted += 1;
+        }
+        if (last) break;
+      }
+      if (rc == DG_OK) {
+        int cyc = 0;
+        rc = cycle_until(m, m->orders, m->fine.get(), q, nullptr, mg, sp->tol, sp->max_cycles, st, &cyc,
+                         &rep->dof_evals, &rn, sp->check_every);
+        rep->cycles += cyc;
+      }
+    }
+    rep->rnorm = rn;
+    rep->status = rc;
+    rep->nodes = m->fine->nodes;
+    if (rc != DG_OK) set_error(rc == DG_EDIVERGED ? "dg_solve_steady: residual diverged"
+                                                  : "dg_solve_steady: cycle cap reached before the tolerance");
+    return rc;
+  });
 }
 
 int dg_transfer_noalloc(int32_t dim, int32_t K, const int32_t* orders_from, const int32_t* orders_to,
                         int32_t nvar, const double* in, double* out, void* stream) {
-  return transfer_noalloc(dim, K, orders_from, orders_to, nvar, in, out, S(stream));
+  return guarded([&]() -> int {
+    return transfer_noalloc(dim, K, orders_from, orders_to, nvar, in, out, S(stream));
+  });
 }
 
 int dg_transfer_state(const dg_mesh* from, const double* q_from, const dg_mesh* to, double* q_to, void* stream) {
-  if (!from || !to || !q_from || !q_to || from->K != to->K || from->dim != to->dim) {
-    set_error("dg_transfer_state: meshes do not match");
-    return DG_EINVAL;
-  }
-  return transfer(from, from->fine.get(), to->fine.get(), 5, q_from, q_to, S(stream));
+  return guarded([&]() -> int {
+    if (!from || !to || !q_from || !q_to || from->K != to->K || from->dim != to->dim) {
+      set_error("dg_transfer_state: meshes do not match");
+      return DG_EINVAL;
+    }
+    return transfer(from, from->fine.get(), to->fine.get(), 5, q_from, q_to, S(stream));
+  });
 }
 
 }  // extern "C"
