@@ -372,7 +372,9 @@ int dg_profile_residual(dg_mesh* mesh, const double* q, const double* s, double*
  * (dg_solve_footprint) fits in what the running solves leave of the budget;
  * it then runs dg_solve_steady with its own parameters and keeps its
  * hierarchy resident until it finishes.  Requests share no device data, so a
- * solve gives bit for bit the same result alone and among others.
+ * solve gives bit for bit the same result alone and among others.  Not part
+ * of the paper: serving many steady solves is this library's addition
+ * around the solver of Sec. 3.
  */
 typedef struct dg_server dg_server;
 
@@ -440,7 +442,8 @@ int dg_server_destroy(dg_server* srv);
  * residual (the other tile kernels see the same tiles); the fastest is kept.  Levels that exist are tuned now
  * (synchronises the stream; captured V-cycle graphs are dropped), later ones
  * when they are built.  Results do not change: every node's arithmetic is
- * the same whatever CTA computes it.  on = 0 keeps the current tiles.
+ * the same whatever CTA computes it.  on = 0 keeps the current tiles.  Not
+ * part of the paper (a choice of GPU work decomposition).
  */
 int dg_set_autotune(dg_mesh* mesh, int on, void* stream);
 
