@@ -147,8 +147,21 @@ void free_all(AllocCtx& a) {
   a.ptrs.clear();
 }
 
-// Runs one request on stream st; fills r's results.
-void run_request(Request& r, cudaStream_t st) {
+// What a finished request hands back; the worker publishes it under the
+// server lock in one step, so a waiter that sees a finished state also sees
+// the result, the report and the timings that go with it.
+struct Outcome {
+  int state = DG_EINVAL;
+  dg_solve_report rep{};
+  std::vector<double> q;
+  std::vector<int32_t> orders;
+  int64_t dev_bytes = 0;
+};
+
+// Runs one request on stream st.  Reads the request's inputs only (they do
+// not change after submission); everything it produces goes to the outcome.
+Outcome run_request(const Request& r, cudaStream_t st) {
+  Outcome out;
   AllocCtx ac;
   dg_mesh* m = nullptr;
   dg_mesh_desc d;
@@ -162,8 +175,8 @@ void run_request(Request& r, cudaStream_t st) {
   if (rc == DG_OK && r.sp.arith != DG_ARITH_FP64) rc = dg_set_arithmetic(m, r.sp.arith);
   if (rc != DG_OK) {
     if (m) dg_mesh_destroy(m);
-    r.state = rc;
-    return;
+    out.state = rc;
+    return out;
   }
   int64_t nodes = 0;
   dg_mesh_layout(m, &nodes, nullptr);
@@ -172,36 +185,39 @@ void run_request(Request& r, cudaStream_t st) {
   double* s = nullptr;
   if (!r.s.empty()) s = static_cast<double*>(alloc_cb(n5 * sizeof(double), &ac));
   if (!q || (!r.s.empty() && !s)) {
-    r.state = DG_ENOMEM;
+    out.state = DG_ENOMEM;
     dg_mesh_destroy(m);
     free_all(ac);
-    return;
+    return out;
   }
-  if (r.q0.empty()) {  // freestream of the parameters, element-blocked
+  std::vector<double> fs;  // freestream of the parameters, element-blocked
+  const double* q0 = r.q0.data();
+  if (r.q0.empty()) {
     std::vector<int64_t> off(r.K + 1);
     dg_mesh_layout(m, &nodes, off.data());
-    r.q0.resize(n5);
+    fs.resize(n5);
     for (int e = 0; e < r.K; ++e) {
       const int64_t nn = off[e + 1] - off[e];
       for (int v = 0; v < 5; ++v)
-        for (int64_t i = 0; i < nn; ++i) r.q0[5 * off[e] + v * nn + i] = r.params[7 + v];
+        for (int64_t i = 0; i < nn; ++i) fs[5 * off[e] + v * nn + i] = r.params[7 + v];
     }
+    q0 = fs.data();
   }
-  cudaMemcpyAsync(q, r.q0.data(), n5 * sizeof(double), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(q, q0, n5 * sizeof(double), cudaMemcpyHostToDevice, st);
   if (s) cudaMemcpyAsync(s, r.s.data(), n5 * sizeof(double), cudaMemcpyHostToDevice, st);
   double* qf = q;
-  rc = dg_solve_steady(&m, &qf, s, &r.sp, alloc_cb, &ac, &r.rep, st);
-  r.state = rc;
+  out.state = dg_solve_steady(&m, &qf, s, &r.sp, alloc_cb, &ac, &out.rep, st);
   int64_t fn = 0;
   dg_mesh_layout(m, &fn, nullptr);
-  r.q.resize((size_t)5 * fn);
-  cudaMemcpyAsync(r.q.data(), qf, r.q.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
-  r.orders_out.resize((size_t)r.K * 3);
-  dg_mesh_orders(m, r.orders_out.data());
+  out.q.resize((size_t)5 * fn);
+  cudaMemcpyAsync(out.q.data(), qf, out.q.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+  out.orders.resize((size_t)r.K * 3);
+  dg_mesh_orders(m, out.orders.data());
   cudaStreamSynchronize(st);
-  r.dev_bytes = dg::mesh_device_bytes(m) + ac.bytes;
+  out.dev_bytes = dg::mesh_device_bytes(m) + ac.bytes;
   dg_mesh_destroy(m);
   free_all(ac);
+  return out;
 }
 
 void worker(dg_server* S) {
@@ -222,14 +238,21 @@ void worker(dg_server* S) {
       r->state = DG_REQ_RUNNING;
       r->t_start = seconds_since(S->t0);
     }
+    Outcome out;
     try {
-      run_request(*r, st);
+      out = run_request(*r, st);
     } catch (const std::exception&) {  // host allocation failure: the request fails, the server lives
-      r->state = DG_ENOMEM;
+      out = Outcome();
+      out.state = DG_ENOMEM;
     }
     {
       std::lock_guard<std::mutex> lk(S->mu);
       S->used -= r->est;
+      r->rep = out.rep;
+      r->q.swap(out.q);
+      r->orders_out.swap(out.orders);
+      r->dev_bytes = out.dev_bytes;
+      r->state = out.state;
       r->t_end = seconds_since(S->t0);
       r->q0.clear();
       r->q0.shrink_to_fit();
