@@ -102,12 +102,15 @@ def volume_flops_per_node(dim, n, affine):
     """Algorithmic FP64 flops per node of the volume kernel (FMA = 2): BR1
     gradient contraction per direction 27 n (general metrics: 3 metric
     products + 12 FMA per point) or 8 n + 24 (affine element: 4 FMA per point,
-    then the 12-term metric product once), lifting 54 per direction, gradient
-    face traces 48 per direction, nodal viscous + advective contravariant
-    fluxes 68 per direction, divergence 10 n per direction, primitives,
-    viscosity and scalings 34."""
+    then the 12-term metric product once); lifting of U* per direction 54
+    (general: two faces, 3 metric products + 12 FMA each) or 16 (affine: the
+    two faces' U* join the contraction, 4 FMA each); gradient face traces 48
+    per direction; nodal viscous + advective contravariant fluxes 68 per
+    direction; divergence 10 n per direction; primitives, viscosity and
+    scalings 34."""
     grad = (8 * n + 24) if affine else 27 * n
-    return 34 + dim * (grad + 10 * n + 54 + 48 + 68)
+    lift = 16 if affine else 54
+    return 34 + dim * (grad + 10 * n + lift + 48 + 68)
 
 
 class ClockSampler:

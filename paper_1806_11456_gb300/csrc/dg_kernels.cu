@@ -814,8 +814,18 @@ DEV void stage_tile(const LevelArgsT<R>& A, const ElemTile& t, int nn, int T, co
 // Volume part of the gradient at node i of the tile: sum_d D^d (Ja^d U).
 // AFFINE: the metrics are constant in the element, so Ja^d is factored out
 // of the contraction (same value, 4 instead of 15 operations per point).
-template <typename R, int DIM, bool AFFINE>
-DEV void gradient_volume(const R* sD, const R* sA, int T, int nn, int i, int n0, int n1, int n2, R* g) {
+// LIFT (affine elements only): the surface part of the BR1 gradient joins the
+// same per-direction sum.  On an affine element the outward face metric of
+// faces 2d and 2d+1 is -Ja^d and +Ja^d (the face value of a constant field),
+// so the lifted U* of those two faces (weights l(-1)/w and l(+1)/w) is added
+// to the contraction before the one metric product: 8 FMA per direction
+// instead of 30 operations.  ust: U* at the element's face nodes (4
+// variables, stride fn), fo_e: the element's six face offsets.
+template <typename R, int DIM, bool AFFINE, bool LIFT = false>
+DEV void gradient_volume(const R* sD, const R* sA, int T, int nn, int i, int n0, int n1, int n2, R* g,
+                         const typename Store<R>::T* __restrict__ ust = nullptr, const int32_t* fo_e = nullptr,
+                         int64_t fn = 0) {
+  static_assert(AFFINE || !LIFT, "the folded lifting needs constant metrics");
   const int le = i / nn, node = i - le * nn;
   const int idx0 = node % n0, idx1 = (node / n0) % n1, idx2 = node / (n0 * n1);
 #pragma unroll
@@ -833,6 +843,17 @@ DEV void gradient_volume(const R* sD, const R* sA, int T, int nn, int i, int n0,
         const R c = Drow[a];
 #pragma unroll
         for (int v = 0; v < 4; ++v) cu[v] = madd(cu[v], c, sA[v * T + la]);
+      }
+      if (LIFT) {
+        const int ta = (d == 0) ? 1 : 0, tb = (d == 2) ? 1 : 2;  // face_dirs of faces 2d, 2d+1
+        const int fp = pick(tb, idx0, idx1, idx2) * pick(ta, n0, n1, n2) + pick(ta, idx0, idx1, idx2);
+        const int64_t pm = fo_e[2 * d] + fp, pp = fo_e[2 * d + 1] + fp;
+        const R wm = -Tab<R>::lmw(nd, id), wp = Tab<R>::lpw(nd, id);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          cu[v] = madd(cu[v], wm, Store<R>::get(ust, v * fn + pm));
+          cu[v] = madd(cu[v], wp, Store<R>::get(ust, v * fn + pp));
+        }
       }
       const R j0 = sA[(4 + d * 3 + 0) * T + i], j1 = sA[(4 + d * 3 + 1) * T + i], j2 = sA[(4 + d * 3 + 2) * T + i];
 #pragma unroll
@@ -941,24 +962,30 @@ __global__ void __launch_bounds__(kVolThreads) __maxnreg__(DIM == 2 ? 96 : 104) 
   // ---- gradient: volume part + lifting of U*, times 1/J ----
   for (int i = threadIdx.x; i < T; i += blockDim.x) {
     R g[12];
-    gradient_volume<R, DIM, AFFINE>(sD, sA, T, nn, i, n0, n1, n2, g);
     const int le = i / nn, node = i - le * nn;
     const int e = A.tile_elems[t.first + le];
-    const int idx0 = node % n0, idx1 = (node / n0) % n1, idx2 = node / (n0 * n1);
+    if (AFFINE) {
+      gradient_volume<R, DIM, true, true>(sD, sA, T, nn, i, n0, n1, n2, g, ust, A.fo + e * 6, A.fn);
+    } else {
+      gradient_volume<R, DIM, false>(sD, sA, T, nn, i, n0, n1, n2, g);
+      // lifting of U* n S from every face (curved metrics: per face node)
+      const int idx0 = node % n0, idx1 = (node / n0) % n1, idx2 = node / (n0 * n1);
 #pragma unroll
-    for (int f = 0; f < 2 * DIM; ++f) {
-      int d, ta, tb, side;
-      face_dirs(f, d, ta, tb, side);
-      const int nd = pick(d, n0, n1, n2), id = pick(d, idx0, idx1, idx2);
-      const R lw = side ? Tab<R>::lpw(nd, id) : Tab<R>::lmw(nd, id);
-      const int64_t p = A.fo[e * 6 + f] + pick(tb, idx0, idx1, idx2) * pick(ta, n0, n1, n2) + pick(ta, idx0, idx1, idx2);
-      const R m0 = lw * SR::get(A.fnS, p), m1 = lw * SR::get(A.fnS, A.fn + p), m2 = lw * SR::get(A.fnS, 2 * A.fn + p);
+      for (int f = 0; f < 2 * DIM; ++f) {
+        int d, ta, tb, side;
+        face_dirs(f, d, ta, tb, side);
+        const int nd = pick(d, n0, n1, n2), id = pick(d, idx0, idx1, idx2);
+        const R lw = side ? Tab<R>::lpw(nd, id) : Tab<R>::lmw(nd, id);
+        const int64_t p =
+            A.fo[e * 6 + f] + pick(tb, idx0, idx1, idx2) * pick(ta, n0, n1, n2) + pick(ta, idx0, idx1, idx2);
+        const R m0 = lw * SR::get(A.fnS, p), m1 = lw * SR::get(A.fnS, A.fn + p), m2 = lw * SR::get(A.fnS, 2 * A.fn + p);
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const R us = SR::get(ust, v * A.fn + p);
-        g[v * 3 + 0] = madd(g[v * 3 + 0], m0, us);
-        g[v * 3 + 1] = madd(g[v * 3 + 1], m1, us);
-        g[v * 3 + 2] = madd(g[v * 3 + 2], m2, us);
+        for (int v = 0; v < 4; ++v) {
+          const R us = SR::get(ust, v * A.fn + p);
+          g[v * 3 + 0] = madd(g[v * 3 + 0], m0, us);
+          g[v * 3 + 1] = madd(g[v * 3 + 1], m1, us);
+          g[v * 3 + 2] = madd(g[v * 3 + 2], m2, us);
+        }
       }
     }
     const R iJ = SR::get(A.geo, 9 * A.nodes + A.off[e] + node);

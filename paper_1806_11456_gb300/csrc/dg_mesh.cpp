@@ -394,6 +394,28 @@ Level::~Level() {
 // otherwise), ordered by launch class: tiles of <= 128 nodes, <= 256, larger.
 // Replaces any earlier lists of the level (graphs captured with them must be
 // dropped by the caller).
+// SMs of the current device (1 if it cannot be queried)
+static int sm_count() {
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+    return 1;
+  return nsm;
+}
+
+// Element tiles that build_tiles makes with the given packing (whole
+// elements of one order triple per tile, pack / nodes-per-element of them)
+static int64_t count_tiles(const std::vector<int32_t>& nvec, int K, int pack) {
+  std::map<std::array<int, 3>, int64_t> groups;
+  for (int e = 0; e < K; ++e) groups[{nvec[e * 3], nvec[e * 3 + 1], nvec[e * 3 + 2]}]++;
+  int64_t tiles = 0;
+  for (const auto& kv : groups) {
+    const int per = std::max(1, pack / (kv.first[0] * kv.first[1] * kv.first[2]));
+    tiles += (kv.second + per - 1) / per;
+  }
+  return tiles;
+}
+
 int build_tiles(Level* L, int pack) {
   const int K = L->K;
   const std::vector<int32_t>& nvec = L->nvec_host;
@@ -612,16 +634,17 @@ int build_level(const dg_mesh* m, const std::vector<int32_t>& orders, Level* L) 
   mnS.assign((size_t)3 * mnodes, 0.0);
   for (int64_t p = 0; p < mnodes; ++p)
     for (int c = 0; c < 3; ++c) mnS[(size_t)c * mnodes + p] = mgeo[p][c];
-  // mortar tiles: whole mortars, at most kMortarTile nodes each; every
-  // mortar records where its face nodes start among the tile's outputs
-  std::vector<MortarTile> mtiles;
-  {
+  // mortar tiles: whole mortars, at most `target` nodes each (a larger
+  // mortar forms its own tile); every mortar records where its face nodes
+  // start among the tile's outputs
+  auto pack_mortars = [&](int target) {
+    std::vector<MortarTile> tiles;
     MortarTile cur{0, 0, 0, 0, 0};
     for (int i = 0; i < (int)mortars.size(); ++i) {
       MortarDev& M = mortars[i];
       int sz = M.ma * M.mb;
-      if (cur.count > 0 && cur.nodes + sz > kMortarTile) {
-        mtiles.push_back(cur);
+      if (cur.count > 0 && cur.nodes + sz > target) {
+        tiles.push_back(cur);
         cur = MortarTile{i, 0, M.node_off, 0, 0};
       }
       if (cur.count == 0) {
@@ -640,7 +663,29 @@ int build_level(const dg_mesh* m, const std::vector<int32_t>& orders, Level* L) 
       cur.nodes += sz;
       cur.outs += outs;
     }
-    if (cur.count > 0) mtiles.push_back(cur);
+    if (cur.count > 0) tiles.push_back(cur);
+    return tiles;
+  };
+  // The mortar kernels run one thread per mortar node and are latency bound
+  // on small levels, where their time follows the most loaded SM.  Half-size
+  // tiles are taken when they lower that load (nodes of the fullest tile x
+  // tiles per SM, rounded up) by a tenth or more and all of them are resident
+  // at once (8 CTAs per SM: the mortar kernels' launch bounds).
+  std::vector<MortarTile> mtiles = pack_mortars(kMortarTile / 2);
+  {
+    const int64_t nsm = sm_count();
+    auto load = [&](const std::vector<MortarTile>& t) {
+      int64_t mx = 0;
+      for (const MortarTile& x : t) mx = std::max<int64_t>(mx, x.nodes);
+      return ((int64_t)t.size() + nsm - 1) / nsm * mx;
+    };
+    const int64_t half_load = load(mtiles);
+    const bool fits = (int64_t)mtiles.size() <= 8 * nsm;
+    std::vector<MortarTile> full = pack_mortars(kMortarTile);  // (also restores the full tiles' out_off)
+    if (fits && 10 * half_load <= 9 * load(full))
+      mtiles = pack_mortars(kMortarTile / 2);
+    else
+      mtiles = std::move(full);
   }
   L->n_mtiles = (int)mtiles.size();
   // ---- upload ----
@@ -655,7 +700,14 @@ int build_level(const dg_mesh* m, const std::vector<int32_t>& orders, Level* L) 
   DG_TRY(dev_upload(&L->bytes, &L->d_mnS, mnS));
   DG_TRY(dev_upload(&L->bytes, &L->d_mtiles, mtiles));
   DG_TRY(dev_upload(&L->bytes, &L->d_slot, m->elem_slot));
-  DG_TRY(build_tiles(L, kTileNodes));
+  // Element tiles: kTileNodes nodes each, halved (down to a quarter) while
+  // the level has fewer tiles than SMs.  The element kernels run one thread
+  // per node and an SM's FP64 pipe serialises its tiles' arithmetic, so a
+  // coarse level (N = 1: 32 elements per 128-node tile) packed at full size
+  // would leave most SMs idle.
+  int pack = kTileNodes;
+  while (pack > kTileNodes / 4 && count_tiles(nvec, K, pack) < sm_count()) pack /= 2;
+  DG_TRY(build_tiles(L, pack));
   DG_TRY(dev_zeros(&L->bytes, &L->d_trq, (size_t)5 * acc));
   DG_TRY(dev_zeros(&L->bytes, &L->d_ust, (size_t)4 * acc));
   DG_TRY(dev_zeros(&L->bytes, &L->d_trg, (size_t)12 * acc));

@@ -70,12 +70,25 @@ def main():
     else:
         qd = torch.tensor(q, device="cuda")
     r = torch.empty_like(qd)
-    for _ in range(args.warmup + args.iters):
+
+    def one():
         if args.vcycles:
             M.vcycle(qd, None, beta1=3, beta2=3, beta_c=10, graph=True)
         else:
             M.residual(qd, None, r=r)
+
+    for _ in range(args.warmup):
+        one()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.iters):
+        one()
+    e1.record()
+    torch.cuda.synchronize()
+    what = "V-cycle" if args.vcycles else "residual"
+    print(f"{args.workload} {args.arith}: {e0.elapsed_time(e1) / max(args.iters, 1):.4f} ms per {what} "
+          f"(mean of {args.iters}, CUDA events, after {args.warmup} warm-up)")
 
 
 if __name__ == "__main__":
