@@ -706,7 +706,8 @@ int build_level(const dg_mesh* m, const std::vector<int32_t>& orders, Level* L) 
   // coarse level (N = 1: 32 elements per 128-node tile) packed at full size
   // would leave most SMs idle.
   int pack = kTileNodes;
-  while (pack > kTileNodes / 4 && count_tiles(nvec, K, pack) < sm_count()) pack /= 2;
+  const int64_t nsm_tiles = sm_count();
+  while (pack > kTileNodes / 4 && count_tiles(nvec, K, pack) < nsm_tiles) pack /= 2;
   DG_TRY(build_tiles(L, pack));
   DG_TRY(dev_zeros(&L->bytes, &L->d_trq, (size_t)5 * acc));
   DG_TRY(dev_zeros(&L->bytes, &L->d_ust, (size_t)4 * acc));
