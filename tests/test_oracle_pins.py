@@ -359,6 +359,36 @@ def test_viscous_divergence_zero_for_linear_velocity():
 
 
 # ---------------------------------------------------------------------------
+# Pseudo-time step (Sec. 2): C_a h / ((|v| + c) N^2) and C_nu h^2 / (nu N^4)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("re", [1e4, 2.0])
+def test_cfl_time_step_on_a_sheared_box(re):
+    """On an affine sheared box the length h_d = 2/|grad xi^d| is the distance
+    between the element's two faces of direction d: dx/sqrt(1 + s^2) for the
+    faces x - s y = const, dy for the faces y = const.  With a uniform free
+    stream (|v| = 1, c = 1/M, T = 1 so mu = 1 and nu = 1/Re) the step is the
+    smaller of the two limits over both directions; high Re makes the
+    convective limit bind, low Re the viscous one.  Different spacings and
+    orders per direction make a transposed metric or a swapped order fail."""
+    Lx, Ly, nx, ny, shear = 1.5, 1.0, 3, 2, 0.5
+    mesh = syn.periodic_box(nx, ny, 1, L=(Lx, Ly, 1.0), dim=2)
+    xmap = np.array(mesh["xmap"], dtype=float)
+    xmap[..., 0] += shear * xmap[..., 1]
+    mesh = dict(mesh, xmap=xmap)
+    orders = np.tile(np.array([[3, 5, 0]], dtype=np.int32), (mesh["K"], 1))
+    mach = 0.3
+    prm = syn.flow_params(mach=mach, re=re)
+    q = syn.freestream_state(mesh, orders, prm)
+    h = [(Lx / nx) / math.sqrt(1.0 + shear * shear), Ly / ny]
+    ca, cnu, c, nu = prm[5], prm[6], 1.0 / mach, 1.0 / re
+    want = min(min(ca * hd / ((1.0 + c) * N * N), cnu * hd * hd / (nu * N ** 4)) for hd, N in zip(h, (3, 5)))
+    got = orc.cfl_dt(mesh, orders, prm, q)
+    assert abs(got - want) <= 1e-12 * want
+    conv = min(ca * hd / ((1.0 + c) * N * N) for hd, N in zip(h, (3, 5)))
+    assert (want == conv) == (re > 100)  # the intended limit binds
+
+
+# ---------------------------------------------------------------------------
 # RK3 smoother (Sec. 3.1, Williamson)
 # ---------------------------------------------------------------------------
 def test_rk3_stability_polynomial():
