@@ -88,6 +88,10 @@ def test_restriction_is_l2_projection_and_exact_on_low_degree():
     vc = syn.to_blocked(np.tile(fc, (5, 1)), N, 3)
     got = orc.transfer(3, P, N, vf)
     assert np.max(np.abs(got - vc)) < 1e-12
+    # prolongation is interpolation: the same polynomial given at the coarse
+    # nodes reappears at the fine nodes
+    up = orc.transfer(3, N, P, vc)
+    assert np.max(np.abs(up - vf)) < 1e-12
     # L2 property: the projection error is orthogonal to the coarse space --
     # restricting the prolongation of the restriction changes nothing
     v = rng.normal(size=orc.nodes_total(P, 3) * 5)
