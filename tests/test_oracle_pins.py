@@ -205,6 +205,27 @@ def test_free_stream_preservation(name, isolated):
     assert np.max(np.abs(r)) <= tol * _scale(mesh, orders, prm)
 
 
+@pytest.mark.parametrize("dim,tag", [(2, syn.BC_WALL), (3, syn.BC_WALL), (2, syn.BC_SLIP), (3, syn.BC_SLIP)])
+def test_gas_at_rest_in_a_closed_box(dim, tag):
+    """A gas at rest with uniform pressure and temperature is an exact steady
+    solution in a box closed by no-slip adiabatic or free-slip walls, so the
+    residual vanishes to roundoff; a wrong sign of the wall pressure flux, a
+    ghost velocity that is not mirrored, or a heat flux through an adiabatic
+    wall would leave a truncation-level residual at the wall."""
+    ys = [0.0, 0.3, 1.0]
+    zs = [0.0, 0.6, 1.0] if dim == 3 else None
+    bc = dict(xmin=tag, xmax=tag, ymin=tag, ymax=tag, zmin=tag, zmax=tag)
+    mesh = syn.box_mesh([0.0, 0.5, 0.8, 1.2], ys, zs, bc=bc)
+    orders = syn.random_orders(mesh["K"], dim, 1, 5, 17)
+    prm = syn.flow_params(mach=0.3, re=100.0)
+    p = 1.0 / (prm[0] * prm[2] ** 2)
+    nn, off = syn.layout_offsets(orders, dim)
+    rest = np.array([1.0, 0.0, 0.0, 0.0, p / (prm[0] - 1.0)])
+    q = syn.to_blocked(np.tile(rest[:, None], (1, off[-1])), orders, dim)
+    r = orc.residual(mesh, orders, prm, q)
+    assert np.max(np.abs(r)) <= 1e-13 * _scale(mesh, orders, prm)
+
+
 @pytest.mark.parametrize("name", ["periodic3d_mixed", "rotated3d_mixed"])
 def test_discrete_conservation(name):
     mesh, dim, lo, hi = MESHES[name]()
