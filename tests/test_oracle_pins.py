@@ -249,6 +249,37 @@ def test_discrete_conservation(name):
     assert mag.max() > 1e-3
 
 
+@pytest.mark.parametrize("dim,tag", [(2, syn.BC_WALL), (3, syn.BC_WALL), (2, syn.BC_SLIP), (3, syn.BC_SLIP)])
+def test_closed_box_conserves_mass_and_energy(dim, tag):
+    """Nothing crosses a no-slip adiabatic wall or a free-slip wall: no mass
+    (zero normal velocity), no work and no heat (zero wall velocity or no
+    viscous flux, zero heat flux).  So in a box closed by either, the total
+    mass and energy of any state are conserved by the discrete operator,
+    sum over nodes of w J r = 0 for rho and rho E, while momentum is not (the
+    walls push).  A heat flux or a viscous work term at an adiabatic wall, or
+    a ghost state that lets mass through, breaks it."""
+    ys = [0.0, 0.3, 1.0]
+    zs = [0.0, 0.6, 1.0] if dim == 3 else None
+    bc = dict(xmin=tag, xmax=tag, ymin=tag, ymax=tag, zmin=tag, zmax=tag)
+    mesh = syn.box_mesh([0.0, 0.5, 0.8, 1.2], ys, zs, bc=bc)
+    orders = syn.random_orders(mesh["K"], dim, 1, 5, 19)
+    prm = syn.flow_params(mach=0.3, re=100.0)
+    q = syn.perturbed_state(mesh, orders, prm, 4, amp=0.05)
+    r = orc.residual(mesh, orders, prm, q)
+    _, J = orc.geometry(mesh, orders)
+    nn, off = syn.layout_offsets(orders, dim)
+    tot, mag = np.zeros(5), np.zeros(5)
+    for e in range(mesh["K"]):
+        n = orders[e] + 1
+        w = [np.polynomial.legendre.leggauss(int(k))[1] for k in n]
+        W = np.einsum("k,j,i->kji", w[2], w[1], w[0]).reshape(-1)
+        blk = r[5 * off[e]:5 * off[e + 1]].reshape(5, -1) * W * J[off[e]:off[e + 1]]
+        tot += blk.sum(1)
+        mag += np.abs(blk).sum(1)
+    assert abs(tot[0]) <= 1e-13 * mag.max() and abs(tot[4]) <= 1e-13 * mag.max()
+    assert np.max(np.abs(tot[1:1 + dim])) > 1e-6 * mag.max()  # the walls do push
+
+
 def test_spectral_convergence_manufactured():
     mesh = syn.periodic_box(4, 4, 1)
     prm = syn.flow_params(mach=0.3, re=100.0)
