@@ -527,6 +527,38 @@ def test_tau_vanishes_for_free_stream_and_for_fields_constant_along_direction():
     assert np.max(t[:, 0][t[:, 0] >= 0]) > 1e-4   # the x-direction does see it
 
 
+@pytest.mark.parametrize("dim,P,n", [(2, 7, (4, 5)), (2, 7, (3, 3)), (3, 5, (3, 4, 3))])
+def test_tau_splits_into_directional_parts(dim, P, n):
+    """Sec. 3.2.1, the decoupled anisotropic estimate: the truncation error of
+    an anisotropic reduction P -> n is approximately the sum of the
+    directional errors, each reducing one direction alone (here mapped to the
+    n grid).  The remainder is a cross term
+    of the directional errors and is far smaller than either part on a smooth
+    field.  Each part carries a share of the total, so a dropped direction, a
+    wrong restriction or a sign error in the correction term fails."""
+    mesh = syn.periodic_box(2, 2, 2 if dim == 3 else 1, dim=dim)
+    K = mesh["K"]
+    Po = np.tile(np.array([[P, P, P if dim == 3 else 0]], dtype=np.int32), (K, 1))
+    prm = syn.flow_params(mach=0.3, re=100.0)
+    q = syn.smooth_state(mesh, Po, prm, 9, amp=0.05, wavelength=1.0)
+    rP = orc.residual(mesh, Po, prm, q, None, True)
+
+    def tau_at(o):  # R^n(I q) - I R^P(q), isolated operator
+        return orc.residual(mesh, o, prm, orc.transfer(dim, Po, o, q), None, True) - orc.transfer(dim, Po, o, rP)
+
+    On = Po.copy()
+    On[:, :dim] = n
+    full = tau_at(On)
+    parts = []
+    for i in range(dim):
+        Oi = Po.copy()
+        Oi[:, i] = n[i]
+        parts.append(orc.transfer(dim, Oi, On, tau_at(Oi)))
+    scale = np.max(np.abs(full))
+    assert all(np.max(np.abs(p)) > 0.1 * scale for p in parts)
+    assert np.max(np.abs(full - sum(parts))) < 1e-2 * scale
+
+
 def test_tau_decays_spectrally_along_direction():
     mesh = syn.periodic_box(6, 6, 1, dim=2)
     orders = syn.uniform_orders(mesh["K"], 2, 8)
