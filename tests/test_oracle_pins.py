@@ -135,6 +135,32 @@ def test_roe_consistency_and_antisymmetry():
         assert np.allclose(f1, -f2, rtol=1e-13, atol=1e-12)
 
 
+def test_roe_is_the_upwind_flux_when_every_wave_moves_one_way():
+    """Roe's linearisation satisfies A(qR - qL) = F(qR) - F(qL) exactly, so
+    when all five eigenvalues u_n - c, u_n, u_n + c of the averaged state are
+    positive, |A| = A and the flux is F(qL); all negative, F(qR).  Arbitrary
+    supersonic states with different densities, velocities and pressures make
+    a wrong average (arithmetic instead of sqrt(rho)-weighted, or a wrong
+    enthalpy) miss it by O(jump)."""
+    prm = syn.flow_params(mach=0.3)
+    g, M = prm[0], prm[2]
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        t = np.cross(n, rng.normal(size=3))
+        states = []
+        for _side in range(2):
+            rho = rng.uniform(0.6, 1.6)
+            p = rng.uniform(0.7, 1.4) / (g * M * M)
+            c = np.sqrt(g * p / rho)
+            u = rng.uniform(1.6, 2.5) * c * n + rng.uniform(-1, 1) * t  # |u_n| > 1.6 c on both sides
+            states.append(np.array([rho, *(rho * u), p / (g - 1) + 0.5 * rho * u @ u]))
+        qL, qR = states
+        assert np.allclose(orc.roe(prm, qL, qR, n), orc.adv_flux(prm, qL, n), rtol=1e-12, atol=1e-10)
+        assert np.allclose(orc.roe(prm, qL, qR, -n), orc.adv_flux(prm, qR, -n), rtol=1e-12, atol=1e-10)
+
+
 def test_roe_exact_for_single_shear_and_contact_jump():
     # a pure contact (density jump, same u_n and p) moving right: upwinding
     # picks the left state's flux exactly
