@@ -67,6 +67,26 @@ def test_server_results_equal_alone(dg):
             S.release(rid)
 
 
+def test_a_finished_request_carries_its_result(dg):
+    """Waiting on one request and reading it at once, while other slots are
+    still running, sees the whole outcome: a finished state comes with its
+    end time, report and result (they are published together)."""
+    reqs = _requests(7, 1)
+    kw = dict(tol=1e-30, max_cycles=3, fmg=True, fmg_tol=1e-30, mg=MG)
+    with dg.Server(hbm_budget=8 << 30, slots=4) as S:
+        ids = [S.submit(m, o, p, q0=q, s=s, **kw) for (m, o, p, q, s) in reqs]
+        for rid, (m, o, p, q, s) in zip(ids, reqs):
+            S.wait(rid)
+            info = S.info(rid)
+            assert info["state"] == -5
+            assert 0.0 <= info["t_submit"] <= info["t_start"] <= info["t_end"] and info["t_end"] > 0.0
+            assert info["rep"]["cycles"] > 0 and info["rep"]["nodes"] == q.size // 5
+            qs, os_ = S.result(rid)
+            assert qs.size == q.size and np.any(qs != 0.0)
+            assert np.array_equal(os_, o)
+            S.release(rid)
+
+
 def test_server_adaptation_equals_alone(dg):
     mesh = syn.periodic_box(3, 2, 1, dim=2)
     prm = syn.flow_params(mach=0.3, re=100.0)
