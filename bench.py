@@ -592,6 +592,39 @@ def cpu_baseline_sample(mesh, prm, orders, q, budget_s=15.0):
             "sample": f"{n} oracle residual evaluations of the full workload, single thread"}
 
 
+def cpu_baseline_all_cores(budget_s=8.0, timeout_s=120.0):
+    """The same oracle sample run as one independent single-thread process per
+    host core, all started together: the host's aggregate DOF/s with every
+    core busy (memory bandwidth shared as it would be).  The oracle itself is
+    unchanged.  None if any process fails or outlives timeout_s (it is then
+    killed)."""
+    try:
+        ncores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        ncores = os.cpu_count() or 1
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; m, p, o, q = bench.workload(); "
+            "print(json.dumps(bench.cpu_baseline_sample(m, p, o, q, budget_s=%r)))" % (ROOT, budget_s))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1")
+    procs = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                              text=True, env=env) for _ in range(ncores)]
+    deadline = time.monotonic() + timeout_s
+    vals, evals = [], 0
+    for pr in procs:
+        try:
+            out, _ = pr.communicate(timeout=max(1.0, deadline - time.monotonic()))
+            res = json.loads(out.strip().splitlines()[-1])
+            vals.append(float(res["value"]))
+            evals += int(res["sample"].split()[0])
+        except Exception:
+            pr.kill()
+            pr.wait()
+    if len(vals) != ncores:
+        return None
+    return {"value": sum(vals), "unit": "DOF/s", "cores": ncores, "kind": "oracle",
+            "sample": f"{ncores} concurrent single-thread oracle processes, {evals} residual evaluations of the "
+                      f"full workload in all, about {budget_s:g} s each"}
+
+
 # ---------------------------------------------------------------------------
 # GB300 arm
 # ---------------------------------------------------------------------------
@@ -750,6 +783,11 @@ def run_gb300(args, rank, world):
         if args.mg_compare > 0:
             out["mg_compare"] = mg_compare(dg, torch, dev, args.mg_compare)
         out["cpu_baseline"] = cpu_baseline_sample(mesh, prm, orders, q_np) if world == 1 else None
+        if world == 1:
+            try:
+                out["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores()
+            except (OSError, ValueError) as exc:  # no process could be started: report why
+                out["cpu_baseline"]["all_cores"] = {"unavailable": str(exc)[:200]}
         print(json.dumps(out))
 
 
