@@ -252,6 +252,52 @@ def test_gas_at_rest_in_a_closed_box(dim, tag):
     assert np.max(np.abs(r)) <= 1e-13 * _scale(mesh, orders, prm)
 
 
+def _rotation(axis, angle):
+    k = np.asarray(axis, float) / np.linalg.norm(axis)
+    Kx = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+    return np.eye(3) + math.sin(angle) * Kx + (1 - math.cos(angle)) * Kx @ Kx  # Rodrigues
+
+
+@pytest.mark.parametrize("case", ["periodic3d", "bounded2d"])
+def test_residual_is_rotation_covariant(case):
+    """The Navier-Stokes operator has no preferred direction: rotating the
+    mesh, the momentum of the state, the source and the far-field state by
+    one rotation rotates the momentum residual and leaves mass and energy
+    unchanged.  The rotated elements are no longer axis-aligned, so every
+    metric cross term, every off-diagonal stress and the boundary ghosts on
+    oblique walls enter; an index slip in any of them breaks the covariance."""
+    if case == "periodic3d":
+        mesh, dim = syn.periodic_box(2, 2, 2), 3
+        Rm = _rotation([0.3, -0.7, 0.5], 0.9)
+    else:
+        bc = dict(xmin=syn.BC_FREESTREAM, xmax=syn.BC_OUTFLOW, ymax=syn.BC_FREESTREAM,
+                  ymin=lambda i, k: syn.BC_SLIP if i == 0 else syn.BC_WALL)
+        mesh, dim = syn.box_mesh(np.linspace(-0.2, 1, 4), [0, 0.05, 0.2, 0.5], bc=bc), 2
+        Rm = _rotation([0, 0, 1], 0.7)
+    orders = syn.random_orders(mesh["K"], dim, 1, 5 if dim == 2 else 4, 29)
+    prm = syn.flow_params(mach=0.3, re=100.0)
+    q = syn.perturbed_state(mesh, orders, prm, 5, amp=0.05)
+    s = syn.random_source(mesh, orders, 6, amp=1e-3)
+    _, off = syn.layout_offsets(orders, dim)
+
+    def rot(v):
+        v = v.copy()
+        for e in range(mesh["K"]):
+            blk = v[5 * off[e]:5 * off[e + 1]].reshape(5, -1)
+            blk[1:4] = Rm @ blk[1:4]
+        return v
+
+    r = orc.residual(mesh, orders, prm, q, s)
+    prm2 = prm.copy()
+    prm2[8:11] = Rm @ prm[8:11]
+    mesh2 = dict(mesh, xmap=np.array(mesh["xmap"], float) @ Rm.T)
+    r2 = orc.residual(mesh2, orders, prm2, rot(q), rot(s))
+    assert np.max(np.abs(r2 - rot(r))) <= 1e-13 * np.max(np.abs(r))
+    # the state matters: the unrotated state on the rotated mesh is far off
+    r3 = orc.residual(mesh2, orders, prm2, q, s)
+    assert np.max(np.abs(r3 - rot(r))) > 1e-3 * np.max(np.abs(r))
+
+
 @pytest.mark.parametrize("name", ["periodic3d_mixed", "rotated3d_mixed"])
 def test_discrete_conservation(name):
     mesh, dim, lo, hi = MESHES[name]()
