@@ -74,6 +74,16 @@ def _cases():
         o = syn.random_orders(mesh["K"], 3, 1, 4, 14)
         return mesh, o, prm, syn.perturbed_state(mesh, o, prm, 9)
     c["curved_sphere_mortars"] = sphere
+    def tilted():  # affine but not axis-aligned: every metric component nonzero
+        mesh = syn.periodic_box(3, 2, 2)
+        k = np.array([0.3, -0.7, 0.5]) / np.linalg.norm([0.3, -0.7, 0.5])
+        Kx = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+        Rm = np.eye(3) + np.sin(0.9) * Kx + (1 - np.cos(0.9)) * Kx @ Kx
+        mesh = dict(mesh, xmap=np.array(mesh["xmap"], float) @ Rm.T)
+        prm = syn.flow_params(mach=0.3, re=100.0)
+        o = syn.random_orders(mesh["K"], 3, 1, 5, 15)
+        return mesh, o, prm, syn.perturbed_state(mesh, o, prm, 10)
+    c["tilted_affine_mortars"] = tilted
     return c
 
 
