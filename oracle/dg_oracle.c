@@ -19,8 +19,11 @@
  *     factorisation, no strong-form rewrite.
  *   - Roe advective flux and Bassi-Rebay 1 viscous flux and gradient
  *     (Sec. 2, numerical fluxes), projection mortars on faces whose sides
- *     carry different orders (Sec. 2, non-conforming remark; the mortar
- *     construction is this project's reading, see the design notes).
+ *     carry different orders (Sec. 2, non-conforming remark).  The paper
+ *     gives no mortar detail; the reading used: per tangential direction
+ *     max(N+, N-) + 1 Gauss points in the first side's face frame, both
+ *     traces interpolated there, U* and F*.S formed there and L2-projected
+ *     back onto each side's face space.
  *   - The isolated operator F-hat: the element's own flux in place of the
  *     numerical flux on its boundary (Sec. 3.2.1, isolated truncation error).
  *   - A(Q) = M^{-1} F(Q) and the residual r = S - A(Q) (Sec. 3.1, nonlinRes).
