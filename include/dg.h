@@ -439,11 +439,13 @@ int dg_server_destroy(dg_server* srv);
  * per CTA) the volume kernel of every launch class (tiles of <= 128, <= 256,
  * <= 729 nodes) is timed with two CTA sizes on a freestream state, the
  * faster size kept, and the packings are compared on the time of the whole
- * residual (the other tile kernels see the same tiles); the fastest is kept.  Levels that exist are tuned now
- * (synchronises the stream; captured V-cycle graphs are dropped), later ones
- * when they are built.  Results do not change: every node's arithmetic is
- * the same whatever CTA computes it.  on = 0 keeps the current tiles.  Not
- * part of the paper (a choice of GPU work decomposition).
+ * residual (the other tile kernels see the same tiles); the fastest is kept.
+ * Levels that exist are tuned now (synchronises the stream; captured V-cycle
+ * graphs are dropped), later ones when they are built.  Results do not
+ * change: every node's arithmetic is the same whatever CTA computes it.
+ * on = 0 keeps the current tiles.  Without tuning a level packs 128 nodes
+ * per CTA, or 64 or 32 when it has fewer such tiles than the device has SMs.
+ * Not part of the paper (a choice of GPU work decomposition).
  */
 int dg_set_autotune(dg_mesh* mesh, int on, void* stream);
 
