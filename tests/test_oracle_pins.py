@@ -705,6 +705,38 @@ def test_order_selection_matches_brute_force(dim):
     assert mism <= 2
 
 
+def test_2d_jump_rule_raises_orders_as_little_as_possible():
+    """Sec. 4.1.2: neighbours may differ by at most one order per direction,
+    and the rule only raises.  On an axis-aligned mesh the directions match
+    across every face, so the least map above the input that satisfies the
+    rule has the closed form m(e) = max over elements f of N(f) - d(e, f),
+    d the number of face crossings between e and f.  The fix-point must be
+    exactly that: no order raised more than the rule requires."""
+    from collections import deque
+    mesh = syn.box_mesh(np.linspace(0, 1, 6), np.linspace(0, 1, 5), None)
+    K = mesh["K"]
+    ft = np.asarray(mesh["ftab"]).reshape(K, 6, 4)
+    dist = np.zeros((K, K), dtype=int)
+    for src in range(K):
+        d = np.full(K, -1)
+        d[src] = 0
+        todo = deque([src])
+        while todo:
+            e = todo.popleft()
+            for f in range(4):
+                nb = ft[e, f, 0]
+                if nb >= 0 and d[nb] < 0:
+                    d[nb] = d[e] + 1
+                    todo.append(nb)
+        dist[src] = d
+    for seed in range(4):
+        orders = syn.random_orders(K, 2, 1, 9, 30 + seed)
+        want = orders.copy()
+        for i in range(2):
+            want[:, i] = np.max(orders[None, :, i] - dist, axis=1)
+        assert np.array_equal(orc.limit_jumps(mesh, orders, "2d"), want)
+
+
 def test_jump_rules_fix_point():
     mesh = syn.box_mesh(np.linspace(0, 1, 7), np.linspace(0, 1, 6), None)
     rng = np.random.default_rng(1)
