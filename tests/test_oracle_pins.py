@@ -529,6 +529,32 @@ def test_rk3_stability_polynomial():
         assert abs(q - (1 + z + z * z / 2 + z ** 3 / 6)) < 1e-15
 
 
+def test_rk3_sweep_equals_its_butcher_form():
+    """Williamson's 2N-storage third-order scheme is the Runge-Kutta method
+    with c = (0, 1/3, 3/4), a21 = 1/3, a31 = -3/16, a32 = 15/16 and weights
+    (1/6, 3/10, 8/15) (eliminating the register g from the three stages gives
+    these).  One sweep of the oracle on the discrete operator must equal that
+    form stage for stage; a register not reset, a stage residual taken at the
+    wrong state or a swapped coefficient changes the result at first order."""
+    mesh = syn.periodic_box(2, 2, 1, dim=2)
+    orders = syn.random_orders(mesh["K"], 2, 1, 4, 3)
+    prm = syn.flow_params(mach=0.3, re=100.0)
+    q0 = syn.perturbed_state(mesh, orders, prm, 8, amp=0.05)
+    s = syn.random_source(mesh, orders, 9, amp=1e-2)
+    dt = 0.5 * orc.cfl_dt(mesh, orders, prm, q0)
+
+    def f(q):
+        return orc.residual(mesh, orders, prm, q, s)
+
+    k1 = f(q0)
+    k2 = f(q0 + dt / 3.0 * k1)
+    k3 = f(q0 + dt * (-3.0 / 16.0 * k1 + 15.0 / 16.0 * k2))
+    want = q0 + dt * (k1 / 6.0 + 3.0 * k2 / 10.0 + 8.0 * k3 / 15.0)
+    got = orc.rk3_sweep(mesh, orders, prm, q0, s, dt=dt)
+    change = np.max(np.abs(want - q0))
+    assert change > 0 and np.max(np.abs(got - want)) <= 1e-12 * change
+
+
 # ---------------------------------------------------------------------------
 # FAS V-cycle (Algorithm 1)
 # ---------------------------------------------------------------------------
