@@ -298,6 +298,44 @@ def test_residual_is_rotation_covariant(case):
     assert np.max(np.abs(r3 - rot(r))) > 1e-3 * np.max(np.abs(r))
 
 
+def test_br1_stencil_reaches_neighbours_of_neighbours():
+    """Sec. 2, BR1: the viscous flux on a face averages both sides' lifted
+    gradients, and each side's gradient lifts U* from all of its own faces.
+    So a change of one element's state reaches the residual of every element
+    within two face crossings and of no element farther away: elements at
+    distance >= 3 keep their residual bit for bit, elements at distance 2
+    (the second-neighbour reach of BR1) change."""
+    from collections import deque
+    mesh = syn.periodic_box(6, 6, 1, dim=2)
+    K = mesh["K"]
+    ft = np.asarray(mesh["ftab"]).reshape(K, 6, 4)
+    orders = syn.random_orders(K, 2, 1, 4, 5)
+    prm = syn.flow_params(mach=0.3, re=100.0)
+    q = syn.perturbed_state(mesh, orders, prm, 3, amp=0.05)
+    _, off = syn.layout_offsets(orders, 2)
+    X = 14
+    q2 = q.copy()
+    blk = slice(5 * off[X], 5 * off[X + 1])
+    q2[blk] *= 1 + 0.01 * np.random.default_rng(0).uniform(-1, 1, size=q2[blk].size)
+    r1, r2 = orc.residual(mesh, orders, prm, q), orc.residual(mesh, orders, prm, q2)
+    dist = np.full(K, -1)
+    dist[X] = 0
+    todo = deque([X])
+    while todo:
+        e = todo.popleft()
+        for f in range(4):
+            nb = ft[e, f, 0]
+            if nb >= 0 and dist[nb] < 0:
+                dist[nb] = dist[e] + 1
+                todo.append(nb)
+    for e in range(K):
+        b = slice(5 * off[e], 5 * off[e + 1])
+        if dist[e] >= 3:
+            assert np.array_equal(r1[b], r2[b]), e
+        else:
+            assert np.max(np.abs(r1[b] - r2[b])) > 0.0, e
+
+
 @pytest.mark.parametrize("name", ["periodic3d_mixed", "rotated3d_mixed"])
 def test_discrete_conservation(name):
     mesh, dim, lo, hi = MESHES[name]()
