@@ -334,6 +334,11 @@ def test_br1_stencil_reaches_neighbours_of_neighbours():
             assert np.array_equal(r1[b], r2[b]), e
         else:
             assert np.max(np.abs(r1[b] - r2[b])) > 0.0, e
+    # the isolated operator (Sec. 3.2.1) is element-local: only X changes
+    i1 = orc.residual(mesh, orders, prm, q, None, True)
+    i2 = orc.residual(mesh, orders, prm, q2, None, True)
+    changed = [e for e in range(K) if not np.array_equal(i1[5 * off[e]:5 * off[e + 1]], i2[5 * off[e]:5 * off[e + 1]])]
+    assert changed == [X]
 
 
 @pytest.mark.parametrize("name", ["periodic3d_mixed", "rotated3d_mixed"])
