@@ -806,6 +806,27 @@ def test_2d_jump_rule_raises_orders_as_little_as_possible():
         assert np.array_equal(orc.limit_jumps(mesh, orders, "2d"), want)
 
 
+def test_3d_jump_rule_gives_the_least_valid_map():
+    """Sec. 4.2.1: every element keeps N >= floor(2 N_nb / 3) against each face
+    neighbour, orders only rise.  Maps that satisfy these monotone
+    constraints are closed under the componentwise minimum, so a least one
+    above the input exists; on a chain of axis-aligned hexes each direction
+    is independent and small enough to enumerate every candidate map.  The
+    fix-point must be that least map."""
+    mesh = syn.box_mesh(np.linspace(0, 1, 5), [0, 1], [0, 1])
+    K = mesh["K"]
+    nbrs = [[int(mesh["ftab"][e, f, 0]) for f in range(6) if mesh["ftab"][e, f, 0] >= 0] for e in range(K)]
+    for seed in range(6):
+        orders = syn.random_orders(K, 3, 1, 9, 40 + seed)
+        got = orc.limit_jumps(mesh, orders, "3d")
+        for i in range(3):
+            best = None
+            for cand in itertools.product(*[range(int(orders[e, i]), 10) for e in range(K)]):
+                if all(cand[e] >= (2 * cand[nb]) // 3 for e in range(K) for nb in nbrs[e]):
+                    best = cand if best is None else tuple(min(a, b) for a, b in zip(best, cand))
+            assert tuple(int(x) for x in got[:, i]) == best, (seed, i)
+
+
 def test_jump_rules_fix_point():
     mesh = syn.box_mesh(np.linspace(0, 1, 7), np.linspace(0, 1, 6), None)
     rng = np.random.default_rng(1)
