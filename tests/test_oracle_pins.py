@@ -894,18 +894,24 @@ def test_smoothing_control_follows_the_two_rules(N, seed, eta, expect):
     assert np.array_equal(got, fixed)
 
 
-def test_oracle_reproduces_its_stored_residual():
-    """Regression: the oracle's residual on a fixed tiny case equals the values
-    tests/golden/make_golden.py stored (an intended change to the oracle's
-    arithmetic regenerates them, with the passage that justifies it)."""
+def test_oracle_reproduces_its_stored_outputs():
+    """Regression: the oracle's residual, V-cycle, tau table and adapted order
+    map on a fixed tiny case equal what tests/golden/make_golden.py stored
+    (an intended change to the oracle's arithmetic regenerates them, with the
+    passage that justifies it).  Order maps and the measured/unmeasured
+    pattern of the tau table must match exactly."""
     import importlib.util
     import os
     here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
     spec = importlib.util.spec_from_file_location("make_golden", os.path.join(here, "make_golden.py"))
     mg = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(mg)
-    mesh, orders, prm, q, s = mg.case()
-    stored = np.loadtxt(os.path.join(here, "oracle_residual_box2x2x1.txt"))
-    r = orc.residual(mesh, orders, prm, q, s)
-    assert r.shape == stored.shape
-    assert np.max(np.abs(r - stored)) <= 1e-13 * np.max(np.abs(stored))
+    for name, got in mg.compute().items():
+        stored = np.loadtxt(os.path.join(here, name))
+        assert got.shape == stored.shape, name
+        if "adapt" in name:
+            assert np.array_equal(got, stored), name
+            continue
+        if "tau" in name:
+            assert np.array_equal(got < 0, stored < 0), name
+        assert np.max(np.abs(got - stored)) <= 1e-13 * np.max(np.abs(stored)), name
