@@ -395,14 +395,22 @@ def test_closed_box_conserves_mass_and_energy(dim, tag):
     assert np.max(np.abs(tot[1:1 + dim])) > 1e-6 * mag.max()  # the walls do push
 
 
-def test_spectral_convergence_manufactured():
+@pytest.mark.parametrize("mixed", [False, True])
+def test_spectral_convergence_manufactured(mixed):
+    """The truncation error of the manufactured solution decays spectrally
+    with the order; with orders N..N+2 varying per element and direction
+    (mortars on most faces) it must decay as well: an inexact mortar
+    interpolation or projection would stall it at the non-conforming faces."""
     mesh = syn.periodic_box(4, 4, 1)
     prm = syn.flow_params(mach=0.3, re=100.0)
     ph = syn.manufactured_phases(0)
+    rng = np.random.default_rng(3)
     errs = []
     Ns = list(range(2, 9))
     for N in Ns:
         o = syn.uniform_orders(mesh["K"], 3, N)
+        if mixed:
+            o[:, :2] += rng.integers(0, 3, size=(mesh["K"], 2)).astype(np.int32)
         o[:, 2] = 1
         X = syn.node_coordinates(mesh, o)
         q = syn.manufactured_state(mesh, o, 0, prm[2], prm[0])
