@@ -12,9 +12,11 @@ LIB = os.path.join(HERE, "libdg_oracle.so")
 def build(force=False):
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
         return LIB
+    tmp = "%s.%d.tmp" % (LIB, os.getpid())  # built aside and renamed: concurrent builders never see a partial file
     cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fPIC", "-shared",
-           "-o", LIB, SRC, "-lm"]
+           "-o", tmp, SRC, "-lm"]
     subprocess.check_call(cmd)
+    os.replace(tmp, LIB)
     return LIB
 
 
