@@ -923,3 +923,405 @@ def test_oracle_reproduces_its_stored_outputs():
         if "tau" in name:
             assert np.array_equal(got < 0, stored < 0), name
         assert np.max(np.abs(got - stored)) <= 1e-13 * np.max(np.abs(stored)), name
+
+# ---------------------------------------------------------------------------
+# boundary conditions with closed forms (Sec. 2 boundary conditions, Sec. 4.1)
+# ---------------------------------------------------------------------------
+def _lagrange_at_end(n, side):
+    """l_j(+1) or l_j(-1) on the n Legendre-Gauss nodes, from numpy's nodes
+    and the product formula (no oracle table)."""
+    x, _ = np.polynomial.legendre.leggauss(n)
+    s = 1.0 if side > 0 else -1.0
+    return np.array([np.prod([(s - x[i]) / (x[j] - x[i]) for i in range(n) if i != j]) for j in range(n)])
+
+
+def _box_sizes(mesh, e):
+    """Edge lengths of an axis-aligned box element (2D: the z extent of the
+    reference extrusion, 2)."""
+    X = np.asarray(mesh["xmap"])[e]
+    h = X.max(axis=0) - X.min(axis=0)
+    if mesh["dim"] == 2:
+        h[2] = 2.0
+    return h
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_subsonic_outflow_ghost_carries_the_far_field_pressure(dim):
+    """Subsonic outflow (Sec. 4.1 test case): the ghost state keeps the
+    interior density and velocity and takes the far-field pressure.  For a
+    uniform state on a box that is periodic except for two outflow faces the
+    residual has a closed form: the volume term of a constant flux cancels the
+    element's own boundary flux, interior faces carry F(q), and at an outflow
+    face of outward normal n the lifted jump Roe(q, q_ghost, n) - F(q).n
+    remains, so at node (i, ...) of an element of width h_x
+        r = -(2/h_x) sum over the two x faces of l_i(+-1)/w_i (Roe - F.n).
+    The interior pressure differs from p_inf, so a ghost that kept it (Roe
+    flux = F.n, residual 0) or used the wrong energy fails.  Viscous terms are
+    made negligible (Re = 1e14)."""
+    zs = [0.0, 0.4, 1.0] if dim == 3 else None
+    mesh = syn.box_mesh([0.1, 0.8], [0.0, 0.3, 0.5], zs, periodic=(False, True, True),
+                        bc=dict(xmin=syn.BC_OUTFLOW, xmax=syn.BC_OUTFLOW))
+    K = mesh["K"]
+    orders = syn.random_orders(K, dim, 2, 4, 23)
+    prm = syn.flow_params(mach=0.3, re=1e14)
+    g = prm[0]
+    pinf = 1.0 / (g * prm[2] ** 2)
+    rho, u, v, w, p = 1.2, 0.4, 0.15, (0.1 if dim == 3 else 0.0), 1.3 * pinf
+    qc = np.array([rho, rho * u, rho * v, rho * w, p / (g - 1) + 0.5 * rho * (u * u + v * v + w * w)])
+    qg = qc.copy()
+    qg[4] = pinf / (g - 1) + 0.5 * rho * (u * u + v * v + w * w)
+
+    def Fn(q, n):
+        pp = (g - 1) * (q[4] - 0.5 * (q[1] ** 2 + q[2] ** 2 + q[3] ** 2) / q[0])
+        un = (q[1] * n[0] + q[2] * n[1] + q[3] * n[2]) / q[0]
+        return np.array([q[0] * un, q[1] * un + pp * n[0], q[2] * un + pp * n[1], q[3] * un + pp * n[2],
+                         (q[4] + pp) * un])
+
+    jumps = {s: orc.roe(prm, qc, qg, np.array([s, 0.0, 0.0])) - Fn(qc, np.array([s, 0.0, 0.0])) for s in (-1, 1)}
+    assert min(np.max(np.abs(j)) for j in jumps.values()) > 0.1  # the pressure jump is felt
+    nn, off = syn.layout_offsets(orders, dim)
+    q = syn.to_blocked(np.tile(qc[:, None], (1, off[-1])), orders, dim)
+    r = orc.residual(mesh, orders, prm, q)
+    want = np.zeros_like(r)
+    for e in range(K):
+        n = orders[e] + 1
+        if dim == 2:
+            n[2] = 1
+        _, wx = np.polynomial.legendre.leggauss(int(n[0]))
+        hx = _box_sizes(mesh, e)[0]
+        blk = np.zeros((5, n[2], n[1], n[0]))
+        for s in (-1, 1):
+            lw = _lagrange_at_end(int(n[0]), s) / wx
+            blk -= (2.0 / hx) * jumps[s][:, None, None, None] * lw[None, None, None, :]
+        want[5 * off[e]:5 * off[e + 1]] = blk.reshape(-1)
+    scale = np.max(np.abs(want))
+    assert scale > 1.0
+    assert np.max(np.abs(r - want)) <= 1e-11 * scale
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_no_slip_wall_shear_stress_of_a_couette_profile(dim):
+    """No-slip adiabatic wall (Sec. 4.1): the viscous wall flux is the stress
+    of the interior gradient at zero velocity.  With rho = 1, p = p_inf (so
+    T = 1 and mu = 1), v = w = 0 and the Couette profile u = a y, the wall
+    feels the shear stress mu a and nothing else; a free-slip top carries no
+    viscous flux and no x-momentum.  Discrete conservation then fixes the
+    total of the x-momentum residual,
+        sum over nodes of w J r_(rho u) = -mu a A_wall / Re,
+    A_wall the wall area (2D: the reference extrusion of depth 2), while mass,
+    y-momentum and energy sum to zero.  A dropped or mis-signed wall stress,
+    or a wall flux built from the ghost's negated gradient, fails.  Orders are
+    at least 2: the total energy p/(gamma-1) + u^2/2 is quadratic in y, and
+    only then are the face traces of the conserved state exact."""
+    a, re = 2.5, 50.0
+    xs = [0.0, 0.4, 0.9, 1.3]
+    zs = [0.0, 0.5, 1.0] if dim == 3 else None
+    mesh = syn.box_mesh(xs, [0.0, 0.05, 0.15, 0.4], zs, periodic=(True, False, True),
+                        bc=dict(ymin=syn.BC_WALL, ymax=syn.BC_SLIP))
+    K = mesh["K"]
+    orders = syn.random_orders(K, dim, 2, 4, 29)
+    prm = syn.flow_params(mach=0.3, re=re)
+    g = prm[0]
+    pinf = 1.0 / (g * prm[2] ** 2)
+    X = syn.node_coordinates(mesh, orders)
+    u = a * X[:, 1]
+    zero = 0.0 * u
+    q = syn.to_blocked(syn.conserved(1.0 + zero, u, zero, zero, pinf + zero, g), orders, dim)
+    r = orc.residual(mesh, orders, prm, q)
+    nn, off = syn.layout_offsets(orders, dim)
+    tot, mag = np.zeros(5), 0.0
+    for e in range(K):
+        n = orders[e] + 1
+        if dim == 2:
+            n[2] = 1
+        w = [np.polynomial.legendre.leggauss(int(k))[1] for k in n]
+        W = np.einsum("k,j,i->kji", w[2], w[1], w[0]).reshape(-1) * np.prod(_box_sizes(mesh, e) / 2.0)
+        blk = r[5 * off[e]:5 * off[e + 1]].reshape(5, -1) * W
+        tot += blk.sum(1)
+        mag = max(mag, np.abs(blk).sum())
+    area = (xs[-1] - xs[0]) * ((zs[-1] - zs[0]) if dim == 3 else 2.0)
+    want = -1.0 * a * area / re
+    assert abs(tot[1] - want) <= 1e-12 * mag, (tot[1], want)
+    assert abs(tot[0]) <= 1e-13 * mag and abs(tot[2]) <= 1e-12 * mag and abs(tot[4]) <= 1e-12 * mag
+
+
+# ---------------------------------------------------------------------------
+# adaptation with a stage cap and the conforming-wall rule (Sec. 3.3.4, 4.2.1)
+# ---------------------------------------------------------------------------
+def _brute_select_capped(ttab, P, tau_max, n_min, n_max, dim, cap):
+    """_brute_select with the stage cap of Sec. 3.3.4: candidate orders stop
+    at min(n_max, cap) and that bound replaces N_max when nothing qualifies."""
+    return _brute_select(ttab, P, tau_max, n_min, min(n_max, cap), dim)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_capped_order_selection_matches_brute_force(dim):
+    """A stage of the multi-stage adaptation caps the new orders (Sec. 3.3.4).
+    The capped selection must be the brute-force choice over the capped
+    candidate set; the cases include caps below the reference order (only the
+    inner map is searched, and the fallback is the cap, not N_max)."""
+    rng = np.random.default_rng(10 + dim)
+    mism, below_ref, fallback = 0, 0, 0
+    for trial in range(300):
+        P = rng.integers(2, 8, size=3)
+        ttab = np.full((3, 16), -1.0)
+        for i in range(dim):
+            rate = rng.uniform(0.1, 1.5)
+            base = 10 ** rng.uniform(-4, 0)
+            for N in range(1, P[i]):
+                ttab[i, N] = base * 10 ** (-rate * N) * 10 ** rng.uniform(-0.3, 0.3)
+        tau_max = 10 ** rng.uniform(-6, -1)
+        cap = int(rng.integers(1, 9))
+        got = orc.select_orders(ttab, P, tau_max, 1, 9, dim, cap=cap)[:dim]
+        want = _brute_select_capped(ttab, P, tau_max, 1, 9, dim, cap)
+        assert max(got) <= cap
+        below_ref += int(cap < int(P[:dim].max()) - 1)
+        fallback += int(want == [cap] * dim)
+        if got != want:
+            mism += 1
+    assert below_ref > 30 and fallback > 10  # both branches of the cap are exercised
+    assert mism <= 2  # flips at last-bit ties of the two fits only
+
+
+@pytest.mark.parametrize("dim,rule", [(2, "2d"), (3, "3d")])
+def test_conforming_wall_rule_gives_the_least_valid_map(dim, rule):
+    """Sec. 4.2.1: elements on the tagged wall get conforming orders with their
+    wall neighbours, on top of the order-jump rule, and orders only rise.  On
+    a chain of axis-aligned elements of which only the middle three touch the
+    tagged boundary, every direction is independent; the constraints are
+    monotone, so the least map above the input exists and enumeration finds
+    it.  The fix-point must return exactly that map: the tagged elements share
+    their largest order, the others obey only the jump rule."""
+    tagged = {1, 2, 3}
+    zs = [0.0, 1.0] if dim == 3 else None
+    side = "ymin"
+
+    def tag(i, k):
+        return syn.BC_WALL if i in tagged else syn.BC_SLIP
+
+    mesh = syn.box_mesh(np.linspace(0, 1, 6), [0.0, 1.0], zs, bc={side: tag})
+    K = mesh["K"]
+    nbrs = [[int(mesh["ftab"][e, f, 0]) for f in range(2 * dim) if mesh["ftab"][e, f, 0] >= 0] for e in range(K)]
+    raised = 0
+    for seed in range(6):
+        orders = syn.random_orders(K, dim, 1, 8, 60 + seed)
+        got = orc.limit_jumps(mesh, orders, rule, conform_tag=syn.BC_WALL)
+        for i in range(dim):
+            top = int(orders[:, i].max())
+            best = None
+            for cand in itertools.product(*[range(int(orders[e, i]), top + 1) for e in range(K)]):
+                ok = True
+                for e in range(K):
+                    for nb in nbrs[e]:
+                        need = cand[nb] - 1 if rule == "2d" else (2 * cand[nb]) // 3
+                        if e in tagged and nb in tagged:
+                            need = max(need, cand[nb])
+                        if cand[e] < need:
+                            ok = False
+                if ok:
+                    best = cand if best is None else tuple(min(x, y) for x, y in zip(best, cand))
+            assert tuple(int(x) for x in got[:, i]) == best, (seed, i)
+            assert len({best[e] for e in tagged}) == 1
+            raised += int(best != tuple(int(x) for x in orders[:, i]))
+    assert raised > 0
+
+
+# ---------------------------------------------------------------------------
+# steady driver: FMG ramp, reference solve, multi-stage adaptation
+# (Sec. 3.1.1, 3.3.2, 3.3.4)
+# ---------------------------------------------------------------------------
+class _DriverProbe:
+    """Stand-ins for the operator, the V-cycle and the tau estimate with which
+    the steady driver's control flow has a closed form: A = identity on every
+    level (r = S - Q), and a V-cycle halves the residual exactly
+    (Q <- Q + (S - Q)/2).  Every cycle and every estimate is recorded."""
+
+    def __init__(self, tables=()):
+        self.cycles = []   # (orders, q in, s in)
+        self.taus = []     # (orders, q)
+        self.tables = list(tables)
+
+    def residual(self, mesh, o, prm, q, s=None, isolated=False):
+        return (0.0 if s is None else s) - q
+
+    def vcycle(self, mesh, o, prm, q, s, b1, b2, bc, direction=None, coarsest=1, delta_n=1, control=0, eta=1.1):
+        self.cycles.append((o.copy(), q.copy(), None if s is None else s.copy()))
+        return q + 0.5 * ((0.0 if s is None else s) - q)
+
+    def tau(self, mesh, o, prm, q, s, dir_mask=7, with_correction=True, isolated=True):
+        self.taus.append((o.copy(), q.copy()))
+        return self.tables[len(self.taus) - 1]
+
+    def install(self, monkeypatch):
+        monkeypatch.setattr(orc, "residual", self.residual)
+        monkeypatch.setattr(orc, "fas_vcycle", self.vcycle)
+        monkeypatch.setattr(orc, "tau_estimate", self.tau)
+
+
+def _halve_until(q, s, target):
+    """The expected cycle count and end state of cycling (S - Q) below target
+    with the halving cycle, checked before every cycle."""
+    S = 0.0 if s is None else s
+    c = 0
+    while not np.max(np.abs(S - q)) < target:
+        q = q + 0.5 * (S - q)
+        c += 1
+    return q, c
+
+
+_MG = dict(beta1=1, beta2=1, beta_c=1)
+
+
+def test_steady_driver_fmg_ramp_hands_each_level_up_by_interpolation(monkeypatch):
+    """Sec. 3.1.1: the full-multigrid start cycles order 1, then 2, ... up to
+    one below the reference order, each until max|r| < fmg_tol (the paper:
+    1e-1), each starting from the previous level's state interpolated up (the
+    first from the initial state projected down), with the source projected
+    to the level; the reference orders then take the last FMG state
+    interpolated up and cycle to tol.  Starting at order 2, skipping the
+    hand-off, or dropping the source on the FMG levels fails."""
+    probe = _DriverProbe()
+    probe.install(monkeypatch)
+    mesh = syn.box_mesh(np.linspace(0, 1, 4), np.linspace(0, 1, 3), None)
+    dim, K = 2, mesh["K"]
+    P = syn.random_orders(K, dim, 3, 4, 5)
+    P[0, :2] = 4
+    rng = np.random.default_rng(3)
+    q0 = rng.uniform(-2, 2, size=5 * orc.nodes_total(P, dim))
+    s = rng.uniform(-1, 1, size=q0.size)
+    fmg_tol, tol = 1e-1, 1e-9
+    orders, q, rep = orc.solve_steady(mesh, P, None, q0, s, tol, 100, _MG, fmg=True, fmg_tol=fmg_tol)
+    # the expected ramp, level by level
+    want, prev_o, prev_q = [], None, None
+    for lv in (1, 2, 3):
+        o = orc.level_orders(P, lv, dim)
+        ql = orc.transfer(dim, P, o, q0) if prev_o is None else orc.transfer(dim, prev_o, o, prev_q)
+        sl = orc.transfer(dim, P, o, s)
+        qe, c = _halve_until(ql, sl, fmg_tol)
+        assert c >= 1
+        want.append((o, ql, sl, c))
+        prev_o, prev_q = o, qe
+    qP = orc.transfer(dim, prev_o, P, prev_q)
+    qend, cP = _halve_until(qP, s, tol)
+    seq = [(o, c) for o, _, _, c in want] + [(P, cP)]
+    assert len(probe.cycles) == sum(c for _, c in seq)
+    k = 0
+    for (o, c), first in zip(seq, [(w[1], w[2]) for w in want] + [(qP, s)]):
+        for j in range(c):
+            got_o, got_q, got_s = probe.cycles[k + j]
+            assert np.array_equal(got_o, o)
+            assert got_s is not None and np.max(np.abs(got_s - first[1])) < 1e-14
+        assert np.max(np.abs(probe.cycles[k][1] - first[0])) < 1e-13  # hand-off state
+        k += c
+    assert rep["fmg_cycles"] == sum(w[3] for w in want) and rep["cycles"] == len(probe.cycles)
+    assert rep["status"] == "ok" and np.array_equal(orders, P)
+    assert np.max(np.abs(q - qend)) < 1e-13
+
+
+def test_steady_driver_stages_reconverge_and_stop_on_the_uncapped_selection(monkeypatch):
+    """Sec. 3.3.2 and 3.3.4: the reference solve converges to ref_factor *
+    tau_max, the tau estimate is taken there, the new orders are capped at
+    the stage's order, and every later stage first re-converges to
+    ref_factor * tau_max on the adapted mesh.  A stage is the last when the
+    selection WITHOUT the cap needs no order above the stage's cap.  The
+    first table asks for order 5 (uncapped) while stage 1 caps at 3: the
+    capped map is all 3s, so a driver that tested the capped selection would
+    stop after one stage.  The second table asks for at most order 3 <= 6:
+    the driver stops there and cycles to tol."""
+    mesh = syn.box_mesh(np.linspace(0, 1, 4), np.linspace(0, 1, 3), None)
+    dim, K = 2, mesh["K"]
+    P = syn.uniform_orders(K, dim, 4)
+    tau_max, ref, tol = 1e-4, 0.1, 1e-9
+    t0 = np.full((K, 3, 16), -1.0)
+    t1 = np.full((K, 3, 16), -1.0)
+    for e in range(K):
+        for i in range(dim):
+            for N in range(1, 4):
+                t0[e, i, N] = 10.0 ** (-N)          # uncapped: N = 5 per direction
+            for N in range(1, 3):
+                t1[e, i, N] = 10.0 ** (-2.0 * N - 0.5 * (e % 2) * i)  # uncapped: (3,3) or (3,2)
+    probe = _DriverProbe([t0, t1])
+    probe.install(monkeypatch)
+    rng = np.random.default_rng(4)
+    q0 = rng.uniform(-1, 1, size=5 * orc.nodes_total(P, dim))
+    adapt = dict(tau_max=tau_max, ref_factor=ref, n_min=1, n_max=8, jump_rule=0, stages=(3, 6))
+    orders, q, rep = orc.solve_steady(mesh, P, None, q0, None, tol, 200, _MG, adapt=adapt)
+    # independent expectation of the two stages' maps
+    free0 = np.array([orc.select_orders(t0[e], P[e], tau_max, 1, 8, dim) for e in range(K)])
+    cap0 = np.array([orc.select_orders(t0[e], P[e], tau_max, 1, 8, dim, cap=3) for e in range(K)])
+    assert free0[:, :dim].max() == 5 and cap0[:, :dim].max() == 3
+    A1 = cap0.astype(np.int32)
+    A2 = np.array([orc.select_orders(t1[e], A1[e], tau_max, 1, 8, dim, cap=6) for e in range(K)], dtype=np.int32)
+    assert A2[:, :dim].max() <= 6 and not np.array_equal(A2, A1)
+    assert len(probe.taus) == 2
+    assert np.array_equal(probe.taus[0][0], P) and np.array_equal(probe.taus[1][0], A1)
+    assert np.array_equal(orders, A2) and rep["adapted"] == 2
+    # the cycle sequence: reference solve at P, stage 2's re-convergence on A1, final solve on A2
+    qa, ca = _halve_until(q0, None, tau_max * ref)
+    assert np.max(np.abs(probe.taus[0][1] - qa)) < 1e-15
+    qb, cb = _halve_until(orc.transfer(dim, P, A1, qa), None, tau_max * ref)
+    assert np.max(np.abs(probe.taus[1][1] - qb)) < 1e-15
+    qc, cc = _halve_until(orc.transfer(dim, A1, A2, qb), None, tol)
+    got = [(o.tobytes(), s is None) for o, _, s in probe.cycles]
+    want = [(P.tobytes(), True)] * ca + [(A1.tobytes(), True)] * cb + [(A2.tobytes(), True)] * cc
+    assert got == want
+    assert rep["cycles"] == ca + cb + cc and rep["status"] == "ok"
+    assert np.max(np.abs(q - qc)) < 1e-15
+
+
+@pytest.mark.parametrize("isolated", [True, False])
+def test_tau_forms_agree_on_a_converged_state_and_vanish_along_constant_directions(isolated):
+    """Sec. 3.2.1: the quasi-a-priori estimate without correction, R^l(I q),
+    and the form with correction, R^l(I q) - I R^P(q), are the same once q
+    solves the problem at P (R^P(q) = 0, eq TruncError!), for the full and for
+    the isolated operator; with the source restricted alongside the state.
+    And for a field constant along eta the eta-estimate vanishes with the
+    full operator as with the isolated one (Sec. 3.3.1: coarsening eta
+    loses nothing).  For the full operator that needs one x-order on every
+    element: y-neighbours with different x-orders interpolate q(x) by
+    different polynomials, and the jump between their traces is a genuine
+    y-dependence of the discrete residual.  A dropped correction term, an
+    unrestricted source or a wrong restriction direction fails."""
+    mesh = syn.box_mesh(np.linspace(0, 1, 4), np.linspace(0, 1, 3), None, periodic=(True, True, True))
+    orders = syn.random_orders(mesh["K"], 2, 3, 5, 2)
+    orders[:, 0] = 4
+    prm = syn.flow_params(mach=0.3, re=100.0)
+    q = syn.smooth_state(mesh, orders, prm, 5, amp=0.05, wavelength=1.0)
+    S = orc.operator_A(mesh, orders, prm, q, isolated)  # q solves A(q) = S exactly
+    tw = orc.tau_estimate(mesh, orders, prm, q, S, dir_mask=3, with_correction=True, isolated=isolated)
+    tn = orc.tau_estimate(mesh, orders, prm, q, S, dir_mask=3, with_correction=False, isolated=isolated)
+    meas = tw >= 0
+    assert np.array_equal(meas, tn >= 0) and meas.sum() > 0
+    scale = np.max(tw[meas])
+    assert scale > 1e-6
+    assert np.max(np.abs(tw[meas] - tn[meas])) <= 1e-9 * scale
+    # a field of x alone
+    X = syn.node_coordinates(mesh, orders)
+    g, M = prm[0], prm[2]
+    rho = 1 + 0.1 * np.sin(2 * np.pi * X[:, 0])
+    u = 1 + 0.1 * np.cos(2 * np.pi * X[:, 0])
+    p = (1 + 0.05 * np.sin(2 * np.pi * X[:, 0] + 1)) / (g * M * M)
+    qx = syn.to_blocked(syn.conserved(rho, u, 0 * u, 0 * u, p, g), orders, 2)
+    t = orc.tau_estimate(mesh, orders, prm, qx, None, dir_mask=3, isolated=isolated)
+    assert np.max(t[:, 1][t[:, 1] >= 0]) < 1e-10
+    assert np.max(t[:, 0][t[:, 0] >= 0]) > 1e-4
+
+
+@pytest.mark.parametrize("direction,delta_n", [(0, 1), (1, 1), (None, 2)])
+def test_converged_state_is_a_fixed_point_of_directional_and_coarse_step_cycles(direction, delta_n):
+    """Algorithm 1 with the directional coarsening of Sec. 3.3.1 and with an
+    order drop of 2 between levels: at a solution of A(q) = S every level's
+    FAS problem is solved by the restricted state (its source is built from
+    it), so the cycle returns q unchanged up to roundoff.  A coarse source
+    that is not A_c(I q) + I r, or a correction I(Q_c - Q_c0) with a wrong
+    sign or transfer, moves q."""
+    mesh = syn.periodic_box(2, 2, 1, dim=2)
+    orders = syn.random_orders(mesh["K"], 2, 3, 5, 8)
+    prm = syn.flow_params(mach=0.3, re=100.0)
+    q = syn.perturbed_state(mesh, orders, prm, 3)
+    S = -orc.residual(mesh, orders, prm, q)
+    q1 = orc.fas_vcycle(mesh, orders, prm, q, S, 1, 1, 2, direction=direction, delta_n=delta_n)
+    assert np.max(np.abs(q1 - q)) < 1e-11 * np.max(np.abs(q))
+    # and away from the solution the same cycle does move it
+    q2 = orc.fas_vcycle(mesh, orders, prm, q, 0.0 * S, 1, 1, 2, direction=direction, delta_n=delta_n)
+    assert np.max(np.abs(q2 - q)) > 1e-6 * np.max(np.abs(q))
