@@ -252,7 +252,8 @@ typedef struct {
  * lexicographically smaller orders), N_max where nothing qualifies, then the
  * order-jump fix-point (only raises orders).
  *  new_orders  K x 3 int32 host output.
- * Pure host computation; deterministic.
+ * Pure host computation; deterministic.  DG_ENOTCONVERGED (new_orders
+ * untouched) if the jump fix-point has not settled after 100,000 sweeps.
  */
 int dg_adapt(const dg_mesh* mesh, const double* tau_host, const dg_adapt_params* ap,
              int32_t* new_orders);
@@ -324,8 +325,8 @@ int dg_transfer_state(const dg_mesh* from, const double* q_from, const dg_mesh* 
 /*
  * dg_transfer_noalloc -- the order-map transfer of dg_transfer_state for
  * callers that cannot allocate device memory at the time of the call (a host
- * code that hands all device memory to its own pool at start-up, or a caller
- * recording a CUDA graph): it takes no mesh handle and allocates nothing.
+ * code that hands all device memory to its own pool at start-up and has none
+ * left for a library): it takes no mesh handle and allocates nothing.
  * The paper has no counterpart to this entry point; it is a service of this
  * library.
  *  dim          2 or 3.
@@ -333,7 +334,8 @@ int dg_transfer_state(const dg_mesh* from, const double* q_from, const dg_mesh* 
  *               message naming the limit).
  *  orders_from, orders_to  K x 3 int32 HOST arrays of the two order maps
  *               (N3 = 0 in 2D); read before the call returns.
- *  nvar         variables per node (5 for a state).
+ *  nvar         variables per node (5 for a state), 1 <= nvar <= 64
+ *               (larger: DG_EINVAL).
  *  in, out      caller-owned DEVICE arrays in the element-blocked layout of
  *               the two order maps (nvar values per node, variable-major per
  *               element); out may not alias in.

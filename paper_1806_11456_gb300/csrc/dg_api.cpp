@@ -443,7 +443,10 @@ static void face_map(int fA, int fB, int o, int* m) {
   }
 }
 
-static void limit_jumps(const dg_mesh* m, std::vector<int32_t>& o, int rule, int conform_tag) {
+// Jacobi sweeps of the order-jump rules until nothing changes.  The rules only
+// raise orders and never above the largest order of the map, so the sweeps
+// settle within K x max order of them; the cap only guards that argument.
+static int limit_jumps(const dg_mesh* m, std::vector<int32_t>& o, int rule, int conform_tag) {
   const int dim = m->dim, K = m->K;
   std::vector<char> touches(K, 0);
   if (conform_tag >= 0)
@@ -468,9 +471,11 @@ static void limit_jumps(const dg_mesh* m, std::vector<int32_t>& o, int rule, int
           if (need > nw[e * 3 + i]) nw[e * 3 + i] = need;
         }
       }
-    if (nw == o) return;
+    if (nw == o) return DG_OK;
     o.swap(nw);
   }
+  set_error("dg_adapt: the order-jump fix-point did not settle within 100000 sweeps");
+  return DG_ENOTCONVERGED;
 }
 
 }  // namespace dg
@@ -911,7 +916,7 @@ int dg_adapt(const dg_mesh* m, const double* tau_host, const dg_adapt_params* ap
     for (int e = 0; e < m->K; ++e)
       select_element(tau_host + (size_t)e * 3 * kTauSlots, &m->orders[e * 3], *ap, m->dim, &o[e * 3]);
     if (ap->jump_rule == 1 || ap->jump_rule == 2 || ap->conform_tag >= 0)
-      limit_jumps(m, o, ap->jump_rule, ap->conform_tag);
+      DG_TRY(limit_jumps(m, o, ap->jump_rule, ap->conform_tag));
     std::memcpy(new_orders, o.data(), o.size() * sizeof(int32_t));
     return DG_OK;
   });

@@ -26,6 +26,19 @@ constexpr int kTauSlots = 16;           // orders per direction in the tau table
 
 void set_error(const std::string& msg);
 
+// Process-wide state kept once per CUDA device (device tables, one-time
+// set-up flags): get(dev) is the entry of device `dev`, or nullptr for an
+// index outside [0, kMax).  Pure host bookkeeping; callers serialise access.
+template <typename T>
+class PerDevice {
+ public:
+  static constexpr int kMax = 64;
+  T* get(int dev) { return (dev >= 0 && dev < kMax) ? &slots_[dev] : nullptr; }
+
+ private:
+  T slots_[kMax] = {};
+};
+
 #define DG_CUDA_TRY(call)                                                              \
   do {                                                                                 \
     cudaError_t _e = (call);                                                           \

@@ -56,16 +56,12 @@ __constant__ DevTables2 c_tab2;
 __constant__ float2* c_Dhat2;
 __constant__ float2* c_D2;
 __constant__ float2* c_T2;
-static float2* g_dev_Dhat2 = nullptr;
-static float2* g_dev_D2 = nullptr;
-static float2* g_dev_T2 = nullptr;
 
 static float2 split2(double x) {
   float h = (float)x;
   return make_float2(h, (float)(x - (double)h));
 }
 
-static double* g_dev_Dhat = nullptr;
 // Kernels launched by this library: a process total and a per-thread count
 // (a graph capture measures its own launches with the latter).
 static std::atomic<unsigned long long> g_launches_total{0};
@@ -80,9 +76,16 @@ void add_launches(unsigned long long n) {
   g_launches_total.fetch_add(n, std::memory_order_relaxed);
   t_launches += n;
 }
-static double* g_dev_D = nullptr;
-static double* g_dev_T = nullptr;
-static int g_tables_device = -1;
+// Device copies of the derivative and transfer tables, one set per device:
+// the __constant__ pointers above are per-device symbols, and each device's
+// must point at that device's own copy.
+struct DeviceTables {
+  double *Dhat = nullptr, *D = nullptr, *T = nullptr;
+  float2 *Dhat2 = nullptr, *D2 = nullptr, *T2 = nullptr;
+  bool ready = false;       // tables uploaded and symbols set on this device
+  bool smem_ready = false;  // kernel shared-memory attributes set on this device
+};
+static PerDevice<DeviceTables> g_dev_tables;
 
 static std::mutex g_setup_mutex;  // one-time per-device setup (tables, kernel attributes)
 
@@ -90,7 +93,13 @@ int upload_tables() {
   std::lock_guard<std::mutex> lock(g_setup_mutex);
   int dev = 0;
   DG_CUDA_TRY(cudaGetDevice(&dev));
-  if (g_tables_device == dev) return DG_OK;
+  DeviceTables* dt = g_dev_tables.get(dev);
+  if (!dt) {
+    set_error("device index " + std::to_string(dev) + " beyond the library's limit of " +
+              std::to_string(PerDevice<DeviceTables>::kMax) + " devices");
+    return DG_EINVAL;
+  }
+  if (dt->ready) return DG_OK;
   const Tables1D& T = tables();
   DevTables h;
   memset(&h, 0, sizeof(h));
@@ -114,17 +123,17 @@ int upload_tables() {
   std::vector<double> Tm((size_t)kNP * kNP * kNP * kNP, 0.0);
   for (int nf = 1; nf < kNP; ++nf)
     for (int nt = 1; nt < kNP; ++nt) transfer_matrix(nf, nt, &Tm[((size_t)nf * kNP + nt) * kNP * kNP]);
-  if (!g_dev_Dhat) {
-    DG_CUDA_TRY(cudaMalloc(&g_dev_Dhat, Dh.size() * sizeof(double)));
-    DG_CUDA_TRY(cudaMalloc(&g_dev_D, Dc.size() * sizeof(double)));
-    DG_CUDA_TRY(cudaMalloc(&g_dev_T, Tm.size() * sizeof(double)));
+  if (!dt->Dhat) {
+    DG_CUDA_TRY(cudaMalloc(&dt->Dhat, Dh.size() * sizeof(double)));
+    DG_CUDA_TRY(cudaMalloc(&dt->D, Dc.size() * sizeof(double)));
+    DG_CUDA_TRY(cudaMalloc(&dt->T, Tm.size() * sizeof(double)));
   }
-  DG_CUDA_TRY(cudaMemcpy(g_dev_Dhat, Dh.data(), Dh.size() * sizeof(double), cudaMemcpyHostToDevice));
-  DG_CUDA_TRY(cudaMemcpy(g_dev_D, Dc.data(), Dc.size() * sizeof(double), cudaMemcpyHostToDevice));
-  DG_CUDA_TRY(cudaMemcpy(g_dev_T, Tm.data(), Tm.size() * sizeof(double), cudaMemcpyHostToDevice));
-  DG_CUDA_TRY(cudaMemcpyToSymbol(c_Dhat, &g_dev_Dhat, sizeof(double*)));
-  DG_CUDA_TRY(cudaMemcpyToSymbol(c_D, &g_dev_D, sizeof(double*)));
-  DG_CUDA_TRY(cudaMemcpyToSymbol(c_T, &g_dev_T, sizeof(double*)));
+  DG_CUDA_TRY(cudaMemcpy(dt->Dhat, Dh.data(), Dh.size() * sizeof(double), cudaMemcpyHostToDevice));
+  DG_CUDA_TRY(cudaMemcpy(dt->D, Dc.data(), Dc.size() * sizeof(double), cudaMemcpyHostToDevice));
+  DG_CUDA_TRY(cudaMemcpy(dt->T, Tm.data(), Tm.size() * sizeof(double), cudaMemcpyHostToDevice));
+  DG_CUDA_TRY(cudaMemcpyToSymbol(c_Dhat, &dt->Dhat, sizeof(double*)));
+  DG_CUDA_TRY(cudaMemcpyToSymbol(c_D, &dt->D, sizeof(double*)));
+  DG_CUDA_TRY(cudaMemcpyToSymbol(c_T, &dt->T, sizeof(double*)));
   // float-pair copies
   DevTables2 h2;
   memset(&h2, 0, sizeof(h2));
@@ -140,18 +149,18 @@ int upload_tables() {
   for (size_t i = 0; i < Dh.size(); ++i) Dh2[i] = split2(Dh[i]);
   for (size_t i = 0; i < Dc.size(); ++i) Dc2[i] = split2(Dc[i]);
   for (size_t i = 0; i < Tm.size(); ++i) Tm2[i] = split2(Tm[i]);
-  if (!g_dev_Dhat2) {
-    DG_CUDA_TRY(cudaMalloc(&g_dev_Dhat2, Dh2.size() * sizeof(float2)));
-    DG_CUDA_TRY(cudaMalloc(&g_dev_D2, Dc2.size() * sizeof(float2)));
-    DG_CUDA_TRY(cudaMalloc(&g_dev_T2, Tm2.size() * sizeof(float2)));
+  if (!dt->Dhat2) {
+    DG_CUDA_TRY(cudaMalloc(&dt->Dhat2, Dh2.size() * sizeof(float2)));
+    DG_CUDA_TRY(cudaMalloc(&dt->D2, Dc2.size() * sizeof(float2)));
+    DG_CUDA_TRY(cudaMalloc(&dt->T2, Tm2.size() * sizeof(float2)));
   }
-  DG_CUDA_TRY(cudaMemcpy(g_dev_Dhat2, Dh2.data(), Dh2.size() * sizeof(float2), cudaMemcpyHostToDevice));
-  DG_CUDA_TRY(cudaMemcpy(g_dev_D2, Dc2.data(), Dc2.size() * sizeof(float2), cudaMemcpyHostToDevice));
-  DG_CUDA_TRY(cudaMemcpy(g_dev_T2, Tm2.data(), Tm2.size() * sizeof(float2), cudaMemcpyHostToDevice));
-  DG_CUDA_TRY(cudaMemcpyToSymbol(c_Dhat2, &g_dev_Dhat2, sizeof(float2*)));
-  DG_CUDA_TRY(cudaMemcpyToSymbol(c_D2, &g_dev_D2, sizeof(float2*)));
-  DG_CUDA_TRY(cudaMemcpyToSymbol(c_T2, &g_dev_T2, sizeof(float2*)));
-  g_tables_device = dev;
+  DG_CUDA_TRY(cudaMemcpy(dt->Dhat2, Dh2.data(), Dh2.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  DG_CUDA_TRY(cudaMemcpy(dt->D2, Dc2.data(), Dc2.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  DG_CUDA_TRY(cudaMemcpy(dt->T2, Tm2.data(), Tm2.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  DG_CUDA_TRY(cudaMemcpyToSymbol(c_Dhat2, &dt->Dhat2, sizeof(float2*)));
+  DG_CUDA_TRY(cudaMemcpyToSymbol(c_D2, &dt->D2, sizeof(float2*)));
+  DG_CUDA_TRY(cudaMemcpyToSymbol(c_T2, &dt->T2, sizeof(float2*)));
+  dt->ready = true;
   return DG_OK;
 }
 
@@ -1347,10 +1356,14 @@ static int set_attrs() {
 
 static int configure_smem() {
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  static int done_dev = -1;
   int dev = 0;
   DG_CUDA_TRY(cudaGetDevice(&dev));
-  if (done_dev == dev) return DG_OK;
+  DeviceTables* dt = g_dev_tables.get(dev);
+  if (!dt) {
+    set_error("device index " + std::to_string(dev) + " beyond the library's device limit");
+    return DG_EINVAL;
+  }
+  if (dt->smem_ready) return DG_OK;
   int rc;
   if ((rc = set_attrs<double, 2, false>()) != DG_OK) return rc;
   if ((rc = set_attrs<double, 2, true>()) != DG_OK) return rc;
@@ -1362,7 +1375,7 @@ static int configure_smem() {
   if ((rc = set_attrs<dd, 3, true>()) != DG_OK) return rc;
   DG_CUDA_TRY(cudaFuncSetAttribute(k_transfer, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)(2 * kTransferMaxSlab * sizeof(double))));
-  done_dev = dev;
+  dt->smem_ready = true;
   return DG_OK;
 }
 
@@ -1909,8 +1922,8 @@ static int tau_reduce(const Level* L, const double* r, const double* rho, int di
 // Allocation-free order-map transfer (dg_transfer_noalloc in dg.h)
 //
 // Some callers cannot allocate device memory when they need a transfer: a
-// host code that reserves all device memory up front in its own pool, or a
-// caller that is recording a CUDA graph.  This variant of k_transfer needs no
+// host code that reserves all device memory up front in its own pool leaves
+// none for a library.  This variant of k_transfer needs no
 // mesh handle and no library-allocated buffer: its only scratch -- one
 // 8-int record per element (both node-count triples and both node offsets) --
 // lives in the static device array below, and its 1-D projection /
@@ -1922,6 +1935,7 @@ static int tau_reduce(const Level* L, const double* r, const double* rho, int di
 // ---------------------------------------------------------------------------
 constexpr int kNoAllocMaxElems = 65536;  // 65,536 elements -> 2 MiB of records
 constexpr int kNoAllocRec = 8;
+constexpr int kNoAllocMaxVars = 64;      // variables per node
 static __device__ __align__(256) int32_t g_noalloc_records[kNoAllocMaxElems * kNoAllocRec];
 
 namespace {
@@ -2018,8 +2032,12 @@ static int noalloc_setup(int32_t** ptr) {
 
 int transfer_noalloc(int dim, int K, const int32_t* orders_from, const int32_t* orders_to, int nvar,
                      const double* in, double* out, cudaStream_t st) {
-  if ((dim != 2 && dim != 3) || K < 1 || nvar < 1 || !orders_from || !orders_to || !in || !out) {
+  if ((dim != 2 && dim != 3) || K < 1 || !orders_from || !orders_to || !in || !out) {
     set_error("dg_transfer_noalloc: bad argument");
+    return DG_EINVAL;
+  }
+  if (nvar < 1 || nvar > kNoAllocMaxVars) {  // keeps nodes x nvar far inside 32 bits in the kernel
+    set_error("dg_transfer_noalloc: nvar must lie in [1, " + std::to_string(kNoAllocMaxVars) + "]");
     return DG_EINVAL;
   }
   if (K > kNoAllocMaxElems) {

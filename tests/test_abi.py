@@ -25,7 +25,10 @@ def declared_functions():
 
 def test_header_declares_the_boundary():
     names = declared_functions()
-    for must in ["dg_mesh_create", "dg_residual", "dg_pmg_vcycle", "dg_tau_estimate", "dg_adapt"]:
+    # the calls of the boundary: mesh with an order map, residual, V-cycle,
+    # tau estimate, adaptation, steady solve
+    for must in ["dg_mesh_create", "dg_mesh_layout", "dg_mesh_destroy", "dg_residual", "dg_pmg_vcycle",
+                 "dg_tau_estimate", "dg_adapt", "dg_solve_steady"]:
         assert must in names
 
 
@@ -44,3 +47,17 @@ def test_binding_fails_loudly_without_gpu(built):
     mesh = syn.periodic_box(1, 1, 1)
     with pytest.raises(built.DGError):
         built.Mesh(mesh, syn.uniform_orders(1, 3, 2), syn.flow_params())
+
+
+def test_noalloc_transfer_rejects_bad_nvar_before_any_device_call(built):
+    """The allocation-free transfer checks its arguments on the host first: a
+    variable count outside [1, 64] is DG_EINVAL with a message, and nothing
+    touches the (here dummy) device pointers."""
+    lib = ctypes.CDLL(built.LIB_PATH)
+    lib.dg_last_error.restype = ctypes.c_char_p
+    o = (ctypes.c_int32 * 6)(1, 1, 0, 2, 2, 0)
+    dummy = ctypes.c_void_p(16)
+    for nvar in (0, 65, 1 << 30):
+        rc = lib.dg_transfer_noalloc(2, 2, o, o, nvar, dummy, dummy, None)
+        assert rc == -1
+        assert b"nvar" in lib.dg_last_error()

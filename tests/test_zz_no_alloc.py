@@ -1,13 +1,15 @@
 """dg_transfer_noalloc -- the transfer for callers that cannot allocate device
 memory -- against the allocating dg_transfer_state, through the C ABI, on two
 calls in a row (the second call reuses the shared static record array the
-first one filled).  Tolerance: 1e-12 of max |q|, as for the other state
+first one filled), and against the oracle's tensor-product L2 projection /
+interpolation (Sec. 3.1).  Tolerance: 1e-12 of max |q|, as for the other state
 comparisons."""
 import ctypes
 
 import numpy as np
 import pytest
 
+from oracle import oracle as orc
 from paper_1806_11456_gb300 import synthetic as syn
 
 pytestmark = pytest.mark.gpu
@@ -55,12 +57,16 @@ def test_noalloc_transfer_matches_allocating_transfer_two_calls(dg, dim):
     torch.cuda.synchronize()
     scale = float(q1.abs().max())
     assert float((out12 - ref12).abs().max()) <= TOL * scale
+    want12 = orc.transfer(dim, o1, o2, q1.cpu().numpy())
+    assert float(np.max(np.abs(out12.cpu().numpy() - want12))) <= TOL * scale
     # second call in a row: o2 -> o3 on the first call's output
     ref23 = B.transfer_state_to(C, ref12)
     out23 = torch.full((5 * C.nodes,), float("nan"), dtype=torch.float64, device="cuda")
     assert _noalloc(dg, dim, o2, o3, out12, out23) == 0
     torch.cuda.synchronize()
     assert float((out23 - ref23).abs().max()) <= TOL * scale
+    want23 = orc.transfer(dim, o2, o3, want12)
+    assert float(np.max(np.abs(out23.cpu().numpy() - want23))) <= TOL * scale
 
 
 def test_noalloc_rejects_more_elements_than_its_limit(dg):
