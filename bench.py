@@ -722,10 +722,14 @@ def run_gb300(args, rank, world):
     vol_ms = prof["volume"]
     achieved = flops / (vol_ms * 1e-3) / 1e12
     residual_ms = sum(stages.values())
+    rates = dg.measure_fma_rates()  # FP64 / FP32 FMA probe on this device, right after the timed steps
     roof = {"kernel": "k_volume", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
             "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": captured_traffic(),
             "traffic_unit": "DRAM bytes per launch (ncu capture of the current kernel source, else null)",
             "peak_source": "FP64 nominal derived: 2 DFMA/clk/SM x 152 SMs x 2070 MHz",
+            "peak_measured": rates["fp64_tflops"], "frac_measured": achieved / rates["fp64_tflops"],
+            "peak_measured_source": "dg_measure_fma_rates: independent FP64 FMA chains on every SM, best of 3",
+            "fp32_peak_measured": rates["fp32_tflops"],
             "flops_per_launch": flops, "ms_per_launch": vol_ms, "dominant_stage": dom,
             "stage_ms": prof, "residual_dof_per_s": 5.0 * nodes / (residual_ms * 1e-3)}
 

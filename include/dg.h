@@ -455,6 +455,16 @@ int dg_set_autotune(dg_mesh* mesh, int on, void* stream);
  * elements, out[1..3] CTA sizes of the three launch classes. */
 int dg_mesh_tuning(const dg_mesh* mesh, int32_t* out);
 
+/*
+ * dg_measure_fma_rates -- measurement aid (the paper has no counterpart): the
+ * device's fused multiply-add throughput in FP64 and in FP32, in TFLOP/s
+ * (an FMA counts 2 flops), best of three timed launches of independent FMA
+ * chains on every SM (CUDA events on `stream`).  These are the denominators
+ * of the roofline of the ALU-bound operator kernels.  Allocates and frees a
+ * small device buffer; takes about 0.2 s; synchronises the stream.
+ */
+int dg_measure_fma_rates(double* fp64_tflops, double* fp32_tflops, void* stream);
+
 /* dg_kernel_launches -- cumulative number of CUDA kernels this library has
  * launched in the process (host-side count; a measurement aid). */
 int dg_kernel_launches(int64_t* count);

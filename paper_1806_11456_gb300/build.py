@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdgpmg.so")
-SOURCES = ["dg_kernels.cu", "dg_mesh.cpp", "dg_api.cpp", "dg_server.cpp"]
+SOURCES = ["dg_kernels.cu", "dg_peaks.cu", "dg_mesh.cpp", "dg_api.cpp", "dg_server.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
           "-I", os.path.join(HERE, "..", "include")]

@@ -1092,6 +1092,16 @@ int dg_solve_steady(dg_mesh** meshp, double** qp, const double* s, const dg_solv
   });
 }
 
+int dg_measure_fma_rates(double* fp64_tflops, double* fp32_tflops, void* stream) {
+  return guarded([&]() -> int {
+    if (!fp64_tflops || !fp32_tflops) {
+      set_error("dg_measure_fma_rates: null argument");
+      return DG_EINVAL;
+    }
+    return measure_fma_rates(fp64_tflops, fp32_tflops, S(stream));
+  });
+}
+
 int dg_transfer_noalloc(int32_t dim, int32_t K, const int32_t* orders_from, const int32_t* orders_to,
                         int32_t nvar, const double* in, double* out, void* stream) {
   return guarded([&]() -> int {

@@ -249,5 +249,7 @@ int read_scalar(const double* d, double* h, cudaStream_t st);
 int transfer_noalloc(int dim, int K, const int32_t* orders_from, const int32_t* orders_to, int nvar,
                      const double* in, double* out, cudaStream_t st);
 int reset_max(double* d, cudaStream_t st);
+// FMA rates of the current device in TFLOP/s (dg_peaks.cu)
+int measure_fma_rates(double* fp64_tflops, double* fp32_tflops, cudaStream_t st);
 int reset_min(double* d, cudaStream_t st);
 }  // namespace dg

@@ -87,7 +87,7 @@ EXPORTS = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_layout", "dg_residual",
            "dg_kernel_launches", "dg_transfer_noalloc", "dg_solve_steady", "dg_mesh_orders", "dg_set_arithmetic",
            "dg_batch_create", "dg_batch_info", "dg_residual_norms", "dg_solve_footprint", "dg_server_create",
            "dg_server_submit", "dg_server_wait", "dg_server_info", "dg_server_result", "dg_server_release",
-           "dg_server_destroy", "dg_set_autotune", "dg_mesh_tuning", "dg_last_error"]
+           "dg_server_destroy", "dg_set_autotune", "dg_mesh_tuning", "dg_measure_fma_rates", "dg_last_error"]
 ARITH = {"fp64": 0, "df32": 1}
 KERNEL_STAGES = ["trace_q", "mortar_u_star", "volume", "mortar_flux", "surface", "isolated"]
 
@@ -132,6 +132,7 @@ def lib(path=LIB_PATH):
     L.dg_server_result.argtypes = [_vp, ctypes.c_int64, _dp, _ip]
     L.dg_server_release.argtypes = [_vp, ctypes.c_int64]
     L.dg_server_destroy.argtypes = [_vp]
+    L.dg_measure_fma_rates.argtypes = [_dp, _dp, _vp]
     _lib = L
     return L
 
@@ -154,6 +155,17 @@ def _stream(stream):
     import torch
     s = torch.cuda.current_stream() if stream is None else stream
     return ctypes.c_void_p(s.cuda_stream)
+
+
+def measure_fma_rates(stream=None):
+    """FP64 and FP32 FMA throughput of the current device in TFLOP/s."""
+    import torch
+    if not torch.cuda.is_available():
+        raise DGError("no CUDA device: the DGSEM library has no CPU path")
+    L = lib()
+    f64, f32 = ctypes.c_double(), ctypes.c_double()
+    _check(L.dg_measure_fma_rates(ctypes.byref(f64), ctypes.byref(f32), _stream(stream)))
+    return {"fp64_tflops": f64.value, "fp32_tflops": f32.value}
 
 
 def kernel_launches():

@@ -4,6 +4,7 @@ solve inside a batch must advance exactly as it does alone."""
 import numpy as np
 import pytest
 
+from oracle import oracle as orc
 from paper_1806_11456_gb300 import synthetic as syn
 
 pytestmark = pytest.mark.gpu
@@ -77,6 +78,9 @@ def test_batch_equals_alone(dg, kind, arith):
         ra = ra.cpu().numpy()
         assert np.array_equal(rb[5 * off[k]:5 * off[k + 1]], ra)
         assert norms[k] == na
+        if k == 0:  # and the batched residual is the oracle's (Sec. 2), element by element
+            ro = orc.residual(m, o, p, q)
+            assert np.max(np.abs(rb[5 * off[k]:5 * off[k + 1]] - ro)) <= 1e-12 * orc.volume_scale(m, o, p, q)
     # V-cycles (graph replay) and the explicit time step per solve
     B.vcycle(qb, None, graph=True, **kw)
     B.vcycle(qb, None, graph=True, **kw)
@@ -87,6 +91,10 @@ def test_batch_equals_alone(dg, kind, arith):
         A.vcycle(qa, None, **kw)
         A.vcycle(qa, None, **kw)
         assert np.array_equal(qbn[5 * off[k]:5 * off[k + 1]], qa.cpu().numpy()), k
+        if k == 0 and kind == "2d":  # two batched V-cycles against Algorithm 1 in the oracle
+            qo = orc.fas_vcycle(m, o, p, q, None, kw["beta1"], kw["beta2"], kw["beta_c"])
+            qo = orc.fas_vcycle(m, o, p, qo, None, kw["beta1"], kw["beta2"], kw["beta_c"])
+            assert np.max(np.abs(qbn[5 * off[k]:5 * off[k + 1]] - qo)) <= 1e-12 * np.max(np.abs(qo))
 
 
 def test_batch_steady_solve_reports_every_solve(dg):

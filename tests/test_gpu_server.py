@@ -3,6 +3,7 @@ budget.  Each solve must give the same bits in the mix as alone."""
 import numpy as np
 import pytest
 
+from oracle import oracle as orc
 from paper_1806_11456_gb300 import synthetic as syn
 
 pytestmark = pytest.mark.gpu
@@ -64,6 +65,11 @@ def test_server_results_equal_alone(dg):
             assert np.array_equal(os_, oa)
             assert np.array_equal(qs, qa), rid
             assert info["rep"]["cycles"] == rep["cycles"]
+            if rid == ids[0]:  # the served solve against the oracle's steady driver (Sec. 3.1.1)
+                oo, qo, orep = orc.solve_steady(m, o, p, q, s, kw["tol"], kw["max_cycles"], MG, fmg=True,
+                                                fmg_tol=kw["fmg_tol"])
+                assert np.array_equal(oo, os_) and orep["cycles"] == info["rep"]["cycles"]
+                assert np.max(np.abs(qs - qo)) <= 1e-12 * np.max(np.abs(qo))
             S.release(rid)
 
 
