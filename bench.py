@@ -191,35 +191,15 @@ def run_reference(args, rank):
 def steady_problem(dg, torch, dev, mesh, o, prm, q_target, seed, amp=0.01):
     """A steady problem whose discrete solution is q_target: S = A(q_target),
     evaluated by the library (the residual with no source is -A), and a
-    start q_target + amp * |q_target| * w with w a smooth periodic wave
-    sin(2 pi (x + 2y) + phase_v), seeded phases (resolved on every mesh here,
-    including the one-element-thick 4x4x1 box).  On a periodic mesh the
-    pseudo-time iteration conserves the discrete totals of the five
-    variables, so w is given zero weighted mean per variable (Gauss weights;
-    the meshes here have equal elements).  Per-node noise as the start does
-    not converge to 1e-10 with the fixed-count cycle on these boxes (it
-    stalls near 1e-5), a smooth perturbation does in a few hundred cycles."""
+    start q_target plus a smooth zero-mean wave (synthetic.zero_mean_wave).
+    Per-node noise as the start does not converge to 1e-10 with the
+    fixed-count cycle on these boxes (it stalls near 1e-5), a smooth
+    perturbation does in a few hundred cycles."""
     from paper_1806_11456_gb300 import synthetic as syn
     M = dg.Mesh(mesh, o, prm)
     r = M.residual(torch.tensor(q_target, device=dev))
     S = (-r).cpu().numpy()
-    rng = np.random.default_rng(seed)
-    dim = mesh["dim"]
-    nn, off = syn.layout_offsets(o, dim)
-    W = []
-    for e in range(mesh["K"]):
-        w = np.ones(1)
-        for d in range(dim):
-            w = np.multiply.outer(np.polynomial.legendre.leggauss(int(o[e, d]) + 1)[1], w)
-        W.append(w.reshape(-1))
-    W = np.concatenate(W)
-    X = syn.node_coordinates(mesh, o)
-    phase = rng.uniform(0.0, 2.0 * np.pi, 5)
-    wave = np.stack([np.sin(2.0 * np.pi * (X[:, 0] + 2.0 * X[:, 1]) + phase[v]) for v in range(5)])
-    wave -= (wave @ W / W.sum())[:, None]
-    scale = np.abs(syn.from_blocked(q_target, o, dim)).max(axis=1)[:, None]
-    q0 = q_target + amp * syn.to_blocked(wave * scale, o, dim)
-    return S, q0
+    return S, syn.zero_mean_wave(mesh, o, q_target, seed, amp)
 
 
 def time_to_tolerance(dg, torch, dev, tol=1e-10, max_cycles=3000):
@@ -227,13 +207,14 @@ def time_to_tolerance(dg, torch, dev, tol=1e-10, max_cycles=3000):
     (N = 3, Mach 0.3, Re 100) whose discrete solution is the manufactured
     field: S = A(q*), start q* plus a 1% smooth zero-mean wave; repeated
     V-cycles 3 -> 1 (3/3/10 sweeps), CUDA graphs, a residual check every 10
-    cycles; FP64 and double-float."""
+    cycles; FP64, double-float and the mixed form (FP64 residual, FP32
+    tangent-linear correction cycle)."""
     from paper_1806_11456_gb300 import synthetic as syn
     mesh, o, prm, q_star = syn.manufactured_box_4x4x1()
     S, q0 = steady_problem(dg, torch, dev, mesh, o, prm, q_star, seed=11)
     out = {"workload": "periodic box 4x4x1, N=3, S = A(q*) with q* the manufactured field, start q* + 1% smooth zero-mean wave",
            "tol": tol, "cycle": "V 3->1, 3/3/10 sweeps, graph replay, norm every 10 cycles"}
-    for arith in ("fp64", "df32"):
+    for arith in ("fp64", "df32", "mixed"):
         M = dg.Mesh(mesh, o, prm).set_arithmetic(arith)
         qd = torch.tensor(q0, device=dev)
         sd = torch.tensor(S, device=dev)

@@ -134,14 +134,28 @@ int dg_mesh_layout(const dg_mesh* mesh, int64_t* total_nodes, int64_t* elem_offs
 /* Arithmetic of the operator kernels (dg_set_arithmetic). */
 #define DG_ARITH_FP64 0 /* native FP64 */
 #define DG_ARITH_DF32 1 /* double-float: pairs of FP32 numbers, ~48-bit significands, on the FP32 pipes */
+#define DG_ARITH_MIXED 2 /* FP64 defect, FP32 tangent-linear correction cycle (see dg_set_arithmetic) */
 
 /*
- * dg_set_arithmetic -- choose how the operator kernels (residual, isolated
- * residual, tau) evaluate A(Q): DG_ARITH_FP64 (default) or DG_ARITH_DF32.
+ * dg_set_arithmetic -- choose how the operator kernels evaluate A(Q):
+ *  DG_ARITH_FP64 (default) native FP64 everywhere.
+ *  DG_ARITH_DF32  double-float on every level (residual, isolated residual,
+ *                 tau, smoother).
+ *  DG_ARITH_MIXED precision by role: FP64 for the finest-level residual (the
+ *                 one that defines convergence and feeds every residual check
+ *                 and dg_residual), for the right-hand sides of the coarse
+ *                 problems, and for the tau estimate (a difference of
+ *                 residuals that cancels); FP32 for every smoother sweep and
+ *                 every coarse-level operator evaluation.  dg_pmg_vcycle then
+ *                 runs a defect-correction cycle: r = S - A(Q) in FP64, one
+ *                 V-cycle of Algorithm 1's shape (same levels, sweeps and L2
+ *                 transfers) on the linearised problem J(Q) d = r with the
+ *                 Jacobian-vector products J(I Q) d evaluated in FP32 tangent
+ *                 arithmetic (their rounding error scales with |d|, so the
+ *                 cycle converges to the FP64 solution), and Q += d.  Fixed
+ *                 sweep counts only (mg->control must be 0).
  * Memory formats do not change (FP64 state, source and residual arrays) and
- * the smoother's state update stays FP64; only the arithmetic inside the
- * operator changes.  Applies to every level of the mesh; cached V-cycle
- * graphs are dropped.
+ * the smoother's state update stays FP64.  Cached V-cycle graphs are dropped.
  */
 int dg_set_arithmetic(dg_mesh* mesh, int mode);
 
@@ -159,6 +173,17 @@ int dg_mesh_orders(const dg_mesh* mesh, int32_t* orders_out);
  */
 int dg_residual(dg_mesh* mesh, const double* q, const double* s, double* r, int flags,
                 double* rnorm_host, void* stream);
+
+/*
+ * dg_residual_tangent -- the linearised residual r = b - J(q) dq, J(q) the
+ * Jacobian of the operator A at q (Sec. 3.1, nonlinRes, linearised; the
+ * correction equation of the mixed-precision cycle), evaluated in FP32
+ * tangent arithmetic: every operation of the DGSEM operator carries the
+ * directional derivative along dq.  Inputs and output are FP64.
+ *  q, dq   device arrays (5 x total_nodes): linearisation point and
+ *          correction.  b: device array or NULL for 0.  r may alias neither.
+ */
+int dg_residual_tangent(dg_mesh* mesh, const double* q, const double* dq, const double* b, double* r, void* stream);
 
 /*
  * dg_cfl_dt -- the explicit time step of Sec. 2: minimum over Gauss points

@@ -14,6 +14,12 @@ Sections of the paper each function follows:
                                  Sec. 3.3.1 (anisotropic coarsening)
   adapt_orders                   Sec. 3.3.2 (six-step order selection),
                                  Sec. 4.1.2 / 4.2.1 (order-jump rules)
+  tangent_residual, mixed_vcycle the linearised residual b - J(q) dq (Sec. 3.1,
+                                 nonlinRes, differentiated along dq) and the
+                                 library's mixed-precision defect-correction
+                                 cycle built on it; not a method of the paper
+                                 but a restatement, for parity, of how the
+                                 library splits precision around Algorithm 1
 """
 from __future__ import annotations
 
@@ -109,6 +115,15 @@ def volume_scale(mesh, orders, prm, q):
     lib().or_residual(mesh["dim"], mesh["K"], mesh["M"], _d(mesh["xmap"]), _i(mesh["ftab"]), _i(orders),
                       _d(prm), _d(q), ctypes.cast(None, _dp), r.ctypes.data_as(_dp), 2)
     return float(np.max(np.abs(r)))
+
+
+def volume_term(mesh, orders, prm, q):
+    """The volume term of A(q) alone (M^{-1} of the volume integral)."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    r = np.zeros_like(q)
+    lib().or_residual(mesh["dim"], mesh["K"], mesh["M"], _d(mesh["xmap"]), _i(mesh["ftab"]), _i(orders),
+                      _d(prm), _d(q), ctypes.cast(None, _dp), r.ctypes.data_as(_dp), 2)
+    return -r
 
 
 def gradients(mesh, orders, prm, q):
@@ -274,6 +289,71 @@ def fas_vcycle(mesh, orders, prm, q, s, beta1, beta2, beta_c, direction=None, co
         return q - q0
 
     return cycle(top, q.copy(), s, True)
+
+
+# ---------------------------------------------------------------------------
+# linearised residual and the mixed-precision defect-correction cycle
+# ---------------------------------------------------------------------------
+TANGENT_STEP = 1e-4  # finite-difference step, relative to max|q| / max|dq|
+
+
+def directional_derivative(f, q, dq, step=TANGENT_STEP):
+    """d/dh f(q + h dq) at h = 0 by the fourth-order central difference
+    (-f(q+2h) + 8 f(q+h) - 8 f(q-h) + f(q-2h)) / (12 h), with h dq a
+    relative perturbation of size `step` of q."""
+    nq, nd = float(np.max(np.abs(q))), float(np.max(np.abs(dq)))
+    if nd == 0.0:
+        return np.zeros_like(q)
+    h = step * nq / nd
+    return (-f(q + 2 * h * dq) + 8 * f(q + h * dq) - 8 * f(q - h * dq) + f(q - 2 * h * dq)) / (12 * h)
+
+
+def tangent_residual(mesh, orders, prm, q, dq, b=None):
+    """b - J(q) dq, J the Jacobian of A at q, by directional differences of
+    the residual (b None = 0)."""
+    Jdq = directional_derivative(lambda x: operator_A(mesh, orders, prm, x), q, dq)
+    return (0.0 if b is None else b) - Jdq
+
+
+def mixed_vcycle(mesh, orders, prm, q, s, beta1, beta2, beta_c, direction=None, coarsest=1, delta_n=1):
+    """One defect-correction cycle: r = S - A(q) at the finest level, one
+    V-cycle of Algorithm 1's shape (levels, sweeps, RK3 smoother, L2
+    restriction and prolongation) on the linearised problem J d = r in which
+    level l is linearised at the restriction of q, its right-hand side is the
+    restriction of the finer level's linear residual b - J d, and its
+    correction starts from 0; then q + d.  The RK3 step of a level comes from
+    its linearisation point.  Returns the new q."""
+    dim = mesh["dim"]
+    top = n_levels(orders, dim, direction)
+    seq = [top]
+    while seq[-1] - delta_n >= coarsest:
+        seq.append(seq[-1] - delta_n)
+    lv_orders = {lv: level_orders(orders, lv, dim, direction) for lv in seq}
+
+    def smooth_linear(o, base, d, b, sweeps):
+        dt = cfl_dt(mesh, o, prm, base)
+        for _ in range(sweeps):
+            g = np.zeros_like(d)
+            for k in range(3):
+                rk = tangent_residual(mesh, o, prm, base, d, b)
+                g = RK3_A[k] * g + dt * rk
+                d = d + RK3_B[k] * g
+        return d
+
+    def cycle(k, base, b):
+        o = lv_orders[seq[k]]
+        d = np.zeros_like(base)
+        if k + 1 == len(seq):
+            return smooth_linear(o, base, d, b, beta_c)
+        oc = lv_orders[seq[k + 1]]
+        d = smooth_linear(o, base, d, b, beta1)
+        rl = tangent_residual(mesh, o, prm, base, d, b)
+        dc = cycle(k + 1, transfer(dim, o, oc, base), transfer(dim, o, oc, rl))
+        d = d + transfer(dim, oc, o, dc)
+        return smooth_linear(o, base, d, b, beta2)
+
+    r = residual(mesh, orders, prm, q, s)
+    return q + cycle(0, q, r)
 
 
 # ---------------------------------------------------------------------------

@@ -76,6 +76,7 @@ struct Cycle {
   std::vector<Level*> lv;  // lv[k]: k-th level from the top (lv[0] = finest)
   int evals = 0;
   double dofs = 0.0;
+  const double* q_fine = nullptr;  // mixed-precision cycle: the finest state (linearisation point)
 };
 
 // `sweeps` RK3 sweeps; with a mask (per slot 1/0, device) the slots whose
@@ -197,6 +198,69 @@ static int vcycle_level(Cycle& C, size_t k, double* Qf, const double* Sf) {
   return DG_OK;
 }
 
+// ---------------------------------------------------------------------------
+// mixed precision: FP64 defect, FP32 tangent-linear correction cycle
+// ---------------------------------------------------------------------------
+// One mixed cycle is a defect correction.  The finest residual r = S - A(Q)
+// is formed in FP64 (it is also the residual that defines convergence); a
+// V-cycle with the levels, sweeps and transfers of Algorithm 1 then solves
+// the linearised problem J(Q) d = r approximately, every operator evaluation
+// in it being the Jacobian-vector product J(Q_l) d_l in FP32 tangent
+// arithmetic, whose rounding error scales with |d| (no floor from the FP32
+// evaluation of the full operator); Q += d.  On level l the linearisation
+// point is the restriction of the finest state, Q_l = I Q, and the coarse
+// right-hand side I (b - J d) is formed in FP64 -- the linear counterpart of
+// the FAS source A_c(I Q) + I r, whose A_c(I Q) term cancels against the
+// coarse operator's value at Q_l.  Near convergence the cycle contracts like
+// the FAS cycle; far from it the linearisation error is O(|d|^2).
+static int smooth_tangent(Cycle& C, Level* L, const double* base, double* d, const double* b, int sweeps) {
+  // pseudo-time step of the linear problem from its linearisation point,
+  // fixed during the block
+  double* dt = C.m->d_scalars;
+  if (sweeps > 0) DG_TRY(cfl_dt(C.m, L, base, dt, C.st));
+  for (int k = 0; k < sweeps; ++k)
+    for (int stage = 0; stage < 3; ++stage) {
+      const int tfl = kTracesNext | ((k > 0 || stage > 0) ? kTracesCurrent : 0);
+      DG_TRY(residual_tangent(C.m, L, base, d, b, nullptr, C.st, nullptr, stage, L->d_G, dt, tfl));
+      C.evals++;
+      C.dofs += 5.0 * L->nodes;
+    }
+  return DG_OK;
+}
+
+static int tangent_level(Cycle& C, size_t k) {
+  Level* L = C.lv[k];
+  DG_TRY(ensure_work(L));
+  const double* base = (k == 0) ? C.q_fine : L->d_Q0;
+  double* d = L->d_Q;
+  const double* b = L->d_S;
+  DG_TRY(fill(d, 0.0, 5 * L->nodes, C.st));
+  if (k + 1 == C.lv.size()) return smooth_tangent(C, L, base, d, b, C.mg.beta_c);
+  Level* Cc = C.lv[k + 1];
+  DG_TRY(ensure_work(Cc));
+  DG_TRY(smooth_tangent(C, L, base, d, b, C.mg.beta1));
+  DG_TRY(residual_tangent(C.m, L, base, d, b, L->d_R, C.st, nullptr, -1, nullptr, nullptr));
+  C.evals++;
+  C.dofs += 5.0 * L->nodes;
+  DG_TRY(transfer(C.m, L, Cc, 5, L->d_R, Cc->d_S, C.st));  // coarse right-hand side I (b - J d), FP64
+  DG_TRY(transfer(C.m, L, Cc, 5, base, Cc->d_Q0, C.st));   // coarse linearisation point I Q
+  DG_TRY(tangent_level(C, k + 1));
+  DG_TRY(transfer(C.m, Cc, L, 5, Cc->d_Q, d, C.st, nullptr, true));  // d += I d_c
+  DG_TRY(smooth_tangent(C, L, base, d, b, C.mg.beta2));
+  return DG_OK;
+}
+
+static int mixed_cycle(Cycle& C, double* Q, const double* Sv) {
+  Level* L = C.lv[0];
+  DG_TRY(ensure_work(L));
+  DG_TRY(residual(C.m, L, Q, Sv, L->d_S, false, C.st, nullptr, -1, nullptr, nullptr));  // FP64 defect
+  C.evals++;
+  C.dofs += 5.0 * L->nodes;
+  C.q_fine = Q;
+  DG_TRY(tangent_level(C, 0));
+  return axpby(Q, 1.0, L->d_Q, 1.0, 5 * L->nodes, C.st);  // Q += d
+}
+
 static std::vector<int32_t> capped(const std::vector<int32_t>& o, int dim, int level, int direction) {
   std::vector<int32_t> r = o;
   size_t K = o.size() / 3;
@@ -257,8 +321,13 @@ static int run_vcycle(dg_mesh* m, const std::vector<int32_t>& top_orders, double
   DG_TRY(cycle_levels(m, top_orders, mg, &C.lv));
   *nlev = (int)C.lv.size();
   for (Level* L : C.lv) DG_TRY(prepare_arith(m, L, st));  // never allocate inside a capture
+  const bool mixed = m->arith == DG_ARITH_MIXED;
+  if (mixed && mg.control > 0) {
+    set_error("the mixed-precision cycle runs fixed sweep counts (control = 0)");
+    return DG_EINVAL;
+  }
   if (!mg.graph || mg.control > 0) {  // controlled sweep counts are decided on the host
-    DG_TRY(vcycle_level(C, 0, Q, Sv));
+    DG_TRY(mixed ? mixed_cycle(C, Q, Sv) : vcycle_level(C, 0, Q, Sv));
     *evals = C.evals;
     *dofs = C.dofs;
     return DG_OK;
@@ -275,7 +344,7 @@ static int run_vcycle(dg_mesh* m, const std::vector<int32_t>& top_orders, double
     unsigned long long l0 = launches();
     std::unique_lock<std::mutex> lock(device_sync_mutex());  // no cudaFree elsewhere while capturing
     DG_CUDA_TRY(cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal));
-    int rc = vcycle_level(G, 0, Q, Sv);
+    int rc = mixed ? mixed_cycle(G, Q, Sv) : vcycle_level(G, 0, Q, Sv);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(m->cap_stream, &graph);
     lock.unlock();
@@ -661,6 +730,7 @@ int dg_mesh_destroy(dg_mesh* m) {
       if (m->d_orders) cudaFree(m->d_orders);
       if (m->d_gas64) cudaFree(m->d_gas64);
       if (m->d_gas32x2) cudaFree(m->d_gas32x2);
+      if (m->d_gastf) cudaFree(m->d_gastf);
       if (m->d_gasd) cudaFree(m->d_gasd);
     }
     delete m;  // the levels lock again while they free
@@ -715,7 +785,7 @@ int dg_mesh_layout(const dg_mesh* m, int64_t* total_nodes, int64_t* elem_offsets
 
 int dg_set_arithmetic(dg_mesh* m, int mode) {
   return guarded([&]() -> int {
-    if (!m || (mode != DG_ARITH_FP64 && mode != DG_ARITH_DF32)) {
+    if (!m || (mode != DG_ARITH_FP64 && mode != DG_ARITH_DF32 && mode != DG_ARITH_MIXED)) {
       set_error("dg_set_arithmetic: bad argument");
       return DG_EINVAL;
     }
@@ -772,6 +842,16 @@ int dg_residual(dg_mesh* m, const double* q, const double* s, double* r, int fla
       *rnorm_host = mx;
     }
     return DG_OK;
+  });
+}
+
+int dg_residual_tangent(dg_mesh* m, const double* q, const double* dq, const double* b, double* r, void* stream) {
+  return guarded([&]() -> int {
+    if (!m || !q || !dq || !r || r == q || r == dq) {
+      set_error("dg_residual_tangent: null or aliased arrays");
+      return DG_EINVAL;
+    }
+    return residual_tangent(m, m->fine.get(), q, dq, b, r, S(stream), nullptr, -1, nullptr, nullptr);
   });
 }
 

@@ -151,6 +151,9 @@ struct Level {
   double* d_geo2 = nullptr;             // float-pair copies for the double-float kernels (lazy)
   double* d_fnS2 = nullptr;
   double* d_mnS2 = nullptr;
+  double* d_geoT = nullptr;             // value-only float pairs for the tangent kernels (lazy)
+  double* d_fnST = nullptr;
+  double* d_mnST = nullptr;
   std::vector<int32_t> nvec_host;       // K x 3 node counts (host copy)
   // multigrid work arrays (allocated on first use)
   double *d_Q = nullptr, *d_S = nullptr, *d_Q0 = nullptr, *d_G = nullptr, *d_R = nullptr;
@@ -174,6 +177,7 @@ struct dg_mesh {
   std::vector<int32_t> slot_elem_off;         // nslots + 1
   void* d_gas64 = nullptr;       // per-slot gas constants (FP64)
   void* d_gas32x2 = nullptr;     // per-slot gas constants (float pairs)
+  void* d_gastf = nullptr;       // per-slot gas constants (tangent pairs, derivative 0)
   dg::GasD* d_gasd = nullptr;    // per-slot CFL constants
   std::vector<int32_t> orders;
   std::unique_ptr<dg::Level> fine;
@@ -231,6 +235,13 @@ int residual(const dg_mesh* m, Level* L, const double* q, const double* s, doubl
              cudaStream_t st, double* d_norm, int rk_stage, double* rk_g, const double* d_dt,
              int trace_flags = 0, double* dt_next = nullptr);
 int cfl_dt(const dg_mesh* m, Level* L, const double* q, double* d_dt, cudaStream_t st);
+// The linearised residual r = b - J(base) dq with J the Jacobian of the
+// operator A at `base`, evaluated in FP32 tangent arithmetic (the correction
+// solves of the mixed-precision cycle); the RK arguments as in residual()
+// (an RK stage updates dq in place).
+int residual_tangent(const dg_mesh* m, Level* L, const double* base, const double* dq, const double* b, double* r,
+                     cudaStream_t st, double* d_norm, int rk_stage, double* rk_g, const double* d_dt,
+                     int trace_flags = 0);
 int profile_residual(const dg_mesh* m, Level* L, const double* q, const double* s, double* r, int iters,
                      double* ms_out, cudaStream_t st);
 int transfer(const dg_mesh* m, const Level* from, const Level* to, int nvar, const double* in, double* out,

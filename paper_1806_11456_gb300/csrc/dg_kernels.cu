@@ -56,6 +56,11 @@ __constant__ DevTables2 c_tab2;
 __constant__ float2* c_Dhat2;
 __constant__ float2* c_D2;
 __constant__ float2* c_T2;
+// the same tables as tangent pairs (value, 0) for the tangent kernels; the
+// boundary interpolation vectors are read from c_tab2's leading parts
+__constant__ float2* c_DhatT;
+__constant__ float2* c_DT;
+__constant__ float2* c_TT;
 
 static float2 split2(double x) {
   float h = (float)x;
@@ -82,6 +87,7 @@ void add_launches(unsigned long long n) {
 struct DeviceTables {
   double *Dhat = nullptr, *D = nullptr, *T = nullptr;
   float2 *Dhat2 = nullptr, *D2 = nullptr, *T2 = nullptr;
+  float2 *DhatT = nullptr, *DT = nullptr, *TT = nullptr;
   bool ready = false;       // tables uploaded and symbols set on this device
   bool smem_ready = false;  // kernel shared-memory attributes set on this device
 };
@@ -160,6 +166,21 @@ int upload_tables() {
   DG_CUDA_TRY(cudaMemcpyToSymbol(c_Dhat2, &dt->Dhat2, sizeof(float2*)));
   DG_CUDA_TRY(cudaMemcpyToSymbol(c_D2, &dt->D2, sizeof(float2*)));
   DG_CUDA_TRY(cudaMemcpyToSymbol(c_T2, &dt->T2, sizeof(float2*)));
+  // value-only pairs (derivative 0) for the tangent arithmetic
+  for (size_t i = 0; i < Dh.size(); ++i) Dh2[i] = make_float2((float)Dh[i], 0.0f);
+  for (size_t i = 0; i < Dc.size(); ++i) Dc2[i] = make_float2((float)Dc[i], 0.0f);
+  for (size_t i = 0; i < Tm.size(); ++i) Tm2[i] = make_float2((float)Tm[i], 0.0f);
+  if (!dt->DhatT) {
+    DG_CUDA_TRY(cudaMalloc(&dt->DhatT, Dh2.size() * sizeof(float2)));
+    DG_CUDA_TRY(cudaMalloc(&dt->DT, Dc2.size() * sizeof(float2)));
+    DG_CUDA_TRY(cudaMalloc(&dt->TT, Tm2.size() * sizeof(float2)));
+  }
+  DG_CUDA_TRY(cudaMemcpy(dt->DhatT, Dh2.data(), Dh2.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  DG_CUDA_TRY(cudaMemcpy(dt->DT, Dc2.data(), Dc2.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  DG_CUDA_TRY(cudaMemcpy(dt->TT, Tm2.data(), Tm2.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  DG_CUDA_TRY(cudaMemcpyToSymbol(c_DhatT, &dt->DhatT, sizeof(float2*)));
+  DG_CUDA_TRY(cudaMemcpyToSymbol(c_DT, &dt->DT, sizeof(float2*)));
+  DG_CUDA_TRY(cudaMemcpyToSymbol(c_TT, &dt->TT, sizeof(float2*)));
   dt->ready = true;
   return DG_OK;
 }
@@ -178,6 +199,10 @@ DEV double cst<double>(float x) {
 template <>
 DEV dd cst<dd>(float x) {
   return dd(x, 0.0f);
+}
+template <>
+DEV tf cst<tf>(float x) {
+  return tf(x, 0.0f);
 }
 
 // Gas constants in R (split into float pairs on the host for R = dd).
@@ -207,6 +232,13 @@ dd host_r<dd>(double x) {
   dd v;
   v.hi = (float)x;
   v.lo = (float)(x - (double)v.hi);
+  return v;
+}
+template <>
+tf host_r<tf>(double x) {
+  tf v;
+  v.v = (float)x;
+  v.t = 0.0f;  // constants of the gas do not depend on the state
   return v;
 }
 
@@ -424,6 +456,16 @@ struct Tab<dd> {
   static DEV const float2* Dcol() { return c_D2; }
   static DEV const float2* T() { return c_T2; }
 };
+template <>
+struct Tab<tf> {
+  static DEV tf lp(int n, int j) { return tf(c_tab2.lp[n][j].x, 0.0f); }
+  static DEV tf lm(int n, int j) { return tf(c_tab2.lm[n][j].x, 0.0f); }
+  static DEV tf lpw(int n, int j) { return tf(c_tab2.lpw[n][j].x, 0.0f); }
+  static DEV tf lmw(int n, int j) { return tf(c_tab2.lmw[n][j].x, 0.0f); }
+  static DEV const float2* Dhat() { return c_DhatT; }
+  static DEV const float2* Dcol() { return c_DT; }
+  static DEV const float2* T() { return c_TT; }
+};
 
 // ---------------------------------------------------------------------------
 // shared helpers for element tiles
@@ -442,6 +484,7 @@ struct LevelArgsT {
   const int32_t* tile_elems;
   const int32_t* slot;  // solve slot of each element (batched meshes; all 0 otherwise)
   int dim;
+  const double* base;   // tangent arithmetic: the linearisation point (the state argument is then the correction)
 };
 
 template <typename R>
@@ -460,6 +503,7 @@ LevelArgsT<double> largs<double>(const Level* L) {
   a.tile_elems = L->d_tile_elems;
   a.slot = L->d_slot;
   a.dim = L->dim;
+  a.base = nullptr;
   return a;
 }
 template <>
@@ -476,6 +520,24 @@ LevelArgsT<dd> largs<dd>(const Level* L) {
   a.tile_elems = L->d_tile_elems;
   a.slot = L->d_slot;
   a.dim = L->dim;
+  a.base = nullptr;
+  return a;
+}
+template <>
+LevelArgsT<tf> largs<tf>(const Level* L) {
+  LevelArgsT<tf> a;
+  a.n = L->d_n;
+  a.off = L->d_off;
+  a.geo = reinterpret_cast<const float2*>(L->d_geoT);
+  a.nodes = L->nodes;
+  a.fo = L->d_fo;
+  a.fn = L->face_nodes;
+  a.fnS = reinterpret_cast<const float2*>(L->d_fnST);
+  a.tiles = L->d_tiles;
+  a.tile_elems = L->d_tile_elems;
+  a.slot = L->d_slot;
+  a.dim = L->dim;
+  a.base = nullptr;
   return a;
 }
 
@@ -581,9 +643,8 @@ __global__ void __launch_bounds__(kTileNodes) k_trace_q(LevelArgsT<R> A, const d
   for (int i = threadIdx.x; i < T; i += blockDim.x) {
     int le = i / nn, node = i - le * nn;
     int e = A.tile_elems[t.first + le];
-    const double* qe = q + (size_t)5 * A.off[e];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) sq[v * T + i] = from_double<R>(qe[v * nn + node]);
+    for (int v = 0; v < 5; ++v) sq[v * T + i] = state_value<R>(q, A.base, (size_t)5 * A.off[e] + v * nn + node);
   }
   __syncthreads();
   write_face_traces<R, DIM>(A, t, sq, T, trq);
@@ -606,8 +667,9 @@ static MortarArgsT<R> margs(const Level* L) {
   MortarArgsT<R> a;
   a.mortars = L->d_mortars;
   a.mnode_mortar = L->d_mnode_mortar;
-  a.mnS = std::is_same<R, dd>::value ? reinterpret_cast<const typename Store<R>::T*>(L->d_mnS2)
-                                     : reinterpret_cast<const typename Store<R>::T*>(L->d_mnS);
+  a.mnS = std::is_same<R, dd>::value   ? reinterpret_cast<const typename Store<R>::T*>(L->d_mnS2)
+          : std::is_same<R, tf>::value ? reinterpret_cast<const typename Store<R>::T*>(L->d_mnST)
+                                       : reinterpret_cast<const typename Store<R>::T*>(L->d_mnS);
   a.mnodes = L->mortar_nodes;
   a.tiles = L->d_mtiles;
   return a;
@@ -802,11 +864,10 @@ DEV void stage_tile(const LevelArgsT<R>& A, const ElemTile& t, int nn, int T, co
     int e = A.tile_elems[t.first + le];
     const GasT<R>& G = gas[A.slot[e]];
     const int64_t gn = A.off[e] + node;
-    const double* qe = q + (size_t)5 * A.off[e];
     R qq[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      qq[v] = from_double<R>(qe[v * nn + node]);
+      qq[v] = state_value<R>(q, A.base, (size_t)5 * A.off[e] + v * nn + node);
       sq[v * T + i] = qq[v];
     }
     R ir, u[3], p, Tt;
@@ -1154,7 +1215,7 @@ __global__ void __launch_bounds__(kTileNodes) k_surface(LevelArgsT<R> A, const t
             qn += rk.b * gv;
             rk.qupd[base + v * nn] = qn;
           }
-          if (traces) sq[v * T + i] = from_double<R>(qn);
+          if (traces) sq[v * T + i] = state_of<R>(qn, A.base, base + v * nn);
           qnew[v] = qn;
         }
       }
@@ -1373,6 +1434,13 @@ static int configure_smem() {
   if ((rc = set_attrs<dd, 2, true>()) != DG_OK) return rc;
   if ((rc = set_attrs<dd, 3, false>()) != DG_OK) return rc;
   if ((rc = set_attrs<dd, 3, true>()) != DG_OK) return rc;
+  {
+    const int big = (int)((3 * kNP * kNP + 32 * kMaxElemNodes) * sizeof(double));
+    DG_CUDA_TRY(cudaFuncSetAttribute(k_volume<tf, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    DG_CUDA_TRY(cudaFuncSetAttribute(k_volume<tf, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    DG_CUDA_TRY(cudaFuncSetAttribute(k_volume<tf, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    DG_CUDA_TRY(cudaFuncSetAttribute(k_volume<tf, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  }
   DG_CUDA_TRY(cudaFuncSetAttribute(k_transfer, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)(2 * kTransferMaxSlab * sizeof(double))));
   dt->smem_ready = true;
@@ -1487,6 +1555,29 @@ static int ensure_dd(Level* L, cudaStream_t st) {
   return DG_OK;
 }
 
+// value-only pairs (derivative 0) of a level's geometry for the tangent
+// kernels, made once
+__global__ void k_split_value(const double* __restrict__ x, float2* __restrict__ y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = make_float2((float)x[i], 0.0f);
+}
+static int value_array(const double* x, double** y, int64_t n, cudaStream_t st) {
+  DG_CUDA_TRY(cudaMalloc((void**)y, std::max<int64_t>(1, n) * sizeof(float2)));
+  count_launch();
+  k_split_value<<<grid_for(n), 256, 0, st>>>(x, reinterpret_cast<float2*>(*y), n);
+  DG_CUDA_TRY(cudaGetLastError());
+  return DG_OK;
+}
+static int ensure_tf(Level* L, cudaStream_t st) {
+  if (L->d_geoT) return DG_OK;
+  int rc;
+  if ((rc = value_array(L->d_geo, &L->d_geoT, 10 * L->nodes, st)) != DG_OK) return rc;
+  if ((rc = value_array(L->d_fnS, &L->d_fnST, 3 * L->face_nodes, st)) != DG_OK) return rc;
+  if ((rc = value_array(L->d_mnS, &L->d_mnST, 3 * L->mortar_nodes, st)) != DG_OK) return rc;
+  L->bytes += (int64_t)sizeof(float2) * (10 * L->nodes + 3 * L->face_nodes + 3 * L->mortar_nodes);
+  return DG_OK;
+}
+
 template <typename R>
 static const GasT<R>* gas_table(const dg_mesh* m);
 template <>
@@ -1497,6 +1588,10 @@ template <>
 const GasT<dd>* gas_table<dd>(const dg_mesh* m) {
   return reinterpret_cast<const GasT<dd>*>(m->d_gas32x2);
 }
+template <>
+const GasT<tf>* gas_table<tf>(const dg_mesh* m) {
+  return reinterpret_cast<const GasT<tf>*>(m->d_gastf);
+}
 
 // per-slot gas constants on the device (FP64, float pairs, CFL)
 int upload_gas(dg_mesh* m) {
@@ -1504,10 +1599,12 @@ int upload_gas(dg_mesh* m) {
   std::vector<GasT<double>> g64(S);
   std::vector<GasT<dd>> g2(S);
   std::vector<GasD> gd(S);
+  std::vector<GasT<tf>> gt(S);
   for (int k = 0; k < S; ++k) {
     g64[k] = make_gas<double>(m->slot_prm[k]);
     g2[k] = make_gas<dd>(m->slot_prm[k]);
     gd[k] = make_gas_d(m->slot_prm[k]);
+    gt[k] = make_gas<tf>(m->slot_prm[k]);
   }
   DG_CUDA_TRY(cudaMalloc(&m->d_gas64, S * sizeof(GasT<double>)));
   DG_CUDA_TRY(cudaMalloc(&m->d_gas32x2, S * sizeof(GasT<dd>)));
@@ -1515,11 +1612,15 @@ int upload_gas(dg_mesh* m) {
   DG_CUDA_TRY(cudaMemcpy(m->d_gas64, g64.data(), S * sizeof(GasT<double>), cudaMemcpyHostToDevice));
   DG_CUDA_TRY(cudaMemcpy(m->d_gas32x2, g2.data(), S * sizeof(GasT<dd>), cudaMemcpyHostToDevice));
   DG_CUDA_TRY(cudaMemcpy(m->d_gasd, gd.data(), S * sizeof(GasD), cudaMemcpyHostToDevice));
+  DG_CUDA_TRY(cudaMalloc(&m->d_gastf, S * sizeof(GasT<tf>)));
+  DG_CUDA_TRY(cudaMemcpy(m->d_gastf, gt.data(), S * sizeof(GasT<tf>), cudaMemcpyHostToDevice));
   return DG_OK;
 }
 
 int prepare_arith(const dg_mesh* m, Level* L, cudaStream_t st) {
-  return (m->arith == DG_ARITH_DF32) ? ensure_dd(L, st) : DG_OK;
+  if (m->arith == DG_ARITH_DF32) return ensure_dd(L, st);
+  if (m->arith == DG_ARITH_MIXED) return ensure_tf(L, st);
+  return DG_OK;
 }
 
 // ---- per-kernel launch helpers (arithmetic / dimension / affine dispatch) ----
@@ -1532,10 +1633,11 @@ static ST<R>* buf(double* p) {
 }
 
 template <typename R>
-static void launch_trace(const Level* L, const double* q, cudaStream_t st) {
+static void launch_trace(const Level* L, const double* q, cudaStream_t st, const double* base = nullptr) {
   count_launch();
   const size_t sm = 5 * L->tile_smem_nodes * sizeof(double);
   LevelArgsT<R> A = largs<R>(L);
+  A.base = base;
   if (L->dim == 2)
     k_trace_q<R, 2><<<L->n_tiles, kTileNodes, sm, st>>>(A, q, buf<R>(L->d_trq));
   else
@@ -1560,8 +1662,9 @@ static void for_tile_classes(const Level* L, F launch, int only = -1, int thread
 
 template <typename R>
 static void launch_volume(const Level* L, const GasT<R>* G, const double* q, cudaStream_t st, int only = -1,
-                          int threads_override = 0) {
+                          int threads_override = 0, const double* base = nullptr) {
   LevelArgsT<R> A = largs<R>(L);
+  A.base = base;
   const ST<R>* ust = buf<R>(L->d_ust);
   ST<R>* trg = buf<R>(L->d_trg);
   ST<R>* vol = buf<R>(L->d_vol);
@@ -1599,9 +1702,10 @@ static void launch_isolated(const Level* L, const GasT<R>* G, const double* q, c
 }
 template <typename R>
 static void launch_surface(const Level* L, const double* s, double* r, double* norm, const RKArgs& rk,
-                           cudaStream_t st) {
+                           cudaStream_t st, const double* base = nullptr) {
   count_launch();
   LevelArgsT<R> A = largs<R>(L);
+  A.base = base;
   const size_t sm = rk.trq_next ? 5 * L->tile_smem_nodes * sizeof(double) : 0;
   if (L->dim == 2)
     k_surface<R, 2><<<L->n_tiles, kTileNodes, sm, st>>>(A, buf<R>(L->d_vol), buf<R>(L->d_fst), s, r, norm, rk);
@@ -1639,7 +1743,7 @@ static RKArgs rk_args(int rk_stage, double* rk_g, const double* d_dt, const doub
 template <typename R>
 static int residual_t(const dg_mesh* m, Level* L, const double* q, const double* s, double* r, bool isolated,
                       cudaStream_t st, double* d_norm, int rk_stage, double* rk_g, const double* d_dt,
-                      int trace_flags, double* dt_next) {
+                      int trace_flags, double* dt_next, const double* base = nullptr) {
   const GasT<R>* G = gas_table<R>(m);
   if (isolated) {
     TauArgs ta{nullptr, nullptr, nullptr, 0, 0};
@@ -1647,9 +1751,9 @@ static int residual_t(const dg_mesh* m, Level* L, const double* q, const double*
     DG_CUDA_TRY(cudaGetLastError());
     return DG_OK;
   }
-  if (!(trace_flags & kTracesCurrent)) launch_trace<R>(L, q, st);
+  if (!(trace_flags & kTracesCurrent)) launch_trace<R>(L, q, st, base);
   launch_mortar<R>(1, L, G, st);
-  launch_volume<R>(L, G, q, st);
+  launch_volume<R>(L, G, q, st, -1, 0, base);
   launch_mortar<R>(2, L, G, st);
   RKArgs rk = rk_args(rk_stage, rk_g, d_dt, q);
   if (rk_stage >= 0 && (trace_flags & kTracesNext)) rk.trq_next = buf<R>(L->d_trq);
@@ -1659,9 +1763,18 @@ static int residual_t(const dg_mesh* m, Level* L, const double* q, const double*
     rk.geo64 = L->d_geo;
     rk.nslots = m->nslots;
   }
-  launch_surface<R>(L, s, r, d_norm, rk, st);
+  launch_surface<R>(L, s, r, d_norm, rk, st, base);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
+}
+
+int residual_tangent(const dg_mesh* m, Level* L, const double* base, const double* dq, const double* b, double* r,
+                     cudaStream_t st, double* d_norm, int rk_stage, double* rk_g, const double* d_dt,
+                     int trace_flags) {
+  int rc = configure_smem();
+  if (rc != DG_OK) return rc;
+  if ((rc = ensure_tf(L, st)) != DG_OK) return rc;
+  return residual_t<tf>(m, L, dq, b, r, false, st, d_norm, rk_stage, rk_g, d_dt, trace_flags, nullptr, base);
 }
 
 int residual(const dg_mesh* m, Level* L, const double* q, const double* s, double* r, bool isolated,
@@ -1726,7 +1839,7 @@ __global__ void __launch_bounds__(kTileNodes) k_fill_freestream(LevelArgsT<doubl
 template <typename R>
 static int residual_t(const dg_mesh* m, Level* L, const double* q, const double* s, double* r, bool isolated,
                       cudaStream_t st, double* d_norm, int rk_stage, double* rk_g, const double* d_dt,
-                      int trace_flags, double* dt_next);
+                      int trace_flags, double* dt_next, const double* base);
 
 template <typename R>
 static int tune_t(dg_mesh* m, Level* L, const double* q, cudaStream_t st) {

@@ -384,7 +384,8 @@ Level::~Level() {
   std::lock_guard<std::mutex> lock(device_sync_mutex());  // cudaFree synchronises the device
   void* ptrs[] = {d_n,   d_off,   d_geo,       d_fo,    d_fnS,          d_trq,  d_ust,  d_trg,
                   d_fst, d_mortars, d_mnode_mortar, d_mnS, d_mtiles, d_tile_elems, d_tiles, d_vol,
-                  d_Q,   d_S,     d_Q0,        d_G,     d_R,            d_geo2, d_fnS2, d_mnS2, d_slot};
+                  d_Q,   d_S,     d_Q0,        d_G,     d_R,            d_geo2, d_fnS2, d_mnS2, d_slot,
+                  d_geoT, d_fnST, d_mnST};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }

@@ -8,6 +8,13 @@
 //              FastTwoSum, and the FMA form of TwoProd (Dekker 1971; Knuth,
 //              TAOCP vol. 2, 4.2.2).  Division and square root take one
 //              Newton/Karp correction on top of the FP32 result.
+// R = tf     : a first-order forward-mode (tangent) pair of FP32 numbers:
+//              v, the value at the linearisation point, and t, the
+//              directional derivative along a correction.  Every operation
+//              applies the chain rule, so an operator evaluated on tf
+//              returns J(Q) dQ, its Jacobian applied to a correction, with a
+//              rounding error proportional to |dQ| (the mixed-precision
+//              cycle's correction solves use it).
 // Every kernel loads and stores FP64 in memory; the state update of the
 // smoother stays in FP64.
 #pragma once
@@ -88,6 +95,36 @@ DGR dd sqrt(dd a) {
 }
 DGR dd fabs(dd a) { return (a.hi < 0.0f) ? -a : a; }
 DGR dd fmax(dd a, dd b) { return (a < b) ? b : a; }
+// ---- tangent pairs ----
+struct tf {
+  float v, t;
+  tf() = default;
+  DGR constexpr tf(float a, float b) : v(a), t(b) {}
+};
+DGR tf operator+(tf a, tf b) { return tf(a.v + b.v, a.t + b.t); }
+DGR tf operator-(tf a) { return tf(-a.v, -a.t); }
+DGR tf operator-(tf a, tf b) { return tf(a.v - b.v, a.t - b.t); }
+DGR tf operator*(tf a, tf b) { return tf(a.v * b.v, fmaf(a.v, b.t, a.t * b.v)); }
+DGR tf operator/(tf a, tf b) {
+  const float q = a.v / b.v;
+  return tf(q, (a.t - q * b.t) / b.v);  // (a/b)' = (a' - (a/b) b') / b
+}
+DGR tf madd(tf acc, tf a, tf b) { return tf(fmaf(a.v, b.v, acc.v), fmaf(a.v, b.t, fmaf(a.t, b.v, acc.t))); }
+DGR tf& operator+=(tf& a, tf b) { return a = a + b; }
+DGR tf& operator-=(tf& a, tf b) { return a = a - b; }
+DGR tf& operator*=(tf& a, tf b) { return a = a * b; }
+DGR bool operator<(tf a, tf b) { return a.v < b.v; }
+DGR bool operator>(tf a, tf b) { return a.v > b.v; }
+DGR tf sqrt(tf a) {
+  if (a.v <= 0.0f) return tf(0.0f, 0.0f);
+  const float r = sqrtf(a.v);
+  return tf(r, 0.5f * a.t / r);  // (sqrt a)' = a' / (2 sqrt a)
+}
+DGR tf fabs(tf a) { return (a.v < 0.0f) ? -a : a; }  // |a|' = sign(a) a'
+DGR tf fmax(tf a, tf b) { return (a.v < b.v) ? b : a; }
+// the operator's output in tangent arithmetic is its derivative J(Q) dQ
+DGR double to_double(tf a) { return (double)a.t; }
+
 // the double versions live in the same namespace, so that the dd overloads
 // above do not hide them
 __host__ __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
@@ -112,6 +149,26 @@ template <>
 DGR dd from_double<dd>(double x) {
   return dd(x);
 }
+// A state value for the operator kernels: q[i] in FP64 or double-float; in
+// tangent arithmetic the pair (base[i], q[i]) -- the linearisation point and
+// the correction the Jacobian is applied to.
+template <typename R>
+DGR R state_value(const double* q, const double* base, size_t i) {
+  return from_double<R>(q[i]);
+}
+template <>
+DGR tf state_value<tf>(const double* q, const double* base, size_t i) {
+  return tf((float)base[i], (float)q[i]);
+}
+// the same for a state value already in a register (the smoother's update)
+template <typename R>
+DGR R state_of(double qi, const double* base, size_t i) {
+  return from_double<R>(qi);
+}
+template <>
+DGR tf state_of<tf>(double qi, const double* base, size_t i) {
+  return tf((float)base[i], (float)qi);
+}
 
 // storage type of tables for R (double for R = double, float2 for R = dd)
 template <typename R>
@@ -130,6 +187,17 @@ struct Store<dd> {
     return dd(v.x, v.y);
   }
   static DGR void put(float2* p, size_t i, dd v) { p[i] = make_float2(v.hi, v.lo); }
+};
+// tangent pairs: (value, derivative); tables and geometry are stored with a
+// zero derivative
+template <>
+struct Store<tf> {
+  using T = float2;
+  static DGR tf get(const float2* p, size_t i) {
+    float2 v = p[i];
+    return tf(v.x, v.y);
+  }
+  static DGR void put(float2* p, size_t i, tf v) { p[i] = make_float2(v.v, v.t); }
 };
 
 }  // namespace dg

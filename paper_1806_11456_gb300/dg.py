@@ -87,8 +87,9 @@ EXPORTS = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_layout", "dg_residual",
            "dg_kernel_launches", "dg_transfer_noalloc", "dg_solve_steady", "dg_mesh_orders", "dg_set_arithmetic",
            "dg_batch_create", "dg_batch_info", "dg_residual_norms", "dg_solve_footprint", "dg_server_create",
            "dg_server_submit", "dg_server_wait", "dg_server_info", "dg_server_result", "dg_server_release",
-           "dg_server_destroy", "dg_set_autotune", "dg_mesh_tuning", "dg_measure_fma_rates", "dg_last_error"]
-ARITH = {"fp64": 0, "df32": 1}
+           "dg_server_destroy", "dg_set_autotune", "dg_mesh_tuning", "dg_measure_fma_rates", "dg_residual_tangent",
+           "dg_last_error"]
+ARITH = {"fp64": 0, "df32": 1, "mixed": 2}
 KERNEL_STAGES = ["trace_q", "mortar_u_star", "volume", "mortar_flux", "surface", "isolated"]
 
 
@@ -133,6 +134,7 @@ def lib(path=LIB_PATH):
     L.dg_server_release.argtypes = [_vp, ctypes.c_int64]
     L.dg_server_destroy.argtypes = [_vp]
     L.dg_measure_fma_rates.argtypes = [_dp, _dp, _vp]
+    L.dg_residual_tangent.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
     _lib = L
     return L
 
@@ -304,8 +306,9 @@ class Mesh:
         return dict(pack=int(out[0]), class_threads=[int(x) for x in out[1:]])
 
     def set_arithmetic(self, mode):
-        """'fp64' (native FP64) or 'df32' (double-float pairs on the FP32 pipes)
-        for the operator kernels."""
+        """'fp64' (native FP64), 'df32' (double-float pairs on the FP32 pipes)
+        or 'mixed' (FP64 finest residual, coarse right-hand sides and tau;
+        FP32 tangent-linear correction cycle) for the operator kernels."""
         _check(lib().dg_set_arithmetic(self.h, ARITH[mode]))
         self.arith = mode
         return self
@@ -328,6 +331,15 @@ class Mesh:
         rn = ctypes.c_double(0.0)
         _check(lib().dg_residual(self.h, _ptr(q), _ptr(s), _ptr(r), flags, ctypes.byref(rn), _stream(stream)))
         return (r, rn.value) if norm else r
+
+    def residual_tangent(self, q, dq, b=None, r=None, stream=None):
+        """b - J(q) dq with the operator's Jacobian at q applied in FP32 tangent
+        arithmetic (b None: 0)."""
+        import torch
+        if r is None:
+            r = torch.empty_like(q)
+        _check(lib().dg_residual_tangent(self.h, _ptr(q), _ptr(dq), _ptr(b), _ptr(r), _stream(stream)))
+        return r
 
     def cfl_dt(self, q, stream=None):
         dt = ctypes.c_double()

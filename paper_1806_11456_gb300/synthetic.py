@@ -469,6 +469,49 @@ def perturbed_state(mesh, orders, prm, seed, amp=0.05):
     return to_blocked(conserved(rho, u, v, w, p, gamma), orders, mesh["dim"])
 
 
+def oblique_state(mesh, orders, prm, seed, amp=0.02, vel=(0.8, 0.5, 0.3)):
+    """A uniform flow of velocity `vel` (oblique to every face of an
+    axis-aligned mesh) with independent seeded per-node perturbations of
+    relative size `amp` of rho, the velocity components and p: no face-normal
+    velocity comes near zero, so comparisons of derivatives of the operator
+    stay clear of the kinks of |lambda| in an upwind flux."""
+    dim = mesh["dim"]
+    X = node_coordinates(mesh, orders)
+    g, M = prm[0], prm[2]
+    rng = np.random.default_rng(seed)
+    n = X.shape[0]
+
+    def f(c):
+        return c + amp * rng.uniform(-1, 1, n)
+
+    w = f(vel[2]) if dim == 3 else 0.0 * X[:, 0]
+    return to_blocked(conserved(f(1.0), f(vel[0]), f(vel[1]), w, f(1.0) / (g * M * M), g), orders, dim)
+
+
+def zero_mean_wave(mesh, orders, q_target, seed, amp=0.01):
+    """q_target plus amp * |q_target| * w, w the smooth periodic wave
+    sin(2 pi (x + 2y) + phase_v) with seeded phases (resolved on every mesh
+    used here, including the one-element-thick 4x4x1 box).  On a periodic mesh
+    the pseudo-time iteration conserves the discrete totals of the five
+    variables, so w is given zero weighted mean per variable (Gauss weights;
+    meshes of equal elements)."""
+    rng = np.random.default_rng(seed)
+    dim = mesh["dim"]
+    W = []
+    for e in range(mesh["K"]):
+        w = np.ones(1)
+        for d in range(dim):
+            w = np.multiply.outer(np.polynomial.legendre.leggauss(int(orders[e, d]) + 1)[1], w)
+        W.append(w.reshape(-1))
+    W = np.concatenate(W)
+    X = node_coordinates(mesh, orders)
+    phase = rng.uniform(0.0, 2.0 * np.pi, 5)
+    wave = np.stack([np.sin(2.0 * np.pi * (X[:, 0] + 2.0 * X[:, 1]) + phase[v]) for v in range(5)])
+    wave -= (wave @ W / W.sum())[:, None]
+    scale = np.abs(from_blocked(q_target, orders, dim)).max(axis=1)[:, None]
+    return q_target + amp * to_blocked(wave * scale, orders, dim)
+
+
 def smooth_state(mesh, orders, prm, seed, amp=0.05, wavelength=5.0):
     """Freestream plus smooth seeded perturbations of rho, u, v, w, p: each a
     sum of three plane waves with random directions, wavelength ~ `wavelength`

@@ -78,14 +78,19 @@ def test_benchmarked_tau_table_and_adapted_map_match_the_oracle(dg, plate, plate
     to = orc.tau_estimate(mesh, o, prm, qg, None, dir_mask=3)
     assert np.array_equal(t < 0, to < 0)
     assert np.max(np.abs(t - to)) <= TOL * orc.volume_scale(mesh, o, prm, qg)
-    # adaptation: bit-identical on a shared table, and from each side's own table
+    # adaptation: bit-identical on a shared table, and from each side's own
+    # table.  The per-node perturbation puts every estimate between about 1e2
+    # and 1e5, so the benchmark's threshold keeps N = 7 everywhere; the larger
+    # thresholds give non-uniform maps that exercise the selection and the
+    # jump rule.
     ap = dict(n_min=1, n_max=7, jump_rule=1)
-    want = orc.adapt_orders(mesh, o, to, TAU_MAX, 1, 7, rule="2d")
-    got_shared = M.adapt(to, TAU_MAX, **ap)
-    assert np.array_equal(got_shared, want)
-    got_own = M.adapt(t, TAU_MAX, **ap)
-    assert np.array_equal(got_own, want)
-    assert len({tuple(r[:2]) for r in want}) > 1  # the map is not uniform: the selection is exercised
+    kinds = set()
+    for tau_max in (TAU_MAX, 1e3, 3e3):
+        want = orc.adapt_orders(mesh, o, to, tau_max, 1, 7, rule="2d")
+        assert np.array_equal(M.adapt(to, tau_max, **ap), want)
+        assert np.array_equal(M.adapt(t, tau_max, **ap), want)
+        kinds |= {tuple(r[:2]) for r in want}
+    assert len(kinds) > 5
 
 
 def test_full_sphere_vcycle_matches_the_oracle(dg):

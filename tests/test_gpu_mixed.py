@@ -1,0 +1,157 @@
+"""The mixed-precision form (dg_set_arithmetic 'mixed') against the FP64
+oracle.
+
+Roles: the finest-level residual, the coarse right-hand sides and the tau
+estimate stay FP64 (compared at the FP64 bar, 1e-12 of the term scale); the
+smoother and every coarse-level operator evaluation are FP32 Jacobian-vector
+products J(Q) dQ in tangent arithmetic.  Their bound, per variable v:
+|J dQ (GPU) - J dQ (oracle)|_inf <= TOL_TF * s_v, with s_v the magnitude of
+the tangent's volume term for variable v (max over nodes of the directional
+derivative of the oracle's volume term) -- FP32 rounding of the terms, not of
+the result, which cancels.  The oracle differentiates its FP64 residual by
+fourth-order central differences (accurate to ~1e-9 of the term scale on
+these smooth states); the states are oblique flows, so no face-normal
+velocity sits at the kink of the Roe dissipation's |lambda|.  The mixed
+V-cycle is compared with the oracle's restatement of the same cycle within
+TOL_CYCLE of the size of the correction it applies, and a mixed steady solve
+must satisfy the oracle's FP64 equations to its tolerance."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1806_11456_gb300 import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+TOL_TF = 2e-5
+TOL_CYCLE = 1e-4
+
+
+@pytest.fixture(scope="module")
+def dg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__ as g
+    g.build()
+    from paper_1806_11456_gb300 import dg as mod
+    return mod
+
+
+def _dev(x):
+    import torch
+    return torch.tensor(np.asarray(x, dtype=np.float64), device="cuda")
+
+
+def _cases():
+    c = {}
+
+    def box2d():
+        mesh = syn.periodic_box(3, 3, 1, dim=2)
+        prm = syn.flow_params(mach=0.3, re=100.0)
+        return mesh, syn.random_orders(mesh["K"], 2, 2, 5, 31), prm
+
+    def mortars3d():
+        mesh = syn.periodic_box(3, 2, 2)
+        prm = syn.flow_params(mach=0.3, re=100.0)
+        return mesh, syn.random_orders(mesh["K"], 3, 1, 4, 32), prm
+
+    def plate():
+        mesh = syn.box_mesh(np.linspace(-0.2, 1, 6), [0, 0.01, 0.05, 0.12, 0.3],
+                            bc=dict(xmin=1, xmax=2, ymin=lambda i, k: 3 if i < 1 else 4, ymax=1))
+        prm = syn.flow_params(mach=0.2, re=1e4)
+        return mesh, syn.random_orders(mesh["K"], 2, 1, 6, 33), prm
+
+    def sphere():
+        mesh = syn.rotate_elements(syn.cubed_sphere_mesh(2, 2), seed=5, frac=0.6)
+        prm = syn.flow_params(mach=0.2, re=200.0)
+        return mesh, syn.random_orders(mesh["K"], 3, 1, 4, 34), prm
+
+    c["box2d"], c["mortars3d"], c["plate2d_all_bcs"], c["curved_sphere"] = box2d, mortars3d, plate, sphere
+    return c
+
+
+CASES = _cases()
+
+
+def _tangent_scale(mesh, o, prm, q, dq):
+    """Per-variable magnitude of the tangent's volume term."""
+    dV = orc.directional_derivative(lambda x: orc.volume_term(mesh, o, prm, x), q, dq)
+    return np.abs(syn.from_blocked(dV, o, mesh["dim"])).max(axis=1)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_tangent_residual_matches_the_oracle_derivative(dg, name):
+    mesh, o, prm = CASES[name]()
+    q = syn.oblique_state(mesh, o, prm, 3)
+    rng = np.random.default_rng(4)
+    dq = rng.normal(size=q.size) * 1e-2 * np.abs(q)
+    b = syn.random_source(mesh, o, 5, amp=1e-2)
+    M = dg.Mesh(mesh, o, prm)
+    r = M.residual_tangent(_dev(q), _dev(dq), _dev(b)).cpu().numpy()
+    ro = orc.tangent_residual(mesh, o, prm, q, dq, b)
+    err = np.abs(syn.from_blocked(r - ro, o, mesh["dim"])).max(axis=1)
+    scale = _tangent_scale(mesh, o, prm, q, dq)
+    print(name, "tangent error / scale per variable:", err / scale)
+    assert np.all(err <= TOL_TF * scale), err / scale
+
+
+def test_mixed_mode_keeps_the_fp64_residual_and_tau(dg):
+    """The roles that stay FP64: the residual (convergence) and the tau
+    estimate give the same bits as the FP64 mode."""
+    mesh, o, prm = CASES["box2d"]()
+    q = syn.oblique_state(mesh, o, prm, 6)
+    A = dg.Mesh(mesh, o, prm)
+    B = dg.Mesh(mesh, o, prm).set_arithmetic("mixed")
+    qd = _dev(q)
+    assert np.array_equal(A.residual(qd).cpu().numpy(), B.residual(qd).cpu().numpy())
+    assert np.array_equal(A.tau_estimate(qd, None, dir_mask=3), B.tau_estimate(qd, None, dir_mask=3))
+
+
+@pytest.mark.parametrize("name,kw", [
+    ("box2d", dict(beta1=2, beta2=1, beta_c=3)),
+    ("plate2d_all_bcs", dict(beta1=1, beta2=2, beta_c=2)),
+    ("mortars3d", dict(beta1=1, beta2=1, beta_c=2, delta_n=2)),
+])
+@pytest.mark.parametrize("graph", [False, True])
+def test_mixed_vcycle_matches_the_oracle_cycle(dg, name, kw, graph):
+    mesh, o, prm = CASES[name]()
+    qs = syn.oblique_state(mesh, o, prm, 7, amp=0.01)
+    S = orc.operator_A(mesh, o, prm, qs)          # qs solves A(q) = S
+    q0 = syn.oblique_state(mesh, o, prm, 8, amp=0.01)  # a start near it
+    M = dg.Mesh(mesh, o, prm).set_arithmetic("mixed")
+    qd = _dev(q0)
+    if graph:
+        M.vcycle(qd.clone(), _dev(S), graph=True, **kw)
+    rep = M.vcycle(qd, _dev(S), graph=graph, **kw)
+    qo = orc.mixed_vcycle(mesh, o, prm, q0, S, kw["beta1"], kw["beta2"], kw["beta_c"], delta_n=kw.get("delta_n", 1))
+    corr = np.max(np.abs(qo - q0))
+    assert rep["levels"] >= 2 and corr > 0
+    err = np.max(np.abs(qd.cpu().numpy() - qo))
+    print(name, "mixed cycle error / correction:", err / corr)
+    assert err <= TOL_CYCLE * corr
+
+
+def test_mixed_steady_solve_satisfies_the_fp64_equations(dg):
+    """A steady problem whose discrete solution is known (S = A(q*)): the
+    mixed form cycles until its FP64 residual is below 1e-10; the oracle's
+    FP64 residual of the result is then below that tolerance too (to the
+    parity bar), and the state is q* as closely as the FP64 form gets it."""
+    import torch
+    mesh, o, prm, q_star = syn.manufactured_box_4x4x1()
+    S = orc.operator_A(mesh, o, prm, q_star)
+    q0 = syn.zero_mean_wave(mesh, o, q_star, 11, amp=0.01)
+    out = {}
+    for arith in ("fp64", "mixed"):
+        M = dg.Mesh(mesh, o, prm).set_arithmetic(arith)
+        qd, rep = M.solve_steady(_dev(q0), _dev(S), tol=1e-10, max_cycles=3000,
+                                 mg=dict(beta1=3, beta2=3, beta_c=10), check_every=10)
+        assert rep["status"] == 0, (arith, rep)
+        out[arith] = (qd.cpu().numpy(), rep)
+    qm = out["mixed"][0]
+    ro = orc.residual(mesh, o, prm, qm, S)
+    assert np.max(np.abs(ro)) <= 1e-10 + TOL * orc.volume_scale(mesh, o, prm, qm)
+    dev64 = np.max(np.abs(out["fp64"][0] - q_star))
+    devm = np.max(np.abs(qm - q_star))
+    print("cycles fp64 / mixed:", out["fp64"][1]["cycles"], out["mixed"][1]["cycles"], "deviation:", dev64, devm)
+    assert devm <= 10 * dev64 + 1e-12 * np.max(np.abs(q_star))

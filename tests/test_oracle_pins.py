@@ -1325,3 +1325,86 @@ def test_converged_state_is_a_fixed_point_of_directional_and_coarse_step_cycles(
     # and away from the solution the same cycle does move it
     q2 = orc.fas_vcycle(mesh, orders, prm, q, 0.0 * S, 1, 1, 2, direction=direction, delta_n=delta_n)
     assert np.max(np.abs(q2 - q)) > 1e-6 * np.max(np.abs(q))
+
+
+# ---------------------------------------------------------------------------
+# linearised residual and the mixed-precision cycle (the library's precision
+# split around Sec. 3.1 / Algorithm 1)
+# ---------------------------------------------------------------------------
+def test_directional_derivative_of_the_residual():
+    """The linearised residual is a derivative: linear in dq, the first-order
+    term of A(q + e dq) - A(q) (the remainder falls as e^2), independent of
+    the difference step, and zero along a uniform change of a uniform state
+    on a periodic mesh (every uniform state is steady there)."""
+    mesh = syn.periodic_box(2, 2, 1, dim=2)
+    o = syn.random_orders(mesh["K"], 2, 2, 4, 3)
+    prm = syn.flow_params(mach=0.3, re=100.0)
+    q = syn.oblique_state(mesh, o, prm, 1)
+    rng = np.random.default_rng(0)
+    d1, d2 = rng.normal(size=q.size) * 1e-2, rng.normal(size=q.size) * 1e-2
+    A = lambda x: orc.operator_A(mesh, o, prm, x)
+    J1, J2 = (orc.directional_derivative(A, q, d) for d in (d1, d2))
+    J12 = orc.directional_derivative(A, q, d1 + d2)
+    sc = np.max(np.abs(J12))
+    assert np.max(np.abs(J12 - J1 - J2)) < 1e-8 * sc
+    assert np.max(np.abs(orc.directional_derivative(A, q, 3.0 * d1) - 3.0 * J1)) < 1e-8 * sc
+    assert np.max(np.abs(orc.directional_derivative(A, q, d1, step=3e-5) - J1)) < 1e-8 * sc
+    rem = [np.max(np.abs(A(q + e * d1) - A(q) - e * J1)) for e in (1e-1, 5e-2)]
+    assert 3.5 < rem[0] / rem[1] < 4.5
+    # a uniform perturbation of a uniform state on a periodic mesh
+    qu = syn.freestream_state(mesh, o, prm)
+    nn, off = syn.layout_offsets(o, 2)
+    du = syn.to_blocked(np.tile(np.array([0.01, 0.02, -0.01, 0.0, 0.5])[:, None], (1, off[-1])), o, 2)
+    assert np.max(np.abs(orc.tangent_residual(mesh, o, prm, qu, du))) < 1e-9
+
+
+def test_mixed_cycle_equals_the_fas_cycle_for_a_linear_operator(monkeypatch):
+    """For a linear operator the FAS cycle of Algorithm 1 and the
+    defect-correction cycle of the linearised problem are the same iteration
+    (the coarse FAS source A_c(I q) + I r minus A_c at the coarse start state
+    is the linear right-hand side I r), so with equal time steps they return
+    the same state.  A wrong coarse right-hand side, a missing prolongation
+    of the correction or a wrong linearisation point breaks the equality."""
+    rng = np.random.default_rng(5)
+    mesh = syn.periodic_box(2, 2, 1, dim=2)
+    dim = 2
+    of = syn.random_orders(mesh["K"], dim, 2, 3, 6)
+    mats = {}
+
+    def mat(n):  # one fixed operator per level size (levels of every coarsening used below)
+        if n not in mats:
+            mats[n] = np.random.default_rng(n).normal(size=(n, n)) / n + np.eye(n)
+        return mats[n]
+
+    def fake_res(mesh_, o, prm, q, s=None, isolated=False):
+        return (0.0 if s is None else s) - mat(len(q)) @ q
+
+    monkeypatch.setattr(orc, "residual", fake_res)
+    monkeypatch.setattr(orc, "cfl_dt", lambda mesh_, o, prm, q: 0.3)
+    q = rng.normal(size=5 * orc.nodes_total(of, dim))
+    S = rng.normal(size=q.size)
+    for kw in (dict(), dict(delta_n=2), dict(direction=1)):
+        want = orc.fas_vcycle(mesh, of, None, q, S, 2, 1, 3, **kw)
+        got = orc.mixed_vcycle(mesh, of, None, q, S, 2, 1, 3, **kw)
+        assert np.max(np.abs(got - want)) < 1e-9 * np.max(np.abs(want - q)), kw
+        assert np.max(np.abs(want - q)) > 1e-2
+
+
+def test_mixed_cycle_fixed_point_and_second_order_agreement_with_fas():
+    """At a solution of A(q) = S the mixed cycle returns q (its defect is zero);
+    near one, it differs from the nonlinear FAS cycle only by the
+    linearisation error, O(e^2) in the distance e from the solution."""
+    mesh = syn.periodic_box(2, 1, 1, dim=2)
+    o = syn.uniform_orders(mesh["K"], 2, 2)
+    prm = syn.flow_params(mach=0.3, re=100.0)
+    qs = syn.oblique_state(mesh, o, prm, 4, amp=0.01)
+    S = orc.operator_A(mesh, o, prm, qs)
+    q1 = orc.mixed_vcycle(mesh, o, prm, qs, S, 1, 1, 2)
+    assert np.max(np.abs(q1 - qs)) < 1e-10 * np.max(np.abs(qs))
+    pert = np.random.default_rng(2).normal(size=qs.size) * np.abs(qs)
+    diffs = []
+    for e in (2e-3, 1e-3):
+        q0 = qs + e * pert
+        diffs.append(np.max(np.abs(orc.mixed_vcycle(mesh, o, prm, q0, S, 1, 1, 2)
+                                   - orc.fas_vcycle(mesh, o, prm, q0, S, 1, 1, 2))))
+    assert 3.0 < diffs[0] / diffs[1] < 5.0
