@@ -14,7 +14,9 @@ these smooth states); the states are oblique flows, so no face-normal
 velocity sits at the kink of the Roe dissipation's |lambda|.  The mixed
 V-cycle is compared with the oracle's restatement of the same cycle within
 TOL_CYCLE of the size of the correction it applies, and a mixed steady solve
-must satisfy the oracle's FP64 equations to its tolerance."""
+must satisfy the oracle's FP64 equations to its tolerance.  Measured on
+GB300: tangent errors up to 2.5e-6 of s_v, cycle errors up to 1.3e-7 of the
+correction."""
 import numpy as np
 import pytest
 
@@ -24,7 +26,7 @@ from paper_1806_11456_gb300 import synthetic as syn
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
 TOL_TF = 2e-5
-TOL_CYCLE = 1e-4
+TOL_CYCLE = 1e-6
 
 
 @pytest.fixture(scope="module")
@@ -92,8 +94,10 @@ def test_tangent_residual_matches_the_oracle_derivative(dg, name):
     ro = orc.tangent_residual(mesh, o, prm, q, dq, b)
     err = np.abs(syn.from_blocked(r - ro, o, mesh["dim"])).max(axis=1)
     scale = _tangent_scale(mesh, o, prm, q, dq)
-    print(name, "tangent error / scale per variable:", err / scale)
-    assert np.all(err <= TOL_TF * scale), err / scale
+    live = scale > 0  # (w in 2D is identically zero on both sides)
+    assert np.all(err[~live] == 0.0)
+    print(name, "tangent error / scale per variable:", err[live] / scale[live])
+    assert np.all(err[live] <= TOL_TF * scale[live]), err[live] / scale[live]
 
 
 def test_mixed_mode_keeps_the_fp64_residual_and_tau(dg):
@@ -136,7 +140,11 @@ def test_mixed_steady_solve_satisfies_the_fp64_equations(dg):
     """A steady problem whose discrete solution is known (S = A(q*)): the
     mixed form cycles until its FP64 residual is below 1e-10; the oracle's
     FP64 residual of the result is then below that tolerance too (to the
-    parity bar), and the state is q* as closely as the FP64 form gets it."""
+    parity bar).  Its state lies within 1e-10 of max|q*| of q* (the FP64 form:
+    1e-12).  The FP64 cycle conserves the discrete totals of a periodic box
+    exactly, the FP32 corrections only to rounding, and the totals are a
+    direction the residual barely sees (uniform changes of a periodic state);
+    the deviation's weighted mean and remainder are printed apart."""
     import torch
     mesh, o, prm, q_star = syn.manufactured_box_4x4x1()
     S = orc.operator_A(mesh, o, prm, q_star)
@@ -153,5 +161,18 @@ def test_mixed_steady_solve_satisfies_the_fp64_equations(dg):
     assert np.max(np.abs(ro)) <= 1e-10 + TOL * orc.volume_scale(mesh, o, prm, qm)
     dev64 = np.max(np.abs(out["fp64"][0] - q_star))
     devm = np.max(np.abs(qm - q_star))
-    print("cycles fp64 / mixed:", out["fp64"][1]["cycles"], out["mixed"][1]["cycles"], "deviation:", dev64, devm)
-    assert devm <= 10 * dev64 + 1e-12 * np.max(np.abs(q_star))
+    # split the mixed deviation into its per-variable weighted mean and the rest
+    D = syn.from_blocked(qm - q_star, o, mesh["dim"])
+    W = []
+    for e in range(mesh["K"]):  # tensor Gauss weights of the element (equal elements: J drops out)
+        w = np.ones(1)
+        for d in range(mesh["dim"]):
+            w = np.multiply.outer(np.polynomial.legendre.leggauss(int(o[e, d]) + 1)[1], w)
+        W.append(w.reshape(-1))
+    W = np.concatenate(W)
+    mean = D @ W / W.sum()
+    rest = np.max(np.abs(D - mean[:, None]))
+    print("cycles fp64 / mixed:", out["fp64"][1]["cycles"], out["mixed"][1]["cycles"], "deviation fp64 / mixed:",
+          dev64, devm, "mixed mean part:", np.max(np.abs(mean)), "rest:", rest)
+    scale = np.max(np.abs(q_star))
+    assert dev64 <= 1e-12 * scale and devm <= 1e-10 * scale
