@@ -747,6 +747,31 @@ def run_gb300(args, rank, world):
             "dtype": "f32x2 (double-float, ~48-bit significand)", "stage_ms": prof_df,
             "residual_dof_per_s": 5.0 * nodes / (df_res_ms * 1e-3),
             "parity": "same 1e-12 bar against the FP64 oracle (tests/test_gpu_parity.py)"}
+    # the same step in the mixed form: FP64 finest residual, coarse
+    # right-hand sides and tau; FP32 tangent-linear correction cycle
+    M.set_arithmetic("mixed")
+    for _ in range(2):
+        q.copy_(q0)
+        step(q)
+    mx_ms, mx_dofs = 0.0, 0.0
+    for _ in range(args.steps):
+        q.copy_(q0)
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dofs, _ = step(q)
+        e1.record(stream)
+        e1.synchronize()
+        mx_ms += e0.elapsed_time(e1)
+        mx_dofs += dofs
+    prof_mx = M.profile_residual(q0, None, iters=50)
+    mx_res_ms = sum(v for k, v in prof_mx.items() if k != "isolated")
+    mixed = {"value": world * mx_dofs / (mx_ms * 1e-3), "unit": "DOF/s", "ms_per_step": mx_ms / args.steps,
+             "dtype": "f64 finest residual, coarse right-hand sides and tau; f32 tangent smoothing and coarse operators",
+             "stage_ms": prof_mx, "tangent_residual_dof_per_s": 5.0 * nodes / (mx_res_ms * 1e-3),
+             "note": "a step here is one defect-correction cycle (a different iteration from the FAS cycle of the "
+                     "headline); errors against the oracle in tests/test_gpu_mixed.py"}
     M.set_arithmetic("fp64")
 
     if rank == 0:
@@ -756,6 +781,7 @@ def run_gb300(args, rank, world):
                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                "config": dict(cfg, parallelism=f"replicas{world}"), "e2e": e2e,
                "gpu_launches": None, "roofline": roof, "clocks": clk, "step_ms_parts": parts, "df32": df32,
+               "mixed": mixed,
                "autotune": autotune}
         out["gpu_launches"] = int(launches)  # library kernels launched in the timed steps
         out["time_to_tol"] = time_to_tolerance(dg, torch, dev)

@@ -383,7 +383,10 @@ int dg_transfer_noalloc(int32_t dim, int32_t K, const int32_t* orders_from, cons
  * and writes the mean duration per launch in ms to ms_out[0..5]: face
  * traces, mortar pass 1 (BR1 U*), volume (BR1 gradient + flux divergence),
  * mortar pass 2 (Roe + BR1 flux), surface + residual, and ms_out[5] the
- * isolated operator.  r receives the residual.  Synchronises the stream.
+ * isolated operator.  r receives the residual.  With DG_ARITH_MIXED the
+ * five operator stages are timed as the mixed cycle runs them, in FP32
+ * tangent arithmetic (J(q) q), and the isolated operator in FP64.
+ * Synchronises the stream.
  */
 int dg_profile_residual(dg_mesh* mesh, const double* q, const double* s, double* r, int iters,
                         double* ms_out, void* stream);

@@ -136,6 +136,7 @@ struct Level {
   double* d_mnS = nullptr;              // 3 x mortar_nodes
   MortarTile* d_mtiles = nullptr;
   int n_mtiles = 0;
+  bool mortars_conforming = false;      // every mortar conforming: one-pass mortar kernels
   int32_t* d_tile_elems = nullptr;
   int32_t* d_slot = nullptr;            // solve slot of each element
   ElemTile* d_tiles = nullptr;

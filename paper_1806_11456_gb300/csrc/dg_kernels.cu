@@ -309,12 +309,12 @@ DEV void visc_flux(const R* u, R mu, const R* grad, const R* nv, const GasT<R>& 
 }
 
 // Roe flux for unit normal n (textbook averages, five waves, no entropy fix)
+// (the primitives 1/rho, u, p of both states are passed in: the mortar kernel
+// reuses them for the viscous fluxes)
 template <typename R>
-DEV void roe(const R* qL, const R* qR, const R* n, const GasT<R>& G, R* f) {
+DEV void roe(const R* qL, const R* qR, R irL, const R* uL, R pL, R irR, const R* uR, R pR, const R* n,
+             const GasT<R>& G, R* f) {
   const R half = cst<R>(0.5f);
-  R irL, uL[3], pL, TL, irR, uR[3], pR, TR;
-  to_prim(qL, G, irL, uL, pL, TL);
-  to_prim(qR, G, irR, uR, pR, TR);
   const R unL = uL[0] * n[0] + uL[1] * n[1] + uL[2] * n[2];
   const R unR = uR[0] * n[0] + uR[1] * n[1] + uR[2] * n[2];
   const R HL = (qL[4] + pL) * irL, HR = (qR[4] + pR) * irR;
@@ -725,13 +725,14 @@ DEV void mortar_node_value(const LevelArgsT<R>& A, const MortarArgsT<R>& MA, con
     return;
   }
   R f[5];
-  roe(qL, qR, nu, G, f);
+  R irL, uL[3], pLs, TL, irR, uR[3], pRs, TR;
+  to_prim(qL, G, irL, uL, pLs, TL);
+  to_prim(qR, G, irR, uR, pRs, TR);
+  roe(qL, qR, irL, uL, pLs, irR, uR, pRs, nu, G, f);
   if (!(M.eR < 0 && M.bc == DG_BC_SLIP)) {
     R g[12], fv[5];
     face_interp<R, 12>(trg + pL, A.fn, nLa, nLb, M.ma, M.mb, a, b, g);
-    R ir, u[3], p, T;
-    to_prim(qL, G, ir, u, p, T);
-    const R mu = mu_of_T(T, G);
+    const R mu = mu_of_T(TL, G);
     if (M.eR < 0 && M.bc == DG_BC_WALL) {
       const R z[3] = {cst<R>(0.0f), cst<R>(0.0f), cst<R>(0.0f)};
       visc_flux(z, mu, g, nu, G, false, fv);
@@ -739,12 +740,11 @@ DEV void mortar_node_value(const LevelArgsT<R>& A, const MortarArgsT<R>& MA, con
       for (int v = 0; v < 5; ++v) f[v] -= G.invRe * fv[v];
     } else {
       const R hre = half * G.invRe;
-      visc_flux(u, mu, g, nu, G, true, fv);
+      visc_flux(uL, mu, g, nu, G, true, fv);
 #pragma unroll
       for (int v = 0; v < 5; ++v) f[v] -= hre * fv[v];
       if (M.eR >= 0) face_interp<R, 12>(trg + pR, A.fn, Ra, Rb, Ma, Mb, ia, ib, g);  // else: interior gradient
-      to_prim(qR, G, ir, u, p, T);
-      visc_flux(u, mu_of_T(T, G), g, nu, G, true, fv);
+      visc_flux(uR, mu_of_T(TR, G), g, nu, G, true, fv);
 #pragma unroll
       for (int v = 0; v < 5; ++v) f[v] -= hre * fv[v];
     }
@@ -836,6 +836,45 @@ __global__ void __launch_bounds__(kMortarTile, 8) k_mortar(LevelArgsT<R> A, Mort
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v) SR::put(out, v * A.fn + dst, neg ? -acc[v] : acc[v]);
+  }
+}
+
+// k_mortar_conf<PASS>: the same two passes on a level whose mortars are all
+// conforming (both sides carry the mortar's order in each tangential
+// direction, e.g. every level of a uniform-order mesh).  The L2 projection
+// back is then the identity, so each thread computes one mortar node and
+// writes it to the L side's face node and, through the face orientation, to
+// the R side's (negated for the flux): no shared memory, no barrier, no
+// search for the owning mortar, and CTAs of any size.  Same bits as the tile
+// kernel, whose identity projection is an exact copy.
+constexpr int kMortarConfThreads = 128;
+
+template <typename R, int PASS>
+__global__ void __launch_bounds__(kMortarConfThreads, 3)
+    k_mortar_conf(LevelArgsT<R> A, MortarArgsT<R> MA, const GasT<R>* __restrict__ gas,
+                  const typename Store<R>::T* __restrict__ trq, const typename Store<R>::T* __restrict__ trg,
+                  typename Store<R>::T* __restrict__ out) {
+  using SR = Store<R>;
+  constexpr int NV = (PASS == 1) ? 4 : 5;
+  const int64_t gp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gp >= MA.mnodes) return;
+  const MortarDev M = MA.mortars[MA.mnode_mortar[gp]];
+  R o[5];
+  mortar_node_value<R, PASS>(A, MA, gas[A.slot[M.eL]], trq, trg, gp, o);
+  const int loc = (int)(gp - M.node_off);
+  const int a = loc % M.ma, b = loc / M.ma;
+  const int64_t dL = A.fo[M.eL * 6 + M.fL] + b * M.ma + a;  // L face node = mortar node (L frame)
+#pragma unroll
+  for (int v = 0; v < NV; ++v) SR::put(out, v * A.fn + dL, o[v]);
+  if (M.eR >= 0) {
+    const bool sw = M.orient & 1;
+    const int Ma = sw ? M.mb : M.ma, Mb = sw ? M.ma : M.mb;
+    int ia = sw ? b : a, ib = sw ? a : b;
+    if (M.orient & 2) ia = Ma - 1 - ia;
+    if (M.orient & 4) ib = Mb - 1 - ib;
+    const int64_t dR = A.fo[M.eR * 6 + M.fR] + ib * Ma + ia;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) SR::put(out, v * A.fn + dR, PASS == 2 ? -o[v] : o[v]);
   }
 }
 
@@ -1717,6 +1756,16 @@ static void launch_mortar(int pass, const Level* L, const GasT<R>* G, cudaStream
   count_launch();
   LevelArgsT<R> A = largs<R>(L);
   MortarArgsT<R> MA = margs<R>(L);
+  if (L->mortars_conforming) {
+    const int grid = (int)std::max<int64_t>(1, (L->mortar_nodes + kMortarConfThreads - 1) / kMortarConfThreads);
+    if (pass == 1)
+      k_mortar_conf<R, 1><<<grid, kMortarConfThreads, 0, st>>>(A, MA, G, buf<R>(L->d_trq), nullptr,
+                                                               buf<R>(L->d_ust));
+    else
+      k_mortar_conf<R, 2><<<grid, kMortarConfThreads, 0, st>>>(A, MA, G, buf<R>(L->d_trq), buf<R>(L->d_trg),
+                                                               buf<R>(L->d_fst));
+    return;
+  }
   if (pass == 1)
     k_mortar<R, 1><<<L->n_mtiles, kMortarTile, 0, st>>>(A, MA, G, buf<R>(L->d_trq), nullptr, buf<R>(L->d_ust));
   else
@@ -1791,7 +1840,7 @@ int residual(const dg_mesh* m, Level* L, const double* q, const double* s, doubl
 
 template <typename R>
 static int profile_t(const dg_mesh* m, Level* L, const double* q, const double* s, double* r, int iters,
-                     double* ms_out, cudaStream_t st) {
+                     double* ms_out, cudaStream_t st, const double* base = nullptr) {
   const GasT<R>* G = gas_table<R>(m);
   RKArgs rk = rk_args(-1, nullptr, nullptr, nullptr);
   TauArgs ta{nullptr, nullptr, nullptr, 0, 0};
@@ -1802,12 +1851,15 @@ static int profile_t(const dg_mesh* m, Level* L, const double* q, const double* 
     DG_CUDA_TRY(cudaEventRecord(e0, st));
     for (int it = 0; it < iters; ++it) {
       switch (k) {
-        case 0: launch_trace<R>(L, q, st); break;
+        case 0: launch_trace<R>(L, q, st, base); break;
         case 1: launch_mortar<R>(1, L, G, st); break;
-        case 2: launch_volume<R>(L, G, q, st); break;
+        case 2: launch_volume<R>(L, G, q, st, -1, 0, base); break;
         case 3: launch_mortar<R>(2, L, G, st); break;
-        case 4: launch_surface<R>(L, s, r, nullptr, rk, st); break;
-        default: launch_isolated<R>(L, G, q, s, r, ta, st); break;
+        case 4: launch_surface<R>(L, s, r, nullptr, rk, st, base); break;
+        default:
+          if (std::is_same<R, tf>::value) break;  // tau stays FP64 in the mixed form: timed in FP64 below
+          launch_isolated<R>(L, G, q, s, r, ta, st);
+          break;
       }
     }
     DG_CUDA_TRY(cudaEventRecord(e1, st));
@@ -1940,6 +1992,17 @@ int profile_residual(const dg_mesh* m, Level* L, const double* q, const double* 
   int rc = residual(m, L, q, s, r, false, st, nullptr, -1, nullptr, nullptr);
   if (rc != DG_OK) return rc;
   if (m->arith == DG_ARITH_DF32) return profile_t<dd>(m, L, q, s, r, iters, ms_out, st);
+  if (m->arith == DG_ARITH_MIXED) {
+    // the operator stages as the mixed cycle runs them: tangent kernels,
+    // J(q) dq with dq = q (any direction costs the same); the isolated
+    // operator in FP64
+    if ((rc = residual_tangent(m, L, q, q, s, r, st, nullptr, -1, nullptr, nullptr)) != DG_OK) return rc;
+    double iso[6];
+    if ((rc = profile_t<double>(m, L, q, s, r, iters, iso, st)) != DG_OK) return rc;
+    if ((rc = profile_t<tf>(m, L, q, s, r, iters, ms_out, st, q)) != DG_OK) return rc;
+    ms_out[5] = iso[5];
+    return DG_OK;
+  }
   return profile_t<double>(m, L, q, s, r, iters, ms_out, st);
 }
 

@@ -632,6 +632,8 @@ int build_level(const dg_mesh* m, const std::vector<int32_t>& orders, Level* L) 
     }
   L->n_mortars = (int)mortars.size();
   L->mortar_nodes = mnodes;
+  L->mortars_conforming = true;
+  for (const MortarDev& M : mortars) L->mortars_conforming = L->mortars_conforming && (M.flags & 1);
   mnS.assign((size_t)3 * mnodes, 0.0);
   for (int64_t p = 0; p < mnodes; ++p)
     for (int c = 0; c < 3; ++c) mnS[(size_t)c * mnodes + p] = mgeo[p][c];
