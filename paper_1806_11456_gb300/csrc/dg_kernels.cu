@@ -190,6 +190,34 @@ int upload_tables() {
 // ---------------------------------------------------------------------------
 #define DEV __device__ __forceinline__
 
+// Programmatic dependent launch.  The kernels of the operator chain are
+// launched with the programmatic-serialisation attribute (launch_k below),
+// so the GPU processes the launch of a kernel while its predecessor in the
+// stream still runs, instead of after it.  Each such kernel starts with
+// pdl_enter(): griddepcontrol.wait returns once the preceding kernel has
+// completed and its writes are visible (the kernel reads and writes nothing
+// before it), then launch_dependents lets the next kernel launch.  On a
+// launch without a programmatic predecessor the wait returns at once.
+DEV void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+static void launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  (void)cudaLaunchKernelEx(&cfg, kern, args...);  // a launch error is read by the caller's cudaGetLastError
+}
+
 template <typename R>
 DEV R cst(float x);
 template <>
@@ -635,6 +663,7 @@ DEV void write_face_traces(const LevelArgsT<R>& A, const ElemTile& t, const R* s
 template <typename R, int DIM>
 __global__ void __launch_bounds__(kTileNodes) k_trace_q(LevelArgsT<R> A, const double* __restrict__ q,
                                                         typename Store<R>::T* __restrict__ trq) {
+  pdl_enter();
   extern __shared__ double smem_raw[];
   R* sq = reinterpret_cast<R*>(smem_raw);
   const ElemTile t = A.tiles[blockIdx.x];
@@ -790,6 +819,7 @@ __global__ void __launch_bounds__(kMortarTile, 8) k_mortar(LevelArgsT<R> A, Mort
                                                            const typename Store<R>::T* __restrict__ trq,
                                                            const typename Store<R>::T* __restrict__ trg,
                                                            typename Store<R>::T* __restrict__ out) {
+  pdl_enter();
   using SR = Store<R>;
   constexpr int NV = (PASS == 1) ? 4 : 5;
   __shared__ R sval[kMortarTileMax * 5];
@@ -847,13 +877,14 @@ __global__ void __launch_bounds__(kMortarTile, 8) k_mortar(LevelArgsT<R> A, Mort
 // the R side's (negated for the flux): no shared memory, no barrier, no
 // search for the owning mortar, and CTAs of any size.  Same bits as the tile
 // kernel, whose identity projection is an exact copy.
-constexpr int kMortarConfThreads = 128;
+constexpr int kMortarConfThreads = 32;  // one warp: spreads a level's warps evenly over the SMs
 
 template <typename R, int PASS>
-__global__ void __launch_bounds__(kMortarConfThreads, 3)
+__global__ void __launch_bounds__(kMortarConfThreads, 12)
     k_mortar_conf(LevelArgsT<R> A, MortarArgsT<R> MA, const GasT<R>* __restrict__ gas,
                   const typename Store<R>::T* __restrict__ trq, const typename Store<R>::T* __restrict__ trg,
                   typename Store<R>::T* __restrict__ out) {
+  pdl_enter();
   using SR = Store<R>;
   constexpr int NV = (PASS == 1) ? 4 : 5;
   const int64_t gp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1055,6 +1086,7 @@ __global__ void __launch_bounds__(kVolThreads) __maxnreg__(DIM == 2 ? 96 : 104) 
                                                         const typename Store<R>::T* __restrict__ ust,
                                                         typename Store<R>::T* __restrict__ trg,
                                                         typename Store<R>::T* __restrict__ vol) {
+  pdl_enter();
   using SR = Store<R>;
   extern __shared__ double smem_raw[];
   const ElemTile t = A.tiles[tile0 + blockIdx.x];
@@ -1202,6 +1234,7 @@ __global__ void __launch_bounds__(kTileNodes) k_surface(LevelArgsT<R> A, const t
                                                         const typename Store<R>::T* __restrict__ fst,
                                                         const double* __restrict__ s, double* __restrict__ r,
                                                         double* norm, RKArgs rk) {
+  pdl_enter();
   using SR = Store<R>;
   extern __shared__ double smem_raw[];
   R* sq = reinterpret_cast<R*>(smem_raw);  // updated state (5 x T) when rk.trq_next is set
@@ -1284,6 +1317,7 @@ __global__ void __launch_bounds__(kVolThreads) __maxnreg__(DIM == 2 ? 96 : 128) 
                                                           const double* __restrict__ q,
                                                           const double* __restrict__ s, double* __restrict__ r,
                                                           TauArgs tau) {
+  pdl_enter();
   using SR = Store<R>;
   extern __shared__ double smem_raw[];
   const ElemTile t = A.tiles[tile0 + blockIdx.x];
@@ -1339,6 +1373,7 @@ __global__ void __launch_bounds__(kVolThreads) __maxnreg__(DIM == 2 ? 96 : 128) 
 template <int DIM>
 __global__ void __launch_bounds__(kTileNodes) k_cfl(LevelArgsT<double> A, const GasD* __restrict__ gasd,
                                                     const double* __restrict__ q, double* dtmin) {
+  pdl_enter();
   const ElemTile t = A.tiles[blockIdx.x];
   const int n0 = t.n[0], n1 = t.n[1], n2 = t.n[2];
   const int nn = n0 * n1 * n2;
@@ -1383,6 +1418,7 @@ __global__ void __launch_bounds__(kTransferThreads) k_transfer(const int32_t* __
                                                                const double* __restrict__ in,
                                                                const double* __restrict__ sub,
                                                                double* __restrict__ out, int accumulate) {
+  pdl_enter();
   extern __shared__ double sbuf[];
   const int e = blockIdx.x;
   const int f0 = nf[e * 3], f1 = nf[e * 3 + 1], f2 = nf[e * 3 + 2];
@@ -1432,13 +1468,16 @@ __global__ void __launch_bounds__(kTransferThreads) k_transfer(const int32_t* __
 }
 
 __global__ void k_fill(double* p, double v, int64_t n) {
+  pdl_enter();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
 }
 __global__ void k_axpby(double* y, double a, const double* x, double b, int64_t n) {
+  pdl_enter();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = a * x[i] + b * y[i];
 }
 __global__ void k_sub3(double* o, const double* a, const double* b, int64_t n) {
+  pdl_enter();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     o[i] = a[i] - b[i];
 }
@@ -1492,6 +1531,7 @@ int prepare_capture() { return configure_smem(); }
 // level's layout) into out[slot]; out must be zeroed first
 __global__ void __launch_bounds__(kTileNodes) k_slot_maxabs(LevelArgsT<double> A, const double* __restrict__ x,
                                                             double* out) {
+  pdl_enter();
   const ElemTile t = A.tiles[blockIdx.x];
   const int nn = t.n[0] * t.n[1] * t.n[2];
   const int T = t.count * nn;
@@ -1517,6 +1557,7 @@ __global__ void __launch_bounds__(kTileNodes) k_slot_maxabs(LevelArgsT<double> A
 
 // dt[k] = 0 for every slot k whose mask is 0 (k_surface then leaves it unchanged)
 __global__ void k_mask_dt(double* dt, const double* mask, int n) {
+  pdl_enter();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < n && mask[k] == 0.0) dt[k] = 0.0;
 }
@@ -1531,33 +1572,33 @@ int slot_maxabs(const dg_mesh* m, const Level* L, const double* x, double* out, 
   const int rc = fill(out, 0.0, m->nslots, st);
   if (rc != DG_OK) return rc;
   count_launch();
-  k_slot_maxabs<<<L->n_tiles, kTileNodes, 0, st>>>(largs<double>(L), x, out);
+  launch_k(k_slot_maxabs, L->n_tiles, kTileNodes, 0, st, largs<double>(L), x, out);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
 }
 
 int mask_dt(const dg_mesh* m, double* dt, const double* mask, cudaStream_t st) {
   count_launch();
-  k_mask_dt<<<(m->nslots + 127) / 128, 128, 0, st>>>(dt, mask, m->nslots);
+  launch_k(k_mask_dt, (m->nslots + 127) / 128, 128, 0, st, dt, mask, m->nslots);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
 }
 
 int fill(double* p, double v, int64_t n, cudaStream_t st) {
   count_launch();
-  k_fill<<<grid_for(n), 256, 0, st>>>(p, v, n);
+  launch_k(k_fill, grid_for(n), 256, 0, st, p, v, n);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
 }
 int axpby(double* y, double a, const double* x, double b, int64_t n, cudaStream_t st) {
   count_launch();
-  k_axpby<<<grid_for(n), 256, 0, st>>>(y, a, x, b, n);
+  launch_k(k_axpby, grid_for(n), 256, 0, st, y, a, x, b, n);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
 }
 int sub3(double* o, const double* a, const double* b, int64_t n, cudaStream_t st) {
   count_launch();
-  k_sub3<<<grid_for(n), 256, 0, st>>>(o, a, b, n);
+  launch_k(k_sub3, grid_for(n), 256, 0, st, o, a, b, n);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
 }
@@ -1678,9 +1719,9 @@ static void launch_trace(const Level* L, const double* q, cudaStream_t st, const
   LevelArgsT<R> A = largs<R>(L);
   A.base = base;
   if (L->dim == 2)
-    k_trace_q<R, 2><<<L->n_tiles, kTileNodes, sm, st>>>(A, q, buf<R>(L->d_trq));
+    launch_k(k_trace_q<R, 2>, L->n_tiles, kTileNodes, sm, st, A, q, buf<R>(L->d_trq));
   else
-    k_trace_q<R, 3><<<L->n_tiles, kTileNodes, sm, st>>>(A, q, buf<R>(L->d_trq));
+    launch_k(k_trace_q<R, 3>, L->n_tiles, kTileNodes, sm, st, A, q, buf<R>(L->d_trq));
 }
 // The staged element kernels run once per tile class: tiles of <= 128 nodes
 // with 128 threads, <= 256 with 256, larger (one element of up to 729 nodes)
@@ -1710,14 +1751,14 @@ static void launch_volume(const Level* L, const GasT<R>* G, const double* q, cud
   for_tile_classes(L, [&](int t0, int nt, int th, size_t sm) {
     if (L->dim == 2) {
       if (L->affine)
-        k_volume<R, 2, true><<<nt, th, sm, st>>>(A, t0, G, q, ust, trg, vol);
+        launch_k(k_volume<R, 2, true>, nt, th, sm, st, A, t0, G, q, ust, trg, vol);
       else
-        k_volume<R, 2, false><<<nt, th, sm, st>>>(A, t0, G, q, ust, trg, vol);
+        launch_k(k_volume<R, 2, false>, nt, th, sm, st, A, t0, G, q, ust, trg, vol);
     } else {
       if (L->affine)
-        k_volume<R, 3, true><<<nt, th, sm, st>>>(A, t0, G, q, ust, trg, vol);
+        launch_k(k_volume<R, 3, true>, nt, th, sm, st, A, t0, G, q, ust, trg, vol);
       else
-        k_volume<R, 3, false><<<nt, th, sm, st>>>(A, t0, G, q, ust, trg, vol);
+        launch_k(k_volume<R, 3, false>, nt, th, sm, st, A, t0, G, q, ust, trg, vol);
     }
   }, only, threads_override);
 }
@@ -1728,14 +1769,14 @@ static void launch_isolated(const Level* L, const GasT<R>* G, const double* q, c
   for_tile_classes(L, [&](int t0, int nt, int th, size_t sm) {
     if (L->dim == 2) {
       if (L->affine)
-        k_isolated<R, 2, true><<<nt, th, sm, st>>>(A, t0, G, q, s, r, ta);
+        launch_k(k_isolated<R, 2, true>, nt, th, sm, st, A, t0, G, q, s, r, ta);
       else
-        k_isolated<R, 2, false><<<nt, th, sm, st>>>(A, t0, G, q, s, r, ta);
+        launch_k(k_isolated<R, 2, false>, nt, th, sm, st, A, t0, G, q, s, r, ta);
     } else {
       if (L->affine)
-        k_isolated<R, 3, true><<<nt, th, sm, st>>>(A, t0, G, q, s, r, ta);
+        launch_k(k_isolated<R, 3, true>, nt, th, sm, st, A, t0, G, q, s, r, ta);
       else
-        k_isolated<R, 3, false><<<nt, th, sm, st>>>(A, t0, G, q, s, r, ta);
+        launch_k(k_isolated<R, 3, false>, nt, th, sm, st, A, t0, G, q, s, r, ta);
     }
   });
 }
@@ -1747,9 +1788,9 @@ static void launch_surface(const Level* L, const double* s, double* r, double* n
   A.base = base;
   const size_t sm = rk.trq_next ? 5 * L->tile_smem_nodes * sizeof(double) : 0;
   if (L->dim == 2)
-    k_surface<R, 2><<<L->n_tiles, kTileNodes, sm, st>>>(A, buf<R>(L->d_vol), buf<R>(L->d_fst), s, r, norm, rk);
+    launch_k(k_surface<R, 2>, L->n_tiles, kTileNodes, sm, st, A, buf<R>(L->d_vol), buf<R>(L->d_fst), s, r, norm, rk);
   else
-    k_surface<R, 3><<<L->n_tiles, kTileNodes, sm, st>>>(A, buf<R>(L->d_vol), buf<R>(L->d_fst), s, r, norm, rk);
+    launch_k(k_surface<R, 3>, L->n_tiles, kTileNodes, sm, st, A, buf<R>(L->d_vol), buf<R>(L->d_fst), s, r, norm, rk);
 }
 template <typename R>
 static void launch_mortar(int pass, const Level* L, const GasT<R>* G, cudaStream_t st) {
@@ -1759,17 +1800,17 @@ static void launch_mortar(int pass, const Level* L, const GasT<R>* G, cudaStream
   if (L->mortars_conforming) {
     const int grid = (int)std::max<int64_t>(1, (L->mortar_nodes + kMortarConfThreads - 1) / kMortarConfThreads);
     if (pass == 1)
-      k_mortar_conf<R, 1><<<grid, kMortarConfThreads, 0, st>>>(A, MA, G, buf<R>(L->d_trq), nullptr,
+      launch_k(k_mortar_conf<R, 1>, grid, kMortarConfThreads, 0, st, A, MA, G, buf<R>(L->d_trq), nullptr,
                                                                buf<R>(L->d_ust));
     else
-      k_mortar_conf<R, 2><<<grid, kMortarConfThreads, 0, st>>>(A, MA, G, buf<R>(L->d_trq), buf<R>(L->d_trg),
+      launch_k(k_mortar_conf<R, 2>, grid, kMortarConfThreads, 0, st, A, MA, G, buf<R>(L->d_trq), buf<R>(L->d_trg),
                                                                buf<R>(L->d_fst));
     return;
   }
   if (pass == 1)
-    k_mortar<R, 1><<<L->n_mtiles, kMortarTile, 0, st>>>(A, MA, G, buf<R>(L->d_trq), nullptr, buf<R>(L->d_ust));
+    launch_k(k_mortar<R, 1>, L->n_mtiles, kMortarTile, 0, st, A, MA, G, buf<R>(L->d_trq), nullptr, buf<R>(L->d_ust));
   else
-    k_mortar<R, 2><<<L->n_mtiles, kMortarTile, 0, st>>>(A, MA, G, buf<R>(L->d_trq), buf<R>(L->d_trg),
+    launch_k(k_mortar<R, 2>, L->n_mtiles, kMortarTile, 0, st, A, MA, G, buf<R>(L->d_trq), buf<R>(L->d_trg),
                                                         buf<R>(L->d_fst));
 }
 
@@ -2011,9 +2052,9 @@ int cfl_dt(const dg_mesh* m, Level* L, const double* q, double* d_dt, cudaStream
   if (rc != DG_OK) return rc;
   count_launch();
   if (L->dim == 2)
-    k_cfl<2><<<L->n_tiles, kTileNodes, 0, st>>>(largs<double>(L), m->d_gasd, q, d_dt);
+    launch_k(k_cfl<2>, L->n_tiles, kTileNodes, 0, st, largs<double>(L), m->d_gasd, q, d_dt);
   else
-    k_cfl<3><<<L->n_tiles, kTileNodes, 0, st>>>(largs<double>(L), m->d_gasd, q, d_dt);
+    launch_k(k_cfl<3>, L->n_tiles, kTileNodes, 0, st, largs<double>(L), m->d_gasd, q, d_dt);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
 }
@@ -2037,7 +2078,7 @@ int transfer(const dg_mesh* m, const Level* from, const Level* to, int nvar, con
     return DG_EINVAL;
   }
   count_launch();
-  k_transfer<<<from->K, kTransferThreads, 2 * slab * sizeof(double), st>>>(from->d_n, from->d_off, to->d_n,
+  launch_k(k_transfer, from->K, kTransferThreads, 2 * slab * sizeof(double), st, from->d_n, from->d_off, to->d_n,
                                                                           to->d_off, nvar, in, sub, out,
                                                                           accumulate ? 1 : 0);
   DG_CUDA_TRY(cudaGetLastError());
@@ -2070,6 +2111,7 @@ int tau_accumulate(const dg_mesh* m, Level* L, const double* q, const double* s,
 
 __global__ void k_tau_reduce(LevelArgsT<double> A, const double* __restrict__ r, const double* __restrict__ rho, int dir,
                              int slot, const int32_t* __restrict__ fine_orders, double* table) {
+  pdl_enter();
   const ElemTile t = A.tiles[blockIdx.x];
   const int nn = t.n[0] * t.n[1] * t.n[2];
   const int T = t.count * nn;
@@ -2089,7 +2131,7 @@ __global__ void k_tau_reduce(LevelArgsT<double> A, const double* __restrict__ r,
 static int tau_reduce(const Level* L, const double* r, const double* rho, int dir, int slot,
                       const int32_t* fine_orders, double* table, cudaStream_t st) {
   count_launch();
-  k_tau_reduce<<<L->n_tiles, kTileNodes, 0, st>>>(largs<double>(L), r, rho, dir, slot, fine_orders, table);
+  launch_k(k_tau_reduce, L->n_tiles, kTileNodes, 0, st, largs<double>(L), r, rho, dir, slot, fine_orders, table);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
 }
