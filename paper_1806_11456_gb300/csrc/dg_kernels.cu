@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <climits>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -196,11 +197,27 @@ int upload_tables() {
 // stream still runs, instead of after it.  Each such kernel starts with
 // pdl_enter(): griddepcontrol.wait returns once the preceding kernel has
 // completed and its writes are visible (the kernel reads and writes nothing
-// before it), then launch_dependents lets the next kernel launch.  On a
-// launch without a programmatic predecessor the wait returns at once.
-DEV void pdl_enter() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+// before it).  No kernel triggers its dependents early: they launch as its
+// CTAs exit, so a dependent's CTAs are not placed on whichever SMs happened
+// to have room while this kernel ran (the FP64 kernels' time follows their
+// most loaded SM).  On a launch without a programmatic predecessor the wait
+// returns at once.
+DEV void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Where the attribute is set: DG_LAUNCH_PDL=0 never, 1 on streams that are
+// not being captured, 2 (default) also inside captured graphs.  Measured on
+// GB300, flat plate 60x24 at N = 7, one V-cycle 7 -> 1 (2/2/4 sweeps):
+//   FP64   direct 8.54 -> 7.52 ms, graph 7.58 -> 7.52 ms
+//   mixed  direct 4.75 -> 3.61 ms, graph 3.83 -> 3.62 ms
+// (an earlier form that triggered dependents at kernel entry made the FP64
+// cycle slower, 10.3 ms, through the placement of the dependents' CTAs).
+// The knob selects the launch mode only; the work is the same.
+static int pdl_mode() {
+  static const int mode = [] {
+    const char* e = std::getenv("DG_LAUNCH_PDL");
+    return e ? std::atoi(e) : 2;
+  }();
+  return mode;
 }
 
 template <typename... KArgs, typename... Args>
@@ -214,7 +231,14 @@ static void launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 0;
+  const int mode = pdl_mode();
+  if (mode == 2) {
+    cfg.numAttrs = 1;
+  } else if (mode == 1) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) cfg.numAttrs = 1;
+  }
   (void)cudaLaunchKernelEx(&cfg, kern, args...);  // a launch error is read by the caller's cudaGetLastError
 }
 
