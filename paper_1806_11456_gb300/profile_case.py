@@ -9,7 +9,9 @@ Workloads: flat_plate (60 x 24 stretched plate, N = 7, 92,160 nodes, the
 bench's headline mesh); box3d (periodic 48^3 affine hexes, N = 3, 7.1 M nodes,
 283 MB of state: larger than L2); sphere (13,824 quadratic hexes, orders
 U[1,6]^3); tiny3d (periodic 3^3 box, N = 2: a serving-sized request).
---vcycles runs V-cycles instead of residuals.
+--vcycles runs V-cycles instead of residuals.  --arith mixed evaluates the
+linearised residual J(q) q in FP32 tangent arithmetic (the operator kernels of
+the mixed-precision cycle) in place of the residual.
 """
 import argparse
 import os
@@ -48,7 +50,7 @@ def main():
     ap.add_argument("workload", choices=["flat_plate", "box3d", "sphere", "tiny3d"])
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--iters", type=int, default=3)
-    ap.add_argument("--arith", default="fp64", choices=["fp64", "df32"])
+    ap.add_argument("--arith", default="fp64", choices=["fp64", "df32", "mixed"])
     ap.add_argument("--vcycles", action="store_true",
                     help="run V-cycles (3/3/10 sweeps, graph replay) instead of residual evaluations")
     args = ap.parse_args()
@@ -74,6 +76,8 @@ def main():
     def one():
         if args.vcycles:
             M.vcycle(qd, None, beta1=3, beta2=3, beta_c=10, graph=True)
+        elif args.arith == "mixed":
+            M.residual_tangent(qd, qd, None, r=r)
         else:
             M.residual(qd, None, r=r)
 
