@@ -512,6 +512,32 @@ def zero_mean_wave(mesh, orders, q_target, seed, amp=0.01):
     return q_target + amp * to_blocked(wave * scale, orders, dim)
 
 
+def boundary_layer_state(mesh, orders, prm, delta=0.05):
+    """rho = 1, p = p_inf, u = 1 - exp(-y / delta), v = w = 0: a smooth
+    boundary-layer-like field, zero velocity on the wall y = 0."""
+    X = node_coordinates(mesh, orders)
+    g, M = prm[0], prm[2]
+    y = X[:, 1]
+    one = np.ones_like(y)
+    u = 1.0 - np.exp(-y / delta)
+    return to_blocked(conserved(one, u, 0 * y, 0 * y, one / (g * M * M), g), orders, mesh["dim"])
+
+
+def plate_steady_case(seed=3):
+    """A plate-shaped steady problem that explicit pseudo-time cycles can
+    converge to 1e-10 (a variant of the stretched flat-plate workload): the
+    flat-plate boundary conditions on 24 x 8 uniform elements of size 0.05
+    (x in [-0.2, 1], y in [0, 0.4]), N = 3, Mach 0.2, Re 1e4.  Its discrete
+    solution is the boundary-layer-like field q* of boundary_layer_state: the
+    caller forms S = A(q*).  The start is q* plus a 1 % smooth wave
+    (zero_mean_wave).  Returns mesh, orders, params, q*, start."""
+    mesh = flat_plate_mesh(nx=24, ny=8, dy0=0.05, ratio=1.0)
+    prm = flow_params(mach=0.2, re=1e4)
+    o = uniform_orders(mesh["K"], 2, 3)
+    qs = boundary_layer_state(mesh, o, prm)
+    return mesh, o, prm, qs, zero_mean_wave(mesh, o, qs, seed, amp=0.01)
+
+
 def smooth_state(mesh, orders, prm, seed, amp=0.05, wavelength=5.0):
     """Freestream plus smooth seeded perturbations of rho, u, v, w, p: each a
     sum of three plane waves with random directions, wavelength ~ `wavelength`
