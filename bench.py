@@ -394,8 +394,10 @@ def serving(dg, torch, dev, rate=4.0, window=4.0, slots=8, budget=150 << 30, see
     second over `window` seconds) and are submitted at their arrival times;
     each is solved to max|r| < 1e-10 (V 3/3/10, graph replay).  The same
     arrival stream is served by `slots` concurrent slots in double-float
-    arithmetic (the serving form), by the same slots in FP64, and by one
-    slot in FP64 (the plain form, one solve at a time)."""
+    arithmetic, by the same slots in FP64, by two slots with shared launches
+    (up to 8 compatible requests per batch, joining at check points) in FP64
+    and in the mixed form, and by one slot in FP64 (the plain form, one solve
+    at a time; its per-request outcomes are listed)."""
     import threading as th
     rng = np.random.default_rng(seed)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * window * 3)))
@@ -403,10 +405,10 @@ def serving(dg, torch, dev, rate=4.0, window=4.0, slots=8, budget=150 << 30, see
     reqs = serving_requests(dg, torch, dev, len(arrivals), seed)
     kw = dict(tol=1e-10, max_cycles=1500, check_every=10, mg=dict(beta1=3, beta2=3, beta_c=10, graph=1))
 
-    def run(n_slots, arith):
+    def run(n_slots, arith, batch_max=1, details=False):
         kwa = dict(kw, arith=arith)
         ids = [None] * len(reqs)
-        with dg.Server(hbm_budget=budget, slots=n_slots) as S:
+        with dg.Server(hbm_budget=budget, slots=n_slots, batch_max=batch_max) as S:
             t0 = time.perf_counter()
 
             def feed():
@@ -425,21 +427,29 @@ def serving(dg, torch, dev, rate=4.0, window=4.0, slots=8, budget=150 << 30, see
         lat = np.array([x["t_end"] - x["t_submit"] for x in infos])
         dofs = sum(x["rep"]["dof_evals"] for x in infos)
         ok = sum(1 for x in infos if x["state"] == 0)
-        return {"slots": n_slots, "arith": arith, "p50_s": float(np.percentile(lat, 50)),
-                "p99_s": float(np.percentile(lat, 99)),
-                "mean_s": float(lat.mean()), "makespan_s": makespan, "dof_per_s": dofs / makespan,
-                "converged": ok, "cycles_mean": float(np.mean([x["rep"]["cycles"] for x in infos]))}
+        out = {"slots": n_slots, "arith": arith, "batch_max": batch_max, "p50_s": float(np.percentile(lat, 50)),
+               "p99_s": float(np.percentile(lat, 99)),
+               "mean_s": float(lat.mean()), "makespan_s": makespan, "dof_per_s": dofs / makespan,
+               "converged": ok, "cycles_mean": float(np.mean([x["rep"]["cycles"] for x in infos])),
+               "max_batch_peers": int(max(x["batch_peers"] for x in infos))}
+        if details:
+            out["requests"] = [{"dof": 5 * x["rep"]["nodes"], "cycles": x["rep"]["cycles"], "status": x["state"],
+                                "rnorm": x["rep"]["rnorm"], "latency_s": float(l)} for x, l in zip(infos, lat)]
+        return out
 
     conc = run(slots, "df32")
     conc64 = run(slots, "fp64")
-    seq = run(1, "fp64")
+    shared64 = run(2, "fp64", batch_max=8)
+    shared_mx = run(2, "mixed", batch_max=8)
+    seq = run(1, "fp64", details=True)
     nodes = [int(np.sum(np.prod(o[:, :m["dim"]] + 1, axis=1))) for (m, o, *_r) in reqs]
     return {"workload": f"{len(reqs)} requests, Poisson {rate}/s over {window} s: periodic 2D boxes 2-6 per side "
                         "N in {2,3} and 3D boxes 3 per side N = 2, Mach U[0.25,0.4], Re U_log[50,200], "
                         "S = A(q*), to max|r| < 1e-10 (at most 1500 V-cycles 3/3/10, residual checked every 10)",
             "requests": len(reqs), "dof_range": [5 * min(nodes), 5 * max(nodes)],
             "offered_dof_per_s": 5.0 * sum(nodes) / window,
-            "concurrent": conc, "concurrent_fp64": conc64, "one_at_a_time": seq,
+            "concurrent": conc, "concurrent_fp64": conc64, "shared_fp64": shared64, "shared_mixed": shared_mx,
+            "one_at_a_time": seq,
             "p99_speedup": seq["p99_s"] / conc["p99_s"], "p50_speedup": seq["p50_s"] / conc["p50_s"]}
 
 

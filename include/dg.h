@@ -118,6 +118,17 @@ int dg_batch_create(const dg_mesh_desc* descs, const int32_t* const* orders, int
  * values, host; may be NULL) in the batch layout. */
 int dg_batch_info(const dg_mesh* mesh, int32_t* nsolves, int64_t* solve_node_offsets);
 
+/*
+ * dg_batch_set_active -- hold solves of a batch: active is a host array of
+ * nsolves flags; a solve whose flag is 0 is not advanced by any later call
+ * (its time step is 0 in every sweep, so its state stays bitwise unchanged,
+ * and the smoothing-control rules count it as satisfied), while the others
+ * advance exactly as before.  Lets solves of a batch finish at different
+ * times.  Not part of the paper (batching is this library's).  Synchronises
+ * the stream.
+ */
+int dg_batch_set_active(dg_mesh* mesh, const int32_t* active, void* stream);
+
 /* dg_residual_norms -- max |S - A(Q)| of every solve of the mesh (host
  * array of nsolves doubles; 1 for a plain mesh).  Synchronises the stream. */
 int dg_residual_norms(dg_mesh* mesh, const double* q, const double* s, double* norms, void* stream);
@@ -405,6 +416,20 @@ int dg_profile_residual(dg_mesh* mesh, const double* q, const double* s, double*
  * solve gives bit for bit the same result alone and among others.  Not part
  * of the paper: serving many steady solves is this library's addition
  * around the solver of Sec. 3.
+ *
+ * Shared launches (batch_max > 1).  A slot that takes a request which needs
+ * neither full multigrid nor adaptation also takes the queued requests that
+ * can share its cycle -- same dimension, mapping order, arithmetic, multigrid
+ * parameters and top order -- up to batch_max and the memory budget, and runs
+ * them as one batch (dg_batch_create): every kernel of a V-cycle is one
+ * launch over the elements of all of them.  Each member keeps its own
+ * tolerance, cycle cap and residual-check interval: its residual is checked
+ * at its own check points, and a member that stops is held
+ * (dg_batch_set_active) and handed back at once.  Requests that arrive while
+ * the batch runs join it at the next check point (the batch is rebuilt with
+ * the running members' states copied over exactly), and held members are
+ * dropped at such rebuilds.  A batch advances each solve exactly as it does
+ * alone, so every result is bit for bit the one of the same request alone.
  */
 typedef struct dg_server dg_server;
 
@@ -412,6 +437,8 @@ typedef struct {
   int64_t hbm_budget; /* bytes of device memory the running solves may hold together (by estimate) */
   int32_t slots;      /* solves that run at the same time (>= 1) */
   int32_t device;     /* CUDA device of every solve */
+  int32_t batch_max;  /* > 1: shared launches, up to batch_max requests per slot (see below); <= 1: one per slot */
+  int32_t reserved;
 } dg_server_params;
 
 #define DG_REQ_QUEUED 1  /* dg_request_info.state: waiting for a slot or for memory */
@@ -426,6 +453,8 @@ typedef struct {
   double t_submit;        /* seconds since dg_server_create */
   double t_start;
   double t_end;
+  int32_t batch_peers;    /* most other requests it shared launches with (0: it ran alone) */
+  int32_t reserved;
 } dg_request_info;
 
 /* Estimate of the device bytes a steady solve of this mesh and order map

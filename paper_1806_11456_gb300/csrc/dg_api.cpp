@@ -95,6 +95,7 @@ static int smooth_level(Cycle& C, Level* L, double* Q, const double* Sv, int swe
     double* dt = dtb[k & 1];
     double* dt_next = (k + 1 < sweeps) ? dtb[(k + 1) & 1] : nullptr;
     if (mask) DG_TRY(mask_dt(C.m, dt, mask, C.st));
+    if (C.m->freeze) DG_TRY(mask_dt(C.m, dt, C.m->d_scalars + 6 * C.m->nslots, C.st));  // held solves
     for (int stage = 0; stage < 3; ++stage) {
       const int tf = kTracesNext | ((k > 0 || stage > 0) ? kTracesCurrent : 0);
       DG_TRY(residual(C.m, L, Q, Sv, nullptr, false, C.st, nullptr, stage, L->d_G, dt, tf, dt_next));
@@ -136,7 +137,10 @@ static int vcycle_level(Cycle& C, size_t k, double* Qf, const double* Sf) {
   double* dP = C.m->d_scalars + 3 * ns;
   double* dmask = C.m->d_scalars + 4 * ns;
   std::vector<double> h(2 * ns), rpre(ns, 0.0);
-  std::vector<char> done(ns, 0);
+  std::vector<char> held(ns, 0), done(ns, 0);
+  if (C.m->freeze)  // held solves take no part in the rules: they count as done
+    for (int j = 0; j < ns; ++j) held[j] = C.m->active[j] ? 0 : 1;
+  done = held;
   const double* mask = nullptr;
   // hold the slots that are done for the next block (none while all still run)
   auto hold_done = [&]() -> int {
@@ -175,7 +179,7 @@ static int vcycle_level(Cycle& C, size_t k, double* Qf, const double* Sf) {
   DG_TRY(vcycle_level(C, k + 1, nullptr, nullptr));
   DG_TRY(transfer(C.m, Cc, L, 5, Cc->d_Q, Q, C.st, Cc->d_Q0, true));
   // post-smoothing: blocks of beta2 sweeps until max|r| <= its value after the pre-smoothing
-  std::fill(done.begin(), done.end(), 0);
+  done = held;
   mask = nullptr;
   for (int blk = 1;; ++blk) {
     DG_TRY(smooth_level(C, L, Q, Sv, C.mg.beta2, mask));
@@ -218,6 +222,7 @@ static int smooth_tangent(Cycle& C, Level* L, const double* base, double* d, con
   // fixed during the block
   double* dt = C.m->d_scalars;
   if (sweeps > 0) DG_TRY(cfl_dt(C.m, L, base, dt, C.st));
+  if (sweeps > 0 && C.m->freeze) DG_TRY(mask_dt(C.m, dt, C.m->d_scalars + 6 * C.m->nslots, C.st));
   for (int k = 0; k < sweeps; ++k)
     for (int stage = 0; stage < 3; ++stage) {
       const int tfl = kTracesNext | ((k > 0 || stage > 0) ? kTracesCurrent : 0);
@@ -336,6 +341,7 @@ static int run_vcycle(dg_mesh* m, const std::vector<int32_t>& top_orders, double
   const void* ptrs[2] = {Q, Sv};
   key.append((const char*)ptrs, sizeof(ptrs));
   key.append((const char*)&mg, sizeof(mg));
+  key.push_back(m->freeze ? 'h' : '-');
   auto it = m->graphs.find(key);
   if (it == m->graphs.end()) {
     DG_TRY(prepare_capture());
@@ -610,7 +616,7 @@ int dg_mesh_create(const dg_mesh_desc* desc, const int32_t* orders, dg_mesh** ou
     int rc = build_level(m, m->orders, m->fine.get());
     if (rc == DG_OK) rc = upload_gas(m);
     if (rc == DG_OK) {
-      cudaError_t e1 = cudaMalloc(&m->d_scalars, (6 * m->nslots + 16) * sizeof(double));
+      cudaError_t e1 = cudaMalloc(&m->d_scalars, (7 * m->nslots + 16) * sizeof(double));
       cudaError_t e2 = cudaMalloc(&m->d_tau, (size_t)m->K * 3 * kTauSlots * sizeof(double));
       cudaError_t e3 = cudaMalloc(&m->d_orders, m->orders.size() * sizeof(int32_t));
       if (e3 == cudaSuccess)
@@ -673,7 +679,7 @@ int dg_batch_create(const dg_mesh_desc* descs, const int32_t* const* orders, int
     int rc = build_level(m, m->orders, m->fine.get());
     if (rc == DG_OK) rc = upload_gas(m);
     if (rc == DG_OK) {
-      cudaError_t e1 = cudaMalloc(&m->d_scalars, (6 * m->nslots + 16) * sizeof(double));
+      cudaError_t e1 = cudaMalloc(&m->d_scalars, (7 * m->nslots + 16) * sizeof(double));
       cudaError_t e2 = cudaMalloc(&m->d_tau, (size_t)m->K * 3 * kTauSlots * sizeof(double));
       cudaError_t e3 = cudaMalloc(&m->d_orders, m->orders.size() * sizeof(int32_t));
       if (e3 == cudaSuccess)
@@ -688,6 +694,24 @@ int dg_batch_create(const dg_mesh_desc* descs, const int32_t* const* orders, int
       return rc;
     }
     *out = m;
+    return DG_OK;
+  });
+}
+
+int dg_batch_set_active(dg_mesh* m, const int32_t* active, void* stream) {
+  return guarded([&]() -> int {
+    if (!m || !active) {
+      set_error("dg_batch_set_active: null argument");
+      return DG_EINVAL;
+    }
+    const int ns = m->nslots;
+    std::vector<double> h(ns);
+    m->active.assign(active, active + ns);
+    for (int k = 0; k < ns; ++k) h[k] = active[k] ? 1.0 : 0.0;
+    cudaStream_t st = S(stream);
+    DG_CUDA_TRY(cudaMemcpyAsync(m->d_scalars + 6 * ns, h.data(), ns * sizeof(double), cudaMemcpyHostToDevice, st));
+    DG_CUDA_TRY(cudaStreamSynchronize(st));  // h is a local buffer
+    m->freeze = true;  // (held from now on; cached graphs were captured without the mask)
     return DG_OK;
   });
 }

@@ -183,7 +183,9 @@ struct dg_mesh {
   std::vector<int32_t> orders;
   std::unique_ptr<dg::Level> fine;
   std::map<std::vector<int32_t>, std::unique_ptr<dg::Level>> levels;  // coarse levels by order map
-  double* d_scalars = nullptr;   // per slot: [0, n) dt, [n, 2n) max|r|, [2n, 3n) and [3n, 4n) the
+  bool freeze = false;           // some solves may be held (dg_batch_set_active): every sweep masks their dt
+  std::vector<int32_t> active;   // per solve 1 = advanced, 0 = held (when freeze)
+  double* d_scalars = nullptr;   // per slot: [6n, 7n) the active mask; [0, n) dt, [n, 2n) max|r|, [2n, 3n) and [3n, 4n) the
                                  // smoothing-control norms, [4n, 5n) 1/0 smoothing mask, [5n, 6n) the
                                  // alternate dt of every other sweep (n = nslots)
   double* d_tau = nullptr;       // K x 3 x 16 tau table

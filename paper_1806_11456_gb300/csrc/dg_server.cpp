@@ -9,6 +9,8 @@
 // kernels of concurrent solves overlap on the device; requests share no
 // device data, so a solve gives the same bits alone and among others.
 #include <algorithm>
+#include <climits>
+#include <cmath>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -44,6 +46,7 @@ struct Request {
   std::vector<int32_t> orders_out;
   int64_t dev_bytes = 0;
   double t_submit = 0, t_start = 0, t_end = 0;
+  int batch_peers = 0;  // most other requests it shared launches with
 };
 
 // Device bytes of one multigrid level with the given order map (the buffers
@@ -220,6 +223,321 @@ Outcome run_request(const Request& r, cudaStream_t st) {
   return out;
 }
 
+// ---------------------------------------------------------------------------
+// Shared launches (batch_max > 1): requests that can share a V-cycle run as
+// one batch; each keeps its own stopping rule (that of the steady driver
+// without full multigrid or adaptation: residual checked before the first
+// cycle, after every check_every cycles and at the cap).
+// ---------------------------------------------------------------------------
+int top_order(const Request& r) {
+  int top = 1;
+  for (int e = 0; e < r.K; ++e)
+    for (int d = 0; d < r.dim; ++d) top = std::max(top, (int)r.orders[e * 3 + d]);
+  return top;
+}
+
+bool batchable(const Request& r) { return !r.sp.adapt && !r.sp.fmg; }
+
+bool same_cycle(const dg_mg_params& a, const dg_mg_params& b) {
+  return a.beta1 == b.beta1 && a.beta2 == b.beta2 && a.beta_c == b.beta_c && a.direction == b.direction &&
+         a.coarsest == b.coarsest && a.delta_n == b.delta_n && a.graph == b.graph && a.control == b.control &&
+         a.eta == b.eta;
+}
+
+// Requests whose solves a batch advances exactly as alone: same dimension and
+// mapping order (a batch's geometry), arithmetic and cycle, and the same top
+// order (a batch cycle visits the levels of its largest top order).
+bool compatible(const Request& a, const Request& b) {
+  return batchable(a) && batchable(b) && a.dim == b.dim && a.M == b.M && a.sp.arith == b.sp.arith &&
+         same_cycle(a.sp.mg, b.sp.mg) && top_order(a) == top_order(b);
+}
+
+struct Member {
+  std::shared_ptr<Request> r;
+  int cycles = 0;         // V-cycles run for it
+  double rn = 0.0;        // max |r| at its last check
+  double dofs = 0.0;      // its share of the operator evaluations
+  int64_t nodes = 0;
+  int checked_at = -1;    // cycle count at its last residual check (-1: none yet)
+  int slot = -1;          // index in the current batch
+};
+
+// One slot's batch of requests that share launches.
+struct Cohort {
+  dg_server* S;
+  cudaStream_t st;
+  std::vector<Member> mem;     // running members, in batch order
+  dg_mesh* b = nullptr;        // current batch
+  double* q = nullptr;         // its state and source (5 x nodes each)
+  double* s = nullptr;
+  AllocCtx ac;                 // q and s
+  int64_t nodes = 0;
+  std::vector<int64_t> off;    // node offsets of the solves
+  std::vector<int32_t> active; // per batch slot: 1 running, 0 finished (held)
+
+  Cohort(dg_server* srv, cudaStream_t stream) : S(srv), st(stream) {}
+
+  // Take queued requests that can join (in arrival order), up to batch_max
+  // running members and the memory budget.  Needs the server lock.
+  bool gather_locked() {
+    bool took = false;
+    const Request& ref = *mem.front().r;
+    for (auto it = S->queue.begin(); it != S->queue.end() && (int)mem.size() < S->p.batch_max;) {
+      const std::shared_ptr<Request>& c = *it;
+      if (compatible(ref, *c) && S->used + c->est <= S->p.hbm_budget) {
+        S->used += c->est;
+        c->state = DG_REQ_RUNNING;
+        c->t_start = seconds_since(S->t0);
+        Member m;
+        m.r = c;
+        mem.push_back(m);
+        it = S->queue.erase(it);
+        took = true;
+      } else {
+        ++it;
+      }
+    }
+    return took;
+  }
+
+  // The running members' current states (or their starts) in a new batch of
+  // the running members; the old batch and arrays are freed.
+  int rebuild() {
+    const int n = (int)mem.size();
+    std::vector<dg_mesh_desc> descs(n);
+    std::vector<const int32_t*> ords(n);
+    for (int k = 0; k < n; ++k) {
+      const Request& r = *mem[k].r;
+      descs[k].dim = r.dim;
+      descs[k].K = r.K;
+      descs[k].M = r.M;
+      descs[k].xmap = r.xmap.data();
+      descs[k].ftab = r.ftab.data();
+      std::memcpy(descs[k].params, r.params, sizeof(r.params));
+      ords[k] = r.orders.data();
+    }
+    dg_mesh* nb = nullptr;
+    int rc = dg_batch_create(descs.data(), ords.data(), n, &nb);
+    if (rc == DG_OK && mem.front().r->sp.arith != DG_ARITH_FP64) rc = dg_set_arithmetic(nb, mem.front().r->sp.arith);
+    if (rc != DG_OK) {
+      if (nb) dg_mesh_destroy(nb);
+      return rc;
+    }
+    int32_t ns = 0;
+    std::vector<int64_t> noff(n + 1);
+    dg_batch_info(nb, &ns, noff.data());
+    const int64_t nn = noff[n];
+    AllocCtx nac;
+    double* nq = static_cast<double*>(alloc_cb((size_t)5 * nn * sizeof(double), &nac));
+    double* nsrc = static_cast<double*>(alloc_cb((size_t)5 * nn * sizeof(double), &nac));
+    if (!nq || !nsrc) {
+      dg_mesh_destroy(nb);
+      free_all(nac);
+      return DG_ENOMEM;
+    }
+    std::vector<std::vector<double>> staged;  // host starts, alive until the copies are done
+    for (int k = 0; k < n; ++k) {
+      Member& m = mem[k];
+      const Request& r = *m.r;
+      const int64_t len = noff[k + 1] - noff[k];
+      m.nodes = len;
+      double* dq = nq + 5 * noff[k];
+      if (m.slot >= 0) {  // a running member: its current state, exactly
+        cudaMemcpyAsync(dq, q + 5 * off[m.slot], (size_t)5 * len * sizeof(double), cudaMemcpyDeviceToDevice, st);
+      } else if (!r.q0.empty()) {
+        cudaMemcpyAsync(dq, r.q0.data(), (size_t)5 * len * sizeof(double), cudaMemcpyHostToDevice, st);
+      } else {  // the freestream of its parameters
+        std::vector<double> fs((size_t)5 * len);
+        int64_t o = 0;
+        for (int e = 0; e < r.K; ++e) {
+          int64_t ne = 1;
+          for (int d = 0; d < r.dim; ++d) ne *= r.orders[e * 3 + d] + 1;
+          for (int v = 0; v < 5; ++v)
+            for (int64_t i = 0; i < ne; ++i) fs[(size_t)(5 * o + v * ne + i)] = r.params[7 + v];
+          o += ne;
+        }
+        staged.push_back(std::move(fs));
+        cudaMemcpyAsync(dq, staged.back().data(), (size_t)5 * len * sizeof(double), cudaMemcpyHostToDevice, st);
+      }
+      double* ds = nsrc + 5 * noff[k];
+      if (!r.s.empty())
+        cudaMemcpyAsync(ds, r.s.data(), (size_t)5 * len * sizeof(double), cudaMemcpyHostToDevice, st);
+      else  // no source: zeros give the same bits as a NULL source
+        cudaMemsetAsync(ds, 0, (size_t)5 * len * sizeof(double), st);
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+      dg_mesh_destroy(nb);
+      free_all(nac);
+      return DG_ECUDA;
+    }
+    release_batch();
+    b = nb;
+    q = nq;
+    s = nsrc;
+    ac = std::move(nac);
+    nodes = nn;
+    off = noff;
+    active.assign(n, 1);
+    for (int k = 0; k < n; ++k) mem[k].slot = k;
+    const int peers = n - 1;
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      for (Member& m : mem) m.r->batch_peers = std::max(m.r->batch_peers, peers);
+    }
+    return DG_OK;
+  }
+
+  void release_batch() {
+    if (b) dg_mesh_destroy(b);
+    b = nullptr;
+    free_all(ac);
+    ac = AllocCtx();
+    q = s = nullptr;
+  }
+
+  // Hand a member's result back (copy of its state, report), hold its solve
+  // in the batch and drop it from the running members.
+  void finish(size_t k, int status) {
+    Member& m = mem[k];
+    Outcome out;
+    out.state = status;
+    out.rep.cycles = m.cycles;
+    out.rep.status = status;
+    out.rep.rnorm = m.rn;
+    out.rep.dof_evals = m.dofs;
+    out.rep.nodes = m.nodes;
+    out.q.resize((size_t)5 * m.nodes);
+    cudaMemcpyAsync(out.q.data(), q + 5 * off[m.slot], out.q.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    out.orders = m.r->orders;
+    out.dev_bytes = (int64_t)((double)(dg::mesh_device_bytes(b) + ac.bytes) * (double)m.nodes / (double)nodes);
+    active[m.slot] = 0;
+    publish(*m.r, out);
+    mem.erase(mem.begin() + (long)k);
+  }
+
+  void publish(Request& r, Outcome& out) {
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->used -= r.est;
+      r.rep = out.rep;
+      r.q.swap(out.q);
+      r.orders_out.swap(out.orders);
+      r.dev_bytes = out.dev_bytes;
+      r.state = out.state;
+      r.t_end = seconds_since(S->t0);
+      r.q0.clear();
+      r.q0.shrink_to_fit();
+      r.s.clear();
+      r.s.shrink_to_fit();
+    }
+    S->cv_done.notify_all();
+    S->cv_work.notify_all();
+  }
+
+  // Fail every running member with rc.
+  void fail_all(int rc) {
+    for (Member& m : mem) {
+      Outcome out;
+      out.state = rc;
+      out.rep.status = rc;
+      out.rep.cycles = m.cycles;
+      publish(*m.r, out);
+    }
+    mem.clear();
+  }
+
+  // The check of the steady driver at a member's check point: stop when
+  // max |r| < tol, on a NaN/inf residual, or at the cycle cap.
+  int decide(const Member& m) const {
+    const dg_solve_params& sp = m.r->sp;
+    if (m.rn < sp.tol) return DG_OK;
+    if (std::isnan(m.rn) || std::isinf(m.rn)) return DG_EDIVERGED;
+    if (m.cycles >= sp.max_cycles) return DG_ENOTCONVERGED;
+    return 1;  // go on
+  }
+
+  static int every(const Member& m) { return std::max(1, (int)m.r->sp.check_every); }
+
+  bool at_check(const Member& m) const {
+    if (m.checked_at == m.cycles) return false;  // (a rebuild at a check point: already checked)
+    return m.checked_at < 0 || m.cycles % every(m) == 0 || m.cycles >= m.r->sp.max_cycles;
+  }
+
+  // Residual checks of the members at a check point; members that stop are
+  // handed back.  Returns DG_OK or an error of the library.
+  int checks() {
+    std::vector<double> norms(active.size());
+    int rc = dg_residual_norms(b, q, s, norms.data(), st);
+    if (rc != DG_OK) return rc;
+    bool held = false;
+    for (size_t k = 0; k < mem.size();) {
+      Member& m = mem[k];
+      if (at_check(m)) {
+        m.rn = norms[m.slot];
+        m.checked_at = m.cycles;
+        m.dofs += 5.0 * (double)m.nodes;
+        const int d = decide(m);
+        if (d <= 0) {
+          finish(k, d);
+          held = true;
+          continue;
+        }
+      }
+      ++k;
+    }
+    if (held && !mem.empty()) rc = dg_batch_set_active(b, active.data(), st);
+    return rc;
+  }
+
+  // Cycles until the next member reaches a check point.
+  int cycles_to_next_check() const {
+    int n = INT32_MAX;
+    for (const Member& m : mem) {
+      const int cap = m.r->sp.max_cycles;
+      const int next = std::min((m.cycles / every(m) + 1) * every(m), cap);
+      n = std::min(n, next - m.cycles);
+    }
+    return std::max(1, n);
+  }
+
+  void run() {
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      gather_locked();
+    }
+    int rc = rebuild();
+    while (rc == DG_OK && !mem.empty()) {
+      if ((rc = checks()) != DG_OK) break;
+      bool joined;
+      {
+        std::lock_guard<std::mutex> lk(S->mu);
+        joined = !mem.empty() ? gather_locked() : false;
+      }
+      const int held = (int)active.size() - (int)std::count(active.begin(), active.end(), 1);
+      if (joined || (held > 0 && held >= (int)mem.size() && !mem.empty())) {
+        if ((rc = rebuild()) != DG_OK) break;
+        continue;  // new members take their first check before any cycle
+      }
+      if (mem.empty()) {  // all done: take a new compatible group if one waits
+        break;
+      }
+      const int n = cycles_to_next_check();
+      const dg_mg_params mg = mem.front().r->sp.mg;
+      for (int c = 0; c < n && rc == DG_OK; ++c) {
+        dg_cycle_report crep{};
+        rc = dg_pmg_vcycle(b, q, s, &mg, 0, &crep, st);
+        for (Member& m : mem) {
+          m.cycles += 1;
+          m.dofs += crep.dof_evals * (double)m.nodes / (double)nodes;
+        }
+      }
+    }
+    if (rc != DG_OK) fail_all(rc);
+    release_batch();
+  }
+};
+
 void worker(dg_server* S) {
   cudaSetDevice(S->p.device);
   cudaStream_t st = nullptr;
@@ -237,6 +555,19 @@ void worker(dg_server* S) {
       S->used += r->est;
       r->state = DG_REQ_RUNNING;
       r->t_start = seconds_since(S->t0);
+    }
+    if (S->p.batch_max > 1 && batchable(*r)) {  // shared launches with compatible requests
+      Cohort c(S, st);
+      Member m;
+      m.r = r;
+      c.mem.push_back(m);
+      try {
+        c.run();
+      } catch (const std::exception&) {  // host allocation failure: its requests fail, the server lives
+        c.fail_all(DG_ENOMEM);
+        c.release_batch();
+      }
+      continue;
     }
     Outcome out;
     try {
@@ -402,6 +733,8 @@ int dg_server_info(dg_server* S, int64_t id, dg_request_info* info) {
   info->t_submit = r->t_submit;
   info->t_start = r->t_start;
   info->t_end = r->t_end;
+  info->batch_peers = r->batch_peers;
+  info->reserved = 0;
   return DG_OK;
 }
 

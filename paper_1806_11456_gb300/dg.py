@@ -47,13 +47,15 @@ ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 
 
 class ServerParams(ctypes.Structure):
-    _fields_ = [("hbm_budget", ctypes.c_int64), ("slots", ctypes.c_int32), ("device", ctypes.c_int32)]
+    _fields_ = [("hbm_budget", ctypes.c_int64), ("slots", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("batch_max", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class RequestInfo(ctypes.Structure):
     _fields_ = [("state", ctypes.c_int32), ("K", ctypes.c_int32), ("rep", SolveReport),
                 ("est_bytes", ctypes.c_int64), ("dev_bytes", ctypes.c_int64), ("t_submit", ctypes.c_double),
-                ("t_start", ctypes.c_double), ("t_end", ctypes.c_double)]
+                ("t_start", ctypes.c_double), ("t_end", ctypes.c_double), ("batch_peers", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 REQ_QUEUED, REQ_RUNNING = 1, 2
@@ -88,7 +90,7 @@ EXPORTS = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_layout", "dg_residual",
            "dg_batch_create", "dg_batch_info", "dg_residual_norms", "dg_solve_footprint", "dg_server_create",
            "dg_server_submit", "dg_server_wait", "dg_server_info", "dg_server_result", "dg_server_release",
            "dg_server_destroy", "dg_set_autotune", "dg_mesh_tuning", "dg_measure_fma_rates", "dg_residual_tangent",
-           "dg_last_error"]
+           "dg_batch_set_active", "dg_last_error"]
 ARITH = {"fp64": 0, "df32": 1, "mixed": 2}
 KERNEL_STAGES = ["trace_q", "mortar_u_star", "volume", "mortar_flux", "surface", "isolated"]
 
@@ -135,6 +137,7 @@ def lib(path=LIB_PATH):
     L.dg_server_destroy.argtypes = [_vp]
     L.dg_measure_fma_rates.argtypes = [_dp, _dp, _vp]
     L.dg_residual_tangent.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+    L.dg_batch_set_active.argtypes = [_vp, _ip, _vp]
     _lib = L
     return L
 
@@ -254,6 +257,12 @@ class Mesh:
         off = np.zeros(n.value + 1, dtype=np.int64)
         _check(lib().dg_batch_info(self.h, ctypes.byref(n), off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
         return off
+
+    def set_active(self, active, stream=None):
+        """Hold the solves whose flag is 0 (dg_batch_set_active)."""
+        a = np.ascontiguousarray(active, dtype=np.int32)
+        _check(lib().dg_batch_set_active(self.h, a.ctypes.data_as(_ip), _stream(stream)))
+        return self
 
     def residual_norms(self, q, s=None, stream=None):
         n = ctypes.c_int32()
@@ -444,14 +453,15 @@ def solve_footprint(mesh, orders, params):
 class Server:
     """Serving loop (dg_server_*): steady solves submitted as host arrays run
     in `slots` concurrent workers, admitted while their memory estimates fit
-    in `hbm_budget` bytes."""
+    in `hbm_budget` bytes; with batch_max > 1 each worker runs up to
+    batch_max compatible requests in shared launches."""
 
-    def __init__(self, hbm_budget, slots=4, device=None):
+    def __init__(self, hbm_budget, slots=4, device=None, batch_max=1):
         import torch
         if not torch.cuda.is_available():
             raise DGError("no CUDA device: the DGSEM library has no CPU path")
         p = ServerParams()
-        p.hbm_budget, p.slots = int(hbm_budget), int(slots)
+        p.hbm_budget, p.slots, p.batch_max = int(hbm_budget), int(slots), int(batch_max)
         p.device = torch.cuda.current_device() if device is None else int(device)
         self.h = _vp()
         _check(lib().dg_server_create(ctypes.byref(p), ctypes.byref(self.h)))
@@ -478,7 +488,7 @@ class Server:
         _check(lib().dg_server_info(self.h, int(rid), ctypes.byref(i)))
         r = i.rep
         return dict(state=i.state, K=i.K, est_bytes=i.est_bytes, dev_bytes=i.dev_bytes, t_submit=i.t_submit,
-                    t_start=i.t_start, t_end=i.t_end,
+                    t_start=i.t_start, t_end=i.t_end, batch_peers=i.batch_peers,
                     rep=dict(cycles=r.cycles, fmg_cycles=r.fmg_cycles, adapted=r.adapted, status=r.status,
                              rnorm=r.rnorm, rnorm_adapt=r.rnorm_adapt, dof_evals=r.dof_evals, nodes=r.nodes))
 

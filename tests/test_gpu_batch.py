@@ -112,3 +112,36 @@ def test_batch_rejects_mixed_dimensions(dg):
     b = _solves_3d(1, 4)[0]
     with pytest.raises(dg.DGError):
         dg.Mesh.batch([(a[0], a[1], a[2]), (b[0], b[1], b[2])])
+
+
+@pytest.mark.parametrize("arith", ["fp64", "mixed"])
+def test_held_solves_stay_put_and_the_others_advance_as_alone(dg, arith):
+    """dg_batch_set_active: a held solve's state is bitwise unchanged by later
+    cycles (its time step is 0 in every sweep, so every correction it gets is
+    exactly 0), while the other solves advance as they do alone; with the
+    smoothing control on, the held solve counts as satisfied."""
+    items = _solves_2d(3, 11)
+    B = dg.Mesh.batch([(m, o, p) for (m, o, p, _) in items]).set_arithmetic(arith)
+    off = B.solve_slices()
+    qb = _dev(np.concatenate([q for (*_, q) in items]))
+    kw = dict(beta1=1, beta2=2, beta_c=3)
+    B.vcycle(qb, None, graph=True, **kw)
+    before = qb.cpu().numpy()
+    B.set_active([1, 0, 1])
+    for graph in (True, False):
+        B.vcycle(qb, None, graph=graph, **kw)
+    if arith == "fp64":
+        B.vcycle(qb, None, control=2, **kw)
+    after = qb.cpu().numpy()
+    assert np.array_equal(after[5 * off[1]:5 * off[2]], before[5 * off[1]:5 * off[2]])
+    for k in (0, 2):
+        m, o, p, q = items[k]
+        A = dg.Mesh(m, o, p).set_arithmetic(arith)
+        qa = _dev(q)
+        A.vcycle(qa, None, graph=True, **kw)
+        A.vcycle(qa, None, graph=True, **kw)
+        A.vcycle(qa, None, graph=False, **kw)
+        if arith == "fp64":
+            A.vcycle(qa, None, control=2, **kw)
+        assert np.array_equal(after[5 * off[k]:5 * off[k + 1]], qa.cpu().numpy()), k
+        assert not np.array_equal(after[5 * off[k]:5 * off[k + 1]], before[5 * off[k]:5 * off[k + 1]])

@@ -158,3 +158,58 @@ def test_double_float_requests_equal_alone(dg):
             qd, _ = M.solve_steady(torch.tensor(q, device="cuda"), torch.tensor(s, device="cuda"),
                                    tol=1e-30, max_cycles=3, mg=MG)
             assert np.array_equal(qs, qd.cpu().numpy())
+
+
+def _shared_requests(n, seed, top=3):
+    """2D requests that can share launches (same top order) with different
+    flow parameters, sizes and order maps, and a 3D one that cannot."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        mesh = syn.periodic_box(int(rng.integers(2, 5)), int(rng.integers(2, 4)), 1, dim=2)
+        o = syn.random_orders(mesh["K"], 2, 1, top, seed * 10 + k)
+        o[0, :2] = top
+        prm = syn.flow_params(mach=float(rng.uniform(0.1, 0.4)), re=float(10 ** rng.uniform(2, 4)))
+        q = syn.perturbed_state(mesh, o, prm, k, amp=0.02)
+        s = syn.random_source(mesh, o, k + 1, amp=1e-3) if k % 2 == 0 else None
+        out.append((mesh, o, prm, q, s))
+    mesh = syn.rotate_elements(syn.periodic_box(2, 2, 2), seed=3, frac=0.5)
+    o = syn.random_orders(mesh["K"], 3, 2, 3, 77)
+    prm = syn.flow_params(mach=0.3, re=200.0)
+    out.append((mesh, o, prm, syn.perturbed_state(mesh, o, prm, 9, amp=0.02), None))
+    return out
+
+
+def test_shared_launches_equal_alone(dg):
+    """Shared launches (batch_max > 1): one slot runs the compatible requests
+    as one batch, members with their own cycle caps, tolerances and check
+    intervals leave at their own check points, and requests submitted while
+    the batch runs join it.  Every result -- state, cycles and status -- is
+    bit for bit that of the same request alone; the incompatible 3D request
+    runs on its own."""
+    import time
+    reqs = _shared_requests(7, 3)
+    kws = []
+    for k in range(len(reqs)):
+        kw = dict(tol=1e-30, max_cycles=3 + k % 4, check_every=1 + k % 3, mg=MG)
+        if k == 2:
+            kw["tol"] = 1e30  # stops at its first check, before any cycle
+        kws.append(kw)
+    with dg.Server(hbm_budget=8 << 30, slots=1, batch_max=4) as S:
+        ids = []
+        for k, ((m, o, p, q, s), kw) in enumerate(zip(reqs, kws)):
+            ids.append(S.submit(m, o, p, q0=q, s=s, **kw))
+            if k == 3:
+                time.sleep(0.2)  # the rest arrive while the first batch runs
+        S.wait()
+        peers = []
+        for rid, (m, o, p, q, s), kw in zip(ids, reqs, kws):
+            info = S.info(rid)
+            qs, os_ = S.result(rid)
+            qa, oa, rep = _alone(dg, m, o, p, q, s, **kw)
+            assert np.array_equal(os_, oa)
+            assert info["rep"]["cycles"] == rep["cycles"] and info["state"] == rep["status"], (rid, info, rep)
+            assert np.array_equal(qs, qa), rid
+            peers.append(info["batch_peers"])
+    assert max(peers[:-1]) >= 1      # the 2D requests shared launches
+    assert peers[-1] == 0            # the 3D one could not
