@@ -403,7 +403,8 @@ def serving(dg, torch, dev, rate=4.0, window=4.0, slots=8, budget=150 << 30, see
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * window * 3)))
     arrivals = arrivals[arrivals < window]
     reqs = serving_requests(dg, torch, dev, len(arrivals), seed)
-    kw = dict(tol=1e-10, max_cycles=1500, check_every=10, mg=dict(beta1=3, beta2=3, beta_c=10, graph=1))
+    # (at most 4000 cycles: the slowest request, a 720-DOF box, needs more than 1500)
+    kw = dict(tol=1e-10, max_cycles=4000, check_every=10, mg=dict(beta1=3, beta2=3, beta_c=10, graph=1))
 
     def run(n_slots, arith, batch_max=1, details=False):
         kwa = dict(kw, arith=arith)
@@ -445,7 +446,7 @@ def serving(dg, torch, dev, rate=4.0, window=4.0, slots=8, budget=150 << 30, see
     nodes = [int(np.sum(np.prod(o[:, :m["dim"]] + 1, axis=1))) for (m, o, *_r) in reqs]
     return {"workload": f"{len(reqs)} requests, Poisson {rate}/s over {window} s: periodic 2D boxes 2-6 per side "
                         "N in {2,3} and 3D boxes 3 per side N = 2, Mach U[0.25,0.4], Re U_log[50,200], "
-                        "S = A(q*), to max|r| < 1e-10 (at most 1500 V-cycles 3/3/10, residual checked every 10)",
+                        "S = A(q*), to max|r| < 1e-10 (at most 4000 V-cycles 3/3/10, residual checked every 10)",
             "requests": len(reqs), "dof_range": [5 * min(nodes), 5 * max(nodes)],
             "offered_dof_per_s": 5.0 * sum(nodes) / window,
             "concurrent": conc, "concurrent_fp64": conc64, "shared_fp64": shared64, "shared_mixed": shared_mx,
