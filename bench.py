@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--c2-solve", action="store_true",
                     help="also run the steady driver with adaptation on the flat plate (several minutes)")
+    ap.add_argument("--serving-large", action="store_true",
+                    help="also serve larger requests (1e4-5e4 DOF, random order maps; a few minutes)")
     ap.add_argument("--mg-compare", type=int, default=0, metavar="CYCLES",
                     help="also compare isotropic and anisotropic V-cycles on the flat plate for CYCLES cycles "
                          "(about a second per cycle; off by default)")
@@ -316,6 +318,15 @@ def batched_solves(dg, torch, dev, steps=5):
     b_ms, b_dofs = timed(batch_step, steps)
     b_launches = (dg.kernel_launches() - launches0) // steps
     batch_once = [x.cpu().numpy() for x in q]
+    # the same batched step in the mixed form (FP32 tangent smoothing and
+    # coarse operators, FP64 finest residual): config-4 precision
+    for H in handles:
+        H.set_arithmetic("mixed")
+    for _ in range(2):
+        batch_step()
+    m_ms, m_dofs = timed(batch_step, steps)
+    for H in handles:
+        H.set_arithmetic("fp64")
     norms = np.concatenate([H.residual_norms(x) for H, x in zip(handles, q)])
     stage = {}
     for d, H, x0 in zip((2, 3), handles, q0):
@@ -356,6 +367,9 @@ def batched_solves(dg, torch, dev, steps=5):
             "dof": 5 * nodes, "step": "one V-cycle 8->1 (b1=2,b2=2,bc=4) of every solve, CUDA graph per handle",
             "batched": {"value": b_dofs / (b_ms * 1e-3), "unit": "DOF/s", "ms_per_step": b_ms,
                         "launches_per_step": int(b_launches)},
+            "batched_mixed": {"value": m_dofs / (m_ms * 1e-3), "unit": "DOF/s", "ms_per_step": m_ms,
+                              "note": "one mixed-precision cycle of every solve (a different iteration from the FAS "
+                                      "cycle; FP64 finest residual, FP32 tangent smoothing and coarse operators)"},
             "one_at_a_time": {"value": s_dofs / (s_ms * 1e-3), "unit": "DOF/s", "ms_per_step": s_ms,
                               "launches_per_step": int(s_launches)},
             "speedup": s_ms / b_ms, "bitwise_equal_alone": bool(same), "residual_stages": stage,
@@ -452,6 +466,76 @@ def serving(dg, torch, dev, rate=4.0, window=4.0, slots=8, budget=150 << 30, see
             "concurrent": conc, "concurrent_fp64": conc64, "shared_fp64": shared64, "shared_mixed": shared_mx,
             "one_at_a_time": seq,
             "p99_speedup": seq["p99_s"] / conc["p99_s"], "p50_speedup": seq["p50_s"] / conc["p50_s"]}
+
+
+def serving_large(dg, torch, dev, rate=2.0, window=4.0, seed=6):
+    """Serving with larger requests (opt-in, --serving-large): Poisson
+    arrivals (rate per second over `window` seconds) of periodic 2D boxes of
+    12-28 elements per side at orders U[2,3]^2 (top order 3) and 3D boxes of
+    4 or 8 per side at orders U[1,2]^3 (top order 2), elements of size 0.25
+    (the domain grows with the request), Mach U[0.25,0.4], Re U_log[50,200],
+    each a steady problem S = A(q*) with q* the manufactured field, started
+    at q* plus a 1 % smooth wave, solved to max|r| < 1e-10 (at most 6000
+    V-cycles 3/3/10, residual every 10).  Served one at a time in FP64, by 8
+    concurrent slots in FP64, and by 2 slots with shared launches (up to 8
+    per batch) in the mixed form."""
+    from paper_1806_11456_gb300 import synthetic as syn
+    import threading as th
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * window * 3)))
+    arrivals = arrivals[arrivals < window]
+    reqs = []
+    for k in range(len(arrivals)):
+        mach = float(rng.uniform(0.25, 0.4))
+        re = float(np.exp(rng.uniform(np.log(50.0), np.log(200.0))))
+        prm = syn.flow_params(mach=mach, re=re)
+        if k % 3 == 2:
+            n = int(rng.choice([4, 8]))
+            mesh = syn.periodic_box(n, n, n, L=(n / 4, n / 4, n / 4))
+            o = syn.random_orders(mesh["K"], 3, 1, 2, seed * 100 + k)
+            o[0] = 2
+        else:
+            n = int(rng.choice([12, 16, 20, 24, 28]))
+            mesh = syn.periodic_box(n, n, 1, L=(n / 4, n / 4, 1.0), dim=2)
+            o = syn.random_orders(mesh["K"], 2, 2, 3, seed * 100 + k)
+            o[0, :2] = 3
+        q_star = syn.manufactured_state(mesh, o, seed * 1000 + k, mach, prm[0], amp=0.05)
+        S, q0 = steady_problem(dg, torch, dev, mesh, o, prm, q_star, seed=k)
+        reqs.append((mesh, o, prm, q0, S))
+    kw = dict(tol=1e-10, max_cycles=6000, check_every=10, mg=dict(beta1=3, beta2=3, beta_c=10, graph=1))
+
+    def run(n_slots, arith, batch_max=1):
+        ids = [None] * len(reqs)
+        with dg.Server(hbm_budget=150 << 30, slots=n_slots, batch_max=batch_max) as S:
+            t0 = time.perf_counter()
+
+            def feed():
+                for i, (t, (m, o, p, q0, src)) in enumerate(zip(arrivals, reqs)):
+                    dt = t - (time.perf_counter() - t0)
+                    if dt > 0:
+                        time.sleep(dt)
+                    ids[i] = S.submit(m, o, p, q0=q0, s=src, arith=arith, **kw)
+
+            feeder = th.Thread(target=feed)
+            feeder.start()
+            feeder.join()
+            S.wait()
+            makespan = time.perf_counter() - t0
+            infos = [S.info(i) for i in ids]
+        lat = np.array([x["t_end"] - x["t_submit"] for x in infos])
+        return {"slots": n_slots, "arith": arith, "batch_max": batch_max, "p50_s": float(np.percentile(lat, 50)),
+                "p99_s": float(np.percentile(lat, 99)), "makespan_s": makespan,
+                "served_dof_evals_per_s": sum(x["rep"]["dof_evals"] for x in infos) / makespan,
+                "converged": sum(1 for x in infos if x["state"] == 0),
+                "cycles": [x["rep"]["cycles"] for x in infos], "max_batch_peers": max(x["batch_peers"] for x in infos)}
+
+    nodes = [int(np.sum(np.prod(o[:, :m["dim"]] + 1, axis=1))) for (m, o, *_r) in reqs]
+    return {"workload": f"{len(reqs)} requests, Poisson {rate}/s over {window} s: periodic 2D boxes 12-28 per side "
+                        "orders U[2,3]^2 and 3D boxes 4 or 8 per side orders U[1,2]^3, element size 0.25, "
+                        "S = A(q*), to max|r| < 1e-10 (scaled down from 20/s over 120 s and 1e4-2e7 DOF)",
+            "dof": [5 * n for n in nodes], "offered_dof_per_s": 5.0 * sum(nodes) / window,
+            "one_at_a_time": run(1, "fp64"), "concurrent_fp64": run(8, "fp64"),
+            "shared_mixed": run(2, "mixed", batch_max=8)}
 
 
 def precision_report(dg, torch, dev):
@@ -838,6 +922,8 @@ def run_gb300(args, rank, world):
         out["precision"] = precision_report(dg, torch, dev)
         if args.c2_solve:
             out["c2_solve"] = c2_solve(dg, torch, dev)
+        if args.serving_large:
+            out["serving_large"] = serving_large(dg, torch, dev)
         if args.mg_compare > 0:
             out["mg_compare"] = mg_compare(dg, torch, dev, args.mg_compare)
         out["cpu_baseline"] = cpu_baseline_sample(mesh, prm, orders, q_np) if world == 1 else None
