@@ -1207,6 +1207,198 @@ __global__ void __launch_bounds__(kVolThreads) __maxnreg__(DIM == 2 ? 96 : 104) 
 }
 
 // ---------------------------------------------------------------------------
+// k_volume_split: the same volume stage for levels with few warps per SM
+// ---------------------------------------------------------------------------
+// On a coarse level a tile holds few nodes and the SMs hold about one warp
+// each, so a launch lasts as long as one thread's serial FP64 instruction
+// stream.  This variant gives each phase more independent work items -- one
+// per (node, variable) in the gradient and the divergence, per (node,
+// direction) in the nodal fluxes, per (face node, component) in the traces
+// -- so that four to five times as many warps share the SM's FP64 pipe.
+// Every output is computed by the same operations in the same order as in
+// k_volume, so the results are the same bits.
+
+// BR1 gradient of variable v of (u, v, w, T) at node i before the 1/J
+// scaling: the work of gradient_volume (and, on curved elements, of the
+// lifting of U*) for one variable.
+template <typename R, int DIM, bool AFFINE>
+DEV void gradient_var(const LevelArgsT<R>& A, const R* sD, const R* sA, int T, int nn, int i, int n0, int n1,
+                      int n2, int v, int e, const typename Store<R>::T* __restrict__ ust, R* g) {
+  using SR = Store<R>;
+  const int le = i / nn, node = i - le * nn;
+  const int idx0 = node % n0, idx1 = (node / n0) % n1, idx2 = node / (n0 * n1);
+  g[0] = cst<R>(0.0f);
+  g[1] = cst<R>(0.0f);
+  g[2] = cst<R>(0.0f);
+  const int32_t* fo_e = A.fo + e * 6;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const int id = pick(d, idx0, idx1, idx2), nd = pick(d, n0, n1, n2);
+    const int sd = (d == 0) ? 1 : (d == 1 ? n0 : n0 * n1);
+    const int base = le * nn + node - id * sd;
+    const R* Drow = sD + d * kNP * kNP + id * kNP;
+    if (AFFINE) {
+      R cu = cst<R>(0.0f);
+      for (int a = 0; a < nd; ++a) cu = madd(cu, Drow[a], sA[v * T + base + a * sd]);
+      const int ta = (d == 0) ? 1 : 0, tb = (d == 2) ? 1 : 2;
+      const int fp = pick(tb, idx0, idx1, idx2) * pick(ta, n0, n1, n2) + pick(ta, idx0, idx1, idx2);
+      const int64_t pm = fo_e[2 * d] + fp, pp = fo_e[2 * d + 1] + fp;
+      const R wm = -Tab<R>::lmw(nd, id), wp = Tab<R>::lpw(nd, id);
+      cu = madd(cu, wm, SR::get(ust, v * A.fn + pm));
+      cu = madd(cu, wp, SR::get(ust, v * A.fn + pp));
+      const R j0 = sA[(4 + d * 3 + 0) * T + i], j1 = sA[(4 + d * 3 + 1) * T + i], j2 = sA[(4 + d * 3 + 2) * T + i];
+      g[0] = madd(g[0], j0, cu);
+      g[1] = madd(g[1], j1, cu);
+      g[2] = madd(g[2], j2, cu);
+    } else {
+      for (int a = 0; a < nd; ++a) {
+        const int la = base + a * sd;
+        const R c = Drow[a];
+        const R j0 = c * sA[(4 + d * 3 + 0) * T + la];
+        const R j1 = c * sA[(4 + d * 3 + 1) * T + la];
+        const R j2 = c * sA[(4 + d * 3 + 2) * T + la];
+        const R uv = sA[v * T + la];
+        g[0] = madd(g[0], j0, uv);
+        g[1] = madd(g[1], j1, uv);
+        g[2] = madd(g[2], j2, uv);
+      }
+    }
+  }
+  if (!AFFINE) {
+#pragma unroll
+    for (int f = 0; f < 2 * DIM; ++f) {
+      int d, ta, tb, side;
+      face_dirs(f, d, ta, tb, side);
+      const int nd = pick(d, n0, n1, n2), id = pick(d, idx0, idx1, idx2);
+      const R lw = side ? Tab<R>::lpw(nd, id) : Tab<R>::lmw(nd, id);
+      const int64_t p = fo_e[f] + pick(tb, idx0, idx1, idx2) * pick(ta, n0, n1, n2) + pick(ta, idx0, idx1, idx2);
+      const R m0 = lw * SR::get(A.fnS, p), m1 = lw * SR::get(A.fnS, A.fn + p), m2 = lw * SR::get(A.fnS, 2 * A.fn + p);
+      const R us = SR::get(ust, v * A.fn + p);
+      g[0] = madd(g[0], m0, us);
+      g[1] = madd(g[1], m1, us);
+      g[2] = madd(g[2], m2, us);
+    }
+  }
+}
+
+// The blockDim must be at least DIM x (the tile's nodes): the nodal-flux
+// phase reads every input of its item before a barrier and writes after it.
+template <typename R, int DIM, bool AFFINE>
+__global__ void __launch_bounds__(kVolThreads) __maxnreg__(DIM == 2 ? 96 : 104)
+    k_volume_split(LevelArgsT<R> A, int tile0, const GasT<R>* __restrict__ gas, const double* __restrict__ q,
+                   const typename Store<R>::T* __restrict__ ust, typename Store<R>::T* __restrict__ trg,
+                   typename Store<R>::T* __restrict__ vol) {
+  pdl_enter();
+  using SR = Store<R>;
+  extern __shared__ double smem_raw[];
+  const ElemTile t = A.tiles[tile0 + blockIdx.x];
+  const int n0 = t.n[0], n1 = t.n[1], n2 = t.n[2];
+  const int nn = n0 * n1 * n2;
+  const int T = t.count * nn;
+  R* sD = reinterpret_cast<R*>(smem_raw);
+  R* sq = sD + 3 * kNP * kNP;
+  R* sA = sq + 5 * T;
+  R* sG = sA + 15 * T;
+  load_dtables<R>(sD, Tab<R>::Dhat(), n0, n1, n2, DIM);
+  stage_tile<R>(A, t, nn, T, gas, q, sq, sA);
+  __syncthreads();
+  // ---- gradient: one (node, variable) per item ----
+  for (int w = threadIdx.x; w < 4 * T; w += blockDim.x) {
+    const int i = w % T, v = w / T;
+    const int le = i / nn, node = i - le * nn;
+    const int e = A.tile_elems[t.first + le];
+    R g[3];
+    gradient_var<R, DIM, AFFINE>(A, sD, sA, T, nn, i, n0, n1, n2, v, e, ust, g);
+    const R iJ = SR::get(A.geo, 9 * A.nodes + A.off[e] + node);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) sG[(v * 3 + c) * T + i] = g[c] * iJ;
+  }
+  __syncthreads();
+  // ---- gradient face traces: one (face node, component) per item ----
+  {
+    int FE = 0;
+#pragma unroll
+    for (int f = 0; f < 2 * DIM; ++f) FE += face_size(f, n0, n1, n2);
+    const int nf = t.count * FE;
+    for (int w = threadIdx.x; w < 12 * nf; w += blockDim.x) {
+      const int fi = w % nf, k = w / nf;
+      int le = fi / FE, r = fi - le * FE;
+      int f = 0;
+      while (r >= face_size(f, n0, n1, n2)) {
+        r -= face_size(f, n0, n1, n2);
+        ++f;
+      }
+      int d, ta, tb, side;
+      face_dirs(f, d, ta, tb, side);
+      const int nta = pick(ta, n0, n1, n2), nd = pick(d, n0, n1, n2);
+      int ia = r % nta, ib = r / nta;
+      int i0 = (d == 0) ? 0 : ia;
+      int i1 = (d == 1) ? 0 : (d == 0 ? ia : ib);
+      int i2 = (d == 2) ? 0 : ib;
+      int base = (i2 * n1 + i1) * n0 + i0;
+      int sdd = (d == 0) ? 1 : (d == 1 ? n0 : n0 * n1);
+      int e = A.tile_elems[t.first + le];
+      int64_t p = A.fo[e * 6 + f] + r;
+      const R* s0 = sG + le * nn + base;
+      R acc = cst<R>(0.0f);
+      for (int j = 0; j < nd; ++j) acc = madd(acc, (side ? Tab<R>::lp(nd, j) : Tab<R>::lm(nd, j)), s0[k * T + j * sdd]);
+      SR::put(trg, k * A.fn + p, acc);
+    }
+  }
+  // ---- nodal contravariant fluxes: one (node, direction) per item ----
+  {
+    const int w = threadIdx.x;
+    const bool act = w < DIM * T;
+    const int i = act ? w % T : 0, d = act ? w / T : 0;
+    R qq[5], u[3], Tt, nv[3], gr[12];
+    if (act) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) qq[v] = sq[v * T + i];
+      u[0] = sA[0 * T + i];
+      u[1] = sA[1 * T + i];
+      u[2] = sA[2 * T + i];
+      Tt = sA[3 * T + i];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) nv[c] = sA[(4 + 3 * d + c) * T + i];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) gr[k] = sG[k * T + i];
+    }
+    __syncthreads();  // every item has read its inputs before any overwrites them
+    if (act) {
+      const GasT<R>& G = gas[A.slot[A.tile_elems[t.first + i / nn]]];
+      const R p = Tt * qq[0] * G.igM2;
+      const R mu = mu_of_T(Tt, G);
+      const R un = u[0] * nv[0] + u[1] * nv[1] + u[2] * nv[2];
+      R fv[5];
+      visc_flux(u, mu, gr, nv, G, true, fv);
+      sA[(d * 5 + 0) * T + i] = qq[0] * un;
+      sA[(d * 5 + 1) * T + i] = qq[1] * un + p * nv[0] - G.invRe * fv[1];
+      sA[(d * 5 + 2) * T + i] = qq[2] * un + p * nv[1] - G.invRe * fv[2];
+      sA[(d * 5 + 3) * T + i] = qq[3] * un + p * nv[2] - G.invRe * fv[3];
+      sA[(d * 5 + 4) * T + i] = (qq[4] + p) * un - G.invRe * fv[4];
+    }
+  }
+  __syncthreads();
+  // ---- weak-form divergence: one (node, variable) per item ----
+  for (int w = threadIdx.x; w < 5 * T; w += blockDim.x) {
+    const int i = w % T, v = w / T;
+    const int le = i / nn, node = i - le * nn;
+    const int idx0 = node % n0, idx1 = (node / n0) % n1, idx2 = node / (n0 * n1);
+    R acc = cst<R>(0.0f);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const int id = pick(d, idx0, idx1, idx2), nd = pick(d, n0, n1, n2);
+      const int sd = (d == 0) ? 1 : (d == 1 ? n0 : n0 * n1);
+      const int base = le * nn + node - id * sd;
+      const R* Drow = sD + d * kNP * kNP + id * kNP;
+      for (int a = 0; a < nd; ++a) acc = madd(acc, Drow[a], sA[(d * 5 + v) * T + base + a * sd]);
+    }
+    const int e = A.tile_elems[t.first + le];
+    SR::put(vol, (size_t)5 * A.off[e] + node + v * nn, acc);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // k_surface: surface terms, r = S - A; optional RK3 stage and max|r|
 // ---------------------------------------------------------------------------
 // CFL limit of Sec. 2 at one node: min over directions d with N_d > 0 of
@@ -1513,6 +1705,7 @@ template <typename R, int DIM, bool AFF>
 static int set_attrs() {
   const int big = (int)((3 * kNP * kNP + 32 * kMaxElemNodes) * sizeof(double));
   DG_CUDA_TRY(cudaFuncSetAttribute(k_volume<R, DIM, AFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  DG_CUDA_TRY(cudaFuncSetAttribute(k_volume_split<R, DIM, AFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   DG_CUDA_TRY(cudaFuncSetAttribute(k_isolated<R, DIM, AFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   return DG_OK;
 }
@@ -1542,6 +1735,10 @@ static int configure_smem() {
     DG_CUDA_TRY(cudaFuncSetAttribute(k_volume<tf, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     DG_CUDA_TRY(cudaFuncSetAttribute(k_volume<tf, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     DG_CUDA_TRY(cudaFuncSetAttribute(k_volume<tf, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    DG_CUDA_TRY(cudaFuncSetAttribute(k_volume_split<tf, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    DG_CUDA_TRY(cudaFuncSetAttribute(k_volume_split<tf, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    DG_CUDA_TRY(cudaFuncSetAttribute(k_volume_split<tf, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    DG_CUDA_TRY(cudaFuncSetAttribute(k_volume_split<tf, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   }
   DG_CUDA_TRY(cudaFuncSetAttribute(k_transfer, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)(2 * kTransferMaxSlab * sizeof(double))));
@@ -1764,6 +1961,34 @@ static void for_tile_classes(const Level* L, F launch, int only = -1, int thread
   }
 }
 
+// Whether a level's small-element tiles (class 0) take k_volume_split:
+// DG_VOLUME_SPLIT=0 never, 2 always, 1 (default) when those tiles give the
+// plain kernel fewer than 8 warps per SM.  The results are the same bits
+// either way; the knob selects the kernel only.
+static int volume_split_mode() {
+  static const int mode = [] {
+    const char* e = std::getenv("DG_VOLUME_SPLIT");
+    return e ? std::atoi(e) : 1;
+  }();
+  return mode;
+}
+static int sm_count_cached() {
+  static const int n = [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return 152;
+    return v > 0 ? v : 152;
+  }();
+  return n;
+}
+static bool volume_split(const Level* L) {
+  const int mode = volume_split_mode();
+  if (mode == 0 || L->tile_class_end[0] == 0) return false;
+  if (mode == 2) return true;
+  const int64_t warps = (int64_t)L->tile_class_end[0] * ((L->tile_class_nodes[0] + 31) / 32);
+  return warps < 8 * (int64_t)sm_count_cached();
+}
+
 template <typename R>
 static void launch_volume(const Level* L, const GasT<R>* G, const double* q, cudaStream_t st, int only = -1,
                           int threads_override = 0, const double* base = nullptr) {
@@ -1772,7 +1997,28 @@ static void launch_volume(const Level* L, const GasT<R>* G, const double* q, cud
   const ST<R>* ust = buf<R>(L->d_ust);
   ST<R>* trg = buf<R>(L->d_trg);
   ST<R>* vol = buf<R>(L->d_vol);
+  const bool split = threads_override == 0 && (only < 0 || only == 0) && volume_split(L);
+  if (split) {  // class 0 in the split kernel; the other classes below
+    const int T0 = L->tile_class_nodes[0];
+    const int th = std::min(kVolThreads, std::max(((5 * T0 + 31) / 32) * 32, 32));
+    const size_t sm = (size_t)(3 * kNP * kNP + 32 * T0) * sizeof(double);
+    const int nt = L->tile_class_end[0];
+    if (only == 0) count_launch();  // (otherwise for_tile_classes counts class 0 below)
+    if (L->dim == 2) {
+      if (L->affine)
+        launch_k(k_volume_split<R, 2, true>, nt, th, sm, st, A, 0, G, q, ust, trg, vol);
+      else
+        launch_k(k_volume_split<R, 2, false>, nt, th, sm, st, A, 0, G, q, ust, trg, vol);
+    } else {
+      if (L->affine)
+        launch_k(k_volume_split<R, 3, true>, nt, th, sm, st, A, 0, G, q, ust, trg, vol);
+      else
+        launch_k(k_volume_split<R, 3, false>, nt, th, sm, st, A, 0, G, q, ust, trg, vol);
+    }
+    if (only == 0) return;
+  }
   for_tile_classes(L, [&](int t0, int nt, int th, size_t sm) {
+    if (split && t0 == 0) return;  // class 0 ran in the split kernel
     if (L->dim == 2) {
       if (L->affine)
         launch_k(k_volume<R, 2, true>, nt, th, sm, st, A, t0, G, q, ust, trg, vol);
