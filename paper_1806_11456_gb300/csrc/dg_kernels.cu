@@ -1962,9 +1962,13 @@ static void for_tile_classes(const Level* L, F launch, int only = -1, int thread
 }
 
 // Whether a level's small-element tiles (class 0) take k_volume_split:
-// DG_VOLUME_SPLIT=0 never, 2 always, 1 (default) when those tiles give the
-// plain kernel fewer than 8 warps per SM.  The results are the same bits
-// either way; the knob selects the kernel only.
+// DG_VOLUME_SPLIT=0 never, 2 always, 1 (default) for FP64 tiles of at most
+// 32 nodes that give the plain kernel fewer than 8 warps per SM.  Measured
+// on the flat plate (FP64 volume stage per level, plain / split): N = 1
+// 14.8 / 12.4 us, N = 2 15.9 / 16.2, N = 3 23.2 / 32.7, N = 7 62.7 / 90.9;
+// the tangent arithmetic was never faster split.  Larger tiles make
+// 5 x 128-thread CTAs, one per SM, in two waves.  The results are the same
+// bits either way; the knob selects the kernel only.
 static int volume_split_mode() {
   static const int mode = [] {
     const char* e = std::getenv("DG_VOLUME_SPLIT");
@@ -1981,10 +1985,11 @@ static int sm_count_cached() {
   }();
   return n;
 }
-static bool volume_split(const Level* L) {
+static bool volume_split(const Level* L, bool fp64) {
   const int mode = volume_split_mode();
   if (mode == 0 || L->tile_class_end[0] == 0) return false;
   if (mode == 2) return true;
+  if (!fp64 || L->tile_class_nodes[0] > 32) return false;
   const int64_t warps = (int64_t)L->tile_class_end[0] * ((L->tile_class_nodes[0] + 31) / 32);
   return warps < 8 * (int64_t)sm_count_cached();
 }
@@ -1997,7 +2002,8 @@ static void launch_volume(const Level* L, const GasT<R>* G, const double* q, cud
   const ST<R>* ust = buf<R>(L->d_ust);
   ST<R>* trg = buf<R>(L->d_trg);
   ST<R>* vol = buf<R>(L->d_vol);
-  const bool split = threads_override == 0 && (only < 0 || only == 0) && volume_split(L);
+  const bool split =
+      threads_override == 0 && (only < 0 || only == 0) && volume_split(L, std::is_same<R, double>::value);
   if (split) {  // class 0 in the split kernel; the other classes below
     const int T0 = L->tile_class_nodes[0];
     const int th = std::min(kVolThreads, std::max(((5 * T0 + 31) / 32) * 32, 32));
