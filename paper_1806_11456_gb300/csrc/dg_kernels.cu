@@ -933,6 +933,122 @@ __global__ void __launch_bounds__(kMortarConfThreads, 12)
   }
 }
 
+// k_mortar_conf_flux: the flux pass of k_mortar_conf with each node's work
+// on two warps: 32 mortar nodes per CTA, the first warp forms the Roe flux,
+// the second the BR1 viscous fluxes of both sides; both then combine them
+// in the order of mortar_node_value (Roe, minus the L viscous term, minus
+// the R one), so the bits are the same, and write the L and the R face
+// node.  Each warp's serial FP64 chain is about half of one thread's in
+// k_mortar_conf<2>, and an SM holds twice the warps.
+template <typename R>
+__global__ void __launch_bounds__(64, 6)
+    k_mortar_conf_flux(LevelArgsT<R> A, MortarArgsT<R> MA, const GasT<R>* __restrict__ gas,
+                       const typename Store<R>::T* __restrict__ trq, const typename Store<R>::T* __restrict__ trg,
+                       typename Store<R>::T* __restrict__ out) {
+  pdl_enter();
+  using SR = Store<R>;
+  __shared__ R s_roe[32][5], s_vl[32][5], s_vr[32][5];
+  const int lane = threadIdx.x & 31, part = threadIdx.x >> 5;
+  const int64_t gp = blockIdx.x * (int64_t)32 + lane;
+  const bool act = gp < MA.mnodes;
+  const R half = cst<R>(0.5f);
+  MortarDev M{};
+  int a = 0, b = 0, Ma = 0, ia = 0, ib = 0;
+  R S = cst<R>(0.0f);
+  if (act) {
+    M = MA.mortars[MA.mnode_mortar[gp]];
+    const GasT<R>& G = gas[A.slot[M.eL]];
+    const int loc = (int)(gp - M.node_off);
+    a = loc % M.ma;
+    b = loc / M.ma;
+    int dL, taL, tbL, sL;
+    face_dirs(M.fL, dL, taL, tbL, sL);
+    const int nLa = A.n[M.eL * 3 + taL], nLb = A.n[M.eL * 3 + tbL];
+    const int64_t pL = A.fo[M.eL * 6 + M.fL];
+    R qL[5], qR[5];
+    face_interp<R, 5>(trq + pL, A.fn, nLa, nLb, M.ma, M.mb, a, b, qL);
+    const R nS0 = SR::get(MA.mnS, gp), nS1 = SR::get(MA.mnS, MA.mnodes + gp), nS2 = SR::get(MA.mnS, 2 * MA.mnodes + gp);
+    S = sqrt(nS0 * nS0 + nS1 * nS1 + nS2 * nS2);
+    const R iS = cst<R>(1.0f) / S;
+    const R nu[3] = {nS0 * iS, nS1 * iS, nS2 * iS};
+    int Ra = 0, Rb = 0, Mb = 0;
+    int64_t pR = 0;
+    if (M.eR >= 0) {
+      int dR, taR, tbR, sR;
+      face_dirs(M.fR, dR, taR, tbR, sR);
+      Ra = A.n[M.eR * 3 + taR];
+      Rb = A.n[M.eR * 3 + tbR];
+      const bool sw = M.orient & 1;
+      Ma = sw ? M.mb : M.ma;
+      Mb = sw ? M.ma : M.mb;
+      ia = sw ? b : a;
+      ib = sw ? a : b;
+      if (M.orient & 2) ia = Ma - 1 - ia;
+      if (M.orient & 4) ib = Mb - 1 - ib;
+      pR = A.fo[M.eR * 6 + M.fR];
+      face_interp<R, 5>(trq + pR, A.fn, Ra, Rb, Ma, Mb, ia, ib, qR);
+    } else {
+      ghost(M.bc, qL, nu, G, qR);
+    }
+    R irL, uL[3], pLs, TL, irR, uR[3], pRs, TR;
+    to_prim(qL, G, irL, uL, pLs, TL);
+    to_prim(qR, G, irR, uR, pRs, TR);
+    if (part == 0) {
+      R f[5];
+      roe(qL, qR, irL, uL, pLs, irR, uR, pRs, nu, G, f);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) s_roe[lane][v] = f[v];
+    } else if (!(M.eR < 0 && M.bc == DG_BC_SLIP)) {
+      R g[12], fv[5];
+      face_interp<R, 12>(trg + pL, A.fn, nLa, nLb, M.ma, M.mb, a, b, g);
+      const R mu = mu_of_T(TL, G);
+      if (M.eR < 0 && M.bc == DG_BC_WALL) {
+        const R z[3] = {cst<R>(0.0f), cst<R>(0.0f), cst<R>(0.0f)};
+        visc_flux(z, mu, g, nu, G, false, fv);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) s_vl[lane][v] = fv[v];
+      } else {
+        visc_flux(uL, mu, g, nu, G, true, fv);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) s_vl[lane][v] = fv[v];
+        if (M.eR >= 0) face_interp<R, 12>(trg + pR, A.fn, Ra, Rb, Ma, Mb, ia, ib, g);  // else: interior gradient
+        visc_flux(uR, mu_of_T(TR, G), g, nu, G, true, fv);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) s_vr[lane][v] = fv[v];
+      }
+    }
+  }
+  __syncthreads();
+  if (!act) return;
+  const GasT<R>& G = gas[A.slot[M.eL]];
+  R o[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) o[v] = s_roe[lane][v];
+  if (!(M.eR < 0 && M.bc == DG_BC_SLIP)) {
+    if (M.eR < 0 && M.bc == DG_BC_WALL) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) o[v] -= G.invRe * s_vl[lane][v];
+    } else {
+      const R hre = half * G.invRe;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) o[v] -= hre * s_vl[lane][v];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) o[v] -= hre * s_vr[lane][v];
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 5; ++v) o[v] = S * o[v];
+  if (part == 0) {  // L face node = mortar node (L frame)
+    const int64_t dL = A.fo[M.eL * 6 + M.fL] + b * M.ma + a;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) SR::put(out, v * A.fn + dL, o[v]);
+  } else if (M.eR >= 0) {  // R face node through the orientation, negated
+    const int64_t dR = A.fo[M.eR * 6 + M.fR] + ib * Ma + ia;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) SR::put(out, v * A.fn + dR, -o[v]);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // element kernels: staging, BR1 gradient, fluxes, divergence
 // ---------------------------------------------------------------------------
@@ -1976,6 +2092,16 @@ static int volume_split_mode() {
   }();
   return mode;
 }
+// DG_MORTAR_FLUX_SPLIT=0 runs the flux pass of conforming levels in
+// k_mortar_conf<2> (one warp per 32 nodes); 1 (default) in
+// k_mortar_conf_flux (two).  Same bits; the knob selects the kernel only.
+static int mortar_flux_split_mode() {
+  static const int mode = [] {
+    const char* e = std::getenv("DG_MORTAR_FLUX_SPLIT");
+    return e ? std::atoi(e) : 1;
+  }();
+  return mode;
+}
 static int sm_count_cached() {
   static const int n = [] {
     int dev = 0, v = 0;
@@ -2078,6 +2204,9 @@ static void launch_mortar(int pass, const Level* L, const GasT<R>* G, cudaStream
     if (pass == 1)
       launch_k(k_mortar_conf<R, 1>, grid, kMortarConfThreads, 0, st, A, MA, G, buf<R>(L->d_trq), nullptr,
                                                                buf<R>(L->d_ust));
+    else if (mortar_flux_split_mode() != 0)  // two warps per 32 mortar nodes (same bits)
+      launch_k(k_mortar_conf_flux<R>, grid, 64, 0, st, A, MA, G, buf<R>(L->d_trq), buf<R>(L->d_trg),
+               buf<R>(L->d_fst));
     else
       launch_k(k_mortar_conf<R, 2>, grid, kMortarConfThreads, 0, st, A, MA, G, buf<R>(L->d_trq), buf<R>(L->d_trg),
                                                                buf<R>(L->d_fst));
