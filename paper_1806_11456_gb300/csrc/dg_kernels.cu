@@ -2093,14 +2093,27 @@ static int volume_split_mode() {
   return mode;
 }
 // DG_MORTAR_FLUX_SPLIT=0 runs the flux pass of conforming levels in
-// k_mortar_conf<2> (one warp per 32 nodes); 1 (default) in
-// k_mortar_conf_flux (two).  Same bits; the knob selects the kernel only.
+// k_mortar_conf<2> (one warp per 32 nodes), 2 always in k_mortar_conf_flux
+// (two), 1 (default) in k_mortar_conf_flux for the FP32-pipe arithmetics
+// and, in FP64, on levels with fewer than 3 warps of mortar nodes per SM.
+// Measured on the flat plate (FP64 flux pass, one / two warps): N = 1 14.4 /
+// 10.4 us, N = 3 14.4 / 13.5, N = 4 14.6 / 15.9, N = 7 18.2 / 20.4 (above
+// ~3 warps per SM the duplicated trace and primitive work outweighs the
+// latency it hides); the tangent form gains on every level (N = 7: 5.4 /
+// 5.2 us).  Same bits; the knob selects the kernel only.
 static int mortar_flux_split_mode() {
   static const int mode = [] {
     const char* e = std::getenv("DG_MORTAR_FLUX_SPLIT");
     return e ? std::atoi(e) : 1;
   }();
   return mode;
+}
+static int sm_count_cached();
+static bool mortar_flux_split(const Level* L, bool fp64) {
+  const int mode = mortar_flux_split_mode();
+  if (mode == 0) return false;
+  if (mode == 2 || !fp64) return true;
+  return (L->mortar_nodes + 31) / 32 < 3 * (int64_t)sm_count_cached();
 }
 static int sm_count_cached() {
   static const int n = [] {
@@ -2204,7 +2217,7 @@ static void launch_mortar(int pass, const Level* L, const GasT<R>* G, cudaStream
     if (pass == 1)
       launch_k(k_mortar_conf<R, 1>, grid, kMortarConfThreads, 0, st, A, MA, G, buf<R>(L->d_trq), nullptr,
                                                                buf<R>(L->d_ust));
-    else if (mortar_flux_split_mode() != 0)  // two warps per 32 mortar nodes (same bits)
+    else if (mortar_flux_split(L, std::is_same<R, double>::value))  // two warps per 32 nodes (same bits)
       launch_k(k_mortar_conf_flux<R>, grid, 64, 0, st, A, MA, G, buf<R>(L->d_trq), buf<R>(L->d_trg),
                buf<R>(L->d_fst));
     else

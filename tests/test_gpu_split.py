@@ -1,8 +1,8 @@
 """Kernel variants that split a node's work over more threads give the same
 bits as the plain kernels: the volume stage's k_volume_split (knob
 DG_VOLUME_SPLIT, 2 = on every level, 0 = off) and the two-warp flux pass of
-conforming levels, k_mortar_conf_flux (DG_MORTAR_FLUX_SPLIT, 1 = on, 0 =
-off).  Child processes evaluate the same residuals and V-cycles with each
+conforming levels, k_mortar_conf_flux (DG_MORTAR_FLUX_SPLIT, 2 = on every
+level, 0 = off).  Child processes evaluate the same residuals and V-cycles with each
 setting: plate with every boundary type, 3D mortars, curved shell (random
 orders), and uniform-order plate, rotated box (all face orientations) and
 curved shell (conforming mortars), in FP64, double-float and the tangent
@@ -64,7 +64,7 @@ def _run(tmp_path, **knobs):
     return dict(np.load(path))
 
 
-@pytest.mark.parametrize("knob,off,on", [("DG_VOLUME_SPLIT", 0, 2), ("DG_MORTAR_FLUX_SPLIT", 0, 1)])
+@pytest.mark.parametrize("knob,off,on", [("DG_VOLUME_SPLIT", 0, 2), ("DG_MORTAR_FLUX_SPLIT", 0, 2)])
 def test_split_kernels_give_the_same_bits(tmp_path, knob, off, on):
     import torch
     if not torch.cuda.is_available():
