@@ -101,15 +101,27 @@ def tau_dof_evals(orders, dim):
 
 
 def volume_flops_per_node(dim, n, affine):
-    """Algorithmic FP64 flops per node of the volume kernel (FMA = 2): BR1
-    gradient contraction per direction 27 n (general metrics: 3 metric
-    products + 12 FMA per point) or 8 n + 24 (affine element: 4 FMA per point,
-    then the 12-term metric product once); lifting of U* per direction 54
-    (general: two faces, 3 metric products + 12 FMA each) or 16 (affine: the
-    two faces' U* join the contraction, 4 FMA each); gradient face traces 48
-    per direction; nodal viscous + advective contravariant fluxes 68 per
-    direction; divergence 10 n per direction; primitives, viscosity and
-    scalings 34."""
+    """Algorithmic FP64 flops per node of the volume kernel (FMA = 2, a
+    division or square root 1), n nodes per direction.
+
+    3D, per direction: BR1 gradient contraction 27 n (general metrics: 3
+    metric products + 12 FMA per point) or 8 n + 24 (affine: 4 FMA per
+    point, then the 12-term metric product once); lifting of U* 54 (general:
+    two faces, 3 metric products + 12 FMA each) or 16 (affine: the two faces'
+    U* join the contraction); gradient face traces 48 (12 values); nodal
+    viscous + advective contravariant fluxes 68; divergence 10 n; and per
+    node primitives, p, viscosity and the 1/J scalings 34.
+
+    2D (one-element-thick extrusion: z-derivatives and the z-components of
+    the in-plane metrics are zero and left out), per direction: contraction
+    8 n + 16 (affine: 8-term metric product) or 18 n (general); lifting 16
+    or 36; gradient face traces 32 (8 values); nodal fluxes 53 (viscous flux
+    32, normal velocity 3, five flux components 18); divergence 10 n; per
+    node primitives 14, p and viscosity 7, 1/J scaling of 8 values 8."""
+    if dim == 2:
+        grad = (8 * n + 16) if affine else 18 * n
+        lift = 16 if affine else 36
+        return 29 + 2 * (grad + lift + 32 + 53 + 10 * n)
     grad = (8 * n + 24) if affine else 27 * n
     lift = 16 if affine else 54
     return 34 + dim * (grad + 10 * n + lift + 48 + 68)

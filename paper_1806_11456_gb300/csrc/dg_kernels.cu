@@ -340,9 +340,31 @@ DEV R mu_of_T(R T, const GasT<R>& G) {
   return T * sqrt(T) * G.Su1 / (T + G.Su);
 }
 
-// viscous flux (no 1/Re) on vector nv; grad[v*3+c] = d(u,v,w,T)_v / dx_c
-template <typename R>
+// viscous flux (no 1/Re) on vector nv; grad[v*3+c] = d(u,v,w,T)_v / dx_c.
+// DIM = 2: a field of the one-element-thick extrusion, whose z-derivatives
+// (grad[v*3+2]) and z-components of the face and metric vectors (nv[2]) are
+// exactly zero: their terms are left out (the same values; the velocity w
+// and its in-plane derivatives stay).
+template <typename R, int DIM = 3>
 DEV void visc_flux(const R* u, R mu, const R* grad, const R* nv, const GasT<R>& G, bool heat, R* f) {
+  if (DIM == 2) {
+    const R div = grad[0] + grad[4];
+    const R lam = -(G.two3 * mu * div);
+    const R mu2 = cst<R>(2.0f) * mu;
+    const R t00 = mu2 * grad[0] + lam, t11 = mu2 * grad[4] + lam;
+    const R t01 = mu * (grad[1] + grad[3]), t02 = mu * grad[6], t12 = mu * grad[7];
+    const R tn0 = t00 * nv[0] + t01 * nv[1];
+    const R tn1 = t01 * nv[0] + t11 * nv[1];
+    const R tn2 = t02 * nv[0] + t12 * nv[1];
+    f[0] = cst<R>(0.0f);
+    f[1] = tn0;
+    f[2] = tn1;
+    f[3] = tn2;
+    R e = u[0] * tn0 + u[1] * tn1 + u[2] * tn2;
+    if (heat) e += G.hc * mu * (grad[9] * nv[0] + grad[10] * nv[1]);
+    f[4] = e;
+    return;
+  }
   const R div = grad[0] + grad[4] + grad[8];
   const R lam = -(G.two3 * mu * div);
   const R mu2 = cst<R>(2.0f) * mu;
@@ -358,6 +380,15 @@ DEV void visc_flux(const R* u, R mu, const R* grad, const R* nv, const GasT<R>& 
   R e = u[0] * tn0 + u[1] * tn1 + u[2] * tn2;
   if (heat) e += G.hc * mu * (grad[9] * nv[0] + grad[10] * nv[1] + grad[11] * nv[2]);
   f[4] = e;
+}
+
+// visc_flux for a dimension known at run time (the mortar kernels serve both)
+template <typename R>
+DEV void visc_flux_dim(int dim, const R* u, R mu, const R* grad, const R* nv, const GasT<R>& G, bool heat, R* f) {
+  if (dim == 2)
+    visc_flux<R, 2>(u, mu, grad, nv, G, heat, f);
+  else
+    visc_flux<R, 3>(u, mu, grad, nv, G, heat, f);
 }
 
 // Roe flux for unit normal n (textbook averages, five waves, no entropy fix)
@@ -788,16 +819,16 @@ DEV void mortar_node_value(const LevelArgsT<R>& A, const MortarArgsT<R>& MA, con
     const R mu = mu_of_T(TL, G);
     if (M.eR < 0 && M.bc == DG_BC_WALL) {
       const R z[3] = {cst<R>(0.0f), cst<R>(0.0f), cst<R>(0.0f)};
-      visc_flux(z, mu, g, nu, G, false, fv);
+      visc_flux_dim(A.dim, z, mu, g, nu, G, false, fv);
 #pragma unroll
       for (int v = 0; v < 5; ++v) f[v] -= G.invRe * fv[v];
     } else {
       const R hre = half * G.invRe;
-      visc_flux(uL, mu, g, nu, G, true, fv);
+      visc_flux_dim(A.dim, uL, mu, g, nu, G, true, fv);
 #pragma unroll
       for (int v = 0; v < 5; ++v) f[v] -= hre * fv[v];
       if (M.eR >= 0) face_interp<R, 12>(trg + pR, A.fn, Ra, Rb, Ma, Mb, ia, ib, g);  // else: interior gradient
-      visc_flux(uR, mu_of_T(TR, G), g, nu, G, true, fv);
+      visc_flux_dim(A.dim, uR, mu_of_T(TR, G), g, nu, G, true, fv);
 #pragma unroll
       for (int v = 0; v < 5; ++v) f[v] -= hre * fv[v];
     }
@@ -1004,15 +1035,15 @@ __global__ void __launch_bounds__(64, 6)
       const R mu = mu_of_T(TL, G);
       if (M.eR < 0 && M.bc == DG_BC_WALL) {
         const R z[3] = {cst<R>(0.0f), cst<R>(0.0f), cst<R>(0.0f)};
-        visc_flux(z, mu, g, nu, G, false, fv);
+        visc_flux_dim(A.dim, z, mu, g, nu, G, false, fv);
 #pragma unroll
         for (int v = 0; v < 5; ++v) s_vl[lane][v] = fv[v];
       } else {
-        visc_flux(uL, mu, g, nu, G, true, fv);
+        visc_flux_dim(A.dim, uL, mu, g, nu, G, true, fv);
 #pragma unroll
         for (int v = 0; v < 5; ++v) s_vl[lane][v] = fv[v];
         if (M.eR >= 0) face_interp<R, 12>(trg + pR, A.fn, Ra, Rb, Ma, Mb, ia, ib, g);  // else: interior gradient
-        visc_flux(uR, mu_of_T(TR, G), g, nu, G, true, fv);
+        visc_flux_dim(A.dim, uR, mu_of_T(TR, G), g, nu, G, true, fv);
 #pragma unroll
         for (int v = 0; v < 5; ++v) s_vr[lane][v] = fv[v];
       }
@@ -1066,7 +1097,7 @@ DEV void load_dtables(R* sD, const typename Store<R>::T* src, int n0, int n1, in
 
 // Stage the tile: conserved state (sq), primitives u,v,w,T (sA[0..3]) and the
 // nine metric components (sA[4..12]).
-template <typename R>
+template <typename R, int DIM>
 DEV void stage_tile(const LevelArgsT<R>& A, const ElemTile& t, int nn, int T, const GasT<R>* __restrict__ gas,
                     const double* __restrict__ q, R* sq, R* sA) {
   for (int i = threadIdx.x; i < T; i += blockDim.x) {
@@ -1086,8 +1117,10 @@ DEV void stage_tile(const LevelArgsT<R>& A, const ElemTile& t, int nn, int T, co
     sA[1 * T + i] = u[1];
     sA[2 * T + i] = u[2];
     sA[3 * T + i] = Tt;
+    // a 2D field reads only the in-plane components of Ja^1 and Ja^2
 #pragma unroll
-    for (int c = 0; c < 9; ++c) sA[(4 + c) * T + i] = Store<R>::get(A.geo, c * A.nodes + gn);
+    for (int c = 0; c < 9; ++c)
+      if (DIM == 3 || c == 0 || c == 1 || c == 3 || c == 4) sA[(4 + c) * T + i] = Store<R>::get(A.geo, c * A.nodes + gn);
   }
 }
 
@@ -1135,12 +1168,16 @@ DEV void gradient_volume(const R* sD, const R* sA, int T, int nn, int i, int n0,
           cu[v] = madd(cu[v], wp, Store<R>::get(ust, v * fn + pp));
         }
       }
-      const R j0 = sA[(4 + d * 3 + 0) * T + i], j1 = sA[(4 + d * 3 + 1) * T + i], j2 = sA[(4 + d * 3 + 2) * T + i];
+      const R j0 = sA[(4 + d * 3 + 0) * T + i], j1 = sA[(4 + d * 3 + 1) * T + i];
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         g[v * 3 + 0] = madd(g[v * 3 + 0], j0, cu[v]);
         g[v * 3 + 1] = madd(g[v * 3 + 1], j1, cu[v]);
-        g[v * 3 + 2] = madd(g[v * 3 + 2], j2, cu[v]);
+      }
+      if (DIM == 3) {  // (2D: the metric's z-column is zero, so is every z-derivative)
+        const R j2 = sA[(4 + d * 3 + 2) * T + i];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) g[v * 3 + 2] = madd(g[v * 3 + 2], j2, cu[v]);
       }
     } else {
       for (int a = 0; a < nd; ++a) {
@@ -1148,13 +1185,13 @@ DEV void gradient_volume(const R* sD, const R* sA, int T, int nn, int i, int n0,
         const R c = Drow[a];
         const R j0 = c * sA[(4 + d * 3 + 0) * T + la];
         const R j1 = c * sA[(4 + d * 3 + 1) * T + la];
-        const R j2 = c * sA[(4 + d * 3 + 2) * T + la];
+        const R j2 = (DIM == 3) ? c * sA[(4 + d * 3 + 2) * T + la] : cst<R>(0.0f);
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           const R uv = sA[v * T + la];
           g[v * 3 + 0] = madd(g[v * 3 + 0], j0, uv);
           g[v * 3 + 1] = madd(g[v * 3 + 1], j1, uv);
-          g[v * 3 + 2] = madd(g[v * 3 + 2], j2, uv);
+          if (DIM == 3) g[v * 3 + 2] = madd(g[v * 3 + 2], j2, uv);
         }
       }
     }
@@ -1173,7 +1210,7 @@ DEV void nodal_fluxes(const R* sq, R* sA, const R* sG, int T, int i, const GasT<
   u[2] = sA[2 * T + i];
   const R Tt = sA[3 * T + i];
 #pragma unroll
-  for (int c = 0; c < 3 * DIM; ++c) Ja[c] = sA[(4 + c) * T + i];
+  for (int c = 0; c < 3 * DIM; ++c) Ja[c] = (DIM == 3 || c % 3 != 2) ? sA[(4 + c) * T + i] : cst<R>(0.0f);
 #pragma unroll
   for (int k = 0; k < 12; ++k) gr[k] = sG[k * T + i];
   const R p = Tt * qq[0] * G.igM2;
@@ -1182,14 +1219,23 @@ DEV void nodal_fluxes(const R* sq, R* sA, const R* sG, int T, int i, const GasT<
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
     const R* nv = Ja + 3 * d;
-    const R un = u[0] * nv[0] + u[1] * nv[1] + u[2] * nv[2];
     R fv[5];
-    visc_flux(u, mu, gr, nv, G, true, fv);
-    F[d * 5 + 0] = qq[0] * un;
-    F[d * 5 + 1] = qq[1] * un + p * nv[0] - G.invRe * fv[1];
-    F[d * 5 + 2] = qq[2] * un + p * nv[1] - G.invRe * fv[2];
-    F[d * 5 + 3] = qq[3] * un + p * nv[2] - G.invRe * fv[3];
-    F[d * 5 + 4] = (qq[4] + p) * un - G.invRe * fv[4];
+    visc_flux<R, DIM>(u, mu, gr, nv, G, true, fv);
+    if (DIM == 2) {  // nv[2] = 0
+      const R un = u[0] * nv[0] + u[1] * nv[1];
+      F[d * 5 + 0] = qq[0] * un;
+      F[d * 5 + 1] = qq[1] * un + p * nv[0] - G.invRe * fv[1];
+      F[d * 5 + 2] = qq[2] * un + p * nv[1] - G.invRe * fv[2];
+      F[d * 5 + 3] = qq[3] * un - G.invRe * fv[3];
+      F[d * 5 + 4] = (qq[4] + p) * un - G.invRe * fv[4];
+    } else {
+      const R un = u[0] * nv[0] + u[1] * nv[1] + u[2] * nv[2];
+      F[d * 5 + 0] = qq[0] * un;
+      F[d * 5 + 1] = qq[1] * un + p * nv[0] - G.invRe * fv[1];
+      F[d * 5 + 2] = qq[2] * un + p * nv[1] - G.invRe * fv[2];
+      F[d * 5 + 3] = qq[3] * un + p * nv[2] - G.invRe * fv[3];
+      F[d * 5 + 4] = (qq[4] + p) * un - G.invRe * fv[4];
+    }
   }
 #pragma unroll
   for (int k = 0; k < 5 * DIM; ++k) sA[k * T + i] = F[k];
@@ -1238,7 +1284,7 @@ __global__ void __launch_bounds__(kVolThreads) __maxnreg__(DIM == 2 ? 96 : 104) 
   R* sA = sq + 5 * T;                          // 15 * T: U(4) + Ja(9) | Ftilde(15)
   R* sG = sA + 15 * T;                         // 12 * T
   load_dtables<R>(sD, Tab<R>::Dhat(), n0, n1, n2, DIM);
-  stage_tile<R>(A, t, nn, T, gas, q, sq, sA);
+  stage_tile<R, DIM>(A, t, nn, T, gas, q, sq, sA);
   __syncthreads();
   // ---- gradient: volume part + lifting of U*, times 1/J ----
   for (int i = threadIdx.x; i < T; i += blockDim.x) {
@@ -1259,19 +1305,20 @@ __global__ void __launch_bounds__(kVolThreads) __maxnreg__(DIM == 2 ? 96 : 104) 
         const R lw = side ? Tab<R>::lpw(nd, id) : Tab<R>::lmw(nd, id);
         const int64_t p =
             A.fo[e * 6 + f] + pick(tb, idx0, idx1, idx2) * pick(ta, n0, n1, n2) + pick(ta, idx0, idx1, idx2);
-        const R m0 = lw * SR::get(A.fnS, p), m1 = lw * SR::get(A.fnS, A.fn + p), m2 = lw * SR::get(A.fnS, 2 * A.fn + p);
+        const R m0 = lw * SR::get(A.fnS, p), m1 = lw * SR::get(A.fnS, A.fn + p);
+        const R m2 = (DIM == 3) ? lw * SR::get(A.fnS, 2 * A.fn + p) : cst<R>(0.0f);
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           const R us = SR::get(ust, v * A.fn + p);
           g[v * 3 + 0] = madd(g[v * 3 + 0], m0, us);
           g[v * 3 + 1] = madd(g[v * 3 + 1], m1, us);
-          g[v * 3 + 2] = madd(g[v * 3 + 2], m2, us);
+          if (DIM == 3) g[v * 3 + 2] = madd(g[v * 3 + 2], m2, us);
         }
       }
     }
     const R iJ = SR::get(A.geo, 9 * A.nodes + A.off[e] + node);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) sG[k * T + i] = g[k] * iJ;
+    for (int k = 0; k < 12; ++k) sG[k * T + i] = (DIM == 2 && k % 3 == 2) ? cst<R>(0.0f) : g[k] * iJ;
   }
   __syncthreads();
   // ---- gradient face traces ----
@@ -1301,7 +1348,8 @@ __global__ void __launch_bounds__(kVolThreads) __maxnreg__(DIM == 2 ? 96 : 104) 
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
         R acc = cst<R>(0.0f);
-        for (int j = 0; j < nd; ++j) acc = madd(acc, (side ? Tab<R>::lp(nd, j) : Tab<R>::lm(nd, j)), s0[k * T + j * sdd]);
+        if (DIM == 3 || k % 3 != 2)  // (2D: the z-derivatives are zero)
+          for (int j = 0; j < nd; ++j) acc = madd(acc, (side ? Tab<R>::lp(nd, j) : Tab<R>::lm(nd, j)), s0[k * T + j * sdd]);
         SR::put(trg, k * A.fn + p, acc);
       }
     }
@@ -1362,21 +1410,21 @@ DEV void gradient_var(const LevelArgsT<R>& A, const R* sD, const R* sA, int T, i
       const R wm = -Tab<R>::lmw(nd, id), wp = Tab<R>::lpw(nd, id);
       cu = madd(cu, wm, SR::get(ust, v * A.fn + pm));
       cu = madd(cu, wp, SR::get(ust, v * A.fn + pp));
-      const R j0 = sA[(4 + d * 3 + 0) * T + i], j1 = sA[(4 + d * 3 + 1) * T + i], j2 = sA[(4 + d * 3 + 2) * T + i];
+      const R j0 = sA[(4 + d * 3 + 0) * T + i], j1 = sA[(4 + d * 3 + 1) * T + i];
       g[0] = madd(g[0], j0, cu);
       g[1] = madd(g[1], j1, cu);
-      g[2] = madd(g[2], j2, cu);
+      if (DIM == 3) g[2] = madd(g[2], sA[(4 + d * 3 + 2) * T + i], cu);
     } else {
       for (int a = 0; a < nd; ++a) {
         const int la = base + a * sd;
         const R c = Drow[a];
         const R j0 = c * sA[(4 + d * 3 + 0) * T + la];
         const R j1 = c * sA[(4 + d * 3 + 1) * T + la];
-        const R j2 = c * sA[(4 + d * 3 + 2) * T + la];
+        const R j2 = (DIM == 3) ? c * sA[(4 + d * 3 + 2) * T + la] : cst<R>(0.0f);
         const R uv = sA[v * T + la];
         g[0] = madd(g[0], j0, uv);
         g[1] = madd(g[1], j1, uv);
-        g[2] = madd(g[2], j2, uv);
+        if (DIM == 3) g[2] = madd(g[2], j2, uv);
       }
     }
   }
@@ -1388,11 +1436,11 @@ DEV void gradient_var(const LevelArgsT<R>& A, const R* sD, const R* sA, int T, i
       const int nd = pick(d, n0, n1, n2), id = pick(d, idx0, idx1, idx2);
       const R lw = side ? Tab<R>::lpw(nd, id) : Tab<R>::lmw(nd, id);
       const int64_t p = fo_e[f] + pick(tb, idx0, idx1, idx2) * pick(ta, n0, n1, n2) + pick(ta, idx0, idx1, idx2);
-      const R m0 = lw * SR::get(A.fnS, p), m1 = lw * SR::get(A.fnS, A.fn + p), m2 = lw * SR::get(A.fnS, 2 * A.fn + p);
+      const R m0 = lw * SR::get(A.fnS, p), m1 = lw * SR::get(A.fnS, A.fn + p);
       const R us = SR::get(ust, v * A.fn + p);
       g[0] = madd(g[0], m0, us);
       g[1] = madd(g[1], m1, us);
-      g[2] = madd(g[2], m2, us);
+      if (DIM == 3) g[2] = madd(g[2], lw * SR::get(A.fnS, 2 * A.fn + p), us);
     }
   }
 }
@@ -1416,7 +1464,7 @@ __global__ void __launch_bounds__(kVolThreads) __maxnreg__(DIM == 2 ? 96 : 104)
   R* sA = sq + 5 * T;
   R* sG = sA + 15 * T;
   load_dtables<R>(sD, Tab<R>::Dhat(), n0, n1, n2, DIM);
-  stage_tile<R>(A, t, nn, T, gas, q, sq, sA);
+  stage_tile<R, DIM>(A, t, nn, T, gas, q, sq, sA);
   __syncthreads();
   // ---- gradient: one (node, variable) per item ----
   for (int w = threadIdx.x; w < 4 * T; w += blockDim.x) {
@@ -1427,7 +1475,7 @@ __global__ void __launch_bounds__(kVolThreads) __maxnreg__(DIM == 2 ? 96 : 104)
     gradient_var<R, DIM, AFFINE>(A, sD, sA, T, nn, i, n0, n1, n2, v, e, ust, g);
     const R iJ = SR::get(A.geo, 9 * A.nodes + A.off[e] + node);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) sG[(v * 3 + c) * T + i] = g[c] * iJ;
+    for (int c = 0; c < 3; ++c) sG[(v * 3 + c) * T + i] = (DIM == 2 && c == 2) ? cst<R>(0.0f) : g[c] * iJ;
   }
   __syncthreads();
   // ---- gradient face traces: one (face node, component) per item ----
@@ -1457,7 +1505,8 @@ __global__ void __launch_bounds__(kVolThreads) __maxnreg__(DIM == 2 ? 96 : 104)
       int64_t p = A.fo[e * 6 + f] + r;
       const R* s0 = sG + le * nn + base;
       R acc = cst<R>(0.0f);
-      for (int j = 0; j < nd; ++j) acc = madd(acc, (side ? Tab<R>::lp(nd, j) : Tab<R>::lm(nd, j)), s0[k * T + j * sdd]);
+      if (DIM == 3 || k % 3 != 2)  // (2D: the z-derivatives are zero)
+        for (int j = 0; j < nd; ++j) acc = madd(acc, (side ? Tab<R>::lp(nd, j) : Tab<R>::lm(nd, j)), s0[k * T + j * sdd]);
       SR::put(trg, k * A.fn + p, acc);
     }
   }
@@ -1475,7 +1524,7 @@ __global__ void __launch_bounds__(kVolThreads) __maxnreg__(DIM == 2 ? 96 : 104)
       u[2] = sA[2 * T + i];
       Tt = sA[3 * T + i];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) nv[c] = sA[(4 + 3 * d + c) * T + i];
+      for (int c = 0; c < 3; ++c) nv[c] = (DIM == 3 || c != 2) ? sA[(4 + 3 * d + c) * T + i] : cst<R>(0.0f);
 #pragma unroll
       for (int k = 0; k < 12; ++k) gr[k] = sG[k * T + i];
     }
@@ -1484,14 +1533,23 @@ __global__ void __launch_bounds__(kVolThreads) __maxnreg__(DIM == 2 ? 96 : 104)
       const GasT<R>& G = gas[A.slot[A.tile_elems[t.first + i / nn]]];
       const R p = Tt * qq[0] * G.igM2;
       const R mu = mu_of_T(Tt, G);
-      const R un = u[0] * nv[0] + u[1] * nv[1] + u[2] * nv[2];
       R fv[5];
-      visc_flux(u, mu, gr, nv, G, true, fv);
-      sA[(d * 5 + 0) * T + i] = qq[0] * un;
-      sA[(d * 5 + 1) * T + i] = qq[1] * un + p * nv[0] - G.invRe * fv[1];
-      sA[(d * 5 + 2) * T + i] = qq[2] * un + p * nv[1] - G.invRe * fv[2];
-      sA[(d * 5 + 3) * T + i] = qq[3] * un + p * nv[2] - G.invRe * fv[3];
-      sA[(d * 5 + 4) * T + i] = (qq[4] + p) * un - G.invRe * fv[4];
+      visc_flux<R, DIM>(u, mu, gr, nv, G, true, fv);
+      if (DIM == 2) {  // as nodal_fluxes: nv[2] = 0
+        const R un = u[0] * nv[0] + u[1] * nv[1];
+        sA[(d * 5 + 0) * T + i] = qq[0] * un;
+        sA[(d * 5 + 1) * T + i] = qq[1] * un + p * nv[0] - G.invRe * fv[1];
+        sA[(d * 5 + 2) * T + i] = qq[2] * un + p * nv[1] - G.invRe * fv[2];
+        sA[(d * 5 + 3) * T + i] = qq[3] * un - G.invRe * fv[3];
+        sA[(d * 5 + 4) * T + i] = (qq[4] + p) * un - G.invRe * fv[4];
+      } else {
+        const R un = u[0] * nv[0] + u[1] * nv[1] + u[2] * nv[2];
+        sA[(d * 5 + 0) * T + i] = qq[0] * un;
+        sA[(d * 5 + 1) * T + i] = qq[1] * un + p * nv[0] - G.invRe * fv[1];
+        sA[(d * 5 + 2) * T + i] = qq[2] * un + p * nv[1] - G.invRe * fv[2];
+        sA[(d * 5 + 3) * T + i] = qq[3] * un + p * nv[2] - G.invRe * fv[3];
+        sA[(d * 5 + 4) * T + i] = (qq[4] + p) * un - G.invRe * fv[4];
+      }
     }
   }
   __syncthreads();
@@ -1661,7 +1719,7 @@ __global__ void __launch_bounds__(kVolThreads) __maxnreg__(DIM == 2 ? 96 : 128) 
   R* sA = sq + 5 * T;
   R* sG = sA + 15 * T;
   load_dtables<R>(sD, Tab<R>::Dcol(), n0, n1, n2, DIM);
-  stage_tile<R>(A, t, nn, T, gas, q, sq, sA);
+  stage_tile<R, DIM>(A, t, nn, T, gas, q, sq, sA);
   __syncthreads();
   for (int i = threadIdx.x; i < T; i += blockDim.x) {
     R g[12];
@@ -1670,7 +1728,7 @@ __global__ void __launch_bounds__(kVolThreads) __maxnreg__(DIM == 2 ? 96 : 128) 
     const int e = A.tile_elems[t.first + le];
     const R iJ = SR::get(A.geo, 9 * A.nodes + A.off[e] + node);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) sG[k * T + i] = g[k] * iJ;
+    for (int k = 0; k < 12; ++k) sG[k * T + i] = (DIM == 2 && k % 3 == 2) ? cst<R>(0.0f) : g[k] * iJ;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < T; i += blockDim.x)

@@ -32,7 +32,7 @@ def test_reference_arm_prints_one_contract_line():
 
 def test_volume_flop_count_terms():
     import bench
-    # flat plate: 2D, n = 8, affine: 34 + 2 (8n + 24 + 10n + 16 + 48 + 68)
-    assert bench.volume_flops_per_node(2, 8, True) == 34 + 2 * (64 + 24 + 80 + 16 + 48 + 68) == 634
+    # flat plate: 2D, n = 8, affine: 29 + 2 (8n + 16 + 16 + 32 + 53 + 10n)
+    assert bench.volume_flops_per_node(2, 8, True) == 29 + 2 * (64 + 16 + 16 + 32 + 53 + 80) == 551
     # curved elements: gradient 27 n and lifting 54 per direction
     assert bench.volume_flops_per_node(3, 4, False) == 34 + 3 * (108 + 40 + 54 + 48 + 68)
