@@ -315,14 +315,23 @@ def tangent_residual(mesh, orders, prm, q, dq, b=None):
     return (0.0 if b is None else b) - Jdq
 
 
-def mixed_vcycle(mesh, orders, prm, q, s, beta1, beta2, beta_c, direction=None, coarsest=1, delta_n=1):
+def mixed_vcycle(mesh, orders, prm, q, s, beta1, beta2, beta_c, direction=None, coarsest=1, delta_n=1,
+                 control=0, eta=1.1):
     """One defect-correction cycle: r = S - A(q) at the finest level, one
     V-cycle of Algorithm 1's shape (levels, sweeps, RK3 smoother, L2
     restriction and prolongation) on the linearised problem J d = r in which
     level l is linearised at the restriction of q, its right-hand side is the
     restriction of the finer level's linear residual b - J d, and its
     correction starts from 0; then q + d.  The RK3 step of a level comes from
-    its linearisation point.  Returns the new q."""
+    its linearisation point.  Returns the new q.
+
+    control > 0 applies the residual-based smoothing design of Sec. 3.1.2 to
+    the linear residual b - J d of each level above the coarsest, with the
+    same rules and block limit as fas_vcycle: pre-smoothing repeats blocks of
+    beta1 sweeps until max|b - J d| < eta max|I (b - J d)|, post-smoothing
+    repeats blocks of beta2 sweeps until max|b - J d| is no larger than after
+    the pre-smoothing.  For a linear operator these are the FAS rules'
+    residuals exactly (b - J d = S - A(q0 + d))."""
     dim = mesh["dim"]
     top = n_levels(orders, dim, direction)
     seq = [top]
@@ -346,11 +355,26 @@ def mixed_vcycle(mesh, orders, prm, q, s, beta1, beta2, beta_c, direction=None, 
         if k + 1 == len(seq):
             return smooth_linear(o, base, d, b, beta_c)
         oc = lv_orders[seq[k + 1]]
-        d = smooth_linear(o, base, d, b, beta1)
-        rl = tangent_residual(mesh, o, prm, base, d, b)
-        dc = cycle(k + 1, transfer(dim, o, oc, base), transfer(dim, o, oc, rl))
+        blocks = 0
+        while True:  # pre-smoothing
+            d = smooth_linear(o, base, d, b, beta1)
+            blocks += 1
+            rl = tangent_residual(mesh, o, prm, base, d, b)
+            rc = transfer(dim, o, oc, rl)
+            if control <= 0 or blocks >= control or np.max(np.abs(rl)) < eta * np.max(np.abs(rc)):
+                break
+        r_pre = np.max(np.abs(rl))
+        dc = cycle(k + 1, transfer(dim, o, oc, base), rc)
         d = d + transfer(dim, oc, o, dc)
-        return smooth_linear(o, base, d, b, beta2)
+        blocks = 0
+        while True:  # post-smoothing
+            d = smooth_linear(o, base, d, b, beta2)
+            blocks += 1
+            if control <= 0 or blocks >= control:
+                break
+            if np.max(np.abs(tangent_residual(mesh, o, prm, base, d, b))) <= r_pre:
+                break
+        return d
 
     r = residual(mesh, orders, prm, q, s)
     return q + cycle(0, q, r)

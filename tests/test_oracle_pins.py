@@ -1363,8 +1363,10 @@ def test_mixed_cycle_equals_the_fas_cycle_for_a_linear_operator(monkeypatch):
     defect-correction cycle of the linearised problem are the same iteration
     (the coarse FAS source A_c(I q) + I r minus A_c at the coarse start state
     is the linear right-hand side I r), so with equal time steps they return
-    the same state.  A wrong coarse right-hand side, a missing prolongation
-    of the correction or a wrong linearisation point breaks the equality."""
+    the same state, with the residual-based smoothing rules of Sec. 3.1.2 too
+    (their residuals are the same vectors).  A wrong coarse right-hand side, a
+    missing prolongation of the correction, a wrong linearisation point or a
+    rule that reads the wrong residual breaks the equality."""
     rng = np.random.default_rng(5)
     mesh = syn.periodic_box(2, 2, 1, dim=2)
     dim = 2
@@ -1383,11 +1385,15 @@ def test_mixed_cycle_equals_the_fas_cycle_for_a_linear_operator(monkeypatch):
     monkeypatch.setattr(orc, "cfl_dt", lambda mesh_, o, prm, q: 0.3)
     q = rng.normal(size=5 * orc.nodes_total(of, dim))
     S = rng.normal(size=q.size)
-    for kw in (dict(), dict(delta_n=2), dict(direction=1)):
+    for kw in (dict(), dict(delta_n=2), dict(direction=1), dict(control=4), dict(control=4, eta=0.7),
+               dict(control=3, direction=0)):
         want = orc.fas_vcycle(mesh, of, None, q, S, 2, 1, 3, **kw)
         got = orc.mixed_vcycle(mesh, of, None, q, S, 2, 1, 3, **kw)
         assert np.max(np.abs(got - want)) < 1e-9 * np.max(np.abs(want - q)), kw
         assert np.max(np.abs(want - q)) > 1e-2
+        if kw.get("control"):  # the rules ran extra blocks: the controlled cycle differs from the fixed one
+            fixed = dict(kw, control=0)
+            assert np.max(np.abs(got - orc.mixed_vcycle(mesh, of, None, q, S, 2, 1, 3, **fixed))) > 1e-6, kw
 
 
 def test_mixed_cycle_fixed_point_and_second_order_agreement_with_fas():
