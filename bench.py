@@ -216,34 +216,54 @@ def steady_problem(dg, torch, dev, mesh, o, prm, q_target, seed, amp=0.01):
     return S, syn.zero_mean_wave(mesh, o, q_target, seed, amp)
 
 
+def cycle_to_tolerance(dg, torch, dev, mesh, o, prm, q0, S, arith, mg, tol, max_cycles, q_star=None):
+    """Repeated V-cycles from q0 until max|S - A(q)| < tol (checked every 10
+    cycles, and at the start), timed on the host with the device
+    synchronised on both sides.  With mg["control"] = 0 the cycles replay a
+    CUDA graph; with control > 0 the paper's residual-based smoothing rules
+    decide the sweep counts on the host."""
+    M = dg.Mesh(mesh, o, prm).set_arithmetic(arith)
+    qd = torch.tensor(q0, device=dev)
+    sd = torch.tensor(S, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    k = 0
+    rn = M.residual(qd, sd, norm=True)[1]
+    while rn >= tol and k < max_cycles and np.isfinite(rn):
+        M.vcycle(qd, sd, graph=not mg.get("control", 0), **mg)
+        k += 1
+        if k % 10 == 0:
+            rn = M.residual(qd, sd, norm=True)[1]
+    torch.cuda.synchronize()
+    out = {"seconds": time.perf_counter() - t0, "cycles": k, "final_rnorm": rn, "converged": rn < tol}
+    if q_star is not None:
+        out["max_dev_from_q_star"] = float(np.max(np.abs(qd.cpu().numpy() - q_star)))
+    return out
+
+
 def time_to_tolerance(dg, torch, dev, tol=1e-10, max_cycles=3000):
     """Time to max|r| < tol of a steady problem on the 4x4x1 periodic unit box
     (N = 3, Mach 0.3, Re 100) whose discrete solution is the manufactured
     field: S = A(q*), start q* plus a 1% smooth zero-mean wave; repeated
-    V-cycles 3 -> 1 (3/3/10 sweeps), CUDA graphs, a residual check every 10
-    cycles; FP64, double-float and the mixed form (FP64 residual, FP32
-    tangent-linear correction cycle)."""
+    V-cycles 3 -> 1 (3/3/10 sweeps), a residual check every 10 cycles; FP64,
+    double-float and the mixed form (FP64 residual, FP32 tangent-linear
+    correction cycle), with fixed sweep counts (CUDA graphs) and with the
+    residual-based smoothing control of Sec. 3.1.2 (at most 10 blocks,
+    eta 1.1)."""
     from paper_1806_11456_gb300 import synthetic as syn
     mesh, o, prm, q_star = syn.manufactured_box_4x4x1()
     S, q0 = steady_problem(dg, torch, dev, mesh, o, prm, q_star, seed=11)
     out = {"workload": "periodic box 4x4x1, N=3, S = A(q*) with q* the manufactured field, start q* + 1% smooth zero-mean wave",
            "tol": tol, "cycle": "V 3->1, 3/3/10 sweeps, graph replay, norm every 10 cycles"}
+    fixed = dict(beta1=3, beta2=3, beta_c=10)
     for arith in ("fp64", "df32", "mixed"):
-        M = dg.Mesh(mesh, o, prm).set_arithmetic(arith)
-        qd = torch.tensor(q0, device=dev)
-        sd = torch.tensor(S, device=dev)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        k = 0
-        rn = M.residual(qd, sd, norm=True)[1]
-        while rn >= tol and k < max_cycles:
-            M.vcycle(qd, sd, beta1=3, beta2=3, beta_c=10, graph=True)
-            k += 1
-            if k % 10 == 0:
-                rn = M.residual(qd, sd, norm=True)[1]
-        torch.cuda.synchronize()
-        out[arith] = {"seconds": time.perf_counter() - t0, "cycles": k, "final_rnorm": rn, "converged": rn < tol,
-                      "max_dev_from_q_star": float(np.max(np.abs(qd.cpu().numpy() - q_star)))}
+        out[arith] = cycle_to_tolerance(dg, torch, dev, mesh, o, prm, q0, S, arith, fixed, tol, max_cycles, q_star)
+    ctl = dict(fixed, control=10, eta=1.1)
+    out["controlled"] = {"cycle": "V 3->1, blocks of 3/3 sweeps (10 at the coarsest) under the smoothing control "
+                                  "(at most 10 blocks, eta 1.1), norm every 10 cycles"}
+    for arith in ("fp64", "mixed"):
+        out["controlled"][arith] = cycle_to_tolerance(dg, torch, dev, mesh, o, prm, q0, S, arith, ctl, tol,
+                                                      max_cycles, q_star)
     return out
 
 
@@ -252,33 +272,30 @@ def time_to_tolerance_plate(dg, torch, dev, tol=1e-10, max_cycles=40000):
     flat-plate workload that explicit pseudo-time cycles converge: the
     flat-plate boundary conditions on 24 x 8 uniform elements (h = 0.05),
     N = 3, Mach 0.2, Re 1e4, S = A(q*) with q* a boundary-layer-like field,
-    start q* + 1 % smooth wave; V-cycles 3 -> 1 (2/2/4 sweeps), CUDA graphs,
-    residual every 10 cycles; FP64 against the mixed form.  (The stretched
-    60 x 24 plate itself does not reach 1e-10 with the global time step: its
-    1e-3 wall cells set the step of the whole mesh.)"""
+    start q* + 1 % smooth wave; V-cycles 3 -> 1 (2/2/4 sweeps), residual
+    every 10 cycles; FP64 against the mixed form, with fixed sweep counts
+    (CUDA graphs) and with the smoothing control (at most 10 blocks,
+    eta 1.1).  (The stretched 60 x 24 plate itself does not reach 1e-10 with
+    the global time step: its 1e-3 wall cells set the step of the whole
+    mesh.)"""
     from paper_1806_11456_gb300 import synthetic as syn
     mesh, o, prm, q_star, q0 = syn.plate_steady_case()
     S = (-dg.Mesh(mesh, o, prm).residual(torch.tensor(q_star, device=dev))).cpu().numpy()
     out = {"workload": "plate-shaped variant: 24x8 uniform elements h=0.05 with the flat-plate boundary conditions, "
                        "N=3, Mach 0.2, Re 1e4, S = A(q*) with q* a boundary-layer-like field, start q* + 1% smooth wave",
            "tol": tol, "cycle": "V 3->1, 2/2/4 sweeps, graph replay, norm every 10 cycles"}
+    fixed = dict(beta1=2, beta2=2, beta_c=4)
     for arith in ("fp64", "mixed"):
-        M = dg.Mesh(mesh, o, prm).set_arithmetic(arith)
-        qd = torch.tensor(q0, device=dev)
-        sd = torch.tensor(S, device=dev)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        k = 0
-        rn = M.residual(qd, sd, norm=True)[1]
-        while rn >= tol and k < max_cycles and np.isfinite(rn):
-            M.vcycle(qd, sd, beta1=2, beta2=2, beta_c=4, graph=True)
-            k += 1
-            if k % 10 == 0:
-                rn = M.residual(qd, sd, norm=True)[1]
-        torch.cuda.synchronize()
-        out[arith] = {"seconds": time.perf_counter() - t0, "cycles": k, "final_rnorm": rn, "converged": rn < tol,
-                      "max_dev_from_q_star": float(np.max(np.abs(qd.cpu().numpy() - q_star)))}
+        out[arith] = cycle_to_tolerance(dg, torch, dev, mesh, o, prm, q0, S, arith, fixed, tol, max_cycles, q_star)
     out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    ctl = dict(fixed, control=10, eta=1.1)
+    out["controlled"] = {"cycle": "V 3->1, blocks of 2/2 sweeps (4 at the coarsest) under the smoothing control "
+                                  "(at most 10 blocks, eta 1.1), norm every 10 cycles"}
+    for arith in ("fp64", "mixed"):
+        out["controlled"][arith] = cycle_to_tolerance(dg, torch, dev, mesh, o, prm, q0, S, arith, ctl, tol,
+                                                      max_cycles, q_star)
+    c = out["controlled"]
+    c["speedup_mixed_vs_fp64"] = c["fp64"]["seconds"] / c["mixed"]["seconds"]
     return out
 
 
@@ -415,22 +432,26 @@ def serving_requests(dg, torch, dev, n, seed=4):
     return out
 
 
-def serving(dg, torch, dev, rate=4.0, window=4.0, slots=8, budget=150 << 30, seed=4):
+def serving(dg, torch, dev, rate=4.0, window=4.0, slots=8, budget=150 << 30, seed=4, control=10, legs=None):
     """Serving loop: requests arrive as a seeded Poisson process (rate per
     second over `window` seconds) and are submitted at their arrival times;
-    each is solved to max|r| < 1e-10 (V 3/3/10, graph replay).  The same
-    arrival stream is served by `slots` concurrent slots in double-float
-    arithmetic, by the same slots in FP64, by two slots with shared launches
-    (up to 8 compatible requests per batch, joining at check points) in FP64
-    and in the mixed form, and by one slot in FP64 (the plain form, one solve
-    at a time; its per-request outcomes are listed)."""
+    each is solved to max|r| < 1e-10 by V-cycles 3/3/10 under the paper's
+    residual-based smoothing control of Sec. 3.1.2 (at most `control`
+    blocks, eta 1.1; sweep counts decided on the host; control = 0 runs fixed
+    counts with graph replay instead).  The same arrival stream is served by
+    `slots` concurrent slots in double-float arithmetic, by the same slots in
+    FP64, by two slots with shared launches (up to 8 compatible requests per
+    batch, joining at check points) in FP64 and in the mixed form, and by one
+    slot in FP64 (the plain form, one solve at a time; its per-request
+    outcomes are listed).  `legs` picks a subset."""
     import threading as th
     rng = np.random.default_rng(seed)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * window * 3)))
     arrivals = arrivals[arrivals < window]
     reqs = serving_requests(dg, torch, dev, len(arrivals), seed)
-    # (at most 4000 cycles: the slowest request, a 720-DOF box, needs more than 1500)
-    kw = dict(tol=1e-10, max_cycles=4000, check_every=10, mg=dict(beta1=3, beta2=3, beta_c=10, graph=1))
+    # at most 4000 cycles: under fixed counts one 720-DOF box diverges after ~3,300
+    kw = dict(tol=1e-10, max_cycles=4000, check_every=10,
+              mg=dict(beta1=3, beta2=3, beta_c=10, graph=1, control=control, eta=1.1))
 
     def run(n_slots, arith, batch_max=1, details=False):
         kwa = dict(kw, arith=arith)
@@ -464,23 +485,21 @@ def serving(dg, torch, dev, rate=4.0, window=4.0, slots=8, budget=150 << 30, see
                                 "rnorm": x["rep"]["rnorm"], "latency_s": float(l)} for x, l in zip(infos, lat)]
         return out
 
-    conc = run(slots, "df32")
-    conc64 = run(slots, "fp64")
-    shared64 = run(2, "fp64", batch_max=8)
-    shared_mx = run(2, "mixed", batch_max=8)
-    seq = run(1, "fp64", details=True)
+    plan = {"concurrent": (slots, "df32", 1), "concurrent_fp64": (slots, "fp64", 1), "shared_fp64": (2, "fp64", 8),
+            "shared_mixed": (2, "mixed", 8), "one_at_a_time": (1, "fp64", 1)}
+    res = {k: run(*v, details=(k == "one_at_a_time")) for k, v in plan.items() if legs is None or k in legs}
     nodes = [int(np.sum(np.prod(o[:, :m["dim"]] + 1, axis=1))) for (m, o, *_r) in reqs]
     return {"workload": f"{len(reqs)} requests, Poisson {rate}/s over {window} s: periodic 2D boxes 2-6 per side "
                         "N in {2,3} and 3D boxes 3 per side N = 2, Mach U[0.25,0.4], Re U_log[50,200], "
-                        "S = A(q*), to max|r| < 1e-10 (at most 4000 V-cycles 3/3/10, residual checked every 10)",
+                        "S = A(q*), to max|r| < 1e-10 (at most 4000 V-cycles 3/3/10, residual checked every 10"
+                        + (f", residual-based smoothing control of at most {control} blocks, eta 1.1)" if control
+                           else ", fixed sweep counts)"),
             "requests": len(reqs), "dof_range": [5 * min(nodes), 5 * max(nodes)],
             "offered_dof_per_s": 5.0 * sum(nodes) / window,
-            "concurrent": conc, "concurrent_fp64": conc64, "shared_fp64": shared64, "shared_mixed": shared_mx,
-            "one_at_a_time": seq,
-            "p99_speedup": seq["p99_s"] / conc["p99_s"], "p50_speedup": seq["p50_s"] / conc["p50_s"]}
+            "control": control, **res}
 
 
-def serving_large(dg, torch, dev, rate=2.0, window=4.0, seed=6):
+def serving_large(dg, torch, dev, rate=2.0, window=4.0, seed=6, control=10, legs=None):
     """Serving with larger requests (opt-in, --serving-large): Poisson
     arrivals (rate per second over `window` seconds) of periodic 2D boxes of
     12-28 elements per side at orders U[2,3]^2 (top order 3) and 3D boxes of
@@ -488,9 +507,10 @@ def serving_large(dg, torch, dev, rate=2.0, window=4.0, seed=6):
     (the domain grows with the request), Mach U[0.25,0.4], Re U_log[50,200],
     each a steady problem S = A(q*) with q* the manufactured field, started
     at q* plus a 1 % smooth wave, solved to max|r| < 1e-10 (at most 6000
-    V-cycles 3/3/10, residual every 10).  Served one at a time in FP64, by 8
-    concurrent slots in FP64, and by 2 slots with shared launches (up to 8
-    per batch) in the mixed form."""
+    V-cycles 3/3/10 under the smoothing control of at most `control` blocks,
+    residual every 10).  Served one at a time in FP64, by 8 concurrent slots
+    in FP64, and by 2 slots with shared launches (up to 8 per batch) in the
+    mixed form."""
     from paper_1806_11456_gb300 import synthetic as syn
     import threading as th
     rng = np.random.default_rng(seed)
@@ -514,7 +534,8 @@ def serving_large(dg, torch, dev, rate=2.0, window=4.0, seed=6):
         q_star = syn.manufactured_state(mesh, o, seed * 1000 + k, mach, prm[0], amp=0.05)
         S, q0 = steady_problem(dg, torch, dev, mesh, o, prm, q_star, seed=k)
         reqs.append((mesh, o, prm, q0, S))
-    kw = dict(tol=1e-10, max_cycles=6000, check_every=10, mg=dict(beta1=3, beta2=3, beta_c=10, graph=1))
+    kw = dict(tol=1e-10, max_cycles=6000, check_every=10,
+              mg=dict(beta1=3, beta2=3, beta_c=10, graph=1, control=control, eta=1.1))
 
     def run(n_slots, arith, batch_max=1):
         ids = [None] * len(reqs)
@@ -544,17 +565,19 @@ def serving_large(dg, torch, dev, rate=2.0, window=4.0, seed=6):
     nodes = [int(np.sum(np.prod(o[:, :m["dim"]] + 1, axis=1))) for (m, o, *_r) in reqs]
     return {"workload": f"{len(reqs)} requests, Poisson {rate}/s over {window} s: periodic 2D boxes 12-28 per side "
                         "orders U[2,3]^2 and 3D boxes 4 or 8 per side orders U[1,2]^3, element size 0.25, "
-                        "S = A(q*), to max|r| < 1e-10 (scaled down from 20/s over 120 s and 1e4-2e7 DOF)",
+                        "S = A(q*), to max|r| < 1e-10 (scaled down from 20/s over 120 s and 1e4-2e7 DOF)"
+                        + (f"; smoothing control of at most {control} blocks, eta 1.1" if control else ""),
             "dof": [5 * n for n in nodes], "offered_dof_per_s": 5.0 * sum(nodes) / window,
-            "one_at_a_time": run(1, "fp64"), "concurrent_fp64": run(8, "fp64"),
-            "shared_mixed": run(2, "mixed", batch_max=8)}
+            **{k: run(*v) for k, v in {"one_at_a_time": (1, "fp64"), "concurrent_fp64": (8, "fp64"),
+                                        "shared_mixed": (2, "mixed", 8)}.items() if legs is None or k in legs}}
 
 
 def precision_report(dg, torch, dev):
     """Error of each double-float output against the FP64 path on the
     sphere workload (13,824 quadratic hexes, orders U[1,6]^3, Mach 0.2,
     Re 200; the FP64 path matches the oracle to 1e-12 in the parity tests):
-    the residual, one V-cycle 6 -> 1 (1/1/2 sweeps) and the tau table."""
+    the residual, one V-cycle 6 -> 1 (1/1/2 sweeps) and the tau table; and
+    the mixed form's outputs on the same workload (mixed_precision_report)."""
     from paper_1806_11456_gb300 import synthetic as syn
     mesh, o, prm = syn.sphere_shell_13824()
     q = syn.smooth_state(mesh, o, prm, 5, amp=0.02)
@@ -573,6 +596,39 @@ def precision_report(dg, torch, dev):
     meas = t["fp64"] >= 0
     out["tau_rel_err"] = float(np.max(np.abs(t["df32"] - t["fp64"])[meas]) / np.max(t["fp64"][meas]))
     out["tau_measured_same"] = bool(np.array_equal(t["df32"] >= 0, meas))
+    out["mixed"] = mixed_precision_report(dg, torch, dev, mesh, o, prm, q, M["fp64"], r["fp64"], t["fp64"])
+    return out
+
+
+def mixed_precision_report(dg, torch, dev, mesh, o, prm, q, M64, r64, t64):
+    """Errors of the mixed form's outputs on the sphere workload against the
+    FP64 path (which matches the oracle to 1e-12 in the parity tests).  Its
+    FP64 roles (residual, tau) must give the FP64 bits.  Its FP32 tangent
+    J(q) dq is compared with the fourth-order central difference of the FP64
+    residual along dq (the oracle's definition of the derivative, relative
+    step 1e-4), per variable relative to max |J dq| of that variable.  One
+    mixed V-cycle 6 -> 1 (1/1/2 sweeps) is compared with one FAS V-cycle:
+    the two are different iterations, so that difference holds the
+    linearisation error besides FP32 rounding."""
+    from paper_1806_11456_gb300 import synthetic as syn
+    Mm = dg.Mesh(mesh, o, prm).set_arithmetic("mixed")
+    qd = torch.tensor(q, device=dev)
+    out = {"residual_bitwise": bool(np.array_equal(Mm.residual(qd).cpu().numpy(), r64)),
+           "tau_bitwise": bool(np.array_equal(Mm.tau_estimate(qd, None, dir_mask=7), t64))}
+    dq = np.random.default_rng(4).normal(size=q.size) * 1e-2 * np.abs(q)
+    dqd = torch.tensor(dq, device=dev)
+    jdq = -Mm.residual_tangent(qd, dqd).cpu().numpy()
+    h = 1e-4 * float(np.max(np.abs(q))) / float(np.max(np.abs(dq)))
+    A = lambda x: -M64.residual(torch.tensor(x, device=dev)).cpu().numpy()
+    fd = (-A(q + 2 * h * dq) + 8 * A(q + h * dq) - 8 * A(q - h * dq) + A(q - 2 * h * dq)) / (12 * h)
+    err = np.abs(syn.from_blocked(jdq - fd, o, 3)).max(axis=1)
+    scale = np.abs(syn.from_blocked(fd, o, 3)).max(axis=1)
+    out["tangent_rel_err_per_var"] = [float(e / s) for e, s in zip(err, scale)]
+    qa, qb = torch.tensor(q, device=dev), torch.tensor(q, device=dev)
+    M64.vcycle(qa, None, beta1=1, beta2=1, beta_c=2)
+    Mm.vcycle(qb, None, beta1=1, beta2=1, beta_c=2)
+    qa, qb = qa.cpu().numpy(), qb.cpu().numpy()
+    out["vcycle_diff_rel_to_correction"] = float(np.max(np.abs(qb - qa)) / np.max(np.abs(qa - q)))
     return out
 
 

@@ -163,8 +163,9 @@ int dg_mesh_layout(const dg_mesh* mesh, int64_t* total_nodes, int64_t* elem_offs
  *                 transfers) on the linearised problem J(Q) d = r with the
  *                 Jacobian-vector products J(I Q) d evaluated in FP32 tangent
  *                 arithmetic (their rounding error scales with |d|, so the
- *                 cycle converges to the FP64 solution), and Q += d.  Fixed
- *                 sweep counts only (mg->control must be 0).
+ *                 cycle converges to the FP64 solution), and Q += d.  With
+ *                 mg->control > 0 the smoothing rules of Sec. 3.1.2 read
+ *                 each level's linear residual b - J d (FP64 norms).
  * Memory formats do not change (FP64 state, source and residual arrays) and
  * the smoother's state update stays FP64.  Cached V-cycle graphs are dropped.
  */

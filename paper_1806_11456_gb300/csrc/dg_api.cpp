@@ -106,6 +106,77 @@ static int smooth_level(Cycle& C, Level* L, double* Q, const double* Sv, int swe
   return DG_OK;
 }
 
+// Residual-based smoothing of Sec. 3.1.2 on one level, decided per solve slot
+// on the host.  d_scalars holds per slot [2n, 3n) max|r^P|, [3n, 4n)
+// max|I r^P|, [4n, 5n) the mask of the slots still smoothing.  Held solves
+// (dg_batch_set_active) take no part in the rules: they count as done.
+struct SmoothingRules {
+  Cycle& C;
+  const int ns;
+  const bool on;
+  const double eta;
+  double* const dN;
+  double* const dP;
+  double* const dmask;
+  std::vector<double> h, rpre;
+  std::vector<char> held, done;
+  const double* mask = nullptr;  // null while every slot still smooths
+
+  explicit SmoothingRules(Cycle& c)
+      : C(c), ns(c.m->nslots), on(c.mg.control > 0), eta(c.mg.eta > 0.0 ? c.mg.eta : 1.1),
+        dN(c.m->d_scalars + 2 * ns), dP(c.m->d_scalars + 3 * ns), dmask(c.m->d_scalars + 4 * ns),
+        h(2 * ns), rpre(ns, 0.0), held(ns, 0) {
+    if (C.m->freeze)
+      for (int j = 0; j < ns; ++j) held[j] = C.m->active[j] ? 0 : 1;
+    done = held;
+  }
+  // hold the slots that are done for the next block
+  int hold_done() {
+    std::vector<double> hm(ns);
+    for (int j = 0; j < ns; ++j) hm[j] = done[j] ? 0.0 : 1.0;
+    DG_CUDA_TRY(cudaMemcpyAsync(dmask, hm.data(), ns * sizeof(double), cudaMemcpyHostToDevice, C.st));
+    DG_CUDA_TRY(cudaStreamSynchronize(C.st));
+    mask = dmask;
+    return DG_OK;
+  }
+  // after pre-smoothing block `blk`, with dN and dP filled: a slot is done
+  // once max|r^P| < eta max|I r^P| or after `control` blocks
+  int pre(int blk, bool* all) {
+    DG_CUDA_TRY(cudaMemcpyAsync(h.data(), dN, 2 * ns * sizeof(double), cudaMemcpyDeviceToHost, C.st));
+    DG_CUDA_TRY(cudaStreamSynchronize(C.st));
+    return decide([&](int j) {
+      rpre[j] = h[j];
+      return h[j] < eta * h[ns + j] || blk >= C.mg.control;
+    }, all);
+  }
+  // the post-smoothing rule starts afresh
+  void restart() {
+    done = held;
+    mask = nullptr;
+  }
+  // after a post-smoothing block, with dN filled: a slot is done once max|r|
+  // is no larger than after its pre-smoothing
+  int post(bool* all) {
+    DG_CUDA_TRY(cudaMemcpyAsync(h.data(), dN, ns * sizeof(double), cudaMemcpyDeviceToHost, C.st));
+    DG_CUDA_TRY(cudaStreamSynchronize(C.st));
+    return decide([&](int j) { return h[j] <= rpre[j]; }, all);
+  }
+
+ private:
+  template <typename F>
+  int decide(F&& rule, bool* all) {
+    bool a = true, any = false;
+    for (int j = 0; j < ns; ++j) {
+      if (!done[j] && rule(j)) done[j] = 1;
+      a = a && done[j];
+      any = any || done[j];
+    }
+    *all = a;
+    if (!a && any) return hold_done();
+    return DG_OK;
+  }
+};
+
 static int vcycle_level(Cycle& C, size_t k, double* Qf, const double* Sf) {
   const bool finest = (k == 0);
   Level* L = C.lv[k];
@@ -127,77 +198,36 @@ static int vcycle_level(Cycle& C, size_t k, double* Qf, const double* Sf) {
   }
   Level* Cc = C.lv[k + 1];
   DG_TRY(ensure_work(Cc));
-  // Residual-based smoothing (Sec. 3.1.2), decided per solve slot on the host:
-  // d_scalars holds per slot [2n, 3n) max|r^P|, [3n, 4n) max|I r^P|, [4n, 5n)
-  // the mask of the slots still smoothing.
-  const int ns = C.m->nslots;
-  const bool ctl = C.mg.control > 0;
-  const double eta = C.mg.eta > 0.0 ? C.mg.eta : 1.1;
-  double* dN = C.m->d_scalars + 2 * ns;
-  double* dP = C.m->d_scalars + 3 * ns;
-  double* dmask = C.m->d_scalars + 4 * ns;
-  std::vector<double> h(2 * ns), rpre(ns, 0.0);
-  std::vector<char> held(ns, 0), done(ns, 0);
-  if (C.m->freeze)  // held solves take no part in the rules: they count as done
-    for (int j = 0; j < ns; ++j) held[j] = C.m->active[j] ? 0 : 1;
-  done = held;
-  const double* mask = nullptr;
-  // hold the slots that are done for the next block (none while all still run)
-  auto hold_done = [&]() -> int {
-    std::vector<double> hm(ns);
-    for (int j = 0; j < ns; ++j) hm[j] = done[j] ? 0.0 : 1.0;
-    DG_CUDA_TRY(cudaMemcpyAsync(dmask, hm.data(), ns * sizeof(double), cudaMemcpyHostToDevice, C.st));
-    DG_CUDA_TRY(cudaStreamSynchronize(C.st));
-    mask = dmask;
-    return DG_OK;
-  };
+  SmoothingRules R(C);
   // pre-smoothing: blocks of beta1 sweeps until max|r^P| < eta max|I r^P|
   for (int blk = 1;; ++blk) {
-    DG_TRY(smooth_level(C, L, Q, Sv, C.mg.beta1, mask));
-    if (ctl) DG_TRY(fill(dN, 0.0, ns, C.st));
-    DG_TRY(residual(C.m, L, Q, Sv, L->d_R, false, C.st, ctl ? dN : nullptr, -1, nullptr, nullptr));
+    DG_TRY(smooth_level(C, L, Q, Sv, C.mg.beta1, R.mask));
+    if (R.on) DG_TRY(fill(R.dN, 0.0, R.ns, C.st));
+    DG_TRY(residual(C.m, L, Q, Sv, L->d_R, false, C.st, R.on ? R.dN : nullptr, -1, nullptr, nullptr));
     C.evals++;
     C.dofs += 5.0 * L->nodes;
     DG_TRY(transfer(C.m, L, Cc, 5, L->d_R, Cc->d_S, C.st));
-    if (!ctl) break;
-    DG_TRY(slot_maxabs(C.m, Cc, Cc->d_S, dP, C.st));
-    DG_CUDA_TRY(cudaMemcpyAsync(h.data(), dN, 2 * ns * sizeof(double), cudaMemcpyDeviceToHost, C.st));
-    DG_CUDA_TRY(cudaStreamSynchronize(C.st));
-    bool all = true, any = false;
-    for (int j = 0; j < ns; ++j) {
-      if (!done[j]) {
-        rpre[j] = h[j];
-        if (h[j] < eta * h[ns + j] || blk >= C.mg.control) done[j] = 1;
-      }
-      all = all && done[j];
-      any = any || done[j];
-    }
+    if (!R.on) break;
+    DG_TRY(slot_maxabs(C.m, Cc, Cc->d_S, R.dP, C.st));
+    bool all = false;
+    DG_TRY(R.pre(blk, &all));
     if (all) break;
-    if (any) DG_TRY(hold_done());
   }
   DG_TRY(transfer(C.m, L, Cc, 5, Q, Cc->d_Q, C.st));
   DG_TRY(vcycle_level(C, k + 1, nullptr, nullptr));
   DG_TRY(transfer(C.m, Cc, L, 5, Cc->d_Q, Q, C.st, Cc->d_Q0, true));
   // post-smoothing: blocks of beta2 sweeps until max|r| <= its value after the pre-smoothing
-  done = held;
-  mask = nullptr;
+  R.restart();
   for (int blk = 1;; ++blk) {
-    DG_TRY(smooth_level(C, L, Q, Sv, C.mg.beta2, mask));
-    if (!ctl || blk >= C.mg.control) break;
-    DG_TRY(fill(dN, 0.0, ns, C.st));
-    DG_TRY(residual(C.m, L, Q, Sv, L->d_R, false, C.st, dN, -1, nullptr, nullptr));
+    DG_TRY(smooth_level(C, L, Q, Sv, C.mg.beta2, R.mask));
+    if (!R.on || blk >= C.mg.control) break;
+    DG_TRY(fill(R.dN, 0.0, R.ns, C.st));
+    DG_TRY(residual(C.m, L, Q, Sv, L->d_R, false, C.st, R.dN, -1, nullptr, nullptr));
     C.evals++;
     C.dofs += 5.0 * L->nodes;
-    DG_CUDA_TRY(cudaMemcpyAsync(h.data(), dN, ns * sizeof(double), cudaMemcpyDeviceToHost, C.st));
-    DG_CUDA_TRY(cudaStreamSynchronize(C.st));
-    bool all = true, any = false;
-    for (int j = 0; j < ns; ++j) {
-      if (!done[j] && h[j] <= rpre[j]) done[j] = 1;
-      all = all && done[j];
-      any = any || done[j];
-    }
+    bool all = false;
+    DG_TRY(R.post(&all));
     if (all) break;
-    if (any) DG_TRY(hold_done());
   }
   return DG_OK;
 }
@@ -217,11 +247,13 @@ static int vcycle_level(Cycle& C, size_t k, double* Qf, const double* Sf) {
 // the FAS source A_c(I Q) + I r, whose A_c(I Q) term cancels against the
 // coarse operator's value at Q_l.  Near convergence the cycle contracts like
 // the FAS cycle; far from it the linearisation error is O(|d|^2).
-static int smooth_tangent(Cycle& C, Level* L, const double* base, double* d, const double* b, int sweeps) {
+static int smooth_tangent(Cycle& C, Level* L, const double* base, double* d, const double* b, int sweeps,
+                          const double* mask = nullptr) {
   // pseudo-time step of the linear problem from its linearisation point,
-  // fixed during the block
+  // fixed during the block; slots whose mask is 0 get dt = 0 (held)
   double* dt = C.m->d_scalars;
   if (sweeps > 0) DG_TRY(cfl_dt(C.m, L, base, dt, C.st));
+  if (sweeps > 0 && mask) DG_TRY(mask_dt(C.m, dt, mask, C.st));
   if (sweeps > 0 && C.m->freeze) DG_TRY(mask_dt(C.m, dt, C.m->d_scalars + 6 * C.m->nslots, C.st));
   for (int k = 0; k < sweeps; ++k)
     for (int stage = 0; stage < 3; ++stage) {
@@ -233,6 +265,10 @@ static int smooth_tangent(Cycle& C, Level* L, const double* base, double* d, con
   return DG_OK;
 }
 
+// The linear V-cycle on level k: J(base) d = b with d starting at 0.  With
+// mg.control > 0 the smoothing rules of Sec. 3.1.2 read the linear residual
+// b - J d, as the FAS rules read S - A(Q) (for a linear operator they are the
+// same vectors).
 static int tangent_level(Cycle& C, size_t k) {
   Level* L = C.lv[k];
   DG_TRY(ensure_work(L));
@@ -243,15 +279,35 @@ static int tangent_level(Cycle& C, size_t k) {
   if (k + 1 == C.lv.size()) return smooth_tangent(C, L, base, d, b, C.mg.beta_c);
   Level* Cc = C.lv[k + 1];
   DG_TRY(ensure_work(Cc));
-  DG_TRY(smooth_tangent(C, L, base, d, b, C.mg.beta1));
-  DG_TRY(residual_tangent(C.m, L, base, d, b, L->d_R, C.st, nullptr, -1, nullptr, nullptr));
-  C.evals++;
-  C.dofs += 5.0 * L->nodes;
-  DG_TRY(transfer(C.m, L, Cc, 5, L->d_R, Cc->d_S, C.st));  // coarse right-hand side I (b - J d), FP64
-  DG_TRY(transfer(C.m, L, Cc, 5, base, Cc->d_Q0, C.st));   // coarse linearisation point I Q
+  SmoothingRules R(C);
+  for (int blk = 1;; ++blk) {  // pre-smoothing
+    DG_TRY(smooth_tangent(C, L, base, d, b, C.mg.beta1, R.mask));
+    if (R.on) DG_TRY(fill(R.dN, 0.0, R.ns, C.st));
+    DG_TRY(residual_tangent(C.m, L, base, d, b, L->d_R, C.st, R.on ? R.dN : nullptr, -1, nullptr, nullptr));
+    C.evals++;
+    C.dofs += 5.0 * L->nodes;
+    DG_TRY(transfer(C.m, L, Cc, 5, L->d_R, Cc->d_S, C.st));  // coarse right-hand side I (b - J d), FP64
+    if (!R.on) break;
+    DG_TRY(slot_maxabs(C.m, Cc, Cc->d_S, R.dP, C.st));
+    bool all = false;
+    DG_TRY(R.pre(blk, &all));
+    if (all) break;
+  }
+  DG_TRY(transfer(C.m, L, Cc, 5, base, Cc->d_Q0, C.st));  // coarse linearisation point I Q
   DG_TRY(tangent_level(C, k + 1));
   DG_TRY(transfer(C.m, Cc, L, 5, Cc->d_Q, d, C.st, nullptr, true));  // d += I d_c
-  DG_TRY(smooth_tangent(C, L, base, d, b, C.mg.beta2));
+  R.restart();
+  for (int blk = 1;; ++blk) {  // post-smoothing
+    DG_TRY(smooth_tangent(C, L, base, d, b, C.mg.beta2, R.mask));
+    if (!R.on || blk >= C.mg.control) break;
+    DG_TRY(fill(R.dN, 0.0, R.ns, C.st));
+    DG_TRY(residual_tangent(C.m, L, base, d, b, L->d_R, C.st, R.dN, -1, nullptr, nullptr));
+    C.evals++;
+    C.dofs += 5.0 * L->nodes;
+    bool all = false;
+    DG_TRY(R.post(&all));
+    if (all) break;
+  }
   return DG_OK;
 }
 
@@ -327,10 +383,6 @@ static int run_vcycle(dg_mesh* m, const std::vector<int32_t>& top_orders, double
   *nlev = (int)C.lv.size();
   for (Level* L : C.lv) DG_TRY(prepare_arith(m, L, st));  // never allocate inside a capture
   const bool mixed = m->arith == DG_ARITH_MIXED;
-  if (mixed && mg.control > 0) {
-    set_error("the mixed-precision cycle runs fixed sweep counts (control = 0)");
-    return DG_EINVAL;
-  }
   if (!mg.graph || mg.control > 0) {  // controlled sweep counts are decided on the host
     DG_TRY(mixed ? mixed_cycle(C, Q, Sv) : vcycle_level(C, 0, Q, Sv));
     *evals = C.evals;

@@ -136,6 +136,63 @@ def test_mixed_vcycle_matches_the_oracle_cycle(dg, name, kw, graph):
     assert err <= TOL_CYCLE * corr
 
 
+# the smoothing rules of Sec. 3.1.2 on the linear residual b - J d: the
+# number of operator evaluations (sweeps and rule checks) must equal the
+# oracle's, so every rule took the same decision on both sides
+@pytest.mark.parametrize("name,kw", [
+    ("box2d", dict(beta1=1, beta2=1, beta_c=3, control=5, eta=1.1)),
+    ("box2d", dict(beta1=1, beta2=1, beta_c=3, control=5, eta=2.0)),
+    ("plate2d_all_bcs", dict(beta1=1, beta2=1, beta_c=2, control=4, eta=1.5)),
+    ("mortars3d", dict(beta1=1, beta2=1, beta_c=2, control=3, eta=1.1)),
+])
+def test_mixed_vcycle_with_smoothing_control_matches_the_oracle(dg, name, kw, monkeypatch):
+    mesh, o, prm = CASES[name]()
+    qs = syn.oblique_state(mesh, o, prm, 7, amp=0.01)
+    S = orc.operator_A(mesh, o, prm, qs)
+    q0 = syn.oblique_state(mesh, o, prm, 8, amp=0.01)
+    M = dg.Mesh(mesh, o, prm).set_arithmetic("mixed")
+    qd = _dev(q0)
+    rep = M.vcycle(qd, _dev(S), **kw)
+    calls = []
+    tangent = orc.tangent_residual
+
+    def counted(*a, **k):
+        calls.append(1)
+        return tangent(*a, **k)
+
+    monkeypatch.setattr(orc, "tangent_residual", counted)
+    qo = orc.mixed_vcycle(mesh, o, prm, q0, S, kw["beta1"], kw["beta2"], kw["beta_c"],
+                          control=kw["control"], eta=kw["eta"])
+    fixed = 3 * (kw["beta1"] + kw["beta2"]) + 1
+    print(name, kw, "evaluations gpu / oracle:", rep["residual_evals"], 1 + len(calls))
+    assert rep["residual_evals"] == 1 + len(calls)  # the FP64 defect + the tangent evaluations
+    corr = np.max(np.abs(qo - q0))
+    err = np.max(np.abs(qd.cpu().numpy() - qo))
+    print(name, "controlled mixed cycle error / correction:", err / corr)
+    assert corr > 0 and err <= TOL_CYCLE * corr
+    assert len(calls) > (rep["levels"] - 1) * fixed + 3 * kw["beta_c"]  # the rules added blocks or checks
+
+
+def test_mixed_smoothing_control_per_solve_in_a_batch(dg):
+    """Three solves whose rules take different decisions: each comes out of
+    the batched controlled mixed cycle with the bits it gets alone."""
+    items = []
+    for seed in (2, 0, 1):
+        mesh = syn.box_mesh(np.linspace(-0.2, 1, 5), [0, 0.05, 0.12, 0.3], bc=dict(xmin=1, xmax=2, ymin=4, ymax=1))
+        o = syn.uniform_orders(mesh["K"], 2, 3)
+        prm = syn.flow_params(mach=0.3, re=100.0)
+        items.append((mesh, o, prm, syn.perturbed_state(mesh, o, prm, seed, amp=0.05)))
+    B = dg.Mesh.batch([(m, o, p) for (m, o, p, _) in items]).set_arithmetic("mixed")
+    off = B.solve_slices()
+    qb = _dev(np.concatenate([q for (*_, q) in items]))
+    B.vcycle(qb, None, 1, 1, 2, control=6, eta=1.5)
+    qbn = qb.cpu().numpy()
+    for k, (m, o, p, q) in enumerate(items):
+        qa = _dev(q)
+        dg.Mesh(m, o, p).set_arithmetic("mixed").vcycle(qa, None, 1, 1, 2, control=6, eta=1.5)
+        assert np.array_equal(qbn[5 * off[k]:5 * off[k + 1]], qa.cpu().numpy()), k
+
+
 def test_mixed_steady_solve_satisfies_the_fp64_equations(dg):
     """A steady problem whose discrete solution is known (S = A(q*)): the
     mixed form cycles until its FP64 residual is below 1e-10; the oracle's
