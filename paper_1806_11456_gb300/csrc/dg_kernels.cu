@@ -1789,12 +1789,15 @@ __global__ void __launch_bounds__(kTileNodes) k_cfl(LevelArgsT<double> A, const 
 
 // ---------------------------------------------------------------------------
 // transfers between order maps: out_e = (T2 x T1 x T0) (in_e - sub_e),
-// sum-factorised through shared memory (one direction per pass, one
-// variable at a time so the buffers stay within 2 x the largest slab)
+// sum-factorised through shared memory, one direction per pass.  A pass
+// covers `vgroup` variables at once (all five unless an element's slab is
+// too large for that), and a flat direction (one node on both sides, the z
+// direction of a 2D mesh) is skipped: its factor is the 1 x 1 identity.
 // ---------------------------------------------------------------------------
 constexpr int kTransferThreads = 128;
 // largest per-variable slab: 3D elements have <= 729 nodes and n <= 13 per
-// direction, so f1*f2 <= 364 and t0 <= 13 bound the x-pass intermediate
+// direction, so f1*f2 <= 364 and t0 <= 13 bound the x-pass intermediate;
+// the shared memory holds two slabs of that size (or more smaller ones)
 constexpr int kTransferMaxSlab = 4800;
 
 DEV int transfer_slab(int f0, int f1, int f2, int t0, int t1, int t2) {
@@ -1805,7 +1808,7 @@ __global__ void __launch_bounds__(kTransferThreads) k_transfer(const int32_t* __
                                                                const int32_t* __restrict__ offf,
                                                                const int32_t* __restrict__ nt,
                                                                const int32_t* __restrict__ offt, int nvar,
-                                                               const double* __restrict__ in,
+                                                               int vgroup, const double* __restrict__ in,
                                                                const double* __restrict__ sub,
                                                                double* __restrict__ out, int accumulate) {
   pdl_enter();
@@ -1817,41 +1820,55 @@ __global__ void __launch_bounds__(kTransferThreads) k_transfer(const int32_t* __
   const double* T0 = c_T + ((size_t)f0 * kNP + t0) * kNP * kNP;
   const double* T1 = c_T + ((size_t)f1 * kNP + t1) * kNP * kNP;
   const double* T2 = c_T + ((size_t)f2 * kNP + t2) * kNP * kNP;
-  const int maxn = transfer_slab(f0, f1, f2, t0, t1, t2);
+  const int slab = transfer_slab(f0, f1, f2, t0, t1, t2);
   double* bA = sbuf;
-  double* bB = sbuf + maxn;
+  double* bB = sbuf + (size_t)vgroup * slab;
   const int n1x = f2 * f1 * t0, n2y = f2 * t1 * t0;
-  for (int v = 0; v < nvar; ++v) {
-    const double* ie = in + (size_t)nvar * offf[e] + (size_t)v * nnf;
-    const double* se = sub ? sub + (size_t)nvar * offf[e] + (size_t)v * nnf : nullptr;
-    double* oe = out + (size_t)nvar * offt[e] + (size_t)v * nnt;
-    for (int i = threadIdx.x; i < nnf; i += blockDim.x) bA[i] = se ? ie[i] - se[i] : ie[i];
+  const bool flat = (f2 == 1 && t2 == 1);
+  for (int v0 = 0; v0 < nvar; v0 += vgroup) {
+    const int nv = min(vgroup, nvar - v0);
+    const size_t ib = (size_t)nvar * offf[e] + (size_t)v0 * nnf;
+    double* oe = out + (size_t)nvar * offt[e] + (size_t)v0 * nnt;
+    for (int i = threadIdx.x; i < nv * nnf; i += blockDim.x) {
+      const int v = i / nnf, k = i - v * nnf;
+      bA[v * slab + k] = sub ? in[ib + i] - sub[ib + i] : in[ib + i];
+    }
     __syncthreads();
-    for (int i = threadIdx.x; i < n1x; i += blockDim.x) {  // x pass: [k2][k1][j0]
-      int j0 = i % t0, k12 = i / t0;
-      const double* src = bA + k12 * f0;
+    for (int i = threadIdx.x; i < nv * n1x; i += blockDim.x) {  // x pass: [k2][k1][j0]
+      const int v = i / n1x, r = i - v * n1x;
+      const int j0 = r % t0, k12 = r / t0;
+      const double* src = bA + v * slab + k12 * f0;
       double acc = 0.0;
       for (int k0 = 0; k0 < f0; ++k0) acc += T0[j0 * f0 + k0] * src[k0];
-      bB[i] = acc;
+      bB[v * slab + r] = acc;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < n2y; i += blockDim.x) {  // y pass: [k2][j1][j0]
-      int j0 = i % t0, j1 = (i / t0) % t1, k2 = i / (t0 * t1);
-      const double* src = bB + k2 * f1 * t0 + j0;
+    for (int i = threadIdx.x; i < nv * n2y; i += blockDim.x) {  // y pass: [k2][j1][j0]
+      const int v = i / n2y, r = i - v * n2y;
+      const int j0 = r % t0, j1 = (r / t0) % t1, k2 = r / (t0 * t1);
+      const double* src = bB + v * slab + k2 * f1 * t0 + j0;
       double acc = 0.0;
       for (int k1 = 0; k1 < f1; ++k1) acc += T1[j1 * f1 + k1] * src[k1 * t0];
-      bA[i] = acc;
+      if (!flat) {
+        bA[v * slab + r] = acc;
+      } else if (accumulate) {  // flat: [j1][j0] is the output layout
+        oe[v * nnt + r] += acc;
+      } else {
+        oe[v * nnt + r] = acc;
+      }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < nnt; i += blockDim.x) {  // z pass: [j2][j1][j0]
-      int j01 = i % (t0 * t1), j2 = i / (t0 * t1);
-      const double* src = bA + j01;
+    if (flat) continue;
+    for (int i = threadIdx.x; i < nv * nnt; i += blockDim.x) {  // z pass: [j2][j1][j0]
+      const int v = i / nnt, r = i - v * nnt;
+      const int j01 = r % (t0 * t1), j2 = r / (t0 * t1);
+      const double* src = bA + v * slab + j01;
       double acc = 0.0;
       for (int k2 = 0; k2 < f2; ++k2) acc += T2[j2 * f2 + k2] * src[k2 * t1 * t0];
       if (accumulate)
-        oe[i] += acc;
+        oe[v * nnt + r] += acc;
       else
-        oe[i] = acc;
+        oe[v * nnt + r] = acc;
     }
     __syncthreads();
   }
@@ -2549,14 +2566,15 @@ int transfer(const dg_mesh* m, const Level* from, const Level* to, int nvar, con
     size_t b = std::max((size_t)f[2] * f[1] * t[0], (size_t)f[2] * t[1] * t[0]);
     slab = std::max(slab, std::max(a, b));
   }
-  if (slab > (size_t)kTransferMaxSlab) {
+  if (slab > (size_t)kTransferMaxSlab || nvar < 1) {
     set_error("transfer: element too large for the shared-memory slab");
     return DG_EINVAL;
   }
+  // as many variables per pass as two slabs each fit in the reserved shared memory
+  const int vgroup = std::max(1, std::min(nvar, (int)(kTransferMaxSlab / slab)));
   count_launch();
-  launch_k(k_transfer, from->K, kTransferThreads, 2 * slab * sizeof(double), st, from->d_n, from->d_off, to->d_n,
-                                                                          to->d_off, nvar, in, sub, out,
-                                                                          accumulate ? 1 : 0);
+  launch_k(k_transfer, from->K, kTransferThreads, 2 * (size_t)vgroup * slab * sizeof(double), st, from->d_n,
+           from->d_off, to->d_n, to->d_off, nvar, vgroup, in, sub, out, accumulate ? 1 : 0);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
 }
