@@ -227,15 +227,16 @@ def cycle_to_tolerance(dg, torch, dev, mesh, o, prm, q0, S, arith, mg, tol, max_
     sd = torch.tensor(S, device=dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    k = 0
+    k, evals = 0, 0
     rn = M.residual(qd, sd, norm=True)[1]
     while rn >= tol and k < max_cycles and np.isfinite(rn):
-        M.vcycle(qd, sd, graph=not mg.get("control", 0), **mg)
+        evals += M.vcycle(qd, sd, graph=not mg.get("control", 0), **mg)["residual_evals"]
         k += 1
         if k % 10 == 0:
             rn = M.residual(qd, sd, norm=True)[1]
     torch.cuda.synchronize()
-    out = {"seconds": time.perf_counter() - t0, "cycles": k, "final_rnorm": rn, "converged": rn < tol}
+    out = {"seconds": time.perf_counter() - t0, "cycles": k, "final_rnorm": rn, "converged": rn < tol,
+           "operator_evals_per_cycle": evals / max(k, 1)}
     if q_star is not None:
         out["max_dev_from_q_star"] = float(np.max(np.abs(qd.cpu().numpy() - q_star)))
     return out

@@ -250,6 +250,12 @@ typedef struct {
  *  q       device finest-level state, updated in place.  s: source or NULL.
  *  rep     optional report; with want_norm != 0 rep->rnorm is filled
  *          (synchronises the stream).
+ * With the environment variable DG_FUSED_SMOOTH=1 or 2, a smoothing block of
+ * a small level whose mortars are all conforming runs as one cooperative
+ * launch whose phases meet at grid barriers (same results; off by default).
+ * Their waits are bounded: should one run out, the cycle's state is void and
+ * the next call that reads a residual norm (want_norm, dg_residual with
+ * DG_NORM, dg_residual_norms, dg_solve_steady) returns DG_ECUDA.
  */
 int dg_pmg_vcycle(dg_mesh* mesh, double* q, const double* s, const dg_mg_params* mg,
                   int want_norm, dg_cycle_report* rep, void* stream);

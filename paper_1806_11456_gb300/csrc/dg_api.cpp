@@ -90,12 +90,22 @@ static int smooth_level(Cycle& C, Level* L, double* Q, const double* Sv, int swe
   // surface kernel writes the traces of the state it updates, so only the
   // block's first stage computes them from Q.
   double* dtb[2] = {C.m->d_scalars, C.m->d_scalars + 5 * C.m->nslots};
+  const double* hold = C.m->freeze ? C.m->d_scalars + 6 * C.m->nslots : nullptr;
+  if (sweeps > 0) {  // a small conforming level: the whole block in one cooperative launch
+    const int rc = smooth_block_fused(C.m, L, Q, Sv, sweeps, mask, hold, dtb[0], dtb[1], C.st);
+    if (rc == DG_OK) {
+      C.evals += 3 * sweeps;
+      C.dofs += 15.0 * sweeps * L->nodes;
+      return DG_OK;
+    }
+    if (rc != kNotFused) return rc;
+  }
   if (sweeps > 0) DG_TRY(cfl_dt(C.m, L, Q, dtb[0], C.st));
   for (int k = 0; k < sweeps; ++k) {
     double* dt = dtb[k & 1];
     double* dt_next = (k + 1 < sweeps) ? dtb[(k + 1) & 1] : nullptr;
     if (mask) DG_TRY(mask_dt(C.m, dt, mask, C.st));
-    if (C.m->freeze) DG_TRY(mask_dt(C.m, dt, C.m->d_scalars + 6 * C.m->nslots, C.st));  // held solves
+    if (hold) DG_TRY(mask_dt(C.m, dt, hold, C.st));  // held solves
     for (int stage = 0; stage < 3; ++stage) {
       const int tf = kTracesNext | ((k > 0 || stage > 0) ? kTracesCurrent : 0);
       DG_TRY(residual(C.m, L, Q, Sv, nullptr, false, C.st, nullptr, stage, L->d_G, dt, tf, dt_next));
@@ -252,9 +262,19 @@ static int smooth_tangent(Cycle& C, Level* L, const double* base, double* d, con
   // pseudo-time step of the linear problem from its linearisation point,
   // fixed during the block; slots whose mask is 0 get dt = 0 (held)
   double* dt = C.m->d_scalars;
+  const double* hold = C.m->freeze ? C.m->d_scalars + 6 * C.m->nslots : nullptr;
+  if (sweeps > 0) {  // a small conforming level: the whole block in one cooperative launch
+    const int rc = smooth_tangent_fused(C.m, L, base, d, b, sweeps, mask, hold, dt, C.st);
+    if (rc == DG_OK) {
+      C.evals += 3 * sweeps;
+      C.dofs += 15.0 * sweeps * L->nodes;
+      return DG_OK;
+    }
+    if (rc != kNotFused) return rc;
+  }
   if (sweeps > 0) DG_TRY(cfl_dt(C.m, L, base, dt, C.st));
   if (sweeps > 0 && mask) DG_TRY(mask_dt(C.m, dt, mask, C.st));
-  if (sweeps > 0 && C.m->freeze) DG_TRY(mask_dt(C.m, dt, C.m->d_scalars + 6 * C.m->nslots, C.st));
+  if (sweeps > 0 && hold) DG_TRY(mask_dt(C.m, dt, hold, C.st));
   for (int k = 0; k < sweeps; ++k)
     for (int stage = 0; stage < 3; ++stage) {
       const int tfl = kTracesNext | ((k > 0 || stage > 0) ? kTracesCurrent : 0);
@@ -342,6 +362,7 @@ static int level_norms(dg_mesh* m, Level* L, const double* Q, const double* Sv, 
   double* h = norms ? norms : tmp.data();
   DG_CUDA_TRY(cudaMemcpyAsync(h, dn, m->nslots * sizeof(double), cudaMemcpyDeviceToHost, st));
   DG_CUDA_TRY(cudaStreamSynchronize(st));
+  DG_TRY(fused_sync_check(m, st));
   double mx = 0.0;
   for (int k = 0; k < m->nslots; ++k) mx = (h[k] != h[k]) ? h[k] : std::max(mx, h[k]);
   if (out) *out = mx;
@@ -669,6 +690,7 @@ int dg_mesh_create(const dg_mesh_desc* desc, const int32_t* orders, dg_mesh** ou
     if (rc == DG_OK) rc = upload_gas(m);
     if (rc == DG_OK) {
       cudaError_t e1 = cudaMalloc(&m->d_scalars, (7 * m->nslots + 16) * sizeof(double));
+      if (e1 == cudaSuccess) e1 = cudaMemset(m->d_scalars, 0, (7 * m->nslots + 16) * sizeof(double));
       cudaError_t e2 = cudaMalloc(&m->d_tau, (size_t)m->K * 3 * kTauSlots * sizeof(double));
       cudaError_t e3 = cudaMalloc(&m->d_orders, m->orders.size() * sizeof(int32_t));
       if (e3 == cudaSuccess)
@@ -732,6 +754,7 @@ int dg_batch_create(const dg_mesh_desc* descs, const int32_t* const* orders, int
     if (rc == DG_OK) rc = upload_gas(m);
     if (rc == DG_OK) {
       cudaError_t e1 = cudaMalloc(&m->d_scalars, (7 * m->nslots + 16) * sizeof(double));
+      if (e1 == cudaSuccess) e1 = cudaMemset(m->d_scalars, 0, (7 * m->nslots + 16) * sizeof(double));
       cudaError_t e2 = cudaMalloc(&m->d_tau, (size_t)m->K * 3 * kTauSlots * sizeof(double));
       cudaError_t e3 = cudaMalloc(&m->d_orders, m->orders.size() * sizeof(int32_t));
       if (e3 == cudaSuccess)
@@ -913,6 +936,7 @@ int dg_residual(dg_mesh* m, const double* q, const double* s, double* r, int fla
       std::vector<double> h(m->nslots);
       DG_CUDA_TRY(cudaMemcpyAsync(h.data(), dnorm, m->nslots * sizeof(double), cudaMemcpyDeviceToHost, st));
       DG_CUDA_TRY(cudaStreamSynchronize(st));
+      DG_TRY(fused_sync_check(m, st));  // a fused smoothing block that failed voids the state
       double mx = 0.0;
       for (double v : h) mx = (v != v) ? v : std::max(mx, v);
       *rnorm_host = mx;

@@ -251,6 +251,18 @@ int transfer(const dg_mesh* m, const Level* from, const Level* to, int nvar, con
              cudaStream_t st, const double* sub = nullptr, bool accumulate = false);
 // max |x| per solve slot over a level vector (out zeroed here; device)
 int slot_maxabs(const dg_mesh* m, const Level* L, const double* x, double* out, cudaStream_t st);
+// One smoothing block of a small conforming level in a single cooperative
+// launch (k_smooth_block), the same bits as the separate launches.  They
+// return kNotFused, with nothing launched, when the level or the arithmetic
+// does not qualify; the caller then launches the stages one by one.
+constexpr int kNotFused = 1;
+int smooth_block_fused(const dg_mesh* m, Level* L, double* q, const double* s, int sweeps, const double* mask,
+                       const double* hold, double* dt0, double* dt1, cudaStream_t st);
+int smooth_tangent_fused(const dg_mesh* m, Level* L, const double* base, double* d, const double* b, int sweeps,
+                         const double* mask, const double* hold, double* dt, cudaStream_t st);
+// Reads (and clears) the fused kernel's barrier-failure flag: DG_ECUDA if a
+// grid barrier wait ran out since the last check.  Synchronises the stream.
+int fused_sync_check(const dg_mesh* m, cudaStream_t st);
 // dt[k] = 0 where mask[k] == 0 (nslots entries, device)
 int mask_dt(const dg_mesh* m, double* dt, const double* mask, cudaStream_t st);
 int fill(double* p, double v, int64_t n, cudaStream_t st);

@@ -715,13 +715,11 @@ DEV void write_face_traces(const LevelArgsT<R>& A, const ElemTile& t, const R* s
   }
 }
 
+// face traces of the state of one element tile (sq: 5 x tile nodes of shared memory)
 template <typename R, int DIM>
-__global__ void __launch_bounds__(kTileNodes) k_trace_q(LevelArgsT<R> A, const double* __restrict__ q,
-                                                        typename Store<R>::T* __restrict__ trq) {
-  pdl_enter();
-  extern __shared__ double smem_raw[];
-  R* sq = reinterpret_cast<R*>(smem_raw);
-  const ElemTile t = A.tiles[blockIdx.x];
+DEV void trace_tile(const LevelArgsT<R>& A, int tile, const double* __restrict__ q,
+                    typename Store<R>::T* __restrict__ trq, R* sq) {
+  const ElemTile t = A.tiles[tile];
   const int nn = t.n[0] * t.n[1] * t.n[2];
   const int T = t.count * nn;
   for (int i = threadIdx.x; i < T; i += blockDim.x) {
@@ -732,6 +730,14 @@ __global__ void __launch_bounds__(kTileNodes) k_trace_q(LevelArgsT<R> A, const d
   }
   __syncthreads();
   write_face_traces<R, DIM>(A, t, sq, T, trq);
+}
+
+template <typename R, int DIM>
+__global__ void __launch_bounds__(kTileNodes) k_trace_q(LevelArgsT<R> A, const double* __restrict__ q,
+                                                        typename Store<R>::T* __restrict__ trq) {
+  pdl_enter();
+  extern __shared__ double smem_raw[];
+  trace_tile<R, DIM>(A, blockIdx.x, q, trq, reinterpret_cast<R*>(smem_raw));
 }
 
 // ---------------------------------------------------------------------------
@@ -934,15 +940,13 @@ __global__ void __launch_bounds__(kMortarTile, 8) k_mortar(LevelArgsT<R> A, Mort
 // kernel, whose identity projection is an exact copy.
 constexpr int kMortarConfThreads = 32;  // one warp: spreads a level's warps evenly over the SMs
 
+// mortar node gp of a conforming level (no-op past the last node)
 template <typename R, int PASS>
-__global__ void __launch_bounds__(kMortarConfThreads, 12)
-    k_mortar_conf(LevelArgsT<R> A, MortarArgsT<R> MA, const GasT<R>* __restrict__ gas,
-                  const typename Store<R>::T* __restrict__ trq, const typename Store<R>::T* __restrict__ trg,
-                  typename Store<R>::T* __restrict__ out) {
-  pdl_enter();
+DEV void mortar_conf_node(const LevelArgsT<R>& A, const MortarArgsT<R>& MA, const GasT<R>* __restrict__ gas,
+                          const typename Store<R>::T* __restrict__ trq, const typename Store<R>::T* __restrict__ trg,
+                          typename Store<R>::T* __restrict__ out, int64_t gp) {
   using SR = Store<R>;
   constexpr int NV = (PASS == 1) ? 4 : 5;
-  const int64_t gp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (gp >= MA.mnodes) return;
   const MortarDev M = MA.mortars[MA.mnode_mortar[gp]];
   R o[5];
@@ -962,6 +966,15 @@ __global__ void __launch_bounds__(kMortarConfThreads, 12)
 #pragma unroll
     for (int v = 0; v < NV; ++v) SR::put(out, v * A.fn + dR, PASS == 2 ? -o[v] : o[v]);
   }
+}
+
+template <typename R, int PASS>
+__global__ void __launch_bounds__(kMortarConfThreads, 12)
+    k_mortar_conf(LevelArgsT<R> A, MortarArgsT<R> MA, const GasT<R>* __restrict__ gas,
+                  const typename Store<R>::T* __restrict__ trq, const typename Store<R>::T* __restrict__ trg,
+                  typename Store<R>::T* __restrict__ out) {
+  pdl_enter();
+  mortar_conf_node<R, PASS>(A, MA, gas, trq, trg, out, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
 }
 
 // k_mortar_conf_flux: the flux pass of k_mortar_conf with each node's work
@@ -1266,16 +1279,16 @@ DEV void divergence(const R* sD, const R* sA, int T, int nn, int i, int n0, int 
 // Register caps: 96 in 2D keeps five 128-thread CTAs per SM (a 100-register
 // build rounds to 104 and fits only four); 104 in 3D, 128 for the isolated
 // kernel in 3D (it spills at 104).
+// volume stage of one element tile: BR1 gradient (volume part + lifting of
+// U*), the gradient face traces, the nodal fluxes and the weak-form
+// divergence (smem_raw: 3 kNP^2 + 32 x tile nodes of shared memory)
 template <typename R, int DIM, bool AFFINE>
-__global__ void __launch_bounds__(kVolThreads) __maxnreg__(DIM == 2 ? 96 : 104) k_volume(LevelArgsT<R> A, int tile0, const GasT<R>* __restrict__ gas,
-                                                        const double* __restrict__ q,
-                                                        const typename Store<R>::T* __restrict__ ust,
-                                                        typename Store<R>::T* __restrict__ trg,
-                                                        typename Store<R>::T* __restrict__ vol) {
-  pdl_enter();
+DEV void volume_tile(const LevelArgsT<R>& A, int tile, const GasT<R>* __restrict__ gas,
+                     const double* __restrict__ q, const typename Store<R>::T* __restrict__ ust,
+                     typename Store<R>::T* __restrict__ trg, typename Store<R>::T* __restrict__ vol,
+                     double* smem_raw) {
   using SR = Store<R>;
-  extern __shared__ double smem_raw[];
-  const ElemTile t = A.tiles[tile0 + blockIdx.x];
+  const ElemTile t = A.tiles[tile];
   const int n0 = t.n[0], n1 = t.n[1], n2 = t.n[2];
   const int nn = n0 * n1 * n2;
   const int T = t.count * nn;
@@ -1370,6 +1383,17 @@ __global__ void __launch_bounds__(kVolThreads) __maxnreg__(DIM == 2 ? 96 : 104) 
   }
 }
 
+template <typename R, int DIM, bool AFFINE>
+__global__ void __launch_bounds__(kVolThreads) __maxnreg__(DIM == 2 ? 96 : 104) k_volume(LevelArgsT<R> A, int tile0, const GasT<R>* __restrict__ gas,
+                                                        const double* __restrict__ q,
+                                                        const typename Store<R>::T* __restrict__ ust,
+                                                        typename Store<R>::T* __restrict__ trg,
+                                                        typename Store<R>::T* __restrict__ vol) {
+  pdl_enter();
+  extern __shared__ double smem_raw[];
+  volume_tile<R, DIM, AFFINE>(A, tile0 + blockIdx.x, gas, q, ust, trg, vol, smem_raw);
+}
+
 // ---------------------------------------------------------------------------
 // k_volume_split: the same volume stage for levels with few warps per SM
 // ---------------------------------------------------------------------------
@@ -1448,14 +1472,12 @@ DEV void gradient_var(const LevelArgsT<R>& A, const R* sD, const R* sA, int T, i
 // The blockDim must be at least DIM x (the tile's nodes): the nodal-flux
 // phase reads every input of its item before a barrier and writes after it.
 template <typename R, int DIM, bool AFFINE>
-__global__ void __launch_bounds__(kVolThreads) __maxnreg__(DIM == 2 ? 96 : 104)
-    k_volume_split(LevelArgsT<R> A, int tile0, const GasT<R>* __restrict__ gas, const double* __restrict__ q,
-                   const typename Store<R>::T* __restrict__ ust, typename Store<R>::T* __restrict__ trg,
-                   typename Store<R>::T* __restrict__ vol) {
-  pdl_enter();
+DEV void volume_split_tile(const LevelArgsT<R>& A, int tile, const GasT<R>* __restrict__ gas,
+                           const double* __restrict__ q, const typename Store<R>::T* __restrict__ ust,
+                           typename Store<R>::T* __restrict__ trg, typename Store<R>::T* __restrict__ vol,
+                           double* smem_raw) {
   using SR = Store<R>;
-  extern __shared__ double smem_raw[];
-  const ElemTile t = A.tiles[tile0 + blockIdx.x];
+  const ElemTile t = A.tiles[tile];
   const int n0 = t.n[0], n1 = t.n[1], n2 = t.n[2];
   const int nn = n0 * n1 * n2;
   const int T = t.count * nn;
@@ -1571,6 +1593,15 @@ __global__ void __launch_bounds__(kVolThreads) __maxnreg__(DIM == 2 ? 96 : 104)
     SR::put(vol, (size_t)5 * A.off[e] + node + v * nn, acc);
   }
 }
+template <typename R, int DIM, bool AFFINE>
+__global__ void __launch_bounds__(kVolThreads) __maxnreg__(DIM == 2 ? 96 : 104)
+    k_volume_split(LevelArgsT<R> A, int tile0, const GasT<R>* __restrict__ gas, const double* __restrict__ q,
+                   const typename Store<R>::T* __restrict__ ust, typename Store<R>::T* __restrict__ trg,
+                   typename Store<R>::T* __restrict__ vol) {
+  pdl_enter();
+  extern __shared__ double smem_raw[];
+  volume_split_tile<R, DIM, AFFINE>(A, tile0 + blockIdx.x, gas, q, ust, trg, vol, smem_raw);
+}
 
 // ---------------------------------------------------------------------------
 // k_surface: surface terms, r = S - A; optional RK3 stage and max|r|
@@ -1619,18 +1650,18 @@ struct RKArgs {
   int nslots;
 };
 
+// surface stage of one element tile: the lifting of the face fluxes, 1/J,
+// r = S - A (or the RK3 stage update), optionally the updated state's face
+// traces and the next sweep's time step (smem_raw: 5 x tile nodes)
 template <typename R, int DIM>
-__global__ void __launch_bounds__(kTileNodes) k_surface(LevelArgsT<R> A, const typename Store<R>::T* __restrict__ vol,
-                                                        const typename Store<R>::T* __restrict__ fst,
-                                                        const double* __restrict__ s, double* __restrict__ r,
-                                                        double* norm, RKArgs rk) {
-  pdl_enter();
+DEV void surface_tile(const LevelArgsT<R>& A, int tile, const typename Store<R>::T* __restrict__ vol,
+                      const typename Store<R>::T* __restrict__ fst, const double* __restrict__ s,
+                      double* __restrict__ r, double* norm, const RKArgs& rk, double* smem_raw) {
   using SR = Store<R>;
-  extern __shared__ double smem_raw[];
   R* sq = reinterpret_cast<R*>(smem_raw);  // updated state (5 x T) when rk.trq_next is set
   const bool traces = rk.stage >= 0 && rk.trq_next != nullptr;
-  const ElemTile t = A.tiles[blockIdx.x];
-  if (rk.dt_next && rk.stage == 1 && blockIdx.x == 0)
+  const ElemTile t = A.tiles[tile];
+  if (rk.dt_next && rk.stage == 1 && tile == 0)
     for (int k = threadIdx.x; k < rk.nslots; k += blockDim.x) rk.dt_next[k] = 1e300;
   const bool cfl = rk.dt_next && rk.stage == 2;
   const int n0 = t.n[0], n1 = t.n[1], n2 = t.n[2];
@@ -1690,6 +1721,16 @@ __global__ void __launch_bounds__(kTileNodes) k_surface(LevelArgsT<R> A, const t
     __syncthreads();
     write_face_traces<R, DIM>(A, t, sq, T, static_cast<typename Store<R>::T*>(rk.trq_next));
   }
+}
+
+template <typename R, int DIM>
+__global__ void __launch_bounds__(kTileNodes) k_surface(LevelArgsT<R> A, const typename Store<R>::T* __restrict__ vol,
+                                                        const typename Store<R>::T* __restrict__ fst,
+                                                        const double* __restrict__ s, double* __restrict__ r,
+                                                        double* norm, RKArgs rk) {
+  pdl_enter();
+  extern __shared__ double smem_raw[];
+  surface_tile<R, DIM>(A, blockIdx.x, vol, fst, s, r, norm, rk, smem_raw);
 }
 
 // ---------------------------------------------------------------------------
@@ -1760,11 +1801,11 @@ __global__ void __launch_bounds__(kVolThreads) __maxnreg__(DIM == 2 ? 96 : 128) 
 // ---------------------------------------------------------------------------
 // k_cfl: global minimum of the explicit step (FP64)
 // ---------------------------------------------------------------------------
+// per-slot minimum of the explicit step over the nodes of one element tile
 template <int DIM>
-__global__ void __launch_bounds__(kTileNodes) k_cfl(LevelArgsT<double> A, const GasD* __restrict__ gasd,
-                                                    const double* __restrict__ q, double* dtmin) {
-  pdl_enter();
-  const ElemTile t = A.tiles[blockIdx.x];
+DEV void cfl_tile(const LevelArgsT<double>& A, int tile, const GasD* __restrict__ gasd, const double* __restrict__ q,
+                  double* dtmin) {
+  const ElemTile t = A.tiles[tile];
   const int n0 = t.n[0], n1 = t.n[1], n2 = t.n[2];
   const int nn = n0 * n1 * n2;
   const int T = t.count * nn;
@@ -1785,6 +1826,13 @@ __global__ void __launch_bounds__(kTileNodes) k_cfl(LevelArgsT<double> A, const 
     }
     warp_slot_reduce<false>(dtmin, slot, best, active);
   }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kTileNodes) k_cfl(LevelArgsT<double> A, const GasD* __restrict__ gasd,
+                                                    const double* __restrict__ q, double* dtmin) {
+  pdl_enter();
+  cfl_tile<DIM>(A, blockIdx.x, gasd, q, dtmin);
 }
 
 // ---------------------------------------------------------------------------
@@ -2370,6 +2418,322 @@ int residual(const dg_mesh* m, Level* L, const double* q, const double* s, doubl
     return residual_t<dd>(m, L, q, s, r, isolated, st, d_norm, rk_stage, rk_g, d_dt, trace_flags, dt_next);
   }
   return residual_t<double>(m, L, q, s, r, isolated, st, d_norm, rk_stage, rk_g, d_dt, trace_flags, dt_next);
+}
+
+// ---------------------------------------------------------------------------
+// k_smooth_block: one smoothing block (the CFL step, then `sweeps` RK3 sweeps
+// of trace / U* / volume / flux / surface stages) of a small conforming level
+// in one cooperative launch.  On such a level every kernel of the chain runs
+// a few CTAs whose time is one CTA's latency chain, and the launch gaps
+// between the ~13 launches of a sweep cost as much as the work.  Here the
+// stages are phases of one persistent kernel: each phase loops over its work
+// items (element tiles or 128 mortar nodes) with the per-item code of the
+// separate kernels, and phases are separated by a grid barrier.  Each output
+// is computed by the same operations in the same order as in the separate
+// kernels, so the results are the same bits.
+// ---------------------------------------------------------------------------
+// Grid barrier state (16 bytes of device memory per mesh, zeroed at
+// creation).  A cooperative launch makes every block resident, so a barrier
+// always completes; the wait is still bounded: a block that polls
+// kGridSyncSpins times records `failed` and the kernel returns, and later
+// launches return at entry until the host reads and clears the flag
+// (fused_sync_check).
+struct GridSync {
+  unsigned int count;
+  unsigned int gen;
+  int failed;
+  int pad;
+};
+constexpr unsigned int kGridSyncSpins = 1u << 21;  // about a second of polling (two L2 round trips a poll)
+
+// The block's writes are ordered before its arrival by the barrier and
+// thread 0's release (cumulative over the CTA); the others' writes are
+// visible after thread 0's acquire of the new generation and the barrier
+// that follows.
+DEV unsigned int ld_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+DEV bool grid_sync(GridSync* gs, unsigned int nblocks) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned int g, old;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(&gs->gen) : "memory");
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(&gs->count) : "memory");
+    if (old == nblocks - 1) {
+      asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(&gs->count) : "memory");
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&gs->gen) : "memory");  // release the others
+    } else {
+      unsigned int spins = 0;
+      volatile int* vfail = &gs->failed;
+      while (ld_acquire(&gs->gen) == g) {
+        if (++spins > kGridSyncSpins || *vfail) {
+          atomicExch(&gs->failed, 1);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <typename R>
+struct FusedArgs {
+  using ST = typename Store<R>::T;
+  LevelArgsT<R> A;    // A.base: the linearisation point of the tangent form (else null)
+  MortarArgsT<R> MA;
+  const GasT<R>* gas;
+  LevelArgsT<double> A64;  // FP64 geometry for the time step
+  const GasD* gasd;
+  const double* cfl_q;  // state the block's time step is computed from
+  double* q;            // state (or correction) updated in place
+  const double* s;      // source (or linear right-hand side)
+  double* g;            // RK register
+  double* dt0;
+  double* dt1;          // the next sweep's step (FAS form); unused when !dt_next
+  const double* mask;   // per slot: 0 holds the slot (smoothing control), or null
+  const double* hold;   // per slot: 0 holds the slot (held solves), or null
+  const double* geo64;
+  ST* trq;
+  ST* trg;
+  ST* ust;
+  ST* vol;
+  ST* fst;
+  double a[3], b[3];    // RK3 coefficients of the three stages
+  int64_t mnodes;
+  int mper;             // mortar nodes per block (a contiguous run: the level's nodes spread over every block)
+  int ntiles;
+  int nslots;
+  int sweeps;
+  int dt_next;          // 1: reduce the next sweep's step in the last stage (FAS form); 0: one step per block
+  int vsplit;           // 1: the volume phase takes the split form (the one k_volume_split runs)
+  GridSync* sync;
+};
+
+template <typename R, int DIM, bool AFFINE>
+__global__ void __launch_bounds__(kTileNodes, 1) k_smooth_block(FusedArgs<R> F) {
+  pdl_enter();
+  extern __shared__ double smem_raw[];
+  GridSync* gs = F.sync;
+  if (*reinterpret_cast<volatile int*>(&gs->failed)) return;
+  const unsigned int nb = gridDim.x;
+  const int64_t m0 = (int64_t)blockIdx.x * F.mper;  // this block's run of mortar nodes
+  // the block's first time step (the work of k_fill and k_cfl)
+  if (blockIdx.x == 0)
+    for (int j = threadIdx.x; j < F.nslots; j += blockDim.x) F.dt0[j] = 1e300;
+  if (!grid_sync(gs, nb)) return;
+  for (int w = blockIdx.x; w < F.ntiles; w += gridDim.x) cfl_tile<DIM>(F.A64, w, F.gasd, F.cfl_q, F.dt0);
+  if (!grid_sync(gs, nb)) return;
+  for (int k = 0; k < F.sweeps; ++k) {
+    double* dt = (F.dt_next && (k & 1)) ? F.dt1 : F.dt0;
+    double* dtn = (F.dt_next && k + 1 < F.sweeps) ? ((k & 1) ? F.dt0 : F.dt1) : nullptr;
+    if (F.mask || F.hold) {  // (the work of k_mask_dt)
+      if (blockIdx.x == 0)
+        for (int j = threadIdx.x; j < F.nslots; j += blockDim.x) {
+          if (F.mask && F.mask[j] == 0.0) dt[j] = 0.0;
+          if (F.hold && F.hold[j] == 0.0) dt[j] = 0.0;
+        }
+      if (!grid_sync(gs, nb)) return;
+    }
+    for (int stage = 0; stage < 3; ++stage) {
+      if (k == 0 && stage == 0) {  // the block's first traces; later ones come from the surface phase
+        for (int w = blockIdx.x; w < F.ntiles; w += gridDim.x) {
+          trace_tile<R, DIM>(F.A, w, F.q, F.trq, reinterpret_cast<R*>(smem_raw));
+          __syncthreads();
+        }
+        if (!grid_sync(gs, nb)) return;
+      }
+      for (int i = threadIdx.x; i < F.mper; i += blockDim.x)
+        mortar_conf_node<R, 1>(F.A, F.MA, F.gas, F.trq, nullptr, F.ust, m0 + i);
+      if (!grid_sync(gs, nb)) return;
+      for (int w = blockIdx.x; w < F.ntiles; w += gridDim.x) {
+        if (F.vsplit)
+          volume_split_tile<R, DIM, AFFINE>(F.A, w, F.gas, F.q, F.ust, F.trg, F.vol, smem_raw);
+        else
+          volume_tile<R, DIM, AFFINE>(F.A, w, F.gas, F.q, F.ust, F.trg, F.vol, smem_raw);
+        __syncthreads();
+      }
+      if (!grid_sync(gs, nb)) return;
+      for (int i = threadIdx.x; i < F.mper; i += blockDim.x)
+        mortar_conf_node<R, 2>(F.A, F.MA, F.gas, F.trq, F.trg, F.fst, m0 + i);
+      if (!grid_sync(gs, nb)) return;
+      RKArgs rk;
+      rk.stage = stage;
+      rk.a = F.a[stage];
+      rk.b = F.b[stage];
+      rk.g = F.g;
+      rk.dt = dt;
+      rk.qupd = F.q;
+      rk.trq_next = F.trq;
+      rk.dt_next = dtn;
+      rk.gasd = dtn ? F.gasd : nullptr;
+      rk.geo64 = dtn ? F.geo64 : nullptr;
+      rk.nslots = dtn ? F.nslots : 0;
+      for (int w = blockIdx.x; w < F.ntiles; w += gridDim.x) {
+        surface_tile<R, DIM>(F.A, w, F.vol, F.fst, F.s, nullptr, nullptr, rk, smem_raw);
+        __syncthreads();
+      }
+      if (k + 1 < F.sweeps || stage < 2)
+        if (!grid_sync(gs, nb)) return;
+    }
+  }
+}
+
+// DG_FUSED_SMOOTH=0 (default) never fuses, 1 fuses levels with at most
+// kFusedMaxTiles element tiles, 2 every level that qualifies.  The results
+// are the same bits either way; the knob selects the launch form only.
+// Measured on GB300 (CUDA events, V-cycles replayed from graphs), separate
+// launches / fused blocks (1):
+//   periodic 3x3x3 box, N = 2, V 2 -> 1, 3/3/10 sweeps: FP64 2.00 / 2.41 ms,
+//     mixed form 1.52 / 1.90 ms
+//   flat plate 60x24, N = 7, V 7 -> 1, 2/2/4 sweeps (N <= 3 fused): FP64
+//     6.60 / 6.98 ms, mixed form 3.20 / 3.64 ms
+//   4x4x1 box to 1e-10 (550 cycles): FP64 1.59 / 1.92 s
+// A grid barrier costs about 2 us more than the gap between two kernels
+// launched back to back with programmatic dependent launch (in a graph or
+// not), so fusing does not pay while each phase is one warp's latency chain.
+static int fused_mode() {
+  static const int mode = [] {
+    const char* e = std::getenv("DG_FUSED_SMOOTH");
+    return e ? std::atoi(e) : 0;
+  }();
+  return mode;
+}
+constexpr int kFusedMaxTiles = 304;  // two tiles per SM
+
+static GridSync* fused_sync(const dg_mesh* m) { return reinterpret_cast<GridSync*>(m->d_scalars + 7 * m->nslots); }
+
+template <typename R, int DIM, bool AFF>
+static int launch_fused(const dg_mesh* m, const Level* L, FusedArgs<R> F, cudaStream_t st) {
+  // shared memory: the volume phase's staging of a tile of at most 128 nodes
+  // (37.5 KB, below the default limit, so no attribute is set per device)
+  static_assert((3 * kNP * kNP + 32 * kTileNodes) * sizeof(double) <= 48 * 1024, "fused kernel shared memory");
+  const size_t smem = std::max((size_t)(3 * kNP * kNP + 32 * L->tile_smem_nodes), (size_t)(5 * L->tile_smem_nodes)) *
+                      sizeof(double);
+  // resident blocks per SM at the largest shared memory (the grid never exceeds what is co-resident)
+  static const int occ = [] {
+    int v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_smooth_block<R, DIM, AFF>, kTileNodes,
+                                                      (3 * kNP * kNP + 32 * kTileNodes) * sizeof(double)) !=
+        cudaSuccess)
+      return 0;
+    return v;
+  }();
+  if (occ < 1) return kNotFused;
+  // one block per tile, or per 32 mortar nodes where those are more (the
+  // separate kernels' one-warp mortar CTAs), up to what is co-resident
+  const int64_t mwarps = (F.mnodes + 31) / 32;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(std::max<int64_t>(F.ntiles, mwarps),
+                                                                (int64_t)occ * sm_count_cached()));
+  F.mper = (int)((F.mnodes + grid - 1) / grid);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kTileNodes);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  count_launch();
+  DG_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_smooth_block<R, DIM, AFF>, F));
+  return DG_OK;
+}
+
+template <typename R>
+static int smooth_fused_t(const dg_mesh* m, Level* L, double* q, const double* s, const double* cfl_q,
+                          const double* base, int sweeps, bool dt_next, const double* mask, const double* hold,
+                          double* dt0, double* dt1, cudaStream_t st) {
+  FusedArgs<R> F;
+  F.A = largs<R>(L);
+  F.A.base = base;
+  F.MA = margs<R>(L);
+  F.gas = gas_table<R>(m);
+  F.A64 = largs<double>(L);
+  F.gasd = m->d_gasd;
+  F.cfl_q = cfl_q;
+  F.q = q;
+  F.s = s;
+  F.g = L->d_G;
+  F.dt0 = dt0;
+  F.dt1 = dt1;
+  F.mask = mask;
+  F.hold = hold;
+  F.geo64 = L->d_geo;
+  F.trq = buf<R>(L->d_trq);
+  F.trg = buf<R>(L->d_trg);
+  F.ust = buf<R>(L->d_ust);
+  F.vol = buf<R>(L->d_vol);
+  F.fst = buf<R>(L->d_fst);
+  for (int k = 0; k < 3; ++k) {
+    const RKArgs rk = rk_args(k, nullptr, nullptr, nullptr);
+    F.a[k] = rk.a;
+    F.b[k] = rk.b;
+  }
+  F.mnodes = L->mortar_nodes;
+  F.ntiles = L->n_tiles;
+  F.nslots = m->nslots;
+  F.sweeps = sweeps;
+  F.dt_next = dt_next ? 1 : 0;
+  // (the split form needs at least DIM threads per tile node: 128 threads cover tiles of up to 128 / DIM nodes;
+  // larger tiles take the plain form, the same bits)
+  F.vsplit = (volume_split(L, std::is_same<R, double>::value) && L->tile_class_nodes[0] * L->dim <= kTileNodes) ? 1 : 0;
+  F.mper = 0;
+  F.sync = fused_sync(m);
+  if (L->dim == 2)
+    return L->affine ? launch_fused<R, 2, true>(m, L, F, st) : launch_fused<R, 2, false>(m, L, F, st);
+  return L->affine ? launch_fused<R, 3, true>(m, L, F, st) : launch_fused<R, 3, false>(m, L, F, st);
+}
+
+static bool fused_eligible(const Level* L) {
+  const int mode = fused_mode();
+  if (mode == 0 || !L->mortars_conforming || L->n_tiles < 1) return false;
+  if (L->tile_class_end[0] != L->n_tiles || L->tile_class_nodes[0] > kTileNodes) return false;  // 128-node tiles only
+  if (mode == 1 && L->n_tiles > kFusedMaxTiles) return false;
+  static const int coop = [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess)
+      return 0;
+    return v;
+  }();
+  return coop != 0;
+}
+
+int smooth_block_fused(const dg_mesh* m, Level* L, double* q, const double* s, int sweeps, const double* mask,
+                       const double* hold, double* dt0, double* dt1, cudaStream_t st) {
+  if (sweeps < 1 || m->arith == DG_ARITH_DF32 || !fused_eligible(L)) return kNotFused;  // FP64 operator only
+  int rc = configure_smem();
+  if (rc != DG_OK) return rc;
+  return smooth_fused_t<double>(m, L, q, s, q, nullptr, sweeps, true, mask, hold, dt0, dt1, st);
+}
+
+int smooth_tangent_fused(const dg_mesh* m, Level* L, const double* base, double* d, const double* b, int sweeps,
+                         const double* mask, const double* hold, double* dt, cudaStream_t st) {
+  if (sweeps < 1 || !fused_eligible(L)) return kNotFused;
+  int rc = configure_smem();
+  if (rc != DG_OK) return rc;
+  if ((rc = ensure_tf(L, st)) != DG_OK) return rc;
+  return smooth_fused_t<tf>(m, L, d, b, base, base, sweeps, false, mask, hold, dt, dt, st);
+}
+
+int fused_sync_check(const dg_mesh* m, cudaStream_t st) {
+  GridSync h{};
+  DG_CUDA_TRY(cudaMemcpyAsync(&h, fused_sync(m), sizeof(h), cudaMemcpyDeviceToHost, st));
+  DG_CUDA_TRY(cudaStreamSynchronize(st));
+  if (h.failed) {
+    DG_CUDA_TRY(cudaMemsetAsync(fused_sync(m), 0, sizeof(GridSync), st));
+    DG_CUDA_TRY(cudaStreamSynchronize(st));
+    set_error("fused smoothing kernel: a grid barrier wait ran out (results of the cycle are void)");
+    return DG_ECUDA;
+  }
+  return DG_OK;
 }
 
 template <typename R>
