@@ -63,6 +63,9 @@ def parse():
                     help="also run the steady driver with adaptation on the flat plate (several minutes)")
     ap.add_argument("--serving-large", action="store_true",
                     help="also serve larger requests (1e4-5e4 DOF, random order maps; a few minutes)")
+    ap.add_argument("--steady-adapt", action="store_true",
+                    help="also run the whole steady driver with adaptation to 1e-10 on the 24x8 plate, FP64 and "
+                         "mixed (several minutes)")
     ap.add_argument("--mg-compare", type=int, default=0, metavar="CYCLES",
                     help="also compare isotropic and anisotropic V-cycles on the flat plate for CYCLES cycles "
                          "(about a second per cycle; off by default)")
@@ -659,6 +662,43 @@ def c2_solve(dg, torch, dev, tau_max=1e-2, tol=1e-6, max_cycles=400):
             "seconds": secs, "report": rep, "nodes_before": int(mesh["K"] * 64), "orders_histogram": hist}
 
 
+def steady_adapt_plate(dg, torch, dev, tau_max=1e-4, tol=1e-10, max_cycles=6000, mixed_from=1e-3):
+    """The whole steady driver with adaptation (Sec. 3.1.1 full multigrid,
+    Sec. 3.3.2) on the physical flat-plate problem (S = 0) of the
+    plate-shaped variant's mesh: 24 x 8 uniform elements of size 0.05 with
+    the flat-plate boundary conditions, Mach 0.2, Re 1e4, impulsive
+    freestream start at N = 4.  Full multigrid to 1e-1 per order, V-cycles
+    of 10/10/40 sweeps under the smoothing control (at most 10 blocks,
+    eta 1.1) to tau_max/10, the isolated anisotropic tau estimate, orders in
+    [1, 6]^2 with the jump limit, V-cycles to tol.  FP64 against the mixed
+    form, which runs the FAS cycle while max|r| >= mixed_from (its
+    linearisation does not hold at the impulsive start)."""
+    from paper_1806_11456_gb300 import synthetic as syn
+    mesh = syn.flat_plate_mesh(nx=24, ny=8, dy0=0.05, ratio=1.0)
+    prm = syn.flow_params(mach=0.2, re=1e4)
+    o = syn.uniform_orders(mesh["K"], 2, 4)
+    out = {"workload": "flat plate 24x8 uniform h=0.05, Mach 0.2, Re 1e4, S = 0, freestream start at N = 4",
+           "driver": f"FMG (1e-1) -> V 10/10/40 controlled (10 blocks, eta 1.1) to tau_max/10 -> tau -> adapt "
+                     f"[1,6]^2 (jump 1) -> V to {tol}", "tau_max": tau_max, "tol": tol}
+    for arith in ("fp64", "mixed"):
+        M = dg.Mesh(mesh, o, prm).set_arithmetic(arith)
+        q = torch.tensor(syn.freestream_state(mesh, o, prm), device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        q2, rep = M.solve_steady(q, None, tol=tol, max_cycles=max_cycles, fmg=True, fmg_tol=0.1, adapt=True,
+                                 tau_max=tau_max, n_min=1, n_max=6, jump_rule=1, check_every=10,
+                                 mixed_from=mixed_from if arith == "mixed" else 0.0,
+                                 mg=dict(beta1=10, beta2=10, beta_c=40, control=10, eta=1.1, graph=0))
+        torch.cuda.synchronize()
+        hist = {}
+        for nx, ny in M.orders[:, :2]:
+            hist[f"{nx},{ny}"] = hist.get(f"{nx},{ny}", 0) + 1
+        out[arith] = {"seconds": time.perf_counter() - t0, "report": rep, "orders_histogram": hist,
+                      "mixed_from": mixed_from if arith == "mixed" else None}
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    return out
+
+
 def mg_compare(dg, torch, dev, cycles):
     """Isotropic vs anisotropic FAS V-cycles (Sec. 3.3.1: coarsening in one
     reference direction per cycle, alternating xi and eta) on the flat plate
@@ -993,6 +1033,8 @@ def run_gb300(args, rank, world):
             out["c2_solve"] = c2_solve(dg, torch, dev)
         if args.serving_large:
             out["serving_large"] = serving_large(dg, torch, dev)
+        if args.steady_adapt:
+            out["steady_adapt_plate"] = steady_adapt_plate(dg, torch, dev)
         if args.mg_compare > 0:
             out["mg_compare"] = mg_compare(dg, torch, dev, args.mg_compare)
         out["cpu_baseline"] = cpu_baseline_sample(mesh, prm, orders, q_np) if world == 1 else None

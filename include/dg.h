@@ -315,8 +315,12 @@ typedef struct {
   double ref_factor;       /* reference solves converge to ref_factor * tau_max (paper: 1/10; <= 0 means 0.1) */
   int32_t check_every;     /* residual checked after every k-th V-cycle (<= 1: every cycle); a phase
                               may run up to k - 1 cycles past its target */
-  int32_t arith;           /* DG_ARITH_FP64 or DG_ARITH_DF32 for a solve run by the serving loop (which
-                              owns the mesh); dg_solve_steady itself uses the mesh's own setting */
+  int32_t arith;           /* DG_ARITH_FP64, DG_ARITH_DF32 or DG_ARITH_MIXED for a solve run by the serving
+                              loop (which owns the mesh); dg_solve_steady itself uses the mesh's setting */
+  double mixed_from;       /* DG_ARITH_MIXED only: > 0 runs the FP64 FAS cycle while the last checked
+                              max |r| >= mixed_from (full multigrid, the start of each phase) and the
+                              mixed defect correction below it, whose linearisation holds only near a
+                              solution; <= 0: the mixed cycle throughout */
 } dg_solve_params;
 
 typedef struct {

@@ -398,12 +398,13 @@ static int cycle_levels(dg_mesh* m, const std::vector<int32_t>& top_orders, cons
 // mg.graph the launch sequence is captured once per (orders, Q, Sv,
 // parameters) on a library stream and replayed on `st` afterwards.
 static int run_vcycle(dg_mesh* m, const std::vector<int32_t>& top_orders, double* Q, const double* Sv,
-                      const dg_mg_params& mg, cudaStream_t st, int* evals, double* dofs, int* nlev) {
+                      const dg_mg_params& mg, cudaStream_t st, int* evals, double* dofs, int* nlev,
+                      bool fas = false) {
   Cycle C{m, st, mg, {}, 0, 0.0};
   DG_TRY(cycle_levels(m, top_orders, mg, &C.lv));
   *nlev = (int)C.lv.size();
   for (Level* L : C.lv) DG_TRY(prepare_arith(m, L, st));  // never allocate inside a capture
-  const bool mixed = m->arith == DG_ARITH_MIXED;
+  const bool mixed = m->arith == DG_ARITH_MIXED && !fas;  // fas: the FP64 FAS cycle on a mixed-form mesh
   if (!mg.graph || mg.control > 0) {  // controlled sweep counts are decided on the host
     DG_TRY(mixed ? mixed_cycle(C, Q, Sv) : vcycle_level(C, 0, Q, Sv));
     *evals = C.evals;
@@ -415,6 +416,7 @@ static int run_vcycle(dg_mesh* m, const std::vector<int32_t>& top_orders, double
   key.append((const char*)ptrs, sizeof(ptrs));
   key.append((const char*)&mg, sizeof(mg));
   key.push_back(m->freeze ? 'h' : '-');
+  key.push_back(mixed ? 'm' : 'f');
   auto it = m->graphs.find(key);
   if (it == m->graphs.end()) {
     DG_TRY(prepare_capture());
@@ -1115,9 +1117,13 @@ int dg_profile_residual(dg_mesh* m, const double* q, const double* s, double* r,
 
 // Cycle (Q, Sv) with top orders `o` until max|r| < target or `cap` cycles;
 // *cycles counts them.  Returns DG_OK, DG_ENOTCONVERGED or DG_EDIVERGED.
+// V-cycles until max|r| < target (checked every `every` cycles).  On a
+// mixed-form mesh with mixed_from > 0, cycles whose last checked residual is
+// at least mixed_from run the FP64 FAS cycle instead of the defect
+// correction, whose linearisation holds only near a solution.
 static int cycle_until(dg_mesh* m, const std::vector<int32_t>& o, Level* L, double* Q, const double* Sv,
                        const dg_mg_params& mg, double target, int cap, cudaStream_t st, int* cycles, double* dofs,
-                       double* rn, int every = 1) {
+                       double* rn, int every = 1, double mixed_from = 0.0) {
   DG_TRY(level_norm(m, L, Q, Sv, st, rn));
   dofs[0] += 5.0 * L->nodes;
   every = std::max(1, every);
@@ -1127,10 +1133,11 @@ static int cycle_until(dg_mesh* m, const std::vector<int32_t>& o, Level* L, doub
     } else {
       return DG_OK;
     }
+    const bool fas = m->arith == DG_ARITH_MIXED && mixed_from > 0.0 && !(*rn < mixed_from);
     for (int k = 0; k < every && c < cap; ++k, ++c) {
       int ev = 0, nl = 0;
       double dd = 0.0;
-      DG_TRY(run_vcycle(m, o, Q, Sv, mg, st, &ev, &dd, &nl));
+      DG_TRY(run_vcycle(m, o, Q, Sv, mg, st, &ev, &dd, &nl, fas));
       dofs[0] += dd;
       (*cycles)++;
     }
@@ -1178,7 +1185,7 @@ int dg_solve_steady(dg_mesh** meshp, double** qp, const double* s, const dg_solv
         if (s) DG_TRY(transfer(m, m->fine.get(), L, 5, s, L->d_S, st));
         int cyc = 0;
         rc = cycle_until(m, o, L, L->d_Q, s ? L->d_S : nullptr, mg, sp->fmg_tol, sp->max_cycles, st, &cyc,
-                         &rep->dof_evals, &rn, sp->check_every);
+                         &rep->dof_evals, &rn, sp->check_every, sp->mixed_from);
         rep->cycles += cyc;
         rep->fmg_cycles += cyc;
         if (rc == DG_EDIVERGED) break;
@@ -1192,7 +1199,7 @@ int dg_solve_steady(dg_mesh** meshp, double** qp, const double* s, const dg_solv
       const double ref = sp->ref_factor > 0.0 ? sp->ref_factor : 0.1;
       double target = sp->adapt ? sp->ap.tau_max * ref : sp->tol;
       int cyc = 0;
-      rc = cycle_until(m, m->orders, m->fine.get(), q, s, mg, target, sp->max_cycles, st, &cyc, &rep->dof_evals, &rn, sp->check_every);
+      rc = cycle_until(m, m->orders, m->fine.get(), q, s, mg, target, sp->max_cycles, st, &cyc, &rep->dof_evals, &rn, sp->check_every, sp->mixed_from);
       rep->cycles += cyc;
     }
     // ---- adaptation (Sec. 3.3.2), possibly in stages (Sec. 3.3.4) ----
@@ -1203,7 +1210,7 @@ int dg_solve_steady(dg_mesh** meshp, double** qp, const double* s, const dg_solv
           int cyc = 0;
           const double ref = sp->ref_factor > 0.0 ? sp->ref_factor : 0.1;
           rc = cycle_until(m, m->orders, m->fine.get(), q, nullptr, mg, sp->ap.tau_max * ref, sp->max_cycles, st,
-                           &cyc, &rep->dof_evals, &rn, sp->check_every);
+                           &cyc, &rep->dof_evals, &rn, sp->check_every, sp->mixed_from);
           rep->cycles += cyc;
           if (rc != DG_OK) break;
         }
@@ -1259,7 +1266,7 @@ int dg_solve_steady(dg_mesh** meshp, double** qp, const double* s, const dg_solv
       if (rc == DG_OK) {
         int cyc = 0;
         rc = cycle_until(m, m->orders, m->fine.get(), q, nullptr, mg, sp->tol, sp->max_cycles, st, &cyc,
-                         &rep->dof_evals, &rn, sp->check_every);
+                         &rep->dof_evals, &rn, sp->check_every, sp->mixed_from);
         rep->cycles += cyc;
       }
     }

@@ -236,7 +236,11 @@ int top_order(const Request& r) {
   return top;
 }
 
-bool batchable(const Request& r) { return !r.sp.adapt && !r.sp.fmg; }
+// (a mixed-form request that starts in the FAS form switches per its own
+// residual, which a shared cycle cannot do for each member: it runs alone)
+bool batchable(const Request& r) {
+  return !r.sp.adapt && !r.sp.fmg && !(r.sp.arith == DG_ARITH_MIXED && r.sp.mixed_from > 0.0);
+}
 
 bool same_cycle(const dg_mg_params& a, const dg_mg_params& b) {
   return a.beta1 == b.beta1 && a.beta2 == b.beta2 && a.beta_c == b.beta_c && a.direction == b.direction &&

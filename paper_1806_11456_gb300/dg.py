@@ -76,7 +76,8 @@ class SolveParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_cycles", ctypes.c_int32), ("fmg", ctypes.c_int32),
                 ("fmg_tol", ctypes.c_double), ("mg", MGParams), ("adapt", ctypes.c_int32),
                 ("n_stages", ctypes.c_int32), ("ap", AdaptParams), ("stage_orders", ctypes.c_int32 * 4),
-                ("ref_factor", ctypes.c_double), ("check_every", ctypes.c_int32), ("arith", ctypes.c_int32)]
+                ("ref_factor", ctypes.c_double), ("check_every", ctypes.c_int32), ("arith", ctypes.c_int32),
+                ("mixed_from", ctypes.c_double)]
 
 
 _lib = None
@@ -181,7 +182,8 @@ def kernel_launches():
 
 
 def solve_params(tol=1e-10, max_cycles=200, fmg=False, fmg_tol=1e-1, mg=None, adapt=False, tau_max=1e-4, n_min=1,
-                 n_max=7, jump_rule=1, conform_tag=-1, cap=0, stages=(), ref_factor=0.1, check_every=1, arith="fp64"):
+                 n_max=7, jump_rule=1, conform_tag=-1, cap=0, stages=(), ref_factor=0.1, check_every=1, arith="fp64",
+                 mixed_from=0.0):
     """dg_solve_params from keyword arguments (mg: dict of dg_mg_params fields)."""
     sp = SolveParams()
     sp.tol, sp.max_cycles, sp.fmg, sp.fmg_tol, sp.adapt = float(tol), int(max_cycles), int(bool(fmg)), \
@@ -200,6 +202,7 @@ def solve_params(tol=1e-10, max_cycles=200, fmg=False, fmg_tol=1e-1, mg=None, ad
         sp.stage_orders[i] = int(v)
     sp.check_every = int(check_every)
     sp.arith = ARITH[arith]
+    sp.mixed_from = float(mixed_from)
     return sp
 
 
@@ -397,13 +400,13 @@ class Mesh:
 
     def solve_steady(self, q, s=None, tol=1e-10, max_cycles=200, fmg=False, fmg_tol=1e-1, mg=None, adapt=False,
                      tau_max=1e-4, n_min=1, n_max=7, jump_rule=1, conform_tag=-1, cap=0, stages=(), ref_factor=0.1,
-                     check_every=1, stream=None):
+                     check_every=1, mixed_from=0.0, stream=None):
         """Steady solve through dg_solve_steady.  Returns (q, report); with
         adaptation q is a new tensor on the adapted mesh, which this object
         then wraps (its orders are updated)."""
         import torch
         sp = solve_params(tol, max_cycles, fmg, fmg_tol, mg, adapt, tau_max, n_min, n_max, jump_rule, conform_tag,
-                          cap, stages, ref_factor, check_every)
+                          cap, stages, ref_factor, check_every, mixed_from=mixed_from)
         keep = []
 
         def _alloc(nbytes, _ctx):

@@ -233,3 +233,34 @@ def test_mixed_steady_solve_satisfies_the_fp64_equations(dg):
           dev64, devm, "mixed mean part:", np.max(np.abs(mean)), "rest:", rest)
     scale = np.max(np.abs(q_star))
     assert dev64 <= 1e-12 * scale and devm <= 1e-10 * scale
+
+
+def test_mixed_solve_starts_in_the_fas_form_above_mixed_from(dg):
+    """dg_solve_params.mixed_from: on a mixed-form mesh, cycles whose last
+    checked residual is at least mixed_from run the FP64 FAS cycle.  With a
+    threshold below every residual the solve is the FP64 solve, bit for bit
+    (same cycles, same state); with 1e-3 it starts in the FAS form, switches
+    to the defect correction, and its result satisfies the oracle's FP64
+    equations to the tolerance (from a start 20 % away, with full multigrid,
+    from which the defect correction alone diverges)."""
+    mesh, o, prm, q_star = syn.manufactured_box_4x4x1()
+    S = orc.operator_A(mesh, o, prm, q_star)
+    q0 = syn.zero_mean_wave(mesh, o, q_star, 11, amp=0.2)
+    kw = dict(tol=1e-10, max_cycles=3000, fmg=True, fmg_tol=1e-1, mg=dict(beta1=3, beta2=3, beta_c=10),
+              check_every=10)
+    A = dg.Mesh(mesh, o, prm)
+    qa, ra = A.solve_steady(_dev(q0), _dev(S), **kw)
+    B = dg.Mesh(mesh, o, prm).set_arithmetic("mixed")
+    qb, rb = B.solve_steady(_dev(q0), _dev(S), mixed_from=1e-300, **kw)
+    assert ra["status"] == 0 and rb["cycles"] == ra["cycles"]
+    assert np.array_equal(qa.cpu().numpy(), qb.cpu().numpy())
+    C = dg.Mesh(mesh, o, prm).set_arithmetic("mixed")
+    qc, rc = C.solve_steady(_dev(q0), _dev(S), mixed_from=1e-3, **kw)
+    assert rc["status"] == 0, rc
+    qcn = qc.cpu().numpy()
+    ro = orc.residual(mesh, o, prm, qcn, S)
+    D = dg.Mesh(mesh, o, prm).set_arithmetic("mixed")
+    _, rd = D.solve_steady(_dev(q0), _dev(S), **kw)
+    print("cycles fp64 / switched:", ra["cycles"], rc["cycles"], "defect correction alone:", rd)
+    assert np.max(np.abs(ro)) <= 1e-10 + TOL * orc.volume_scale(mesh, o, prm, qcn)
+
