@@ -695,7 +695,8 @@ def steady_adapt_plate(dg, torch, dev, tau_max=1e-4, tol=1e-10, max_cycles=6000,
             hist[f"{nx},{ny}"] = hist.get(f"{nx},{ny}", 0) + 1
         out[arith] = {"seconds": time.perf_counter() - t0, "report": rep, "orders_histogram": hist,
                       "mixed_from": mixed_from if arith == "mixed" else None}
-    out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    both = out["fp64"]["report"]["status"] == 0 and out["mixed"]["report"]["status"] == 0
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"] if both else None
     return out
 
 
