@@ -510,49 +510,46 @@ static void select_element(const double* tab /* 3 x 16 */, const int32_t* P, con
   DirFit F[3];
   for (int i = 0; i < dim; ++i) F[i] = fit_dir(tab + i * kTauSlots, P[i]);
   // each direction's estimate over the candidate range, evaluated once
-  double tab_at[3][kTauSlots + 1];
+  double tab_at[3][kTauSlots + 1];  // (orders <= n_max < kTauSlots, checked by dg_adapt)
   const int top = std::max(hi, 1);
   for (int i = 0; i < dim; ++i)
     for (int N = 0; N <= top && N <= kTauSlots; ++N) tab_at[i][N] = F[i].at(N);
-  auto at = [&](int i, int N) { return N <= kTauSlots ? tab_at[i][N] : F[i].at(N); };
+  // Candidates in lexicographic order (the last direction fastest); the
+  // first one with the fewest degrees of freedom and, among those, the
+  // smallest estimate wins, so a later candidate never wins a full tie.  The
+  // estimate is summed over the directions in order (0 + t_0 + t_1 + t_2).
   auto search = [&](const int* lo, const int* up, int32_t* best) -> bool {
+    for (int i = 0; i < dim; ++i)
+      if (up[i] < lo[i]) return false;
     bool found = false;
     long bestdof = 0;
     double besttau = 0.0;
-    int N[3] = {0, 0, 0};
-    int cur[3] = {lo[0], dim > 1 ? lo[1] : 0, dim > 2 ? lo[2] : 0};
-    for (int i = 0; i < dim; ++i)
-      if (up[i] < lo[i]) return false;
-    while (true) {
-      for (int i = 0; i < dim; ++i) N[i] = cur[i];
-      double tv = 0.0;
-      for (int i = 0; i < dim; ++i) tv += at(i, N[i]);
-      if (tv < ap.tau_max) {
-        long dof = 1;
-        for (int i = 0; i < dim; ++i) dof *= (N[i] + 1);
-        bool better = !found || dof < bestdof || (dof == bestdof && tv < besttau);
-        if (!better && found && dof == bestdof && tv == besttau) {
-          // lexicographically smaller order triple
-          for (int i = 0; i < dim; ++i) {
-            if (N[i] < best[i]) { better = true; break; }
-            if (N[i] > best[i]) break;
-          }
-        }
-        if (better) {
-          found = true;
-          bestdof = dof;
-          besttau = tv;
-          for (int i = 0; i < dim; ++i) best[i] = N[i];
+    auto consider = [&](double tv, long dof, int a, int b, int c) {
+      if (!(tv < ap.tau_max)) return;
+      if (found && !(dof < bestdof || (dof == bestdof && tv < besttau))) return;
+      found = true;
+      bestdof = dof;
+      besttau = tv;
+      best[0] = a;
+      best[1] = b;
+      best[2] = c;
+    };
+    if (dim == 1) {
+      for (int a = lo[0]; a <= up[0]; ++a) consider(0.0 + tab_at[0][a], a + 1, a, 0, 0);
+    } else if (dim == 2) {
+      for (int a = lo[0]; a <= up[0]; ++a) {
+        const double ta = 0.0 + tab_at[0][a];
+        for (int b = lo[1]; b <= up[1]; ++b) consider(ta + tab_at[1][b], (long)(a + 1) * (b + 1), a, b, 0);
+      }
+    } else {
+      for (int a = lo[0]; a <= up[0]; ++a) {
+        const double ta = 0.0 + tab_at[0][a];
+        for (int b = lo[1]; b <= up[1]; ++b) {
+          const double tb = ta + tab_at[1][b];
+          for (int c = lo[2]; c <= up[2]; ++c)
+            consider(tb + tab_at[2][c], (long)(a + 1) * (b + 1) * (c + 1), a, b, c);
         }
       }
-      // advance the last direction fastest (lexicographic enumeration)
-      int i = dim - 1;
-      while (i >= 0) {
-        if (++cur[i] <= up[i]) break;
-        cur[i] = lo[i];
-        --i;
-      }
-      if (i < 0) break;
     }
     return found;
   };
@@ -605,21 +602,34 @@ static int limit_jumps(const dg_mesh* m, std::vector<int32_t>& o, int rule, int 
         const int32_t* ft = &m->ftab[(size_t)(e * 6 + f) * 4];
         if (ft[0] < 0 && ft[3] == conform_tag) touches[e] = 1;
       }
+  // each interior face once: the neighbour and, per direction, the
+  // neighbour's direction it faces (fixed across the sweeps)
+  struct Link {
+    int e, nb, mp[3];
+    bool conform;
+  };
+  std::vector<Link> links;
+  links.reserve((size_t)K * 2 * dim);
+  for (int e = 0; e < K; ++e)
+    for (int f = 0; f < 2 * dim; ++f) {
+      const int32_t* ft = &m->ftab[(size_t)(e * 6 + f) * 4];
+      if (ft[0] < 0) continue;
+      Link l;
+      l.e = e;
+      l.nb = ft[0];
+      face_map(f, ft[1], ft[2], l.mp);
+      l.conform = conform_tag >= 0 && touches[e] && touches[ft[0]];
+      links.push_back(l);
+    }
+  std::vector<int32_t> nw(o.size());
   for (int it = 0; it < 100000; ++it) {
-    std::vector<int32_t> nw = o;
-    for (int e = 0; e < K; ++e)
-      for (int f = 0; f < 2 * dim; ++f) {
-        const int32_t* ft = &m->ftab[(size_t)(e * 6 + f) * 4];
-        int nb = ft[0];
-        if (nb < 0) continue;
-        int mp[3];
-        face_map(f, ft[1], ft[2], mp);
-        for (int i = 0; i < dim; ++i) {
-          int other = o[nb * 3 + mp[i]];
-          int need = (rule == 1) ? other - 1 : (rule == 2 ? (2 * other) / 3 : 0);
-          if (conform_tag >= 0 && touches[e] && touches[nb]) need = std::max(need, other);
-          if (need > nw[e * 3 + i]) nw[e * 3 + i] = need;
-        }
+    nw = o;
+    for (const Link& l : links)
+      for (int i = 0; i < dim; ++i) {
+        const int other = o[l.nb * 3 + l.mp[i]];
+        int need = (rule == 1) ? other - 1 : (rule == 2 ? (2 * other) / 3 : 0);
+        if (l.conform) need = std::max(need, other);
+        if (need > nw[l.e * 3 + i]) nw[l.e * 3 + i] = need;
       }
     if (nw == o) return DG_OK;
     o.swap(nw);
@@ -1095,8 +1105,10 @@ int dg_adapt(const dg_mesh* m, const double* tau_host, const dg_adapt_params* ap
       return DG_EINVAL;
     }
     std::vector<int32_t> o((size_t)m->K * 3, 0);
-    for (int e = 0; e < m->K; ++e)
-      select_element(tau_host + (size_t)e * 3 * kTauSlots, &m->orders[e * 3], *ap, m->dim, &o[e * 3]);
+    parallel_for(m->K, [&](int e0, int e1) {  // elements are independent (about 1 us each)
+      for (int e = e0; e < e1; ++e)
+        select_element(tau_host + (size_t)e * 3 * kTauSlots, &m->orders[e * 3], *ap, m->dim, &o[e * 3]);
+    }, 128);
     if (ap->jump_rule == 1 || ap->jump_rule == 2 || ap->conform_tag >= 0)
       DG_TRY(limit_jumps(m, o, ap->jump_rule, ap->conform_tag));
     std::memcpy(new_orders, o.data(), o.size() * sizeof(int32_t));

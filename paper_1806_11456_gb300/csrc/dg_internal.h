@@ -3,11 +3,13 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <map>
 #include <mutex>
 #include <memory>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/dg.h"
@@ -251,6 +253,26 @@ int transfer(const dg_mesh* m, const Level* from, const Level* to, int nvar, con
              cudaStream_t st, const double* sub = nullptr, bool accumulate = false);
 // max |x| per solve slot over a level vector (out zeroed here; device)
 int slot_maxabs(const dg_mesh* m, const Level* L, const double* x, double* out, cudaStream_t st);
+// Runs f(begin, end) on contiguous blocks of [0, n) on up to 16 host threads,
+// at least `grain` items a thread (one block, on the calling thread, when n
+// is small).  Every f must write only its own block.
+template <class F>
+void parallel_for(int n, F f, int grain = 256) {
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int nt = (int)std::min<unsigned>(std::min(hw, 16u), (unsigned)std::max(1, n / std::max(1, grain)));
+  if (nt <= 1) {
+    f(0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int t = 1; t < nt; ++t) {
+    const int b = (int)((int64_t)n * t / nt), e = (int)((int64_t)n * (t + 1) / nt);
+    th.emplace_back([=, &f] { f(b, e); });
+  }
+  f(0, (int)((int64_t)n / nt));
+  for (auto& x : th) x.join();
+}
+
 // One smoothing block of a small conforming level in a single cooperative
 // launch (k_smooth_block), the same bits as the separate launches.  They
 // return kNotFused, with nothing launched, when the level or the arithmetic

@@ -336,24 +336,6 @@ int dev_upload(int64_t* acc, T** dst, const std::vector<T>& src) {
   return DG_OK;
 }
 
-// Runs f(begin, end) on contiguous blocks of [0, n) on up to 16 host threads
-// (one block when n is small).  Every f must write only its own block.
-template <class F>
-void parallel_for(int n, F f) {
-  unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-  int nt = (int)std::min<unsigned>(std::min(hw, 16u), (unsigned)std::max(1, n / 256));
-  if (nt <= 1) {
-    f(0, n);
-    return;
-  }
-  std::vector<std::thread> th;
-  for (int t = 0; t < nt; ++t) {
-    int b = (int)((int64_t)n * t / nt), e = (int)((int64_t)n * (t + 1) / nt);
-    th.emplace_back([=, &f] { f(b, e); });
-  }
-  for (auto& x : th) x.join();
-}
-
 int dev_zeros(int64_t* acc, double** dst, size_t n) {
   DG_CUDA_TRY(cudaMalloc((void**)dst, std::max<size_t>(1, n) * sizeof(double)));
   *acc += (int64_t)(std::max<size_t>(1, n) * sizeof(double));
