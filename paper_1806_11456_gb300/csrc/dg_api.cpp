@@ -1105,10 +1105,10 @@ int dg_adapt(const dg_mesh* m, const double* tau_host, const dg_adapt_params* ap
       return DG_EINVAL;
     }
     std::vector<int32_t> o((size_t)m->K * 3, 0);
-    parallel_for(m->K, [&](int e0, int e1) {  // elements are independent (about 1 us each)
-      for (int e = e0; e < e1; ++e)
-        select_element(tau_host + (size_t)e * 3 * kTauSlots, &m->orders[e * 3], *ap, m->dim, &o[e * 3]);
-    }, 128);
+    // (on the calling thread: at a few hundred ns an element, starting host
+    // threads costs more than it saves for meshes of a few thousand elements)
+    for (int e = 0; e < m->K; ++e)
+      select_element(tau_host + (size_t)e * 3 * kTauSlots, &m->orders[e * 3], *ap, m->dim, &o[e * 3]);
     if (ap->jump_rule == 1 || ap->jump_rule == 2 || ap->conform_tag >= 0)
       DG_TRY(limit_jumps(m, o, ap->jump_rule, ap->conform_tag));
     std::memcpy(new_orders, o.data(), o.size() * sizeof(int32_t));

@@ -1693,17 +1693,28 @@ DEV void surface_tile(const LevelArgsT<R>& A, int tile, const typename Store<R>:
       }
       const R iJ = SR::get(A.geo, 9 * A.nodes + A.off[e] + node);
       const double dt = (rk.stage >= 0) ? rk.dt[slot] : 0.0;
+      // every load of the node's source, state and RK register before any
+      // store (the stores go through pointers the compiler cannot tell apart)
+      double sv[5], qo[5], go[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sv[v] = s ? s[base + v * nn] : 0.0;
+      if (rk.stage >= 0) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) qo[v] = rk.qupd[base + v * nn];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) go[v] = (dt != 0.0 && rk.stage != 0) ? rk.g[base + v * nn] : 0.0;
+      }
       double qnew[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        const double rv = (s ? s[base + v * nn] : 0.0) - to_double(acc[v] * iJ);
+        const double rv = sv[v] - to_double(acc[v] * iJ);
         lmax = (rv != rv) ? INFINITY : fmax(lmax, fabs(rv));  // a NaN residual reads as +inf
         if (rk.stage < 0) {
           r[base + v * nn] = rv;
         } else {
-          double qn = rk.qupd[base + v * nn];
+          double qn = qo[v];
           if (dt != 0.0) {  // dt = 0: the solve is held (smoothing control)
-            double gv = (rk.stage == 0 ? 0.0 : rk.a * rk.g[base + v * nn]) + dt * rv;
+            double gv = (rk.stage == 0 ? 0.0 : rk.a * go[v]) + dt * rv;
             rk.g[base + v * nn] = gv;
             qn += rk.b * gv;
             rk.qupd[base + v * nn] = qn;
@@ -1723,8 +1734,9 @@ DEV void surface_tile(const LevelArgsT<R>& A, int tile, const typename Store<R>:
   }
 }
 
+// (at least five CTAs per SM: a 720-tile level stays in one wave)
 template <typename R, int DIM>
-__global__ void __launch_bounds__(kTileNodes) k_surface(LevelArgsT<R> A, const typename Store<R>::T* __restrict__ vol,
+__global__ void __launch_bounds__(kTileNodes, 5) k_surface(LevelArgsT<R> A, const typename Store<R>::T* __restrict__ vol,
                                                         const typename Store<R>::T* __restrict__ fst,
                                                         const double* __restrict__ s, double* __restrict__ r,
                                                         double* norm, RKArgs rk) {
