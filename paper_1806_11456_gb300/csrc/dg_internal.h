@@ -205,6 +205,10 @@ struct dg_mesh {
 
 namespace dg {
 int build_level(const dg_mesh* m, const std::vector<int32_t>& orders, Level* L);
+// The metric terms of one element as build_level computes them (host only):
+// Ja[node][i][c] = (J a^i)_c (9 per node) and J[node] at the element's Gauss
+// nodes, node counts n[3], from its (M+1)^dim mapping nodes (3 doubles each).
+void element_geometry_host(int M, int dim, const double* xmap_elem, const int n[3], double* Ja, double* J);
 Level* get_level(dg_mesh* m, const std::vector<int32_t>& orders);
 int ensure_work(Level* L);
 // (re)build a level's element tile lists with `pack` nodes per tile for small elements

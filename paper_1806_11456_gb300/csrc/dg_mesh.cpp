@@ -351,6 +351,14 @@ int dev_zeros(int64_t* acc, double** dst, size_t n) {
     if (_rc != DG_OK) return _rc; \
   } while (0)
 
+void element_geometry_host(int M, int dim, const double* xmap_elem, const int n[3], double* Ja, double* J) {
+  MapEval ME(M, dim);
+  std::vector<double> a, j;
+  element_geometry(ME, xmap_elem, n, dim, a, j);
+  std::copy(a.begin(), a.end(), Ja);
+  std::copy(j.begin(), j.end(), J);
+}
+
 std::mutex& device_sync_mutex() {
   static std::mutex mu;
   return mu;
